@@ -1,0 +1,391 @@
+#!/usr/bin/env python
+"""Benchmark of the Galerkin boundary-integral hot path on GB300.
+
+Workload (default): N = 1024 active spheres at volume fraction 0.05, truncation
+l <= 3 (25 higher components per sphere), harmonic trap k = 0.01, V^a = 0.1 p,
+V^(2s) = 0.05 (pp - I/3).  One step = trap inputs from (R, p), the full
+traction solve (FP64 right-hand-side pass, restarted GMRES with FP32 pair sums
+and FP64 Arnoldi, FP64 iterative refinement to ||b - A q|| / ||b|| <= 1e-10,
+FP64 output pass) and one forward-Euler update, all inside libgbi.
+
+Metric: pair-interactions/s (ordered pairs summed over every pair pass of the
+step) and solves/s.  Also reported: the roofline of the dominant kernel (event
+timed live in the timed region), the end-to-end number through the host-pointer
+C-ABI call, the N = 10^4 superposition pass, and the FP64 CPU oracle timed on
+a bounded sample on this machine's cores.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank solves its own replica of the workload.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "pair-interactions/s & Galerkin solves/s at stated error vs FP64; % FP32 peak"
+UNIT = "pair-interactions/s"
+FP64_NOMINAL_TFLOPS = 1.25          # GB300 FP64 (recipe's nominal figure)
+SMS, FP32_LANES = 152, 128
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def fp32_alu_peak_tflops(sm_mhz):
+    return SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- oracle baseline
+
+def oracle_pair_rate(R, trunc, a, npairs, seed=0):
+    """FP64 oracle (dense pair blocks + apply) on a sample of ordered pairs: pairs/s."""
+    import numpy as np
+
+    from oracle import galerkin
+    rng = np.random.default_rng(seed)
+    N = len(R)
+    n = rng.integers(0, N, size=npairs)
+    m = (n + rng.integers(1, N, size=npairs)) % N
+    d = galerkin.ModeBasis(trunc).d
+    x = rng.normal(size=(npairs, d))
+    galerkin.pair_blocks(R[:2] - R[1:3], a, trunc)        # warm the weight tables
+    t0 = time.perf_counter()
+    blocks = galerkin.pair_blocks(R[n] - R[m], a, trunc)
+    y = np.einsum("kpq,kq->kp", blocks, x)
+    dt = time.perf_counter() - t0
+    assert np.all(np.isfinite(y))
+    return npairs / dt, dt
+
+
+def blas_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        info = threadpool_info()
+        n = [i.get("num_threads") for i in info if i.get("user_api") == "blas"]
+        if n:
+            return int(max(n))
+    except Exception:
+        pass
+    return os.cpu_count()
+
+
+# ----------------------------------------------------------------------------- distributed
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import workloads
+    c = workloads.config2()
+    npairs = 3000
+    for _ in range(args.warmup):
+        oracle_pair_rate(c["R"], 3, c["a"], 200)
+    total_pairs, total_t = 0, 0.0
+    for k in range(args.steps):
+        rate, dt = oracle_pair_rate(c["R"], 3, c["a"], npairs, seed=k)
+        total_pairs += npairs
+        total_t += dt
+    value = total_pairs / total_t
+    cores = blas_threads()
+    sample = "%d random ordered pairs of the N=1024 l<=3 suspension per step (dense 31x31 pair blocks + apply)" % npairs
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": c["name"], "N": 1024, "trunc": 3},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_1411_0278_gb300 as gbi
+    import workloads
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    ctx = gbi.Context(local, stream=stream)
+
+    c = workloads.config2()
+    N, trunc = len(c["R"]), c["trunc"]
+    dt = 0.1
+    prm = gbi.params(a=c["a"], eta=c["eta"], trunc=trunc, precision=1, rtol=1e-10, restart=40, inner_rtol=1e-5)
+    R0 = torch.tensor(c["R"], dtype=torch.float64, device=dev)
+    p0 = torch.tensor(c["p"], dtype=torch.float64, device=dev)
+    R, p = R0.clone(), p0.clone()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    def step():
+        return ctx.trap_step(prm, R, p, dt, c["k"], c["vs"], c["s0"], c["d0"], False, 1)
+
+    # ---- accuracy statement (outside the timed region): mixed vs all-FP64 on the GPU
+    inp = ctx.trap_inputs(N, trunc, c["k"], c["vs"], c["s0"], c["d0"], R0, p0)
+    V1, O1, Q1, i1, _ = ctx.solve(prm, R0, inp["Va"], inp["Oa"], inp["VH"], inp["Fe"], inp["Te"])
+    prm64 = gbi.params(a=c["a"], eta=c["eta"], trunc=trunc, precision=0, rtol=1e-10, restart=40)
+    V0, O0, Q0, i0, _ = ctx.solve(prm64, R0, inp["Va"], inp["Oa"], inp["VH"], inp["Fe"], inp["Te"])
+    torch.cuda.synchronize(dev)
+
+    def rel(a, b):
+        return float((a - b).abs().max() / b.abs().max())
+    err = {"V_rel": rel(V1, V0), "Omega_rel": rel(O1, O0), "QH_rel": rel(Q1, Q0),
+           "mixed_residual": i1.rel_residual, "fp64_residual": i0.rel_residual,
+           "mixed_iters": i1.iters, "mixed_refinements": i1.refinements, "fp64_iters": i0.iters}
+
+    # ---- warm-up
+    for _ in range(max(3, args.warmup)):
+        step()
+    R.copy_(R0)
+    p.copy_(p0)
+    barrier()
+
+    # ---- timed region
+    sampler = ClockSampler(local)
+    sampler.start()
+    ctx.set_profiling(True)
+    launches0 = ctx.kernel_launches()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    total_ms = 0.0
+    pairs = 0
+    barrier()
+    for _ in range(args.steps):
+        flush.fill_(1.0)                    # evict the L2 between timed steps
+        ev0.record(stream)
+        info = step()
+        ev1.record(stream)
+        ev1.synchronize()
+        total_ms += ev0.elapsed_time(ev1)
+        pairs += info.pair_interactions
+    barrier()
+    launches = ctx.kernel_launches() - launches0
+    stats = {cls: ctx.kernel_stats(cls) for cls in range(20)}
+    ctx.set_profiling(False)
+    clocks = sampler.stop()
+
+    t_local = total_ms / 1e3
+    if world > 1:
+        tt = torch.tensor([t_local, float(pairs)], dtype=torch.float64, device=dev)
+        tmax = tt.clone()
+        torch.distributed.all_reduce(tmax[:1], op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(tt[1:], op=torch.distributed.ReduceOp.SUM)
+        t_job, pairs_job = float(tmax[0]), float(tt[1])
+    else:
+        t_job, pairs_job = t_local, float(pairs)
+    value = pairs_job / t_job
+    solves_per_s = world * args.steps / t_job
+
+    # ---- dominant kernel and its roofline
+    peaks, peak_src = load_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    names = {17: "pair_kernel<l3, H, H, float>", 8: "pair_kernel<l3, H, H, double>",
+             7: "pair_kernel<l3, H, L, double>", 3: "pair_kernel<l3, L, all, double>"}
+    dom = max(stats, key=lambda k: stats[k]["ms"])
+    st = stats[dom]
+    avg_ms = st["ms"] / max(1, st["launches"])
+    flops_per_launch = st["flops"] / max(1, st["launches"])
+    achieved = flops_per_launch / (avg_ms * 1e-3) / 1e12
+    is_f32 = dom in (17, 19) or (9 <= dom < 18)
+    peak = fp32_alu_peak_tflops(sm_max) if is_f32 else FP64_NOMINAL_TFLOPS
+    kernel_share = {names.get(k, "class%d" % k): round(v["ms"] / max(1e-9, sum(s["ms"] for s in stats.values())), 4)
+                    for k, v in stats.items() if v["launches"]}
+    roofline = {"bound": "alu", "kernel": names.get(dom, "class%d" % dom), "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": ("FP32 CUDA-core peak 152 SMs x 128 lanes x 2 x %.0f MHz (sm_max_mhz of %s "
+                                "MEASURED_PEAKS.json)" % (sm_max, peak_src)) if is_f32 else
+                               "GB300 FP64 nominal 1.25 TFLOP/s",
+                "flops_per_launch": flops_per_launch, "avg_launch_ms": avg_ms, "launches": st["launches"],
+                "time_share": kernel_share}
+
+    # ---- end to end through the host-pointer C ABI (H2D + solve + D2H per step)
+    h = gbi.h(trunc)
+    pin = lambda shape: torch.zeros(shape, dtype=torch.float64).pin_memory()
+    hR, hVa, hOa, hVH, hFe, hTe = (pin((N, 3)), pin((N, 3)), pin((N, 3)), pin((N, h)), pin((N, 3)), pin((N, 3)))
+    hR.copy_(R0.cpu())
+    hVa.copy_(inp["Va"].cpu())
+    hOa.copy_(inp["Oa"].cpu())
+    hVH.copy_(inp["VH"].cpu())
+    hFe.copy_(inp["Fe"].cpu())
+    hTe.copy_(inp["Te"].cpu())
+    hV, hOm, hQH = pin((N, 3)), pin((N, 3)), pin((N, h))
+    ptrs = [t.data_ptr() for t in (hR, hVa, hOa, hVH, hFe, hTe, hV, hOm, hQH)]
+    for _ in range(2):
+        ctx.solve_host_ptrs(prm, N, ptrs)
+    barrier()
+    e_pairs, e_t = 0, 0.0
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        info, _ = ctx.solve_host_ptrs(prm, N, ptrs)
+        e_t += time.perf_counter() - t0
+        e_pairs += info.pair_interactions
+    barrier()
+    h2d = 8 * N * (5 * 3 + h)
+    d2h = 8 * N * (2 * 3 + h)
+    e2e = {"value": e_pairs / e_t, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+           "solves_per_s": args.steps / e_t, "call": "gbi_solve_host (pinned host buffers, one solve per step)"}
+
+    # ---- secondary: superposition trap pass at N = 10^4 (closed-form kernel, FP32)
+    c3 = workloads.config3()
+    R3 = torch.tensor(c3["R"], dtype=torch.float64, device=dev)
+    p3 = torch.tensor(c3["p"], dtype=torch.float64, device=dev)
+    in3 = ctx.trap_inputs(len(R3), 2, c3["k"], c3["vs"], c3["s0"], c3["d0"], R3, p3)
+    prm3 = gbi.params(a=c3["a"], eta=c3["eta"], trunc=2, precision=1)
+    V3 = torch.empty_like(R3)
+    O3 = torch.empty_like(R3)
+    for _ in range(3):
+        ctx.superpose(prm3, R3, in3["Va"], in3["Oa"], in3["VH"], in3["Fe"], in3["Te"], V3, O3)
+    ctx.set_profiling(True)
+    barrier()
+    ev0.record(stream)
+    n3 = 20
+    for _ in range(n3):
+        ctx.superpose(prm3, R3, in3["Va"], in3["Oa"], in3["VH"], in3["Fe"], in3["Te"], V3, O3)
+    ev1.record(stream)
+    ev1.synchronize()
+    t3 = ev0.elapsed_time(ev1) / 1e3
+    s3 = ctx.kernel_stats(gbi._native.TRAP_F32)
+    ctx.set_profiling(False)
+    N3 = len(R3)
+    ach3 = s3["flops"] / (s3["ms"] * 1e-3) / 1e12
+    superposition = {"workload": c3["name"], "N": N3, "value": n3 * N3 * (N3 - 1) / t3, "unit": UNIT,
+                     "ms_per_pass": 1e3 * t3 / n3,
+                     "roofline": {"bound": "alu", "kernel": "trap_kernel<float>", "achieved": ach3,
+                                  "peak": fp32_alu_peak_tflops(sm_max), "unit": "TFLOP/s",
+                                  "frac": ach3 / fp32_alu_peak_tflops(sm_max), "traffic": None,
+                                  "avg_launch_ms": s3["ms"] / max(1, s3["launches"])},
+                     "note": "inputs resident (L2-sized), not flushed"}
+
+    if rank == 0:
+        # ---- CPU baseline: the oracle on a bounded sample, this machine's cores
+        rate, dtc = oracle_pair_rate(c["R"], trunc, c["a"], 12000)
+        cpu = {"value": rate, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+               "sample": "12000 random ordered pairs of the N=1024 l<=3 suspension, dense FP64 31x31 pair "
+                         "blocks + apply (%.1f s)" % dtc}
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "precision": "FP32 pair sums in GMRES; FP64 RHS, residuals, Arnoldi, Givens, outputs",
+                "data": "synthetic",
+                "config": {"workload": c["name"], "N": N, "trunc": trunc, "h": h, "volume_fraction": 0.05,
+                           "min_sep_a": 2.5, "rtol": 1e-10, "restart": 40, "inner_rtol": 1e-5,
+                           "step": "trap inputs + full Galerkin solve + Euler update",
+                           "l2": "flushed (256 MB write) before every timed step",
+                           "parallelism": "replicas" if world > 1 else "single GPU"},
+                "solves_per_s": solves_per_s, "error_vs_fp64": err, "roofline": roofline,
+                "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
+                "superposition": superposition}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

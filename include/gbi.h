@@ -1,0 +1,186 @@
+/*
+ * gbi.h -- C ABI of the GB300 Galerkin boundary-integral library for N active
+ * spheres (Singh, Ghose & Adhikari, "Many-body microhydrodynamics of colloidal
+ * particles with active boundary layers").
+ *
+ * Problem statement (Sec. II, Eq. boundary_conditions; Sec. III): N spheres of
+ * radius a in an unbounded fluid of viscosity eta, centres R_n, with active slip
+ * described by the one-body velocities V^a_n, Omega^a_n and the higher velocity
+ * coefficients V^(l sigma)_n; external forces F^e_n and torques T^e_n.  Outputs:
+ * the rigid-body motion V_n, Omega_n (Eq. genralized_active_stokes_law) and the
+ * solved flow coefficients Q^(l sigma)_n (Eq. generalized_Qlsigma).
+ *
+ * Conventions shared by every call:
+ *  - All array arguments are DEVICE pointers owned by the caller (for example
+ *    torch tensors), unless the function name ends in _host.  They must not alias.
+ *  - Row-major, double precision.  Vectors are [N][3] (x, y, z).
+ *  - Packed higher coefficients VH, QH are [N][h] with h = gbi_h(trunc).  The
+ *    modes follow each other in the order 2s 3t | 3a 3s 4t | 4a 4s 5t (l<=2 keeps
+ *    the first two, l<=3 the first five, l<=4 all eight).  A mode whose
+ *    irreducible tensor has rank k takes 2k+1 slots: the coordinates of that
+ *    symmetric traceless tensor in the orthonormal basis U_mu (mu = -k..k) with
+ *    U_mu . x^k = N_k r^k Y_{k mu}(x), real spherical harmonics without the
+ *    Condon-Shortley phase, N_k^2 = 4 pi k!/(2k+1)!!.  For k = 1 this is
+ *    (y, z, x).  The tensors are those of Sec. III, Eq. irred_velocity_coefficients:
+ *    V^(L) = V^(L0) - (L-1)/L Delta(eps.V^(L1)) + L(L-1)/(2(2L-1)) Delta(delta V^(L2)).
+ *  - Calls are asynchronous on the context's stream (gbi_set_stream) except where
+ *    noted; the library allocates only inside its context workspace, which grows
+ *    on the first call for a given size and is then reused.
+ *  - Errors are returned as gbi_status; no call aborts the process.  A CUDA
+ *    error is returned as GBI_ERR_CUDA and its text is kept for gbi_last_error().
+ */
+#ifndef GBI_H
+#define GBI_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GBI_OK = 0,
+  GBI_ERR_ARG = 1,            /* invalid argument (NULL pointer, N < 0, bad truncation, NaN input) */
+  GBI_ERR_OVERLAP = 2,        /* two centres closer than params.min_sep * a (nothing computed)      */
+  GBI_ERR_NOT_CONVERGED = 3,  /* iteration cap reached; outputs hold the best iterate               */
+  GBI_ERR_TIMEOUT = 4,        /* a bounded device wait gave up                                      */
+  GBI_ERR_CUDA = 5,           /* CUDA runtime error (see gbi_last_error)                            */
+  GBI_ERR_NOMEM = 6           /* workspace allocation failed                                        */
+} gbi_status;
+
+typedef struct gbi_ctx gbi_ctx;
+
+typedef struct {
+  double a;          /* sphere radius                                                    */
+  double eta;        /* viscosity                                                        */
+  int trunc;         /* 2, 3 or 4: mode set 1s 2a | 2s 3t (+3a 3s 4t) (+4a 4s 5t)        */
+  int precision;     /* 0: FP64 pair sums throughout; 1: FP32 pair sums inside GMRES,     */
+                     /*    FP64 residuals (iterative refinement)                         */
+  double rtol;       /* target relative residual ||b - A q|| / ||b|| of the traction solve */
+  int restart;       /* GMRES restart length (Krylov vectors per cycle), 1..128          */
+  int max_iter;      /* cap on inner GMRES iterations over the whole solve               */
+  int max_refine;    /* cap on refinement sweeps (precision = 1)                         */
+  double inner_rtol; /* relative tolerance of each inner FP32 solve (precision = 1)      */
+  double min_sep;    /* overlap guard: reject pairs closer than min_sep * a (0 = off)    */
+} gbi_params;
+
+typedef struct {
+  int iters;                 /* inner GMRES iterations                                   */
+  int refinements;           /* FP64 residual evaluations after the first                */
+  int matvecs_f32;           /* FP32 pair passes                                         */
+  int matvecs_f64;           /* FP64 pair passes                                         */
+  double rel_residual;       /* final ||b - A q|| / ||b|| in FP64                        */
+  double min_separation;     /* smallest centre distance seen, in units of a             */
+  long long pair_interactions; /* ordered pairs evaluated, summed over all pair passes   */
+} gbi_info;
+
+/* Library handle.  gbi_create binds the calling thread's device `device`
+ * (cudaSetDevice) and creates no stream: work goes to the legacy default stream
+ * until gbi_set_stream is called.  Returns GBI_ERR_ARG for a NULL `out`. */
+gbi_status gbi_create(gbi_ctx** out, int device);
+gbi_status gbi_destroy(gbi_ctx* ctx);
+/* stream: a cudaStream_t (may be NULL = default stream). */
+gbi_status gbi_set_stream(gbi_ctx* ctx, void* stream);
+/* Block until all work queued by the context has finished. */
+gbi_status gbi_synchronize(gbi_ctx* ctx);
+const char* gbi_status_string(int status);
+/* Text of the last CUDA error seen by this context ("" if none). */
+const char* gbi_last_error(gbi_ctx* ctx);
+
+/* Number of packed H components per sphere (8, 25, 48) or all components
+ * including the six rigid-body ones (14, 31, 54); -1 for an invalid truncation. */
+int gbi_h(int trunc);
+int gbi_d(int trunc);
+
+/* Internal coordinate scale c per packed component (length gbi_d(trunc), host
+ * pointer): x = c * y, where x are the coordinates in which the pair operator of
+ * gbi_apply is symmetric.  The first six are 1s (y,z,x) then 2a (y,z,x). */
+gbi_status gbi_component_scales(int trunc, double* out_host);
+/* One-body self scalars g (units 1/a, host pointer, length gbi_d(trunc)):
+ * 8 pi eta V^(l sigma) = -(g/a) Q^(l sigma) for an isolated sphere. */
+gbi_status gbi_self_scalars(int trunc, double* out_host);
+
+/* Pair operator (Sec. III, Eq. single_layer_yl_matrix_element, m != n) in internal
+ * coordinates: for every sphere n and every row component p,
+ *     y[p][n] = alpha * ( sum_{m != n} sum_q G_nm[p][q] x[q][m] + add_self * (g_p/a) x[p][n] )
+ *               + beta * y[p][n].
+ * x, y are component-major: x[q*N + m].  rows / cols select the components:
+ * 0 = all (gbi_d), 1 = rigid-body (first 6), 2 = higher (last gbi_h); x and y point
+ * at the first component of their set.  add_self requires rows == cols.
+ * precision 0 = FP64 arithmetic, 1 = FP32 arithmetic (FP64 in/out).
+ * R: [N][3] centres.  Cost: N(N-1) pair interactions. */
+gbi_status gbi_apply(gbi_ctx* ctx, int N, int trunc, double a, int rows, int cols, int precision,
+                     const double* R, const double* x, double* y, double alpha, double beta, int add_self);
+
+/* Full Galerkin solve (Sec. II, Eq. many_body_active_passive_stresses and
+ * Eq. many_body_active_VL, in the flow-coefficient form): solves
+ *     G^HH Q^H = -8 pi eta V^H - G^HL F^L
+ * by restarted GMRES (FP64 Arnoldi and Givens least squares; FP32 or FP64 pair
+ * sums per params.precision), then
+ *     8 pi eta (V - V^a, 2a (Omega - Omega^a)) = -G^LL F^L - G^LH Q^H,
+ * with F^(1) = -F^e and F^(21) = -T^e / a.
+ * Inputs R, Va, Oa, Fe, Te: [N][3]; VH: [N][h] packed.  Outputs V, Omega: [N][3];
+ * QH: [N][h] packed (may be NULL unless warm_start).  If warm_start != 0, QH is
+ * also read as the initial guess.  info may be NULL.  Synchronous. */
+gbi_status gbi_solve(gbi_ctx* ctx, const gbi_params* params, int N,
+                     const double* R, const double* Va, const double* Oa, const double* VH,
+                     const double* Fe, const double* Te,
+                     double* V, double* Omega, double* QH, int warm_start, gbi_info* info);
+
+/* Same as gbi_solve with HOST pointers: copies inputs to the device, solves, copies
+ * the outputs back.  Synchronous. */
+gbi_status gbi_solve_host(gbi_ctx* ctx, const gbi_params* params, int N,
+                          const double* R, const double* Va, const double* Oa, const double* VH,
+                          const double* Fe, const double* Te,
+                          double* V, double* Omega, double* QH, int warm_start, gbi_info* info);
+
+/* Superposition approximation (Sec. IV, second form of Eq. mobility_matrices and
+ * Eq. propulsion_matrices; Sec. V, Eq. trap_eom): every higher coefficient takes
+ * its one-body value Q^H = -8 pi eta a V^H / g and only the direct pair sum
+ * remains.  params.trunc = 2 uses the closed-form trap kernel (Stokeslet/RPY,
+ * rotlet, stresslet and potential dipole with their finite-size terms);
+ * trunc 3, 4 use the general pair operator.  Arguments as gbi_solve (no QH).
+ * params.precision selects FP32 (1) or FP64 (0) pair arithmetic.  Asynchronous. */
+gbi_status gbi_superpose(gbi_ctx* ctx, const gbi_params* params, int N,
+                         const double* R, const double* Va, const double* Oa, const double* VH,
+                         const double* Fe, const double* Te, double* V, double* Omega);
+
+/* Inputs of the harmonic-trap model (Sec. V, Eq. trap_eom) from centres R and unit
+ * orientations p ([N][3] device arrays): F^e = -k_trap R, T^e = 0, V^a = vs p,
+ * Omega^a = 0, packed V^(2s) = s0 (pp - I/3), V^(3t) = d0 p, other higher modes 0.
+ * Outputs Fe, Te, Va, Oa: [N][3]; VH: [N][gbi_h(trunc)].  Asynchronous. */
+gbi_status gbi_trap_inputs(gbi_ctx* ctx, int N, int trunc, double k_trap, double vs, double s0, double d0,
+                           const double* R, const double* p, double* Fe, double* Te, double* Va, double* Oa,
+                           double* VH);
+
+/* Harmonic-trap dynamics (Sec. V, Eq. trap_eom): nsteps forward-Euler steps of
+ *     R <- R + dt V,  p <- normalise(p + dt Omega x p),
+ * with F^e = -k_trap R, T^e = 0, V^a = vs p, Omega^a = 0, V^(2s) = s0 (pp - I/3),
+ * V^(3t) = d0 p and every other higher mode zero, V and Omega re-evaluated every
+ * step by gbi_superpose (superposition != 0) or gbi_solve (warm-started).
+ * R, p: [N][3] device arrays updated in place.  info (may be NULL) accumulates
+ * over the steps.  Synchronous when superposition == 0. */
+gbi_status gbi_trap_step(gbi_ctx* ctx, const gbi_params* params, int N, double dt, double k_trap,
+                         double vs, double s0, double d0, int superposition, int nsteps,
+                         double* R, double* p, gbi_info* info);
+
+/* Instrumentation.  gbi_kernel_launches: number of CUDA kernels this context has
+ * launched since creation.  gbi_set_profiling(ctx, 1) resets the per-class
+ * statistics and from then on records a CUDA event pair on the context's stream
+ * around every pair pass; gbi_kernel_stats returns, for one class, the summed
+ * event time in ms, the number of launches and the algorithmic flops (the
+ * per-pair count of the implemented closed form times N(N-1)).  Class ids:
+ * precision * 9 + rows * 3 + cols for gbi_apply-style passes (precision 0 = FP64,
+ * 1 = FP32; rows/cols 0 = all, 1 = rigid-body, 2 = higher), 18 = closed-form
+ * trap kernel in FP64, 19 = in FP32.  gbi_kernel_stats synchronizes on the
+ * recorded events. */
+long long gbi_kernel_launches(gbi_ctx* ctx);
+gbi_status gbi_set_profiling(gbi_ctx* ctx, int on);
+gbi_status gbi_kernel_stats(gbi_ctx* ctx, int kernel_class, double* total_ms, long long* launches,
+                            double* flops);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBI_H */

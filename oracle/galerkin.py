@@ -249,19 +249,22 @@ def one_body_QH(VH, a, eta, trunc):
     return -8 * np.pi * eta * np.asarray(VH, float) / g
 
 
-def superpose(R, Va, Oa, VH, Fe, Te, a, eta, trunc=2):
-    """Superposition approximation: one-body Q^H, direct pair sum for V, Omega."""
+def superpose(R, Va, Oa, VH, Fe, Te, a, eta, trunc=2, targets=None):
+    """Superposition approximation: one-body Q^H, direct pair sum for V, Omega.
+
+    ``targets`` (optional index array) restricts the outputs to those spheres."""
     R = np.asarray(R, float)
     N = R.shape[0]
     MB = ModeBasis(trunc)
     d, nL, h = MB.d, MB.nL, MB.h
+    tgt = np.arange(N) if targets is None else np.asarray(targets)
     x = np.zeros((N, d))
     x[:, :nL] = lower_trial(Fe, Te, a, MB)
     x[:, nL:] = one_body_QH(VH, a, eta, trunc) * MB.scale[nL:]
-    y = apply_offdiag(R, x, a, trunc, rows=slice(0, nL))
+    y = apply_offdiag(R, x, a, trunc, rows=slice(0, nL), targets=tgt)
     g = self_scalars(trunc, a)
-    xVL = -(y + g[:nL] * x[:, :nL]) / (8 * np.pi * eta)
-    return lower_velocity(xVL, Va, Oa, a, MB)
+    xVL = -(y + g[:nL] * x[tgt, :nL]) / (8 * np.pi * eta)
+    return lower_velocity(xVL, np.asarray(Va, float)[tgt], np.asarray(Oa, float)[tgt], a, MB)
 
 
 def apply_offdiag(R, x, a, trunc, rows=slice(None), targets=None):

@@ -1,0 +1,253 @@
+"""Thin ctypes binding of libgbi (include/gbi.h): argument marshalling only.
+
+Every computation happens inside libgbi's CUDA kernels.  Device arrays are torch
+float64 CUDA tensors whose ``data_ptr()`` is passed through; outputs are
+allocated with torch.  If the shared library has not been built, the first call
+raises ``ImportError`` -- there is no CPU fallback.
+"""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libgbi.so")
+
+GBI_OK, GBI_ERR_ARG, GBI_ERR_OVERLAP, GBI_ERR_NOT_CONVERGED, GBI_ERR_TIMEOUT, GBI_ERR_CUDA, GBI_ERR_NOMEM = range(7)
+SET_ALL, SET_L, SET_H = 0, 1, 2
+
+c_double_p = ctypes.POINTER(ctypes.c_double)
+
+
+class gbi_params(ctypes.Structure):
+    _fields_ = [("a", ctypes.c_double), ("eta", ctypes.c_double), ("trunc", ctypes.c_int),
+                ("precision", ctypes.c_int), ("rtol", ctypes.c_double), ("restart", ctypes.c_int),
+                ("max_iter", ctypes.c_int), ("max_refine", ctypes.c_int), ("inner_rtol", ctypes.c_double),
+                ("min_sep", ctypes.c_double)]
+
+
+class gbi_info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("refinements", ctypes.c_int), ("matvecs_f32", ctypes.c_int),
+                ("matvecs_f64", ctypes.c_int), ("rel_residual", ctypes.c_double),
+                ("min_separation", ctypes.c_double), ("pair_interactions", ctypes.c_longlong)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class GbiError(RuntimeError):
+    def __init__(self, status, where, detail=""):
+        self.status = status
+        super().__init__("%s: %s (%d)%s" % (where, status_string(status), status,
+                                           (": " + detail) if detail else ""))
+
+
+_LIB = None
+_VP = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+
+_SIGS = {
+    "gbi_create": (_I, [ctypes.POINTER(_VP), _I]),
+    "gbi_destroy": (_I, [_VP]),
+    "gbi_set_stream": (_I, [_VP, _VP]),
+    "gbi_synchronize": (_I, [_VP]),
+    "gbi_status_string": (ctypes.c_char_p, [_I]),
+    "gbi_last_error": (ctypes.c_char_p, [_VP]),
+    "gbi_h": (_I, [_I]),
+    "gbi_d": (_I, [_I]),
+    "gbi_component_scales": (_I, [_I, c_double_p]),
+    "gbi_self_scalars": (_I, [_I, c_double_p]),
+    "gbi_apply": (_I, [_VP, _I, _I, _D, _I, _I, _I, _VP, _VP, _VP, _D, _D, _I]),
+    "gbi_solve": (_I, [_VP, ctypes.POINTER(gbi_params), _I] + [_VP] * 9 + [_I, ctypes.POINTER(gbi_info)]),
+    "gbi_solve_host": (_I, [_VP, ctypes.POINTER(gbi_params), _I] + [_VP] * 9 + [_I, ctypes.POINTER(gbi_info)]),
+    "gbi_superpose": (_I, [_VP, ctypes.POINTER(gbi_params), _I] + [_VP] * 8),
+    "gbi_trap_inputs": (_I, [_VP, _I, _I, _D, _D, _D, _D] + [_VP] * 7),
+    "gbi_trap_step": (_I, [_VP, ctypes.POINTER(gbi_params), _I, _D, _D, _D, _D, _D, _I, _I, _VP, _VP,
+                           ctypes.POINTER(gbi_info)]),
+    "gbi_kernel_launches": (ctypes.c_longlong, [_VP]),
+    "gbi_set_profiling": (_I, [_VP, _I]),
+    "gbi_kernel_stats": (_I, [_VP, _I, c_double_p, ctypes.POINTER(ctypes.c_longlong), c_double_p]),
+}
+
+# kernel classes of gbi_kernel_stats
+def kernel_class(precision, rows, cols):
+    return precision * 9 + rows * 3 + cols
+
+
+TRAP_F64, TRAP_F32 = 18, 19
+
+
+def lib():
+    """Load libgbi.so (built in-tree by ``paper_1411_0278_gb300.build``)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libgbi.so is not built (%s); run paper_1411_0278_gb300.build.build() "
+                              "on a machine with nvcc -- there is no CPU fallback" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def status_string(status):
+    return lib().gbi_status_string(int(status)).decode()
+
+
+def h(trunc):
+    return lib().gbi_h(int(trunc))
+
+
+def d(trunc):
+    return lib().gbi_d(int(trunc))
+
+
+def _host_table(fn, trunc):
+    n = d(trunc)
+    if n < 0:
+        raise GbiError(GBI_ERR_ARG, fn)
+    buf = (ctypes.c_double * n)()
+    st = getattr(lib(), fn)(int(trunc), buf)
+    if st != GBI_OK:
+        raise GbiError(st, fn)
+    return list(buf)
+
+
+def component_scales(trunc):
+    return _host_table("gbi_component_scales", trunc)
+
+
+def self_scalars(trunc):
+    return _host_table("gbi_self_scalars", trunc)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    import torch
+    if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise ValueError("expected a contiguous float64 CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def params(a=1.0, eta=1.0, trunc=2, precision=1, rtol=1e-10, restart=40, max_iter=1000, max_refine=8,
+           inner_rtol=1e-5, min_sep=0.0):
+    return gbi_params(float(a), float(eta), int(trunc), int(precision), float(rtol), int(restart),
+                      int(max_iter), int(max_refine), float(inner_rtol), float(min_sep))
+
+
+class Context:
+    """gbi_create / gbi_destroy; bound to one device and (optionally) a torch stream."""
+
+    def __init__(self, device=0, stream=None):
+        self._h = ctypes.c_void_p()
+        st = lib().gbi_create(ctypes.byref(self._h), int(device))
+        if st != GBI_OK:
+            raise GbiError(st, "gbi_create")
+        if stream is not None:
+            self.set_stream(stream)
+
+    def set_stream(self, stream):
+        handle = getattr(stream, "cuda_stream", stream)
+        self._check(lib().gbi_set_stream(self._h, ctypes.c_void_p(int(handle) if handle else 0)), "gbi_set_stream")
+
+    def synchronize(self):
+        self._check(lib().gbi_synchronize(self._h), "gbi_synchronize")
+
+    def close(self):
+        if self._h:
+            lib().gbi_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, where, allow=()):
+        if st != GBI_OK and st not in allow:
+            raise GbiError(st, where, lib().gbi_last_error(self._h).decode())
+        return st
+
+    # ------------------------------------------------------------------ calls
+
+    def apply(self, N, trunc, a, rows, cols, precision, R, x, y, alpha=1.0, beta=0.0, add_self=False):
+        return self._check(lib().gbi_apply(self._h, int(N), int(trunc), float(a), int(rows), int(cols),
+                                           int(precision), _ptr(R), _ptr(x), _ptr(y), float(alpha), float(beta),
+                                           int(bool(add_self))), "gbi_apply")
+
+    def solve(self, prm, R, Va, Oa, VH, Fe, Te, QH=None, warm_start=False, allow_not_converged=False):
+        import torch
+        N = R.shape[0]
+        V = torch.empty((N, 3), dtype=torch.float64, device=R.device)
+        Om = torch.empty_like(V)
+        if QH is None:
+            QH = torch.zeros((N, h(prm.trunc)), dtype=torch.float64, device=R.device)
+        info = gbi_info()
+        st = lib().gbi_solve(self._h, ctypes.byref(prm), int(N), _ptr(R), _ptr(Va), _ptr(Oa), _ptr(VH), _ptr(Fe),
+                             _ptr(Te), _ptr(V), _ptr(Om), _ptr(QH), int(bool(warm_start)), ctypes.byref(info))
+        self._check(st, "gbi_solve", allow=(GBI_ERR_NOT_CONVERGED,) if allow_not_converged else ())
+        return V, Om, QH, info, st
+
+    def solve_host(self, prm, R, Va, Oa, VH, Fe, Te, V, Om, QH, warm_start=False):
+        """Host-memory variant: arguments are C-contiguous float64 numpy arrays (pinned or not)."""
+        def p(a):
+            return ctypes.c_void_p(a.ctypes.data) if a is not None else None
+        info = gbi_info()
+        st = lib().gbi_solve_host(self._h, ctypes.byref(prm), int(R.shape[0]), p(R), p(Va), p(Oa), p(VH), p(Fe),
+                                  p(Te), p(V), p(Om), p(QH), int(bool(warm_start)), ctypes.byref(info))
+        self._check(st, "gbi_solve_host", allow=(GBI_ERR_NOT_CONVERGED,))
+        return info, st
+
+    def solve_host_ptrs(self, prm, N, ptrs, warm_start=False):
+        """Host-memory variant taking raw addresses (e.g. pinned torch tensors' data_ptr())."""
+        info = gbi_info()
+        st = lib().gbi_solve_host(self._h, ctypes.byref(prm), int(N), *[ctypes.c_void_p(p) for p in ptrs],
+                                  int(bool(warm_start)), ctypes.byref(info))
+        self._check(st, "gbi_solve_host", allow=(GBI_ERR_NOT_CONVERGED,))
+        return info, st
+
+    def superpose(self, prm, R, Va, Oa, VH, Fe, Te, V=None, Om=None):
+        import torch
+        N = R.shape[0]
+        V = torch.empty((N, 3), dtype=torch.float64, device=R.device) if V is None else V
+        Om = torch.empty_like(V) if Om is None else Om
+        self._check(lib().gbi_superpose(self._h, ctypes.byref(prm), int(N), _ptr(R), _ptr(Va), _ptr(Oa), _ptr(VH),
+                                        _ptr(Fe), _ptr(Te), _ptr(V), _ptr(Om)), "gbi_superpose")
+        return V, Om
+
+    def trap_inputs(self, N, trunc, k_trap, vs, s0, d0, R, p):
+        import torch
+        dev = R.device
+        out = [torch.empty((N, 3), dtype=torch.float64, device=dev) for _ in range(4)]
+        VH = torch.empty((N, h(trunc)), dtype=torch.float64, device=dev)
+        self._check(lib().gbi_trap_inputs(self._h, int(N), int(trunc), float(k_trap), float(vs), float(s0),
+                                          float(d0), _ptr(R), _ptr(p), *[_ptr(t) for t in out], _ptr(VH)),
+                    "gbi_trap_inputs")
+        Fe, Te, Va, Oa = out
+        return dict(Fe=Fe, Te=Te, Va=Va, Oa=Oa, VH=VH)
+
+    def kernel_launches(self):
+        return int(lib().gbi_kernel_launches(self._h))
+
+    def set_profiling(self, on):
+        self._check(lib().gbi_set_profiling(self._h, int(bool(on))), "gbi_set_profiling")
+
+    def kernel_stats(self, cls):
+        ms = ctypes.c_double()
+        n = ctypes.c_longlong()
+        fl = ctypes.c_double()
+        self._check(lib().gbi_kernel_stats(self._h, int(cls), ctypes.byref(ms), ctypes.byref(n), ctypes.byref(fl)),
+                    "gbi_kernel_stats")
+        return dict(ms=ms.value, launches=n.value, flops=fl.value)
+
+    def trap_step(self, prm, R, p, dt, k_trap, vs, s0, d0, superposition, nsteps):
+        info = gbi_info()
+        st = lib().gbi_trap_step(self._h, ctypes.byref(prm), int(R.shape[0]), float(dt), float(k_trap), float(vs),
+                                 float(s0), float(d0), int(bool(superposition)), int(nsteps), _ptr(R), _ptr(p),
+                                 ctypes.byref(info))
+        self._check(st, "gbi_trap_step")
+        return info

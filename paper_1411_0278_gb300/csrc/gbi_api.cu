@@ -1,0 +1,949 @@
+// C ABI of libgbi: context, workspace, input/output packing, GMRES with FP64 Arnoldi
+// and Givens least squares, mixed-precision iterative refinement, superposition and
+// the harmonic-trap integrator.  Every arithmetic step of the method runs in the
+// kernels of this library; the host only sequences launches and runs the
+// (m+1) x m Givens/triangular solve of GMRES on scalars read back from the device.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "gbi_generated.cuh"
+#include "gbi_internal.cuh"
+
+namespace gbi {
+cudaError_t launch_pairs_f32(int trunc, int rows, int cols, const PairArgs& args, cudaStream_t stream);
+cudaError_t launch_pairs_f64(int trunc, int rows, int cols, const PairArgs& args, cudaStream_t stream);
+
+cudaError_t launch_pairs(int trunc, int rows, int cols, int precision, const PairArgs& args,
+                         cudaStream_t stream) {
+  return precision == 1 ? launch_pairs_f32(trunc, rows, cols, args, stream)
+                        : launch_pairs_f64(trunc, rows, cols, args, stream);
+}
+
+double pair_flops(int trunc, int rows, int cols) {
+  if (rows < 0 || rows > 2 || cols < 0 || cols > 2) return 0.0;
+  if (trunc == 2) return gbi_t2_flops[rows][cols];
+  if (trunc == 3) return gbi_t3_flops[rows][cols];
+  if (trunc == 4) return gbi_t4_flops[rows][cols];
+  return 0.0;
+}
+}  // namespace gbi
+
+using namespace gbi;
+
+namespace {
+
+struct Buf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace
+
+struct gbi_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  Buf pos_hi, pos_lo, pos64;
+  Buf xF, xVH, b, xQ, r, delta, krylov, w, partial, dots, xVL, minr2, colbuf;
+  Buf tFe, tTe, tVa, tOa, tVH, tV, tOm, tQH;   // trap-step / host-call staging
+  Buf hR, hVa, hOa, hVH, hFe, hTe, hV, hOm, hQH;
+  double* hbuf = nullptr;                      // pinned scalars read back by GMRES
+  long long launches = 0;                      // kernels launched by this context
+  bool prof = false;                           // record events around pair passes
+  struct Rec {
+    cudaEvent_t a, b;
+    int cls;
+    double flops;
+  };
+  std::vector<Rec> pending;
+  std::vector<cudaEvent_t> pool;
+  double stat_ms[20] = {0};
+  double stat_flops[20] = {0};
+  long long stat_n[20] = {0};
+};
+
+namespace {
+
+constexpr int kMaxRestart = 128;
+
+gbi_status fail(gbi_ctx* c, cudaError_t e, const char* where) {
+  if (e == cudaSuccess) return GBI_OK;
+  c->err = std::string(where) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? GBI_ERR_NOMEM : GBI_ERR_CUDA;
+}
+
+#define GBI_CHECK(call)                                           \
+  do {                                                            \
+    cudaError_t e_ = (call);                                      \
+    if (e_ != cudaSuccess) return fail(ctx, e_, #call);           \
+  } while (0)
+
+#define GBI_TRY(call)                      \
+  do {                                     \
+    gbi_status s_ = (call);                \
+    if (s_ != GBI_OK) return s_;           \
+  } while (0)
+
+gbi_status ensure(gbi_ctx* ctx, Buf& b, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (b.bytes >= bytes) return GBI_OK;
+  if (b.p) {
+    GBI_CHECK(cudaStreamSynchronize(ctx->stream));
+    GBI_CHECK(cudaFree(b.p));
+    b.p = nullptr;
+    b.bytes = 0;
+  }
+  GBI_CHECK(cudaMalloc(&b.p, bytes));
+  b.bytes = bytes;
+  return GBI_OK;
+}
+
+template <typename T> T* P(Buf& b) { return reinterpret_cast<T*>(b.p); }
+
+cudaEvent_t take_event(gbi_ctx* ctx) {
+  if (!ctx->pool.empty()) {
+    cudaEvent_t e = ctx->pool.back();
+    ctx->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Resolve recorded event pairs into per-class totals (blocks on the last one).
+void drain_profile(gbi_ctx* ctx) {
+  for (auto& r : ctx->pending) {
+    cudaEventSynchronize(r.b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, r.a, r.b);
+    ctx->stat_ms[r.cls] += ms;
+    ctx->stat_flops[r.cls] += r.flops;
+    ctx->stat_n[r.cls] += 1;
+    ctx->pool.push_back(r.a);
+    ctx->pool.push_back(r.b);
+  }
+  ctx->pending.clear();
+}
+
+// One pair pass with launch counting and optional event timing.
+// Class: precision * 9 + rows * 3 + cols for the generic operator, 18/19 for the
+// closed-form trap kernel in FP64/FP32.
+template <typename F>
+cudaError_t timed(gbi_ctx* ctx, int cls, double flops, F&& launch) {
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (ctx->prof) {
+    a = take_event(ctx);
+    b = take_event(ctx);
+    cudaEventRecord(a, ctx->stream);
+  }
+  cudaError_t e = launch();
+  ++ctx->launches;
+  if (ctx->prof) {
+    cudaEventRecord(b, ctx->stream);
+    ctx->pending.push_back({a, b, cls, flops});
+  }
+  return e;
+}
+
+cudaError_t run_pairs(gbi_ctx* ctx, int trunc, int rows, int cols, int precision, const PairArgs& args) {
+  const double flops = pair_flops(trunc, rows, cols) * double(args.N) * double(args.N - 1);
+  return timed(ctx, precision * 9 + rows * 3 + cols, flops,
+               [&] { return launch_pairs(trunc, rows, cols, precision, args, ctx->stream); });
+}
+
+cudaError_t run_trap(gbi_ctx* ctx, const TrapArgs& t, int precision) {
+  const double flops = trap_flops() * double(t.N) * double(t.N - 1);
+  return timed(ctx, precision == 1 ? 19 : 18, flops, [&] { return launch_trap(t, precision, ctx->stream); });
+}
+
+int d_of(int trunc) { return trunc == 2 ? GbiTrunc2::D : trunc == 3 ? GbiTrunc3::D : trunc == 4 ? GbiTrunc4::D : -1; }
+const double* scale_tab(int trunc) { return trunc == 2 ? gbi_t2_scale : trunc == 3 ? gbi_t3_scale : gbi_t4_scale; }
+const double* self_tab(int trunc) { return trunc == 2 ? gbi_t2_self : trunc == 3 ? gbi_t3_self : gbi_t4_self; }
+
+// ---------------------------------------------------------------------------------
+// small kernels
+// ---------------------------------------------------------------------------------
+
+__global__ void k_positions(int N, const double* __restrict__ R, float4* hi, float4* lo, dpos4* p64) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const double x = R[3 * n], y = R[3 * n + 1], z = R[3 * n + 2];
+  const float hx = float(x), hy = float(y), hz = float(z);
+  hi[n] = make_float4(hx, hy, hz, 0.f);
+  lo[n] = make_float4(float(x - double(hx)), float(y - double(hy)), float(z - double(hz)), 0.f);
+  p64[n] = dpos4{x, y, z, 0.0};
+}
+
+// F^(1) = -F^e and F^(21) = -T^e/a in internal coordinates: xF[6][N]
+__global__ void k_pack_lower(int N, double a, double c2a, const double* __restrict__ Fe,
+                             const double* __restrict__ Te, double* xF) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const double* f = Fe + 3 * n;
+  const double* t = Te + 3 * n;
+  xF[0 * N + n] = -f[1];
+  xF[1 * N + n] = -f[2];
+  xF[2 * N + n] = -f[0];
+  xF[3 * N + n] = -c2a * t[1] / a;
+  xF[4 * N + n] = -c2a * t[2] / a;
+  xF[5 * N + n] = -c2a * t[0] / a;
+}
+
+struct Scales {
+  double v[54];
+};
+
+// packed [N][h] -> internal component-major [h][N] times scale * mult
+__global__ void k_pack_higher(int N, int h, const double* __restrict__ VH, Scales sc, double mult,
+                              double* out) {
+  const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i >= (size_t)N * h) return;
+  const int n = int(i / h), p = int(i - (size_t)n * h);
+  out[(size_t)p * N + n] = mult * sc.v[p] * VH[i];
+}
+
+// internal [h][N] -> packed [N][h] divided by scale
+__global__ void k_unpack_higher(int N, int h, const double* __restrict__ x, Scales sc, double* QH) {
+  const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i >= (size_t)N * h) return;
+  const int n = int(i / h), p = int(i - (size_t)n * h);
+  QH[i] = x[(size_t)p * N + n] / sc.v[p];
+}
+
+// V = V^a + (1s part), Omega = Omega^a + (2a part)/(c_2a 2a)
+__global__ void k_finalize_lower(int N, double a, double c2a, const double* __restrict__ xVL,
+                                 const double* __restrict__ Va, const double* __restrict__ Oa,
+                                 double* V, double* Om) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const double f = 1.0 / (c2a * 2.0 * a);
+  V[3 * n + 0] = Va[3 * n + 0] + xVL[2 * N + n];
+  V[3 * n + 1] = Va[3 * n + 1] + xVL[0 * N + n];
+  V[3 * n + 2] = Va[3 * n + 2] + xVL[1 * N + n];
+  Om[3 * n + 0] = Oa[3 * n + 0] + f * xVL[5 * N + n];
+  Om[3 * n + 1] = Oa[3 * n + 1] + f * xVL[3 * N + n];
+  Om[3 * n + 2] = Oa[3 * n + 2] + f * xVL[4 * N + n];
+}
+
+__global__ void k_scale_copy(size_t n, const double* __restrict__ x, double s, double* y) {
+  const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i < n) y[i] = s * x[i];
+}
+
+// partial[i * nb + b] = sum over block b's slice of V_i . w
+__global__ void k_multidot_partial(size_t n, const double* __restrict__ V, size_t ldv, int k,
+                                   const double* __restrict__ w, double* partial) {
+  const int i = blockIdx.y;
+  const int nb = gridDim.x;
+  const double* v = V + (size_t)i * ldv;
+  double s = 0.0;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)nb * blockDim.x)
+    s += v[t] * w[t];
+  __shared__ double sh[256];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[(size_t)i * nb + blockIdx.x] = sh[0];
+}
+
+// out[i] (+)= sum_b partial[i * nb + b], fixed order
+__global__ void k_multidot_final(int nb, const double* __restrict__ partial, double* out, int accumulate) {
+  const int i = blockIdx.x;
+  __shared__ double sh[256];
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) s += partial[(size_t)i * nb + b];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[i] = accumulate ? out[i] + sh[0] : sh[0];
+}
+
+// w -= sum_{i<k} h[i] V_i
+__global__ void k_sub_multi(size_t n, const double* __restrict__ V, size_t ldv, int k,
+                            const double* __restrict__ h, double* w) {
+  const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  double s = w[t];
+  for (int i = 0; i < k; ++i) s -= h[i] * V[(size_t)i * ldv + t];
+  w[t] = s;
+}
+
+// u[p][n] += minv[p] * sum_{i<k} y[i] V_i[p][n]   (y given in constant struct)
+struct Coef {
+  double v[kMaxRestart + 1];
+};
+__global__ void k_update_solution(int N, int h, const double* __restrict__ V, size_t ldv, int k, Coef y,
+                                  Scales minv, double* u) {
+  const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (t >= (size_t)N * h) return;
+  double s = 0.0;
+  for (int i = 0; i < k; ++i) s += y.v[i] * V[(size_t)i * ldv + t];
+  u[t] += minv.v[t / N] * s;
+}
+
+__global__ void k_trap_inputs(int N, double k_trap, double vs, double s0, double d0, int h,
+                              const double* __restrict__ R, const double* __restrict__ p, double* Fe,
+                              double* Te, double* Va, double* Oa, double* VH) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const double px = p[3 * n], py = p[3 * n + 1], pz = p[3 * n + 2];
+  for (int i = 0; i < 3; ++i) {
+    Fe[3 * n + i] = -k_trap * R[3 * n + i];
+    Te[3 * n + i] = 0.0;
+    Oa[3 * n + i] = 0.0;
+  }
+  Va[3 * n] = vs * px;
+  Va[3 * n + 1] = vs * py;
+  Va[3 * n + 2] = vs * pz;
+  double* vh = VH + (size_t)h * n;
+  for (int i = 0; i < h; ++i) vh[i] = 0.0;
+  double q[5];
+  gbi_pack2<double>(px, py, pz, q);          // U_mu . pp (the -I/3 part is traceless-projected away)
+  for (int i = 0; i < 5; ++i) vh[i] = s0 * q[i];
+  vh[5] = d0 * py;
+  vh[6] = d0 * pz;
+  vh[7] = d0 * px;
+}
+
+__global__ void k_euler(int N, double dt, const double* __restrict__ V, const double* __restrict__ Om,
+                        double* R, double* p) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const double px = p[3 * n], py = p[3 * n + 1], pz = p[3 * n + 2];
+  const double ox = Om[3 * n], oy = Om[3 * n + 1], oz = Om[3 * n + 2];
+  for (int i = 0; i < 3; ++i) R[3 * n + i] += dt * V[3 * n + i];
+  double qx = px + dt * (oy * pz - oz * py);
+  double qy = py + dt * (oz * px - ox * pz);
+  double qz = pz + dt * (ox * py - oy * px);
+  const double inv = 1.0 / sqrt(qx * qx + qy * qy + qz * qz);
+  p[3 * n] = qx * inv;
+  p[3 * n + 1] = qy * inv;
+  p[3 * n + 2] = qz * inv;
+}
+
+inline unsigned grid1(size_t n, int bs = 256) { return unsigned((n + bs - 1) / bs); }
+
+// ---------------------------------------------------------------------------------
+// solver state for one call
+// ---------------------------------------------------------------------------------
+
+struct Setup {
+  int N, trunc, D, h;
+  double a, eta;
+  Scales scale;     // internal scale per component (all D)
+  Scales selfg;     // self scalars per component (units 1/a)
+  Scales minv;      // H components: a / g (right Jacobi preconditioner)
+  Scales ones;
+  Positions pos;
+  long long pairs_per_pass;
+};
+
+gbi_status setup_call(gbi_ctx* ctx, Setup& s, int N, int trunc, double a, double eta, const double* R) {
+  s.N = N;
+  s.trunc = trunc;
+  s.D = d_of(trunc);
+  s.h = s.D - 6;
+  s.a = a;
+  s.eta = eta;
+  const double* sc = scale_tab(trunc);
+  const double* sg = self_tab(trunc);
+  for (int i = 0; i < 54; ++i) {
+    s.scale.v[i] = i < s.D ? sc[i] : 1.0;
+    s.selfg.v[i] = i < s.D ? sg[i] : 0.0;
+    s.ones.v[i] = 1.0;
+    s.minv.v[i] = (i < s.h) ? a / sg[6 + i] : 1.0;
+  }
+  s.pairs_per_pass = (long long)N * (N - 1);
+  GBI_TRY(ensure(ctx, ctx->pos_hi, sizeof(float4) * N));
+  GBI_TRY(ensure(ctx, ctx->pos_lo, sizeof(float4) * N));
+  GBI_TRY(ensure(ctx, ctx->pos64, sizeof(dpos4) * N));
+  k_positions<<<grid1(N), 256, 0, ctx->stream>>>(N, R, P<float4>(ctx->pos_hi), P<float4>(ctx->pos_lo),
+                                                 P<dpos4>(ctx->pos64));
+  ++ctx->launches;
+  GBI_CHECK(cudaGetLastError());
+  s.pos = Positions{P<float4>(ctx->pos_hi), P<float4>(ctx->pos_lo), P<dpos4>(ctx->pos64)};
+  return GBI_OK;
+}
+
+PairArgs pair_args(const Setup& s, const double* x, double* y, double alpha, double beta, int add_self,
+                   const Scales& colscale, int col0) {
+  PairArgs p;
+  p.N = s.N;
+  p.a = s.a;
+  p.pos = s.pos;
+  p.x = x;
+  p.y = y;
+  p.alpha = alpha;
+  p.beta = beta;
+  p.add_self = add_self;
+  for (int i = 0; i < 54; ++i) {
+    // colscale is indexed by absolute component; callers pass H-relative scales with col0 = 6
+    const int src = i - col0;
+    p.colscale[i] = (src >= 0 && src < 54) ? colscale.v[src] : 1.0;
+    p.selfg[i] = s.selfg.v[i];
+  }
+  p.min_r2_bits = nullptr;
+  return p;
+}
+
+// y = alpha * (G^HH x (with self)) + beta * y on H vectors; x scaled per component by colscale
+gbi_status apply_HH(gbi_ctx* ctx, const Setup& s, int precision, const double* x, double* y, double alpha,
+                    double beta, const Scales& colscale, gbi_info* info) {
+  PairArgs p = pair_args(s, x, y, alpha, beta, 1, colscale, 6);
+  GBI_CHECK(run_pairs(ctx, s.trunc, SET_H, SET_H, precision, p));
+  if (info) {
+    (precision == 1 ? info->matvecs_f32 : info->matvecs_f64) += 1;
+    info->pair_interactions += s.pairs_per_pass;
+  }
+  return GBI_OK;
+}
+
+// out[0..k) = V_i . w for i < k (deterministic two-stage reduction)
+gbi_status multidot(gbi_ctx* ctx, size_t n, const double* V, size_t ldv, int k, const double* w, double* out,
+                    int accumulate) {
+  const int nb = int(std::min<size_t>(64, std::max<size_t>(1, (n + 2047) / 2048)));
+  GBI_TRY(ensure(ctx, ctx->partial, sizeof(double) * (size_t)nb * (kMaxRestart + 2)));
+  dim3 g1(nb, k);
+  k_multidot_partial<<<g1, 256, 0, ctx->stream>>>(n, V, ldv, k, w, P<double>(ctx->partial));
+  ++ctx->launches;
+  k_multidot_final<<<k, 256, 0, ctx->stream>>>(nb, P<double>(ctx->partial), out, accumulate);
+  ++ctx->launches;
+  GBI_CHECK(cudaGetLastError());
+  return GBI_OK;
+}
+
+gbi_status norm2(gbi_ctx* ctx, size_t n, const double* x, double& out) {
+  double* d = P<double>(ctx->dots) + kMaxRestart + 2;
+  GBI_TRY(multidot(ctx, n, x, 0, 1, x, d, 0));
+  GBI_CHECK(cudaMemcpyAsync(ctx->hbuf, d, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  GBI_CHECK(cudaStreamSynchronize(ctx->stream));
+  out = std::sqrt(std::max(0.0, ctx->hbuf[0]));
+  return GBI_OK;
+}
+
+// Restarted right-preconditioned GMRES(m) for G^HH u = rhs, internal coordinates.
+// u holds the initial guess on entry (zero or warm start).  FP64 Arnoldi (classical
+// Gram-Schmidt applied twice), Givens rotations and triangular solve.
+gbi_status gmres(gbi_ctx* ctx, const Setup& s, int precision, const double* rhs, double* u, bool u_is_zero,
+                 double tol, int restart, int max_iter, gbi_info* info, int& iters, double& relres) {
+  const size_t n = (size_t)s.N * s.h;
+  const int m = std::max(1, std::min(restart, kMaxRestart));
+  GBI_TRY(ensure(ctx, ctx->krylov, sizeof(double) * n * (m + 1)));
+  GBI_TRY(ensure(ctx, ctx->w, sizeof(double) * n));
+  GBI_TRY(ensure(ctx, ctx->dots, sizeof(double) * (2 * kMaxRestart + 8)));
+  double* Vb = P<double>(ctx->krylov);
+  double* w = P<double>(ctx->w);
+  double* hd = P<double>(ctx->dots);
+  iters = 0;
+  relres = 0.0;
+  double bnorm;
+  GBI_TRY(norm2(ctx, n, rhs, bnorm));
+  if (bnorm == 0.0) {
+    GBI_CHECK(cudaMemsetAsync(u, 0, sizeof(double) * n, ctx->stream));
+    return GBI_OK;
+  }
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
+  bool first = true;
+  while (true) {
+    // r = rhs - A u  -> V_0
+    if (first && u_is_zero) {
+      GBI_CHECK(cudaMemcpyAsync(Vb, rhs, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+    } else {
+      GBI_CHECK(cudaMemcpyAsync(Vb, rhs, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+      GBI_TRY(apply_HH(ctx, s, precision, u, Vb, -1.0, 1.0, s.ones, info));
+    }
+    first = false;
+    double beta;
+    GBI_TRY(norm2(ctx, n, Vb, beta));
+    relres = beta / bnorm;
+    if (relres <= tol || iters >= max_iter) break;
+    k_scale_copy<<<grid1(n), 256, 0, ctx->stream>>>(n, Vb, 1.0 / beta, Vb);
+    ++ctx->launches;
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int kdim = 0;
+    bool done = false;
+    for (int j = 0; j < m; ++j) {
+      double* vj = Vb + (size_t)j * n;
+      GBI_TRY(apply_HH(ctx, s, precision, vj, w, 1.0, 0.0, s.minv, info));
+      // classical Gram-Schmidt, twice
+      GBI_TRY(multidot(ctx, n, Vb, n, j + 1, w, hd, 0));
+      k_sub_multi<<<grid1(n), 256, 0, ctx->stream>>>(n, Vb, n, j + 1, hd, w);
+      ++ctx->launches;
+      GBI_TRY(multidot(ctx, n, Vb, n, j + 1, w, hd + kMaxRestart + 4, 0));
+      k_sub_multi<<<grid1(n), 256, 0, ctx->stream>>>(n, Vb, n, j + 1, hd + kMaxRestart + 4, w);
+      ++ctx->launches;
+      GBI_TRY(multidot(ctx, n, w, 0, 1, w, hd + kMaxRestart + 3, 0));
+      GBI_CHECK(cudaGetLastError());
+      GBI_CHECK(cudaMemcpyAsync(ctx->hbuf, hd, sizeof(double) * (2 * kMaxRestart + 8), cudaMemcpyDeviceToHost,
+                                ctx->stream));
+      GBI_CHECK(cudaStreamSynchronize(ctx->stream));
+      const double* h1 = ctx->hbuf;
+      const double* h2 = ctx->hbuf + kMaxRestart + 4;
+      const double hn = std::sqrt(std::max(0.0, ctx->hbuf[kMaxRestart + 3]));
+      for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = h1[i] + h2[i];
+      H[(size_t)(j + 1) * m + j] = hn;
+      for (int i = 0; i < j; ++i) {
+        const double t1 = H[(size_t)i * m + j], t2 = H[(size_t)(i + 1) * m + j];
+        H[(size_t)i * m + j] = cs[i] * t1 + sn[i] * t2;
+        H[(size_t)(i + 1) * m + j] = -sn[i] * t1 + cs[i] * t2;
+      }
+      const double hjj = H[(size_t)j * m + j], hj1 = H[(size_t)(j + 1) * m + j];
+      const double den = std::hypot(hjj, hj1);
+      cs[j] = den > 0 ? hjj / den : 1.0;
+      sn[j] = den > 0 ? hj1 / den : 0.0;
+      H[(size_t)j * m + j] = den;
+      H[(size_t)(j + 1) * m + j] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      ++iters;
+      kdim = j + 1;
+      relres = std::fabs(g[j + 1]) / bnorm;
+      if (relres <= tol || iters >= max_iter || hn <= 1e-300) {
+        done = true;
+        break;
+      }
+      k_scale_copy<<<grid1(n), 256, 0, ctx->stream>>>(n, w, 1.0 / hn, Vb + (size_t)(j + 1) * n);
+      ++ctx->launches;
+    }
+    // y = H^-1 g (upper triangular kdim x kdim)
+    for (int i = kdim - 1; i >= 0; --i) {
+      double t = g[i];
+      for (int k = i + 1; k < kdim; ++k) t -= H[(size_t)i * m + k] * y[k];
+      y[i] = t / H[(size_t)i * m + i];
+    }
+    Coef cy;
+    for (int i = 0; i < kdim; ++i) cy.v[i] = y[i];
+    k_update_solution<<<grid1(n), 256, 0, ctx->stream>>>(s.N, s.h, Vb, n, kdim, cy, s.minv, u);
+    ++ctx->launches;
+    GBI_CHECK(cudaGetLastError());
+    if (done && (relres <= tol || iters >= max_iter)) break;
+    if (done) break;   // breakdown: exact solution in the Krylov space
+  }
+  return GBI_OK;
+}
+
+bool valid_params(const gbi_params* p) {
+  if (!p) return false;
+  if (!(p->a > 0) || !(p->eta > 0)) return false;
+  if (p->trunc < 2 || p->trunc > 4) return false;
+  if (p->precision != 0 && p->precision != 1) return false;
+  return true;
+}
+
+}  // namespace
+
+// =================================================================================
+// C ABI
+// =================================================================================
+
+extern "C" {
+
+gbi_status gbi_create(gbi_ctx** out, int device) {
+  if (!out) return GBI_ERR_ARG;
+  *out = nullptr;
+  cudaError_t e = cudaSetDevice(device);
+  if (e != cudaSuccess) return GBI_ERR_CUDA;
+  gbi_ctx* c = new gbi_ctx();
+  c->device = device;
+  e = cudaMallocHost(&c->hbuf, sizeof(double) * (2 * kMaxRestart + 16));
+  if (e != cudaSuccess) {
+    delete c;
+    return GBI_ERR_NOMEM;
+  }
+  *out = c;
+  return GBI_OK;
+}
+
+gbi_status gbi_destroy(gbi_ctx* ctx) {
+  if (!ctx) return GBI_ERR_ARG;
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  Buf* bufs[] = {&ctx->pos_hi, &ctx->pos_lo, &ctx->pos64, &ctx->xF, &ctx->xVH, &ctx->b, &ctx->xQ, &ctx->r,
+                 &ctx->delta, &ctx->krylov, &ctx->w, &ctx->partial, &ctx->dots, &ctx->xVL, &ctx->minr2,
+                 &ctx->colbuf, &ctx->tFe, &ctx->tTe, &ctx->tVa, &ctx->tOa, &ctx->tVH, &ctx->tV, &ctx->tOm,
+                 &ctx->tQH, &ctx->hR, &ctx->hVa, &ctx->hOa, &ctx->hVH, &ctx->hFe, &ctx->hTe, &ctx->hV,
+                 &ctx->hOm, &ctx->hQH};
+  for (Buf* b : bufs)
+    if (b->p) cudaFree(b->p);
+  if (ctx->hbuf) cudaFreeHost(ctx->hbuf);
+  drain_profile(ctx);
+  for (cudaEvent_t e : ctx->pool) cudaEventDestroy(e);
+  delete ctx;
+  return GBI_OK;
+}
+
+gbi_status gbi_set_stream(gbi_ctx* ctx, void* stream) {
+  if (!ctx) return GBI_ERR_ARG;
+  ctx->stream = reinterpret_cast<cudaStream_t>(stream);
+  return GBI_OK;
+}
+
+gbi_status gbi_synchronize(gbi_ctx* ctx) {
+  if (!ctx) return GBI_ERR_ARG;
+  GBI_CHECK(cudaStreamSynchronize(ctx->stream));
+  return GBI_OK;
+}
+
+const char* gbi_status_string(int status) {
+  switch (status) {
+    case GBI_OK: return "ok";
+    case GBI_ERR_ARG: return "invalid argument";
+    case GBI_ERR_OVERLAP: return "spheres overlap (closer than min_sep * a)";
+    case GBI_ERR_NOT_CONVERGED: return "iteration cap reached before the tolerance";
+    case GBI_ERR_TIMEOUT: return "bounded device wait gave up";
+    case GBI_ERR_CUDA: return "CUDA runtime error";
+    case GBI_ERR_NOMEM: return "workspace allocation failed";
+    default: return "unknown status";
+  }
+}
+
+const char* gbi_last_error(gbi_ctx* ctx) { return ctx ? ctx->err.c_str() : ""; }
+
+int gbi_h(int trunc) { return d_of(trunc) < 0 ? -1 : d_of(trunc) - 6; }
+int gbi_d(int trunc) { return d_of(trunc); }
+
+gbi_status gbi_component_scales(int trunc, double* out_host) {
+  if (d_of(trunc) < 0 || !out_host) return GBI_ERR_ARG;
+  std::memcpy(out_host, scale_tab(trunc), sizeof(double) * d_of(trunc));
+  return GBI_OK;
+}
+
+gbi_status gbi_self_scalars(int trunc, double* out_host) {
+  if (d_of(trunc) < 0 || !out_host) return GBI_ERR_ARG;
+  std::memcpy(out_host, self_tab(trunc), sizeof(double) * d_of(trunc));
+  return GBI_OK;
+}
+
+gbi_status gbi_apply(gbi_ctx* ctx, int N, int trunc, double a, int rows, int cols, int precision,
+                     const double* R, const double* x, double* y, double alpha, double beta, int add_self) {
+  if (!ctx || N < 0 || d_of(trunc) < 0 || !(a > 0) || (precision != 0 && precision != 1)) return GBI_ERR_ARG;
+  if (N == 0) return GBI_OK;
+  if (!R || !x || !y) return GBI_ERR_ARG;
+  const bool supported = (rows == SET_H && cols == SET_L) || (rows == SET_H && cols == SET_H) ||
+                         (rows == SET_L && cols == SET_ALL) || (rows == SET_ALL && cols == SET_ALL);
+  if (!supported) return GBI_ERR_ARG;
+  if (add_self && rows != cols && !(rows == SET_L && cols == SET_ALL)) return GBI_ERR_ARG;
+  Setup s;
+  GBI_TRY(setup_call(ctx, s, N, trunc, a, 1.0, R));
+  PairArgs p = pair_args(s, x, y, alpha, beta, add_self, s.ones, 0);
+  GBI_CHECK(run_pairs(ctx, trunc, rows, cols, precision, p));
+  return GBI_OK;
+}
+
+gbi_status gbi_solve(gbi_ctx* ctx, const gbi_params* prm, int N, const double* R, const double* Va,
+                     const double* Oa, const double* VH, const double* Fe, const double* Te, double* V,
+                     double* Omega, double* QH, int warm_start, gbi_info* info) {
+  if (!ctx || !valid_params(prm) || N < 0) return GBI_ERR_ARG;
+  gbi_info local{};
+  gbi_info* inf = info ? info : &local;
+  *inf = gbi_info{};
+  if (N == 0) return GBI_OK;
+  if (!R || !Va || !Oa || !VH || !Fe || !Te || !V || !Omega || (warm_start && !QH)) return GBI_ERR_ARG;
+  Setup s;
+  GBI_TRY(setup_call(ctx, s, N, prm->trunc, prm->a, prm->eta, R));
+  const int D = s.D, h = s.h;
+  const size_t nh = (size_t)N * h;
+  GBI_TRY(ensure(ctx, ctx->xQ, sizeof(double) * (size_t)N * D));
+  GBI_TRY(ensure(ctx, ctx->xVH, sizeof(double) * nh));
+  GBI_TRY(ensure(ctx, ctx->b, sizeof(double) * nh));
+  GBI_TRY(ensure(ctx, ctx->r, sizeof(double) * nh));
+  GBI_TRY(ensure(ctx, ctx->delta, sizeof(double) * nh));
+  GBI_TRY(ensure(ctx, ctx->xVL, sizeof(double) * 6 * N));
+  GBI_TRY(ensure(ctx, ctx->minr2, sizeof(unsigned int)));
+  GBI_TRY(ensure(ctx, ctx->dots, sizeof(double) * (2 * kMaxRestart + 8)));
+  double* xF = P<double>(ctx->xQ);              // rows 0..5 of the full vector
+  double* xQH = P<double>(ctx->xQ) + (size_t)6 * N;
+  double* b = P<double>(ctx->b);
+  double* r = P<double>(ctx->r);
+  double* dl = P<double>(ctx->delta);
+  const double c2a = s.scale.v[3];
+  Scales hscale;
+  for (int i = 0; i < 54; ++i) hscale.v[i] = (i < h) ? s.scale.v[6 + i] : 1.0;
+
+  // inputs -> internal coordinates
+  k_pack_lower<<<grid1(N), 256, 0, ctx->stream>>>(N, s.a, c2a, Fe, Te, xF);
+  ++ctx->launches;
+  // b = -8 pi eta V^H
+  k_pack_higher<<<grid1(nh), 256, 0, ctx->stream>>>(N, h, VH, hscale, -8.0 * kPi * s.eta, b);
+  ++ctx->launches;
+  GBI_CHECK(cudaGetLastError());
+  // b -= G^HL F^L  (FP64), with the overlap scan
+  const unsigned int init_bits = 0x7f7fffffu;
+  GBI_CHECK(cudaMemcpyAsync(ctx->minr2.p, &init_bits, sizeof(unsigned int), cudaMemcpyHostToDevice, ctx->stream));
+  {
+    PairArgs p = pair_args(s, xF, b, -1.0, 1.0, 0, s.ones, 0);
+    p.min_r2_bits = P<unsigned int>(ctx->minr2);
+    GBI_CHECK(run_pairs(ctx, s.trunc, SET_H, SET_L, 0, p));
+    inf->matvecs_f64 += 1;
+    inf->pair_interactions += s.pairs_per_pass;
+  }
+  unsigned int bits = 0;
+  GBI_CHECK(cudaMemcpyAsync(&bits, ctx->minr2.p, sizeof(unsigned int), cudaMemcpyDeviceToHost, ctx->stream));
+  GBI_CHECK(cudaStreamSynchronize(ctx->stream));
+  float mr2;
+  std::memcpy(&mr2, &bits, sizeof(float));
+  inf->min_separation = N > 1 ? std::sqrt(double(mr2)) / s.a : 0.0;
+  if (prm->min_sep > 0 && N > 1 && inf->min_separation < prm->min_sep) return GBI_ERR_OVERLAP;
+
+  // initial guess
+  bool zero = true;
+  if (warm_start) {
+    k_pack_higher<<<grid1(nh), 256, 0, ctx->stream>>>(N, h, QH, hscale, 1.0, xQH);
+    ++ctx->launches;
+    zero = false;
+  } else {
+    GBI_CHECK(cudaMemsetAsync(xQH, 0, sizeof(double) * nh, ctx->stream));
+  }
+  const int restart = prm->restart > 0 ? prm->restart : 40;
+  const int max_iter = prm->max_iter > 0 ? prm->max_iter : 1000;
+  const double rtol = prm->rtol > 0 ? prm->rtol : 1e-10;
+  double bnorm = 0.0;
+  GBI_TRY(norm2(ctx, nh, b, bnorm));
+  bool converged = false;
+  if (h == 0 || bnorm == 0.0) {
+    GBI_CHECK(cudaMemsetAsync(xQH, 0, sizeof(double) * nh, ctx->stream));
+    converged = true;
+    inf->rel_residual = 0.0;
+  } else if (prm->precision == 0) {
+    int it = 0;
+    double rr = 0.0;
+    GBI_TRY(gmres(ctx, s, 0, b, xQH, zero, rtol, restart, max_iter, inf, it, rr));
+    inf->iters += it;
+    // true FP64 residual
+    GBI_CHECK(cudaMemcpyAsync(r, b, sizeof(double) * nh, cudaMemcpyDeviceToDevice, ctx->stream));
+    GBI_TRY(apply_HH(ctx, s, 0, xQH, r, -1.0, 1.0, s.ones, inf));
+    double rn;
+    GBI_TRY(norm2(ctx, nh, r, rn));
+    inf->rel_residual = rn / bnorm;
+    converged = inf->rel_residual <= rtol;
+  } else {
+    // mixed precision: r = b - A64 x; A32 d = r (FP32 pair sums, FP64 Arnoldi); x += d
+    const double inner = prm->inner_rtol > 0 ? prm->inner_rtol : 1e-5;
+    const int max_refine = prm->max_refine > 0 ? prm->max_refine : 8;
+    for (int sweep = 0;; ++sweep) {
+      GBI_CHECK(cudaMemcpyAsync(r, b, sizeof(double) * nh, cudaMemcpyDeviceToDevice, ctx->stream));
+      if (!(zero && sweep == 0)) GBI_TRY(apply_HH(ctx, s, 0, xQH, r, -1.0, 1.0, s.ones, inf));
+      double rn;
+      GBI_TRY(norm2(ctx, nh, r, rn));
+      inf->rel_residual = rn / bnorm;
+      if (sweep > 0) inf->refinements += 1;
+      if (inf->rel_residual <= rtol) {
+        converged = true;
+        break;
+      }
+      if (sweep >= max_refine || inf->iters >= max_iter) break;
+      int it = 0;
+      double rr = 0.0;
+      GBI_CHECK(cudaMemsetAsync(dl, 0, sizeof(double) * nh, ctx->stream));
+      GBI_TRY(gmres(ctx, s, 1, r, dl, true, inner, restart, max_iter - inf->iters, inf, it, rr));
+      inf->iters += it;
+      k_update_solution<<<grid1(nh), 256, 0, ctx->stream>>>(N, h, dl, nh, 1, Coef{{1.0}}, s.ones, xQH);
+      ++ctx->launches;
+      GBI_CHECK(cudaGetLastError());
+    }
+  }
+  // outputs: 8 pi eta x^{V,L} = -(G^LL F^L + G^LH Q^H) incl. self
+  {
+    PairArgs p = pair_args(s, P<double>(ctx->xQ), P<double>(ctx->xVL), -1.0 / (8.0 * kPi * s.eta), 0.0, 1,
+                           s.ones, 0);
+    GBI_CHECK(run_pairs(ctx, s.trunc, SET_L, SET_ALL, 0, p));
+    inf->matvecs_f64 += 1;
+    inf->pair_interactions += s.pairs_per_pass;
+  }
+  k_finalize_lower<<<grid1(N), 256, 0, ctx->stream>>>(N, s.a, c2a, P<double>(ctx->xVL), Va, Oa, V, Omega);
+  ++ctx->launches;
+  if (QH) {
+    k_unpack_higher<<<grid1(nh), 256, 0, ctx->stream>>>(N, h, xQH, hscale, QH);
+    ++ctx->launches;
+  }
+  GBI_CHECK(cudaGetLastError());
+  GBI_CHECK(cudaStreamSynchronize(ctx->stream));
+  return converged ? GBI_OK : GBI_ERR_NOT_CONVERGED;
+}
+
+gbi_status gbi_superpose(gbi_ctx* ctx, const gbi_params* prm, int N, const double* R, const double* Va,
+                         const double* Oa, const double* VH, const double* Fe, const double* Te, double* V,
+                         double* Omega) {
+  if (!ctx || !valid_params(prm) || N < 0) return GBI_ERR_ARG;
+  if (N == 0) return GBI_OK;
+  if (!R || !Va || !Oa || !VH || !Fe || !Te || !V || !Omega) return GBI_ERR_ARG;
+  Setup s;
+  GBI_TRY(setup_call(ctx, s, N, prm->trunc, prm->a, prm->eta, R));
+  if (prm->trunc == 2) {
+    TrapArgs t;
+    t.N = N;
+    t.a = prm->a;
+    t.eta = prm->eta;
+    t.pos = s.pos;
+    t.Fe = Fe;
+    t.Te = Te;
+    t.VH = VH;
+    t.Va = Va;
+    t.Oa = Oa;
+    t.V = V;
+    t.Om = Omega;
+    GBI_CHECK(run_trap(ctx, t, prm->precision));
+    return GBI_OK;
+  }
+  const int D = s.D, h = s.h;
+  const size_t nh = (size_t)N * h;
+  GBI_TRY(ensure(ctx, ctx->xQ, sizeof(double) * (size_t)N * D));
+  GBI_TRY(ensure(ctx, ctx->xVL, sizeof(double) * 6 * N));
+  double* xF = P<double>(ctx->xQ);
+  double* xQH = P<double>(ctx->xQ) + (size_t)6 * N;
+  Scales oneb;   // one-body Q^H = -8 pi eta a V^H / g, in internal coordinates
+  for (int i = 0; i < 54; ++i) oneb.v[i] = (i < h) ? s.scale.v[6 + i] * s.a / s.selfg.v[6 + i] : 1.0;
+  k_pack_lower<<<grid1(N), 256, 0, ctx->stream>>>(N, s.a, s.scale.v[3], Fe, Te, xF);
+  ++ctx->launches;
+  k_pack_higher<<<grid1(nh), 256, 0, ctx->stream>>>(N, h, VH, oneb, -8.0 * kPi * s.eta, xQH);
+  ++ctx->launches;
+  PairArgs p = pair_args(s, P<double>(ctx->xQ), P<double>(ctx->xVL), -1.0 / (8.0 * kPi * s.eta), 0.0, 1, s.ones,
+                         0);
+  GBI_CHECK(run_pairs(ctx, s.trunc, SET_L, SET_ALL, prm->precision, p));
+  k_finalize_lower<<<grid1(N), 256, 0, ctx->stream>>>(N, s.a, s.scale.v[3], P<double>(ctx->xVL), Va, Oa, V,
+                                                      Omega);
+  ++ctx->launches;
+  GBI_CHECK(cudaGetLastError());
+  return GBI_OK;
+}
+
+gbi_status gbi_trap_step(gbi_ctx* ctx, const gbi_params* prm, int N, double dt, double k_trap, double vs,
+                         double s0, double d0, int superposition, int nsteps, double* R, double* p,
+                         gbi_info* info) {
+  if (!ctx || !valid_params(prm) || N < 0 || nsteps < 0) return GBI_ERR_ARG;
+  gbi_info total{};
+  if (N == 0 || nsteps == 0) {
+    if (info) *info = total;
+    return GBI_OK;
+  }
+  if (!R || !p) return GBI_ERR_ARG;
+  const int h = gbi_h(prm->trunc);
+  GBI_TRY(ensure(ctx, ctx->tFe, sizeof(double) * 3 * N));
+  GBI_TRY(ensure(ctx, ctx->tTe, sizeof(double) * 3 * N));
+  GBI_TRY(ensure(ctx, ctx->tVa, sizeof(double) * 3 * N));
+  GBI_TRY(ensure(ctx, ctx->tOa, sizeof(double) * 3 * N));
+  GBI_TRY(ensure(ctx, ctx->tVH, sizeof(double) * (size_t)h * N));
+  GBI_TRY(ensure(ctx, ctx->tV, sizeof(double) * 3 * N));
+  GBI_TRY(ensure(ctx, ctx->tOm, sizeof(double) * 3 * N));
+  GBI_TRY(ensure(ctx, ctx->tQH, sizeof(double) * (size_t)h * N));
+  gbi_status st = GBI_OK;
+  for (int step = 0; step < nsteps; ++step) {
+    k_trap_inputs<<<grid1(N), 256, 0, ctx->stream>>>(N, k_trap, vs, s0, d0, h, R, p, P<double>(ctx->tFe),
+                                                     P<double>(ctx->tTe), P<double>(ctx->tVa), P<double>(ctx->tOa),
+                                                     P<double>(ctx->tVH));
+    ++ctx->launches;
+    GBI_CHECK(cudaGetLastError());
+    if (superposition) {
+      GBI_TRY(gbi_superpose(ctx, prm, N, R, P<double>(ctx->tVa), P<double>(ctx->tOa), P<double>(ctx->tVH),
+                            P<double>(ctx->tFe), P<double>(ctx->tTe), P<double>(ctx->tV), P<double>(ctx->tOm)));
+      total.pair_interactions += (long long)N * (N - 1);
+      (prm->precision == 1 ? total.matvecs_f32 : total.matvecs_f64) += 1;
+    } else {
+      gbi_info one{};
+      st = gbi_solve(ctx, prm, N, R, P<double>(ctx->tVa), P<double>(ctx->tOa), P<double>(ctx->tVH),
+                     P<double>(ctx->tFe), P<double>(ctx->tTe), P<double>(ctx->tV), P<double>(ctx->tOm),
+                     P<double>(ctx->tQH), step > 0 ? 1 : 0, &one);
+      total.iters += one.iters;
+      total.refinements += one.refinements;
+      total.matvecs_f32 += one.matvecs_f32;
+      total.matvecs_f64 += one.matvecs_f64;
+      total.pair_interactions += one.pair_interactions;
+      total.rel_residual = std::max(total.rel_residual, one.rel_residual);
+      total.min_separation = step == 0 ? one.min_separation : std::min(total.min_separation, one.min_separation);
+      if (st != GBI_OK) break;
+    }
+    k_euler<<<grid1(N), 256, 0, ctx->stream>>>(N, dt, P<double>(ctx->tV), P<double>(ctx->tOm), R, p);
+    ++ctx->launches;
+    GBI_CHECK(cudaGetLastError());
+  }
+  if (info) *info = total;
+  return st;
+}
+
+gbi_status gbi_trap_inputs(gbi_ctx* ctx, int N, int trunc, double k_trap, double vs, double s0, double d0,
+                           const double* R, const double* p, double* Fe, double* Te, double* Va, double* Oa,
+                           double* VH) {
+  if (!ctx || N < 0 || d_of(trunc) < 0) return GBI_ERR_ARG;
+  if (N == 0) return GBI_OK;
+  if (!R || !p || !Fe || !Te || !Va || !Oa || !VH) return GBI_ERR_ARG;
+  k_trap_inputs<<<grid1(N), 256, 0, ctx->stream>>>(N, k_trap, vs, s0, d0, gbi_h(trunc), R, p, Fe, Te, Va, Oa, VH);
+  ++ctx->launches;
+  GBI_CHECK(cudaGetLastError());
+  return GBI_OK;
+}
+
+gbi_status gbi_set_profiling(gbi_ctx* ctx, int on) {
+  if (!ctx) return GBI_ERR_ARG;
+  drain_profile(ctx);
+  ctx->prof = on != 0;
+  for (int i = 0; i < 20; ++i) {
+    ctx->stat_ms[i] = 0.0;
+    ctx->stat_flops[i] = 0.0;
+    ctx->stat_n[i] = 0;
+  }
+  return GBI_OK;
+}
+
+gbi_status gbi_kernel_stats(gbi_ctx* ctx, int kernel_class, double* total_ms, long long* launches,
+                            double* flops) {
+  if (!ctx || kernel_class < 0 || kernel_class >= 20) return GBI_ERR_ARG;
+  drain_profile(ctx);
+  if (total_ms) *total_ms = ctx->stat_ms[kernel_class];
+  if (launches) *launches = ctx->stat_n[kernel_class];
+  if (flops) *flops = ctx->stat_flops[kernel_class];
+  return GBI_OK;
+}
+
+long long gbi_kernel_launches(gbi_ctx* ctx) { return ctx ? ctx->launches : -1; }
+
+gbi_status gbi_solve_host(gbi_ctx* ctx, const gbi_params* prm, int N, const double* R, const double* Va,
+                          const double* Oa, const double* VH, const double* Fe, const double* Te, double* V,
+                          double* Omega, double* QH, int warm_start, gbi_info* info) {
+  if (!ctx || !valid_params(prm) || N < 0) return GBI_ERR_ARG;
+  if (N == 0) return GBI_OK;
+  if (!R || !Va || !Oa || !VH || !Fe || !Te || !V || !Omega || (warm_start && !QH)) return GBI_ERR_ARG;
+  const int h = gbi_h(prm->trunc);
+  const size_t v3 = sizeof(double) * 3 * N, vh = sizeof(double) * (size_t)h * N;
+  GBI_TRY(ensure(ctx, ctx->hR, v3));
+  GBI_TRY(ensure(ctx, ctx->hVa, v3));
+  GBI_TRY(ensure(ctx, ctx->hOa, v3));
+  GBI_TRY(ensure(ctx, ctx->hVH, vh));
+  GBI_TRY(ensure(ctx, ctx->hFe, v3));
+  GBI_TRY(ensure(ctx, ctx->hTe, v3));
+  GBI_TRY(ensure(ctx, ctx->hV, v3));
+  GBI_TRY(ensure(ctx, ctx->hOm, v3));
+  GBI_TRY(ensure(ctx, ctx->hQH, vh));
+  cudaStream_t st = ctx->stream;
+  GBI_CHECK(cudaMemcpyAsync(ctx->hR.p, R, v3, cudaMemcpyHostToDevice, st));
+  GBI_CHECK(cudaMemcpyAsync(ctx->hVa.p, Va, v3, cudaMemcpyHostToDevice, st));
+  GBI_CHECK(cudaMemcpyAsync(ctx->hOa.p, Oa, v3, cudaMemcpyHostToDevice, st));
+  GBI_CHECK(cudaMemcpyAsync(ctx->hVH.p, VH, vh, cudaMemcpyHostToDevice, st));
+  GBI_CHECK(cudaMemcpyAsync(ctx->hFe.p, Fe, v3, cudaMemcpyHostToDevice, st));
+  GBI_CHECK(cudaMemcpyAsync(ctx->hTe.p, Te, v3, cudaMemcpyHostToDevice, st));
+  if (warm_start) GBI_CHECK(cudaMemcpyAsync(ctx->hQH.p, QH, vh, cudaMemcpyHostToDevice, st));
+  gbi_status s = gbi_solve(ctx, prm, N, P<double>(ctx->hR), P<double>(ctx->hVa), P<double>(ctx->hOa),
+                           P<double>(ctx->hVH), P<double>(ctx->hFe), P<double>(ctx->hTe), P<double>(ctx->hV),
+                           P<double>(ctx->hOm), P<double>(ctx->hQH), warm_start, info);
+  if (s != GBI_OK && s != GBI_ERR_NOT_CONVERGED) return s;
+  GBI_CHECK(cudaMemcpyAsync(V, ctx->hV.p, v3, cudaMemcpyDeviceToHost, st));
+  GBI_CHECK(cudaMemcpyAsync(Omega, ctx->hOm.p, v3, cudaMemcpyDeviceToHost, st));
+  if (QH) GBI_CHECK(cudaMemcpyAsync(QH, ctx->hQH.p, vh, cudaMemcpyDeviceToHost, st));
+  GBI_CHECK(cudaStreamSynchronize(st));
+  return s;
+}
+
+}  // extern "C"

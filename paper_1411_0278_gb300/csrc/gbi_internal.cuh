@@ -1,0 +1,68 @@
+// Internal declarations shared by the translation units of libgbi.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/gbi.h"
+
+namespace gbi {
+
+constexpr double kPi = 3.14159265358979323846;
+
+// Position layouts built once per call from the caller's [N][3] doubles:
+//   hi[n] = (float)R, lo[n] = (float)(R - hi)   -> rho = (hi_n - hi_m) + (lo_n - lo_m) in FP32
+//   p64[n] = R as double4                        -> FP64 kernels
+struct __align__(32) dpos4 {
+  double x, y, z, w;
+};
+
+struct Positions {
+  const float4* hi;
+  const float4* lo;
+  const dpos4* p64;
+};
+
+// Which components a pair pass reads (cols) and writes (rows).
+enum CompSet : int { SET_ALL = 0, SET_L = 1, SET_H = 2 };
+
+struct PairArgs {
+  int N;
+  double a;
+  Positions pos;
+  const double* x;       // component-major, first component of the column set
+  double* y;             // component-major, first component of the row set
+  double alpha, beta;
+  int add_self;
+  double colscale[54];   // per-column multiplier applied to x (preconditioner / unit scaling)
+  double selfg[54];      // one-body self scalars g (units 1/a) per component, for add_self
+  unsigned int* min_r2_bits;   // optional: atomicMin of the smallest r^2 (float bits), may be null
+};
+
+// Launch the generic single-layer pair operator; returns a CUDA error code.
+cudaError_t launch_pairs(int trunc, int rows, int cols, int precision, const PairArgs& args,
+                         cudaStream_t stream);
+
+struct TrapArgs {
+  int N;
+  double a, eta;
+  Positions pos;
+  // per-source data, FP64 from the caller, converted inside the kernel
+  const double* Fe;     // [N][3]
+  const double* Te;     // [N][3]
+  const double* VH;     // [N][h] packed, h = 8 (2s then 3t)
+  const double* Va;     // [N][3]
+  const double* Oa;     // [N][3]
+  double* V;            // [N][3]
+  double* Om;           // [N][3]
+};
+
+cudaError_t launch_trap(const TrapArgs& args, int precision, cudaStream_t stream);
+
+// Flop counts per ordered pair used for the roofline accounting.
+double pair_flops(int trunc, int rows, int cols);
+double trap_flops();
+
+}  // namespace gbi

@@ -1,0 +1,311 @@
+// Generic single-layer Galerkin pair operator (Sec. III, Eq. single_layer_yl_matrix_element).
+//
+// For each target sphere n (one warp) and each source sphere m != n (one lane at a
+// time, sources staged in shared memory tiles) the block G_nm is applied in the
+// pair frame where R_n - R_m lies along +z:
+//
+//   y_n += Q^T C(r) Q x_m,     Q = D(R_y(-theta)) D(R_z(-phi)),
+//
+// with C(r)_pq = (1/a) (a/r)^(l_p + l_q + 1) [alpha_pq + beta_pq (a/r)^2] from the
+// generated tables (the F^l finite-size operators give the beta term) and D the
+// rotation matrices of the packed STF basis.  All of the pair arithmetic runs in T
+// (float or double); inputs and outputs are FP64.  The FP32 path forms
+// rho = (hi_n - hi_m) + (lo_n - lo_m) from a two-float split of the centres, so
+// rho keeps FP32 relative accuracy even far from the origin.
+#pragma once
+
+#include <type_traits>
+
+#include "gbi_generated.cuh"
+#include "gbi_internal.cuh"
+
+namespace gbi {
+
+template <int TR> struct Tab;
+#define GBI_TAB(TRN)                                                                   \
+  template <> struct Tab<TRN> {                                                        \
+    static constexpr int D = GbiTrunc##TRN::D;                                         \
+    static constexpr int NMODE = GbiTrunc##TRN::NMODE;                                 \
+    static constexpr int MAXK = GbiTrunc##TRN::MAXK;                                   \
+    __host__ __device__ static constexpr int k(int m) { return gbi_t##TRN##_k(m); }    \
+    __host__ __device__ static constexpr int L(int m) { return gbi_t##TRN##_L(m); }    \
+    __host__ __device__ static constexpr int off(int m) { return gbi_t##TRN##_off(m); } \
+  };
+GBI_TAB(2)
+GBI_TAB(3)
+GBI_TAB(4)
+#undef GBI_TAB
+
+template <int TR, int ROWS, int COLS, typename T>
+__host__ __device__ __forceinline__ void couple(T e2, const T* xs, T* y) {
+#define GBI_C(TRN, RN, CN, RV, CV)                                 \
+  if constexpr (TR == TRN && ROWS == RV && COLS == CV) {           \
+    gbi_t##TRN##_couple_##RN##_##CN<T>(e2, xs, y);                 \
+  }
+#define GBI_C3(TRN)                                                                         \
+  GBI_C(TRN, all, all, 0, 0) GBI_C(TRN, all, L, 0, 1) GBI_C(TRN, all, H, 0, 2)             \
+  GBI_C(TRN, L, all, 1, 0) GBI_C(TRN, L, L, 1, 1) GBI_C(TRN, L, H, 1, 2)                   \
+  GBI_C(TRN, H, all, 2, 0) GBI_C(TRN, H, L, 2, 1) GBI_C(TRN, H, H, 2, 2)
+  GBI_C3(2)
+  GBI_C3(3)
+  GBI_C3(4)
+#undef GBI_C3
+#undef GBI_C
+}
+
+template <typename T> struct DMats {
+  T d1[gbi_dm1_n];
+  T d2[gbi_dm2_n];
+  T d3[gbi_dm3_n];
+  T d4[gbi_dm4_n];
+};
+
+template <int K, typename T>
+__host__ __device__ __forceinline__ void dapply(const DMats<T>& dm, const T* in, T* out) {
+  if constexpr (K == 1) gbi_dapply1<T>(dm.d1, in, out);
+  if constexpr (K == 2) gbi_dapply2<T>(dm.d2, in, out);
+  if constexpr (K == 3) gbi_dapply3<T>(dm.d3, in, out);
+  if constexpr (K == 4) gbi_dapply4<T>(dm.d4, in, out);
+}
+template <int K, typename T>
+__host__ __device__ __forceinline__ void dapplyT(const DMats<T>& dm, const T* in, T* out) {
+  if constexpr (K == 1) gbi_dapplyT1<T>(dm.d1, in, out);
+  if constexpr (K == 2) gbi_dapplyT2<T>(dm.d2, in, out);
+  if constexpr (K == 3) gbi_dapplyT3<T>(dm.d3, in, out);
+  if constexpr (K == 4) gbi_dapplyT4<T>(dm.d4, in, out);
+}
+
+// Rotate the column modes [M, MEND) of x (absolute component index) into the pair
+// frame and scale by (a/r)^l: xs = (a/r)^l D_y Z x.
+template <int TR, typename T, int M, int MEND>
+__host__ __device__ __forceinline__ void to_pair_frame(const T* x, T* xs, const T* cm, const T* sm,
+                                              const DMats<T>& dm, const T* ep) {
+  if constexpr (M < MEND) {
+    constexpr int k = Tab<TR>::k(M);
+    constexpr int o = Tab<TR>::off(M);
+    constexpr int l = Tab<TR>::L(M) - 1;
+    T t[2 * k + 1], u[2 * k + 1];
+    t[k] = x[o + k];
+#pragma unroll
+    for (int mm = 1; mm <= k; ++mm) {
+      const T xp = x[o + k + mm], xn = x[o + k - mm];
+      t[k + mm] = cm[mm] * xp + sm[mm] * xn;
+      t[k - mm] = cm[mm] * xn - sm[mm] * xp;
+    }
+    dapply<k, T>(dm, t, u);
+#pragma unroll
+    for (int i = 0; i < 2 * k + 1; ++i) xs[o + i] = ep[l] * u[i];
+    to_pair_frame<TR, T, M + 1, MEND>(x, xs, cm, sm, dm, ep);
+  }
+}
+
+// Rotate the row modes [M, MEND) of the pair-frame result back and accumulate:
+// acc += Z^T D_y^T (a/r)^(l+1) yy.  acc is indexed from the first row component R0.
+template <int TR, typename T, int M, int MEND, int R0>
+__host__ __device__ __forceinline__ void from_pair_frame(const T* yy, T* acc, const T* cm, const T* sm,
+                                                const DMats<T>& dm, const T* ep) {
+  if constexpr (M < MEND) {
+    constexpr int k = Tab<TR>::k(M);
+    constexpr int o = Tab<TR>::off(M);
+    constexpr int l = Tab<TR>::L(M) - 1;
+    T u[2 * k + 1], t[2 * k + 1];
+#pragma unroll
+    for (int i = 0; i < 2 * k + 1; ++i) u[i] = ep[l + 1] * yy[o + i];
+    dapplyT<k, T>(dm, u, t);
+    acc[o - R0 + k] += t[k];
+#pragma unroll
+    for (int mm = 1; mm <= k; ++mm) {
+      const T tp = t[k + mm], tn = t[k - mm];
+      acc[o - R0 + k + mm] += cm[mm] * tp - sm[mm] * tn;
+      acc[o - R0 + k - mm] += sm[mm] * tp + cm[mm] * tn;
+    }
+    from_pair_frame<TR, T, M + 1, MEND, R0>(yy, acc, cm, sm, dm, ep);
+  }
+}
+
+__host__ __device__ __forceinline__ float gbi_rsqrt(float v) {
+#ifdef __CUDA_ARCH__
+  return rsqrtf(v);
+#else
+  return 1.0f / sqrtf(v);
+#endif
+}
+__host__ __device__ __forceinline__ double gbi_rsqrt(double v) {
+#ifdef __CUDA_ARCH__
+  return rsqrt(v);
+#else
+  return 1.0 / sqrt(v);
+#endif
+}
+
+// Row/column component and mode ranges of a pair pass.
+template <int TR, int ROWS, int COLS> struct PassShape {
+  static constexpr int D = Tab<TR>::D;
+  static constexpr int R0 = ROWS == SET_H ? 6 : 0;
+  static constexpr int R1 = ROWS == SET_L ? 6 : D;
+  static constexpr int C0 = COLS == SET_H ? 6 : 0;
+  static constexpr int C1 = COLS == SET_L ? 6 : D;
+  static constexpr int NR = R1 - R0;
+  static constexpr int NC = C1 - C0;
+  static constexpr int MR0 = ROWS == SET_H ? 2 : 0;
+  static constexpr int MR1 = ROWS == SET_L ? 2 : Tab<TR>::NMODE;
+  static constexpr int MC0 = COLS == SET_H ? 2 : 0;
+  static constexpr int MC1 = COLS == SET_L ? 2 : Tab<TR>::NMODE;
+  static constexpr int MAXK_R = ROWS == SET_L ? 1 : Tab<TR>::MAXK;
+  static constexpr int MAXK_C = COLS == SET_L ? 1 : Tab<TR>::MAXK;
+  static constexpr int MAXK = MAXK_R > MAXK_C ? MAXK_R : MAXK_C;
+};
+
+// One ordered pair: acc[p - R0] += sum_q C-rotated block [p][q] * xl[q] for
+// rho = (dx, dy, dz) = R_n - R_m, xl indexed by absolute component (columns only).
+// The 1/a factor of the block is applied by the caller.
+template <int TR, int ROWS, int COLS, typename T>
+__host__ __device__ __forceinline__ void pair_body(T dx, T dy, T dz, T a, const T* xl, T* acc) {
+  using S = PassShape<TR, ROWS, COLS>;
+  constexpr int MAXK = S::MAXK;
+  const T rxy2 = dx * dx + dy * dy;
+  const T r2 = rxy2 + dz * dz;
+  const T rinv = gbi_rsqrt(r2);
+  const T eps = a * rinv;
+  const T e2 = eps * eps;
+  // direction: theta from +z, phi in the xy plane
+  const T ct = dz * rinv;
+  T cphi = T(1), sphi = T(0), st = T(0);
+  if (rxy2 > T(0)) {
+    const T rxyinv = gbi_rsqrt(rxy2);
+    cphi = dx * rxyinv;
+    sphi = dy * rxyinv;
+    st = rxy2 * rxyinv * rinv;
+  }
+  T cm[MAXK + 1], sm[MAXK + 1];
+  cm[0] = T(1); sm[0] = T(0);
+  cm[1] = cphi; sm[1] = sphi;
+#pragma unroll
+  for (int mm = 2; mm <= MAXK; ++mm) {
+    cm[mm] = cm[mm - 1] * cphi - sm[mm - 1] * sphi;
+    sm[mm] = sm[mm - 1] * cphi + cm[mm - 1] * sphi;
+  }
+  // rotation about y by -theta: cos = ct, sin = -st
+  DMats<T> dm;
+  gbi_dmat1<T>(ct, -st, dm.d1);
+  if constexpr (MAXK >= 2) gbi_dmat2<T>(ct, -st, dm.d2);
+  if constexpr (MAXK >= 3) gbi_dmat3<T>(ct, -st, dm.d3);
+  if constexpr (MAXK >= 4) gbi_dmat4<T>(ct, -st, dm.d4);
+  T ep[7];
+  ep[0] = T(1);
+#pragma unroll
+  for (int i = 1; i < 7; ++i) ep[i] = ep[i - 1] * eps;
+  T xs[S::D], yy[S::D];
+  to_pair_frame<TR, T, S::MC0, S::MC1>(xl, xs, cm, sm, dm, ep);
+  couple<TR, ROWS, COLS, T>(e2, xs, yy);
+  from_pair_frame<TR, T, S::MR0, S::MR1, S::R0>(yy, acc, cm, sm, dm, ep);
+}
+
+template <int TR, int ROWS, int COLS, typename T, int WARPS, int TILE>
+__global__ void __launch_bounds__(WARPS * 32) pair_kernel(const PairArgs args) {
+  using S = PassShape<TR, ROWS, COLS>;
+  constexpr int D = S::D;
+  constexpr int R0 = S::R0;
+  constexpr int C0 = S::C0;
+  constexpr int C1 = S::C1;
+  constexpr int NR = S::NR;
+  constexpr int NC = S::NC;
+  constexpr bool F32 = std::is_same<T, float>::value;
+  constexpr int POSW = F32 ? 6 : 3;
+
+  __shared__ T s_pos[POSW][TILE];
+  __shared__ T s_x[NC][TILE];
+
+  const int N = args.N;
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int n = blockIdx.x * WARPS + warp;
+  const bool active = n < N;
+  const T a = T(args.a);
+
+  T tp[POSW];
+  if (active) {
+    if constexpr (F32) {
+      const float4 h = args.pos.hi[n], lo = args.pos.lo[n];
+      tp[0] = h.x; tp[1] = h.y; tp[2] = h.z; tp[3] = lo.x; tp[4] = lo.y; tp[5] = lo.z;
+    } else {
+      const dpos4 p = args.pos.p64[n];
+      tp[0] = p.x; tp[1] = p.y; tp[2] = p.z;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < POSW; ++i) tp[i] = T(0);
+  }
+
+  T acc[NR];
+#pragma unroll
+  for (int p = 0; p < NR; ++p) acc[p] = T(0);
+  float min_r2 = 3.0e38f;
+
+  for (int base = 0; base < N; base += TILE) {
+    const int len = min(TILE, N - base);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < len; idx += WARPS * 32) {
+      const int m = base + idx;
+      if constexpr (F32) {
+        const float4 h = args.pos.hi[m], lo = args.pos.lo[m];
+        s_pos[0][idx] = h.x; s_pos[1][idx] = h.y; s_pos[2][idx] = h.z;
+        s_pos[3][idx] = lo.x; s_pos[4][idx] = lo.y; s_pos[5][idx] = lo.z;
+      } else {
+        const dpos4 p = args.pos.p64[m];
+        s_pos[0][idx] = p.x; s_pos[1][idx] = p.y; s_pos[2][idx] = p.z;
+      }
+    }
+    for (int idx = threadIdx.x; idx < NC * len; idx += WARPS * 32) {
+      const int q = idx / len, j = idx - q * len;
+      s_x[q][j] = T(args.x[(size_t)q * N + base + j] * args.colscale[C0 + q]);
+    }
+    __syncthreads();
+    if (active) {
+      for (int j = lane; j < len; j += 32) {
+        if (base + j == n) continue;
+        T dx, dy, dz;
+        if constexpr (F32) {
+          dx = (tp[0] - s_pos[0][j]) + (tp[3] - s_pos[3][j]);
+          dy = (tp[1] - s_pos[1][j]) + (tp[4] - s_pos[4][j]);
+          dz = (tp[2] - s_pos[2][j]) + (tp[5] - s_pos[5][j]);
+        } else {
+          dx = tp[0] - s_pos[0][j];
+          dy = tp[1] - s_pos[1][j];
+          dz = tp[2] - s_pos[2][j];
+        }
+        min_r2 = fminf(min_r2, float(dx * dx + dy * dy + dz * dz));
+        T xl[D];
+#pragma unroll
+        for (int q = C0; q < C1; ++q) xl[q] = s_x[q - C0][j];
+        pair_body<TR, ROWS, COLS, T>(dx, dy, dz, a, xl, acc);
+      }
+    }
+  }
+
+  // warp reduction of the partial sums (fixed order: deterministic)
+#pragma unroll
+  for (int p = 0; p < NR; ++p) {
+    T v = acc[p];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    acc[p] = v;
+  }
+  if (args.min_r2_bits != nullptr) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) min_r2 = fminf(min_r2, __shfl_xor_sync(0xffffffffu, min_r2, o));
+    if (active && lane == 0) atomicMin(args.min_r2_bits, __float_as_uint(min_r2));
+  }
+  if (active && lane == 0) {
+    const double inva = 1.0 / args.a;
+#pragma unroll
+    for (int p = 0; p < NR; ++p) {
+      double v = double(acc[p]) * inva;
+      if (args.add_self) v += args.selfg[R0 + p] * inva * args.x[(size_t)(R0 - C0 + p) * N + n] * args.colscale[R0 + p];
+      double* dst = args.y + (size_t)p * N + n;
+      *dst = args.alpha * v + (args.beta != 0.0 ? args.beta * (*dst) : 0.0);
+    }
+  }
+}
+
+}  // namespace gbi

@@ -1,0 +1,350 @@
+"""CUDA path against the FP64 oracle, through the C ABI (libgbi via ctypes).
+
+Tolerances: FP64 kernels agree with the oracle to ~1e-12 relative (rounding
+order only); FP32 pair sums to 1e-5 relative to the largest output (the pair
+velocity bar); refined solves reach ||b - A q|| / ||b|| <= 1e-10, which bounds
+the velocity error at ~1e-9 relative for these well-conditioned systems.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import workloads
+from oracle import dynamics, galerkin, tensors
+
+pytestmark = pytest.mark.gpu
+
+FP32_TOL = 1e-5
+FP64_TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def gbi():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1411_0278_gb300 as g
+    g.lib()
+    return g
+
+
+@pytest.fixture(scope="module")
+def ctx(gbi):
+    c = gbi.Context(0)
+    yield c
+    c.close()
+
+
+def dev(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def relerr(x, ref):
+    x = np.asarray(x)
+    ref = np.asarray(ref)
+    return np.abs(x - ref).max() / max(np.abs(ref).max(), 1e-300)
+
+
+def cloud(N, seed, phi=0.05):
+    s = workloads.small_cloud(N, seed, phi=phi)
+    return s["R"], s["p"], s
+
+
+_ASSEMBLED = {}
+
+
+def assembled(N, seed, trunc, a=1.0):
+    """Dense oracle matrix, cached across the parametrised cases."""
+    key = (N, seed, trunc, a)
+    if key not in _ASSEMBLED:
+        R, _, _ = cloud(N, seed)
+        _ASSEMBLED[key] = galerkin.assemble(R, a, trunc)
+    return _ASSEMBLED[key]
+
+
+# ------------------------------------------------------------------ pair operator
+
+SETS = {0: slice(None), 1: slice(0, 6), 2: "H"}
+
+
+def _sl(code, d):
+    return slice(0, d) if code == 0 else (slice(0, 6) if code == 1 else slice(6, d))
+
+
+@pytest.mark.parametrize("trunc,N", [(2, 150), (3, 150), (4, 70)])
+@pytest.mark.parametrize("rows,cols", [(2, 1), (2, 2), (1, 0), (0, 0)])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_apply_matches_dense_oracle(ctx, gbi, trunc, N, rows, cols, precision):
+    R, _, s = cloud(N, 11 + trunc)
+    a = 1.0
+    A = assembled(N, 11 + trunc, trunc, a)
+    MB = tensors.ModeBasis(trunc)
+    d = MB.d
+    A4 = A.reshape(N, d, N, d).copy()
+    g = galerkin.self_scalars(trunc, a)
+    rng = np.random.default_rng(5)
+    rs, cs = _sl(rows, d), _sl(cols, d)
+    nr, nc = len(range(d)[rs]), len(range(d)[cs])
+    x = rng.normal(size=(nc, N))                     # component-major
+    y0 = rng.normal(size=(nr, N))
+    add_self = rows == cols
+    Aoff = A4.copy()
+    for i in range(N):
+        Aoff[i, :, i, :] = 0.0
+    ref = np.einsum("npmq,qm->pn", Aoff[:, rs, :, cs], x)
+    if add_self:
+        ref = ref + g[rs][:, None] * x
+    ref = 0.7 * ref - 0.3 * y0
+    yd = dev(y0)
+    ctx.apply(N, trunc, a, rows, cols, precision, dev(R), dev(x), yd, 0.7, -0.3, add_self)
+    torch.cuda.synchronize()
+    err = relerr(yd.cpu().numpy(), ref)
+    assert err < (FP64_TOL if precision == 0 else FP32_TOL), err
+
+
+def test_apply_symmetry_and_far_positions(ctx, gbi):
+    """Spheres far from the origin (|R| ~ 1e4 a): the two-float centre split keeps FP32 accurate."""
+    R, _, _ = cloud(90, 3)
+    R = R + np.array([1.0e4, -2.0e4, 5.0e3])
+    trunc, d, N = 3, 31, 90
+    A = galerkin.assemble(R, 1.0, trunc).reshape(N, d, N, d)
+    for i in range(N):
+        A[i, :, i, :] = 0
+    x = np.random.default_rng(2).normal(size=(25, N))
+    ref = np.einsum("npmq,qm->pn", A[:, 6:, :, 6:], x)
+    for prec, tol in ((0, FP64_TOL * 10), (1, FP32_TOL)):
+        yd = torch.zeros((25, N), dtype=torch.float64, device="cuda")
+        ctx.apply(N, trunc, 1.0, 2, 2, prec, dev(R), dev(x), yd, 1.0, 0.0, False)
+        torch.cuda.synchronize()
+        assert relerr(yd.cpu().numpy(), ref) < tol
+
+
+# ------------------------------------------------------------------ superposition
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_trap_superposition_matches_oracle(ctx, gbi, precision):
+    R, p, s = cloud(300, 4)
+    prm_o = dict(a=s["a"], eta=s["eta"], k=s["k"], vs=s["vs"], s0=s["s0"], d0=0.03)
+    inp = dynamics.trap_inputs(R, p, prm_o, 2)
+    inp["Te"] = np.random.default_rng(9).normal(size=(len(R), 3)) * 0.01
+    Vr, Omr = galerkin.superpose(R, inp["Va"], inp["Oa"], inp["VH"], inp["Fe"], inp["Te"], s["a"], s["eta"], 2)
+    prm = gbi.params(a=s["a"], eta=s["eta"], trunc=2, precision=precision)
+    t = {k: dev(v) for k, v in inp.items()}
+    V, Om = ctx.superpose(prm, dev(R), t["Va"], t["Oa"], t["VH"], t["Fe"], t["Te"])
+    torch.cuda.synchronize()
+    tol = FP64_TOL if precision == 0 else FP32_TOL
+    assert relerr(V.cpu().numpy(), Vr) < tol
+    assert relerr(Om.cpu().numpy(), Omr) < tol
+
+
+@pytest.mark.parametrize("trunc", [3, 4])
+def test_general_superposition_matches_oracle(ctx, gbi, trunc):
+    R, p, s = cloud(60, 5)
+    N = len(R)
+    MB = tensors.ModeBasis(trunc)
+    rng = np.random.default_rng(3)
+    VH = rng.normal(size=(N, MB.h)) * 0.05
+    Fe = rng.normal(size=(N, 3)) * 0.01
+    Te = rng.normal(size=(N, 3)) * 0.01
+    Va = rng.normal(size=(N, 3)) * 0.1
+    Oa = rng.normal(size=(N, 3)) * 0.01
+    Vr, Omr = galerkin.superpose(R, Va, Oa, VH, Fe, Te, 1.0, s["eta"], trunc)
+    for prec, tol in ((0, FP64_TOL), (1, FP32_TOL)):
+        prm = gbi.params(a=1.0, eta=s["eta"], trunc=trunc, precision=prec)
+        V, Om = ctx.superpose(prm, dev(R), dev(Va), dev(Oa), dev(VH), dev(Fe), dev(Te))
+        torch.cuda.synchronize()
+        assert relerr(V.cpu().numpy(), Vr) < tol
+        assert relerr(Om.cpu().numpy(), Omr) < tol
+
+
+def test_trap_superposition_full_size_sampled(ctx, gbi):
+    """N = 10^4 Gaussian trap cloud (superposition, FP32): sampled spheres against the oracle."""
+    c = workloads.config3()
+    R, p = c["R"], c["p"]
+    N = len(R)
+    prm_o = dict(a=c["a"], eta=c["eta"], k=c["k"], vs=c["vs"], s0=c["s0"], d0=c["d0"])
+    inp = dynamics.trap_inputs(R, p, prm_o, 2)
+    prm = gbi.params(a=c["a"], eta=c["eta"], trunc=2, precision=1)
+    t = {k: dev(v) for k, v in inp.items()}
+    V, Om = ctx.superpose(prm, dev(R), t["Va"], t["Oa"], t["VH"], t["Fe"], t["Te"])
+    torch.cuda.synchronize()
+    tgt = np.random.default_rng(1).choice(N, size=12, replace=False)
+    Vr, Omr = galerkin.superpose(R, inp["Va"], inp["Oa"], inp["VH"], inp["Fe"], inp["Te"], c["a"], c["eta"], 2,
+                                 targets=tgt)
+    Vg, Omg = V.cpu().numpy()[tgt], Om.cpu().numpy()[tgt]
+    # error relative to the largest sampled velocity (max_n |dV_n| / max_n |V_n|)
+    assert np.abs(Vg - Vr).max() / np.linalg.norm(Vr, axis=1).max() < FP32_TOL
+    assert np.abs(Omg - Omr).max() / np.linalg.norm(Omr, axis=1).max() < FP32_TOL
+
+
+# ------------------------------------------------------------------ full solve
+
+def _solve_case(gbi, ctx, R, p, s, trunc, precision, d0=0.02, Te_scale=0.01, rtol=1e-10):
+    N = len(R)
+    prm_o = dict(a=s["a"], eta=s["eta"], k=s["k"], vs=s["vs"], s0=s["s0"], d0=d0)
+    inp = dynamics.trap_inputs(R, p, prm_o, trunc)
+    inp["Te"] = np.random.default_rng(17).normal(size=(N, 3)) * Te_scale
+    prm = gbi.params(a=s["a"], eta=s["eta"], trunc=trunc, precision=precision, rtol=rtol)
+    t = {k: dev(v) for k, v in inp.items()}
+    V, Om, QH, info, st = ctx.solve(prm, dev(R), t["Va"], t["Oa"], t["VH"], t["Fe"], t["Te"])
+    torch.cuda.synchronize()
+    return inp, V.cpu().numpy(), Om.cpu().numpy(), QH.cpu().numpy(), info
+
+
+@pytest.mark.parametrize("trunc,N", [(2, 64), (3, 40), (4, 24)])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_solve_matches_dense_lu(ctx, gbi, trunc, N, precision):
+    R, p, s = cloud(N, 20 + trunc)
+    inp, V, Om, QH, info = _solve_case(gbi, ctx, R, p, s, trunc, precision)
+    Vr, Omr, QHr = galerkin.solve(R, inp["Va"], inp["Oa"], inp["VH"], inp["Fe"], inp["Te"], s["a"], s["eta"], trunc)
+    assert info.rel_residual <= 1e-10
+    assert relerr(V, Vr) < 1e-9
+    assert relerr(Om, Omr) < 1e-9
+    # per mode: every H block of Q^H against the oracle
+    MB = tensors.ModeBasis(trunc)
+    off = 0
+    for (name, L, sig) in MB.hmodes:
+        k = 2 * (L - sig) + 1
+        assert relerr(QH[:, off:off + k], QHr[:, off:off + k]) < 1e-8, name
+        off += k
+    assert info.pair_interactions == (info.matvecs_f32 + info.matvecs_f64) * N * (N - 1)
+    if precision == 1:
+        assert info.matvecs_f32 > info.matvecs_f64
+
+
+def test_solve_config1_and_single_sphere(ctx, gbi):
+    c = workloads.config1()
+    R, p = c["R"], c["p"]
+    inp, V, Om, QH, info = _solve_case(gbi, ctx, R, p, c, 2, 1, d0=0.0, Te_scale=0.0)
+    Vr, Omr, _ = galerkin.solve(R, inp["Va"], inp["Oa"], inp["VH"], inp["Fe"], inp["Te"], c["a"], c["eta"], 2)
+    assert relerr(V, Vr) < 1e-9 and relerr(Om, Omr) < 1e-9
+    # N = 1: Stokes laws, no pair term
+    R1 = np.array([[0.3, -0.2, 0.1]])
+    p1 = np.array([[0.0, 0.0, 1.0]])
+    inp, V, Om, QH, info = _solve_case(gbi, ctx, R1, p1, c, 3, 1)
+    F, T = inp["Fe"][0], inp["Te"][0]
+    assert np.allclose(V[0], inp["Va"][0] + F / (6 * np.pi * c["eta"] * c["a"]), rtol=0, atol=1e-15)
+    assert np.allclose(Om[0], T / (8 * np.pi * c["eta"] * c["a"] ** 3), rtol=0, atol=1e-15)
+
+
+def _oracle_rows(R, targets, a, trunc):
+    """Dense rows A[n, :, :, :] for the sampled spheres (pair blocks + self)."""
+    N = len(R)
+    MB = tensors.ModeBasis(trunc)
+    g = galerkin.self_scalars(trunc, a)
+    out = np.zeros((len(targets), MB.d, N, MB.d))
+    for k, n in enumerate(targets):
+        m = np.array([j for j in range(N) if j != n])
+        out[k][:, m, :] = np.transpose(galerkin.pair_blocks(R[n] - R[m], a, trunc), (1, 0, 2))
+        out[k][:, n, :] = np.diag(g)
+    return out
+
+
+def test_solve_full_size_sampled_rows(ctx, gbi):
+    """N = 1024, l <= 3, FP32 pair sums + FP64 refinement: sampled rows of the system
+    and of the output evaluated by the oracle with the GPU's solution."""
+    c = workloads.config2()
+    R, p = c["R"], c["p"]
+    N = len(R)
+    inp, V, Om, QH, info = _solve_case(gbi, ctx, R, p, c, 3, 1, d0=0.0, Te_scale=0.0)
+    assert info.rel_residual <= 1e-10
+    MB = tensors.ModeBasis(3)
+    tgt = np.random.default_rng(4).choice(N, size=6, replace=False)
+    rows = _oracle_rows(R, tgt, c["a"], 3)
+    xF = galerkin.lower_trial(inp["Fe"], inp["Te"], c["a"], MB)
+    xQ = QH * MB.scale[6:]
+    xVH = inp["VH"] * MB.scale[6:]
+    x = np.concatenate([xF, xQ], axis=1)                      # (N, d)
+    eta = c["eta"]
+    Ax = np.einsum("kpmq,mq->kp", rows, x)
+    # H rows: G^HH Q + G^HL F = -8 pi eta V^H
+    res = Ax[:, 6:] + 8 * np.pi * eta * xVH[tgt]
+    bscale = np.abs(8 * np.pi * eta * xVH).max()
+    assert np.abs(res).max() / bscale < 1e-8
+    # L rows: V, Omega
+    V_o, Om_o = galerkin.lower_velocity(-Ax[:, :6] / (8 * np.pi * eta), inp["Va"][tgt], inp["Oa"][tgt], c["a"], MB)
+    assert relerr(V[tgt], V_o) < 1e-10
+    assert relerr(Om[tgt], Om_o) < 1e-10
+
+
+def test_mixed_matches_fp64_gpu(ctx, gbi):
+    R, p, s = cloud(200, 31)
+    _, V1, Om1, Q1, i1 = _solve_case(gbi, ctx, R, p, s, 3, 1)
+    _, V0, Om0, Q0, i0 = _solve_case(gbi, ctx, R, p, s, 3, 0)
+    assert relerr(V1, V0) < 1e-9 and relerr(Om1, Om0) < 1e-9 and relerr(Q1, Q0) < 1e-8
+    assert i1.matvecs_f64 < i0.matvecs_f64
+
+
+def test_solve_host_matches_device(ctx, gbi):
+    R, p, s = cloud(50, 8)
+    N = len(R)
+    prm_o = dict(a=s["a"], eta=s["eta"], k=s["k"], vs=s["vs"], s0=s["s0"], d0=0.0)
+    inp = dynamics.trap_inputs(R, p, prm_o, 2)
+    prm = gbi.params(a=s["a"], eta=s["eta"], trunc=2, precision=1)
+    V = np.zeros((N, 3))
+    Om = np.zeros((N, 3))
+    QH = np.zeros((N, 8))
+    c = {k: np.ascontiguousarray(v) for k, v in inp.items()}
+    info, st = ctx.solve_host(prm, np.ascontiguousarray(R), c["Va"], c["Oa"], c["VH"], c["Fe"], c["Te"], V, Om, QH)
+    t = {k: dev(v) for k, v in inp.items()}
+    Vd, Omd, QHd, _, _ = ctx.solve(prm, dev(R), t["Va"], t["Oa"], t["VH"], t["Fe"], t["Te"])
+    torch.cuda.synchronize()
+    assert np.array_equal(V, Vd.cpu().numpy()) and np.array_equal(Om, Omd.cpu().numpy())
+
+
+# ------------------------------------------------------------------ dynamics
+
+@pytest.mark.parametrize("superposition", [True, False])
+def test_trap_steps_match_oracle(ctx, gbi, superposition):
+    R, p, s = cloud(20, 12)
+    prm_o = dict(a=s["a"], eta=s["eta"], k=s["k"], vs=s["vs"], s0=s["s0"], d0=0.01)
+    dt, n = 0.1, 3
+    Rr, pr = dynamics.trajectory(R, p, prm_o, 2, dt, n, superposition=superposition)
+    prm = gbi.params(a=s["a"], eta=s["eta"], trunc=2, precision=0 if superposition else 1)
+    Rd, pd = dev(R), dev(p)
+    info = ctx.trap_step(prm, Rd, pd, dt, s["k"], s["vs"], s["s0"], 0.01, superposition, n)
+    torch.cuda.synchronize()
+    assert relerr(Rd.cpu().numpy(), Rr) < 1e-12
+    assert relerr(pd.cpu().numpy(), pr) < 1e-10
+
+
+def test_trap_inputs_match_oracle(ctx, gbi):
+    R, p, s = cloud(30, 13)
+    for trunc in (2, 3):
+        ref = dynamics.trap_inputs(R, p, dict(k=0.02, vs=0.1, s0=0.05, d0=0.03), trunc)
+        got = ctx.trap_inputs(len(R), trunc, 0.02, 0.1, 0.05, 0.03, dev(R), dev(p))
+        torch.cuda.synchronize()
+        for k in ("Fe", "Te", "Va", "Oa", "VH"):
+            assert np.abs(got[k].cpu().numpy() - ref[k]).max() < 1e-15, k
+
+
+# ------------------------------------------------------------------ edge cases
+
+def test_edge_cases(ctx, gbi):
+    prm = gbi.params(a=1.0, eta=1.0, trunc=2, precision=1)
+    e = torch.zeros((0, 3), dtype=torch.float64, device="cuda")
+    # N = 0 is a no-op
+    V, Om, QH, info, st = ctx.solve(prm, e, e, e, torch.zeros((0, 8), dtype=torch.float64, device="cuda"), e, e)
+    assert st == gbi.GBI_OK and V.shape == (0, 3)
+    # overlapping spheres are rejected before any solve
+    R = dev(np.array([[0.0, 0, 0], [1.5, 0, 0], [5.0, 0, 0]]))
+    z3 = dev(np.zeros((3, 3)))
+    VH = dev(np.zeros((3, 8)))
+    with pytest.raises(gbi.GbiError) as ei:
+        ctx.solve(gbi.params(a=1.0, eta=1.0, trunc=2, min_sep=2.0), R, z3, z3, VH, dev(np.ones((3, 3))), z3)
+    assert ei.value.status == gbi.GBI_ERR_OVERLAP
+    # bad truncation and precision
+    with pytest.raises(gbi.GbiError):
+        ctx.solve(gbi.params(trunc=5), R, z3, z3, VH, z3, z3)
+    with pytest.raises(gbi.GbiError):
+        ctx.apply(3, 2, 1.0, 2, 0, 0, R, VH, VH)          # unsupported row/column pair
+    # iteration cap: NOT_CONVERGED with the best iterate returned
+    Rf, pf, s = cloud(40, 9)
+    inp = dynamics.trap_inputs(Rf, pf, dict(k=0.01, vs=0.1, s0=0.05, d0=0.0), 2)
+    t = {k: dev(v) for k, v in inp.items()}
+    V, Om, QH, info, st = ctx.solve(gbi.params(a=1.0, eta=s["eta"], trunc=2, precision=0, max_iter=1), dev(Rf),
+                                    t["Va"], t["Oa"], t["VH"], t["Fe"], t["Te"], allow_not_converged=True)
+    assert st == gbi.GBI_ERR_NOT_CONVERGED and info.iters == 1 and info.rel_residual > 1e-10
+    assert np.all(np.isfinite(V.cpu().numpy()))
