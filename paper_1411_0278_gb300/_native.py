@@ -124,7 +124,7 @@ def self_scalars(trunc):
 
 
 def _ptr(t):
-    if t is None:
+    if t is None or t.numel() == 0:
         return None
     import torch
     if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
@@ -185,7 +185,7 @@ class Context:
         V = torch.empty((N, 3), dtype=torch.float64, device=R.device)
         Om = torch.empty_like(V)
         if QH is None:
-            QH = torch.zeros((N, h(prm.trunc)), dtype=torch.float64, device=R.device)
+            QH = torch.zeros((N, max(h(prm.trunc), 0)), dtype=torch.float64, device=R.device)
         info = gbi_info()
         st = lib().gbi_solve(self._h, ctypes.byref(prm), int(N), _ptr(R), _ptr(Va), _ptr(Oa), _ptr(VH), _ptr(Fe),
                              _ptr(Te), _ptr(V), _ptr(Om), _ptr(QH), int(bool(warm_start)), ctypes.byref(info))
