@@ -164,6 +164,26 @@ gbi_status gbi_trap_step(gbi_ctx* ctx, const gbi_params* params, int N, double d
                          double vs, double s0, double d0, int superposition, int nsteps,
                          double* R, double* p, gbi_info* info);
 
+/* gbi_solve without any allocation.  For callers that cannot allocate device memory
+ * while they run -- code inside a framework that owns every allocation, a real-time
+ * loop that forbids cudaMalloc/cudaFree, or a host that pre-plans its memory -- this
+ * entry point performs the same solve as gbi_solve (same arguments and results) but
+ * takes every scratch buffer from one static device array of the library (about
+ * 2.6 MB, held by every GPU that loads the library until the process exits) and its
+ * read-back scalars from a static host array.  It needs no context: work is queued
+ * on `stream` (a cudaStream_t, NULL = default stream) of the current device.
+ * The paper has no counterpart; it is an engineering entry point.
+ * Limits: N <= 1024, N * gbi_h(trunc) <= 8192, params.restart <= 32 (a value <= 0
+ * selects 32); anything larger returns GBI_ERR_ARG before any work.
+ * The first call on a device looks up the array's device address (set-up); make that
+ * first call before any stream capture on the device.  All calls share the array:
+ * calls that overlap on the GPU (other threads or streams) race, and each call
+ * re-initialises whatever must start at zero.  Synchronous. */
+gbi_status gbi_solve_static(void* stream, const gbi_params* params, int N,
+                            const double* R, const double* Va, const double* Oa, const double* VH,
+                            const double* Fe, const double* Te,
+                            double* V, double* Omega, double* QH, int warm_start, gbi_info* info);
+
 /* Instrumentation.  gbi_kernel_launches: number of CUDA kernels this context has
  * launched since creation.  gbi_set_profiling(ctx, 1) resets the per-class
  * statistics and from then on records a CUDA event pair on the context's stream

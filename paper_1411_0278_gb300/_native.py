@@ -63,6 +63,7 @@ _SIGS = {
     "gbi_trap_inputs": (_I, [_VP, _I, _I, _D, _D, _D, _D] + [_VP] * 7),
     "gbi_trap_step": (_I, [_VP, ctypes.POINTER(gbi_params), _I, _D, _D, _D, _D, _D, _I, _I, _VP, _VP,
                            ctypes.POINTER(gbi_info)]),
+    "gbi_solve_static": (_I, [_VP, ctypes.POINTER(gbi_params), _I] + [_VP] * 9 + [_I, ctypes.POINTER(gbi_info)]),
     "gbi_kernel_launches": (ctypes.c_longlong, [_VP]),
     "gbi_set_profiling": (_I, [_VP, _I]),
     "gbi_kernel_stats": (_I, [_VP, _I, c_double_p, ctypes.POINTER(ctypes.c_longlong), c_double_p]),
@@ -130,6 +131,20 @@ def _ptr(t):
     if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
         raise ValueError("expected a contiguous float64 CUDA tensor")
     return ctypes.c_void_p(t.data_ptr())
+
+
+def solve_static(prm, R, Va, Oa, VH, Fe, Te, V, Om, QH, warm_start=False, stream=None):
+    """gbi_solve_static: the solve with all scratch in the library's static device array.
+
+    Outputs V, Om, QH are caller-allocated float64 CUDA tensors; returns (info, status)."""
+    info = gbi_info()
+    handle = getattr(stream, "cuda_stream", stream)
+    st = lib().gbi_solve_static(ctypes.c_void_p(int(handle) if handle else 0), ctypes.byref(prm), int(R.shape[0]),
+                                _ptr(R), _ptr(Va), _ptr(Oa), _ptr(VH), _ptr(Fe), _ptr(Te), _ptr(V), _ptr(Om),
+                                _ptr(QH), int(bool(warm_start)), ctypes.byref(info))
+    if st not in (GBI_OK, GBI_ERR_NOT_CONVERGED):
+        raise GbiError(st, "gbi_solve_static")
+    return info, st
 
 
 def params(a=1.0, eta=1.0, trunc=2, precision=1, rtol=1e-10, restart=40, max_iter=1000, max_refine=8,

@@ -947,3 +947,87 @@ gbi_status gbi_solve_host(gbi_ctx* ctx, const gbi_params* prm, int N, const doub
 }
 
 }  // extern "C"
+
+// =================================================================================
+// Solve without allocation: the whole workspace lives in one file-scope device array.
+// =================================================================================
+
+namespace {
+
+constexpr int kStaticMaxN = 1024;         // spheres
+constexpr int kStaticMaxNH = 8192;        // spheres x higher components (N * gbi_h(trunc))
+constexpr int kStaticMaxRestart = 32;     // Krylov vectors per GMRES cycle
+constexpr int kStaticMaxND = kStaticMaxNH + 6 * kStaticMaxN;
+
+constexpr size_t al256(size_t b) { return (b + 255) / 256 * 256; }
+
+// byte offsets of every workspace buffer gbi_solve touches
+constexpr size_t kOffHi = 0;
+constexpr size_t kOffLo = kOffHi + al256(sizeof(float) * 4 * kStaticMaxN);
+constexpr size_t kOff64 = kOffLo + al256(sizeof(float) * 4 * kStaticMaxN);
+constexpr size_t kOffXQ = kOff64 + al256(sizeof(double) * 4 * kStaticMaxN);
+constexpr size_t kOffXVH = kOffXQ + al256(sizeof(double) * kStaticMaxND);
+constexpr size_t kOffB = kOffXVH + al256(sizeof(double) * kStaticMaxNH);
+constexpr size_t kOffR = kOffB + al256(sizeof(double) * kStaticMaxNH);
+constexpr size_t kOffDelta = kOffR + al256(sizeof(double) * kStaticMaxNH);
+constexpr size_t kOffXVL = kOffDelta + al256(sizeof(double) * kStaticMaxNH);
+constexpr size_t kOffKry = kOffXVL + al256(sizeof(double) * 6 * kStaticMaxN);
+constexpr size_t kOffW = kOffKry + al256(sizeof(double) * (size_t)(kStaticMaxRestart + 1) * kStaticMaxNH);
+constexpr size_t kOffPart = kOffW + al256(sizeof(double) * kStaticMaxNH);
+constexpr size_t kOffDots = kOffPart + al256(sizeof(double) * 64 * (kMaxRestart + 2));
+constexpr size_t kOffMin = kOffDots + al256(sizeof(double) * (2 * kMaxRestart + 8));
+constexpr size_t kStaticBytes = kOffMin + 256;
+
+// The scratch itself (about 2.6 MB).  Every device that loads the library holds it
+// until the process exits.  Host code must not use this symbol as an address.
+__device__ __align__(256) unsigned char g_solve_scratch[kStaticBytes];
+
+constexpr int kStaticMaxDevices = 64;
+void* g_scratch_addr[kStaticMaxDevices] = {nullptr};   // device address, per device ordinal
+double g_static_scalars[2 * kMaxRestart + 16];          // host read-back scalars (pageable)
+
+}  // namespace
+
+extern "C" gbi_status gbi_solve_static(void* stream, const gbi_params* prm, int N, const double* R,
+                                       const double* Va, const double* Oa, const double* VH, const double* Fe,
+                                       const double* Te, double* V, double* Omega, double* QH, int warm_start,
+                                       gbi_info* info) {
+  if (!valid_params(prm) || N < 0) return GBI_ERR_ARG;
+  const int h = gbi_h(prm->trunc);
+  if (N > kStaticMaxN || (long long)N * h > kStaticMaxNH) return GBI_ERR_ARG;
+  if (prm->restart > kStaticMaxRestart) return GBI_ERR_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kStaticMaxDevices) return GBI_ERR_CUDA;
+  if (g_scratch_addr[dev] == nullptr) {
+    // one-time set-up on this device: the device address of the static array
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_solve_scratch) != cudaSuccess || p == nullptr) return GBI_ERR_CUDA;
+    g_scratch_addr[dev] = p;
+  }
+  unsigned char* base = static_cast<unsigned char*>(g_scratch_addr[dev]);
+  gbi_ctx c;
+  c.device = dev;
+  c.stream = reinterpret_cast<cudaStream_t>(stream);
+  c.hbuf = g_static_scalars;
+  auto bind = [&](Buf& b, size_t off, size_t bytes) {
+    b.p = base + off;
+    b.bytes = bytes;
+  };
+  bind(c.pos_hi, kOffHi, kOffLo - kOffHi);
+  bind(c.pos_lo, kOffLo, kOff64 - kOffLo);
+  bind(c.pos64, kOff64, kOffXQ - kOff64);
+  bind(c.xQ, kOffXQ, kOffXVH - kOffXQ);
+  bind(c.xVH, kOffXVH, kOffB - kOffXVH);
+  bind(c.b, kOffB, kOffR - kOffB);
+  bind(c.r, kOffR, kOffDelta - kOffR);
+  bind(c.delta, kOffDelta, kOffXVL - kOffDelta);
+  bind(c.xVL, kOffXVL, kOffKry - kOffXVL);
+  bind(c.krylov, kOffKry, kOffW - kOffKry);
+  bind(c.w, kOffW, kOffPart - kOffW);
+  bind(c.partial, kOffPart, kOffDots - kOffPart);
+  bind(c.dots, kOffDots, kOffMin - kOffDots);
+  bind(c.minr2, kOffMin, 256);
+  gbi_params p = *prm;
+  if (p.restart <= 0) p.restart = kStaticMaxRestart;
+  return gbi_solve(&c, &p, N, R, Va, Oa, VH, Fe, Te, V, Omega, QH, warm_start, info);
+}
