@@ -66,7 +66,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "25"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (OSError, ValueError):
             self.proc = None
@@ -196,7 +196,8 @@ def run_ours(args):
     c = workloads.config2()
     N, trunc = len(c["R"]), c["trunc"]
     dt = 0.1
-    prm = gbi.params(a=c["a"], eta=c["eta"], trunc=trunc, precision=1, rtol=1e-10, restart=40, inner_rtol=1e-5)
+    prm = gbi.params(a=c["a"], eta=c["eta"], trunc=trunc, precision=args.precision, rtol=1e-10, restart=40,
+                     inner_rtol=1e-5)
     R0 = torch.tensor(c["R"], dtype=torch.float64, device=dev)
     p0 = torch.tensor(c["p"], dtype=torch.float64, device=dev)
     R, p = R0.clone(), p0.clone()
@@ -251,7 +252,7 @@ def run_ours(args):
         pairs += info.pair_interactions
     barrier()
     launches = ctx.kernel_launches() - launches0
-    stats = {cls: ctx.kernel_stats(cls) for cls in range(20)}
+    stats = {cls: ctx.kernel_stats(cls) for cls in range(gbi._native.N_KERNEL_CLASSES)}
     ctx.set_profiling(False)
     clocks = sampler.stop()
 
@@ -270,14 +271,18 @@ def run_ours(args):
     # ---- dominant kernel and its roofline
     peaks, peak_src = load_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    names = {17: "pair_kernel<l3, H, H, float>", 8: "pair_kernel<l3, H, H, double>",
-             7: "pair_kernel<l3, H, L, double>", 3: "pair_kernel<l3, L, all, double>"}
+    tname = {0: "double", 1: "float", 2: "double-float"}
+    sname = {0: "all", 1: "L", 2: "H"}
+    names = {pr * 9 + r * 3 + cc: "pair_kernel<l3, %s, %s, %s>" % (sname[r], sname[cc], tname[pr])
+             for pr in range(3) for r in range(3) for cc in range(3)}
+    names[27] = "trap pass FP64"
+    names[28] = "trap pass FP32"
     dom = max(stats, key=lambda k: stats[k]["ms"])
     st = stats[dom]
     avg_ms = st["ms"] / max(1, st["launches"])
     flops_per_launch = st["flops"] / max(1, st["launches"])
     achieved = flops_per_launch / (avg_ms * 1e-3) / 1e12
-    is_f32 = dom in (17, 19) or (9 <= dom < 18)
+    is_f32 = dom == 28 or (9 <= dom < 27)       # FP32 and double-float classes run on the FP32 pipe
     peak = fp32_alu_peak_tflops(sm_max) if is_f32 else FP64_NOMINAL_TFLOPS
     kernel_share = {names.get(k, "class%d" % k): round(v["ms"] / max(1e-9, sum(s["ms"] for s in stats.values())), 4)
                     for k, v in stats.items() if v["launches"]}
@@ -286,6 +291,8 @@ def run_ours(args):
                 "peak_source": ("FP32 CUDA-core peak 152 SMs x 128 lanes x 2 x %.0f MHz (sm_max_mhz of %s "
                                 "MEASURED_PEAKS.json)" % (sm_max, peak_src)) if is_f32 else
                                "GB300 FP64 nominal 1.25 TFLOP/s",
+                "flop_convention": "algorithmic flops of the pair formula (FMA = 2); double-float passes count "
+                                   "the same formula although each flop costs ~10-20 FP32 instructions",
                 "flops_per_launch": flops_per_launch, "avg_launch_ms": avg_ms, "launches": st["launches"],
                 "time_share": kernel_share}
 
@@ -343,7 +350,7 @@ def run_ours(args):
     ach3 = s3["flops"] / (s3["ms"] * 1e-3) / 1e12
     superposition = {"workload": c3["name"], "N": N3, "value": n3 * N3 * (N3 - 1) / t3, "unit": UNIT,
                      "ms_per_pass": 1e3 * t3 / n3,
-                     "roofline": {"bound": "alu", "kernel": "trap_kernel<float>", "achieved": ach3,
+                     "roofline": {"bound": "alu", "kernel": "trap superposition pass (pack + trap_pairs<float> + finish)", "achieved": ach3,
                                   "peak": fp32_alu_peak_tflops(sm_max), "unit": "TFLOP/s",
                                   "frac": ach3 / fp32_alu_peak_tflops(sm_max), "traffic": None,
                                   "avg_launch_ms": s3["ms"] / max(1, s3["launches"])},
@@ -358,7 +365,9 @@ def run_ours(args):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-                "precision": "FP32 pair sums in GMRES; FP64 RHS, residuals, Arnoldi, Givens, outputs",
+                "precision": {0: "FP64 throughout", 1: "FP32 pair sums in GMRES; FP64 RHS, residuals, outputs; FP64 "
+                              "Arnoldi/Givens", 2: "FP32 pair sums in GMRES; double-float (FP32-pipe, ~48-bit) RHS, "
+                              "residuals, outputs; FP64 Arnoldi/Givens"}[args.precision],
                 "data": "synthetic",
                 "config": {"workload": c["name"], "N": N, "trunc": trunc, "h": h, "volume_fraction": 0.05,
                            "min_sep_a": 2.5, "rtol": 1e-10, "restart": 40, "inner_rtol": 1e-5,
@@ -377,9 +386,11 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", type=int, default=2, choices=[0, 1, 2],
+                    help="0 all FP64; 1 FP32 GMRES + FP64 refinement; 2 FP32 GMRES + double-float refinement")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -55,7 +55,10 @@ typedef struct {
   double eta;        /* viscosity                                                        */
   int trunc;         /* 2, 3 or 4: mode set 1s 2a | 2s 3t (+3a 3s 4t) (+4a 4s 5t)        */
   int precision;     /* 0: FP64 pair sums throughout; 1: FP32 pair sums inside GMRES,     */
-                     /*    FP64 residuals (iterative refinement)                         */
+                     /*    FP64 right-hand side, residuals and outputs (iterative         */
+                     /*    refinement); 2: as 1 but those FP64 passes run in double-float */
+                     /*    arithmetic (pairs of floats, ~48-bit significand) on the FP32  */
+                     /*    pipe.  Arnoldi, Givens and the solution update stay FP64.      */
   double rtol;       /* target relative residual ||b - A q|| / ||b|| of the traction solve */
   int restart;       /* GMRES restart length (Krylov vectors per cycle), 1..128          */
   int max_iter;      /* cap on inner GMRES iterations over the whole solve               */
@@ -68,7 +71,7 @@ typedef struct {
   int iters;                 /* inner GMRES iterations                                   */
   int refinements;           /* FP64 residual evaluations after the first                */
   int matvecs_f32;           /* FP32 pair passes                                         */
-  int matvecs_f64;           /* FP64 pair passes                                         */
+  int matvecs_f64;           /* FP64 or double-float pair passes                         */
   double rel_residual;       /* final ||b - A q|| / ||b|| in FP64                        */
   double min_separation;     /* smallest centre distance seen, in units of a             */
   long long pair_interactions; /* ordered pairs evaluated, summed over all pair passes   */
@@ -107,7 +110,8 @@ gbi_status gbi_self_scalars(int trunc, double* out_host);
  * x, y are component-major: x[q*N + m].  rows / cols select the components:
  * 0 = all (gbi_d), 1 = rigid-body (first 6), 2 = higher (last gbi_h); x and y point
  * at the first component of their set.  add_self requires rows == cols.
- * precision 0 = FP64 arithmetic, 1 = FP32 arithmetic (FP64 in/out).
+ * precision 0 = FP64 arithmetic, 1 = FP32 arithmetic, 2 = double-float arithmetic on the
+ * FP32 pipe (not for rows = cols = 0); inputs and outputs FP64 in every case.
  * R: [N][3] centres.  Cost: N(N-1) pair interactions. */
 gbi_status gbi_apply(gbi_ctx* ctx, int N, int trunc, double a, int rows, int cols, int precision,
                      const double* R, const double* x, double* y, double alpha, double beta, int add_self);
@@ -140,7 +144,8 @@ gbi_status gbi_solve_host(gbi_ctx* ctx, const gbi_params* params, int N,
  * remains.  params.trunc = 2 uses the closed-form trap kernel (Stokeslet/RPY,
  * rotlet, stresslet and potential dipole with their finite-size terms);
  * trunc 3, 4 use the general pair operator.  Arguments as gbi_solve (no QH).
- * params.precision selects FP32 (1) or FP64 (0) pair arithmetic.  Asynchronous. */
+ * params.precision selects FP32 (1) or FP64 (0) pair arithmetic; 2 selects FP64 for the
+ * closed-form kernel and double-float for the general one.  Asynchronous. */
 gbi_status gbi_superpose(gbi_ctx* ctx, const gbi_params* params, int N,
                          const double* R, const double* Va, const double* Oa, const double* VH,
                          const double* Fe, const double* Te, double* V, double* Omega);
@@ -191,9 +196,9 @@ gbi_status gbi_solve_static(void* stream, const gbi_params* params, int N,
  * event time in ms, the number of launches and the algorithmic flops (the
  * per-pair count of the implemented closed form times N(N-1)).  Class ids:
  * precision * 9 + rows * 3 + cols for gbi_apply-style passes (precision 0 = FP64,
- * 1 = FP32; rows/cols 0 = all, 1 = rigid-body, 2 = higher), 18 = closed-form
- * trap kernel in FP64, 19 = in FP32.  gbi_kernel_stats synchronizes on the
- * recorded events. */
+ * 1 = FP32, 2 = double-float; rows/cols 0 = all, 1 = rigid-body, 2 = higher),
+ * 27 = closed-form trap pass in FP64, 28 = in FP32.  gbi_kernel_stats synchronizes
+ * on the recorded events. */
 long long gbi_kernel_launches(gbi_ctx* ctx);
 gbi_status gbi_set_profiling(gbi_ctx* ctx, int on);
 gbi_status gbi_kernel_stats(gbi_ctx* ctx, int kernel_class, double* total_ms, long long* launches,

@@ -74,7 +74,8 @@ def kernel_class(precision, rows, cols):
     return precision * 9 + rows * 3 + cols
 
 
-TRAP_F64, TRAP_F32 = 18, 19
+TRAP_F64, TRAP_F32 = 27, 28
+N_KERNEL_CLASSES = 30
 
 
 def lib():

@@ -16,13 +16,27 @@
 #include "gbi_internal.cuh"
 
 namespace gbi {
-cudaError_t launch_pairs_f32(int trunc, int rows, int cols, const PairArgs& args, cudaStream_t stream);
-cudaError_t launch_pairs_f64(int trunc, int rows, int cols, const PairArgs& args, cudaStream_t stream);
+#define GBI_DECL(P)                                                                       \
+  cudaError_t launch_pairs_##P##_2(int, int, const PairArgs&, cudaStream_t);              \
+  cudaError_t launch_pairs_##P##_3(int, int, const PairArgs&, cudaStream_t);              \
+  cudaError_t launch_pairs_##P##_4(int, int, const PairArgs&, cudaStream_t);
+GBI_DECL(f32)
+GBI_DECL(f64)
+GBI_DECL(df)
+#undef GBI_DECL
 
+// precision: 0 = FP64, 1 = FP32, 2 = double-float on the FP32 pipe
 cudaError_t launch_pairs(int trunc, int rows, int cols, int precision, const PairArgs& args,
                          cudaStream_t stream) {
-  return precision == 1 ? launch_pairs_f32(trunc, rows, cols, args, stream)
-                        : launch_pairs_f64(trunc, rows, cols, args, stream);
+#define GBI_DISPATCH(P)                                                   \
+  if (trunc == 2) return launch_pairs_##P##_2(rows, cols, args, stream);  \
+  if (trunc == 3) return launch_pairs_##P##_3(rows, cols, args, stream);  \
+  if (trunc == 4) return launch_pairs_##P##_4(rows, cols, args, stream);  \
+  return cudaErrorInvalidValue;
+  if (precision == 1) { GBI_DISPATCH(f32) }
+  if (precision == 2) { GBI_DISPATCH(df) }
+  GBI_DISPATCH(f64)
+#undef GBI_DISPATCH
 }
 
 double pair_flops(int trunc, int rows, int cols) {
@@ -50,7 +64,7 @@ struct gbi_ctx {
   cudaStream_t stream = nullptr;
   std::string err;
   Buf pos_hi, pos_lo, pos64;
-  Buf xF, xVH, b, xQ, r, delta, krylov, w, partial, dots, xVL, minr2, colbuf;
+  Buf xF, xVH, b, xQ, r, delta, krylov, w, partial, dots, xVL, minr2, colbuf, x32, trapbuf;
   Buf tFe, tTe, tVa, tOa, tVH, tV, tOm, tQH;   // trap-step / host-call staging
   Buf hR, hVa, hOa, hVH, hFe, hTe, hV, hOm, hQH;
   double* hbuf = nullptr;                      // pinned scalars read back by GMRES
@@ -63,9 +77,9 @@ struct gbi_ctx {
   };
   std::vector<Rec> pending;
   std::vector<cudaEvent_t> pool;
-  double stat_ms[20] = {0};
-  double stat_flops[20] = {0};
-  long long stat_n[20] = {0};
+  double stat_ms[30] = {0};
+  double stat_flops[30] = {0};
+  long long stat_n[30] = {0};
 };
 
 namespace {
@@ -133,10 +147,10 @@ void drain_profile(gbi_ctx* ctx) {
 }
 
 // One pair pass with launch counting and optional event timing.
-// Class: precision * 9 + rows * 3 + cols for the generic operator, 18/19 for the
-// closed-form trap kernel in FP64/FP32.
+// Class: precision * 9 + rows * 3 + cols for the generic operator (precision 0 FP64,
+// 1 FP32, 2 double-float), 27/28 for the closed-form trap kernel in FP64/FP32.
 template <typename F>
-cudaError_t timed(gbi_ctx* ctx, int cls, double flops, F&& launch) {
+cudaError_t timed(gbi_ctx* ctx, int cls, double flops, int nlaunch, F&& launch) {
   cudaEvent_t a = nullptr, b = nullptr;
   if (ctx->prof) {
     a = take_event(ctx);
@@ -144,7 +158,7 @@ cudaError_t timed(gbi_ctx* ctx, int cls, double flops, F&& launch) {
     cudaEventRecord(a, ctx->stream);
   }
   cudaError_t e = launch();
-  ++ctx->launches;
+  ctx->launches += nlaunch;
   if (ctx->prof) {
     cudaEventRecord(b, ctx->stream);
     ctx->pending.push_back({a, b, cls, flops});
@@ -152,15 +166,71 @@ cudaError_t timed(gbi_ctx* ctx, int cls, double flops, F&& launch) {
   return e;
 }
 
-cudaError_t run_pairs(gbi_ctx* ctx, int trunc, int rows, int cols, int precision, const PairArgs& args) {
-  const double flops = pair_flops(trunc, rows, cols) * double(args.N) * double(args.N - 1);
-  return timed(ctx, precision * 9 + rows * 3 + cols, flops,
+struct ColScale {
+  double v[54];
+};
+
+// y = float(x * cs[component]) for a component-major [nc][N] block
+__global__ void k_to_f32_s(size_t n, int N, const double* __restrict__ x, ColScale cs, float* __restrict__ y) {
+  const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i < n) y[i] = float(x[i] * cs.v[i / N]);
+}
+
+__global__ void k_to_df_s(size_t n, int N, const double* __restrict__ x, ColScale cs, float* __restrict__ hi,
+                          float* __restrict__ lo) {
+  const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i < n) {
+    const double v = x[i] * cs.v[i / N];
+    const float h = float(v);
+    hi[i] = h;
+    lo[i] = float(v - double(h));
+  }
+}
+
+int ncols_of(int trunc, int cols) {
+  const int D = trunc == 2 ? GbiTrunc2::D : trunc == 3 ? GbiTrunc3::D : GbiTrunc4::D;
+  return cols == SET_L ? 6 : cols == SET_H ? D - 6 : D;
+}
+
+cudaError_t run_pairs(gbi_ctx* ctx, int trunc, int rows, int cols, int precision, const PairArgs& args_in) {
+  const double flops = pair_flops(trunc, rows, cols) * double(args_in.N) * double(args_in.N - 1);
+  PairArgs args = args_in;
+  int extra = 0;
+  if (precision == 2) {
+    // double-float sources: hi = float(x * cs), lo = float(x * cs - hi), once per pass
+    const int nc = ncols_of(trunc, cols);
+    const size_t n = (size_t)nc * args.N;
+    if (ensure(ctx, ctx->x32, 2 * sizeof(float) * n) != GBI_OK) return cudaErrorMemoryAllocation;
+    ColScale cs;
+    const int c0 = cols == SET_H ? 6 : 0;
+    for (int i = 0; i < 54; ++i) cs.v[i] = (i < nc) ? args.colscale[c0 + i] : 1.0;
+    k_to_df_s<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(n, args.N, args.x, cs, P<float>(ctx->x32),
+                                                                     P<float>(ctx->x32) + n);
+    args.x32 = P<float>(ctx->x32);
+    args.x32lo = P<float>(ctx->x32) + n;
+    extra = 1;
+  }
+  if (precision == 1) {
+    // FP32 sources: scale and round once per pass, so the pair loop touches no FP64
+    const int nc = ncols_of(trunc, cols);
+    const size_t n = (size_t)nc * args.N;
+    if (ensure(ctx, ctx->x32, sizeof(float) * n) != GBI_OK) return cudaErrorMemoryAllocation;
+    ColScale cs;
+    const int c0 = cols == SET_H ? 6 : 0;
+    for (int i = 0; i < 54; ++i) cs.v[i] = (i < nc) ? args.colscale[c0 + i] : 1.0;
+    k_to_f32_s<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(n, args.N, args.x, cs, P<float>(ctx->x32));
+    args.x32 = P<float>(ctx->x32);
+    extra = 1;
+  }
+  return timed(ctx, precision * 9 + rows * 3 + cols, flops, 1 + extra,
                [&] { return launch_pairs(trunc, rows, cols, precision, args, ctx->stream); });
 }
 
 cudaError_t run_trap(gbi_ctx* ctx, const TrapArgs& t, int precision) {
   const double flops = trap_flops() * double(t.N) * double(t.N - 1);
-  return timed(ctx, precision == 1 ? 19 : 18, flops, [&] { return launch_trap(t, precision, ctx->stream); });
+  if (ensure(ctx, ctx->trapbuf, trap_scratch_bytes(t.N, precision)) != GBI_OK) return cudaErrorMemoryAllocation;
+  return timed(ctx, precision == 1 ? 28 : 27, flops, 3,
+               [&] { return launch_trap(t, precision, ctx->trapbuf.p, ctx->stream); });
 }
 
 int d_of(int trunc) { return trunc == 2 ? GbiTrunc2::D : trunc == 3 ? GbiTrunc3::D : trunc == 4 ? GbiTrunc4::D : -1; }
@@ -385,6 +455,8 @@ PairArgs pair_args(const Setup& s, const double* x, double* y, double alpha, dou
   p.a = s.a;
   p.pos = s.pos;
   p.x = x;
+  p.x32 = nullptr;
+  p.x32lo = nullptr;
   p.y = y;
   p.alpha = alpha;
   p.beta = beta;
@@ -540,7 +612,7 @@ bool valid_params(const gbi_params* p) {
   if (!p) return false;
   if (!(p->a > 0) || !(p->eta > 0)) return false;
   if (p->trunc < 2 || p->trunc > 4) return false;
-  if (p->precision != 0 && p->precision != 1) return false;
+  if (p->precision < 0 || p->precision > 2) return false;
   return true;
 }
 
@@ -574,7 +646,7 @@ gbi_status gbi_destroy(gbi_ctx* ctx) {
   cudaStreamSynchronize(ctx->stream);
   Buf* bufs[] = {&ctx->pos_hi, &ctx->pos_lo, &ctx->pos64, &ctx->xF, &ctx->xVH, &ctx->b, &ctx->xQ, &ctx->r,
                  &ctx->delta, &ctx->krylov, &ctx->w, &ctx->partial, &ctx->dots, &ctx->xVL, &ctx->minr2,
-                 &ctx->colbuf, &ctx->tFe, &ctx->tTe, &ctx->tVa, &ctx->tOa, &ctx->tVH, &ctx->tV, &ctx->tOm,
+                 &ctx->colbuf, &ctx->x32, &ctx->trapbuf, &ctx->tFe, &ctx->tTe, &ctx->tVa, &ctx->tOa, &ctx->tVH, &ctx->tV, &ctx->tOm,
                  &ctx->tQH, &ctx->hR, &ctx->hVa, &ctx->hOa, &ctx->hVH, &ctx->hFe, &ctx->hTe, &ctx->hV,
                  &ctx->hOm, &ctx->hQH};
   for (Buf* b : bufs)
@@ -630,12 +702,13 @@ gbi_status gbi_self_scalars(int trunc, double* out_host) {
 
 gbi_status gbi_apply(gbi_ctx* ctx, int N, int trunc, double a, int rows, int cols, int precision,
                      const double* R, const double* x, double* y, double alpha, double beta, int add_self) {
-  if (!ctx || N < 0 || d_of(trunc) < 0 || !(a > 0) || (precision != 0 && precision != 1)) return GBI_ERR_ARG;
+  if (!ctx || N < 0 || d_of(trunc) < 0 || !(a > 0) || precision < 0 || precision > 2) return GBI_ERR_ARG;
   if (N == 0) return GBI_OK;
   if (!R || !x || !y) return GBI_ERR_ARG;
   const bool supported = (rows == SET_H && cols == SET_L) || (rows == SET_H && cols == SET_H) ||
                          (rows == SET_L && cols == SET_ALL) || (rows == SET_ALL && cols == SET_ALL);
   if (!supported) return GBI_ERR_ARG;
+  if (precision == 2 && rows == SET_ALL && cols == SET_ALL) return GBI_ERR_ARG;
   if (add_self && rows != cols && !(rows == SET_L && cols == SET_ALL)) return GBI_ERR_ARG;
   Setup s;
   GBI_TRY(setup_call(ctx, s, N, trunc, a, 1.0, R));
@@ -657,6 +730,8 @@ gbi_status gbi_solve(gbi_ctx* ctx, const gbi_params* prm, int N, const double* R
   GBI_TRY(setup_call(ctx, s, N, prm->trunc, prm->a, prm->eta, R));
   const int D = s.D, h = s.h;
   const size_t nh = (size_t)N * h;
+  // arithmetic of the passes that need more than FP32: FP64, or double-float (precision 2)
+  const int hp = prm->precision == 2 ? 2 : 0;
   GBI_TRY(ensure(ctx, ctx->xQ, sizeof(double) * (size_t)N * D));
   GBI_TRY(ensure(ctx, ctx->xVH, sizeof(double) * nh));
   GBI_TRY(ensure(ctx, ctx->b, sizeof(double) * nh));
@@ -687,7 +762,7 @@ gbi_status gbi_solve(gbi_ctx* ctx, const gbi_params* prm, int N, const double* R
   {
     PairArgs p = pair_args(s, xF, b, -1.0, 1.0, 0, s.ones, 0);
     p.min_r2_bits = P<unsigned int>(ctx->minr2);
-    GBI_CHECK(run_pairs(ctx, s.trunc, SET_H, SET_L, 0, p));
+    GBI_CHECK(run_pairs(ctx, s.trunc, SET_H, SET_L, hp, p));
     inf->matvecs_f64 += 1;
     inf->pair_interactions += s.pairs_per_pass;
   }
@@ -736,7 +811,7 @@ gbi_status gbi_solve(gbi_ctx* ctx, const gbi_params* prm, int N, const double* R
     const int max_refine = prm->max_refine > 0 ? prm->max_refine : 8;
     for (int sweep = 0;; ++sweep) {
       GBI_CHECK(cudaMemcpyAsync(r, b, sizeof(double) * nh, cudaMemcpyDeviceToDevice, ctx->stream));
-      if (!(zero && sweep == 0)) GBI_TRY(apply_HH(ctx, s, 0, xQH, r, -1.0, 1.0, s.ones, inf));
+      if (!(zero && sweep == 0)) GBI_TRY(apply_HH(ctx, s, hp, xQH, r, -1.0, 1.0, s.ones, inf));
       double rn;
       GBI_TRY(norm2(ctx, nh, r, rn));
       inf->rel_residual = rn / bnorm;
@@ -760,7 +835,7 @@ gbi_status gbi_solve(gbi_ctx* ctx, const gbi_params* prm, int N, const double* R
   {
     PairArgs p = pair_args(s, P<double>(ctx->xQ), P<double>(ctx->xVL), -1.0 / (8.0 * kPi * s.eta), 0.0, 1,
                            s.ones, 0);
-    GBI_CHECK(run_pairs(ctx, s.trunc, SET_L, SET_ALL, 0, p));
+    GBI_CHECK(run_pairs(ctx, s.trunc, SET_L, SET_ALL, hp, p));
     inf->matvecs_f64 += 1;
     inf->pair_interactions += s.pairs_per_pass;
   }
@@ -890,7 +965,7 @@ gbi_status gbi_set_profiling(gbi_ctx* ctx, int on) {
   if (!ctx) return GBI_ERR_ARG;
   drain_profile(ctx);
   ctx->prof = on != 0;
-  for (int i = 0; i < 20; ++i) {
+  for (int i = 0; i < 30; ++i) {
     ctx->stat_ms[i] = 0.0;
     ctx->stat_flops[i] = 0.0;
     ctx->stat_n[i] = 0;
@@ -900,7 +975,7 @@ gbi_status gbi_set_profiling(gbi_ctx* ctx, int on) {
 
 gbi_status gbi_kernel_stats(gbi_ctx* ctx, int kernel_class, double* total_ms, long long* launches,
                             double* flops) {
-  if (!ctx || kernel_class < 0 || kernel_class >= 20) return GBI_ERR_ARG;
+  if (!ctx || kernel_class < 0 || kernel_class >= 30) return GBI_ERR_ARG;
   drain_profile(ctx);
   if (total_ms) *total_ms = ctx->stat_ms[kernel_class];
   if (launches) *launches = ctx->stat_n[kernel_class];
@@ -976,7 +1051,8 @@ constexpr size_t kOffW = kOffKry + al256(sizeof(double) * (size_t)(kStaticMaxRes
 constexpr size_t kOffPart = kOffW + al256(sizeof(double) * kStaticMaxNH);
 constexpr size_t kOffDots = kOffPart + al256(sizeof(double) * 64 * (kMaxRestart + 2));
 constexpr size_t kOffMin = kOffDots + al256(sizeof(double) * (2 * kMaxRestart + 8));
-constexpr size_t kStaticBytes = kOffMin + 256;
+constexpr size_t kOffX32 = kOffMin + 256;
+constexpr size_t kStaticBytes = kOffX32 + al256(sizeof(float) * kStaticMaxND);
 
 // The scratch itself (about 2.6 MB).  Every device that loads the library holds it
 // until the process exits.  Host code must not use this symbol as an address.
@@ -1027,6 +1103,7 @@ extern "C" gbi_status gbi_solve_static(void* stream, const gbi_params* prm, int 
   bind(c.partial, kOffPart, kOffDots - kOffPart);
   bind(c.dots, kOffDots, kOffMin - kOffDots);
   bind(c.minr2, kOffMin, 256);
+  bind(c.x32, kOffX32, kStaticBytes - kOffX32);
   gbi_params p = *prm;
   if (p.restart <= 0) p.restart = kStaticMaxRestart;
   return gbi_solve(&c, &p, N, R, Va, Oa, VH, Fe, Te, V, Omega, QH, warm_start, info);

@@ -33,6 +33,9 @@ struct PairArgs {
   double a;
   Positions pos;
   const double* x;       // component-major, first component of the column set
+  const float* x32;      // FP32 kernels: x pre-scaled by colscale and rounded (may be null);
+                         // double-float kernels: the hi part of the same
+  const float* x32lo;    // double-float kernels: the lo part (x * colscale - hi)
   double* y;             // component-major, first component of the row set
   double alpha, beta;
   int add_self;
@@ -59,7 +62,11 @@ struct TrapArgs {
   double* Om;           // [N][3]
 };
 
-cudaError_t launch_trap(const TrapArgs& args, int precision, cudaStream_t stream);
+// Three launches (record packing, split pair sums, fixed-order reduction); scratch must
+// hold trap_scratch_bytes(N, precision) bytes, 256-byte aligned.
+cudaError_t launch_trap(const TrapArgs& args, int precision, void* scratch, cudaStream_t stream);
+size_t trap_scratch_bytes(int N, int precision);
+int trap_splits(int N);
 
 // Flop counts per ordered pair used for the roofline accounting.
 double pair_flops(int trunc, int rows, int cols);

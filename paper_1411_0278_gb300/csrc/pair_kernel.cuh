@@ -16,6 +16,7 @@
 
 #include <type_traits>
 
+#include "df.cuh"
 #include "gbi_generated.cuh"
 #include "gbi_internal.cuh"
 
@@ -138,6 +139,15 @@ __host__ __device__ __forceinline__ double gbi_rsqrt(double v) {
 #endif
 }
 
+__host__ __device__ __forceinline__ df gbi_rsqrt(df v) { return df_rsqrt(v); }
+
+__device__ __forceinline__ float gbi_shfl(float v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ double gbi_shfl(double v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ df gbi_shfl(df v, int o) { return df_shfl_xor(v, o); }
+__host__ __device__ __forceinline__ double gbi_to_double(float v) { return double(v); }
+__host__ __device__ __forceinline__ double gbi_to_double(double v) { return v; }
+__host__ __device__ __forceinline__ double gbi_to_double(df v) { return df_to_double(v); }
+
 // Row/column component and mode ranges of a pair pass.
 template <int TR, int ROWS, int COLS> struct PassShape {
   static constexpr int D = Tab<TR>::D;
@@ -201,8 +211,11 @@ __host__ __device__ __forceinline__ void pair_body(T dx, T dy, T dz, T a, const 
   from_pair_frame<TR, T, S::MR0, S::MR1, S::R0>(yy, acc, cm, sm, dm, ep);
 }
 
-template <int TR, int ROWS, int COLS, typename T, int WARPS, int TILE>
-__global__ void __launch_bounds__(WARPS * 32) pair_kernel(const PairArgs args) {
+// Block = TPB target spheres x WPT warps per target.  The WPT warps of a target split
+// its sources (lane-strided within each shared-memory tile); their partial sums are
+// combined in shared memory in a fixed order, so results are deterministic.
+template <int TR, int ROWS, int COLS, typename T, int TPB, int WPT, int TILE>
+__global__ void __launch_bounds__(TPB * WPT * 32) pair_kernel(const PairArgs args) {
   using S = PassShape<TR, ROWS, COLS>;
   constexpr int D = S::D;
   constexpr int R0 = S::R0;
@@ -211,21 +224,27 @@ __global__ void __launch_bounds__(WARPS * 32) pair_kernel(const PairArgs args) {
   constexpr int NR = S::NR;
   constexpr int NC = S::NC;
   constexpr bool F32 = std::is_same<T, float>::value;
-  constexpr int POSW = F32 ? 6 : 3;
+  constexpr bool DF = std::is_same<T, df>::value;
+  constexpr bool SPLIT = F32 || DF;            // centres as two floats (hi, lo)
+  constexpr int POSW = SPLIT ? 6 : 3;
+  constexpr int THREADS = TPB * WPT * 32;
+  using PT = typename std::conditional<SPLIT, float, double>::type;
 
-  __shared__ T s_pos[POSW][TILE];
+  __shared__ PT s_pos[POSW][TILE];
   __shared__ T s_x[NC][TILE];
 
   const int N = args.N;
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
-  const int n = blockIdx.x * WARPS + warp;
+  const int tgt = warp / WPT;            // target slot in the block
+  const int sub = warp - tgt * WPT;      // which share of the sources
+  const int n = blockIdx.x * TPB + tgt;
   const bool active = n < N;
   const T a = T(args.a);
 
-  T tp[POSW];
+  PT tp[POSW];
   if (active) {
-    if constexpr (F32) {
+    if constexpr (SPLIT) {
       const float4 h = args.pos.hi[n], lo = args.pos.lo[n];
       tp[0] = h.x; tp[1] = h.y; tp[2] = h.z; tp[3] = lo.x; tp[4] = lo.y; tp[5] = lo.z;
     } else {
@@ -234,7 +253,7 @@ __global__ void __launch_bounds__(WARPS * 32) pair_kernel(const PairArgs args) {
     }
   } else {
 #pragma unroll
-    for (int i = 0; i < POSW; ++i) tp[i] = T(0);
+    for (int i = 0; i < POSW; ++i) tp[i] = PT(0);
   }
 
   T acc[NR];
@@ -245,9 +264,9 @@ __global__ void __launch_bounds__(WARPS * 32) pair_kernel(const PairArgs args) {
   for (int base = 0; base < N; base += TILE) {
     const int len = min(TILE, N - base);
     __syncthreads();
-    for (int idx = threadIdx.x; idx < len; idx += WARPS * 32) {
+    for (int idx = threadIdx.x; idx < len; idx += THREADS) {
       const int m = base + idx;
-      if constexpr (F32) {
+      if constexpr (SPLIT) {
         const float4 h = args.pos.hi[m], lo = args.pos.lo[m];
         s_pos[0][idx] = h.x; s_pos[1][idx] = h.y; s_pos[2][idx] = h.z;
         s_pos[3][idx] = lo.x; s_pos[4][idx] = lo.y; s_pos[5][idx] = lo.z;
@@ -256,16 +275,36 @@ __global__ void __launch_bounds__(WARPS * 32) pair_kernel(const PairArgs args) {
         s_pos[0][idx] = p.x; s_pos[1][idx] = p.y; s_pos[2][idx] = p.z;
       }
     }
-    for (int idx = threadIdx.x; idx < NC * len; idx += WARPS * 32) {
-      const int q = idx / len, j = idx - q * len;
-      s_x[q][j] = T(args.x[(size_t)q * N + base + j] * args.colscale[C0 + q]);
+    // source coefficients: component-major rows, no integer division in the loop
+    if constexpr (DF) {
+      for (int q = 0; q < NC; ++q) {
+        const float* hi = args.x32 + (size_t)q * N + base;
+        const float* lo = args.x32lo + (size_t)q * N + base;
+        for (int j = threadIdx.x; j < len; j += THREADS) s_x[q][j] = df(hi[j], lo[j]);
+      }
+    } else if (F32 && args.x32 != nullptr) {
+      for (int q = 0; q < NC; ++q) {
+        const float* src = args.x32 + (size_t)q * N + base;
+        for (int j = threadIdx.x; j < len; j += THREADS) s_x[q][j] = T(src[j]);
+      }
+    } else {
+      for (int q = 0; q < NC; ++q) {
+        const double* src = args.x + (size_t)q * N + base;
+        const double cs = args.colscale[C0 + q];
+        for (int j = threadIdx.x; j < len; j += THREADS) s_x[q][j] = T(src[j] * cs);
+      }
     }
     __syncthreads();
     if (active) {
-      for (int j = lane; j < len; j += 32) {
+      for (int j = sub * 32 + lane; j < len; j += WPT * 32) {
         if (base + j == n) continue;
         T dx, dy, dz;
-        if constexpr (F32) {
+        if constexpr (DF) {
+          // exact difference of the hi parts, plus the (tiny) difference of the lo parts
+          dx = df_two_sum(tp[0], -s_pos[0][j]) + df(tp[3] - s_pos[3][j], 0.f);
+          dy = df_two_sum(tp[1], -s_pos[1][j]) + df(tp[4] - s_pos[4][j], 0.f);
+          dz = df_two_sum(tp[2], -s_pos[2][j]) + df(tp[5] - s_pos[5][j], 0.f);
+        } else if constexpr (F32) {
           dx = (tp[0] - s_pos[0][j]) + (tp[3] - s_pos[3][j]);
           dy = (tp[1] - s_pos[1][j]) + (tp[4] - s_pos[4][j]);
           dz = (tp[2] - s_pos[2][j]) + (tp[5] - s_pos[5][j]);
@@ -288,7 +327,7 @@ __global__ void __launch_bounds__(WARPS * 32) pair_kernel(const PairArgs args) {
   for (int p = 0; p < NR; ++p) {
     T v = acc[p];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    for (int o = 16; o > 0; o >>= 1) v += gbi_shfl(v, o);
     acc[p] = v;
   }
   if (args.min_r2_bits != nullptr) {
@@ -296,11 +335,30 @@ __global__ void __launch_bounds__(WARPS * 32) pair_kernel(const PairArgs args) {
     for (int o = 16; o > 0; o >>= 1) min_r2 = fminf(min_r2, __shfl_xor_sync(0xffffffffu, min_r2, o));
     if (active && lane == 0) atomicMin(args.min_r2_bits, __float_as_uint(min_r2));
   }
-  if (active && lane == 0) {
+  if constexpr (WPT > 1) {
+    // combine the WPT warps of each target through shared memory (reuses the tile)
+    __syncthreads();
+    T* red = &s_x[0][0];
+    static_assert(sizeof(s_x) >= sizeof(T) * TPB * WPT * NR || NR == 0, "reduction buffer too small");
+    if (lane == 0) {
+#pragma unroll
+      for (int p = 0; p < NR; ++p) red[(tgt * WPT + sub) * NR + p] = acc[p];
+    }
+    __syncthreads();
+    if (sub == 0 && lane == 0) {
+#pragma unroll
+      for (int p = 0; p < NR; ++p) {
+        T v = red[(tgt * WPT) * NR + p];
+        for (int w = 1; w < WPT; ++w) v += red[(tgt * WPT + w) * NR + p];
+        acc[p] = v;
+      }
+    }
+  }
+  if (active && sub == 0 && lane == 0) {
     const double inva = 1.0 / args.a;
 #pragma unroll
     for (int p = 0; p < NR; ++p) {
-      double v = double(acc[p]) * inva;
+      double v = gbi_to_double(acc[p]) * inva;
       if (args.add_self) v += args.selfg[R0 + p] * inva * args.x[(size_t)(R0 - C0 + p) * N + n] * args.colscale[R0 + p];
       double* dst = args.y + (size_t)p * N + n;
       *dst = args.alpha * v + (args.beta != 0.0 ? args.beta * (*dst) : 0.0);

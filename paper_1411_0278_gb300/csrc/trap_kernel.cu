@@ -3,15 +3,22 @@
 //
 // Each source sphere m carries a force F, a torque T, the one-body stresslet
 // S = a Q^(20) = -(20/3) pi eta a^2 V^(20) and the one-body potential dipole
-// Q^(32) = -2 pi eta a V^(32).  With rho = R_n - R_m and everything divided by 8 pi eta:
+// Q^(32) = -2 pi eta a V^(32).  With rho = R_n - R_m and F, T, S divided by 8 pi eta:
 //   V_n += (1/r + 2a^2/(3r^3)) F + (1/r^3 - 2a^2/r^5)(rho.F) rho          (RPY, F^0 F^0 G)
 //        + (T x rho)/r^3                                                   (rotlet)
 //        - 3 (rho.S.rho) rho/r^5 + a^2 [8 (rho.S.rho) rho/r^7 - 16/5 S.rho/r^5]
 //                                                   (stresslet with F^0 F^1, 4a^2/15 lap)
-//        + (a^3/10) [3 (rho.d) rho/r^5 - d/r^3] * 8 pi eta                (potential dipole)
+//        + (a^3/10) [3 (rho.d) rho/r^5 - d/r^3]                           (potential dipole)
 //   Omega_n += (F x rho)/r^3 + [3 (T.rho) rho/r^5 - T/r^3]/2 + 3 rho x (S.rho)/r^5
 // plus the one-body terms V^a + F/(6 pi eta a) and Omega^a + T/(8 pi eta a^3).
-// One warp per target sphere, lanes stride over sources staged in shared memory.
+//
+// Layout: a prologue kernel packs every source into one 24-word record (position
+// hi/lo or FP64 position, F, T, S, d).  The pair kernel gives each thread TI target
+// spheres; all threads of a block walk the same source records in shared memory
+// (broadcast, vectorised reads), so each record load serves TI pairs.  Sources are
+// split across blockIdx.y; every split writes its partial sums to scratch and a
+// final kernel adds them in a fixed order (deterministic) together with the one-body
+// terms, in FP64.
 #include <type_traits>
 
 #include "gbi_generated.cuh"
@@ -21,159 +28,204 @@ namespace gbi {
 
 namespace {
 
+constexpr int kRec = 24;   // words per source record
 
-template <typename T, int WARPS, int TILE>
-__global__ void __launch_bounds__(WARPS * 32) trap_kernel(const TrapArgs args) {
+template <typename T>
+__global__ void trap_pack(const TrapArgs args, T* __restrict__ rec) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= args.N) return;
   constexpr bool F32 = std::is_same<T, float>::value;
-  constexpr int POSW = F32 ? 6 : 3;
-  __shared__ T s_pos[POSW][TILE];
-  __shared__ T s_src[15][TILE];
-
-  const int N = args.N;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int n = blockIdx.x * WARPS + warp;
-  const bool active = n < N;
   const double inv8pe = 1.0 / (8.0 * kPi * args.eta);
-  const T a = T(args.a);
-  const T a2 = a * a;
+  const double* F = args.Fe + 3 * (size_t)m;
+  const double* Tq = args.Te + 3 * (size_t)m;
+  const double* vh = args.VH + 8 * (size_t)m;
+  double s6[6];
+  gbi_unpack2<double>(vh, s6);
+  const double sf = -(5.0 / 6.0) * args.a * args.a;        // S/(8 pi eta) per V^(20)
+  const double df = args.a * args.a * args.a / 10.0;        // (a^3/10) per V^(32)
+  T* r = rec + (size_t)m * kRec;
+  if constexpr (F32) {
+    const float4 h = args.pos.hi[m], lo = args.pos.lo[m];
+    r[0] = h.x; r[1] = h.y; r[2] = h.z; r[3] = lo.x; r[4] = lo.y; r[5] = lo.z;
+  } else {
+    const dpos4 p = args.pos.p64[m];
+    r[0] = p.x; r[1] = p.y; r[2] = p.z; r[3] = 0; r[4] = 0; r[5] = 0;
+  }
+  r[6] = T(F[0] * inv8pe); r[7] = T(F[1] * inv8pe); r[8] = T(F[2] * inv8pe);
+  r[9] = T(Tq[0] * inv8pe); r[10] = T(Tq[1] * inv8pe); r[11] = T(Tq[2] * inv8pe);
+  for (int i = 0; i < 6; ++i) r[12 + i] = T(sf * s6[i]);
+  // V^(32) packed (y, z, x)
+  r[18] = T(df * vh[7]); r[19] = T(df * vh[5]); r[20] = T(df * vh[6]);
+  r[21] = 0; r[22] = 0; r[23] = 0;
+}
 
-  T tp[POSW];
+template <typename T> struct Vec4;
+template <> struct Vec4<float> { using type = float4; };
+template <> struct Vec4<double> { using type = dpos4; };
+
+template <typename T>
+__device__ __forceinline__ T trap_rsqrt(T v) {
+  if constexpr (std::is_same<T, float>::value) return rsqrtf(v);
+  else return rsqrt(v);
+}
+
+// partial[split][n][6] = sum over this split's sources of the pair terms for target n
+template <typename T, int TI, int THREADS, int TILE>
+__global__ void __launch_bounds__(THREADS) trap_pairs(const TrapArgs args, const T* __restrict__ rec,
+                                                      int chunk, T* __restrict__ partial) {
+  constexpr bool F32 = std::is_same<T, float>::value;
+  using V4 = typename Vec4<T>::type;
+  __shared__ __align__(32) T s_rec[TILE * kRec];
+  const int N = args.N;
+  const int n0 = (blockIdx.x * THREADS + threadIdx.x) * TI;
+  const int m_begin = blockIdx.y * chunk;
+  const int m_end = min(N, m_begin + chunk);
+  const T a2 = T(args.a * args.a);
+
+  T px[TI], py[TI], pz[TI], lx[TI], ly[TI], lz[TI];
+  T v0[TI], v1[TI], v2[TI], w0[TI], w1[TI], w2[TI];
 #pragma unroll
-  for (int i = 0; i < POSW; ++i) tp[i] = T(0);
-  if (active) {
+  for (int t = 0; t < TI; ++t) {
+    const int n = min(n0 + t, N - 1);
     if constexpr (F32) {
       const float4 h = args.pos.hi[n], lo = args.pos.lo[n];
-      tp[0] = h.x; tp[1] = h.y; tp[2] = h.z; tp[3] = lo.x; tp[4] = lo.y; tp[5] = lo.z;
+      px[t] = h.x; py[t] = h.y; pz[t] = h.z; lx[t] = lo.x; ly[t] = lo.y; lz[t] = lo.z;
     } else {
       const dpos4 p = args.pos.p64[n];
-      tp[0] = p.x; tp[1] = p.y; tp[2] = p.z;
+      px[t] = p.x; py[t] = p.y; pz[t] = p.z; lx[t] = 0; ly[t] = 0; lz[t] = 0;
     }
+    v0[t] = v1[t] = v2[t] = w0[t] = w1[t] = w2[t] = T(0);
   }
-  T v0 = 0, v1 = 0, v2 = 0, w0 = 0, w1 = 0, w2 = 0;
 
-  for (int base = 0; base < N; base += TILE) {
-    const int len = min(TILE, N - base);
+  for (int base = m_begin; base < m_end; base += TILE) {
+    const int len = min(TILE, m_end - base);
     __syncthreads();
-    for (int j = threadIdx.x; j < len; j += WARPS * 32) {
-      const int m = base + j;
-      if constexpr (F32) {
-        const float4 h = args.pos.hi[m], lo = args.pos.lo[m];
-        s_pos[0][j] = h.x; s_pos[1][j] = h.y; s_pos[2][j] = h.z;
-        s_pos[3][j] = lo.x; s_pos[4][j] = lo.y; s_pos[5][j] = lo.z;
-      } else {
-        const dpos4 p = args.pos.p64[m];
-        s_pos[0][j] = p.x; s_pos[1][j] = p.y; s_pos[2][j] = p.z;
-      }
-      const double* F = args.Fe + 3 * (size_t)m;
-      const double* Tq = args.Te + 3 * (size_t)m;
-      const double* vh = args.VH + 8 * (size_t)m;
-      double s6[6];
-      gbi_unpack2<double>(vh, s6);
-      const double sf = -(5.0 / 6.0) * args.a * args.a;        // S/(8 pi eta) per V^(20)
-      const double df = args.a * args.a * args.a / 10.0;        // (a^3/10) per V^(32)
-      s_src[0][j] = T(F[0] * inv8pe); s_src[1][j] = T(F[1] * inv8pe); s_src[2][j] = T(F[2] * inv8pe);
-      s_src[3][j] = T(Tq[0] * inv8pe); s_src[4][j] = T(Tq[1] * inv8pe); s_src[5][j] = T(Tq[2] * inv8pe);
-      s_src[6][j] = T(sf * s6[0]); s_src[7][j] = T(sf * s6[1]); s_src[8][j] = T(sf * s6[2]);
-      s_src[9][j] = T(sf * s6[3]); s_src[10][j] = T(sf * s6[4]); s_src[11][j] = T(sf * s6[5]);
-      // V^(32) packed (y, z, x)
-      s_src[12][j] = T(df * vh[7]); s_src[13][j] = T(df * vh[5]); s_src[14][j] = T(df * vh[6]);
+    {
+      const V4* src = reinterpret_cast<const V4*>(rec + (size_t)base * kRec);
+      V4* dst = reinterpret_cast<V4*>(s_rec);
+      for (int i = threadIdx.x; i < len * (kRec / 4); i += THREADS) dst[i] = src[i];
     }
     __syncthreads();
-    if (active) {
-      for (int j = lane; j < len; j += 32) {
-        if (base + j == n) continue;
+    for (int j = 0; j < len; ++j) {
+      const V4* r4 = reinterpret_cast<const V4*>(s_rec + j * kRec);
+      const V4 q0 = r4[0], q1 = r4[1], q2 = r4[2], q3 = r4[3], q4 = r4[4], q5 = r4[5];
+      const T sx = q0.x, sy = q0.y, sz = q0.z, slx = q0.w, sly = q1.x, slz = q1.y;
+      const T Fx = q1.z, Fy = q1.w, Fz = q2.x;
+      const T Tx = q2.y, Ty = q2.z, Tz = q2.w;
+      const T Sxx = q3.x, Sxy = q3.y, Sxz = q3.z, Syy = q3.w, Syz = q4.x, Szz = q4.y;
+      const T dx = q4.z, dy = q4.w, dz = q5.x;
+      const int m = base + j;
+#pragma unroll
+      for (int t = 0; t < TI; ++t) {
+        if (m == n0 + t) continue;
         T x, y, z;
         if constexpr (F32) {
-          x = (tp[0] - s_pos[0][j]) + (tp[3] - s_pos[3][j]);
-          y = (tp[1] - s_pos[1][j]) + (tp[4] - s_pos[4][j]);
-          z = (tp[2] - s_pos[2][j]) + (tp[5] - s_pos[5][j]);
+          x = (px[t] - sx) + (lx[t] - slx);
+          y = (py[t] - sy) + (ly[t] - sly);
+          z = (pz[t] - sz) + (lz[t] - slz);
         } else {
-          x = tp[0] - s_pos[0][j];
-          y = tp[1] - s_pos[1][j];
-          z = tp[2] - s_pos[2][j];
+          x = px[t] - sx;
+          y = py[t] - sy;
+          z = pz[t] - sz;
         }
         const T r2 = x * x + y * y + z * z;
-        T ri;
-        if constexpr (F32) ri = rsqrtf(r2); else ri = rsqrt(r2);
+        const T ri = trap_rsqrt(r2);
         const T ri2 = ri * ri, ri3 = ri * ri2, ri5 = ri3 * ri2, ri7 = ri5 * ri2;
-        const T Fx = s_src[0][j], Fy = s_src[1][j], Fz = s_src[2][j];
-        const T Tx = s_src[3][j], Ty = s_src[4][j], Tz = s_src[5][j];
-        const T Sxx = s_src[6][j], Sxy = s_src[7][j], Sxz = s_src[8][j];
-        const T Syy = s_src[9][j], Syz = s_src[10][j], Szz = s_src[11][j];
-        const T dx = s_src[12][j], dy = s_src[13][j], dz = s_src[14][j];
-        // RPY
         const T rF = x * Fx + y * Fy + z * Fz;
         const T c1 = ri + T(2.0 / 3.0) * a2 * ri3;
         const T c2 = (ri3 - T(2) * a2 * ri5) * rF;
-        // stresslet
         const T Sx = Sxx * x + Sxy * y + Sxz * z;
         const T Sy = Sxy * x + Syy * y + Syz * z;
         const T Sz = Sxz * x + Syz * y + Szz * z;
         const T rSr = x * Sx + y * Sy + z * Sz;
-        const T cs = (T(8) * a2 * ri7 - T(3) * ri5) * rSr;
-        const T cs2 = T(-16.0 / 5.0) * a2 * ri5;
-        // dipole
         const T rd = x * dx + y * dy + z * dz;
-        const T cd = T(3) * ri5 * rd;
-        // torque
         const T rT = x * Tx + y * Ty + z * Tz;
+        // common radial coefficient of rho in V: RPY + stresslet + dipole
+        const T cx = c2 + (T(8) * a2 * ri7 - T(3) * ri5) * rSr + T(3) * ri5 * rd;
+        const T cs2 = T(-16.0 / 5.0) * a2 * ri5;
+        v0[t] += c1 * Fx + cx * x + (Ty * z - Tz * y) * ri3 + cs2 * Sx - ri3 * dx;
+        v1[t] += c1 * Fy + cx * y + (Tz * x - Tx * z) * ri3 + cs2 * Sy - ri3 * dy;
+        v2[t] += c1 * Fz + cx * z + (Tx * y - Ty * x) * ri3 + cs2 * Sz - ri3 * dz;
         const T ct = T(1.5) * ri5 * rT;
-        v0 += c1 * Fx + c2 * x + (Ty * z - Tz * y) * ri3 + cs * x + cs2 * Sx + cd * x - ri3 * dx;
-        v1 += c1 * Fy + c2 * y + (Tz * x - Tx * z) * ri3 + cs * y + cs2 * Sy + cd * y - ri3 * dy;
-        v2 += c1 * Fz + c2 * z + (Tx * y - Ty * x) * ri3 + cs * z + cs2 * Sz + cd * z - ri3 * dz;
         const T t3 = T(3) * ri5;
-        w0 += (Fy * z - Fz * y) * ri3 + ct * x - T(0.5) * ri3 * Tx + t3 * (y * Sz - z * Sy);
-        w1 += (Fz * x - Fx * z) * ri3 + ct * y - T(0.5) * ri3 * Ty + t3 * (z * Sx - x * Sz);
-        w2 += (Fx * y - Fy * x) * ri3 + ct * z - T(0.5) * ri3 * Tz + t3 * (x * Sy - y * Sx);
+        w0[t] += (Fy * z - Fz * y) * ri3 + ct * x - T(0.5) * ri3 * Tx + t3 * (y * Sz - z * Sy);
+        w1[t] += (Fz * x - Fx * z) * ri3 + ct * y - T(0.5) * ri3 * Ty + t3 * (z * Sx - x * Sz);
+        w2[t] += (Fx * y - Fy * x) * ri3 + ct * z - T(0.5) * ri3 * Tz + t3 * (x * Sy - y * Sx);
       }
     }
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    v0 += __shfl_xor_sync(0xffffffffu, v0, o);
-    v1 += __shfl_xor_sync(0xffffffffu, v1, o);
-    v2 += __shfl_xor_sync(0xffffffffu, v2, o);
-    w0 += __shfl_xor_sync(0xffffffffu, w0, o);
-    w1 += __shfl_xor_sync(0xffffffffu, w1, o);
-    w2 += __shfl_xor_sync(0xffffffffu, w2, o);
+  for (int t = 0; t < TI; ++t) {
+    const int n = n0 + t;
+    if (n < N) {
+      T* o = partial + ((size_t)blockIdx.y * N + n) * 6;
+      o[0] = v0[t]; o[1] = v1[t]; o[2] = v2[t]; o[3] = w0[t]; o[4] = w1[t]; o[5] = w2[t];
+    }
   }
-  if (active && lane == 0) {
-    const double mt = 1.0 / (6.0 * kPi * args.eta * args.a);
-    const double mr = 1.0 / (8.0 * kPi * args.eta * args.a * args.a * args.a);
-    const double* F = args.Fe + 3 * (size_t)n;
-    const double* Tq = args.Te + 3 * (size_t)n;
-    const double* va = args.Va + 3 * (size_t)n;
-    const double* oa = args.Oa + 3 * (size_t)n;
-    double* V = args.V + 3 * (size_t)n;
-    double* O = args.Om + 3 * (size_t)n;
-    V[0] = va[0] + mt * F[0] + double(v0);
-    V[1] = va[1] + mt * F[1] + double(v1);
-    V[2] = va[2] + mt * F[2] + double(v2);
-    O[0] = oa[0] + mr * Tq[0] + double(w0);
-    O[1] = oa[1] + mr * Tq[1] + double(w1);
-    O[2] = oa[2] + mr * Tq[2] + double(w2);
+}
+
+// V = V^a + F/(6 pi eta a) + sum_split partial, Omega likewise (fixed split order).
+template <typename T>
+__global__ void trap_finish(const TrapArgs args, const T* __restrict__ partial, int nsplit) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= args.N) return;
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  for (int s = 0; s < nsplit; ++s) {
+    const T* p = partial + ((size_t)s * args.N + n) * 6;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) acc[c] += double(p[c]);
   }
+  const double mt = 1.0 / (6.0 * kPi * args.eta * args.a);
+  const double mr = 1.0 / (8.0 * kPi * args.eta * args.a * args.a * args.a);
+  for (int c = 0; c < 3; ++c) {
+    args.V[3 * (size_t)n + c] = args.Va[3 * (size_t)n + c] + mt * args.Fe[3 * (size_t)n + c] + acc[c];
+    args.Om[3 * (size_t)n + c] = args.Oa[3 * (size_t)n + c] + mr * args.Te[3 * (size_t)n + c] + acc[3 + c];
+  }
+}
+
+constexpr int kTI = 4, kThreads = 128;
+
+template <typename T, int TILE>
+cudaError_t trap_launch_t(const TrapArgs& args, void* scratch, int nsplit, cudaStream_t stream) {
+  T* rec = reinterpret_cast<T*>(scratch);
+  T* partial = rec + (size_t)args.N * kRec;
+  trap_pack<T><<<(args.N + 255) / 256, 256, 0, stream>>>(args, rec);
+  const int chunk = (args.N + nsplit - 1) / nsplit;
+  const dim3 grid((args.N + kThreads * kTI - 1) / (kThreads * kTI), nsplit);
+  trap_pairs<T, kTI, kThreads, TILE><<<grid, kThreads, 0, stream>>>(args, rec, chunk, partial);
+  trap_finish<T><<<(args.N + 255) / 256, 256, 0, stream>>>(args, partial, nsplit);
+  return cudaGetLastError();
 }
 
 }  // namespace
 
 double trap_flops() {
-  // rho (9, two-float), r^2 (5), rsqrt (1), powers (4), RPY (5 + 5 + 4), stresslet S.rho (15),
-  // rho.S.rho (5), coefficients (7), dipole (5 + 2), torque (5 + 2), V update (3 x 22),
-  // Omega update (3 x 17)
-  return 9 + 5 + 1 + 4 + 14 + 15 + 5 + 7 + 7 + 7 + 66 + 51;
+  // rho (9, two-float), r^2 (5), rsqrt (1), powers (4), RPY coefficients (5 + 5 + 4),
+  // S.rho (15), rho.S.rho (5), rho.d (5), rho.T (5), radial coefficient (8), V update (3 x 16),
+  // Omega update (4 + 3 x 15)
+  return 9 + 5 + 1 + 4 + 14 + 15 + 5 + 5 + 5 + 8 + 48 + 49;
 }
 
-cudaError_t launch_trap(const TrapArgs& args, int precision, cudaStream_t stream) {
-  constexpr int WARPS = 8;
+int trap_splits(int N) {
+  // about four blocks per SM on 152 SMs, at least 64 sources per split
+  const int tblocks = (N + kThreads * kTI - 1) / (kThreads * kTI);
+  int s = (608 + tblocks - 1) / tblocks;
+  const int maxs = (N + 63) / 64;
+  if (s > maxs) s = maxs;
+  return s < 1 ? 1 : s;
+}
+
+size_t trap_scratch_bytes(int N, int precision) {
+  const size_t w = precision == 1 ? sizeof(float) : sizeof(double);
+  return w * ((size_t)N * kRec + (size_t)trap_splits(N) * N * 6) + 256;
+}
+
+// Three launches: record packing, pair sums per split, fixed-order reduction.
+cudaError_t launch_trap(const TrapArgs& args, int precision, void* scratch, cudaStream_t stream) {
   if (args.N <= 0) return cudaSuccess;
-  const dim3 grid((args.N + WARPS - 1) / WARPS), block(WARPS * 32);
-  if (precision == 1) {
-    trap_kernel<float, WARPS, 256><<<grid, block, 0, stream>>>(args);
-  } else {
-    trap_kernel<double, WARPS, 128><<<grid, block, 0, stream>>>(args);
-  }
-  return cudaGetLastError();
+  const int ns = trap_splits(args.N);
+  if (precision == 1) return trap_launch_t<float, 128>(args, scratch, ns, stream);
+  return trap_launch_t<double, 64>(args, scratch, ns, stream);
 }
 
 }  // namespace gbi

@@ -19,6 +19,8 @@ pytestmark = pytest.mark.gpu
 
 FP32_TOL = 1e-5
 FP64_TOL = 1e-12
+DF_TOL = 1e-11      # double-float: ~2^-44 per operation, accumulated over a pair and a sum
+TOLS = {0: FP64_TOL, 1: FP32_TOL, 2: DF_TOL}
 
 
 @pytest.fixture(scope="module")
@@ -75,8 +77,10 @@ def _sl(code, d):
 
 @pytest.mark.parametrize("trunc,N", [(2, 150), (3, 150), (4, 70)])
 @pytest.mark.parametrize("rows,cols", [(2, 1), (2, 2), (1, 0), (0, 0)])
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2])
 def test_apply_matches_dense_oracle(ctx, gbi, trunc, N, rows, cols, precision):
+    if precision == 2 and rows == 0 and cols == 0:
+        pytest.skip("double-float is instantiated for the solver passes only")
     R, _, s = cloud(N, 11 + trunc)
     a = 1.0
     A = assembled(N, 11 + trunc, trunc, a)
@@ -101,7 +105,7 @@ def test_apply_matches_dense_oracle(ctx, gbi, trunc, N, rows, cols, precision):
     ctx.apply(N, trunc, a, rows, cols, precision, dev(R), dev(x), yd, 0.7, -0.3, add_self)
     torch.cuda.synchronize()
     err = relerr(yd.cpu().numpy(), ref)
-    assert err < (FP64_TOL if precision == 0 else FP32_TOL), err
+    assert err < TOLS[precision], err
 
 
 def test_apply_symmetry_and_far_positions(ctx, gbi):
@@ -114,7 +118,7 @@ def test_apply_symmetry_and_far_positions(ctx, gbi):
         A[i, :, i, :] = 0
     x = np.random.default_rng(2).normal(size=(25, N))
     ref = np.einsum("npmq,qm->pn", A[:, 6:, :, 6:], x)
-    for prec, tol in ((0, FP64_TOL * 10), (1, FP32_TOL)):
+    for prec, tol in ((0, FP64_TOL * 10), (1, FP32_TOL), (2, DF_TOL * 10)):
         yd = torch.zeros((25, N), dtype=torch.float64, device="cuda")
         ctx.apply(N, trunc, 1.0, 2, 2, prec, dev(R), dev(x), yd, 1.0, 0.0, False)
         torch.cuda.synchronize()
@@ -194,7 +198,7 @@ def _solve_case(gbi, ctx, R, p, s, trunc, precision, d0=0.02, Te_scale=0.01, rto
 
 
 @pytest.mark.parametrize("trunc,N", [(2, 64), (3, 40), (4, 24)])
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2])
 def test_solve_matches_dense_lu(ctx, gbi, trunc, N, precision):
     R, p, s = cloud(N, 20 + trunc)
     inp, V, Om, QH, info = _solve_case(gbi, ctx, R, p, s, trunc, precision)
@@ -210,7 +214,7 @@ def test_solve_matches_dense_lu(ctx, gbi, trunc, N, precision):
         assert relerr(QH[:, off:off + k], QHr[:, off:off + k]) < 1e-8, name
         off += k
     assert info.pair_interactions == (info.matvecs_f32 + info.matvecs_f64) * N * (N - 1)
-    if precision == 1:
+    if precision >= 1:
         assert info.matvecs_f32 > info.matvecs_f64
 
 
@@ -242,13 +246,14 @@ def _oracle_rows(R, targets, a, trunc):
     return out
 
 
-def test_solve_full_size_sampled_rows(ctx, gbi):
-    """N = 1024, l <= 3, FP32 pair sums + FP64 refinement: sampled rows of the system
-    and of the output evaluated by the oracle with the GPU's solution."""
+@pytest.mark.parametrize("precision", [1, 2])
+def test_solve_full_size_sampled_rows(ctx, gbi, precision):
+    """N = 1024, l <= 3, FP32 pair sums + FP64 (or double-float) refinement: sampled rows
+    of the system and of the output evaluated by the oracle with the GPU's solution."""
     c = workloads.config2()
     R, p = c["R"], c["p"]
     N = len(R)
-    inp, V, Om, QH, info = _solve_case(gbi, ctx, R, p, c, 3, 1, d0=0.0, Te_scale=0.0)
+    inp, V, Om, QH, info = _solve_case(gbi, ctx, R, p, c, 3, precision, d0=0.0, Te_scale=0.0)
     assert info.rel_residual <= 1e-10
     MB = tensors.ModeBasis(3)
     tgt = np.random.default_rng(4).choice(N, size=6, replace=False)
@@ -269,9 +274,10 @@ def test_solve_full_size_sampled_rows(ctx, gbi):
     assert relerr(Om[tgt], Om_o) < 1e-10
 
 
-def test_mixed_matches_fp64_gpu(ctx, gbi):
+@pytest.mark.parametrize("precision", [1, 2])
+def test_mixed_matches_fp64_gpu(ctx, gbi, precision):
     R, p, s = cloud(200, 31)
-    _, V1, Om1, Q1, i1 = _solve_case(gbi, ctx, R, p, s, 3, 1)
+    _, V1, Om1, Q1, i1 = _solve_case(gbi, ctx, R, p, s, 3, precision)
     _, V0, Om0, Q0, i0 = _solve_case(gbi, ctx, R, p, s, 3, 0)
     assert relerr(V1, V0) < 1e-9 and relerr(Om1, Om0) < 1e-9 and relerr(Q1, Q0) < 1e-8
     assert i1.matvecs_f64 < i0.matvecs_f64
