@@ -131,6 +131,21 @@ gbi_status gbi_solve(gbi_ctx* ctx, const gbi_params* params, int N,
                      const double* Fe, const double* Te,
                      double* V, double* Omega, double* QH, int warm_start, gbi_info* info);
 
+/* Batched solve of nsys independent suspensions in one set of launches (the
+ * batched workload: many suspensions of uneven N).  offsets_host (host array of
+ * nsys+1 ints, offsets_host[0] = 0, non-decreasing) splits the spheres into
+ * systems; all other arrays are as in gbi_solve, concatenated over the systems.
+ * Every system has its own GMRES state (Krylov basis slice, Hessenberg matrix,
+ * Givens rotations, tolerance test) and its own refinement flag; spheres of
+ * different systems do not interact.  info aggregates over the systems: iters is
+ * the number of lock-step inner iterations, rel_residual the largest system
+ * residual.  Returns GBI_ERR_NOT_CONVERGED if any system missed the tolerance.
+ * Synchronous. */
+gbi_status gbi_batch_solve(gbi_ctx* ctx, const gbi_params* params, int nsys, const int* offsets_host,
+                           const double* R, const double* Va, const double* Oa, const double* VH,
+                           const double* Fe, const double* Te,
+                           double* V, double* Omega, double* QH, int warm_start, gbi_info* info);
+
 /* Same as gbi_solve with HOST pointers: copies inputs to the device, solves, copies
  * the outputs back.  Synchronous. */
 gbi_status gbi_solve_host(gbi_ctx* ctx, const gbi_params* params, int N,
@@ -194,7 +209,9 @@ gbi_status gbi_solve_static(void* stream, const gbi_params* params, int N,
  * statistics and from then on records a CUDA event pair on the context's stream
  * around every pair pass; gbi_kernel_stats returns, for one class, the summed
  * event time in ms, the number of launches and the algorithmic flops (the
- * per-pair count of the implemented closed form times N(N-1)).  Class ids:
+ * per-pair count of the implemented closed form times N(N-1)).  Pair passes that the
+ * device-side GMRES launched after it had stopped (they return at once) are not
+ * counted as launches; their few microseconds stay in the summed time.  Class ids:
  * precision * 9 + rows * 3 + cols for gbi_apply-style passes (precision 0 = FP64,
  * 1 = FP32, 2 = double-float; rows/cols 0 = all, 1 = rigid-body, 2 = higher),
  * 27 = closed-form trap pass in FP64, 28 = in FP32.  gbi_kernel_stats synchronizes

@@ -63,6 +63,8 @@ _SIGS = {
     "gbi_trap_inputs": (_I, [_VP, _I, _I, _D, _D, _D, _D] + [_VP] * 7),
     "gbi_trap_step": (_I, [_VP, ctypes.POINTER(gbi_params), _I, _D, _D, _D, _D, _D, _I, _I, _VP, _VP,
                            ctypes.POINTER(gbi_info)]),
+    "gbi_batch_solve": (_I, [_VP, ctypes.POINTER(gbi_params), _I, ctypes.POINTER(ctypes.c_int)] + [_VP] * 9 +
+                        [_I, ctypes.POINTER(gbi_info)]),
     "gbi_solve_static": (_I, [_VP, ctypes.POINTER(gbi_params), _I] + [_VP] * 9 + [_I, ctypes.POINTER(gbi_info)]),
     "gbi_kernel_launches": (ctypes.c_longlong, [_VP]),
     "gbi_set_profiling": (_I, [_VP, _I]),
@@ -206,6 +208,23 @@ class Context:
         st = lib().gbi_solve(self._h, ctypes.byref(prm), int(N), _ptr(R), _ptr(Va), _ptr(Oa), _ptr(VH), _ptr(Fe),
                              _ptr(Te), _ptr(V), _ptr(Om), _ptr(QH), int(bool(warm_start)), ctypes.byref(info))
         self._check(st, "gbi_solve", allow=(GBI_ERR_NOT_CONVERGED,) if allow_not_converged else ())
+        return V, Om, QH, info, st
+
+    def batch_solve(self, prm, offsets, R, Va, Oa, VH, Fe, Te, QH=None, warm_start=False,
+                    allow_not_converged=False):
+        """gbi_batch_solve: offsets is a host sequence of nsys + 1 sphere offsets."""
+        import torch
+        N = R.shape[0]
+        offs = (ctypes.c_int * len(offsets))(*[int(o) for o in offsets])
+        V = torch.empty((N, 3), dtype=torch.float64, device=R.device)
+        Om = torch.empty_like(V)
+        if QH is None:
+            QH = torch.zeros((N, max(h(prm.trunc), 0)), dtype=torch.float64, device=R.device)
+        info = gbi_info()
+        st = lib().gbi_batch_solve(self._h, ctypes.byref(prm), len(offsets) - 1, offs, _ptr(R), _ptr(Va), _ptr(Oa),
+                                   _ptr(VH), _ptr(Fe), _ptr(Te), _ptr(V), _ptr(Om), _ptr(QH),
+                                   int(bool(warm_start)), ctypes.byref(info))
+        self._check(st, "gbi_batch_solve", allow=(GBI_ERR_NOT_CONVERGED,) if allow_not_converged else ())
         return V, Om, QH, info, st
 
     def solve_host(self, prm, R, Va, Oa, VH, Fe, Te, V, Om, QH, warm_start=False):

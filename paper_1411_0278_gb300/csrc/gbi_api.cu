@@ -64,7 +64,14 @@ struct gbi_ctx {
   cudaStream_t stream = nullptr;
   std::string err;
   Buf pos_hi, pos_lo, pos64;
-  Buf xF, xVH, b, xQ, r, delta, krylov, w, partial, dots, xVL, minr2, colbuf, x32, trapbuf;
+  Buf xF, xVH, b, xQ, r, delta, krylov, w, partial, dots, xVL, minr2, colbuf, x32, trapbuf, gstate;
+  Buf boff, bsys;                              // system offsets / ids of the current batch
+  std::vector<char> hbatch;                    // host copy of the per-system solver states
+  bool allow_graphs = true;                    // replay Arnoldi chunks from a CUDA graph
+  cudaGraphExec_t chunk_exec = nullptr;        // captured chunk of Arnoldi iterations
+  const void* chunk_key[8] = {};
+  long long chunk_ikey[6] = {};
+  int chunk_nodes = 0;
   Buf tFe, tTe, tVa, tOa, tVH, tV, tOm, tQH;   // trap-step / host-call staging
   Buf hR, hVa, hOa, hVH, hFe, hTe, hV, hOm, hQH;
   double* hbuf = nullptr;                      // pinned scalars read back by GMRES
@@ -80,6 +87,7 @@ struct gbi_ctx {
   double stat_ms[30] = {0};
   double stat_flops[30] = {0};
   long long stat_n[30] = {0};
+  long long stat_dead[30] = {0};
 };
 
 namespace {
@@ -170,14 +178,20 @@ struct ColScale {
   double v[54];
 };
 
-// y = float(x * cs[component]) for a component-major [nc][N] block
-__global__ void k_to_f32_s(size_t n, int N, const double* __restrict__ x, ColScale cs, float* __restrict__ y) {
+// y = float(x * cs[component]) for a component-major [nc][N] block (x optionally
+// device-indexed, skipped when the device-side solver has stopped)
+__global__ void k_to_f32_s(size_t n, int N, const double* __restrict__ x, const int* xi, size_t xs,
+                           const int* active, ColScale cs, float* __restrict__ y) {
+  if (active != nullptr && *active == 0) return;
+  if (xi != nullptr) x += (size_t)(*xi) * xs;
   const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (i < n) y[i] = float(x[i] * cs.v[i / N]);
 }
 
-__global__ void k_to_df_s(size_t n, int N, const double* __restrict__ x, ColScale cs, float* __restrict__ hi,
-                          float* __restrict__ lo) {
+__global__ void k_to_df_s(size_t n, int N, const double* __restrict__ x, const int* xi, size_t xs,
+                          const int* active, ColScale cs, float* __restrict__ hi, float* __restrict__ lo) {
+  if (active != nullptr && *active == 0) return;
+  if (xi != nullptr) x += (size_t)(*xi) * xs;
   const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (i < n) {
     const double v = x[i] * cs.v[i / N];
@@ -204,13 +218,14 @@ cudaError_t run_pairs(gbi_ctx* ctx, int trunc, int rows, int cols, int precision
     ColScale cs;
     const int c0 = cols == SET_H ? 6 : 0;
     for (int i = 0; i < 54; ++i) cs.v[i] = (i < nc) ? args.colscale[c0 + i] : 1.0;
-    k_to_df_s<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(n, args.N, args.x, cs, P<float>(ctx->x32),
-                                                                     P<float>(ctx->x32) + n);
+    k_to_df_s<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(n, args.N, args.x, args.x_index,
+                                                                     args.x_stride, args.active, cs,
+                                                                     P<float>(ctx->x32), P<float>(ctx->x32) + n);
     args.x32 = P<float>(ctx->x32);
     args.x32lo = P<float>(ctx->x32) + n;
     extra = 1;
   }
-  if (precision == 1) {
+  if (precision == 1 && args.x32 == nullptr) {
     // FP32 sources: scale and round once per pass, so the pair loop touches no FP64
     const int nc = ncols_of(trunc, cols);
     const size_t n = (size_t)nc * args.N;
@@ -218,7 +233,9 @@ cudaError_t run_pairs(gbi_ctx* ctx, int trunc, int rows, int cols, int precision
     ColScale cs;
     const int c0 = cols == SET_H ? 6 : 0;
     for (int i = 0; i < 54; ++i) cs.v[i] = (i < nc) ? args.colscale[c0 + i] : 1.0;
-    k_to_f32_s<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(n, args.N, args.x, cs, P<float>(ctx->x32));
+    k_to_f32_s<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(n, args.N, args.x, args.x_index,
+                                                                      args.x_stride, args.active, cs,
+                                                                      P<float>(ctx->x32));
     args.x32 = P<float>(ctx->x32);
     extra = 1;
   }
@@ -300,68 +317,6 @@ __global__ void k_finalize_lower(int N, double a, double c2a, const double* __re
   Om[3 * n + 0] = Oa[3 * n + 0] + f * xVL[5 * N + n];
   Om[3 * n + 1] = Oa[3 * n + 1] + f * xVL[3 * N + n];
   Om[3 * n + 2] = Oa[3 * n + 2] + f * xVL[4 * N + n];
-}
-
-__global__ void k_scale_copy(size_t n, const double* __restrict__ x, double s, double* y) {
-  const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (i < n) y[i] = s * x[i];
-}
-
-// partial[i * nb + b] = sum over block b's slice of V_i . w
-__global__ void k_multidot_partial(size_t n, const double* __restrict__ V, size_t ldv, int k,
-                                   const double* __restrict__ w, double* partial) {
-  const int i = blockIdx.y;
-  const int nb = gridDim.x;
-  const double* v = V + (size_t)i * ldv;
-  double s = 0.0;
-  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)nb * blockDim.x)
-    s += v[t] * w[t];
-  __shared__ double sh[256];
-  sh[threadIdx.x] = s;
-  __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) partial[(size_t)i * nb + blockIdx.x] = sh[0];
-}
-
-// out[i] (+)= sum_b partial[i * nb + b], fixed order
-__global__ void k_multidot_final(int nb, const double* __restrict__ partial, double* out, int accumulate) {
-  const int i = blockIdx.x;
-  __shared__ double sh[256];
-  double s = 0.0;
-  for (int b = threadIdx.x; b < nb; b += blockDim.x) s += partial[(size_t)i * nb + b];
-  sh[threadIdx.x] = s;
-  __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) out[i] = accumulate ? out[i] + sh[0] : sh[0];
-}
-
-// w -= sum_{i<k} h[i] V_i
-__global__ void k_sub_multi(size_t n, const double* __restrict__ V, size_t ldv, int k,
-                            const double* __restrict__ h, double* w) {
-  const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (t >= n) return;
-  double s = w[t];
-  for (int i = 0; i < k; ++i) s -= h[i] * V[(size_t)i * ldv + t];
-  w[t] = s;
-}
-
-// u[p][n] += minv[p] * sum_{i<k} y[i] V_i[p][n]   (y given in constant struct)
-struct Coef {
-  double v[kMaxRestart + 1];
-};
-__global__ void k_update_solution(int N, int h, const double* __restrict__ V, size_t ldv, int k, Coef y,
-                                  Scales minv, double* u) {
-  const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (t >= (size_t)N * h) return;
-  double s = 0.0;
-  for (int i = 0; i < k; ++i) s += y.v[i] * V[(size_t)i * ldv + t];
-  u[t] += minv.v[t / N] * s;
 }
 
 __global__ void k_trap_inputs(int N, double k_trap, double vs, double s0, double d0, int h,
@@ -468,143 +423,489 @@ PairArgs pair_args(const Setup& s, const double* x, double* y, double alpha, dou
     p.selfg[i] = s.selfg.v[i];
   }
   p.min_r2_bits = nullptr;
+  p.x_index = nullptr;
+  p.x_stride = 0;
+  p.active = nullptr;
+  p.sys_of = nullptr;
+  p.sys_off = nullptr;
+  p.sys_flag = nullptr;
+  p.sys_flag_stride = 0;
   return p;
 }
 
-// y = alpha * (G^HH x (with self)) + beta * y on H vectors; x scaled per component by colscale
-gbi_status apply_HH(gbi_ctx* ctx, const Setup& s, int precision, const double* x, double* y, double alpha,
-                    double beta, const Scales& colscale, gbi_info* info) {
-  PairArgs p = pair_args(s, x, y, alpha, beta, 1, colscale, 6);
-  GBI_CHECK(run_pairs(ctx, s.trunc, SET_H, SET_H, precision, p));
-  if (info) {
-    (precision == 1 ? info->matvecs_f32 : info->matvecs_f64) += 1;
-    info->pair_interactions += s.pairs_per_pass;
-  }
-  return GBI_OK;
+// ---------------------------------------------------------------------------------
+// Batched GMRES with its control on the device
+// ---------------------------------------------------------------------------------
+//
+// S independent systems (suspensions) share one launch per pass: every vector is
+// component-major over all spheres [h][Ntot], sphere n belongs to system sys[n] with
+// spheres [off[s], off[s+1]).  Each system has its own Krylov state, Hessenberg
+// matrix, Givens rotations, tolerance test and refinement flag; a system that has
+// stopped is skipped by every kernel.  A single suspension is the case S = 1.
+
+struct Batch {
+  int S = 1;
+  int Ntot = 0;
+  const int* off = nullptr;   // device [S+1]
+  const int* sys = nullptr;   // device [Ntot]
+  std::vector<int> h_off;     // host copy of off
+};
+
+// Device-resident state of one system's GMRES / refinement.
+struct GDev {
+  int j;          // Arnoldi index of the vector being expanded
+  int active;     // 1 while the current cycle continues
+  int iters;      // inner iterations of the current inner solve
+  int kdim;       // Krylov dimension reached in the current cycle
+  int converged;  // relative residual estimate <= tol
+  int breakdown;  // happy breakdown (exact solution in the Krylov space)
+  int max_iter, m;
+  int enabled;    // refinement: this system still needs a correction
+  int pad;
+  double bnorm, tol, res, beta, inv_hn;
+  double nb;      // |b_s| (reference of the refinement residual)
+  double rel;     // |b_s - A q_s| / |b_s|
+  double pad2;
+};
+
+struct GPtr {     // per-system views into the gstate buffer
+  GDev* st;
+  double *H, *cs, *sn, *g, *y, *h1, *h2, *nrm;
+  int S, m;
+};
+
+size_t gstate_doubles(int m, int S) {
+  return (size_t)S * (sizeof(GDev) / sizeof(double) + 1) + (size_t)S * ((size_t)(m + 1) * m + 7 * (size_t)(m + 1) + 1) +
+         16;
 }
 
-// out[0..k) = V_i . w for i < k (deterministic two-stage reduction)
-gbi_status multidot(gbi_ctx* ctx, size_t n, const double* V, size_t ldv, int k, const double* w, double* out,
-                    int accumulate) {
-  const int nb = int(std::min<size_t>(64, std::max<size_t>(1, (n + 2047) / 2048)));
-  GBI_TRY(ensure(ctx, ctx->partial, sizeof(double) * (size_t)nb * (kMaxRestart + 2)));
-  dim3 g1(nb, k);
-  k_multidot_partial<<<g1, 256, 0, ctx->stream>>>(n, V, ldv, k, w, P<double>(ctx->partial));
-  ++ctx->launches;
-  k_multidot_final<<<k, 256, 0, ctx->stream>>>(nb, P<double>(ctx->partial), out, accumulate);
-  ++ctx->launches;
+GPtr gptrs(void* base, int m, int S) {
+  GPtr p;
+  p.S = S;
+  p.m = m;
+  p.st = reinterpret_cast<GDev*>(base);
+  double* d = reinterpret_cast<double*>(base) + (size_t)S * (sizeof(GDev) / sizeof(double) + 1);
+  p.H = d; d += (size_t)S * (m + 1) * m;
+  p.cs = d; d += (size_t)S * (m + 1);
+  p.sn = d; d += (size_t)S * (m + 1);
+  p.g = d; d += (size_t)S * (m + 1);
+  p.y = d; d += (size_t)S * (m + 1);
+  p.h1 = d; d += (size_t)S * (m + 1);
+  p.h2 = d; d += (size_t)S * (m + 1);
+  p.nrm = d;
+  return p;
+}
+
+// out (FP64 or FP32) = V_{j_s} * minv over the spheres of active systems (the Arnoldi source)
+template <typename O>
+__global__ void bk_gather(const double* __restrict__ V, size_t n, int Ntot, const int* __restrict__ sys,
+                          const GDev* __restrict__ st, Scales minv, O* __restrict__ out) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  const int q = blockIdx.y;
+  if (p >= Ntot) return;
+  const GDev& g = st[sys[p]];
+  if (!g.active) return;
+  const size_t t = (size_t)q * Ntot + p;
+  out[t] = O(V[(size_t)g.j * n + t] * minv.v[q]);
+}
+
+// out[s][i] = V_i . w over system s, for i <= j_s (one block per system and vector)
+__global__ void bk_dots(const double* __restrict__ V, size_t n, const double* __restrict__ w, int Ntot, int h,
+                        const int* __restrict__ off, const GDev* __restrict__ st, int m, double* out) {
+  const int s = blockIdx.x, i = blockIdx.y;
+  const GDev& g = st[s];
+  if (!g.active || i > g.j) return;
+  const double* v = V + (size_t)i * n;
+  const int lo = off[s], hi = off[s + 1];
+  double acc = 0.0;
+  for (int q = 0; q < h; ++q) {
+    const size_t b = (size_t)q * Ntot;
+    for (int p = lo + threadIdx.x; p < hi; p += blockDim.x) acc += v[b + p] * w[b + p];
+  }
+  __shared__ double sh[256];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[(size_t)s * (m + 1) + i] = sh[0];
+}
+
+// w -= sum_{i <= j_s} coef[s][i] V_i
+__global__ void bk_sub(const double* __restrict__ V, size_t n, double* w, int Ntot, const int* __restrict__ sys,
+                       const GDev* __restrict__ st, int m, const double* __restrict__ coef) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= Ntot) return;
+  const int s = sys[p];
+  const GDev& g = st[s];
+  if (!g.active) return;
+  const size_t t = (size_t)blockIdx.y * Ntot + p;
+  const double* c = coef + (size_t)s * (m + 1);
+  double acc = w[t];
+  for (int i = 0; i <= g.j; ++i) acc -= c[i] * V[(size_t)i * n + t];
+  w[t] = acc;
+}
+
+// out[s] = |x_s|^2 (one block per system); mode 0: active systems, 1: enabled, 2: all
+__global__ void bk_norm(const double* __restrict__ x, int Ntot, int h, const int* __restrict__ off,
+                        const GDev* __restrict__ st, int mode, double* out) {
+  const int s = blockIdx.x;
+  const GDev& g = st[s];
+  if ((mode == 0 && !g.active) || (mode == 1 && !g.enabled)) return;
+  const int lo = off[s], hi = off[s + 1];
+  double acc = 0.0;
+  for (int q = 0; q < h; ++q) {
+    const size_t b = (size_t)q * Ntot;
+    for (int p = lo + threadIdx.x; p < hi; p += blockDim.x) acc += x[b + p] * x[b + p];
+  }
+  __shared__ double sh[256];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[s] = sh[0];
+}
+
+// Hessenberg column j_s, Givens rotations, residual estimate and stopping test of one
+// system per block (parallel loads to shared memory, one thread sweeps the rotations).
+constexpr int kGmMaxM = 128;
+__global__ void bk_finalize(GPtr p) {
+  const int s = blockIdx.x;
+  GDev* st = p.st + s;
+  if (!st->active) return;
+  __shared__ double col[kGmMaxM + 1], scs[kGmMaxM], ssn[kGmMaxM];
+  const int j = st->j, m = p.m;
+  const size_t o1 = (size_t)s * (m + 1);
+  const int tid = threadIdx.x;
+  for (int i = tid; i <= j; i += blockDim.x) col[i] = p.h1[o1 + i] + p.h2[o1 + i];
+  for (int i = tid; i < j; i += blockDim.x) {
+    scs[i] = p.cs[o1 + i];
+    ssn[i] = p.sn[o1 + i];
+  }
+  __syncthreads();
+  if (tid == 0) {
+    const double hn = sqrt(fmax(0.0, p.nrm[s]));
+    for (int i = 0; i < j; ++i) {
+      const double t1 = col[i], t2 = col[i + 1];
+      col[i] = scs[i] * t1 + ssn[i] * t2;
+      col[i + 1] = -ssn[i] * t1 + scs[i] * t2;
+    }
+    col[j + 1] = hn;
+    const double hjj = col[j], hj1 = hn;
+    const double den = hypot(hjj, hj1);
+    const double c = den > 0 ? hjj / den : 1.0, sg = den > 0 ? hj1 / den : 0.0;
+    p.cs[o1 + j] = c;
+    p.sn[o1 + j] = sg;
+    col[j] = den;
+    col[j + 1] = 0.0;
+    const double gj = p.g[o1 + j];
+    p.g[o1 + j + 1] = -sg * gj;
+    p.g[o1 + j] = c * gj;
+    st->iters += 1;
+    st->kdim = j + 1;
+    st->res = fabs(p.g[o1 + j + 1]) / st->bnorm;
+    st->converged = st->res <= st->tol;
+    st->breakdown = hn <= 1e-300;
+    const bool stop = st->converged || st->breakdown || st->iters >= st->max_iter || j + 1 >= m;
+    if (stop) {
+      st->active = 0;
+    } else {
+      st->inv_hn = 1.0 / hn;
+      st->j = j + 1;
+    }
+  }
+  __syncthreads();
+  double* H = p.H + (size_t)s * (m + 1) * m;
+  for (int i = tid; i <= j + 1; i += blockDim.x) H[(size_t)i * m + j] = col[i];
+}
+
+// V_{j_s} = w / h for the newly advanced j_s
+__global__ void bk_scale(double* V, size_t n, const double* __restrict__ w, int Ntot, const int* __restrict__ sys,
+                         const GDev* __restrict__ st) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= Ntot) return;
+  const GDev& g = st[sys[p]];
+  if (!g.active) return;
+  const size_t t = (size_t)blockIdx.y * Ntot + p;
+  V[(size_t)g.j * n + t] = w[t] * g.inv_hn;
+}
+
+// start of a GMRES cycle for every enabled system: beta = |V_0|, g = (beta, 0, ...)
+__global__ void bk_init_cycle(GPtr p, int first) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= p.S) return;
+  GDev* st = p.st + s;
+  const int m = p.m;
+  if (first) st->iters = 0;
+  st->j = 0;
+  st->kdim = 0;
+  st->breakdown = 0;
+  if (!st->enabled || (!first && st->converged)) {
+    st->active = 0;
+    return;
+  }
+  const double beta = sqrt(fmax(0.0, p.nrm[s]));
+  if (first) st->bnorm = beta;
+  st->beta = beta;
+  double* g = p.g + (size_t)s * (m + 1);
+  for (int i = 0; i <= m; ++i) g[i] = 0.0;
+  g[0] = beta;
+  st->res = st->bnorm > 0 ? beta / st->bnorm : 0.0;
+  st->converged = st->res <= st->tol;
+  st->active = (!st->converged && st->iters < st->max_iter && beta > 0) ? 1 : 0;
+  st->inv_hn = beta > 0 ? 1.0 / beta : 0.0;
+}
+
+__global__ void bk_scale0(double* V0, int Ntot, const int* __restrict__ sys, const GDev* __restrict__ st) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= Ntot) return;
+  const GDev& g = st[sys[p]];
+  if (!g.active) return;
+  V0[(size_t)blockIdx.y * Ntot + p] *= g.inv_hn;
+}
+
+// y_s = H_s^-1 g_s on the kdim leading rows (column-oriented back substitution)
+__global__ void bk_solve_y(GPtr p) {
+  const int s = blockIdx.x;
+  const GDev* st = p.st + s;
+  const int k = st->kdim, m = p.m;
+  if (k == 0) return;
+  const double* H = p.H + (size_t)s * (m + 1) * m;
+  const size_t o1 = (size_t)s * (m + 1);
+  __shared__ double rhs[kGmMaxM], yv[kGmMaxM];
+  for (int i = threadIdx.x; i < k; i += blockDim.x) rhs[i] = p.g[o1 + i];
+  __syncthreads();
+  for (int i = k - 1; i >= 0; --i) {
+    if (threadIdx.x == 0) yv[i] = rhs[i] / H[(size_t)i * m + i];
+    __syncthreads();
+    for (int r = threadIdx.x; r < i; r += blockDim.x) rhs[r] -= H[(size_t)r * m + i] * yv[i];
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < k; i += blockDim.x) p.y[o1 + i] = yv[i];
+}
+
+// u += minv * sum_{i < kdim_s} y_s[i] V_i  (systems whose cycle ran)
+__global__ void bk_update(const double* __restrict__ V, size_t n, int Ntot, const int* __restrict__ sys, GPtr p,
+                          Scales minv, double* u) {
+  const int pp = blockIdx.x * blockDim.x + threadIdx.x;
+  if (pp >= Ntot) return;
+  const int s = sys[pp];
+  const int k = p.st[s].kdim;
+  if (k == 0) return;
+  const size_t t = (size_t)blockIdx.y * Ntot + pp;
+  const double* y = p.y + (size_t)s * (p.m + 1);
+  double acc = 0.0;
+  for (int i = 0; i < k; ++i) acc += y[i] * V[(size_t)i * n + t];
+  u[t] += minv.v[blockIdx.y] * acc;
+}
+
+// refinement bookkeeping: mode 0 stores |b_s| (from nrm), mode 1 sets rel and enabled
+__global__ void bk_refine(GPtr p, int mode, double rtol) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= p.S) return;
+  GDev* st = p.st + s;
+  const double v = sqrt(fmax(0.0, p.nrm[s]));
+  if (mode == 0) {
+    st->nb = v;
+    st->enabled = v > 0 ? 1 : 0;
+    st->rel = v > 0 ? 1.0 : 0.0;
+  } else if (st->enabled) {
+    st->rel = st->nb > 0 ? v / st->nb : 0.0;
+    st->enabled = st->rel > rtol ? 1 : 0;
+  }
+}
+
+// x += d on enabled systems
+__global__ void bk_axpy_enabled(const double* __restrict__ d, int Ntot, const int* __restrict__ sys,
+                                const GDev* __restrict__ st, double* x) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= Ntot) return;
+  if (!st[sys[p]].enabled) return;
+  const size_t t = (size_t)blockIdx.y * Ntot + p;
+  x[t] += d[t];
+}
+
+// Restarted right-preconditioned GMRES(m) on every active system of the batch for
+// G^HH u = rhs (internal coordinates).  u holds the initial guess (zero or warm).
+// Arnoldi (classical Gram-Schmidt twice), Givens rotations, the stopping tests and
+// the triangular solves run on the device in FP64; the host launches the iterations
+// in chunks (replayed from a CUDA graph when the stream allows capture) and reads the
+// systems' small states once per chunk.
+gbi_status gmres_batch(gbi_ctx* ctx, const Setup& s, const Batch& B, int precision, const double* rhs, double* u,
+                       bool u_is_zero, double tol, int restart, int max_iter, gbi_info* info, int& iters,
+                       double& relres, std::vector<GDev>& hst);
+
+gbi_status launch_chunk(gbi_ctx* ctx, const Setup& s, const Batch& B, int precision, const GPtr& gp, int m,
+                        double* Vb, double* w, void* xsrc, int kChunk) {
+  const int S = B.S, Ntot = B.Ntot, h = s.h;
+  const size_t n = (size_t)Ntot * h;
+  const dim3 g2((Ntot + 255) / 256, h);
+  PairArgs pa = pair_args(s, precision == 1 ? nullptr : static_cast<const double*>(xsrc), w, 1.0, 0.0, 1, s.ones,
+                          6);
+  if (precision == 1) pa.x32 = static_cast<const float*>(xsrc);
+  pa.sys_of = B.sys;
+  pa.sys_off = B.off;
+  pa.sys_flag = &gp.st[0].active;
+  pa.sys_flag_stride = int(sizeof(GDev) / sizeof(int));
+  for (int c = 0; c < kChunk; ++c) {
+    if (precision == 1)
+      bk_gather<float><<<g2, 256, 0, ctx->stream>>>(Vb, n, Ntot, B.sys, gp.st, s.minv, static_cast<float*>(xsrc));
+    else
+      bk_gather<double><<<g2, 256, 0, ctx->stream>>>(Vb, n, Ntot, B.sys, gp.st, s.minv, static_cast<double*>(xsrc));
+    GBI_CHECK(run_pairs(ctx, s.trunc, SET_H, SET_H, precision, pa));
+    bk_dots<<<dim3(S, m + 1), 256, 0, ctx->stream>>>(Vb, n, w, Ntot, h, B.off, gp.st, m, gp.h1);
+    bk_sub<<<g2, 256, 0, ctx->stream>>>(Vb, n, w, Ntot, B.sys, gp.st, m, gp.h1);
+    bk_dots<<<dim3(S, m + 1), 256, 0, ctx->stream>>>(Vb, n, w, Ntot, h, B.off, gp.st, m, gp.h2);
+    bk_sub<<<g2, 256, 0, ctx->stream>>>(Vb, n, w, Ntot, B.sys, gp.st, m, gp.h2);
+    bk_norm<<<S, 256, 0, ctx->stream>>>(w, Ntot, h, B.off, gp.st, 0, gp.nrm);
+    bk_finalize<<<S, 128, 0, ctx->stream>>>(gp);
+    bk_scale<<<g2, 256, 0, ctx->stream>>>(Vb, n, w, Ntot, B.sys, gp.st);
+    ctx->launches += 8;
+  }
   GBI_CHECK(cudaGetLastError());
   return GBI_OK;
 }
 
-gbi_status norm2(gbi_ctx* ctx, size_t n, const double* x, double& out) {
-  double* d = P<double>(ctx->dots) + kMaxRestart + 2;
-  GBI_TRY(multidot(ctx, n, x, 0, 1, x, d, 0));
-  GBI_CHECK(cudaMemcpyAsync(ctx->hbuf, d, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
-  GBI_CHECK(cudaStreamSynchronize(ctx->stream));
-  out = std::sqrt(std::max(0.0, ctx->hbuf[0]));
-  return GBI_OK;
+__global__ void bk_setup(GPtr p, double tol, int max_iter) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= p.S) return;
+  GDev* st = p.st + s;
+  st->tol = tol;
+  st->max_iter = max_iter;
+  st->m = p.m;
+  st->active = 0;
+  st->converged = 0;
+  st->iters = 0;
 }
 
-// Restarted right-preconditioned GMRES(m) for G^HH u = rhs, internal coordinates.
-// u holds the initial guess on entry (zero or warm start).  FP64 Arnoldi (classical
-// Gram-Schmidt applied twice), Givens rotations and triangular solve.
-gbi_status gmres(gbi_ctx* ctx, const Setup& s, int precision, const double* rhs, double* u, bool u_is_zero,
-                 double tol, int restart, int max_iter, gbi_info* info, int& iters, double& relres) {
-  const size_t n = (size_t)s.N * s.h;
+gbi_status gmres_batch(gbi_ctx* ctx, const Setup& s, const Batch& B, int precision, const double* rhs, double* u,
+                       bool u_is_zero, double tol, int restart, int max_iter, gbi_info* info, int& iters,
+                       double& relres, std::vector<GDev>& hst) {
+  constexpr int kChunk = 6;
+  const int S = B.S, Ntot = B.Ntot, h = s.h;
+  const size_t n = (size_t)Ntot * h;
   const int m = std::max(1, std::min(restart, kMaxRestart));
   GBI_TRY(ensure(ctx, ctx->krylov, sizeof(double) * n * (m + 1)));
   GBI_TRY(ensure(ctx, ctx->w, sizeof(double) * n));
-  GBI_TRY(ensure(ctx, ctx->dots, sizeof(double) * (2 * kMaxRestart + 8)));
+  GBI_TRY(ensure(ctx, ctx->gstate, sizeof(double) * gstate_doubles(m, S)));
+  GBI_TRY(ensure(ctx, ctx->x32, sizeof(double) * n));     // gathered Arnoldi source (float or double)
   double* Vb = P<double>(ctx->krylov);
   double* w = P<double>(ctx->w);
-  double* hd = P<double>(ctx->dots);
+  void* xsrc = ctx->x32.p;
+  const GPtr gp = gptrs(ctx->gstate.p, m, S);
+  const dim3 g2((Ntot + 255) / 256, h);
+  const int sblk = (S + 127) / 128;
   iters = 0;
   relres = 0.0;
-  double bnorm;
-  GBI_TRY(norm2(ctx, n, rhs, bnorm));
-  if (bnorm == 0.0) {
-    GBI_CHECK(cudaMemsetAsync(u, 0, sizeof(double) * n, ctx->stream));
-    return GBI_OK;
+  bk_setup<<<sblk, 128, 0, ctx->stream>>>(gp, tol, std::max(0, max_iter));
+  ++ctx->launches;
+  // chunk graph: captured once per buffer set, replayed afterwards
+  const bool graphs = ctx->allow_graphs && ctx->stream != nullptr && !ctx->prof;
+  if (graphs) {
+    const void* key[8] = {Vb, w, xsrc, ctx->gstate.p, B.sys, B.off, s.pos.hi, s.pos.p64};
+    const long long ikey[6] = {(long long)n, S, m, precision, s.trunc, Ntot};
+    bool same = ctx->chunk_exec != nullptr;
+    for (int i = 0; i < 8 && same; ++i) same = ctx->chunk_key[i] == key[i];
+    for (int i = 0; i < 6 && same; ++i) same = ctx->chunk_ikey[i] == ikey[i];
+    if (!same) {
+      if (ctx->chunk_exec) cudaGraphExecDestroy(ctx->chunk_exec);
+      ctx->chunk_exec = nullptr;
+      const long long saved = ctx->launches;
+      cudaGraph_t graph = nullptr;
+      GBI_CHECK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+      gbi_status st = launch_chunk(ctx, s, B, precision, gp, m, Vb, w, xsrc, kChunk);
+      cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
+      if (st != GBI_OK) return st;
+      GBI_CHECK(e);
+      e = cudaGraphInstantiate(&ctx->chunk_exec, graph, 0);
+      cudaGraphDestroy(graph);
+      GBI_CHECK(e);
+      ctx->chunk_nodes = int(ctx->launches - saved);
+      ctx->launches = saved;
+      for (int i = 0; i < 8; ++i) ctx->chunk_key[i] = key[i];
+      for (int i = 0; i < 6; ++i) ctx->chunk_ikey[i] = ikey[i];
+    }
   }
-  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
+  hst.resize(S);
   bool first = true;
+  std::vector<int> before(S, 0);
   while (true) {
-    // r = rhs - A u  -> V_0
-    if (first && u_is_zero) {
-      GBI_CHECK(cudaMemcpyAsync(Vb, rhs, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
-    } else {
-      GBI_CHECK(cudaMemcpyAsync(Vb, rhs, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
-      GBI_TRY(apply_HH(ctx, s, precision, u, Vb, -1.0, 1.0, s.ones, info));
-    }
-    first = false;
-    double beta;
-    GBI_TRY(norm2(ctx, n, Vb, beta));
-    relres = beta / bnorm;
-    if (relres <= tol || iters >= max_iter) break;
-    k_scale_copy<<<grid1(n), 256, 0, ctx->stream>>>(n, Vb, 1.0 / beta, Vb);
-    ++ctx->launches;
-    std::fill(g.begin(), g.end(), 0.0);
-    g[0] = beta;
-    int kdim = 0;
-    bool done = false;
-    for (int j = 0; j < m; ++j) {
-      double* vj = Vb + (size_t)j * n;
-      GBI_TRY(apply_HH(ctx, s, precision, vj, w, 1.0, 0.0, s.minv, info));
-      // classical Gram-Schmidt, twice
-      GBI_TRY(multidot(ctx, n, Vb, n, j + 1, w, hd, 0));
-      k_sub_multi<<<grid1(n), 256, 0, ctx->stream>>>(n, Vb, n, j + 1, hd, w);
-      ++ctx->launches;
-      GBI_TRY(multidot(ctx, n, Vb, n, j + 1, w, hd + kMaxRestart + 4, 0));
-      k_sub_multi<<<grid1(n), 256, 0, ctx->stream>>>(n, Vb, n, j + 1, hd + kMaxRestart + 4, w);
-      ++ctx->launches;
-      GBI_TRY(multidot(ctx, n, w, 0, 1, w, hd + kMaxRestart + 3, 0));
-      GBI_CHECK(cudaGetLastError());
-      GBI_CHECK(cudaMemcpyAsync(ctx->hbuf, hd, sizeof(double) * (2 * kMaxRestart + 8), cudaMemcpyDeviceToHost,
-                                ctx->stream));
-      GBI_CHECK(cudaStreamSynchronize(ctx->stream));
-      const double* h1 = ctx->hbuf;
-      const double* h2 = ctx->hbuf + kMaxRestart + 4;
-      const double hn = std::sqrt(std::max(0.0, ctx->hbuf[kMaxRestart + 3]));
-      for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = h1[i] + h2[i];
-      H[(size_t)(j + 1) * m + j] = hn;
-      for (int i = 0; i < j; ++i) {
-        const double t1 = H[(size_t)i * m + j], t2 = H[(size_t)(i + 1) * m + j];
-        H[(size_t)i * m + j] = cs[i] * t1 + sn[i] * t2;
-        H[(size_t)(i + 1) * m + j] = -sn[i] * t1 + cs[i] * t2;
+    // V_0 = rhs - A u on the enabled systems, beta_s = |V_0,s|
+    GBI_CHECK(cudaMemcpyAsync(Vb, rhs, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+    if (!(first && u_is_zero)) {
+      PairArgs pr = pair_args(s, u, Vb, -1.0, 1.0, 1, s.ones, 6);
+      pr.sys_of = B.sys;
+      pr.sys_off = B.off;
+      pr.sys_flag = &gp.st[0].enabled;
+      pr.sys_flag_stride = int(sizeof(GDev) / sizeof(int));
+      GBI_CHECK(run_pairs(ctx, s.trunc, SET_H, SET_H, precision, pr));
+      if (info) {
+        (precision == 1 ? info->matvecs_f32 : info->matvecs_f64) += 1;
+        for (int q = 0; q < S; ++q)
+          if (hst[q].enabled) info->pair_interactions += (long long)(B.h_off[q + 1] - B.h_off[q]) * (B.h_off[q + 1] - B.h_off[q] - 1);
       }
-      const double hjj = H[(size_t)j * m + j], hj1 = H[(size_t)(j + 1) * m + j];
-      const double den = std::hypot(hjj, hj1);
-      cs[j] = den > 0 ? hjj / den : 1.0;
-      sn[j] = den > 0 ? hj1 / den : 0.0;
-      H[(size_t)j * m + j] = den;
-      H[(size_t)(j + 1) * m + j] = 0.0;
-      g[j + 1] = -sn[j] * g[j];
-      g[j] = cs[j] * g[j];
-      ++iters;
-      kdim = j + 1;
-      relres = std::fabs(g[j + 1]) / bnorm;
-      if (relres <= tol || iters >= max_iter || hn <= 1e-300) {
-        done = true;
-        break;
-      }
-      k_scale_copy<<<grid1(n), 256, 0, ctx->stream>>>(n, w, 1.0 / hn, Vb + (size_t)(j + 1) * n);
-      ++ctx->launches;
     }
-    // y = H^-1 g (upper triangular kdim x kdim)
-    for (int i = kdim - 1; i >= 0; --i) {
-      double t = g[i];
-      for (int k = i + 1; k < kdim; ++k) t -= H[(size_t)i * m + k] * y[k];
-      y[i] = t / H[(size_t)i * m + i];
-    }
-    Coef cy;
-    for (int i = 0; i < kdim; ++i) cy.v[i] = y[i];
-    k_update_solution<<<grid1(n), 256, 0, ctx->stream>>>(s.N, s.h, Vb, n, kdim, cy, s.minv, u);
-    ++ctx->launches;
+    bk_norm<<<S, 256, 0, ctx->stream>>>(Vb, Ntot, h, B.off, gp.st, 1, gp.nrm);
+    bk_init_cycle<<<sblk, 128, 0, ctx->stream>>>(gp, first ? 1 : 0);
+    bk_scale0<<<g2, 256, 0, ctx->stream>>>(Vb, Ntot, B.sys, gp.st);
+    ctx->launches += 3;
     GBI_CHECK(cudaGetLastError());
-    if (done && (relres <= tol || iters >= max_iter)) break;
-    if (done) break;   // breakdown: exact solution in the Krylov space
+    first = false;
+    for (int q = 0; q < S; ++q) before[q] = hst[q].iters;
+    // Arnoldi iterations in chunks, one host check per chunk
+    bool any = true;
+    {
+      // iteration counters at cycle start (bk_init_cycle keeps them across restarts)
+      ctx->hbatch.resize(sizeof(GDev) * S);
+      GBI_CHECK(cudaMemcpyAsync(ctx->hbatch.data(), gp.st, sizeof(GDev) * S, cudaMemcpyDeviceToHost, ctx->stream));
+      GBI_CHECK(cudaStreamSynchronize(ctx->stream));
+      std::memcpy(hst.data(), ctx->hbatch.data(), sizeof(GDev) * S);
+      any = false;
+      for (int q = 0; q < S; ++q) {
+        before[q] = hst[q].iters;
+        any = any || hst[q].active;
+      }
+    }
+    while (any) {
+      if (graphs) {
+        GBI_CHECK(cudaGraphLaunch(ctx->chunk_exec, ctx->stream));
+        ctx->launches += ctx->chunk_nodes;
+      } else {
+        GBI_TRY(launch_chunk(ctx, s, B, precision, gp, m, Vb, w, xsrc, kChunk));
+      }
+      GBI_CHECK(cudaMemcpyAsync(ctx->hbatch.data(), gp.st, sizeof(GDev) * S, cudaMemcpyDeviceToHost, ctx->stream));
+      GBI_CHECK(cudaStreamSynchronize(ctx->stream));
+      std::vector<GDev> prev = hst;
+      std::memcpy(hst.data(), ctx->hbatch.data(), sizeof(GDev) * S);
+      int live = 0;
+      any = false;
+      for (int q = 0; q < S; ++q) {
+        const int d = hst[q].iters - prev[q].iters;
+        live = std::max(live, d);
+        any = any || hst[q].active;
+        if (info) info->pair_interactions += (long long)d * (B.h_off[q + 1] - B.h_off[q]) * (B.h_off[q + 1] - B.h_off[q] - 1);
+      }
+      if (info) (precision == 1 ? info->matvecs_f32 : info->matvecs_f64) += live;
+      ctx->stat_dead[precision * 9 + SET_H * 3 + SET_H] += kChunk - live;
+    }
+    bk_solve_y<<<S, 128, 0, ctx->stream>>>(gp);
+    bk_update<<<g2, 256, 0, ctx->stream>>>(Vb, n, Ntot, B.sys, gp, s.minv, u);
+    ctx->launches += 2;
+    GBI_CHECK(cudaGetLastError());
+    bool restart_any = false;
+    for (int q = 0; q < S; ++q) {
+      const GDev& g = hst[q];
+      iters = std::max(iters, g.iters);
+      if (g.enabled && g.kdim > 0 && !g.converged && !g.breakdown && g.iters < g.max_iter) restart_any = true;
+    }
+    if (!restart_any) break;
   }
+  relres = 0.0;
+  for (int q = 0; q < S; ++q)
+    if (hst[q].enabled) relres = std::max(relres, hst[q].res);
   return GBI_OK;
 }
 
@@ -614,6 +915,215 @@ bool valid_params(const gbi_params* p) {
   if (p->trunc < 2 || p->trunc > 4) return false;
   if (p->precision < 0 || p->precision > 2) return false;
   return true;
+}
+
+// The full solve for a batch of independent suspensions (S = 1: one suspension).
+// Inputs and outputs are concatenated over the systems ([Ntot][3], [Ntot][h]).
+gbi_status solve_core(gbi_ctx* ctx, const gbi_params* prm, const Batch& B, const double* R, const double* Va,
+                      const double* Oa, const double* VH, const double* Fe, const double* Te, double* V,
+                      double* Omega, double* QH, int warm_start, gbi_info* inf) {
+  const int N = B.Ntot, S = B.S;
+  Setup s;
+  GBI_TRY(setup_call(ctx, s, N, prm->trunc, prm->a, prm->eta, R));
+  long long pairs_all = 0;
+  for (int q = 0; q < S; ++q) {
+    const long long ns = B.h_off[q + 1] - B.h_off[q];
+    pairs_all += ns * (ns - 1);
+  }
+  s.pairs_per_pass = pairs_all;
+  const int D = s.D, h = s.h;
+  const size_t nh = (size_t)N * h;
+  const dim3 g2((N + 255) / 256, h);
+  const int sblk = (S + 127) / 128;
+  // arithmetic of the passes that need more than FP32: FP64, or double-float (precision 2)
+  const int hp = prm->precision == 2 ? 2 : 0;
+  const int restart = std::max(1, std::min(prm->restart > 0 ? prm->restart : 40, kMaxRestart));
+  GBI_TRY(ensure(ctx, ctx->xQ, sizeof(double) * (size_t)N * D));
+  GBI_TRY(ensure(ctx, ctx->xVH, sizeof(double) * nh));
+  GBI_TRY(ensure(ctx, ctx->b, sizeof(double) * nh));
+  GBI_TRY(ensure(ctx, ctx->r, sizeof(double) * nh));
+  GBI_TRY(ensure(ctx, ctx->delta, sizeof(double) * nh));
+  GBI_TRY(ensure(ctx, ctx->xVL, sizeof(double) * 6 * N));
+  GBI_TRY(ensure(ctx, ctx->minr2, sizeof(unsigned int)));
+  GBI_TRY(ensure(ctx, ctx->gstate, sizeof(double) * gstate_doubles(restart, S)));
+  double* xF = P<double>(ctx->xQ);              // rows 0..5 of the full vector
+  double* xQH = P<double>(ctx->xQ) + (size_t)6 * N;
+  double* b = P<double>(ctx->b);
+  double* r = P<double>(ctx->r);
+  double* dl = P<double>(ctx->delta);
+  const GPtr gp = gptrs(ctx->gstate.p, restart, S);
+  const double c2a = s.scale.v[3];
+  Scales hscale;
+  for (int i = 0; i < 54; ++i) hscale.v[i] = (i < h) ? s.scale.v[6 + i] : 1.0;
+  auto batched = [&](PairArgs p, const int* flag) {
+    p.sys_of = B.sys;
+    p.sys_off = B.off;
+    p.sys_flag = flag;
+    p.sys_flag_stride = int(sizeof(GDev) / sizeof(int));
+    return p;
+  };
+  std::vector<GDev> hst(S);
+
+  // inputs -> internal coordinates
+  k_pack_lower<<<grid1(N), 256, 0, ctx->stream>>>(N, s.a, c2a, Fe, Te, xF);
+  // b = -8 pi eta V^H
+  k_pack_higher<<<grid1(nh), 256, 0, ctx->stream>>>(N, h, VH, hscale, -8.0 * kPi * s.eta, b);
+  ctx->launches += 2;
+  GBI_CHECK(cudaGetLastError());
+  // b -= G^HL F^L, with the overlap scan
+  const unsigned int init_bits = 0x7f7fffffu;
+  GBI_CHECK(cudaMemcpyAsync(ctx->minr2.p, &init_bits, sizeof(unsigned int), cudaMemcpyHostToDevice, ctx->stream));
+  {
+    PairArgs p = batched(pair_args(s, xF, b, -1.0, 1.0, 0, s.ones, 0), nullptr);
+    p.min_r2_bits = P<unsigned int>(ctx->minr2);
+    GBI_CHECK(run_pairs(ctx, s.trunc, SET_H, SET_L, hp, p));
+    inf->matvecs_f64 += 1;
+    inf->pair_interactions += pairs_all;
+  }
+  if (prm->min_sep > 0) {
+    unsigned int bits = 0;
+    GBI_CHECK(cudaMemcpyAsync(&bits, ctx->minr2.p, sizeof(unsigned int), cudaMemcpyDeviceToHost, ctx->stream));
+    GBI_CHECK(cudaStreamSynchronize(ctx->stream));
+    float mr2;
+    std::memcpy(&mr2, &bits, sizeof(float));
+    inf->min_separation = pairs_all > 0 ? std::sqrt(double(mr2)) / s.a : 0.0;
+    if (pairs_all > 0 && inf->min_separation < prm->min_sep) return GBI_ERR_OVERLAP;
+  }
+
+  // initial guess
+  bool zero = true;
+  if (warm_start) {
+    k_pack_higher<<<grid1(nh), 256, 0, ctx->stream>>>(N, h, QH, hscale, 1.0, xQH);
+    ++ctx->launches;
+    zero = false;
+  } else {
+    GBI_CHECK(cudaMemsetAsync(xQH, 0, sizeof(double) * nh, ctx->stream));
+  }
+  const int max_iter = prm->max_iter > 0 ? prm->max_iter : 1000;
+  const double rtol = prm->rtol > 0 ? prm->rtol : 1e-10;
+  // |b_s| per system
+  bk_norm<<<S, 256, 0, ctx->stream>>>(b, N, h, B.off, gp.st, 2, gp.nrm);
+  bk_refine<<<sblk, 128, 0, ctx->stream>>>(gp, 0, rtol);
+  ctx->launches += 2;
+  auto read_state = [&]() -> gbi_status {
+    ctx->hbatch.resize(sizeof(GDev) * S);
+    GBI_CHECK(cudaMemcpyAsync(ctx->hbatch.data(), gp.st, sizeof(GDev) * S, cudaMemcpyDeviceToHost, ctx->stream));
+    GBI_CHECK(cudaStreamSynchronize(ctx->stream));
+    std::memcpy(hst.data(), ctx->hbatch.data(), sizeof(GDev) * S);
+    return GBI_OK;
+  };
+  auto pairs_enabled = [&]() {
+    long long c = 0;
+    for (int q = 0; q < S; ++q)
+      if (hst[q].enabled) {
+        const long long ns = B.h_off[q + 1] - B.h_off[q];
+        c += ns * (ns - 1);
+      }
+    return c;
+  };
+  GBI_TRY(read_state());
+  bool converged = false;
+  if (prm->precision == 0) {
+    int it = 0;
+    double rr = 0.0;
+    GBI_TRY(gmres_batch(ctx, s, B, 0, b, xQH, zero, rtol, restart, max_iter, inf, it, rr, hst));
+    inf->iters += it;
+    // true FP64 residual per system
+    GBI_CHECK(cudaMemcpyAsync(r, b, sizeof(double) * nh, cudaMemcpyDeviceToDevice, ctx->stream));
+    PairArgs p = batched(pair_args(s, xQH, r, -1.0, 1.0, 1, s.ones, 6), &gp.st[0].enabled);
+    GBI_CHECK(run_pairs(ctx, s.trunc, SET_H, SET_H, 0, p));
+    inf->matvecs_f64 += 1;
+    inf->pair_interactions += pairs_enabled();
+    bk_norm<<<S, 256, 0, ctx->stream>>>(r, N, h, B.off, gp.st, 1, gp.nrm);
+    bk_refine<<<sblk, 128, 0, ctx->stream>>>(gp, 1, rtol);
+    ctx->launches += 2;
+    GBI_TRY(read_state());
+  } else {
+    // mixed precision: r = b - A_hp x; A_32 d = r (FP32 pair sums, FP64 Arnoldi); x += d
+    const double inner = prm->inner_rtol > 0 ? prm->inner_rtol : 1e-5;
+    const int max_refine = prm->max_refine > 0 ? prm->max_refine : 8;
+    for (int sweep = 0;; ++sweep) {
+      GBI_CHECK(cudaMemcpyAsync(r, b, sizeof(double) * nh, cudaMemcpyDeviceToDevice, ctx->stream));
+      if (!(zero && sweep == 0)) {
+        PairArgs p = batched(pair_args(s, xQH, r, -1.0, 1.0, 1, s.ones, 6), &gp.st[0].enabled);
+        GBI_CHECK(run_pairs(ctx, s.trunc, SET_H, SET_H, hp, p));
+        inf->matvecs_f64 += 1;
+        inf->pair_interactions += pairs_enabled();
+        bk_norm<<<S, 256, 0, ctx->stream>>>(r, N, h, B.off, gp.st, 1, gp.nrm);
+        bk_refine<<<sblk, 128, 0, ctx->stream>>>(gp, 1, rtol);
+        ctx->launches += 2;
+      }
+      if (sweep > 0) inf->refinements += 1;
+      if (sweep >= max_refine || inf->iters >= max_iter) {
+        GBI_TRY(read_state());
+        break;
+      }
+      int it = 0;
+      double rr = 0.0;
+      GBI_CHECK(cudaMemsetAsync(dl, 0, sizeof(double) * nh, ctx->stream));
+      GBI_TRY(gmres_batch(ctx, s, B, 1, r, dl, true, inner, restart, max_iter - inf->iters, inf, it, rr, hst));
+      inf->iters += it;
+      bool any = false;
+      for (int q = 0; q < S; ++q) any = any || hst[q].enabled;
+      if (!any) break;       // every system met the tolerance at this sweep's residual
+      bk_axpy_enabled<<<g2, 256, 0, ctx->stream>>>(dl, N, B.sys, gp.st, xQH);
+      ++ctx->launches;
+      GBI_CHECK(cudaGetLastError());
+    }
+  }
+  converged = true;
+  inf->rel_residual = 0.0;
+  for (int q = 0; q < S; ++q) {
+    inf->rel_residual = std::max(inf->rel_residual, hst[q].rel);
+    if (hst[q].rel > rtol) converged = false;
+  }
+  // outputs: 8 pi eta x^{V,L} = -(G^LL F^L + G^LH Q^H) incl. self
+  {
+    PairArgs p = batched(pair_args(s, P<double>(ctx->xQ), P<double>(ctx->xVL), -1.0 / (8.0 * kPi * s.eta), 0.0, 1,
+                                   s.ones, 0),
+                         nullptr);
+    GBI_CHECK(run_pairs(ctx, s.trunc, SET_L, SET_ALL, hp, p));
+    inf->matvecs_f64 += 1;
+    inf->pair_interactions += pairs_all;
+  }
+  k_finalize_lower<<<grid1(N), 256, 0, ctx->stream>>>(N, s.a, c2a, P<double>(ctx->xVL), Va, Oa, V, Omega);
+  ++ctx->launches;
+  if (QH) {
+    k_unpack_higher<<<grid1(nh), 256, 0, ctx->stream>>>(N, h, xQH, hscale, QH);
+    ++ctx->launches;
+  }
+  GBI_CHECK(cudaGetLastError());
+  if (prm->min_sep <= 0) {
+    unsigned int bits = 0;
+    GBI_CHECK(cudaMemcpyAsync(&bits, ctx->minr2.p, sizeof(unsigned int), cudaMemcpyDeviceToHost, ctx->stream));
+    GBI_CHECK(cudaStreamSynchronize(ctx->stream));
+    float mr2;
+    std::memcpy(&mr2, &bits, sizeof(float));
+    inf->min_separation = pairs_all > 0 ? std::sqrt(double(mr2)) / s.a : 0.0;
+  } else {
+    GBI_CHECK(cudaStreamSynchronize(ctx->stream));
+  }
+  return converged ? GBI_OK : GBI_ERR_NOT_CONVERGED;
+}
+
+// S = 1 batch over the spheres [0, N): offsets and system ids in the context workspace
+gbi_status single_batch(gbi_ctx* ctx, int N, Batch& B) {
+  GBI_TRY(ensure(ctx, ctx->boff, sizeof(int) * 2));
+  GBI_TRY(ensure(ctx, ctx->bsys, sizeof(int) * (size_t)std::max(N, 1)));
+  const int off[2] = {0, N};
+  GBI_CHECK(cudaMemcpyAsync(ctx->boff.p, off, sizeof(off), cudaMemcpyHostToDevice, ctx->stream));
+  GBI_CHECK(cudaMemsetAsync(ctx->bsys.p, 0, sizeof(int) * (size_t)N, ctx->stream));
+  B.S = 1;
+  B.Ntot = N;
+  B.off = P<int>(ctx->boff);
+  B.sys = P<int>(ctx->bsys);
+  B.h_off.assign({0, N});
+  return GBI_OK;
+}
+
+__global__ void k_fill_sys(int S, const int* __restrict__ off, int* sys) {
+  const int s = blockIdx.x;
+  for (int p = off[s] + threadIdx.x; p < off[s + 1]; p += blockDim.x) sys[p] = s;
 }
 
 }  // namespace
@@ -646,7 +1156,7 @@ gbi_status gbi_destroy(gbi_ctx* ctx) {
   cudaStreamSynchronize(ctx->stream);
   Buf* bufs[] = {&ctx->pos_hi, &ctx->pos_lo, &ctx->pos64, &ctx->xF, &ctx->xVH, &ctx->b, &ctx->xQ, &ctx->r,
                  &ctx->delta, &ctx->krylov, &ctx->w, &ctx->partial, &ctx->dots, &ctx->xVL, &ctx->minr2,
-                 &ctx->colbuf, &ctx->x32, &ctx->trapbuf, &ctx->tFe, &ctx->tTe, &ctx->tVa, &ctx->tOa, &ctx->tVH, &ctx->tV, &ctx->tOm,
+                 &ctx->colbuf, &ctx->x32, &ctx->trapbuf, &ctx->gstate, &ctx->boff, &ctx->bsys, &ctx->tFe, &ctx->tTe, &ctx->tVa, &ctx->tOa, &ctx->tVH, &ctx->tV, &ctx->tOm,
                  &ctx->tQH, &ctx->hR, &ctx->hVa, &ctx->hOa, &ctx->hVH, &ctx->hFe, &ctx->hTe, &ctx->hV,
                  &ctx->hOm, &ctx->hQH};
   for (Buf* b : bufs)
@@ -654,6 +1164,7 @@ gbi_status gbi_destroy(gbi_ctx* ctx) {
   if (ctx->hbuf) cudaFreeHost(ctx->hbuf);
   drain_profile(ctx);
   for (cudaEvent_t e : ctx->pool) cudaEventDestroy(e);
+  if (ctx->chunk_exec) cudaGraphExecDestroy(ctx->chunk_exec);
   delete ctx;
   return GBI_OK;
 }
@@ -726,128 +1237,39 @@ gbi_status gbi_solve(gbi_ctx* ctx, const gbi_params* prm, int N, const double* R
   *inf = gbi_info{};
   if (N == 0) return GBI_OK;
   if (!R || !Va || !Oa || !VH || !Fe || !Te || !V || !Omega || (warm_start && !QH)) return GBI_ERR_ARG;
-  Setup s;
-  GBI_TRY(setup_call(ctx, s, N, prm->trunc, prm->a, prm->eta, R));
-  const int D = s.D, h = s.h;
-  const size_t nh = (size_t)N * h;
-  // arithmetic of the passes that need more than FP32: FP64, or double-float (precision 2)
-  const int hp = prm->precision == 2 ? 2 : 0;
-  GBI_TRY(ensure(ctx, ctx->xQ, sizeof(double) * (size_t)N * D));
-  GBI_TRY(ensure(ctx, ctx->xVH, sizeof(double) * nh));
-  GBI_TRY(ensure(ctx, ctx->b, sizeof(double) * nh));
-  GBI_TRY(ensure(ctx, ctx->r, sizeof(double) * nh));
-  GBI_TRY(ensure(ctx, ctx->delta, sizeof(double) * nh));
-  GBI_TRY(ensure(ctx, ctx->xVL, sizeof(double) * 6 * N));
-  GBI_TRY(ensure(ctx, ctx->minr2, sizeof(unsigned int)));
-  GBI_TRY(ensure(ctx, ctx->dots, sizeof(double) * (2 * kMaxRestart + 8)));
-  double* xF = P<double>(ctx->xQ);              // rows 0..5 of the full vector
-  double* xQH = P<double>(ctx->xQ) + (size_t)6 * N;
-  double* b = P<double>(ctx->b);
-  double* r = P<double>(ctx->r);
-  double* dl = P<double>(ctx->delta);
-  const double c2a = s.scale.v[3];
-  Scales hscale;
-  for (int i = 0; i < 54; ++i) hscale.v[i] = (i < h) ? s.scale.v[6 + i] : 1.0;
+  Batch B;
+  GBI_TRY(single_batch(ctx, N, B));
+  return solve_core(ctx, prm, B, R, Va, Oa, VH, Fe, Te, V, Omega, QH, warm_start, inf);
+}
 
-  // inputs -> internal coordinates
-  k_pack_lower<<<grid1(N), 256, 0, ctx->stream>>>(N, s.a, c2a, Fe, Te, xF);
-  ++ctx->launches;
-  // b = -8 pi eta V^H
-  k_pack_higher<<<grid1(nh), 256, 0, ctx->stream>>>(N, h, VH, hscale, -8.0 * kPi * s.eta, b);
+gbi_status gbi_batch_solve(gbi_ctx* ctx, const gbi_params* prm, int nsys, const int* offsets_host, const double* R,
+                           const double* Va, const double* Oa, const double* VH, const double* Fe, const double* Te,
+                           double* V, double* Omega, double* QH, int warm_start, gbi_info* info) {
+  if (!ctx || !valid_params(prm) || nsys < 0 || (nsys > 0 && !offsets_host)) return GBI_ERR_ARG;
+  gbi_info local{};
+  gbi_info* inf = info ? info : &local;
+  *inf = gbi_info{};
+  if (nsys == 0) return GBI_OK;
+  if (offsets_host[0] != 0) return GBI_ERR_ARG;
+  for (int q = 0; q < nsys; ++q)
+    if (offsets_host[q + 1] < offsets_host[q]) return GBI_ERR_ARG;
+  const int N = offsets_host[nsys];
+  if (N == 0) return GBI_OK;
+  if (!R || !Va || !Oa || !VH || !Fe || !Te || !V || !Omega || (warm_start && !QH)) return GBI_ERR_ARG;
+  GBI_TRY(ensure(ctx, ctx->boff, sizeof(int) * (size_t)(nsys + 1)));
+  GBI_TRY(ensure(ctx, ctx->bsys, sizeof(int) * (size_t)N));
+  GBI_CHECK(cudaMemcpyAsync(ctx->boff.p, offsets_host, sizeof(int) * (size_t)(nsys + 1), cudaMemcpyHostToDevice,
+                            ctx->stream));
+  k_fill_sys<<<nsys, 256, 0, ctx->stream>>>(nsys, P<int>(ctx->boff), P<int>(ctx->bsys));
   ++ctx->launches;
   GBI_CHECK(cudaGetLastError());
-  // b -= G^HL F^L  (FP64), with the overlap scan
-  const unsigned int init_bits = 0x7f7fffffu;
-  GBI_CHECK(cudaMemcpyAsync(ctx->minr2.p, &init_bits, sizeof(unsigned int), cudaMemcpyHostToDevice, ctx->stream));
-  {
-    PairArgs p = pair_args(s, xF, b, -1.0, 1.0, 0, s.ones, 0);
-    p.min_r2_bits = P<unsigned int>(ctx->minr2);
-    GBI_CHECK(run_pairs(ctx, s.trunc, SET_H, SET_L, hp, p));
-    inf->matvecs_f64 += 1;
-    inf->pair_interactions += s.pairs_per_pass;
-  }
-  unsigned int bits = 0;
-  GBI_CHECK(cudaMemcpyAsync(&bits, ctx->minr2.p, sizeof(unsigned int), cudaMemcpyDeviceToHost, ctx->stream));
-  GBI_CHECK(cudaStreamSynchronize(ctx->stream));
-  float mr2;
-  std::memcpy(&mr2, &bits, sizeof(float));
-  inf->min_separation = N > 1 ? std::sqrt(double(mr2)) / s.a : 0.0;
-  if (prm->min_sep > 0 && N > 1 && inf->min_separation < prm->min_sep) return GBI_ERR_OVERLAP;
-
-  // initial guess
-  bool zero = true;
-  if (warm_start) {
-    k_pack_higher<<<grid1(nh), 256, 0, ctx->stream>>>(N, h, QH, hscale, 1.0, xQH);
-    ++ctx->launches;
-    zero = false;
-  } else {
-    GBI_CHECK(cudaMemsetAsync(xQH, 0, sizeof(double) * nh, ctx->stream));
-  }
-  const int restart = prm->restart > 0 ? prm->restart : 40;
-  const int max_iter = prm->max_iter > 0 ? prm->max_iter : 1000;
-  const double rtol = prm->rtol > 0 ? prm->rtol : 1e-10;
-  double bnorm = 0.0;
-  GBI_TRY(norm2(ctx, nh, b, bnorm));
-  bool converged = false;
-  if (h == 0 || bnorm == 0.0) {
-    GBI_CHECK(cudaMemsetAsync(xQH, 0, sizeof(double) * nh, ctx->stream));
-    converged = true;
-    inf->rel_residual = 0.0;
-  } else if (prm->precision == 0) {
-    int it = 0;
-    double rr = 0.0;
-    GBI_TRY(gmres(ctx, s, 0, b, xQH, zero, rtol, restart, max_iter, inf, it, rr));
-    inf->iters += it;
-    // true FP64 residual
-    GBI_CHECK(cudaMemcpyAsync(r, b, sizeof(double) * nh, cudaMemcpyDeviceToDevice, ctx->stream));
-    GBI_TRY(apply_HH(ctx, s, 0, xQH, r, -1.0, 1.0, s.ones, inf));
-    double rn;
-    GBI_TRY(norm2(ctx, nh, r, rn));
-    inf->rel_residual = rn / bnorm;
-    converged = inf->rel_residual <= rtol;
-  } else {
-    // mixed precision: r = b - A64 x; A32 d = r (FP32 pair sums, FP64 Arnoldi); x += d
-    const double inner = prm->inner_rtol > 0 ? prm->inner_rtol : 1e-5;
-    const int max_refine = prm->max_refine > 0 ? prm->max_refine : 8;
-    for (int sweep = 0;; ++sweep) {
-      GBI_CHECK(cudaMemcpyAsync(r, b, sizeof(double) * nh, cudaMemcpyDeviceToDevice, ctx->stream));
-      if (!(zero && sweep == 0)) GBI_TRY(apply_HH(ctx, s, hp, xQH, r, -1.0, 1.0, s.ones, inf));
-      double rn;
-      GBI_TRY(norm2(ctx, nh, r, rn));
-      inf->rel_residual = rn / bnorm;
-      if (sweep > 0) inf->refinements += 1;
-      if (inf->rel_residual <= rtol) {
-        converged = true;
-        break;
-      }
-      if (sweep >= max_refine || inf->iters >= max_iter) break;
-      int it = 0;
-      double rr = 0.0;
-      GBI_CHECK(cudaMemsetAsync(dl, 0, sizeof(double) * nh, ctx->stream));
-      GBI_TRY(gmres(ctx, s, 1, r, dl, true, inner, restart, max_iter - inf->iters, inf, it, rr));
-      inf->iters += it;
-      k_update_solution<<<grid1(nh), 256, 0, ctx->stream>>>(N, h, dl, nh, 1, Coef{{1.0}}, s.ones, xQH);
-      ++ctx->launches;
-      GBI_CHECK(cudaGetLastError());
-    }
-  }
-  // outputs: 8 pi eta x^{V,L} = -(G^LL F^L + G^LH Q^H) incl. self
-  {
-    PairArgs p = pair_args(s, P<double>(ctx->xQ), P<double>(ctx->xVL), -1.0 / (8.0 * kPi * s.eta), 0.0, 1,
-                           s.ones, 0);
-    GBI_CHECK(run_pairs(ctx, s.trunc, SET_L, SET_ALL, hp, p));
-    inf->matvecs_f64 += 1;
-    inf->pair_interactions += s.pairs_per_pass;
-  }
-  k_finalize_lower<<<grid1(N), 256, 0, ctx->stream>>>(N, s.a, c2a, P<double>(ctx->xVL), Va, Oa, V, Omega);
-  ++ctx->launches;
-  if (QH) {
-    k_unpack_higher<<<grid1(nh), 256, 0, ctx->stream>>>(N, h, xQH, hscale, QH);
-    ++ctx->launches;
-  }
-  GBI_CHECK(cudaGetLastError());
-  GBI_CHECK(cudaStreamSynchronize(ctx->stream));
-  return converged ? GBI_OK : GBI_ERR_NOT_CONVERGED;
+  Batch B;
+  B.S = nsys;
+  B.Ntot = N;
+  B.off = P<int>(ctx->boff);
+  B.sys = P<int>(ctx->bsys);
+  B.h_off.assign(offsets_host, offsets_host + nsys + 1);
+  return solve_core(ctx, prm, B, R, Va, Oa, VH, Fe, Te, V, Omega, QH, warm_start, inf);
 }
 
 gbi_status gbi_superpose(gbi_ctx* ctx, const gbi_params* prm, int N, const double* R, const double* Va,
@@ -966,6 +1388,7 @@ gbi_status gbi_set_profiling(gbi_ctx* ctx, int on) {
   drain_profile(ctx);
   ctx->prof = on != 0;
   for (int i = 0; i < 30; ++i) {
+    ctx->stat_dead[i] = 0;
     ctx->stat_ms[i] = 0.0;
     ctx->stat_flops[i] = 0.0;
     ctx->stat_n[i] = 0;
@@ -978,8 +1401,10 @@ gbi_status gbi_kernel_stats(gbi_ctx* ctx, int kernel_class, double* total_ms, lo
   if (!ctx || kernel_class < 0 || kernel_class >= 30) return GBI_ERR_ARG;
   drain_profile(ctx);
   if (total_ms) *total_ms = ctx->stat_ms[kernel_class];
-  if (launches) *launches = ctx->stat_n[kernel_class];
-  if (flops) *flops = ctx->stat_flops[kernel_class];
+  const long long live = ctx->stat_n[kernel_class] - (ctx->prof ? ctx->stat_dead[kernel_class] : 0);
+  const double per = ctx->stat_n[kernel_class] > 0 ? ctx->stat_flops[kernel_class] / ctx->stat_n[kernel_class] : 0.0;
+  if (launches) *launches = live;
+  if (flops) *flops = per * double(live);
   return GBI_OK;
 }
 
@@ -1052,7 +1477,11 @@ constexpr size_t kOffPart = kOffW + al256(sizeof(double) * kStaticMaxNH);
 constexpr size_t kOffDots = kOffPart + al256(sizeof(double) * 64 * (kMaxRestart + 2));
 constexpr size_t kOffMin = kOffDots + al256(sizeof(double) * (2 * kMaxRestart + 8));
 constexpr size_t kOffX32 = kOffMin + 256;
-constexpr size_t kStaticBytes = kOffX32 + al256(sizeof(float) * kStaticMaxND);
+constexpr size_t kOffGs = kOffX32 + al256(sizeof(float) * 2 * kStaticMaxND);
+constexpr size_t kOffBoff = kOffGs + al256(sizeof(double) * (64 + (kStaticMaxRestart + 1) * kStaticMaxRestart +
+                                                              8 * (kStaticMaxRestart + 1)));
+constexpr size_t kOffBsys = kOffBoff + 256;
+constexpr size_t kStaticBytes = kOffBsys + al256(sizeof(int) * kStaticMaxN);
 
 // The scratch itself (about 2.6 MB).  Every device that loads the library holds it
 // until the process exits.  Host code must not use this symbol as an address.
@@ -1085,6 +1514,7 @@ extern "C" gbi_status gbi_solve_static(void* stream, const gbi_params* prm, int 
   c.device = dev;
   c.stream = reinterpret_cast<cudaStream_t>(stream);
   c.hbuf = g_static_scalars;
+  c.allow_graphs = false;      // graph instantiation could allocate
   auto bind = [&](Buf& b, size_t off, size_t bytes) {
     b.p = base + off;
     b.bytes = bytes;
@@ -1103,7 +1533,10 @@ extern "C" gbi_status gbi_solve_static(void* stream, const gbi_params* prm, int 
   bind(c.partial, kOffPart, kOffDots - kOffPart);
   bind(c.dots, kOffDots, kOffMin - kOffDots);
   bind(c.minr2, kOffMin, 256);
-  bind(c.x32, kOffX32, kStaticBytes - kOffX32);
+  bind(c.x32, kOffX32, kOffGs - kOffX32);
+  bind(c.gstate, kOffGs, kOffBoff - kOffGs);
+  bind(c.boff, kOffBoff, 256);
+  bind(c.bsys, kOffBsys, kStaticBytes - kOffBsys);
   gbi_params p = *prm;
   if (p.restart <= 0) p.restart = kStaticMaxRestart;
   return gbi_solve(&c, &p, N, R, Va, Oa, VH, Fe, Te, V, Omega, QH, warm_start, info);

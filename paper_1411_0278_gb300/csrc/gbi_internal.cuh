@@ -42,6 +42,18 @@ struct PairArgs {
   double colscale[54];   // per-column multiplier applied to x (preconditioner / unit scaling)
   double selfg[54];      // one-body self scalars g (units 1/a) per component, for add_self
   unsigned int* min_r2_bits;   // optional: atomicMin of the smallest r^2 (float bits), may be null
+  // device-side indexing (GMRES on the device): if x_index is set, the kernel reads
+  // x + (*x_index) * x_stride; if active is set and *active == 0 the pass does nothing
+  const int* x_index;
+  size_t x_stride;
+  const int* active;
+  // batches of independent suspensions: sphere n belongs to system sys_of[n], whose
+  // spheres are [sys_off[s], sys_off[s+1]); only those are its sources.  If sys_flag is
+  // set, targets of a system with sys_flag[s * sys_flag_stride] == 0 are skipped.
+  const int* sys_of;
+  const int* sys_off;
+  const int* sys_flag;
+  int sys_flag_stride;
 };
 
 // Launch the generic single-layer pair operator; returns a CUDA error code.

@@ -233,13 +233,40 @@ __global__ void __launch_bounds__(TPB * WPT * 32) pair_kernel(const PairArgs arg
   __shared__ PT s_pos[POSW][TILE];
   __shared__ T s_x[NC][TILE];
 
+  if (args.active != nullptr && *args.active == 0) return;   // device-side GMRES has stopped
+  const double* __restrict__ xsrc = args.x_index ? args.x + (size_t)(*args.x_index) * args.x_stride : args.x;
   const int N = args.N;
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   const int tgt = warp / WPT;            // target slot in the block
   const int sub = warp - tgt * WPT;      // which share of the sources
   const int n = blockIdx.x * TPB + tgt;
-  const bool active = n < N;
+  // source range of this target's system (the whole set without batching)
+  int src_lo = 0, src_hi = N;
+  bool active = n < N;
+  if (active && args.sys_of != nullptr) {
+    const int sy = args.sys_of[n];
+    src_lo = args.sys_off[sy];
+    src_hi = args.sys_off[sy + 1];
+    if (args.sys_flag != nullptr && args.sys_flag[(size_t)sy * args.sys_flag_stride] == 0) active = false;
+  }
+  // the block's tile range: union of its targets' ranges
+  int blk_lo = active ? src_lo : N, blk_hi = active ? src_hi : 0;
+  if (args.sys_of != nullptr) {
+    __shared__ int s_rng[2];
+    if (threadIdx.x == 0) { s_rng[0] = N; s_rng[1] = 0; }
+    __syncthreads();
+    if (lane == 0 && sub == 0 && active) {
+      atomicMin(&s_rng[0], src_lo);
+      atomicMax(&s_rng[1], src_hi);
+    }
+    __syncthreads();
+    blk_lo = s_rng[0];
+    blk_hi = s_rng[1];
+  } else {
+    blk_lo = 0;
+    blk_hi = N;
+  }
   const T a = T(args.a);
 
   PT tp[POSW];
@@ -261,8 +288,8 @@ __global__ void __launch_bounds__(TPB * WPT * 32) pair_kernel(const PairArgs arg
   for (int p = 0; p < NR; ++p) acc[p] = T(0);
   float min_r2 = 3.0e38f;
 
-  for (int base = 0; base < N; base += TILE) {
-    const int len = min(TILE, N - base);
+  for (int base = blk_lo; base < blk_hi; base += TILE) {
+    const int len = min(TILE, blk_hi - base);
     __syncthreads();
     for (int idx = threadIdx.x; idx < len; idx += THREADS) {
       const int m = base + idx;
@@ -289,7 +316,7 @@ __global__ void __launch_bounds__(TPB * WPT * 32) pair_kernel(const PairArgs arg
       }
     } else {
       for (int q = 0; q < NC; ++q) {
-        const double* src = args.x + (size_t)q * N + base;
+        const double* src = xsrc + (size_t)q * N + base;
         const double cs = args.colscale[C0 + q];
         for (int j = threadIdx.x; j < len; j += THREADS) s_x[q][j] = T(src[j] * cs);
       }
@@ -297,7 +324,8 @@ __global__ void __launch_bounds__(TPB * WPT * 32) pair_kernel(const PairArgs arg
     __syncthreads();
     if (active) {
       for (int j = sub * 32 + lane; j < len; j += WPT * 32) {
-        if (base + j == n) continue;
+        const int m = base + j;
+        if (m == n || m < src_lo || m >= src_hi) continue;
         T dx, dy, dz;
         if constexpr (DF) {
           // exact difference of the hi parts, plus the (tiny) difference of the lo parts
@@ -359,7 +387,12 @@ __global__ void __launch_bounds__(TPB * WPT * 32) pair_kernel(const PairArgs arg
 #pragma unroll
     for (int p = 0; p < NR; ++p) {
       double v = gbi_to_double(acc[p]) * inva;
-      if (args.add_self) v += args.selfg[R0 + p] * inva * args.x[(size_t)(R0 - C0 + p) * N + n] * args.colscale[R0 + p];
+      if (args.add_self) {
+        const size_t k = (size_t)(R0 - C0 + p) * N + n;
+        // FP32 passes read the pre-scaled single-precision source; the others the FP64 one
+        const double xs = (F32 && args.x32 != nullptr) ? double(args.x32[k]) : xsrc[k] * args.colscale[R0 + p];
+        v += args.selfg[R0 + p] * inva * xs;
+      }
       double* dst = args.y + (size_t)p * N + n;
       *dst = args.alpha * v + (args.beta != 0.0 ? args.beta * (*dst) : 0.0);
     }

@@ -354,3 +354,99 @@ def test_edge_cases(ctx, gbi):
                                     t["Va"], t["Oa"], t["VH"], t["Fe"], t["Te"], allow_not_converged=True)
     assert st == gbi.GBI_ERR_NOT_CONVERGED and info.iters == 1 and info.rel_residual > 1e-10
     assert np.all(np.isfinite(V.cpu().numpy()))
+
+
+# ------------------------------------------------------------------ batched suspensions
+
+def _batch_inputs(sizes, trunc, seed=0):
+    Rs, ps, offs = [], [], [0]
+    for k, n in enumerate(sizes):
+        s = workloads.small_cloud(n, 200 + seed * 10 + k)
+        Rs.append(s["R"] + np.array([0.0, 0.0, 0.0]))
+        ps.append(s["p"])
+        offs.append(offs[-1] + n)
+    R = np.concatenate(Rs)
+    p = np.concatenate(ps)
+    prm_o = dict(a=1.0, eta=workloads.ETA_DEFAULT, k=0.01, vs=0.1, s0=0.05, d0=0.02)
+    inp = dynamics.trap_inputs(R, p, prm_o, trunc)
+    inp["Te"] = np.random.default_rng(seed).normal(size=(len(R), 3)) * 0.01
+    return R, inp, offs
+
+
+@pytest.mark.parametrize("trunc", [2, 3])
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_batch_solve_matches_oracle_per_system(ctx, gbi, trunc, precision):
+    """Independent suspensions of uneven size in one batched solve: each system equals
+    the oracle's dense LU solve of that system alone (spheres of different systems
+    overlap in space on purpose: they must not interact)."""
+    sizes = [1, 2, 17, 40, 33]
+    R, inp, offs = _batch_inputs(sizes, trunc)
+    prm = gbi.params(a=1.0, eta=workloads.ETA_DEFAULT, trunc=trunc, precision=precision, rtol=1e-10)
+    t = {k: dev(v) for k, v in inp.items()}
+    V, Om, QH, info, st = ctx.batch_solve(prm, offs, dev(R), t["Va"], t["Oa"], t["VH"], t["Fe"], t["Te"])
+    torch.cuda.synchronize()
+    assert st == gbi.GBI_OK and info.rel_residual <= 1e-10
+    V, Om, QH = V.cpu().numpy(), Om.cpu().numpy(), QH.cpu().numpy()
+    pairs = 0
+    for k in range(len(sizes)):
+        sl = slice(offs[k], offs[k + 1])
+        Vr, Omr, QHr = galerkin.solve(R[sl], inp["Va"][sl], inp["Oa"][sl], inp["VH"][sl], inp["Fe"][sl],
+                                      inp["Te"][sl], 1.0, workloads.ETA_DEFAULT, trunc)
+        assert relerr(V[sl], Vr) < 1e-9, k
+        assert relerr(Om[sl], Omr) < 1e-9, k
+        if sizes[k] > 1:
+            assert relerr(QH[sl], QHr) < 1e-8, k
+        pairs += sizes[k] * (sizes[k] - 1)
+    # RHS and output passes cover every system; the others only the systems still iterating
+    assert 2 * pairs <= info.pair_interactions <= (info.iters + 8) * 3 * pairs
+
+
+def test_batch_graph_replay_matches_direct(gbi):
+    """Arnoldi chunks replayed from a CUDA graph (non-default stream) give the same
+    solution as direct launches on the default stream."""
+    sizes = [30, 64, 9]
+    R, inp, offs = _batch_inputs(sizes, 2, seed=3)
+    t = {k: dev(v) for k, v in inp.items()}
+    prm = gbi.params(a=1.0, eta=workloads.ETA_DEFAULT, trunc=2, precision=2, rtol=1e-10)
+    c0 = gbi.Context(0)
+    V0, O0, Q0, i0, _ = c0.batch_solve(prm, offs, dev(R), t["Va"], t["Oa"], t["VH"], t["Fe"], t["Te"])
+    torch.cuda.synchronize()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        c1 = gbi.Context(0, stream=stream)
+        for _ in range(2):      # second call replays the cached graph
+            V1, O1, Q1, i1, _ = c1.batch_solve(prm, offs, dev(R), t["Va"], t["Oa"], t["VH"], t["Fe"], t["Te"])
+        stream.synchronize()
+    assert torch.equal(V0, V1) and torch.equal(O0, O1) and torch.equal(Q0, Q1)
+    assert i0.iters == i1.iters
+    c0.close()
+    c1.close()
+
+
+def test_batch_workload_sampled_against_single_solves(ctx, gbi):
+    """The 256-suspension workload (N log-uniform in [32, 4096]): batched solve, then a
+    few systems re-solved alone through gbi_solve (itself checked against the oracle)."""
+    c = workloads.config4()
+    systems = c["systems"]
+    offs = [0]
+    Rs, ps = [], []
+    for sy in systems:
+        Rs.append(sy["R"])
+        ps.append(sy["p"])
+        offs.append(offs[-1] + len(sy["R"]))
+    R = np.concatenate(Rs)
+    p = np.concatenate(ps)
+    prm = gbi.params(a=1.0, eta=c["eta"], trunc=2, precision=2, rtol=1e-10)
+    Rd, pd = dev(R), dev(p)
+    inp = ctx.trap_inputs(len(R), 2, c["k"], c["vs"], c["s0"], c["d0"], Rd, pd)
+    V, Om, QH, info, st = ctx.batch_solve(prm, offs, Rd, inp["Va"], inp["Oa"], inp["VH"], inp["Fe"], inp["Te"])
+    torch.cuda.synchronize()
+    assert st == gbi.GBI_OK and info.rel_residual <= 1e-10
+    for k in (0, 97, 255):
+        sl = slice(offs[k], offs[k + 1])
+        Vk, Ok, Qk, ik, sk = ctx.solve(prm, Rd[sl].contiguous(), inp["Va"][sl].contiguous(), inp["Oa"][sl].contiguous(),
+                                       inp["VH"][sl].contiguous(), inp["Fe"][sl].contiguous(),
+                                       inp["Te"][sl].contiguous())
+        torch.cuda.synchronize()
+        assert float((V[sl] - Vk).abs().max() / Vk.abs().max()) < 1e-9, k
+        assert float((Om[sl] - Ok).abs().max() / Ok.abs().max()) < 1e-8, k
