@@ -204,6 +204,28 @@ gbi_status gbi_solve_static(void* stream, const gbi_params* params, int N,
                             const double* Fe, const double* Te,
                             double* V, double* Omega, double* QH, int warm_start, gbi_info* info);
 
+/* Tuning of the pair kernel (engineering; the paper has no counterpart).  The FP32
+ * and double-float pair passes run one block per target sphere whose WPT warps split
+ * the sources; WPT in {2, 4, 8, 16} (8 at most for trunc 4 and double-float) trades
+ * parallelism at small N against per-target reduction work.
+ * gbi_tune times every WPT for the four passes of a mixed-precision solve -- rows H /
+ * columns H in FP32 and in double-float, H/L and L/all in double-float -- on synthetic
+ * input of the given layout: nsys systems, system s holding spheres
+ * [offsets[s], offsets[s+1]) (host array of nsys + 1 increasing ints, offsets[0] = 0;
+ * nsys = 1 describes one suspension, nsys > 1 a gbi_batch_solve batch).  Spheres sit
+ * on a cubic lattice of spacing 3a; each candidate runs once to warm up and then reps
+ * times (reps = 0 selects 5) between CUDA events on the context's stream.  The fastest
+ * WPT is kept in the context for every later pass of the same truncation, pass,
+ * precision, batching and floor(log2(total spheres)).  chosen (host, may be NULL)
+ * receives the 4 choices in the order above.  Allocates and frees its own device
+ * buffers and synchronizes the stream (not capturable).
+ * gbi_set_wpt forces one WPT for every later pass (0 = back to tuned/default).
+ * gbi_pass_wpt returns the WPT a pass with these parameters would use (0 for the
+ * FP64 tiled pass, -1 for invalid arguments). */
+gbi_status gbi_tune(gbi_ctx* ctx, int trunc, int nsys, const int* offsets, int reps, int* chosen);
+gbi_status gbi_set_wpt(gbi_ctx* ctx, int wpt);
+int gbi_pass_wpt(gbi_ctx* ctx, int trunc, int rows, int cols, int precision, int N, int batched);
+
 /* Instrumentation.  gbi_kernel_launches: number of CUDA kernels this context has
  * launched since creation.  gbi_set_profiling(ctx, 1) resets the per-class
  * statistics and from then on records a CUDA event pair on the context's stream

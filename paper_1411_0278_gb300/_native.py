@@ -66,6 +66,9 @@ _SIGS = {
     "gbi_batch_solve": (_I, [_VP, ctypes.POINTER(gbi_params), _I, ctypes.POINTER(ctypes.c_int)] + [_VP] * 9 +
                         [_I, ctypes.POINTER(gbi_info)]),
     "gbi_solve_static": (_I, [_VP, ctypes.POINTER(gbi_params), _I] + [_VP] * 9 + [_I, ctypes.POINTER(gbi_info)]),
+    "gbi_tune": (_I, [_VP, _I, _I, ctypes.POINTER(ctypes.c_int), _I, ctypes.POINTER(ctypes.c_int)]),
+    "gbi_set_wpt": (_I, [_VP, _I]),
+    "gbi_pass_wpt": (_I, [_VP, _I, _I, _I, _I, _I, _I]),
     "gbi_kernel_launches": (ctypes.c_longlong, [_VP]),
     "gbi_set_profiling": (_I, [_VP, _I]),
     "gbi_kernel_stats": (_I, [_VP, _I, c_double_p, ctypes.POINTER(ctypes.c_longlong), c_double_p]),
@@ -264,6 +267,20 @@ class Context:
                     "gbi_trap_inputs")
         Fe, Te, Va, Oa = out
         return dict(Fe=Fe, Te=Te, Va=Va, Oa=Oa, VH=VH)
+
+    def tune(self, trunc, offsets, reps=0):
+        """gbi_tune: time each warps-per-target choice of the pair passes on synthetic
+        input with the sphere layout ``offsets`` (nsys + 1 ints); returns the 4 choices."""
+        off = (ctypes.c_int * len(offsets))(*[int(v) for v in offsets])
+        out = (ctypes.c_int * 4)()
+        self._check(lib().gbi_tune(self._h, int(trunc), len(offsets) - 1, off, int(reps), out), "gbi_tune")
+        return list(out)
+
+    def set_wpt(self, wpt):
+        self._check(lib().gbi_set_wpt(self._h, int(wpt)), "gbi_set_wpt")
+
+    def pass_wpt(self, trunc, rows, cols, precision, N, batched=False):
+        return lib().gbi_pass_wpt(self._h, int(trunc), int(rows), int(cols), int(precision), int(N), int(batched))
 
     def kernel_launches(self):
         return int(lib().gbi_kernel_launches(self._h))

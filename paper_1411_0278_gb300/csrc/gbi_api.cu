@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -88,6 +89,18 @@ struct gbi_ctx {
   double stat_flops[30] = {0};
   long long stat_n[30] = {0};
   long long stat_dead[30] = {0};
+  // warps per target chosen by gbi_tune, keyed by pass, precision, log2(N), batching
+  std::map<long long, int> wpt_table;
+  int force_wpt = 0;                           // gbi_set_wpt override (0: table or default)
+  static long long wpt_key(int trunc, int rows, int cols, int precision, int N, bool batched) {
+    int lg = 0;
+    while (lg < 40 && (2LL << lg) <= N) ++lg;
+    return ((((long long)(trunc * 3 + rows) * 3 + cols) * 3 + precision) * 64 + lg) * 2 + (batched ? 1 : 0);
+  }
+  int tuned_wpt(int trunc, int rows, int cols, int precision, int N, bool batched) const {
+    const auto it = wpt_table.find(wpt_key(trunc, rows, cols, precision, N, batched));
+    return it == wpt_table.end() ? 0 : it->second;
+  }
 };
 
 namespace {
@@ -178,27 +191,48 @@ struct ColScale {
   double v[54];
 };
 
-// y = float(x * cs[component]) for a component-major [nc][N] block (x optionally
-// device-indexed, skipped when the device-side solver has stopped)
-__global__ void k_to_f32_s(size_t n, int N, const double* __restrict__ x, const int* xi, size_t xs,
-                           const int* active, ColScale cs, float* __restrict__ y) {
+// Source records of the FP32 / double-float passes (see PairArgs::x32): from the
+// component-major [nc][N] block x (optionally device-indexed; skipped when the
+// device-side solver has stopped), rec[m] = float(x[.][m] * cs) padded with zeros to
+// ncp floats (double-float: then the lo block).  One block per 32 spheres, transposed
+// through shared memory so that both the reads and the writes are coalesced.
+template <bool DFL>
+__global__ void k_records(int N, int nc, int ncp, const double* __restrict__ x, const int* xi, size_t xs,
+                          const int* active, ColScale cs, float* __restrict__ rec) {
+  extern __shared__ float tile[];   // [32][rf + 1]
   if (active != nullptr && *active == 0) return;
   if (xi != nullptr) x += (size_t)(*xi) * xs;
-  const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (i < n) y[i] = float(x[i] * cs.v[i / N]);
+  const int rf = DFL ? 2 * ncp : ncp;
+  const int m0 = blockIdx.x * 32;
+  const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int m = m0 + lane;
+  for (int q = wy; q < ncp; q += nw) {
+    float h = 0.f, l = 0.f;
+    if (q < nc && m < N) {
+      const double v = x[(size_t)q * N + m] * cs.v[q];
+      h = float(v);
+      l = float(v - double(h));
+    }
+    tile[lane * (rf + 1) + q] = h;
+    if (DFL) tile[lane * (rf + 1) + ncp + q] = l;
+  }
+  __syncthreads();
+  const int cnt = min(32, N - m0);
+  for (int i = threadIdx.x; i < cnt * rf; i += blockDim.x) {
+    const int r = i / rf, c = i - r * rf;
+    rec[(size_t)(m0 + r) * rf + c] = tile[r * (rf + 1) + c];
+  }
 }
 
-__global__ void k_to_df_s(size_t n, int N, const double* __restrict__ x, const int* xi, size_t xs,
-                          const int* active, ColScale cs, float* __restrict__ hi, float* __restrict__ lo) {
-  if (active != nullptr && *active == 0) return;
-  if (xi != nullptr) x += (size_t)(*xi) * xs;
-  const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (i < n) {
-    const double v = x[i] * cs.v[i / N];
-    const float h = float(v);
-    hi[i] = h;
-    lo[i] = float(v - double(h));
-  }
+cudaError_t launch_records(bool dfl, int N, int nc, const double* x, const int* xi, size_t xs, const int* active,
+                           const ColScale& cs, float* rec, cudaStream_t stream) {
+  const int ncp = (nc + 3) & ~3;
+  const int rf = dfl ? 2 * ncp : ncp;
+  const size_t smem = sizeof(float) * 32 * (rf + 1);
+  const dim3 grid((N + 31) / 32), block(256);
+  if (dfl) k_records<true><<<grid, block, smem, stream>>>(N, nc, ncp, x, xi, xs, active, cs, rec);
+  else k_records<false><<<grid, block, smem, stream>>>(N, nc, ncp, x, xi, xs, active, cs, rec);
+  return cudaGetLastError();
 }
 
 int ncols_of(int trunc, int cols) {
@@ -210,32 +244,21 @@ cudaError_t run_pairs(gbi_ctx* ctx, int trunc, int rows, int cols, int precision
   const double flops = pair_flops(trunc, rows, cols) * double(args_in.N) * double(args_in.N - 1);
   PairArgs args = args_in;
   int extra = 0;
-  if (precision == 2) {
-    // double-float sources: hi = float(x * cs), lo = float(x * cs - hi), once per pass
+  if (args.wpt == 0)
+    args.wpt = ctx->force_wpt > 0 ? ctx->force_wpt
+                                  : ctx->tuned_wpt(trunc, rows, cols, precision, args.N, args.sys_of != nullptr);
+  if (precision == 2 || (precision == 1 && args.x32 == nullptr)) {
+    // per-sphere source records (FP32, or the double-float hi/lo pair), once per pass,
+    // so that the pair loop touches no FP64
     const int nc = ncols_of(trunc, cols);
-    const size_t n = (size_t)nc * args.N;
-    if (ensure(ctx, ctx->x32, 2 * sizeof(float) * n) != GBI_OK) return cudaErrorMemoryAllocation;
+    const size_t bytes = sizeof(float) * rec_floats(nc, precision == 2) * (size_t)args.N;
+    if (ensure(ctx, ctx->x32, bytes) != GBI_OK) return cudaErrorMemoryAllocation;
     ColScale cs;
     const int c0 = cols == SET_H ? 6 : 0;
     for (int i = 0; i < 54; ++i) cs.v[i] = (i < nc) ? args.colscale[c0 + i] : 1.0;
-    k_to_df_s<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(n, args.N, args.x, args.x_index,
-                                                                     args.x_stride, args.active, cs,
-                                                                     P<float>(ctx->x32), P<float>(ctx->x32) + n);
-    args.x32 = P<float>(ctx->x32);
-    args.x32lo = P<float>(ctx->x32) + n;
-    extra = 1;
-  }
-  if (precision == 1 && args.x32 == nullptr) {
-    // FP32 sources: scale and round once per pass, so the pair loop touches no FP64
-    const int nc = ncols_of(trunc, cols);
-    const size_t n = (size_t)nc * args.N;
-    if (ensure(ctx, ctx->x32, sizeof(float) * n) != GBI_OK) return cudaErrorMemoryAllocation;
-    ColScale cs;
-    const int c0 = cols == SET_H ? 6 : 0;
-    for (int i = 0; i < 54; ++i) cs.v[i] = (i < nc) ? args.colscale[c0 + i] : 1.0;
-    k_to_f32_s<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(n, args.N, args.x, args.x_index,
-                                                                      args.x_stride, args.active, cs,
-                                                                      P<float>(ctx->x32));
+    const cudaError_t e = launch_records(precision == 2, args.N, nc, args.x, args.x_index, args.x_stride,
+                                         args.active, cs, P<float>(ctx->x32), ctx->stream);
+    if (e != cudaSuccess) return e;
     args.x32 = P<float>(ctx->x32);
     extra = 1;
   }
@@ -412,6 +435,7 @@ PairArgs pair_args(const Setup& s, const double* x, double* y, double alpha, dou
   p.x = x;
   p.x32 = nullptr;
   p.x32lo = nullptr;
+  p.wpt = 0;
   p.y = y;
   p.alpha = alpha;
   p.beta = beta;
@@ -496,7 +520,30 @@ GPtr gptrs(void* base, int m, int S) {
   return p;
 }
 
-// out (FP64 or FP32) = V_{j_s} * minv over the spheres of active systems (the Arnoldi source)
+// FP32 Arnoldi source as per-sphere records (PairArgs::x32): rec[p] = float(V_{j_s} *
+// minv) padded to ncp floats, for the spheres of active systems; transposed through
+// shared memory (one block per 32 spheres) so that reads and writes are coalesced.
+__global__ void bk_gather_rec(const double* __restrict__ V, size_t n, int Ntot, int h, int ncp,
+                              const int* __restrict__ sys, const GDev* __restrict__ st, Scales minv,
+                              float* __restrict__ rec) {
+  extern __shared__ float tile[];   // [32][ncp + 1]
+  const int m0 = blockIdx.x * 32;
+  const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int p = m0 + lane;
+  const GDev* g = p < Ntot ? &st[sys[p]] : nullptr;
+  const bool live = g != nullptr && g->active;
+  const double* v = live ? V + (size_t)g->j * n : nullptr;
+  for (int q = wy; q < ncp; q += nw)
+    tile[lane * (ncp + 1) + q] = (live && q < h) ? float(v[(size_t)q * Ntot + p] * minv.v[q]) : 0.f;
+  __syncthreads();
+  const int cnt = min(32, Ntot - m0);
+  for (int i = threadIdx.x; i < cnt * ncp; i += blockDim.x) {
+    const int r = i / ncp, c = i - r * ncp;
+    rec[(size_t)(m0 + r) * ncp + c] = tile[r * (ncp + 1) + c];
+  }
+}
+
+// out (FP64) = V_{j_s} * minv over the spheres of active systems (the Arnoldi source)
 template <typename O>
 __global__ void bk_gather(const double* __restrict__ V, size_t n, int Ntot, const int* __restrict__ sys,
                           const GDev* __restrict__ st, Scales minv, O* __restrict__ out) {
@@ -746,13 +793,15 @@ gbi_status launch_chunk(gbi_ctx* ctx, const Setup& s, const Batch& B, int precis
   PairArgs pa = pair_args(s, precision == 1 ? nullptr : static_cast<const double*>(xsrc), w, 1.0, 0.0, 1, s.ones,
                           6);
   if (precision == 1) pa.x32 = static_cast<const float*>(xsrc);
+  const int ncp = (h + 3) & ~3;
   pa.sys_of = B.sys;
   pa.sys_off = B.off;
   pa.sys_flag = &gp.st[0].active;
   pa.sys_flag_stride = int(sizeof(GDev) / sizeof(int));
   for (int c = 0; c < kChunk; ++c) {
     if (precision == 1)
-      bk_gather<float><<<g2, 256, 0, ctx->stream>>>(Vb, n, Ntot, B.sys, gp.st, s.minv, static_cast<float*>(xsrc));
+      bk_gather_rec<<<(Ntot + 31) / 32, 256, sizeof(float) * 32 * (ncp + 1), ctx->stream>>>(
+          Vb, n, Ntot, h, ncp, B.sys, gp.st, s.minv, static_cast<float*>(xsrc));
     else
       bk_gather<double><<<g2, 256, 0, ctx->stream>>>(Vb, n, Ntot, B.sys, gp.st, s.minv, static_cast<double*>(xsrc));
     GBI_CHECK(run_pairs(ctx, s.trunc, SET_H, SET_H, precision, pa));
@@ -791,7 +840,8 @@ gbi_status gmres_batch(gbi_ctx* ctx, const Setup& s, const Batch& B, int precisi
   GBI_TRY(ensure(ctx, ctx->krylov, sizeof(double) * n * (m + 1)));
   GBI_TRY(ensure(ctx, ctx->w, sizeof(double) * n));
   GBI_TRY(ensure(ctx, ctx->gstate, sizeof(double) * gstate_doubles(m, S)));
-  GBI_TRY(ensure(ctx, ctx->x32, sizeof(double) * n));     // gathered Arnoldi source (float or double)
+  // gathered Arnoldi source: FP64 component-major, or FP32 records of round4(h) floats
+  GBI_TRY(ensure(ctx, ctx->x32, std::max(sizeof(double) * n, sizeof(float) * (size_t)Ntot * ((h + 3) & ~3))));
   double* Vb = P<double>(ctx->krylov);
   double* w = P<double>(ctx->w);
   void* xsrc = ctx->x32.p;
@@ -1126,6 +1176,121 @@ __global__ void k_fill_sys(int S, const int* __restrict__ off, int* sys) {
   for (int p = off[s] + threadIdx.x; p < off[s + 1]; p += blockDim.x) sys[p] = s;
 }
 
+// ---------------------------------------------------------------------------------
+// Tuning of the pair kernel's warps per target
+// ---------------------------------------------------------------------------------
+
+// Synthetic timing input: sphere i of system s sits at lattice point i - off[s] of a
+// cube of side ceil(cbrt(N_s)) with spacing 3a (so no pair is closer than 3a), and
+// every source component is 1e-3.  The pair kernel's work does not depend on values.
+__global__ void k_tune_fill(int Ntot, int nsys, const int* __restrict__ off, int* __restrict__ sys_of, double a,
+                            float4* __restrict__ hi, float4* __restrict__ lo, double* __restrict__ x, int D) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= Ntot) return;
+  int lo_s = 0, hi_s = nsys - 1;
+  while (lo_s < hi_s) {            // last system with off[s] <= i
+    const int mid = (lo_s + hi_s + 1) / 2;
+    if (off[mid] <= i) lo_s = mid; else hi_s = mid - 1;
+  }
+  const int s = lo_s;
+  sys_of[i] = s;
+  const int k = i - off[s], ns = off[s + 1] - off[s];
+  int side = 1;
+  while (side * side * side < ns) ++side;
+  const float sp = float(3.0 * a);
+  hi[i] = make_float4(sp * float(k % side), sp * float((k / side) % side), sp * float(k / (side * side)), 0.f);
+  lo[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int q = 0; q < D; ++q) x[(size_t)q * Ntot + i] = 1e-3;
+}
+
+struct TuneBufs {
+  void* p[7] = {};
+  ~TuneBufs() {
+    for (void* q : p)
+      if (q) cudaFree(q);
+  }
+};
+
+gbi_status tune_impl(gbi_ctx* ctx, int trunc, int nsys, const int* offsets, int reps, int* chosen) {
+  const int D = d_of(trunc);
+  const int Ntot = offsets[nsys];
+  const bool batched = nsys > 1;
+  TuneBufs tb;
+  const int rf_max = rec_floats(D, true);
+  GBI_CHECK(cudaMalloc(&tb.p[0], sizeof(float4) * Ntot));
+  GBI_CHECK(cudaMalloc(&tb.p[1], sizeof(float4) * Ntot));
+  GBI_CHECK(cudaMalloc(&tb.p[2], sizeof(double) * D * (size_t)Ntot));
+  GBI_CHECK(cudaMalloc(&tb.p[3], sizeof(double) * D * (size_t)Ntot));
+  GBI_CHECK(cudaMalloc(&tb.p[4], sizeof(float) * rf_max * (size_t)Ntot));
+  GBI_CHECK(cudaMalloc(&tb.p[5], sizeof(int) * (size_t)Ntot));
+  GBI_CHECK(cudaMalloc(&tb.p[6], sizeof(int) * (size_t)(nsys + 1)));
+  float4* hi = static_cast<float4*>(tb.p[0]);
+  float4* lo = static_cast<float4*>(tb.p[1]);
+  double* x = static_cast<double*>(tb.p[2]);
+  double* y = static_cast<double*>(tb.p[3]);
+  float* rec = static_cast<float*>(tb.p[4]);
+  int* sys_of = static_cast<int*>(tb.p[5]);
+  int* sys_off = static_cast<int*>(tb.p[6]);
+  GBI_CHECK(cudaMemcpyAsync(sys_off, offsets, sizeof(int) * (nsys + 1), cudaMemcpyHostToDevice, ctx->stream));
+  k_tune_fill<<<(Ntot + 255) / 256, 256, 0, ctx->stream>>>(Ntot, nsys, sys_off, sys_of, 1.0, hi, lo, x, D);
+  GBI_CHECK(cudaGetLastError());
+  ++ctx->launches;
+  cudaEvent_t e0 = take_event(ctx), e1 = take_event(ctx);
+  struct Pass {
+    int rows, cols, precision;
+  };
+  const Pass passes[4] = {{SET_H, SET_H, 1}, {SET_H, SET_H, 2}, {SET_H, SET_L, 2}, {SET_L, SET_ALL, 2}};
+  gbi_status st = GBI_OK;
+  for (int k = 0; k < 4 && st == GBI_OK; ++k) {
+    const Pass& ps = passes[k];
+    PairArgs pa;
+    std::memset(&pa, 0, sizeof(pa));
+    pa.N = Ntot;
+    pa.a = 1.0;
+    pa.pos = Positions{hi, lo, nullptr};
+    pa.x = x;
+    pa.y = y;
+    pa.alpha = 1.0;
+    for (int i = 0; i < 54; ++i) pa.colscale[i] = 1.0;
+    if (batched) {
+      pa.sys_of = sys_of;
+      pa.sys_off = sys_off;
+    }
+    const int nc = ncols_of(trunc, ps.cols);
+    ColScale cs;
+    for (int i = 0; i < 54; ++i) cs.v[i] = 1.0;
+    cudaError_t e = launch_records(ps.precision == 2, Ntot, nc, x, nullptr, 0, nullptr, cs, rec, ctx->stream);
+    pa.x32 = rec;
+    int best = 0;
+    float best_ms = 0.f;
+    for (int w = 2; w <= max_wpt(trunc, ps.precision) && e == cudaSuccess; w *= 2) {
+      pa.wpt = w;
+      e = launch_pairs(trunc, ps.rows, ps.cols, ps.precision, pa, ctx->stream);   // warm-up
+      if (e == cudaSuccess) e = cudaEventRecord(e0, ctx->stream);
+      for (int r = 0; r < reps && e == cudaSuccess; ++r)
+        e = launch_pairs(trunc, ps.rows, ps.cols, ps.precision, pa, ctx->stream);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, ctx->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      ctx->launches += 1 + reps;
+      if (e == cudaSuccess && (best == 0 || ms < best_ms)) {
+        best = w;
+        best_ms = ms;
+      }
+    }
+    if (e != cudaSuccess) {
+      st = fail(ctx, e, "gbi_tune");
+      break;
+    }
+    ctx->wpt_table[gbi_ctx::wpt_key(trunc, ps.rows, ps.cols, ps.precision, Ntot, batched)] = best;
+    if (chosen) chosen[k] = best;
+  }
+  ctx->pool.push_back(e0);
+  ctx->pool.push_back(e1);
+  return st;
+}
+
 }  // namespace
 
 // =================================================================================
@@ -1383,6 +1548,29 @@ gbi_status gbi_trap_inputs(gbi_ctx* ctx, int N, int trunc, double k_trap, double
   return GBI_OK;
 }
 
+gbi_status gbi_tune(gbi_ctx* ctx, int trunc, int nsys, const int* offsets, int reps, int* chosen) {
+  if (!ctx || d_of(trunc) < 0 || nsys < 1 || !offsets || reps < 0) return GBI_ERR_ARG;
+  if (offsets[0] != 0) return GBI_ERR_ARG;
+  for (int s = 0; s < nsys; ++s)
+    if (offsets[s + 1] <= offsets[s]) return GBI_ERR_ARG;
+  if (reps == 0) reps = 5;
+  return tune_impl(ctx, trunc, nsys, offsets, reps, chosen);
+}
+
+gbi_status gbi_set_wpt(gbi_ctx* ctx, int wpt) {
+  if (!ctx || !(wpt == 0 || wpt == 2 || wpt == 4 || wpt == 8 || wpt == 16)) return GBI_ERR_ARG;
+  ctx->force_wpt = wpt;
+  return GBI_OK;
+}
+
+int gbi_pass_wpt(gbi_ctx* ctx, int trunc, int rows, int cols, int precision, int N, int batched) {
+  if (!ctx || d_of(trunc) < 0 || rows < 0 || rows > 2 || cols < 0 || cols > 2 || N < 1) return -1;
+  if (precision == 0) return 0;
+  if (precision != 1 && precision != 2) return -1;
+  const int req = ctx->force_wpt > 0 ? ctx->force_wpt : ctx->tuned_wpt(trunc, rows, cols, precision, N, batched != 0);
+  return stream_wpt(trunc, precision, N, req);
+}
+
 gbi_status gbi_set_profiling(gbi_ctx* ctx, int on) {
   if (!ctx) return GBI_ERR_ARG;
   drain_profile(ctx);
@@ -1477,7 +1665,7 @@ constexpr size_t kOffPart = kOffW + al256(sizeof(double) * kStaticMaxNH);
 constexpr size_t kOffDots = kOffPart + al256(sizeof(double) * 64 * (kMaxRestart + 2));
 constexpr size_t kOffMin = kOffDots + al256(sizeof(double) * (2 * kMaxRestart + 8));
 constexpr size_t kOffX32 = kOffMin + 256;
-constexpr size_t kOffGs = kOffX32 + al256(sizeof(float) * 2 * kStaticMaxND);
+constexpr size_t kOffGs = kOffX32 + al256(sizeof(float) * 2 * (kStaticMaxND + 3 * kStaticMaxN));
 constexpr size_t kOffBoff = kOffGs + al256(sizeof(double) * (64 + (kStaticMaxRestart + 1) * kStaticMaxRestart +
                                                               8 * (kStaticMaxRestart + 1)));
 constexpr size_t kOffBsys = kOffBoff + 256;

@@ -33,9 +33,12 @@ struct PairArgs {
   double a;
   Positions pos;
   const double* x;       // component-major, first component of the column set
-  const float* x32;      // FP32 kernels: x pre-scaled by colscale and rounded (may be null);
-                         // double-float kernels: the hi part of the same
-  const float* x32lo;    // double-float kernels: the lo part (x * colscale - hi)
+  // FP32 and double-float passes read x as per-sphere source records: sphere m owns
+  // rec_floats(NC, df) floats at x32 + m * rec_floats, holding float(x * colscale)
+  // padded to a multiple of 4 (double-float: that hi block, then the lo block
+  // float(x * colscale - hi)).  The FP64 pass reads x itself.
+  const float* x32;
+  const float* x32lo;    // unused (kept zero)
   double* y;             // component-major, first component of the row set
   double alpha, beta;
   int add_self;
@@ -54,7 +57,25 @@ struct PairArgs {
   const int* sys_off;
   const int* sys_flag;
   int sys_flag_stride;
+  int wpt;               // warps per target of the FP32 / double-float kernel (0: default)
 };
+
+// Floats per source record of a pass reading NC columns (see PairArgs::x32).
+inline int rec_floats(int nc, bool df) { return ((nc + 3) & ~3) * (df ? 2 : 1); }
+
+// Largest warps-per-target of the FP32 / double-float pair kernel: a 512-thread block
+// would cap the heavier forms (l <= 4, double-float) at 128 registers and spill.
+inline int max_wpt(int trunc, int precision) { return (trunc == 4 || precision == 2) ? 8 : 16; }
+
+// Warps per target of the FP32 / double-float pair kernel: the requested value (2, 4,
+// 8 or 16), else enough warps to cover 152 SMs at small N and fewer (less reduction
+// work per target) once the N targets alone fill the GPU; capped by max_wpt.
+inline int stream_wpt(int trunc, int precision, int N, int requested) {
+  const int d = N >= 8192 ? 2 : (N >= 4096 ? 4 : (N >= 1024 ? 8 : 16));
+  const int w = requested > 0 ? requested : d;
+  const int cap = max_wpt(trunc, precision);
+  return w < cap ? w : cap;
+}
 
 // Launch the generic single-layer pair operator; returns a CUDA error code.
 cudaError_t launch_pairs(int trunc, int rows, int cols, int precision, const PairArgs& args,

@@ -211,11 +211,14 @@ __host__ __device__ __forceinline__ void pair_body(T dx, T dy, T dz, T a, const 
   from_pair_frame<TR, T, S::MR0, S::MR1, S::R0>(yy, acc, cm, sm, dm, ep);
 }
 
-// Block = TPB target spheres x WPT warps per target.  The WPT warps of a target split
-// its sources (lane-strided within each shared-memory tile); their partial sums are
-// combined in shared memory in a fixed order, so results are deterministic.
+// FP64 form.  Block = TPB target spheres x WPT warps per target; sources are staged in
+// shared-memory tiles.  The WPT warps of a target split its sources (lane-strided
+// within each tile); their partial sums are combined in shared memory in a fixed order,
+// so results are deterministic.  The FP64 pipe (1/64 of the FP32 rate) bounds this
+// pass, so the tile bookkeeping is not what limits it.
 template <int TR, int ROWS, int COLS, typename T, int TPB, int WPT, int TILE>
 __global__ void __launch_bounds__(TPB * WPT * 32) pair_kernel(const PairArgs args) {
+  static_assert(std::is_same<T, double>::value, "the tiled pass is the FP64 one");
   using S = PassShape<TR, ROWS, COLS>;
   constexpr int D = S::D;
   constexpr int R0 = S::R0;
@@ -223,15 +226,10 @@ __global__ void __launch_bounds__(TPB * WPT * 32) pair_kernel(const PairArgs arg
   constexpr int C1 = S::C1;
   constexpr int NR = S::NR;
   constexpr int NC = S::NC;
-  constexpr bool F32 = std::is_same<T, float>::value;
-  constexpr bool DF = std::is_same<T, df>::value;
-  constexpr bool SPLIT = F32 || DF;            // centres as two floats (hi, lo)
-  constexpr int POSW = SPLIT ? 6 : 3;
   constexpr int THREADS = TPB * WPT * 32;
-  using PT = typename std::conditional<SPLIT, float, double>::type;
 
-  __shared__ PT s_pos[POSW][TILE];
-  __shared__ T s_x[NC][TILE];
+  __shared__ double s_pos[3][TILE];
+  __shared__ double s_x[NC][TILE];
 
   if (args.active != nullptr && *args.active == 0) return;   // device-side GMRES has stopped
   const double* __restrict__ xsrc = args.x_index ? args.x + (size_t)(*args.x_index) * args.x_stride : args.x;
@@ -251,7 +249,7 @@ __global__ void __launch_bounds__(TPB * WPT * 32) pair_kernel(const PairArgs arg
     if (args.sys_flag != nullptr && args.sys_flag[(size_t)sy * args.sys_flag_stride] == 0) active = false;
   }
   // the block's tile range: union of its targets' ranges
-  int blk_lo = active ? src_lo : N, blk_hi = active ? src_hi : 0;
+  int blk_lo = 0, blk_hi = N;
   if (args.sys_of != nullptr) {
     __shared__ int s_rng[2];
     if (threadIdx.x == 0) { s_rng[0] = N; s_rng[1] = 0; }
@@ -263,89 +261,46 @@ __global__ void __launch_bounds__(TPB * WPT * 32) pair_kernel(const PairArgs arg
     __syncthreads();
     blk_lo = s_rng[0];
     blk_hi = s_rng[1];
-  } else {
-    blk_lo = 0;
-    blk_hi = N;
   }
-  const T a = T(args.a);
+  const double a = args.a;
 
-  PT tp[POSW];
+  double tp[3] = {0.0, 0.0, 0.0};
   if (active) {
-    if constexpr (SPLIT) {
-      const float4 h = args.pos.hi[n], lo = args.pos.lo[n];
-      tp[0] = h.x; tp[1] = h.y; tp[2] = h.z; tp[3] = lo.x; tp[4] = lo.y; tp[5] = lo.z;
-    } else {
-      const dpos4 p = args.pos.p64[n];
-      tp[0] = p.x; tp[1] = p.y; tp[2] = p.z;
-    }
-  } else {
-#pragma unroll
-    for (int i = 0; i < POSW; ++i) tp[i] = PT(0);
+    const dpos4 p = args.pos.p64[n];
+    tp[0] = p.x; tp[1] = p.y; tp[2] = p.z;
   }
 
-  T acc[NR];
+  double acc[NR];
 #pragma unroll
-  for (int p = 0; p < NR; ++p) acc[p] = T(0);
+  for (int p = 0; p < NR; ++p) acc[p] = 0.0;
   float min_r2 = 3.0e38f;
 
   for (int base = blk_lo; base < blk_hi; base += TILE) {
     const int len = min(TILE, blk_hi - base);
     __syncthreads();
     for (int idx = threadIdx.x; idx < len; idx += THREADS) {
-      const int m = base + idx;
-      if constexpr (SPLIT) {
-        const float4 h = args.pos.hi[m], lo = args.pos.lo[m];
-        s_pos[0][idx] = h.x; s_pos[1][idx] = h.y; s_pos[2][idx] = h.z;
-        s_pos[3][idx] = lo.x; s_pos[4][idx] = lo.y; s_pos[5][idx] = lo.z;
-      } else {
-        const dpos4 p = args.pos.p64[m];
-        s_pos[0][idx] = p.x; s_pos[1][idx] = p.y; s_pos[2][idx] = p.z;
-      }
+      const dpos4 p = args.pos.p64[base + idx];
+      s_pos[0][idx] = p.x; s_pos[1][idx] = p.y; s_pos[2][idx] = p.z;
     }
     // source coefficients: component-major rows, no integer division in the loop
-    if constexpr (DF) {
-      for (int q = 0; q < NC; ++q) {
-        const float* hi = args.x32 + (size_t)q * N + base;
-        const float* lo = args.x32lo + (size_t)q * N + base;
-        for (int j = threadIdx.x; j < len; j += THREADS) s_x[q][j] = df(hi[j], lo[j]);
-      }
-    } else if (F32 && args.x32 != nullptr) {
-      for (int q = 0; q < NC; ++q) {
-        const float* src = args.x32 + (size_t)q * N + base;
-        for (int j = threadIdx.x; j < len; j += THREADS) s_x[q][j] = T(src[j]);
-      }
-    } else {
-      for (int q = 0; q < NC; ++q) {
-        const double* src = xsrc + (size_t)q * N + base;
-        const double cs = args.colscale[C0 + q];
-        for (int j = threadIdx.x; j < len; j += THREADS) s_x[q][j] = T(src[j] * cs);
-      }
+    for (int q = 0; q < NC; ++q) {
+      const double* src = xsrc + (size_t)q * N + base;
+      const double cs = args.colscale[C0 + q];
+      for (int j = threadIdx.x; j < len; j += THREADS) s_x[q][j] = src[j] * cs;
     }
     __syncthreads();
     if (active) {
       for (int j = sub * 32 + lane; j < len; j += WPT * 32) {
         const int m = base + j;
         if (m == n || m < src_lo || m >= src_hi) continue;
-        T dx, dy, dz;
-        if constexpr (DF) {
-          // exact difference of the hi parts, plus the (tiny) difference of the lo parts
-          dx = df_two_sum(tp[0], -s_pos[0][j]) + df(tp[3] - s_pos[3][j], 0.f);
-          dy = df_two_sum(tp[1], -s_pos[1][j]) + df(tp[4] - s_pos[4][j], 0.f);
-          dz = df_two_sum(tp[2], -s_pos[2][j]) + df(tp[5] - s_pos[5][j], 0.f);
-        } else if constexpr (F32) {
-          dx = (tp[0] - s_pos[0][j]) + (tp[3] - s_pos[3][j]);
-          dy = (tp[1] - s_pos[1][j]) + (tp[4] - s_pos[4][j]);
-          dz = (tp[2] - s_pos[2][j]) + (tp[5] - s_pos[5][j]);
-        } else {
-          dx = tp[0] - s_pos[0][j];
-          dy = tp[1] - s_pos[1][j];
-          dz = tp[2] - s_pos[2][j];
-        }
+        const double dx = tp[0] - s_pos[0][j];
+        const double dy = tp[1] - s_pos[1][j];
+        const double dz = tp[2] - s_pos[2][j];
         min_r2 = fminf(min_r2, float(dx * dx + dy * dy + dz * dz));
-        T xl[D];
+        double xl[D];
 #pragma unroll
         for (int q = C0; q < C1; ++q) xl[q] = s_x[q - C0][j];
-        pair_body<TR, ROWS, COLS, T>(dx, dy, dz, a, xl, acc);
+        pair_body<TR, ROWS, COLS, double>(dx, dy, dz, a, xl, acc);
       }
     }
   }
@@ -353,7 +308,7 @@ __global__ void __launch_bounds__(TPB * WPT * 32) pair_kernel(const PairArgs arg
   // warp reduction of the partial sums (fixed order: deterministic)
 #pragma unroll
   for (int p = 0; p < NR; ++p) {
-    T v = acc[p];
+    double v = acc[p];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += gbi_shfl(v, o);
     acc[p] = v;
@@ -366,8 +321,8 @@ __global__ void __launch_bounds__(TPB * WPT * 32) pair_kernel(const PairArgs arg
   if constexpr (WPT > 1) {
     // combine the WPT warps of each target through shared memory (reuses the tile)
     __syncthreads();
-    T* red = &s_x[0][0];
-    static_assert(sizeof(s_x) >= sizeof(T) * TPB * WPT * NR || NR == 0, "reduction buffer too small");
+    double* red = &s_x[0][0];
+    static_assert(sizeof(s_x) >= sizeof(double) * TPB * WPT * NR || NR == 0, "reduction buffer too small");
     if (lane == 0) {
 #pragma unroll
       for (int p = 0; p < NR; ++p) red[(tgt * WPT + sub) * NR + p] = acc[p];
@@ -376,7 +331,7 @@ __global__ void __launch_bounds__(TPB * WPT * 32) pair_kernel(const PairArgs arg
     if (sub == 0 && lane == 0) {
 #pragma unroll
       for (int p = 0; p < NR; ++p) {
-        T v = red[(tgt * WPT) * NR + p];
+        double v = red[(tgt * WPT) * NR + p];
         for (int w = 1; w < WPT; ++w) v += red[(tgt * WPT + w) * NR + p];
         acc[p] = v;
       }
@@ -386,16 +341,164 @@ __global__ void __launch_bounds__(TPB * WPT * 32) pair_kernel(const PairArgs arg
     const double inva = 1.0 / args.a;
 #pragma unroll
     for (int p = 0; p < NR; ++p) {
-      double v = gbi_to_double(acc[p]) * inva;
-      if (args.add_self) {
-        const size_t k = (size_t)(R0 - C0 + p) * N + n;
-        // FP32 passes read the pre-scaled single-precision source; the others the FP64 one
-        const double xs = (F32 && args.x32 != nullptr) ? double(args.x32[k]) : xsrc[k] * args.colscale[R0 + p];
-        v += args.selfg[R0 + p] * inva * xs;
-      }
+      double v = acc[p] * inva;
+      if (args.add_self) v += args.selfg[R0 + p] * inva * xsrc[(size_t)(R0 - C0 + p) * N + n] * args.colscale[R0 + p];
       double* dst = args.y + (size_t)p * N + n;
       *dst = args.alpha * v + (args.beta != 0.0 ? args.beta * (*dst) : 0.0);
     }
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// Streaming form for the FP32 and double-float passes.
+//
+// Source m is one record: NCP = NC rounded up to a multiple of 4 floats holding
+// float(x_m * colscale) (double-float: the hi block then the lo block), read with
+// 16-byte loads through L1 (every warp on an SM walks the same sources, so they hit).
+// One block per target sphere, WPT warps splitting its sources lane by lane: no
+// shared-memory tiles and no block barrier inside the loop.  The per-lane partial
+// sums are combined by a transposing warp reduction and then across the WPT warps in
+// shared memory, both in a fixed order, so the result does not depend on timing.
+// ---------------------------------------------------------------------------------
+
+template <int NC> struct RecShape {
+  static constexpr int NCP = (NC + 3) & ~3;   // floats per block of a record
+  static constexpr int NV = NCP / 4;          // float4 per block
+};
+
+// Component i of a float4 register array (i is a compile-time constant after unrolling).
+__device__ __forceinline__ float f4c(const float4* v, int i) {
+  const float4 t = v[i >> 2];
+  const int c = i & 3;
+  return c == 0 ? t.x : (c == 1 ? t.y : (c == 2 ? t.z : t.w));
+}
+
+// Sum NV per-lane values over the warp.  At each step a lane keeps one half of its
+// values and sends the other half to its partner, so 32 values cost 31 shuffles
+// instead of 160; afterwards lane L holds the total of value 32c + L in out[c].
+template <typename T, int NV>
+__device__ __forceinline__ void warp_transpose_sum(const T* v, T* out) {
+  constexpr int NCH = (NV + 31) / 32;
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int c = 0; c < NCH; ++c) {
+    T w[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) w[i] = (32 * c + i < NV) ? v[32 * c + i] : T(0);
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+      const bool up = (lane & o) != 0;
+#pragma unroll
+      for (int i = 0; i < o; ++i) {
+        const T keep = up ? w[i + o] : w[i];
+        const T send = up ? w[i] : w[i + o];
+        w[i] = keep + gbi_shfl(send, o);
+      }
+    }
+    out[c] = w[0];
+  }
+}
+
+template <int TR, int ROWS, int COLS, typename T, int WPT, int MINB>
+__global__ void __launch_bounds__(WPT * 32, MINB) pair_stream_kernel(const PairArgs args) {
+  using S = PassShape<TR, ROWS, COLS>;
+  constexpr int D = S::D;
+  constexpr int R0 = S::R0;
+  constexpr int C0 = S::C0;
+  constexpr int NR = S::NR;
+  constexpr int NC = S::NC;
+  constexpr bool DF = std::is_same<T, df>::value;
+  static_assert(DF || std::is_same<T, float>::value, "streaming pass is FP32 or double-float");
+  constexpr int NCP = RecShape<NC>::NCP;
+  constexpr int NV = RecShape<NC>::NV;
+  constexpr int RECV = DF ? 2 * NV : NV;       // float4 per source record
+  constexpr int NRC = (NR + 31) / 32;
+  __shared__ T red[WPT > 1 ? WPT : 1][NRC * 32];
+
+  if (args.active != nullptr && *args.active == 0) return;   // device-side GMRES has stopped
+  const int n = blockIdx.x;
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  int src_lo = 0, src_hi = args.N;
+  if (args.sys_of != nullptr) {
+    const int sy = args.sys_of[n];
+    // the whole block belongs to target n, so this return is uniform
+    if (args.sys_flag != nullptr && args.sys_flag[(size_t)sy * args.sys_flag_stride] == 0) return;
+    src_lo = args.sys_off[sy];
+    src_hi = args.sys_off[sy + 1];
+  }
+  const T a = T(args.a);
+  const float4 th = args.pos.hi[n], tl = args.pos.lo[n];
+  const float4* __restrict__ rec = reinterpret_cast<const float4*>(args.x32);
+
+  T acc[NR];
+#pragma unroll
+  for (int p = 0; p < NR; ++p) acc[p] = T(0);
+  float min_r2 = 3.0e38f;
+
+  for (int m = src_lo + warp * 32 + lane; m < src_hi; m += WPT * 32) {
+    const float4 sh = __ldg(args.pos.hi + m), sl = __ldg(args.pos.lo + m);
+    float4 r4[RECV];
+#pragma unroll
+    for (int i = 0; i < RECV; ++i) r4[i] = __ldg(rec + (size_t)m * RECV + i);
+    if (m == n) continue;
+    T dx, dy, dz;
+    if constexpr (DF) {
+      // exact difference of the hi parts, plus the (tiny) difference of the lo parts
+      dx = df_two_sum(th.x, -sh.x) + df(tl.x - sl.x, 0.f);
+      dy = df_two_sum(th.y, -sh.y) + df(tl.y - sl.y, 0.f);
+      dz = df_two_sum(th.z, -sh.z) + df(tl.z - sl.z, 0.f);
+    } else {
+      dx = (th.x - sh.x) + (tl.x - sl.x);
+      dy = (th.y - sh.y) + (tl.y - sl.y);
+      dz = (th.z - sh.z) + (tl.z - sl.z);
+    }
+    min_r2 = fminf(min_r2, float(dx * dx + dy * dy + dz * dz));
+    T xl[D];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+      if constexpr (DF) xl[C0 + q] = df(f4c(r4, q), f4c(r4, NCP + q));
+      else xl[C0 + q] = f4c(r4, q);
+    }
+    pair_body<TR, ROWS, COLS, T>(dx, dy, dz, a, xl, acc);
+  }
+
+  T tot[NRC];
+  warp_transpose_sum<T, NR>(acc, tot);
+  if (args.min_r2_bits != nullptr) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) min_r2 = fminf(min_r2, __shfl_xor_sync(0xffffffffu, min_r2, o));
+    if (lane == 0) atomicMin(args.min_r2_bits, __float_as_uint(min_r2));
+  }
+  if constexpr (WPT > 1) {
+#pragma unroll
+    for (int c = 0; c < NRC; ++c) red[warp][32 * c + lane] = tot[c];
+    __syncthreads();
+    if (warp != 0) return;
+#pragma unroll
+    for (int c = 0; c < NRC; ++c) {
+      T v = red[0][32 * c + lane];
+#pragma unroll
+      for (int w = 1; w < WPT; ++w) v += red[w][32 * c + lane];
+      tot[c] = v;
+    }
+  }
+  const double inva = 1.0 / args.a;
+#pragma unroll
+  for (int c = 0; c < NRC; ++c) {
+    const int p = 32 * c + lane;
+    if (p >= NR) continue;
+    double v = gbi_to_double(tot[c]) * inva;
+    if (args.add_self) {
+      // FP32 passes use the rounded source the pair terms saw; double-float the FP64 one
+      const int q = R0 - C0 + p;
+      const double* xsrc = args.x_index ? args.x + (size_t)(*args.x_index) * args.x_stride : args.x;
+      const double xs = DF ? xsrc[(size_t)q * args.N + n] * args.colscale[R0 + p]
+                           : double(args.x32[(size_t)n * (RECV * 4) + q]);
+      v += args.selfg[R0 + p] * inva * xs;
+    }
+    double* dst = args.y + (size_t)p * args.N + n;
+    *dst = args.alpha * v + (args.beta != 0.0 ? args.beta * (*dst) : 0.0);
   }
 }
 

@@ -5,15 +5,15 @@
 
 namespace gbi {
 
-// Warps per target chosen so that about 2400 warps (one wave at 16 resident warps per
-// SM on 152 SMs) exist when N is small; blocks stay at four warps.  FULL adds the
-// all-rows/all-columns pass (used by gbi_apply only).
+// FULL adds the all-rows/all-columns pass (used by gbi_apply only).
 template <typename T, int TRN, bool FULL>
 cudaError_t launch_pairs_tt(int rows, int cols, const PairArgs& args, cudaStream_t stream) {
-  constexpr int TILE = sizeof(T) == 4 ? 128 : 64;   // 64 for double and double-float
   if (args.N <= 0) return cudaSuccess;
   const int N = args.N;
-  const int wpt = N >= 2048 ? 1 : (N >= 1024 ? 2 : 4);
+  if constexpr (std::is_same<T, double>::value) {
+    // FP64: shared-memory tiles of 64 sources; the FP64 pipe bounds this pass
+    constexpr int TILE = 64;
+    const int wpt = N >= 2048 ? 1 : (N >= 1024 ? 2 : 4);
 #define GBI_L(RV, CV, TPB, WPT)                                                          \
   if (rows == RV && cols == CV && wpt == WPT) {                                          \
     const dim3 grid((N + TPB - 1) / TPB), block(TPB * WPT * 32);                         \
@@ -21,14 +21,37 @@ cudaError_t launch_pairs_tt(int rows, int cols, const PairArgs& args, cudaStream
     return cudaGetLastError();                                                           \
   }
 #define GBI_LW(RV, CV) GBI_L(RV, CV, 4, 1) GBI_L(RV, CV, 2, 2) GBI_L(RV, CV, 1, 4)
-  GBI_LW(SET_H, SET_L)
-  GBI_LW(SET_H, SET_H)
-  GBI_LW(SET_L, SET_ALL)
-  if constexpr (FULL) {
-    GBI_LW(SET_ALL, SET_ALL)
-  }
+    GBI_LW(SET_H, SET_L)
+    GBI_LW(SET_H, SET_H)
+    GBI_LW(SET_L, SET_ALL)
+    if constexpr (FULL) {
+      GBI_LW(SET_ALL, SET_ALL)
+    }
 #undef GBI_LW
 #undef GBI_L
+  } else {
+    // at most 16 resident warps per SM for the FP32 forms of l <= 3 (a 128-register
+    // cap), 8 for l <= 4 and double-float; stream_wpt keeps WPT within the same bound
+    constexpr bool DF = std::is_same<T, df>::value;
+    constexpr int WARPS_SM = (TRN == 4 || DF) ? 8 : 16;
+    const int wpt = stream_wpt(TRN, DF ? 2 : 1, N, args.wpt);
+#define GBI_S(RV, CV, WPT)                                                                         \
+  if (rows == RV && cols == CV && wpt == WPT) {                                                    \
+    constexpr int MINB = WARPS_SM / WPT > 0 ? WARPS_SM / WPT : 1;                                  \
+    pair_stream_kernel<TRN, RV, CV, T, WPT, MINB><<<dim3(N), dim3(WPT * 32), 0, stream>>>(args);   \
+    return cudaGetLastError();                                                                     \
+  }
+#define GBI_SW(RV, CV) \
+  GBI_S(RV, CV, 2) GBI_S(RV, CV, 4) GBI_S(RV, CV, 8) if constexpr (WARPS_SM >= 16) { GBI_S(RV, CV, 16) }
+    GBI_SW(SET_H, SET_L)
+    GBI_SW(SET_H, SET_H)
+    GBI_SW(SET_L, SET_ALL)
+    if constexpr (FULL) {
+      GBI_SW(SET_ALL, SET_ALL)
+    }
+#undef GBI_SW
+#undef GBI_S
+  }
   return cudaErrorInvalidValue;
 }
 

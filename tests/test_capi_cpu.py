@@ -50,6 +50,16 @@ def test_host_calls(gbi):
         gbi.component_scales(7)
 
 
+def test_tuning_calls_validate_without_a_device(gbi):
+    """The tuning entry points reject a missing context before touching the GPU."""
+    import ctypes
+    L = gbi.lib()
+    offs = (ctypes.c_int * 2)(0, 10)
+    assert L.gbi_tune(None, 2, 1, offs, 1, None) == gbi.GBI_ERR_ARG
+    assert L.gbi_set_wpt(None, 4) == gbi.GBI_ERR_ARG
+    assert L.gbi_pass_wpt(None, 2, 2, 2, 1, 100, 0) == -1
+
+
 def test_generated_tables_agree_with_oracle(gbi):
     from oracle import galerkin, tensors
     for trunc in (2, 3, 4):
