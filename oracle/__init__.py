@@ -9,8 +9,10 @@ Modules: ``tensors`` (STF projectors, tensorial harmonics, packed basis, mode
 embeddings), ``taylor`` (exact truncated Taylor series of |rho|^nu),
 ``galerkin`` (pair and self elements, dense system, LU solve, superposition),
 ``quadrature`` (brute-force surface integrals used only to pin the above),
-``dynamics`` (forward-Euler trap update).
+``dynamics`` (forward-Euler trap update), ``mlp`` (features, network, loss,
+gradient and Adam step of the learned near-field correction).
 
-Parity status: every function is pinned by tests/test_oracle_pins.py against
+Parity status: every function is pinned by tests/test_oracle_pins.py and
+tests/test_oracle_mlp_pins.py against
 closed forms, textbook limits or brute-force quadrature; none is "parity unpinned".
 """
