@@ -165,6 +165,14 @@ gbi_status gbi_superpose(gbi_ctx* ctx, const gbi_params* params, int N,
                          const double* R, const double* Va, const double* Oa, const double* VH,
                          const double* Fe, const double* Te, double* V, double* Omega);
 
+/* Superposition approximation of gbi_superpose for a batch of independent
+ * suspensions laid out as in gbi_batch_solve (system s = spheres [offsets_host[s],
+ * offsets_host[s+1])); pairs are summed within each system only.  Every truncation
+ * uses the general pair operator (trunc 2 included).  Asynchronous. */
+gbi_status gbi_batch_superpose(gbi_ctx* ctx, const gbi_params* params, int nsys, const int* offsets_host,
+                               const double* R, const double* Va, const double* Oa, const double* VH,
+                               const double* Fe, const double* Te, double* V, double* Omega);
+
 /* Inputs of the harmonic-trap model (Sec. V, Eq. trap_eom) from centres R and unit
  * orientations p ([N][3] device arrays): F^e = -k_trap R, T^e = 0, V^a = vs p,
  * Omega^a = 0, packed V^(2s) = s0 (pp - I/3), V^(3t) = d0 p, other higher modes 0.
@@ -203,6 +211,74 @@ gbi_status gbi_solve_static(void* stream, const gbi_params* params, int N,
                             const double* R, const double* Va, const double* Oa, const double* VH,
                             const double* Fe, const double* Te,
                             double* V, double* Omega, double* QH, int warm_start, gbi_info* info);
+
+/* ---- Learned near-field correction (an engineering addition; the paper has no
+ * network).  A pairwise network approximates, for every ordered pair (n, m) of the
+ * same system closer than 4a, the part of sphere n's velocity and angular velocity
+ * that the Galerkin solution (Sec. II, Eq. many_body_active_passive_stresses, l <= 4)
+ * adds to the superposition approximation (Sec. IV) for force- and torque-free
+ * spheres with active modes V^a and V^(2s) = s0 (pp - I/3).
+ *
+ * Pair frame (rho = R_n - R_m, r = |rho|):  e_z = rho / r;  e_x = the part of p_n
+ * normal to e_z, normalised (if its squared length is <= 1e-12: that of p_m; if that
+ * is also degenerate: the coordinate axis with the smallest |e_z| component, first
+ * such, made normal to e_z);  e_y = e_z x e_x.
+ * Features (9):  2a/r, (2a/r)^3, d, ln d, p_n.e_z, p_n.e_x, p_m.e_x, p_m.e_y, p_m.e_z,
+ * with d = max(r/a - 2, 0.01).
+ * Network: tanh(W1 f + b1) -> tanh(W2 . + b2) -> tanh(W3 . + b3) -> W4 . + b4, widths
+ * 9, 128, 128, 128, 6; outputs o_0..2 (velocity) and o_3..5 (angular velocity) in the
+ * pair frame.  The correction of sphere n is (s0 / sigma) sum_m sum_c o_c e_c (and
+ * o_(3+c) e_c for Omega), summed over n's pairs in increasing m.
+ * Flat parameters (GBI_MLP_NPARAM floats): W1[128][9], b1[128], W2[128][128], b2[128],
+ * W3[128][128], b3[128], W4[6][128], b4[6].
+ * Inference multiplies BF16 weights and BF16 layer inputs on the tensor cores with
+ * FP32 accumulation; training (FP32 CUDA cores) multiplies the same rounded values
+ * and updates FP32 master weights with Adam (beta1 0.9, beta2 0.999, eps 1e-8).
+ *
+ * gbi_pairs: ordered pairs (n, m), n != m, of the same system with |R_n - R_m| < rcut a
+ * (decided in FP64 as (dx dx + dy dy) + dz dz), grouped by n and sorted by m; systems
+ * as in gbi_batch_solve (nsys <= 1 and offsets NULL: one system).  One system of more
+ * than 4096 spheres uses a cell list and fails with GBI_ERR_ARG if a sphere has more
+ * than 64 such neighbours.  *npairs receives the count; gbi_pairs_get copies the last
+ * list into device arrays tg (targets n), sr (sources m) of *npairs ints.
+ * Synchronizes the stream.
+ * gbi_mlp_set / gbi_mlp_get: load (host FP32, resets Adam) / read the weights and the
+ * label scale sigma > 0.
+ * gbi_mlp_features: features [P][9] and frames [P][9] (rows e_x, e_y, e_z), FP32, of
+ * the pairs (tg[k], sr[k]) (device arrays).
+ * gbi_mlp_forward: network outputs for P feature rows; FR == NULL gives pair-frame
+ * outputs [P][6], otherwise the rotated (lab-frame) ones.
+ * gbi_mlp_correct: builds the 4a pairs of R, evaluates the network and ADDS the
+ * corrections to V, Omega ([N][3], device).  *npairs (may be NULL) = pairs evaluated.
+ * gbi_mlp_labels: labels [N][6] = sigma/s0 ((Vx, Ox) - (Vs, Os)) from exact (x) and
+ * superposition (s) velocities; if *sigma <= 0 it is first set to the power of two
+ * nearest 1 / rms((x - s)/s0).
+ * gbi_mlp_loss_grad: loss = sum_n |P_n - labels_n|^2 / (6N) over all spheres (P_n the
+ * summed rotated outputs) and its gradient (device, GBI_MLP_NPARAM floats), no update.
+ * gbi_mlp_adam: one Adam step with the given gradient (device) and learning rate.
+ * gbi_mlp_train: epochs passes over the systems in order, minibatches of batch_systems
+ * consecutive systems (loss normalised per minibatch), learning rate geometric from
+ * lr0 to lr1 over all steps; loss_hist (host, may be NULL) receives each epoch's mean
+ * minibatch loss.  Synchronous. */
+#define GBI_MLP_NPARAM 35078
+gbi_status gbi_pairs(gbi_ctx* ctx, int N, const double* R, double a, double rcut, int nsys, const int* offsets_host,
+                     int* npairs);
+gbi_status gbi_pairs_get(gbi_ctx* ctx, int* tg, int* sr);
+gbi_status gbi_mlp_set(gbi_ctx* ctx, const float* theta_host, double sigma);
+gbi_status gbi_mlp_get(gbi_ctx* ctx, float* theta_host, double* sigma);
+gbi_status gbi_mlp_features(gbi_ctx* ctx, int P, const double* R, const double* p, const int* tg, const int* sr,
+                            double a, float* F, float* FR);
+gbi_status gbi_mlp_forward(gbi_ctx* ctx, int P, const float* F, const float* FR, float* out);
+gbi_status gbi_mlp_correct(gbi_ctx* ctx, int N, const double* R, const double* p, double a, double s0, int nsys,
+                           const int* offsets_host, double* V, double* Omega, int* npairs);
+gbi_status gbi_mlp_labels(gbi_ctx* ctx, int N, double s0, const double* Vx, const double* Ox, const double* Vs,
+                          const double* Os, double* sigma, double* labels);
+gbi_status gbi_mlp_loss_grad(gbi_ctx* ctx, int N, const double* R, const double* p, double a, int nsys,
+                             const int* offsets_host, const double* labels, double* loss, float* grad);
+gbi_status gbi_mlp_adam(gbi_ctx* ctx, const float* grad, double lr);
+gbi_status gbi_mlp_train(gbi_ctx* ctx, int N, const double* R, const double* p, double a, int nsys,
+                         const int* offsets_host, const double* labels, int epochs, int batch_systems, double lr0,
+                         double lr1, double* loss_hist);
 
 /* Tuning of the pair kernel (engineering; the paper has no counterpart).  The FP32
  * and double-float pair passes run one block per target sphere whose WPT warps split

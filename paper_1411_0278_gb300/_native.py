@@ -65,10 +65,24 @@ _SIGS = {
                            ctypes.POINTER(gbi_info)]),
     "gbi_batch_solve": (_I, [_VP, ctypes.POINTER(gbi_params), _I, ctypes.POINTER(ctypes.c_int)] + [_VP] * 9 +
                         [_I, ctypes.POINTER(gbi_info)]),
+    "gbi_batch_superpose": (_I, [_VP, ctypes.POINTER(gbi_params), _I, ctypes.POINTER(ctypes.c_int)] + [_VP] * 8),
     "gbi_solve_static": (_I, [_VP, ctypes.POINTER(gbi_params), _I] + [_VP] * 9 + [_I, ctypes.POINTER(gbi_info)]),
     "gbi_tune": (_I, [_VP, _I, _I, ctypes.POINTER(ctypes.c_int), _I, ctypes.POINTER(ctypes.c_int)]),
     "gbi_set_wpt": (_I, [_VP, _I]),
     "gbi_pass_wpt": (_I, [_VP, _I, _I, _I, _I, _I, _I]),
+    "gbi_pairs": (_I, [_VP, _I, _VP, _D, _D, _I, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "gbi_pairs_get": (_I, [_VP, _VP, _VP]),
+    "gbi_mlp_set": (_I, [_VP, _VP, _D]),
+    "gbi_mlp_get": (_I, [_VP, _VP, c_double_p]),
+    "gbi_mlp_features": (_I, [_VP, _I, _VP, _VP, _VP, _VP, _D, _VP, _VP]),
+    "gbi_mlp_forward": (_I, [_VP, _I, _VP, _VP, _VP]),
+    "gbi_mlp_correct": (_I, [_VP, _I, _VP, _VP, _D, _D, _I, ctypes.POINTER(ctypes.c_int), _VP, _VP,
+                             ctypes.POINTER(ctypes.c_int)]),
+    "gbi_mlp_labels": (_I, [_VP, _I, _D, _VP, _VP, _VP, _VP, c_double_p, _VP]),
+    "gbi_mlp_loss_grad": (_I, [_VP, _I, _VP, _VP, _D, _I, ctypes.POINTER(ctypes.c_int), _VP, c_double_p, _VP]),
+    "gbi_mlp_adam": (_I, [_VP, _VP, _D]),
+    "gbi_mlp_train": (_I, [_VP, _I, _VP, _VP, _D, _I, ctypes.POINTER(ctypes.c_int), _VP, _I, _I, _D, _D,
+                           c_double_p]),
     "gbi_kernel_launches": (ctypes.c_longlong, [_VP]),
     "gbi_set_profiling": (_I, [_VP, _I]),
     "gbi_kernel_stats": (_I, [_VP, _I, c_double_p, ctypes.POINTER(ctypes.c_longlong), c_double_p]),
@@ -80,6 +94,7 @@ def kernel_class(precision, rows, cols):
 
 
 TRAP_F64, TRAP_F32 = 27, 28
+MLP_NPARAM = 35078
 N_KERNEL_CLASSES = 30
 
 
@@ -130,13 +145,25 @@ def self_scalars(trunc):
     return _host_table("gbi_self_scalars", trunc)
 
 
-def _ptr(t):
+def _ptr(t, dtype=None):
+    """Device address of a contiguous CUDA tensor of the expected dtype (float64 unless given)."""
     if t is None or t.numel() == 0:
         return None
     import torch
-    if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
-        raise ValueError("expected a contiguous float64 CUDA tensor")
+    dtype = torch.float64 if dtype is None else dtype
+    if not (t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise ValueError("expected a contiguous %s CUDA tensor" % dtype)
     return ctypes.c_void_p(t.data_ptr())
+
+
+def _f32(t):
+    import torch
+    return _ptr(t, torch.float32)
+
+
+def _i32(t):
+    import torch
+    return _ptr(t, torch.int32)
 
 
 def solve_static(prm, R, Va, Oa, VH, Fe, Te, V, Om, QH, warm_start=False, stream=None):
@@ -257,6 +284,18 @@ class Context:
                                         _ptr(Fe), _ptr(Te), _ptr(V), _ptr(Om)), "gbi_superpose")
         return V, Om
 
+    def batch_superpose(self, prm, offsets, R, Va, Oa, VH, Fe, Te, V=None, Om=None):
+        """gbi_batch_superpose: superposition velocities of independent suspensions."""
+        import torch
+        N = R.shape[0]
+        offs = (ctypes.c_int * len(offsets))(*[int(o) for o in offsets])
+        V = torch.empty((N, 3), dtype=torch.float64, device=R.device) if V is None else V
+        Om = torch.empty_like(V) if Om is None else Om
+        self._check(lib().gbi_batch_superpose(self._h, ctypes.byref(prm), len(offsets) - 1, offs, _ptr(R), _ptr(Va),
+                                              _ptr(Oa), _ptr(VH), _ptr(Fe), _ptr(Te), _ptr(V), _ptr(Om)),
+                    "gbi_batch_superpose")
+        return V, Om
+
     def trap_inputs(self, N, trunc, k_trap, vs, s0, d0, R, p):
         import torch
         dev = R.device
@@ -281,6 +320,91 @@ class Context:
 
     def pass_wpt(self, trunc, rows, cols, precision, N, batched=False):
         return lib().gbi_pass_wpt(self._h, int(trunc), int(rows), int(cols), int(precision), int(N), int(batched))
+
+    # ---- learned near-field correction
+    @staticmethod
+    def _offs(offsets):
+        if offsets is None:
+            return 0, None
+        return len(offsets) - 1, (ctypes.c_int * len(offsets))(*[int(v) for v in offsets])
+
+    def pairs(self, R, a, rcut, offsets=None):
+        """gbi_pairs + gbi_pairs_get: (targets, sources) int32 device tensors."""
+        import torch
+        nsys, offs = self._offs(offsets)
+        n = ctypes.c_int()
+        self._check(lib().gbi_pairs(self._h, int(R.shape[0]), _ptr(R), float(a), float(rcut), nsys, offs,
+                                    ctypes.byref(n)), "gbi_pairs")
+        tg = torch.empty(n.value, dtype=torch.int32, device=R.device)
+        sr = torch.empty_like(tg)
+        self._check(lib().gbi_pairs_get(self._h, _i32(tg), _i32(sr)), "gbi_pairs_get")
+        return tg, sr
+
+    def mlp_set(self, theta, sigma):
+        import numpy as np
+        th = np.ascontiguousarray(theta, dtype=np.float32)
+        assert th.size == MLP_NPARAM
+        self._check(lib().gbi_mlp_set(self._h, th.ctypes.data, float(sigma)), "gbi_mlp_set")
+
+    def mlp_get(self):
+        import numpy as np
+        th = np.empty(MLP_NPARAM, dtype=np.float32)
+        sig = ctypes.c_double()
+        self._check(lib().gbi_mlp_get(self._h, th.ctypes.data, ctypes.byref(sig)), "gbi_mlp_get")
+        return th, sig.value
+
+    def mlp_features(self, R, p, tg, sr, a):
+        import torch
+        P = int(tg.shape[0])
+        F = torch.empty((P, 9), dtype=torch.float32, device=R.device)
+        FR = torch.empty((P, 9), dtype=torch.float32, device=R.device)
+        self._check(lib().gbi_mlp_features(self._h, P, _ptr(R), _ptr(p), _i32(tg), _i32(sr), float(a), _f32(F),
+                                           _f32(FR)), "gbi_mlp_features")
+        return F, FR
+
+    def mlp_forward(self, F, FR=None):
+        import torch
+        P = int(F.shape[0])
+        out = torch.empty((P, 6), dtype=torch.float32, device=F.device)
+        self._check(lib().gbi_mlp_forward(self._h, P, _f32(F), _f32(FR) if FR is not None else None, _f32(out)),
+                    "gbi_mlp_forward")
+        return out
+
+    def mlp_correct(self, R, p, a, s0, V, Om, offsets=None):
+        nsys, offs = self._offs(offsets)
+        n = ctypes.c_int()
+        self._check(lib().gbi_mlp_correct(self._h, int(R.shape[0]), _ptr(R), _ptr(p), float(a), float(s0), nsys,
+                                          offs, _ptr(V), _ptr(Om), ctypes.byref(n)), "gbi_mlp_correct")
+        return n.value
+
+    def mlp_labels(self, s0, Vx, Ox, Vs, Os, sigma=0.0):
+        import torch
+        N = int(Vx.shape[0])
+        lab = torch.empty((N, 6), dtype=torch.float64, device=Vx.device)
+        sig = ctypes.c_double(float(sigma))
+        self._check(lib().gbi_mlp_labels(self._h, N, float(s0), _ptr(Vx), _ptr(Ox), _ptr(Vs), _ptr(Os),
+                                         ctypes.byref(sig), _ptr(lab)), "gbi_mlp_labels")
+        return lab, sig.value
+
+    def mlp_loss_grad(self, R, p, a, labels, offsets=None):
+        import torch
+        nsys, offs = self._offs(offsets)
+        g = torch.empty(MLP_NPARAM, dtype=torch.float32, device=R.device)
+        loss = ctypes.c_double()
+        self._check(lib().gbi_mlp_loss_grad(self._h, int(R.shape[0]), _ptr(R), _ptr(p), float(a), nsys, offs,
+                                            _ptr(labels), ctypes.byref(loss), _f32(g)), "gbi_mlp_loss_grad")
+        return loss.value, g
+
+    def mlp_adam(self, grad, lr):
+        self._check(lib().gbi_mlp_adam(self._h, _f32(grad), float(lr)), "gbi_mlp_adam")
+
+    def mlp_train(self, R, p, a, offsets, labels, epochs, batch_systems, lr0, lr1):
+        nsys, offs = self._offs(offsets)
+        hist = (ctypes.c_double * max(int(epochs), 1))()
+        self._check(lib().gbi_mlp_train(self._h, int(R.shape[0]), _ptr(R), _ptr(p), float(a), nsys, offs,
+                                        _ptr(labels), int(epochs), int(batch_systems), float(lr0), float(lr1), hist),
+                    "gbi_mlp_train")
+        return list(hist)[:int(epochs)]
 
     def kernel_launches(self):
         return int(lib().gbi_kernel_launches(self._h))

@@ -69,6 +69,7 @@ struct gbi_ctx {
   Buf boff, bsys;                              // system offsets / ids of the current batch
   std::vector<char> hbatch;                    // host copy of the per-system solver states
   bool allow_graphs = true;                    // replay Arnoldi chunks from a CUDA graph
+  bool fixed = false;                          // buffers bound to static storage: never reallocate
   cudaGraphExec_t chunk_exec = nullptr;        // captured chunk of Arnoldi iterations
   const void* chunk_key[8] = {};
   long long chunk_ikey[6] = {};
@@ -89,6 +90,17 @@ struct gbi_ctx {
   double stat_flops[30] = {0};
   long long stat_n[30] = {0};
   long long stat_dead[30] = {0};
+  // learned near-field correction: FP32 master weights, Adam moments, bf16-rounded
+  // copy (training), padded bf16 copy (inference), gradient; neighbour lists; pair
+  // features, outputs and training scratch
+  Buf mlp_th, mlp_m, mlp_v, mlp_thq, mlp_pk, mlp_grad;
+  double mlp_sigma = 0.0;
+  int mlp_step = 0;
+  bool mlp_ready = false;
+  Buf nb_cnt, nb_start, nb_tg, nb_sr, nb_scan, cell_of, cell_cnt, cell_start, cell_fill, cell_items, nb_aux;
+  int nb_pairs = 0, nb_N = 0;
+  Buf mf_F, mf_FR, mf_lab, mf_dO, mf_part, mf_loss;
+  int num_sms = 0;
   // warps per target chosen by gbi_tune, keyed by pass, precision, log2(N), batching
   std::map<long long, int> wpt_table;
   int force_wpt = 0;                           // gbi_set_wpt override (0: table or default)
@@ -128,6 +140,10 @@ gbi_status fail(gbi_ctx* c, cudaError_t e, const char* where) {
 gbi_status ensure(gbi_ctx* ctx, Buf& b, size_t bytes) {
   if (bytes == 0) bytes = 16;
   if (b.bytes >= bytes) return GBI_OK;
+  if (ctx->fixed) {
+    ctx->err = "static scratch too small for this request";
+    return GBI_ERR_NOMEM;
+  }
   if (b.p) {
     GBI_CHECK(cudaStreamSynchronize(ctx->stream));
     GBI_CHECK(cudaFree(b.p));
@@ -495,18 +511,25 @@ struct GDev {
 struct GPtr {     // per-system views into the gstate buffer
   GDev* st;
   double *H, *cs, *sn, *g, *y, *h1, *h2, *nrm;
-  int S, m;
+  double *h1p, *h2p, *nrmp;   // per-chunk partial sums of the dot products and the norm
+  int S, m, CH;
 };
 
-size_t gstate_doubles(int m, int S) {
+// Row chunks per system of the Arnoldi reductions: a few systems get one block per
+// component row (so that a single suspension still spreads over many SMs), large
+// batches one block per system.
+int arnoldi_chunks(int S, int h) { return S >= 64 ? 1 : h; }
+
+size_t gstate_doubles(int m, int S, int CH) {
   return (size_t)S * (sizeof(GDev) / sizeof(double) + 1) + (size_t)S * ((size_t)(m + 1) * m + 7 * (size_t)(m + 1) + 1) +
-         16;
+         (size_t)S * CH * (2 * (size_t)(m + 1) + 1) + 16;
 }
 
-GPtr gptrs(void* base, int m, int S) {
+GPtr gptrs(void* base, int m, int S, int CH) {
   GPtr p;
   p.S = S;
   p.m = m;
+  p.CH = CH;
   p.st = reinterpret_cast<GDev*>(base);
   double* d = reinterpret_cast<double*>(base) + (size_t)S * (sizeof(GDev) / sizeof(double) + 1);
   p.H = d; d += (size_t)S * (m + 1) * m;
@@ -516,7 +539,10 @@ GPtr gptrs(void* base, int m, int S) {
   p.y = d; d += (size_t)S * (m + 1);
   p.h1 = d; d += (size_t)S * (m + 1);
   p.h2 = d; d += (size_t)S * (m + 1);
-  p.nrm = d;
+  p.nrm = d; d += (size_t)S;
+  p.h1p = d; d += (size_t)S * (m + 1) * CH;
+  p.h2p = d; d += (size_t)S * (m + 1) * CH;
+  p.nrmp = d;
   return p;
 }
 
@@ -556,27 +582,48 @@ __global__ void bk_gather(const double* __restrict__ V, size_t n, int Ntot, cons
   out[t] = O(V[(size_t)g.j * n + t] * minv.v[q]);
 }
 
-// out[s][i] = V_i . w over system s, for i <= j_s (one block per system and vector)
-__global__ void bk_dots(const double* __restrict__ V, size_t n, const double* __restrict__ w, int Ntot, int h,
-                        const int* __restrict__ off, const GDev* __restrict__ st, int m, double* out) {
-  const int s = blockIdx.x, i = blockIdx.y;
-  const GDev& g = st[s];
-  if (!g.active || i > g.j) return;
-  const double* v = V + (size_t)i * n;
-  const int lo = off[s], hi = off[s + 1];
-  double acc = 0.0;
-  for (int q = 0; q < h; ++q) {
-    const size_t b = (size_t)q * Ntot;
-    for (int p = lo + threadIdx.x; p < hi; p += blockDim.x) acc += v[b + p] * w[b + p];
-  }
+__device__ __forceinline__ double block_sum_256(double v) {
   __shared__ double sh[256];
-  sh[threadIdx.x] = acc;
+  sh[threadIdx.x] = v;
   __syncthreads();
   for (int o = blockDim.x / 2; o > 0; o >>= 1) {
     if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
     __syncthreads();
   }
-  if (threadIdx.x == 0) out[(size_t)s * (m + 1) + i] = sh[0];
+  return sh[0];
+}
+
+// part[(s (m+1) + i) CH + c] = V_i . w over the component rows of chunk c of system s,
+// for i <= j_s (block (s, i, c); fixed-order block reduction)
+__global__ void bk_dots(const double* __restrict__ V, size_t n, const double* __restrict__ w, int Ntot, int h,
+                        const int* __restrict__ off, const GDev* __restrict__ st, int m, int CH, double* part) {
+  const int s = blockIdx.x, i = blockIdx.y, c = blockIdx.z;
+  const GDev& g = st[s];
+  if (!g.active || i > g.j) return;
+  const double* v = V + (size_t)i * n;
+  const int lo = off[s], hi = off[s + 1];
+  const int q0 = c * h / CH, q1 = (c + 1) * h / CH;
+  double acc = 0.0;
+  for (int q = q0; q < q1; ++q) {
+    const size_t b = (size_t)q * Ntot;
+    for (int p = lo + threadIdx.x; p < hi; p += blockDim.x) acc += v[b + p] * w[b + p];
+  }
+  const double t = block_sum_256(acc);
+  if (threadIdx.x == 0) part[((size_t)s * (m + 1) + i) * CH + c] = t;
+}
+
+// out[s][i] = sum over the chunks (in order) of the partial dot products
+__global__ void bk_dots_sum(const double* __restrict__ part, const GDev* __restrict__ st, int m, int CH,
+                            double* __restrict__ out) {
+  const int s = blockIdx.x;
+  const GDev& g = st[s];
+  if (!g.active) return;
+  for (int i = threadIdx.x; i <= g.j; i += blockDim.x) {
+    const double* q = part + ((size_t)s * (m + 1) + i) * CH;
+    double acc = 0.0;
+    for (int c = 0; c < CH; ++c) acc += q[c];
+    out[(size_t)s * (m + 1) + i] = acc;
+  }
 }
 
 // w -= sum_{i <= j_s} coef[s][i] V_i
@@ -594,26 +641,35 @@ __global__ void bk_sub(const double* __restrict__ V, size_t n, double* w, int Nt
   w[t] = acc;
 }
 
-// out[s] = |x_s|^2 (one block per system); mode 0: active systems, 1: enabled, 2: all
-__global__ void bk_norm(const double* __restrict__ x, int Ntot, int h, const int* __restrict__ off,
-                        const GDev* __restrict__ st, int mode, double* out) {
-  const int s = blockIdx.x;
-  const GDev& g = st[s];
-  if ((mode == 0 && !g.active) || (mode == 1 && !g.enabled)) return;
+__device__ __forceinline__ bool norm_wanted(const GDev& g, int mode) {
+  return !((mode == 0 && !g.active) || (mode == 1 && !g.enabled));
+}
+
+// part[s CH + c] = |x_s|^2 over the rows of chunk c (block (s, c)); mode 0: active
+// systems, 1: enabled, 2: all
+__global__ void bk_norm_part(const double* __restrict__ x, int Ntot, int h, const int* __restrict__ off,
+                             const GDev* __restrict__ st, int mode, int CH, double* part) {
+  const int s = blockIdx.x, c = blockIdx.y;
+  if (!norm_wanted(st[s], mode)) return;
   const int lo = off[s], hi = off[s + 1];
+  const int q0 = c * h / CH, q1 = (c + 1) * h / CH;
   double acc = 0.0;
-  for (int q = 0; q < h; ++q) {
+  for (int q = q0; q < q1; ++q) {
     const size_t b = (size_t)q * Ntot;
     for (int p = lo + threadIdx.x; p < hi; p += blockDim.x) acc += x[b + p] * x[b + p];
   }
-  __shared__ double sh[256];
-  sh[threadIdx.x] = acc;
-  __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) out[s] = sh[0];
+  const double t = block_sum_256(acc);
+  if (threadIdx.x == 0) part[(size_t)s * CH + c] = t;
+}
+
+// out[s] = sum of the chunk partials in order
+__global__ void bk_norm_sum(const double* __restrict__ part, const GDev* __restrict__ st, int S, int mode, int CH,
+                            double* __restrict__ out) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= S || !norm_wanted(st[s], mode)) return;
+  double acc = 0.0;
+  for (int c = 0; c < CH; ++c) acc += part[(size_t)s * CH + c];
+  out[s] = acc;
 }
 
 // Hessenberg column j_s, Givens rotations, residual estimate and stopping test of one
@@ -634,7 +690,9 @@ __global__ void bk_finalize(GPtr p) {
   }
   __syncthreads();
   if (tid == 0) {
-    const double hn = sqrt(fmax(0.0, p.nrm[s]));
+    double nrm = 0.0;
+    for (int c = 0; c < p.CH; ++c) nrm += p.nrmp[(size_t)s * p.CH + c];
+    const double hn = sqrt(fmax(0.0, nrm));
     for (int i = 0; i < j; ++i) {
       const double t1 = col[i], t2 = col[i + 1];
       col[i] = scs[i] * t1 + ssn[i] * t2;
@@ -805,14 +863,17 @@ gbi_status launch_chunk(gbi_ctx* ctx, const Setup& s, const Batch& B, int precis
     else
       bk_gather<double><<<g2, 256, 0, ctx->stream>>>(Vb, n, Ntot, B.sys, gp.st, s.minv, static_cast<double*>(xsrc));
     GBI_CHECK(run_pairs(ctx, s.trunc, SET_H, SET_H, precision, pa));
-    bk_dots<<<dim3(S, m + 1), 256, 0, ctx->stream>>>(Vb, n, w, Ntot, h, B.off, gp.st, m, gp.h1);
+    const dim3 gd(S, m + 1, gp.CH);
+    bk_dots<<<gd, 256, 0, ctx->stream>>>(Vb, n, w, Ntot, h, B.off, gp.st, m, gp.CH, gp.h1p);
+    bk_dots_sum<<<S, 64, 0, ctx->stream>>>(gp.h1p, gp.st, m, gp.CH, gp.h1);
     bk_sub<<<g2, 256, 0, ctx->stream>>>(Vb, n, w, Ntot, B.sys, gp.st, m, gp.h1);
-    bk_dots<<<dim3(S, m + 1), 256, 0, ctx->stream>>>(Vb, n, w, Ntot, h, B.off, gp.st, m, gp.h2);
+    bk_dots<<<gd, 256, 0, ctx->stream>>>(Vb, n, w, Ntot, h, B.off, gp.st, m, gp.CH, gp.h2p);
+    bk_dots_sum<<<S, 64, 0, ctx->stream>>>(gp.h2p, gp.st, m, gp.CH, gp.h2);
     bk_sub<<<g2, 256, 0, ctx->stream>>>(Vb, n, w, Ntot, B.sys, gp.st, m, gp.h2);
-    bk_norm<<<S, 256, 0, ctx->stream>>>(w, Ntot, h, B.off, gp.st, 0, gp.nrm);
+    bk_norm_part<<<dim3(S, gp.CH), 256, 0, ctx->stream>>>(w, Ntot, h, B.off, gp.st, 0, gp.CH, gp.nrmp);
     bk_finalize<<<S, 128, 0, ctx->stream>>>(gp);
     bk_scale<<<g2, 256, 0, ctx->stream>>>(Vb, n, w, Ntot, B.sys, gp.st);
-    ctx->launches += 8;
+    ctx->launches += 10;
   }
   GBI_CHECK(cudaGetLastError());
   return GBI_OK;
@@ -839,13 +900,13 @@ gbi_status gmres_batch(gbi_ctx* ctx, const Setup& s, const Batch& B, int precisi
   const int m = std::max(1, std::min(restart, kMaxRestart));
   GBI_TRY(ensure(ctx, ctx->krylov, sizeof(double) * n * (m + 1)));
   GBI_TRY(ensure(ctx, ctx->w, sizeof(double) * n));
-  GBI_TRY(ensure(ctx, ctx->gstate, sizeof(double) * gstate_doubles(m, S)));
+  GBI_TRY(ensure(ctx, ctx->gstate, sizeof(double) * gstate_doubles(m, S, arnoldi_chunks(S, h))));
   // gathered Arnoldi source: FP64 component-major, or FP32 records of round4(h) floats
   GBI_TRY(ensure(ctx, ctx->x32, std::max(sizeof(double) * n, sizeof(float) * (size_t)Ntot * ((h + 3) & ~3))));
   double* Vb = P<double>(ctx->krylov);
   double* w = P<double>(ctx->w);
   void* xsrc = ctx->x32.p;
-  const GPtr gp = gptrs(ctx->gstate.p, m, S);
+  const GPtr gp = gptrs(ctx->gstate.p, m, S, arnoldi_chunks(S, h));
   const dim3 g2((Ntot + 255) / 256, h);
   const int sblk = (S + 127) / 128;
   iters = 0;
@@ -898,10 +959,11 @@ gbi_status gmres_batch(gbi_ctx* ctx, const Setup& s, const Batch& B, int precisi
           if (hst[q].enabled) info->pair_interactions += (long long)(B.h_off[q + 1] - B.h_off[q]) * (B.h_off[q + 1] - B.h_off[q] - 1);
       }
     }
-    bk_norm<<<S, 256, 0, ctx->stream>>>(Vb, Ntot, h, B.off, gp.st, 1, gp.nrm);
+    bk_norm_part<<<dim3(S, gp.CH), 256, 0, ctx->stream>>>(Vb, Ntot, h, B.off, gp.st, 1, gp.CH, gp.nrmp);
+    bk_norm_sum<<<(S + 127) / 128, 128, 0, ctx->stream>>>(gp.nrmp, gp.st, S, 1, gp.CH, gp.nrm);
     bk_init_cycle<<<sblk, 128, 0, ctx->stream>>>(gp, first ? 1 : 0);
     bk_scale0<<<g2, 256, 0, ctx->stream>>>(Vb, Ntot, B.sys, gp.st);
-    ctx->launches += 3;
+    ctx->launches += 4;
     GBI_CHECK(cudaGetLastError());
     first = false;
     for (int q = 0; q < S; ++q) before[q] = hst[q].iters;
@@ -995,13 +1057,13 @@ gbi_status solve_core(gbi_ctx* ctx, const gbi_params* prm, const Batch& B, const
   GBI_TRY(ensure(ctx, ctx->delta, sizeof(double) * nh));
   GBI_TRY(ensure(ctx, ctx->xVL, sizeof(double) * 6 * N));
   GBI_TRY(ensure(ctx, ctx->minr2, sizeof(unsigned int)));
-  GBI_TRY(ensure(ctx, ctx->gstate, sizeof(double) * gstate_doubles(restart, S)));
+  GBI_TRY(ensure(ctx, ctx->gstate, sizeof(double) * gstate_doubles(restart, S, arnoldi_chunks(S, h))));
   double* xF = P<double>(ctx->xQ);              // rows 0..5 of the full vector
   double* xQH = P<double>(ctx->xQ) + (size_t)6 * N;
   double* b = P<double>(ctx->b);
   double* r = P<double>(ctx->r);
   double* dl = P<double>(ctx->delta);
-  const GPtr gp = gptrs(ctx->gstate.p, restart, S);
+  const GPtr gp = gptrs(ctx->gstate.p, restart, S, arnoldi_chunks(S, h));
   const double c2a = s.scale.v[3];
   Scales hscale;
   for (int i = 0; i < 54; ++i) hscale.v[i] = (i < h) ? s.scale.v[6 + i] : 1.0;
@@ -1052,9 +1114,10 @@ gbi_status solve_core(gbi_ctx* ctx, const gbi_params* prm, const Batch& B, const
   const int max_iter = prm->max_iter > 0 ? prm->max_iter : 1000;
   const double rtol = prm->rtol > 0 ? prm->rtol : 1e-10;
   // |b_s| per system
-  bk_norm<<<S, 256, 0, ctx->stream>>>(b, N, h, B.off, gp.st, 2, gp.nrm);
+  bk_norm_part<<<dim3(S, gp.CH), 256, 0, ctx->stream>>>(b, N, h, B.off, gp.st, 2, gp.CH, gp.nrmp);
+  bk_norm_sum<<<(S + 127) / 128, 128, 0, ctx->stream>>>(gp.nrmp, gp.st, S, 2, gp.CH, gp.nrm);
   bk_refine<<<sblk, 128, 0, ctx->stream>>>(gp, 0, rtol);
-  ctx->launches += 2;
+  ctx->launches += 3;
   auto read_state = [&]() -> gbi_status {
     ctx->hbatch.resize(sizeof(GDev) * S);
     GBI_CHECK(cudaMemcpyAsync(ctx->hbatch.data(), gp.st, sizeof(GDev) * S, cudaMemcpyDeviceToHost, ctx->stream));
@@ -1084,9 +1147,10 @@ gbi_status solve_core(gbi_ctx* ctx, const gbi_params* prm, const Batch& B, const
     GBI_CHECK(run_pairs(ctx, s.trunc, SET_H, SET_H, 0, p));
     inf->matvecs_f64 += 1;
     inf->pair_interactions += pairs_enabled();
-    bk_norm<<<S, 256, 0, ctx->stream>>>(r, N, h, B.off, gp.st, 1, gp.nrm);
+    bk_norm_part<<<dim3(S, gp.CH), 256, 0, ctx->stream>>>(r, N, h, B.off, gp.st, 1, gp.CH, gp.nrmp);
+    bk_norm_sum<<<(S + 127) / 128, 128, 0, ctx->stream>>>(gp.nrmp, gp.st, S, 1, gp.CH, gp.nrm);
     bk_refine<<<sblk, 128, 0, ctx->stream>>>(gp, 1, rtol);
-    ctx->launches += 2;
+    ctx->launches += 3;
     GBI_TRY(read_state());
   } else {
     // mixed precision: r = b - A_hp x; A_32 d = r (FP32 pair sums, FP64 Arnoldi); x += d
@@ -1099,9 +1163,10 @@ gbi_status solve_core(gbi_ctx* ctx, const gbi_params* prm, const Batch& B, const
         GBI_CHECK(run_pairs(ctx, s.trunc, SET_H, SET_H, hp, p));
         inf->matvecs_f64 += 1;
         inf->pair_interactions += pairs_enabled();
-        bk_norm<<<S, 256, 0, ctx->stream>>>(r, N, h, B.off, gp.st, 1, gp.nrm);
+        bk_norm_part<<<dim3(S, gp.CH), 256, 0, ctx->stream>>>(r, N, h, B.off, gp.st, 1, gp.CH, gp.nrmp);
+    bk_norm_sum<<<(S + 127) / 128, 128, 0, ctx->stream>>>(gp.nrmp, gp.st, S, 1, gp.CH, gp.nrm);
         bk_refine<<<sblk, 128, 0, ctx->stream>>>(gp, 1, rtol);
-        ctx->launches += 2;
+        ctx->launches += 3;
       }
       if (sweep > 0) inf->refinements += 1;
       if (sweep >= max_refine || inf->iters >= max_iter) {
@@ -1174,6 +1239,31 @@ gbi_status single_batch(gbi_ctx* ctx, int N, Batch& B) {
 __global__ void k_fill_sys(int S, const int* __restrict__ off, int* sys) {
   const int s = blockIdx.x;
   for (int p = off[s] + threadIdx.x; p < off[s + 1]; p += blockDim.x) sys[p] = s;
+}
+
+bool valid_offsets(int nsys, const int* off) {
+  if (off[0] != 0) return false;
+  for (int q = 0; q < nsys; ++q)
+    if (off[q + 1] < off[q]) return false;
+  return true;
+}
+
+// Device copies of a batch layout (system offsets and the system of every sphere).
+gbi_status make_batch(gbi_ctx* ctx, int nsys, const int* offsets_host, Batch& B) {
+  const int N = offsets_host[nsys];
+  GBI_TRY(ensure(ctx, ctx->boff, sizeof(int) * (size_t)(nsys + 1)));
+  GBI_TRY(ensure(ctx, ctx->bsys, sizeof(int) * (size_t)N));
+  GBI_CHECK(cudaMemcpyAsync(ctx->boff.p, offsets_host, sizeof(int) * (size_t)(nsys + 1), cudaMemcpyHostToDevice,
+                            ctx->stream));
+  k_fill_sys<<<nsys, 256, 0, ctx->stream>>>(nsys, P<int>(ctx->boff), P<int>(ctx->bsys));
+  ++ctx->launches;
+  GBI_CHECK(cudaGetLastError());
+  B.S = nsys;
+  B.Ntot = N;
+  B.off = P<int>(ctx->boff);
+  B.sys = P<int>(ctx->bsys);
+  B.h_off.assign(offsets_host, offsets_host + nsys + 1);
+  return GBI_OK;
 }
 
 // ---------------------------------------------------------------------------------
@@ -1291,6 +1381,123 @@ gbi_status tune_impl(gbi_ctx* ctx, int trunc, int nsys, const int* offsets, int 
   return st;
 }
 
+
+// ---------------------------------------------------------------------------------
+// Learned near-field correction: neighbour lists and network driver
+// ---------------------------------------------------------------------------------
+
+static_assert(GBI_MLP_NPARAM == mlpk::NPARAM, "flat parameter count");
+constexpr int kSmallSystem = 4096;   // one system up to this size: O(N^2) neighbour scan
+
+// Ordered pairs closer than rcut * a within each system, into ctx->nb_* (grouped by
+// target, sorted by source).  Reads the pair count back to the host (synchronizes).
+gbi_status build_pairs(gbi_ctx* ctx, int N, const double* R, double a, double rcut, int nsys,
+                       const int* offsets_host, int& npair) {
+  using namespace mlpk;
+  const double rc2 = (rcut * a) * (rcut * a);
+  const int* sys_of = nullptr;
+  const int* sys_off = nullptr;
+  Batch B;
+  if (nsys > 1) {
+    GBI_TRY(make_batch(ctx, nsys, offsets_host, B));
+    sys_of = B.sys;
+    sys_off = B.off;
+  }
+  GBI_TRY(ensure(ctx, ctx->nb_cnt, sizeof(int) * (size_t)N));
+  GBI_TRY(ensure(ctx, ctx->nb_start, sizeof(int) * (size_t)(N + 1)));
+  GBI_TRY(ensure(ctx, ctx->nb_scan, sizeof(int) * scan_scratch_ints(N)));
+  GBI_TRY(ensure(ctx, ctx->nb_aux, 64 * 6 * sizeof(double) + 16));
+  int* cnt = P<int>(ctx->nb_cnt);
+  int* start = P<int>(ctx->nb_start);
+  const bool cells = nsys <= 1 && N > kSmallSystem;
+  double box[6];
+  double side = rcut * a;
+  int dims[3] = {1, 1, 1};
+  int* overflow = reinterpret_cast<int*>(static_cast<char*>(ctx->nb_aux.p) + 64 * 6 * sizeof(double));
+  if (cells) {
+    GBI_CHECK(mlpk::bbox(N, R, P<double>(ctx->nb_aux), box, ctx->stream));
+    double ext = 0.0;
+    for (int d = 0; d < 3; ++d) ext = std::max(ext, box[3 + d] - box[d]);
+    side = std::max(side, ext / 96.0);           // at most 97^3 cells
+    for (int d = 0; d < 3; ++d) dims[d] = std::max(1, (int)std::ceil((box[3 + d] - box[d]) / side));
+    const int nc = dims[0] * dims[1] * dims[2];
+    GBI_TRY(ensure(ctx, ctx->cell_of, sizeof(int) * (size_t)N));
+    GBI_TRY(ensure(ctx, ctx->cell_cnt, sizeof(int) * (size_t)nc));
+    GBI_TRY(ensure(ctx, ctx->cell_start, sizeof(int) * (size_t)nc));
+    GBI_TRY(ensure(ctx, ctx->cell_fill, sizeof(int) * (size_t)nc));
+    GBI_TRY(ensure(ctx, ctx->cell_items, sizeof(int) * (size_t)N));
+    if (ensure(ctx, ctx->nb_scan, sizeof(int) * std::max(scan_scratch_ints(N), scan_scratch_ints(nc))) != GBI_OK)
+      return GBI_ERR_NOMEM;
+    GBI_CHECK(cells_build(N, R, box, side, dims, P<int>(ctx->cell_of), P<int>(ctx->cell_cnt),
+                          P<int>(ctx->cell_start), P<int>(ctx->cell_fill), P<int>(ctx->cell_items),
+                          P<int>(ctx->nb_scan), ctx->stream));
+    GBI_CHECK(cudaMemsetAsync(overflow, 0, sizeof(int), ctx->stream));
+    GBI_CHECK(nb_cells(N, R, box, side, dims, P<int>(ctx->cell_of), P<int>(ctx->cell_start), P<int>(ctx->cell_cnt),
+                       P<int>(ctx->cell_items), rc2, nullptr, cnt, nullptr, nullptr, overflow, ctx->stream));
+    ctx->launches += 6;
+  } else {
+    GBI_CHECK(nb_count_sys(N, R, sys_of, sys_off, rc2, cnt, ctx->stream));
+    ++ctx->launches;
+  }
+  GBI_CHECK(exclusive_scan(cnt, start, N, P<int>(ctx->nb_scan), ctx->stream));
+  ctx->launches += 3;
+  const int chunks = (N + 1023) / 1024;
+  int total = 0, ovf = 0;
+  GBI_CHECK(cudaMemcpyAsync(&total, P<int>(ctx->nb_scan) + chunks, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  if (cells) GBI_CHECK(cudaMemcpyAsync(&ovf, overflow, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  GBI_CHECK(cudaMemcpyAsync(start + N, P<int>(ctx->nb_scan) + chunks, sizeof(int), cudaMemcpyDeviceToDevice,
+                            ctx->stream));
+  GBI_CHECK(cudaStreamSynchronize(ctx->stream));
+  if (ovf) {
+    ctx->err = "more than 64 neighbours within the cut-off for some sphere (overlapping input?)";
+    return GBI_ERR_ARG;
+  }
+  GBI_TRY(ensure(ctx, ctx->nb_tg, sizeof(int) * (size_t)std::max(total, 1)));
+  GBI_TRY(ensure(ctx, ctx->nb_sr, sizeof(int) * (size_t)std::max(total, 1)));
+  if (cells)
+    GBI_CHECK(nb_cells(N, R, box, side, dims, P<int>(ctx->cell_of), P<int>(ctx->cell_start), P<int>(ctx->cell_cnt),
+                       P<int>(ctx->cell_items), rc2, start, nullptr, P<int>(ctx->nb_tg), P<int>(ctx->nb_sr), overflow,
+                       ctx->stream));
+  else
+    GBI_CHECK(nb_fill_sys(N, R, sys_of, sys_off, rc2, start, P<int>(ctx->nb_tg), P<int>(ctx->nb_sr), ctx->stream));
+  ++ctx->launches;
+  ctx->nb_pairs = total;
+  ctx->nb_N = N;
+  npair = total;
+  return GBI_OK;
+}
+
+gbi_status mlp_require(gbi_ctx* ctx) {
+  if (!ctx->mlp_ready) {
+    ctx->err = "no network loaded (gbi_mlp_set)";
+    return GBI_ERR_ARG;
+  }
+  return GBI_OK;
+}
+
+// pairs (rcut 4a) and their features for N spheres; returns the pair count
+gbi_status mlp_prepare(gbi_ctx* ctx, int N, const double* R, const double* p, double a, int nsys,
+                       const int* offsets_host, int& npair) {
+  GBI_TRY(build_pairs(ctx, N, R, a, 4.0, nsys, offsets_host, npair));
+  const size_t n = (size_t)std::max(npair, 1);
+  GBI_TRY(ensure(ctx, ctx->mf_F, sizeof(float) * mlpk::NIN * n));
+  GBI_TRY(ensure(ctx, ctx->mf_FR, sizeof(float) * 9 * n));
+  GBI_TRY(ensure(ctx, ctx->mf_lab, sizeof(float) * 6 * n));
+  GBI_CHECK(mlpk::features(npair, R, p, P<int>(ctx->nb_tg), P<int>(ctx->nb_sr), a, P<float>(ctx->mf_F),
+                           P<float>(ctx->mf_FR), ctx->stream));
+  ++ctx->launches;
+  return GBI_OK;
+}
+
+int sm_count(gbi_ctx* ctx) {
+  if (ctx->num_sms == 0) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess || v <= 0) v = 152;
+    ctx->num_sms = v;
+  }
+  return ctx->num_sms;
+}
+
 }  // namespace
 
 // =================================================================================
@@ -1323,7 +1530,10 @@ gbi_status gbi_destroy(gbi_ctx* ctx) {
                  &ctx->delta, &ctx->krylov, &ctx->w, &ctx->partial, &ctx->dots, &ctx->xVL, &ctx->minr2,
                  &ctx->colbuf, &ctx->x32, &ctx->trapbuf, &ctx->gstate, &ctx->boff, &ctx->bsys, &ctx->tFe, &ctx->tTe, &ctx->tVa, &ctx->tOa, &ctx->tVH, &ctx->tV, &ctx->tOm,
                  &ctx->tQH, &ctx->hR, &ctx->hVa, &ctx->hOa, &ctx->hVH, &ctx->hFe, &ctx->hTe, &ctx->hV,
-                 &ctx->hOm, &ctx->hQH};
+                 &ctx->hOm, &ctx->hQH, &ctx->mlp_th, &ctx->mlp_m, &ctx->mlp_v, &ctx->mlp_thq, &ctx->mlp_pk,
+                 &ctx->mlp_grad, &ctx->nb_cnt, &ctx->nb_start, &ctx->nb_tg, &ctx->nb_sr, &ctx->nb_scan,
+                 &ctx->cell_of, &ctx->cell_cnt, &ctx->cell_start, &ctx->cell_fill, &ctx->cell_items, &ctx->nb_aux,
+                 &ctx->mf_F, &ctx->mf_FR, &ctx->mf_lab, &ctx->mf_dO, &ctx->mf_part, &ctx->mf_loss};
   for (Buf* b : bufs)
     if (b->p) cudaFree(b->p);
   if (ctx->hbuf) cudaFreeHost(ctx->hbuf);
@@ -1415,26 +1625,50 @@ gbi_status gbi_batch_solve(gbi_ctx* ctx, const gbi_params* prm, int nsys, const 
   gbi_info* inf = info ? info : &local;
   *inf = gbi_info{};
   if (nsys == 0) return GBI_OK;
-  if (offsets_host[0] != 0) return GBI_ERR_ARG;
-  for (int q = 0; q < nsys; ++q)
-    if (offsets_host[q + 1] < offsets_host[q]) return GBI_ERR_ARG;
+  if (!valid_offsets(nsys, offsets_host)) return GBI_ERR_ARG;
   const int N = offsets_host[nsys];
   if (N == 0) return GBI_OK;
   if (!R || !Va || !Oa || !VH || !Fe || !Te || !V || !Omega || (warm_start && !QH)) return GBI_ERR_ARG;
-  GBI_TRY(ensure(ctx, ctx->boff, sizeof(int) * (size_t)(nsys + 1)));
-  GBI_TRY(ensure(ctx, ctx->bsys, sizeof(int) * (size_t)N));
-  GBI_CHECK(cudaMemcpyAsync(ctx->boff.p, offsets_host, sizeof(int) * (size_t)(nsys + 1), cudaMemcpyHostToDevice,
-                            ctx->stream));
-  k_fill_sys<<<nsys, 256, 0, ctx->stream>>>(nsys, P<int>(ctx->boff), P<int>(ctx->bsys));
+  Batch B;
+  GBI_TRY(make_batch(ctx, nsys, offsets_host, B));
+  return solve_core(ctx, prm, B, R, Va, Oa, VH, Fe, Te, V, Omega, QH, warm_start, inf);
+}
+
+gbi_status gbi_batch_superpose(gbi_ctx* ctx, const gbi_params* prm, int nsys, const int* offsets_host,
+                               const double* R, const double* Va, const double* Oa, const double* VH,
+                               const double* Fe, const double* Te, double* V, double* Omega) {
+  if (!ctx || !valid_params(prm) || nsys < 0 || (nsys > 0 && !offsets_host)) return GBI_ERR_ARG;
+  if (nsys == 0) return GBI_OK;
+  if (!valid_offsets(nsys, offsets_host)) return GBI_ERR_ARG;
+  const int N = offsets_host[nsys];
+  if (N == 0) return GBI_OK;
+  if (!R || !Va || !Oa || !VH || !Fe || !Te || !V || !Omega) return GBI_ERR_ARG;
+  Batch B;
+  GBI_TRY(make_batch(ctx, nsys, offsets_host, B));
+  Setup s;
+  GBI_TRY(setup_call(ctx, s, N, prm->trunc, prm->a, prm->eta, R));
+  const int D = s.D, h = s.h;
+  const size_t nh = (size_t)N * h;
+  GBI_TRY(ensure(ctx, ctx->xQ, sizeof(double) * (size_t)N * D));
+  GBI_TRY(ensure(ctx, ctx->xVL, sizeof(double) * 6 * N));
+  double* xF = P<double>(ctx->xQ);
+  double* xQH = P<double>(ctx->xQ) + (size_t)6 * N;
+  Scales oneb;   // one-body Q^H = -8 pi eta a V^H / g, in internal coordinates
+  for (int i = 0; i < 54; ++i) oneb.v[i] = (i < h) ? s.scale.v[6 + i] * s.a / s.selfg.v[6 + i] : 1.0;
+  k_pack_lower<<<grid1(N), 256, 0, ctx->stream>>>(N, s.a, s.scale.v[3], Fe, Te, xF);
+  ++ctx->launches;
+  k_pack_higher<<<grid1(nh), 256, 0, ctx->stream>>>(N, h, VH, oneb, -8.0 * kPi * s.eta, xQH);
+  ++ctx->launches;
+  PairArgs p = pair_args(s, P<double>(ctx->xQ), P<double>(ctx->xVL), -1.0 / (8.0 * kPi * s.eta), 0.0, 1, s.ones,
+                         0);
+  p.sys_of = B.sys;
+  p.sys_off = B.off;
+  GBI_CHECK(run_pairs(ctx, s.trunc, SET_L, SET_ALL, prm->precision, p));
+  k_finalize_lower<<<grid1(N), 256, 0, ctx->stream>>>(N, s.a, s.scale.v[3], P<double>(ctx->xVL), Va, Oa, V,
+                                                      Omega);
   ++ctx->launches;
   GBI_CHECK(cudaGetLastError());
-  Batch B;
-  B.S = nsys;
-  B.Ntot = N;
-  B.off = P<int>(ctx->boff);
-  B.sys = P<int>(ctx->bsys);
-  B.h_off.assign(offsets_host, offsets_host + nsys + 1);
-  return solve_core(ctx, prm, B, R, Va, Oa, VH, Fe, Te, V, Omega, QH, warm_start, inf);
+  return GBI_OK;
 }
 
 gbi_status gbi_superpose(gbi_ctx* ctx, const gbi_params* prm, int N, const double* R, const double* Va,
@@ -1571,6 +1805,220 @@ int gbi_pass_wpt(gbi_ctx* ctx, int trunc, int rows, int cols, int precision, int
   return stream_wpt(trunc, precision, N, req);
 }
 
+gbi_status gbi_pairs(gbi_ctx* ctx, int N, const double* R, double a, double rcut, int nsys, const int* offsets_host,
+                     int* npairs) {
+  if (!ctx || N < 0 || !(a > 0) || !(rcut > 0) || nsys < 0 || (nsys > 1 && !offsets_host)) return GBI_ERR_ARG;
+  if (nsys > 1 && (!valid_offsets(nsys, offsets_host) || offsets_host[nsys] != N)) return GBI_ERR_ARG;
+  if (N == 0) {
+    ctx->nb_pairs = 0;
+    if (npairs) *npairs = 0;
+    return GBI_OK;
+  }
+  if (!R) return GBI_ERR_ARG;
+  int np_ = 0;
+  GBI_TRY(build_pairs(ctx, N, R, a, rcut, nsys, offsets_host, np_));
+  if (npairs) *npairs = np_;
+  return GBI_OK;
+}
+
+gbi_status gbi_pairs_get(gbi_ctx* ctx, int* tg, int* sr) {
+  if (!ctx) return GBI_ERR_ARG;
+  if (ctx->nb_pairs == 0) return GBI_OK;
+  if (!tg || !sr) return GBI_ERR_ARG;
+  GBI_CHECK(cudaMemcpyAsync(tg, ctx->nb_tg.p, sizeof(int) * (size_t)ctx->nb_pairs, cudaMemcpyDeviceToDevice,
+                            ctx->stream));
+  GBI_CHECK(cudaMemcpyAsync(sr, ctx->nb_sr.p, sizeof(int) * (size_t)ctx->nb_pairs, cudaMemcpyDeviceToDevice,
+                            ctx->stream));
+  return GBI_OK;
+}
+
+gbi_status gbi_mlp_set(gbi_ctx* ctx, const float* theta_host, double sigma) {
+  if (!ctx || !theta_host || !(sigma > 0)) return GBI_ERR_ARG;
+  const size_t nb = sizeof(float) * mlpk::NPARAM;
+  GBI_TRY(ensure(ctx, ctx->mlp_th, nb));
+  GBI_TRY(ensure(ctx, ctx->mlp_m, nb));
+  GBI_TRY(ensure(ctx, ctx->mlp_v, nb));
+  GBI_TRY(ensure(ctx, ctx->mlp_thq, nb));
+  GBI_TRY(ensure(ctx, ctx->mlp_grad, nb));
+  GBI_TRY(ensure(ctx, ctx->mlp_pk, mlpk::packed_bytes()));
+  GBI_CHECK(cudaMemcpyAsync(ctx->mlp_th.p, theta_host, nb, cudaMemcpyHostToDevice, ctx->stream));
+  GBI_CHECK(cudaMemsetAsync(ctx->mlp_m.p, 0, nb, ctx->stream));
+  GBI_CHECK(cudaMemsetAsync(ctx->mlp_v.p, 0, nb, ctx->stream));
+  GBI_CHECK(mlpk::pack_weights(P<float>(ctx->mlp_th), P<float>(ctx->mlp_thq), ctx->mlp_pk.p, ctx->stream));
+  ++ctx->launches;
+  GBI_CHECK(cudaStreamSynchronize(ctx->stream));   // theta_host may be reused by the caller
+  ctx->mlp_sigma = sigma;
+  ctx->mlp_step = 0;
+  ctx->mlp_ready = true;
+  return GBI_OK;
+}
+
+gbi_status gbi_mlp_get(gbi_ctx* ctx, float* theta_host, double* sigma) {
+  if (!ctx || !theta_host) return GBI_ERR_ARG;
+  GBI_TRY(mlp_require(ctx));
+  GBI_CHECK(cudaMemcpyAsync(theta_host, ctx->mlp_th.p, sizeof(float) * mlpk::NPARAM, cudaMemcpyDeviceToHost,
+                            ctx->stream));
+  GBI_CHECK(cudaStreamSynchronize(ctx->stream));
+  if (sigma) *sigma = ctx->mlp_sigma;
+  return GBI_OK;
+}
+
+gbi_status gbi_mlp_features(gbi_ctx* ctx, int P, const double* R, const double* p, const int* tg, const int* sr,
+                            double a, float* F, float* FR) {
+  if (!ctx || P < 0 || !(a > 0)) return GBI_ERR_ARG;
+  if (P == 0) return GBI_OK;
+  if (!R || !p || !tg || !sr || !F || !FR) return GBI_ERR_ARG;
+  GBI_CHECK(mlpk::features(P, R, p, tg, sr, a, F, FR, ctx->stream));
+  ++ctx->launches;
+  return GBI_OK;
+}
+
+gbi_status gbi_mlp_forward(gbi_ctx* ctx, int P, const float* F, const float* FR, float* out) {
+  if (!ctx || P < 0) return GBI_ERR_ARG;
+  GBI_TRY(mlp_require(ctx));
+  if (P == 0) return GBI_OK;
+  if (!F || !out) return GBI_ERR_ARG;
+  GBI_CHECK(mlpk::infer(P, F, FR, ctx->mlp_pk.p, out, sm_count(ctx), ctx->stream));
+  ++ctx->launches;
+  return GBI_OK;
+}
+
+gbi_status gbi_mlp_correct(gbi_ctx* ctx, int N, const double* R, const double* p, double a, double s0, int nsys,
+                           const int* offsets_host, double* V, double* Omega, int* npairs) {
+  if (!ctx || N < 0 || !(a > 0) || nsys < 0 || (nsys > 1 && !offsets_host)) return GBI_ERR_ARG;
+  if (nsys > 1 && (!valid_offsets(nsys, offsets_host) || offsets_host[nsys] != N)) return GBI_ERR_ARG;
+  GBI_TRY(mlp_require(ctx));
+  if (npairs) *npairs = 0;
+  if (N == 0) return GBI_OK;
+  if (!R || !p || !V || !Omega) return GBI_ERR_ARG;
+  int np_ = 0;
+  GBI_TRY(mlp_prepare(ctx, N, R, p, a, nsys, offsets_host, np_));
+  GBI_CHECK(mlpk::infer(np_, P<float>(ctx->mf_F), P<float>(ctx->mf_FR), ctx->mlp_pk.p, P<float>(ctx->mf_lab),
+                        sm_count(ctx), ctx->stream));
+  GBI_CHECK(mlpk::sphere_sums(N, P<int>(ctx->nb_start), P<float>(ctx->mf_lab), s0 / ctx->mlp_sigma, V, Omega,
+                              ctx->stream));
+  ctx->launches += 2;
+  if (npairs) *npairs = np_;
+  return GBI_OK;
+}
+
+gbi_status gbi_mlp_loss_grad(gbi_ctx* ctx, int N, const double* R, const double* p, double a, int nsys,
+                             const int* offsets_host, const double* labels, double* loss, float* grad) {
+  if (!ctx || N <= 0 || !(a > 0) || nsys < 0 || (nsys > 1 && !offsets_host)) return GBI_ERR_ARG;
+  if (nsys > 1 && (!valid_offsets(nsys, offsets_host) || offsets_host[nsys] != N)) return GBI_ERR_ARG;
+  if (!R || !p || !labels || !loss || !grad) return GBI_ERR_ARG;
+  GBI_TRY(mlp_require(ctx));
+  int np_ = 0;
+  GBI_TRY(mlp_prepare(ctx, N, R, p, a, nsys, offsets_host, np_));
+  const size_t n = (size_t)std::max(np_, 1);
+  GBI_TRY(ensure(ctx, ctx->mf_dO, sizeof(float) * 6 * n));
+  GBI_TRY(ensure(ctx, ctx->mf_part, sizeof(float) * std::max<size_t>(mlpk::train_part_floats(np_), 1)));
+  const int nlb = (N + 127) / 128;
+  GBI_TRY(ensure(ctx, ctx->mf_loss, sizeof(double) * (size_t)(nlb + 1)));
+  GBI_CHECK(mlpk::train_batch(P<float>(ctx->mlp_thq), P<float>(ctx->mf_F), P<float>(ctx->mf_FR),
+                              P<int>(ctx->nb_start), labels, 0, np_, 0, N, N, P<float>(ctx->mf_lab),
+                              P<float>(ctx->mf_dO), P<float>(ctx->mf_part), P<double>(ctx->mf_loss), grad,
+                              ctx->stream));
+  GBI_CHECK(mlpk::sum_into(P<double>(ctx->mf_loss), nlb, P<double>(ctx->mf_loss) + nlb, ctx->stream));
+  ctx->launches += 5;
+  GBI_CHECK(cudaMemcpyAsync(loss, P<double>(ctx->mf_loss) + nlb, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  GBI_CHECK(cudaStreamSynchronize(ctx->stream));
+  return GBI_OK;
+}
+
+gbi_status gbi_mlp_adam(gbi_ctx* ctx, const float* grad, double lr) {
+  if (!ctx || !grad || !(lr >= 0)) return GBI_ERR_ARG;
+  GBI_TRY(mlp_require(ctx));
+  ++ctx->mlp_step;
+  GBI_CHECK(mlpk::adam(P<float>(ctx->mlp_th), P<float>(ctx->mlp_m), P<float>(ctx->mlp_v), grad, ctx->mlp_step, lr,
+                       P<float>(ctx->mlp_thq), ctx->mlp_pk.p, ctx->stream));
+  ctx->launches += 2;
+  return GBI_OK;
+}
+
+gbi_status gbi_mlp_labels(gbi_ctx* ctx, int N, double s0, const double* Vx, const double* Ox, const double* Vs,
+                          const double* Os, double* sigma, double* labels) {
+  if (!ctx || N <= 0 || !(s0 != 0) || !Vx || !Ox || !Vs || !Os || !sigma || !labels) return GBI_ERR_ARG;
+  if (!(*sigma > 0)) {
+    // sigma = the power of two nearest to 1 / rms of (exact - superposition) / s0
+    const int nb = (N + 255) / 256;
+    GBI_TRY(ensure(ctx, ctx->mf_loss, sizeof(double) * (size_t)(nb + 1)));
+    GBI_CHECK(mlpk::labels(N, s0, 1.0, Vx, Ox, Vs, Os, nullptr, P<double>(ctx->mf_loss), ctx->stream));
+    GBI_CHECK(mlpk::sum_into(P<double>(ctx->mf_loss), nb, P<double>(ctx->mf_loss) + nb, ctx->stream));
+    ctx->launches += 2;
+    double sq = 0.0;
+    GBI_CHECK(cudaMemcpyAsync(&sq, P<double>(ctx->mf_loss) + nb, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    GBI_CHECK(cudaStreamSynchronize(ctx->stream));
+    const double rms = std::sqrt(sq / (6.0 * N));
+    if (!(rms > 0)) return GBI_ERR_ARG;
+    *sigma = std::ldexp(1.0, (int)std::lround(-std::log2(rms)));
+  }
+  GBI_CHECK(mlpk::labels(N, s0, *sigma, Vx, Ox, Vs, Os, labels, nullptr, ctx->stream));
+  ++ctx->launches;
+  return GBI_OK;
+}
+
+gbi_status gbi_mlp_train(gbi_ctx* ctx, int N, const double* R, const double* p, double a, int nsys,
+                         const int* offsets_host, const double* labels, int epochs, int batch_systems, double lr0,
+                         double lr1, double* loss_hist) {
+  if (!ctx || N <= 0 || !(a > 0) || nsys < 1 || !offsets_host || epochs < 0 || batch_systems < 1 || !(lr0 > 0) ||
+      !(lr1 > 0))
+    return GBI_ERR_ARG;
+  if (!valid_offsets(nsys, offsets_host) || offsets_host[nsys] != N) return GBI_ERR_ARG;
+  if (!R || !p || !labels) return GBI_ERR_ARG;
+  GBI_TRY(mlp_require(ctx));
+  int np_ = 0;
+  GBI_TRY(mlp_prepare(ctx, N, R, p, a, nsys, offsets_host, np_));
+  std::vector<int> hstart(N + 1);
+  GBI_CHECK(cudaMemcpyAsync(hstart.data(), ctx->nb_start.p, sizeof(int) * (size_t)(N + 1), cudaMemcpyDeviceToHost,
+                            ctx->stream));
+  GBI_CHECK(cudaStreamSynchronize(ctx->stream));
+  const int nbatch = (nsys + batch_systems - 1) / batch_systems;
+  int max_pairs = 1, max_spheres = 1;
+  for (int b = 0; b < nbatch; ++b) {
+    const int s0 = b * batch_systems, s1 = std::min(nsys, s0 + batch_systems);
+    max_pairs = std::max(max_pairs, hstart[offsets_host[s1]] - hstart[offsets_host[s0]]);
+    max_spheres = std::max(max_spheres, offsets_host[s1] - offsets_host[s0]);
+  }
+  const size_t n = (size_t)std::max(np_, 1);
+  GBI_TRY(ensure(ctx, ctx->mf_dO, sizeof(float) * 6 * n));
+  GBI_TRY(ensure(ctx, ctx->mf_part, sizeof(float) * mlpk::train_part_floats(max_pairs)));
+  const int nlb = (max_spheres + 127) / 128;
+  GBI_TRY(ensure(ctx, ctx->mf_loss, sizeof(double) * (size_t)(nlb + nbatch)));
+  double* lpart = P<double>(ctx->mf_loss);
+  double* lstep = lpart + nlb;
+  const long long total_steps = (long long)epochs * nbatch;
+  long long step = 0;
+  std::vector<double> hl(nbatch);
+  for (int e = 0; e < epochs; ++e) {
+    for (int b = 0; b < nbatch; ++b, ++step) {
+      const int s0 = b * batch_systems, s1 = std::min(nsys, s0 + batch_systems);
+      const int n0 = offsets_host[s0], n1 = offsets_host[s1];
+      GBI_CHECK(mlpk::train_batch(P<float>(ctx->mlp_thq), P<float>(ctx->mf_F), P<float>(ctx->mf_FR),
+                                  P<int>(ctx->nb_start), labels, hstart[n0], hstart[n1], n0, n1, n1 - n0,
+                                  P<float>(ctx->mf_lab), P<float>(ctx->mf_dO), P<float>(ctx->mf_part), lpart,
+                                  P<float>(ctx->mlp_grad), ctx->stream));
+      GBI_CHECK(mlpk::sum_into(lpart, (n1 - n0 + 127) / 128, lstep + b, ctx->stream));
+      // learning rate: geometric from lr0 to lr1 over all steps
+      const double frac = total_steps > 1 ? double(step) / double(total_steps - 1) : 0.0;
+      const double lr = lr0 * std::pow(lr1 / lr0, frac);
+      ++ctx->mlp_step;
+      GBI_CHECK(mlpk::adam(P<float>(ctx->mlp_th), P<float>(ctx->mlp_m), P<float>(ctx->mlp_v),
+                           P<float>(ctx->mlp_grad), ctx->mlp_step, lr, P<float>(ctx->mlp_thq), ctx->mlp_pk.p,
+                           ctx->stream));
+      ctx->launches += 7;
+    }
+    GBI_CHECK(cudaMemcpyAsync(hl.data(), lstep, sizeof(double) * nbatch, cudaMemcpyDeviceToHost, ctx->stream));
+    GBI_CHECK(cudaStreamSynchronize(ctx->stream));
+    if (loss_hist) {
+      double acc = 0.0;
+      for (double v : hl) acc += v;
+      loss_hist[e] = acc / nbatch;
+    }
+  }
+  return GBI_OK;
+}
+
 gbi_status gbi_set_profiling(gbi_ctx* ctx, int on) {
   if (!ctx) return GBI_ERR_ARG;
   drain_profile(ctx);
@@ -1667,7 +2115,8 @@ constexpr size_t kOffMin = kOffDots + al256(sizeof(double) * (2 * kMaxRestart + 
 constexpr size_t kOffX32 = kOffMin + 256;
 constexpr size_t kOffGs = kOffX32 + al256(sizeof(float) * 2 * (kStaticMaxND + 3 * kStaticMaxN));
 constexpr size_t kOffBoff = kOffGs + al256(sizeof(double) * (64 + (kStaticMaxRestart + 1) * kStaticMaxRestart +
-                                                              8 * (kStaticMaxRestart + 1)));
+                                                              8 * (kStaticMaxRestart + 1) +
+                                                              48 * (2 * (kStaticMaxRestart + 1) + 1)));
 constexpr size_t kOffBsys = kOffBoff + 256;
 constexpr size_t kStaticBytes = kOffBsys + al256(sizeof(int) * kStaticMaxN);
 
@@ -1703,6 +2152,7 @@ extern "C" gbi_status gbi_solve_static(void* stream, const gbi_params* prm, int 
   c.stream = reinterpret_cast<cudaStream_t>(stream);
   c.hbuf = g_static_scalars;
   c.allow_graphs = false;      // graph instantiation could allocate
+  c.fixed = true;
   auto bind = [&](Buf& b, size_t off, size_t bytes) {
     b.p = base + off;
     b.bytes = bytes;

@@ -101,6 +101,41 @@ cudaError_t launch_trap(const TrapArgs& args, int precision, void* scratch, cuda
 size_t trap_scratch_bytes(int N, int precision);
 int trap_splits(int N);
 
+// Learned near-field correction (mlp_kernel.cu).  Layout and definitions: gbi.h.
+namespace mlpk {
+constexpr int NIN = 9, NH = 128, NOUT = 6;
+constexpr int NPARAM = NH * NIN + NH + 2 * (NH * NH + NH) + NOUT * NH + NOUT;   // 35078
+size_t scan_scratch_ints(int n);
+cudaError_t exclusive_scan(const int* in, int* out, int n, int* scratch, cudaStream_t st);
+cudaError_t bbox(int N, const double* R, double* part_dev, double* out_host, cudaStream_t st);
+cudaError_t nb_count_sys(int N, const double* R, const int* sys_of, const int* sys_off, double rc2, int* cnt,
+                         cudaStream_t st);
+cudaError_t nb_fill_sys(int N, const double* R, const int* sys_of, const int* sys_off, double rc2, const int* start,
+                        int* tg, int* sr, cudaStream_t st);
+cudaError_t cells_build(int N, const double* R, const double* box, double side, int* dims, int* cell_of,
+                        int* cell_cnt, int* cell_start, int* cell_fill, int* items, int* scratch, cudaStream_t st);
+cudaError_t nb_cells(int N, const double* R, const double* box, double side, const int* dims, const int* cell_of,
+                     const int* cell_start, const int* cell_cnt, const int* items, double rc2, const int* start,
+                     int* cnt, int* tg, int* sr, int* overflow, cudaStream_t st);
+cudaError_t features(int P, const double* R, const double* p, const int* tg, const int* sr, double a, float* F,
+                     float* FR, cudaStream_t st);
+size_t packed_bytes();
+cudaError_t pack_weights(const float* theta, float* thq, void* packed, cudaStream_t st);
+cudaError_t infer(int P, const float* F, const float* FR, const void* packed, float* out, int num_sms,
+                  cudaStream_t st);
+cudaError_t sphere_sums(int N, const int* start, const float* lab, double scale, double* V, double* Om,
+                        cudaStream_t st);
+size_t train_part_floats(int max_pairs);
+cudaError_t train_batch(const float* thq, const float* F, const float* FR, const int* start, const double* labels,
+                        int p_begin, int p_end, int n_begin, int n_end, int ns_total, float* lab, float* dO,
+                        float* part, double* loss_part, float* grad, cudaStream_t st);
+cudaError_t adam(float* th, float* m, float* v, const float* g, int t, double lr, float* thq, void* packed,
+                 cudaStream_t st);
+cudaError_t sum_into(const double* parts, int n, double* dst, cudaStream_t st);
+cudaError_t labels(int N, double s0, double sigma, const double* Vx, const double* Ox, const double* Vs,
+                   const double* Os, double* out, double* sq_part, cudaStream_t st);
+}  // namespace mlpk
+
 // Flop counts per ordered pair used for the roofline accounting.
 double pair_flops(int trunc, int rows, int cols);
 double trap_flops();

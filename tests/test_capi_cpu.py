@@ -60,6 +60,20 @@ def test_tuning_calls_validate_without_a_device(gbi):
     assert L.gbi_pass_wpt(None, 2, 2, 2, 1, 100, 0) == -1
 
 
+def test_nearfield_calls_validate_without_a_device(gbi):
+    import ctypes
+    import numpy as np
+    from paper_1411_0278_gb300 import nearfield
+    L = gbi.lib()
+    th = nearfield.init_theta(0)
+    assert th.size == gbi._native.MLP_NPARAM and th.dtype == np.float32
+    assert L.gbi_mlp_set(None, th.ctypes.data, 1.0) == gbi.GBI_ERR_ARG
+    assert L.gbi_mlp_forward(None, 1, None, None, None) == gbi.GBI_ERR_ARG
+    n = ctypes.c_int()
+    assert L.gbi_pairs(None, 10, None, 1.0, 4.0, 0, None, ctypes.byref(n)) == gbi.GBI_ERR_ARG
+    assert L.gbi_mlp_train(None, 10, None, None, 1.0, 1, None, None, 1, 1, 1e-3, 1e-4, None) == gbi.GBI_ERR_ARG
+
+
 def test_generated_tables_agree_with_oracle(gbi):
     from oracle import galerkin, tensors
     for trunc in (2, 3, 4):

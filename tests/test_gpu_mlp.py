@@ -1,0 +1,219 @@
+"""Learned near-field correction on the GPU against the FP64 oracle (oracle/mlp.py).
+
+* neighbour lists: the exact set of pairs closer than rcut a (integer work: bit-exact);
+* features: FP32 against FP64, 2e-5 absolute;
+* tensor-core inference: the oracle multiplies the same bf16-rounded weights and layer
+  inputs in FP64; a rounding decision of an activation can still differ by one bf16
+  step (2^-8 relative), so outputs agree to 1e-2 of their largest magnitude;
+* training gradient (FP32 CUDA cores) against the oracle's backpropagation: 2e-2 in
+  relative 2-norm (same bf16 argument); Adam step: FP32 against FP64, 1e-5;
+* labels: the batched l <= 4 solve per system against single solves, and the batched
+  superposition against the single-system one;
+* the trained network reduces the error of the superposition approximation against
+  the plain l <= 4 solve, on held-out systems and on a dense suspension.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import workloads
+from oracle import mlp as omlp
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gbi():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1411_0278_gb300 as g
+    g.lib()
+    return g
+
+
+@pytest.fixture()
+def ctx(gbi):
+    c = gbi.Context(0)
+    yield c
+    c.close()
+
+
+def dev(a, dtype=torch.float64):
+    return torch.tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def brute_pairs(R, rc, offsets=None):
+    """Plain definition, vectorised: (dx dx + dy dy) + dz dz < rc^2, sorted by (n, m)."""
+    N = len(R)
+    offsets = [0, N] if offsets is None else offsets
+    tg, sr = [], []
+    for s in range(len(offsets) - 1):
+        lo, hi = offsets[s], offsets[s + 1]
+        X = R[lo:hi]
+        d = X[:, None, :] - X[None, :, :]
+        d2 = (d[..., 0] * d[..., 0] + d[..., 1] * d[..., 1]) + d[..., 2] * d[..., 2]
+        np.fill_diagonal(d2, np.inf)
+        n, m = np.nonzero(d2 < rc * rc)
+        tg.append(n + lo)
+        sr.append(m + lo)
+    return np.concatenate(tg), np.concatenate(sr)
+
+
+@pytest.mark.parametrize("N,phi,cells", [(300, 0.1, False), (6000, 0.1, True), (5000, 0.02, True)])
+def test_pairs_exact_set(ctx, gbi, N, phi, cells):
+    s = workloads.suspension(N, phi, 2.05, workloads.SEED_BASE + 500 + N)
+    R = s["R"] + np.array([1.0e3, -2.0e3, 5.0])
+    tg, sr = ctx.pairs(dev(R), 1.0, 4.0)
+    bt, bs = brute_pairs(R, 4.0)
+    assert len(bt) > N
+    np.testing.assert_array_equal(tg.cpu().numpy(), bt)
+    np.testing.assert_array_equal(sr.cpu().numpy(), bs)
+
+
+def test_pairs_batched_systems(ctx, gbi):
+    d = workloads.nearfield_systems(40, 60, k=1)
+    tg, sr = ctx.pairs(dev(d["R"]), 1.0, 4.0, d["offsets"])
+    bt, bs = brute_pairs(d["R"], 4.0, d["offsets"])
+    np.testing.assert_array_equal(tg.cpu().numpy(), bt)
+    np.testing.assert_array_equal(sr.cpu().numpy(), bs)
+    t2, s2 = omlp.pair_list(d["R"][:50], 1.0, [o for o in d["offsets"] if o <= 50])
+    np.testing.assert_array_equal(tg.cpu().numpy()[:len(t2)], t2)
+
+
+def _random_pairs(P, seed):
+    rng = np.random.default_rng(seed)
+    R = rng.uniform(-20, 20, size=(2 * P, 3))
+    R[1::2] = R[0::2] + workloads.unit_vectors(P, rng) * rng.uniform(2.0, 4.0, size=(P, 1))
+    p = workloads.unit_vectors(2 * P, rng)
+    if P > 2:
+        p[4] = (R[4] - R[5]) / np.linalg.norm(R[4] - R[5])      # p_n along the axis: p_m branch
+    tg = np.arange(0, 2 * P, 2)
+    sr = tg + 1
+    return R, p, tg, sr
+
+
+def test_features_match_oracle(ctx, gbi):
+    R, p, tg, sr = _random_pairs(700, 3)
+    F, FR = ctx.mlp_features(dev(R), dev(p), dev(tg, torch.int32), dev(sr, torch.int32), 1.0)
+    Fo, FRo = omlp.features_for_pairs(R, p, 1.0, tg, sr)
+    np.testing.assert_allclose(F.cpu().numpy(), Fo, atol=2e-5, rtol=0)
+    np.testing.assert_allclose(FR.cpu().numpy().reshape(-1, 3, 3), FRo, atol=2e-5, rtol=0)
+
+
+@pytest.mark.parametrize("P", [1, 63, 64, 1000])
+def test_tensor_core_forward_matches_oracle(ctx, gbi, P):
+    from paper_1411_0278_gb300 import nearfield
+    th = nearfield.init_theta(7)
+    th[omlp.NPARAM - 6:] = [0.1, -0.2, 0.3, 0.0, 0.05, -0.05]
+    ctx.mlp_set(th, 4.0)
+    R, p, tg, sr = _random_pairs(P, 5 + P)
+    Fo, FRo = omlp.features_for_pairs(R, p, 1.0, tg, sr)
+    Fd = dev(Fo, torch.float32)
+    out = ctx.mlp_forward(Fd).cpu().numpy()
+    ref, _ = omlp.forward(th.astype(np.float64), Fo.astype(np.float32).astype(np.float64), bf16=True)
+    scale = np.abs(ref).max()
+    assert np.abs(out - ref).max() <= 1e-2 * scale
+    lab = ctx.mlp_forward(Fd, dev(FRo.reshape(-1, 9), torch.float32)).cpu().numpy()
+    np.testing.assert_allclose(lab, omlp.rotate_out(ref, FRo), atol=1e-2 * scale, rtol=0)
+
+
+def test_training_gradient_matches_oracle(ctx, gbi):
+    from paper_1411_0278_gb300 import nearfield
+    d = workloads.nearfield_systems(30, 50, k=2)
+    th = nearfield.init_theta(11)
+    ctx.mlp_set(th, 2.0)
+    rng = np.random.default_rng(4)
+    labels = rng.normal(size=(len(d["R"]), 6))
+    loss, g = ctx.mlp_loss_grad(dev(d["R"]), dev(d["p"]), 1.0, dev(labels), d["offsets"])
+    tg, sr = omlp.pair_list(d["R"], 1.0, d["offsets"])
+    F, FR = omlp.features_for_pairs(d["R"], d["p"], 1.0, tg, sr)
+    lo, go = omlp.loss_and_grad(th.astype(np.float64), F, FR, tg, labels, bf16=True)
+    assert abs(loss - lo) <= 2e-3 * lo
+    g = g.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(g - go) <= 2e-2 * np.linalg.norm(go)
+    for name, shp in omlp.SHAPES:      # every block of the layout carries gradient
+        k0 = sum(int(np.prod(s)) for n_, s in omlp.SHAPES[:[n for n, _ in omlp.SHAPES].index(name)])
+        blk = slice(k0, k0 + int(np.prod(shp)))
+        assert np.linalg.norm(g[blk] - go[blk]) <= 5e-2 * np.linalg.norm(go[blk]), name
+
+
+def test_adam_matches_oracle(ctx, gbi):
+    from paper_1411_0278_gb300 import nearfield
+    th = nearfield.init_theta(3)
+    ctx.mlp_set(th, 1.0)
+    rng = np.random.default_rng(8)
+    g1, g2 = rng.normal(size=omlp.NPARAM), rng.normal(size=omlp.NPARAM)
+    ctx.mlp_adam(dev(g1, torch.float32), 1e-3)
+    ctx.mlp_adam(dev(g2, torch.float32), 5e-4)
+    got, sig = ctx.mlp_get()
+    assert sig == 1.0
+    t = th.astype(np.float64)
+    m = np.zeros_like(t)
+    v = np.zeros_like(t)
+    t, m, v = omlp.adam_step(t, g1.astype(np.float32).astype(np.float64), m, v, 1, 1e-3)
+    t, m, v = omlp.adam_step(t, g2.astype(np.float32).astype(np.float64), m, v, 2, 5e-4)
+    np.testing.assert_allclose(got, t, atol=1e-6, rtol=1e-5)
+
+
+def test_correct_adds_scaled_sums(ctx, gbi):
+    from paper_1411_0278_gb300 import nearfield
+    s = workloads.suspension(400, 0.1, 2.05, workloads.SEED_BASE + 77)
+    th = nearfield.init_theta(5)
+    ctx.mlp_set(th, 8.0)
+    R, p = dev(s["R"]), dev(s["p"])
+    V0 = torch.randn(400, 3, dtype=torch.float64, device="cuda")
+    O0 = torch.randn(400, 3, dtype=torch.float64, device="cuda")
+    V, O = V0.clone(), O0.clone()
+    npairs = ctx.mlp_correct(R, p, 1.0, 0.05, V, O)
+    tg, sr = omlp.pair_list(s["R"], 1.0)
+    assert npairs == len(tg)
+    F, FR = omlp.features_for_pairs(s["R"], s["p"], 1.0, tg, sr)
+    pred = omlp.predict(th.astype(np.float64), F, FR, tg, 400, bf16=True) * (0.05 / 8.0)
+    got = np.concatenate([(V - V0).cpu().numpy(), (O - O0).cpu().numpy()], axis=1)
+    assert np.abs(got - pred).max() <= 1e-2 * np.abs(pred).max()
+
+
+def test_batched_labels_match_single_system_calls(ctx, gbi):
+    """Label inputs: batched l <= 4 solve and l <= 2 superposition per system = single calls."""
+    from paper_1411_0278_gb300 import nearfield
+    d = workloads.nearfield_systems(3, 4, k=3)
+    R, p = dev(d["R"]), dev(d["p"])
+    Vx, Ox, Vs, Os, _ = nearfield.exact_and_superposition(ctx, R, p, d["offsets"], 1.0, d["eta"], d["vs"], d["s0"])
+    prm4 = gbi.params(a=1.0, eta=d["eta"], trunc=4, precision=0, rtol=1e-12, restart=60)
+    prm2 = gbi.params(a=1.0, eta=d["eta"], trunc=2, precision=0)
+    for s in range(len(d["offsets"]) - 1):
+        lo, hi = d["offsets"][s], d["offsets"][s + 1]
+        Rs, ps = R[lo:hi].contiguous(), p[lo:hi].contiguous()
+        i4 = ctx.trap_inputs(hi - lo, 4, 0.0, d["vs"], d["s0"], 0.0, Rs, ps)
+        V, O, _, _, _ = ctx.solve(prm4, Rs, i4["Va"], i4["Oa"], i4["VH"], i4["Fe"], i4["Te"])
+        i2 = ctx.trap_inputs(hi - lo, 2, 0.0, d["vs"], d["s0"], 0.0, Rs, ps)
+        V2, O2 = ctx.superpose(prm2, Rs, i2["Va"], i2["Oa"], i2["VH"], i2["Fe"], i2["Te"])
+        torch.cuda.synchronize()
+        sc = float((V - i4["Va"]).abs().max())
+        assert float((Vx[lo:hi] - V).abs().max()) <= 1e-8 * sc
+        assert float((Ox[lo:hi] - O).abs().max()) <= 1e-8 * float(O.abs().max())
+        assert float((Vs[lo:hi] - V2).abs().max()) <= 1e-10 * sc
+        assert float((Os[lo:hi] - O2).abs().max()) <= 1e-10 * float(O2.abs().max())
+
+
+def test_trained_network_beats_superposition(ctx, gbi):
+    """Train on 2- and 3-sphere systems; on held-out systems and on a dense suspension the
+    network must cut the error of the superposition approximation against the l <= 4 solve."""
+    from paper_1411_0278_gb300 import nearfield
+    tr = workloads.nearfield_systems(3000, 3000, k=10)
+    te = workloads.nearfield_systems(300, 300, k=11)
+    a, eta, vs, s0 = 1.0, tr["eta"], tr["vs"], tr["s0"]
+    dtr = nearfield.make_dataset(ctx, dev(tr["R"]), dev(tr["p"]), tr["offsets"], a, eta, vs, s0)
+    hist = nearfield.train(ctx, dtr, epochs=40, batch_systems=256, lr0=3e-3, lr1=1e-4, seed=1)
+    assert hist[-1] < 0.5 * hist[0]
+    dte = nearfield.make_dataset(ctx, dev(te["R"]), dev(te["p"]), te["offsets"], a, eta, vs, s0,
+                                 sigma=dtr["sigma"])
+    ev = nearfield.evaluate(ctx, dte)
+    assert ev["with_network"]["V"] < 0.5 * ev["superposition"]["V"], ev
+    assert ev["with_network"]["Omega"] < 0.5 * ev["superposition"]["Omega"], ev
+    # a dense suspension (volume fraction 0.1, 2.05a exclusion) against the plain solve
+    s = workloads.suspension(300, 0.1, 2.05, workloads.SEED_BASE + 5300)
+    dsus = nearfield.make_dataset(ctx, dev(s["R"]), dev(s["p"]), [0, 300], a, eta, vs, s0, sigma=dtr["sigma"])
+    ev2 = nearfield.evaluate(ctx, dsus)
+    assert ev2["with_network"]["V"] < ev2["superposition"]["V"], ev2

@@ -15,7 +15,11 @@ Workloads (seeds 1411027800 + id):
    V^a = 0.1 p, s0 = 0.05, d0 = 0, superposition, dt = 0.05.
 4. 256 independent suspensions, N log-uniform in [32, 4096], volume fraction
    uniform in [0.01, 0.2]; RSA at 2.5 a when it fills, else a jittered cubic lattice.
-5. N = 10^5 at volume fraction 0.1 (side 161.2 a), RSA at 2.05 a.
+5. N = 10^5 at volume fraction 0.1 (side 161.2 a), RSA at 2.05 a; force- and
+   torque-free (no trap), V^a = 0.1 p, V^(2s) = 0.05 (pp - I/3).
+6. Near-field training sets: independent 2- and 3-sphere systems, every sphere
+   within [2.05 a, 4 a) of an earlier one and no two closer than 2.05 a,
+   orientations uniform (seeds 1411027800 + 6000 + k).
 
 The paper's own runs (10^4 squirmers in a trap, O(10^5) stresslet
 superposition) used PyStokes; no dataset exists, so these seeded clouds stand
@@ -144,8 +148,33 @@ def config4(nsys=256):
 
 def config5(N=100000):
     s = suspension(N, 0.1, 2.05, SEED_BASE + 5)
-    s.update(trap_params(), trunc=2, name="N100000_phi0.1")
+    s.update(trap_params(k=0.0), trunc=2, name="N%d_phi0.1_nearfield" % N)
     return s
+
+
+def nearfield_systems(n2, n3, k=0, rmin=2.05, rmax=4.0):
+    """n2 two-sphere and n3 three-sphere systems (a = 1) for the near-field network.
+
+    Sphere 0 sits at a random point of a 10 a cube; each later sphere is placed at a
+    distance uniform in [rmin, rmax) from a uniformly chosen earlier sphere, in a
+    uniform direction, and redrawn while closer than rmin to any sphere.  Returns
+    R [Ntot, 3], p [Ntot, 3] and the system offsets (2-sphere systems first)."""
+    rng = np.random.default_rng(SEED_BASE + 6000 + k)
+    Rs, offs = [], [0]
+    for sz, cnt in ((2, n2), (3, n3)):
+        for _ in range(cnt):
+            pts = [rng.uniform(-5.0, 5.0, size=3)]
+            while len(pts) < sz:
+                base = pts[rng.integers(len(pts))]
+                d = unit_vectors(1, rng)[0]
+                q = base + rng.uniform(rmin, rmax) * d
+                if all(np.linalg.norm(q - x) >= rmin for x in pts):
+                    pts.append(q)
+            Rs.extend(pts)
+            offs.append(offs[-1] + sz)
+    R = np.array(Rs)
+    p = unit_vectors(len(R), rng)
+    return dict(R=R, p=p, offsets=offs, **trap_params(k=0.0))
 
 
 def small_cloud(N, seed, phi=0.05, dmin=2.5):
