@@ -181,6 +181,105 @@ def run_reference(args):
 TUNED_PASSES = ["HH_f32", "HH_df", "HL_df", "Lall_df"]
 
 
+def learned_nearfield(ctx, gbi, dev, stream, peaks):
+    """Learned near-field correction: label generation and training on 2- and 3-sphere
+    systems, errors against the plain l <= 4 solve (held-out systems and a dense
+    2000-sphere suspension), and the N = 10^5 evaluation (superposition + network)."""
+    import time
+    import torch
+    import workloads
+    from paper_1411_0278_gb300 import nearfield
+
+    def T(x):
+        return torch.tensor(x, dtype=torch.float64, device=dev)
+
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps=1):
+        torch.cuda.synchronize(dev)
+        ev0.record(stream)
+        for _ in range(reps):
+            out = fn()
+        ev1.record(stream)
+        ev1.synchronize()
+        return out, ev0.elapsed_time(ev1) / reps
+
+    tr = workloads.nearfield_systems(100000, 100000, k=20)
+    a, eta, vs, s0 = 1.0, tr["eta"], tr["vs"], tr["s0"]
+    t0 = time.time()
+    dtr = nearfield.make_dataset(ctx, T(tr["R"]), T(tr["p"]), tr["offsets"], a, eta, vs, s0)
+    torch.cuda.synchronize(dev)
+    t_label = time.time() - t0
+    epochs = 40
+    t0 = time.time()
+    hist = nearfield.train(ctx, dtr, epochs=epochs, batch_systems=1024, lr0=3e-3, lr1=3e-5, seed=1)
+    t_train = time.time() - t0
+    te = workloads.nearfield_systems(1000, 1000, k=21)
+    dte = nearfield.make_dataset(ctx, T(te["R"]), T(te["p"]), te["offsets"], a, eta, vs, s0, sigma=dtr["sigma"])
+    held = nearfield.evaluate(ctx, dte)
+
+    # dense suspension: plain l <= 4 solve against superposition (+ network)
+    ss = workloads.suspension(2000, 0.1, 2.05, workloads.SEED_BASE + 5200)
+    Rs, ps = T(ss["R"]), T(ss["p"])
+    i4 = ctx.trap_inputs(2000, 4, 0.0, vs, s0, 0.0, Rs, ps)
+    i2 = ctx.trap_inputs(2000, 2, 0.0, vs, s0, 0.0, Rs, ps)
+    prm4 = gbi.params(a=a, eta=eta, trunc=4, precision=2, rtol=1e-10, restart=40, max_iter=2000, inner_rtol=1e-5)
+    prm2 = gbi.params(a=a, eta=eta, trunc=2, precision=1)
+    ctx.tune(4, [0, 2000])
+    (Vx, Ox, _, ix, _), ms_exact = timed(lambda: ctx.solve(prm4, Rs, i4["Va"], i4["Oa"], i4["VH"], i4["Fe"], i4["Te"]))
+
+    def learned():
+        V, O = ctx.superpose(prm2, Rs, i2["Va"], i2["Oa"], i2["VH"], i2["Fe"], i2["Te"])
+        ctx.mlp_correct(Rs, ps, a, s0, V, O)
+        return V, O
+    learned()
+    (Vl, Ol), ms_learned = timed(learned, 3)
+    Vsup, Osup = ctx.superpose(prm2, Rs, i2["Va"], i2["Oa"], i2["VH"], i2["Fe"], i2["Te"])
+    torch.cuda.synchronize(dev)
+    Va = i2["Va"]
+    dense = {"N": 2000, "superposition": dict(zip(("V", "Omega"), nearfield.relative_errors(Vsup, Osup, Vx, Ox, Va))),
+             "with_network": dict(zip(("V", "Omega"), nearfield.relative_errors(Vl, Ol, Vx, Ox, Va))),
+             "exact_ms": ms_exact, "exact_iters": ix.iters, "exact_rel_residual": ix.rel_residual,
+             "learned_ms": ms_learned, "speedup_learned_vs_exact": ms_exact / ms_learned}
+
+    # N = 10^5: superposition (closed-form l <= 2 kernel, FP32) plus the network
+    c5 = workloads.config5()
+    N5 = len(c5["R"])
+    R5, p5 = T(c5["R"]), T(c5["p"])
+    in5 = ctx.trap_inputs(N5, 2, 0.0, vs, s0, 0.0, R5, p5)
+    V5 = torch.empty((N5, 3), dtype=torch.float64, device=dev)
+    O5 = torch.empty_like(V5)
+    npairs = [0]
+
+    def full():
+        ctx.superpose(prm2, R5, in5["Va"], in5["Oa"], in5["VH"], in5["Fe"], in5["Te"], V5, O5)
+        npairs[0] = ctx.mlp_correct(R5, p5, a, s0, V5, O5)
+    full()
+    _, ms_full = timed(full, 3)
+    # the network alone on the same pairs
+    tg, sr = ctx.pairs(R5, a, 4.0)
+    F, FR = ctx.mlp_features(R5, p5, tg, sr, a)
+    ctx.mlp_forward(F, FR)
+    _, ms_net = timed(lambda: ctx.mlp_forward(F, FR), 10)
+    P = int(tg.shape[0])
+    flops_net = 2.0 * (9 * 128 + 2 * 128 * 128 + 128 * 6) * P
+    bf16_peak = peaks.get("bf16_tflops", 1900.0)
+    pairs5 = N5 * (N5 - 1) + P
+    return {"workload": c5["name"], "N": N5, "value": pairs5 / (ms_full / 1e3), "unit": UNIT,
+            "ms_per_evaluation": ms_full, "network_pairs": P,
+            "network": {"ms": ms_net, "achieved_tflops": flops_net / (ms_net / 1e3) / 1e12,
+                        "peak_bf16_tflops": bf16_peak,
+                        "frac": flops_net / (ms_net / 1e3) / 1e12 / bf16_peak,
+                        "kernel": "k_infer (mma.sync m16n8k16 bf16, FP32 accumulate)"},
+            "training": {"systems": len(tr["offsets"]) - 1, "spheres": len(tr["R"]), "label_s": t_label,
+                         "train_s": t_train, "epochs": epochs, "loss_first": hist[0], "loss_last": hist[-1],
+                         "sigma": dtr["sigma"]},
+            "heldout_2_3_body": held, "dense_suspension": dense,
+            "note": "errors are relative to the plain l<=4 Galerkin solve: ||V - Vx|| / ||Vx - Va||, "
+                    "||Omega - Ox|| / ||Ox||"}
+
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -408,6 +507,9 @@ def run_ours(args):
                "systems_per_s": n4 * len(c4["systems"]) / (b_ms / 1e3), "lockstep_iters": i4.iters,
                "rel_residual": i4.rel_residual, "tuned_wpt": dict(zip(TUNED_PASSES, tuned4))}
 
+    # ---- secondary: learned near-field correction (training, errors, N = 10^5 evaluation)
+    learned = learned_nearfield(ctx, gbi, dev, stream, load_peaks()[0])
+
     if rank == 0:
         # ---- CPU baseline: the oracle on a bounded sample, this machine's cores
         rate, dtc = oracle_pair_rate(c["R"], trunc, c["a"], 12000)
@@ -428,7 +530,7 @@ def run_ours(args):
                            "parallelism": "replicas" if world > 1 else "single GPU"},
                 "solves_per_s": solves_per_s, "error_vs_fp64": err, "roofline": roofline,
                 "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
-                "superposition": superposition, "batched": batched,
+                "superposition": superposition, "batched": batched, "learned_nearfield": learned,
                 "tuned_wpt": dict(zip(TUNED_PASSES, tuned))}
         print(json.dumps(line), flush=True)
     ctx.close()

@@ -197,7 +197,7 @@ gbi_status gbi_trap_step(gbi_ctx* ctx, const gbi_params* params, int N, double d
  * loop that forbids cudaMalloc/cudaFree, or a host that pre-plans its memory -- this
  * entry point performs the same solve as gbi_solve (same arguments and results) but
  * takes every scratch buffer from one static device array of the library (about
- * 2.6 MB, held by every GPU that loads the library until the process exits) and its
+ * 3 MB, held by every GPU that loads the library until the process exits) and its
  * read-back scalars from a static host array.  It needs no context: work is queued
  * on `stream` (a cudaStream_t, NULL = default stream) of the current device.
  * The paper has no counterpart; it is an engineering entry point.
@@ -269,6 +269,12 @@ gbi_status gbi_mlp_get(gbi_ctx* ctx, float* theta_host, double* sigma);
 gbi_status gbi_mlp_features(gbi_ctx* ctx, int P, const double* R, const double* p, const int* tg, const int* sr,
                             double a, float* F, float* FR);
 gbi_status gbi_mlp_forward(gbi_ctx* ctx, int P, const float* F, const float* FR, float* out);
+/* Inference engine of gbi_mlp_forward / gbi_mlp_correct: 0 = warp-level mma.sync
+ * m16n8k16 (64 pairs per tile), 1 = tcgen05.mma with the accumulator in tensor memory
+ * (128 pairs per tile; synchronizes the stream to read its completion status and
+ * returns GBI_ERR_TIMEOUT if an MMA completion wait gave up).  Both multiply the same
+ * bf16 values with FP32 accumulation. */
+gbi_status gbi_mlp_set_engine(gbi_ctx* ctx, int engine);
 gbi_status gbi_mlp_correct(gbi_ctx* ctx, int N, const double* R, const double* p, double a, double s0, int nsys,
                            const int* offsets_host, double* V, double* Omega, int* npairs);
 gbi_status gbi_mlp_labels(gbi_ctx* ctx, int N, double s0, const double* Vx, const double* Ox, const double* Vs,

@@ -76,6 +76,7 @@ _SIGS = {
     "gbi_mlp_get": (_I, [_VP, _VP, c_double_p]),
     "gbi_mlp_features": (_I, [_VP, _I, _VP, _VP, _VP, _VP, _D, _VP, _VP]),
     "gbi_mlp_forward": (_I, [_VP, _I, _VP, _VP, _VP]),
+    "gbi_mlp_set_engine": (_I, [_VP, _I]),
     "gbi_mlp_correct": (_I, [_VP, _I, _VP, _VP, _D, _D, _I, ctypes.POINTER(ctypes.c_int), _VP, _VP,
                              ctypes.POINTER(ctypes.c_int)]),
     "gbi_mlp_labels": (_I, [_VP, _I, _D, _VP, _VP, _VP, _VP, c_double_p, _VP]),
@@ -369,6 +370,10 @@ class Context:
         self._check(lib().gbi_mlp_forward(self._h, P, _f32(F), _f32(FR) if FR is not None else None, _f32(out)),
                     "gbi_mlp_forward")
         return out
+
+    def mlp_set_engine(self, engine):
+        """0: mma.sync inference kernel, 1: tcgen05 (tensor memory) inference kernel."""
+        self._check(lib().gbi_mlp_set_engine(self._h, int(engine)), "gbi_mlp_set_engine")
 
     def mlp_correct(self, R, p, a, s0, V, Om, offsets=None):
         nsys, offs = self._offs(offsets)

@@ -93,7 +93,8 @@ struct gbi_ctx {
   // learned near-field correction: FP32 master weights, Adam moments, bf16-rounded
   // copy (training), padded bf16 copy (inference), gradient; neighbour lists; pair
   // features, outputs and training scratch
-  Buf mlp_th, mlp_m, mlp_v, mlp_thq, mlp_pk, mlp_grad;
+  Buf mlp_th, mlp_m, mlp_v, mlp_thq, mlp_pk, mlp_grad, mlp_pk_tc, mlp_err;
+  int mlp_engine = 0;                          // inference: 0 mma.sync, 1 tcgen05
   double mlp_sigma = 0.0;
   int mlp_step = 0;
   bool mlp_ready = false;
@@ -510,7 +511,7 @@ struct GDev {
 
 struct GPtr {     // per-system views into the gstate buffer
   GDev* st;
-  double *H, *cs, *sn, *g, *y, *h1, *h2, *nrm;
+  double *H, *cs, *sn, *g, *y, *nrm;
   double *h1p, *h2p, *nrmp;   // per-chunk partial sums of the dot products and the norm
   int S, m, CH;
 };
@@ -521,7 +522,7 @@ struct GPtr {     // per-system views into the gstate buffer
 int arnoldi_chunks(int S, int h) { return S >= 64 ? 1 : h; }
 
 size_t gstate_doubles(int m, int S, int CH) {
-  return (size_t)S * (sizeof(GDev) / sizeof(double) + 1) + (size_t)S * ((size_t)(m + 1) * m + 7 * (size_t)(m + 1) + 1) +
+  return (size_t)S * (sizeof(GDev) / sizeof(double) + 1) + (size_t)S * ((size_t)(m + 1) * m + 5 * (size_t)(m + 1) + 1) +
          (size_t)S * CH * (2 * (size_t)(m + 1) + 1) + 16;
 }
 
@@ -537,49 +538,11 @@ GPtr gptrs(void* base, int m, int S, int CH) {
   p.sn = d; d += (size_t)S * (m + 1);
   p.g = d; d += (size_t)S * (m + 1);
   p.y = d; d += (size_t)S * (m + 1);
-  p.h1 = d; d += (size_t)S * (m + 1);
-  p.h2 = d; d += (size_t)S * (m + 1);
   p.nrm = d; d += (size_t)S;
   p.h1p = d; d += (size_t)S * (m + 1) * CH;
   p.h2p = d; d += (size_t)S * (m + 1) * CH;
   p.nrmp = d;
   return p;
-}
-
-// FP32 Arnoldi source as per-sphere records (PairArgs::x32): rec[p] = float(V_{j_s} *
-// minv) padded to ncp floats, for the spheres of active systems; transposed through
-// shared memory (one block per 32 spheres) so that reads and writes are coalesced.
-__global__ void bk_gather_rec(const double* __restrict__ V, size_t n, int Ntot, int h, int ncp,
-                              const int* __restrict__ sys, const GDev* __restrict__ st, Scales minv,
-                              float* __restrict__ rec) {
-  extern __shared__ float tile[];   // [32][ncp + 1]
-  const int m0 = blockIdx.x * 32;
-  const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int p = m0 + lane;
-  const GDev* g = p < Ntot ? &st[sys[p]] : nullptr;
-  const bool live = g != nullptr && g->active;
-  const double* v = live ? V + (size_t)g->j * n : nullptr;
-  for (int q = wy; q < ncp; q += nw)
-    tile[lane * (ncp + 1) + q] = (live && q < h) ? float(v[(size_t)q * Ntot + p] * minv.v[q]) : 0.f;
-  __syncthreads();
-  const int cnt = min(32, Ntot - m0);
-  for (int i = threadIdx.x; i < cnt * ncp; i += blockDim.x) {
-    const int r = i / ncp, c = i - r * ncp;
-    rec[(size_t)(m0 + r) * ncp + c] = tile[r * (ncp + 1) + c];
-  }
-}
-
-// out (FP64) = V_{j_s} * minv over the spheres of active systems (the Arnoldi source)
-template <typename O>
-__global__ void bk_gather(const double* __restrict__ V, size_t n, int Ntot, const int* __restrict__ sys,
-                          const GDev* __restrict__ st, Scales minv, O* __restrict__ out) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  const int q = blockIdx.y;
-  if (p >= Ntot) return;
-  const GDev& g = st[sys[p]];
-  if (!g.active) return;
-  const size_t t = (size_t)q * Ntot + p;
-  out[t] = O(V[(size_t)g.j * n + t] * minv.v[q]);
 }
 
 __device__ __forceinline__ double block_sum_256(double v) {
@@ -612,32 +575,45 @@ __global__ void bk_dots(const double* __restrict__ V, size_t n, const double* __
   if (threadIdx.x == 0) part[((size_t)s * (m + 1) + i) * CH + c] = t;
 }
 
-// out[s][i] = sum over the chunks (in order) of the partial dot products
-__global__ void bk_dots_sum(const double* __restrict__ part, const GDev* __restrict__ st, int m, int CH,
-                            double* __restrict__ out) {
-  const int s = blockIdx.x;
-  const GDev& g = st[s];
-  if (!g.active) return;
-  for (int i = threadIdx.x; i <= g.j; i += blockDim.x) {
-    const double* q = part + ((size_t)s * (m + 1) + i) * CH;
-    double acc = 0.0;
-    for (int c = 0; c < CH; ++c) acc += q[c];
-    out[(size_t)s * (m + 1) + i] = acc;
-  }
-}
-
-// w -= sum_{i <= j_s} coef[s][i] V_i
+// w -= sum_{i <= j_s} coef[s][i] V_i with coef[s][i] = sum over the CH chunk partials (in
+// order).  A block whose spheres all belong to one system sums the partials once into
+// shared memory; otherwise every thread sums them for its own system.
 __global__ void bk_sub(const double* __restrict__ V, size_t n, double* w, int Ntot, const int* __restrict__ sys,
-                       const GDev* __restrict__ st, int m, const double* __restrict__ coef) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+                       const GDev* __restrict__ st, int m, int CH, const double* __restrict__ part) {
+  __shared__ double sc[kMaxRestart + 1];
+  const int p0 = blockIdx.x * blockDim.x;
+  const int pl = min(Ntot - 1, p0 + (int)blockDim.x - 1);
+  const int sb = sys[p0];
+  const bool uniform = sys[pl] == sb;
+  if (uniform) {
+    const GDev& g = st[sb];
+    if (!g.active) return;
+    for (int i = threadIdx.x; i <= g.j; i += blockDim.x) {
+      const double* q = part + ((size_t)sb * (m + 1) + i) * CH;
+      double acc = 0.0;
+      for (int c = 0; c < CH; ++c) acc += q[c];
+      sc[i] = acc;
+    }
+    __syncthreads();
+  }
+  const int p = p0 + threadIdx.x;
   if (p >= Ntot) return;
   const int s = sys[p];
   const GDev& g = st[s];
   if (!g.active) return;
   const size_t t = (size_t)blockIdx.y * Ntot + p;
-  const double* c = coef + (size_t)s * (m + 1);
   double acc = w[t];
-  for (int i = 0; i <= g.j; ++i) acc -= c[i] * V[(size_t)i * n + t];
+  for (int i = 0; i <= g.j; ++i) {
+    double c;
+    if (uniform) {
+      c = sc[i];
+    } else {
+      const double* q = part + ((size_t)s * (m + 1) + i) * CH;
+      c = 0.0;
+      for (int k = 0; k < CH; ++k) c += q[k];
+    }
+    acc -= c * V[(size_t)i * n + t];
+  }
   w[t] = acc;
 }
 
@@ -683,7 +659,16 @@ __global__ void bk_finalize(GPtr p) {
   const int j = st->j, m = p.m;
   const size_t o1 = (size_t)s * (m + 1);
   const int tid = threadIdx.x;
-  for (int i = tid; i <= j; i += blockDim.x) col[i] = p.h1[o1 + i] + p.h2[o1 + i];
+  for (int i = tid; i <= j; i += blockDim.x) {
+    const double* a1 = p.h1p + (o1 + i) * p.CH;
+    const double* a2 = p.h2p + (o1 + i) * p.CH;
+    double c1 = 0.0, c2 = 0.0;
+    for (int c = 0; c < p.CH; ++c) {
+      c1 += a1[c];
+      c2 += a2[c];
+    }
+    col[i] = c1 + c2;
+  }
   for (int i = tid; i < j; i += blockDim.x) {
     scs[i] = p.cs[o1 + i];
     ssn[i] = p.sn[o1 + i];
@@ -727,15 +712,38 @@ __global__ void bk_finalize(GPtr p) {
   for (int i = tid; i <= j + 1; i += blockDim.x) H[(size_t)i * m + j] = col[i];
 }
 
-// V_{j_s} = w / h for the newly advanced j_s
+// Arnoldi source of the next pair pass, written by the kernels that produce V_j:
+// FP32 records (PairArgs::x32, ncp floats per sphere, zero padding) or FP64
+// component-major, both scaled by the column multipliers minv.
+struct SrcOut {
+  float* rec;
+  double* dbl;
+  int ncp;
+  Scales minv;
+};
+
+__device__ __forceinline__ void write_src(const SrcOut& o, int Ntot, int h, int q, int p, double v) {
+  if (o.rec != nullptr) {
+    float* r = o.rec + (size_t)p * o.ncp;
+    r[q] = float(v * o.minv.v[q]);
+    if (q == 0)
+      for (int k = h; k < o.ncp; ++k) r[k] = 0.f;
+  } else if (o.dbl != nullptr) {
+    o.dbl[(size_t)q * Ntot + p] = v * o.minv.v[q];
+  }
+}
+
+// V_{j_s} = w / h for the newly advanced j_s (and its Arnoldi source)
 __global__ void bk_scale(double* V, size_t n, const double* __restrict__ w, int Ntot, const int* __restrict__ sys,
-                         const GDev* __restrict__ st) {
+                         const GDev* __restrict__ st, SrcOut src) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= Ntot) return;
   const GDev& g = st[sys[p]];
   if (!g.active) return;
   const size_t t = (size_t)blockIdx.y * Ntot + p;
-  V[(size_t)g.j * n + t] = w[t] * g.inv_hn;
+  const double v = w[t] * g.inv_hn;
+  V[(size_t)g.j * n + t] = v;
+  write_src(src, Ntot, gridDim.y, blockIdx.y, p, v);
 }
 
 // start of a GMRES cycle for every enabled system: beta = |V_0|, g = (beta, 0, ...)
@@ -764,12 +772,16 @@ __global__ void bk_init_cycle(GPtr p, int first) {
   st->inv_hn = beta > 0 ? 1.0 / beta : 0.0;
 }
 
-__global__ void bk_scale0(double* V0, int Ntot, const int* __restrict__ sys, const GDev* __restrict__ st) {
+__global__ void bk_scale0(double* V0, int Ntot, const int* __restrict__ sys, const GDev* __restrict__ st,
+                          SrcOut src) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= Ntot) return;
   const GDev& g = st[sys[p]];
   if (!g.active) return;
-  V0[(size_t)blockIdx.y * Ntot + p] *= g.inv_hn;
+  const size_t t = (size_t)blockIdx.y * Ntot + p;
+  const double v = V0[t] * g.inv_hn;
+  V0[t] = v;
+  write_src(src, Ntot, gridDim.y, blockIdx.y, p, v);
 }
 
 // y_s = H_s^-1 g_s on the kdim leading rows (column-oriented back substitution)
@@ -843,6 +855,19 @@ gbi_status gmres_batch(gbi_ctx* ctx, const Setup& s, const Batch& B, int precisi
                        bool u_is_zero, double tol, int restart, int max_iter, gbi_info* info, int& iters,
                        double& relres, std::vector<GDev>& hst);
 
+// Where the kernels producing V_j put the next pair pass's source (see SrcOut).
+SrcOut src_out(const Setup& s, int precision, void* xsrc) {
+  SrcOut o;
+  o.rec = precision == 1 ? static_cast<float*>(xsrc) : nullptr;
+  o.dbl = precision == 1 ? nullptr : static_cast<double*>(xsrc);
+  o.ncp = (s.h + 3) & ~3;
+  o.minv = s.minv;
+  return o;
+}
+
+// kChunk Arnoldi iterations of every active system: pair pass on the source of V_j
+// (written by the previous bk_scale / bk_scale0), two rounds of classical Gram-Schmidt,
+// norm, Givens update and V_{j+1} with its source -- eight kernels per iteration.
 gbi_status launch_chunk(gbi_ctx* ctx, const Setup& s, const Batch& B, int precision, const GPtr& gp, int m,
                         double* Vb, double* w, void* xsrc, int kChunk) {
   const int S = B.S, Ntot = B.Ntot, h = s.h;
@@ -851,29 +876,22 @@ gbi_status launch_chunk(gbi_ctx* ctx, const Setup& s, const Batch& B, int precis
   PairArgs pa = pair_args(s, precision == 1 ? nullptr : static_cast<const double*>(xsrc), w, 1.0, 0.0, 1, s.ones,
                           6);
   if (precision == 1) pa.x32 = static_cast<const float*>(xsrc);
-  const int ncp = (h + 3) & ~3;
   pa.sys_of = B.sys;
   pa.sys_off = B.off;
   pa.sys_flag = &gp.st[0].active;
   pa.sys_flag_stride = int(sizeof(GDev) / sizeof(int));
+  const SrcOut so = src_out(s, precision, xsrc);
+  const dim3 gd(S, m + 1, gp.CH);
   for (int c = 0; c < kChunk; ++c) {
-    if (precision == 1)
-      bk_gather_rec<<<(Ntot + 31) / 32, 256, sizeof(float) * 32 * (ncp + 1), ctx->stream>>>(
-          Vb, n, Ntot, h, ncp, B.sys, gp.st, s.minv, static_cast<float*>(xsrc));
-    else
-      bk_gather<double><<<g2, 256, 0, ctx->stream>>>(Vb, n, Ntot, B.sys, gp.st, s.minv, static_cast<double*>(xsrc));
     GBI_CHECK(run_pairs(ctx, s.trunc, SET_H, SET_H, precision, pa));
-    const dim3 gd(S, m + 1, gp.CH);
     bk_dots<<<gd, 256, 0, ctx->stream>>>(Vb, n, w, Ntot, h, B.off, gp.st, m, gp.CH, gp.h1p);
-    bk_dots_sum<<<S, 64, 0, ctx->stream>>>(gp.h1p, gp.st, m, gp.CH, gp.h1);
-    bk_sub<<<g2, 256, 0, ctx->stream>>>(Vb, n, w, Ntot, B.sys, gp.st, m, gp.h1);
+    bk_sub<<<g2, 256, 0, ctx->stream>>>(Vb, n, w, Ntot, B.sys, gp.st, m, gp.CH, gp.h1p);
     bk_dots<<<gd, 256, 0, ctx->stream>>>(Vb, n, w, Ntot, h, B.off, gp.st, m, gp.CH, gp.h2p);
-    bk_dots_sum<<<S, 64, 0, ctx->stream>>>(gp.h2p, gp.st, m, gp.CH, gp.h2);
-    bk_sub<<<g2, 256, 0, ctx->stream>>>(Vb, n, w, Ntot, B.sys, gp.st, m, gp.h2);
+    bk_sub<<<g2, 256, 0, ctx->stream>>>(Vb, n, w, Ntot, B.sys, gp.st, m, gp.CH, gp.h2p);
     bk_norm_part<<<dim3(S, gp.CH), 256, 0, ctx->stream>>>(w, Ntot, h, B.off, gp.st, 0, gp.CH, gp.nrmp);
     bk_finalize<<<S, 128, 0, ctx->stream>>>(gp);
-    bk_scale<<<g2, 256, 0, ctx->stream>>>(Vb, n, w, Ntot, B.sys, gp.st);
-    ctx->launches += 10;
+    bk_scale<<<g2, 256, 0, ctx->stream>>>(Vb, n, w, Ntot, B.sys, gp.st, so);
+    ctx->launches += 7;
   }
   GBI_CHECK(cudaGetLastError());
   return GBI_OK;
@@ -962,7 +980,7 @@ gbi_status gmres_batch(gbi_ctx* ctx, const Setup& s, const Batch& B, int precisi
     bk_norm_part<<<dim3(S, gp.CH), 256, 0, ctx->stream>>>(Vb, Ntot, h, B.off, gp.st, 1, gp.CH, gp.nrmp);
     bk_norm_sum<<<(S + 127) / 128, 128, 0, ctx->stream>>>(gp.nrmp, gp.st, S, 1, gp.CH, gp.nrm);
     bk_init_cycle<<<sblk, 128, 0, ctx->stream>>>(gp, first ? 1 : 0);
-    bk_scale0<<<g2, 256, 0, ctx->stream>>>(Vb, Ntot, B.sys, gp.st);
+    bk_scale0<<<g2, 256, 0, ctx->stream>>>(Vb, Ntot, B.sys, gp.st, src_out(s, precision, xsrc));
     ctx->launches += 4;
     GBI_CHECK(cudaGetLastError());
     first = false;
@@ -1498,6 +1516,26 @@ int sm_count(gbi_ctx* ctx) {
   return ctx->num_sms;
 }
 
+// Network inference with the selected engine; the tcgen05 kernel reports a wait that
+// gave up through a device flag, read back here (synchronizes the stream).
+gbi_status mlp_infer(gbi_ctx* ctx, int np_, const float* F, const float* FR, float* out) {
+  if (ctx->mlp_engine == 1) {
+    GBI_CHECK(mlpk::infer_tc(np_, F, FR, ctx->mlp_pk_tc.p, out, P<int>(ctx->mlp_err), sm_count(ctx), ctx->stream));
+    ++ctx->launches;
+    int e = 0;
+    GBI_CHECK(cudaMemcpyAsync(&e, ctx->mlp_err.p, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    GBI_CHECK(cudaStreamSynchronize(ctx->stream));
+    if (e) {
+      ctx->err = "tensor-core inference: an MMA completion wait gave up";
+      return GBI_ERR_TIMEOUT;
+    }
+    return GBI_OK;
+  }
+  GBI_CHECK(mlpk::infer(np_, F, FR, ctx->mlp_pk.p, out, sm_count(ctx), ctx->stream));
+  ++ctx->launches;
+  return GBI_OK;
+}
+
 }  // namespace
 
 // =================================================================================
@@ -1531,7 +1569,7 @@ gbi_status gbi_destroy(gbi_ctx* ctx) {
                  &ctx->colbuf, &ctx->x32, &ctx->trapbuf, &ctx->gstate, &ctx->boff, &ctx->bsys, &ctx->tFe, &ctx->tTe, &ctx->tVa, &ctx->tOa, &ctx->tVH, &ctx->tV, &ctx->tOm,
                  &ctx->tQH, &ctx->hR, &ctx->hVa, &ctx->hOa, &ctx->hVH, &ctx->hFe, &ctx->hTe, &ctx->hV,
                  &ctx->hOm, &ctx->hQH, &ctx->mlp_th, &ctx->mlp_m, &ctx->mlp_v, &ctx->mlp_thq, &ctx->mlp_pk,
-                 &ctx->mlp_grad, &ctx->nb_cnt, &ctx->nb_start, &ctx->nb_tg, &ctx->nb_sr, &ctx->nb_scan,
+                 &ctx->mlp_grad, &ctx->mlp_pk_tc, &ctx->mlp_err, &ctx->nb_cnt, &ctx->nb_start, &ctx->nb_tg, &ctx->nb_sr, &ctx->nb_scan,
                  &ctx->cell_of, &ctx->cell_cnt, &ctx->cell_start, &ctx->cell_fill, &ctx->cell_items, &ctx->nb_aux,
                  &ctx->mf_F, &ctx->mf_FR, &ctx->mf_lab, &ctx->mf_dO, &ctx->mf_part, &ctx->mf_loss};
   for (Buf* b : bufs)
@@ -1841,11 +1879,15 @@ gbi_status gbi_mlp_set(gbi_ctx* ctx, const float* theta_host, double sigma) {
   GBI_TRY(ensure(ctx, ctx->mlp_thq, nb));
   GBI_TRY(ensure(ctx, ctx->mlp_grad, nb));
   GBI_TRY(ensure(ctx, ctx->mlp_pk, mlpk::packed_bytes()));
+  GBI_TRY(ensure(ctx, ctx->mlp_pk_tc, mlpk::packed_tc_bytes()));
+  GBI_TRY(ensure(ctx, ctx->mlp_err, sizeof(int)));
+  GBI_CHECK(cudaMemsetAsync(ctx->mlp_err.p, 0, sizeof(int), ctx->stream));
   GBI_CHECK(cudaMemcpyAsync(ctx->mlp_th.p, theta_host, nb, cudaMemcpyHostToDevice, ctx->stream));
   GBI_CHECK(cudaMemsetAsync(ctx->mlp_m.p, 0, nb, ctx->stream));
   GBI_CHECK(cudaMemsetAsync(ctx->mlp_v.p, 0, nb, ctx->stream));
   GBI_CHECK(mlpk::pack_weights(P<float>(ctx->mlp_th), P<float>(ctx->mlp_thq), ctx->mlp_pk.p, ctx->stream));
-  ++ctx->launches;
+  GBI_CHECK(mlpk::pack_weights_tc(P<float>(ctx->mlp_th), ctx->mlp_pk_tc.p, ctx->stream));
+  ctx->launches += 2;
   GBI_CHECK(cudaStreamSynchronize(ctx->stream));   // theta_host may be reused by the caller
   ctx->mlp_sigma = sigma;
   ctx->mlp_step = 0;
@@ -1878,8 +1920,12 @@ gbi_status gbi_mlp_forward(gbi_ctx* ctx, int P, const float* F, const float* FR,
   GBI_TRY(mlp_require(ctx));
   if (P == 0) return GBI_OK;
   if (!F || !out) return GBI_ERR_ARG;
-  GBI_CHECK(mlpk::infer(P, F, FR, ctx->mlp_pk.p, out, sm_count(ctx), ctx->stream));
-  ++ctx->launches;
+  return mlp_infer(ctx, P, F, FR, out);
+}
+
+gbi_status gbi_mlp_set_engine(gbi_ctx* ctx, int engine) {
+  if (!ctx || engine < 0 || engine > 1) return GBI_ERR_ARG;
+  ctx->mlp_engine = engine;
   return GBI_OK;
 }
 
@@ -1893,11 +1939,10 @@ gbi_status gbi_mlp_correct(gbi_ctx* ctx, int N, const double* R, const double* p
   if (!R || !p || !V || !Omega) return GBI_ERR_ARG;
   int np_ = 0;
   GBI_TRY(mlp_prepare(ctx, N, R, p, a, nsys, offsets_host, np_));
-  GBI_CHECK(mlpk::infer(np_, P<float>(ctx->mf_F), P<float>(ctx->mf_FR), ctx->mlp_pk.p, P<float>(ctx->mf_lab),
-                        sm_count(ctx), ctx->stream));
+  GBI_TRY(mlp_infer(ctx, np_, P<float>(ctx->mf_F), P<float>(ctx->mf_FR), P<float>(ctx->mf_lab)));
   GBI_CHECK(mlpk::sphere_sums(N, P<int>(ctx->nb_start), P<float>(ctx->mf_lab), s0 / ctx->mlp_sigma, V, Omega,
                               ctx->stream));
-  ctx->launches += 2;
+  ctx->launches += 1;
   if (npairs) *npairs = np_;
   return GBI_OK;
 }

@@ -132,6 +132,11 @@ cudaError_t train_batch(const float* thq, const float* F, const float* FR, const
 cudaError_t adam(float* th, float* m, float* v, const float* g, int t, double lr, float* thq, void* packed,
                  cudaStream_t st);
 cudaError_t sum_into(const double* parts, int n, double* dst, cudaStream_t st);
+// tcgen05 inference (mlp_tc.cu): own packed layout; *err is set if a wait gave up
+size_t packed_tc_bytes();
+cudaError_t pack_weights_tc(const float* theta, void* packed, cudaStream_t st);
+cudaError_t infer_tc(int P, const float* F, const float* FR, const void* packed, float* out, int* err, int num_sms,
+                     cudaStream_t st);
 cudaError_t labels(int N, double s0, double sigma, const double* Vx, const double* Ox, const double* Vs,
                    const double* Os, double* out, double* sq_part, cudaStream_t st);
 }  // namespace mlpk

@@ -1,0 +1,302 @@
+// Near-field network inference on the 5th-generation tensor cores (tcgen05).
+//
+// Same network and numerics as k_infer in mlp_kernel.cu (bf16 weights and layer
+// inputs, FP32 accumulation, tanh in FP32): one 128-pair tile per step, each layer
+// one chain of tcgen05.mma.cta_group::1.kind::f16 (M = 128 pairs, N = 128 neurons or 16
+// outputs, K = 16 per instruction) issued by a single thread, operands in shared
+// memory in the no-swizzle K-major core-matrix layout (8 rows x 16 bytes per core
+// matrix), the FP32 accumulator in tensor memory (128 lanes x 128 columns) read back
+// with tcgen05.ld by the four warps (warp w owns lanes 32w..32w+31 = pairs of the
+// tile).  Completion of each MMA chain is signalled through an mbarrier
+// (tcgen05.commit); every wait has an iteration limit after which the kernel records
+// an error, releases its tensor memory and returns.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gbi_internal.cuh"
+
+namespace gbi {
+namespace mlpk {
+namespace {
+
+constexpr int OFF_W1 = 0;
+constexpr int OFF_B1 = OFF_W1 + NH * NIN;
+constexpr int OFF_W2 = OFF_B1 + NH;
+constexpr int OFF_B2 = OFF_W2 + NH * NH;
+constexpr int OFF_W3 = OFF_B2 + NH;
+constexpr int OFF_B3 = OFF_W3 + NH * NH;
+constexpr int OFF_W4 = OFF_B3 + NH;
+constexpr int OFF_B4 = OFF_W4 + NOUT * NH;
+
+constexpr int TM = 128;          // pairs per tile (MMA M)
+constexpr int K1 = 16;           // layer-1 K (9 features, zero-padded)
+constexpr int N4 = 16;           // output layer N (6 outputs, zero-padded)
+constexpr int CM = 64;           // bf16 elements per core matrix (8 rows x 8)
+
+// core-matrix layout of an R x K operand (K-major): element (r, k) at
+//   ((r / 8) * (K / 8) + k / 8) * 64 + (r % 8) * 8 + k % 8
+// so K-adjacent core matrices are 128 bytes apart (LBO) and 8-row groups K * 16 bytes (SBO)
+__host__ __device__ constexpr int cm_index(int r, int k, int K) { return ((r >> 3) * (K >> 3) + (k >> 3)) * CM + (r & 7) * 8 + (k & 7); }
+
+// packed weights (bf16): W1 [128 x 16], W2 [128 x 128], W3 [128 x 128], W4 [16 x 128], then
+// FP32 biases b1, b2, b3 [128], b4 [16]
+constexpr int PW1 = 0;
+constexpr int PW2 = PW1 + NH * K1;
+constexpr int PW3 = PW2 + NH * NH;
+constexpr int PW4 = PW3 + NH * NH;
+constexpr int PWEND = PW4 + N4 * NH;      // bf16 elements
+constexpr int PBIAS = 3 * NH + N4;         // floats
+static_assert((PWEND * 2) % 16 == 0, "bias block alignment");
+
+__global__ void k_pack_tc(const float* __restrict__ th, __nv_bfloat16* __restrict__ pk) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < NH * K1) {
+    const int n = i / K1, k = i % K1;
+    pk[PW1 + cm_index(n, k, K1)] = __float2bfloat16_rn(k < NIN ? th[OFF_W1 + n * NIN + k] : 0.f);
+  }
+  if (i < NH * NH) {
+    const int n = i / NH, k = i % NH;
+    pk[PW2 + cm_index(n, k, NH)] = __float2bfloat16_rn(th[OFF_W2 + n * NH + k]);
+    pk[PW3 + cm_index(n, k, NH)] = __float2bfloat16_rn(th[OFF_W3 + n * NH + k]);
+  }
+  if (i < N4 * NH) {
+    const int n = i / NH, k = i % NH;
+    pk[PW4 + cm_index(n, k, NH)] = __float2bfloat16_rn(n < NOUT ? th[OFF_W4 + n * NH + k] : 0.f);
+  }
+  float* b = reinterpret_cast<float*>(pk + PWEND);
+  if (i < NH) {
+    b[i] = th[OFF_B1 + i];
+    b[NH + i] = th[OFF_B2 + i];
+    b[2 * NH + i] = th[OFF_B3 + i];
+  }
+  if (i < N4) b[3 * NH + i] = i < NOUT ? th[OFF_B4 + i] : 0.f;
+}
+
+// ---- PTX wrappers --------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t saddr(const void* p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
+
+// shared-memory matrix descriptor: no swizzle, K-major, LBO/SBO in bytes
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;   // descriptor version of this architecture
+  return d;                 // base offset 0, relative LBO, layout 0 = no swizzle
+}
+
+// instruction descriptor of kind::f16: FP32 accumulator, bf16 A and B, both K-major
+__host__ __device__ constexpr uint32_t instr_desc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t accum) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mbar)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(done)
+      : "r"(mbar), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+constexpr long long kWaitLimit = 1ll << 22;   // try_wait rounds before giving up
+
+struct TcSmem {
+  __nv_bfloat16 w[PWEND];          // weights, core-matrix layout
+  float bias[PBIAS];
+  __nv_bfloat16 a1[TM * K1];       // layer-1 operand (features)
+  __nv_bfloat16 act[TM * NH];      // hidden-layer operand
+  unsigned long long mbar;
+  uint32_t tmem_base;
+  int abort;
+};
+
+__global__ void __launch_bounds__(128) k_infer_tc(int P, const float* __restrict__ F, const float* __restrict__ FR,
+                                                   const __nv_bfloat16* __restrict__ pk, float* __restrict__ out,
+                                                   int* __restrict__ err) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  TcSmem& s = *reinterpret_cast<TcSmem*>(smem_raw);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  {
+    const int4* src = reinterpret_cast<const int4*>(pk);
+    int4* dst = reinterpret_cast<int4*>(s.w);
+    const int n16 = int((sizeof(__nv_bfloat16) * PWEND + sizeof(float) * PBIAS) / 16);
+    for (int i = tid; i < n16; i += blockDim.x) dst[i] = src[i];
+  }
+  const uint32_t mbar = saddr(&s.mbar);
+  if (tid == 0) {
+    s.abort = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(mbar), "r"(1) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(saddr(&s.tmem_base)),
+                 "r"(128)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  fence_async_smem();
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = s.tmem_base;
+  const uint32_t lane_base = (uint32_t)(warp * 32) << 16;   // this warp's TMEM lanes
+  const uint32_t a1_addr = saddr(s.a1), act_addr = saddr(s.act), w_addr = saddr(s.w);
+  const uint32_t id_hidden = instr_desc(TM, NH), id_out = instr_desc(TM, N4);
+  uint32_t parity = 0;
+  const int ntiles = (P + TM - 1) / TM;
+
+  // issue one layer (thread 0) and wait for it (all threads); false if the wait gave up
+  auto run_layer = [&](uint32_t a_addr, int K, uint32_t b_addr, uint32_t idesc) -> bool {
+    fence_async_smem();   // operands written through the generic proxy
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (tid == 0) {
+      const uint32_t sbo_a = (uint32_t)K * 16;   // 8 rows x K bf16
+      const uint32_t sbo_b = (uint32_t)K * 16;
+      for (int ks = 0; ks < K / 16; ++ks) {
+        const uint64_t ad = smem_desc(a_addr + ks * 256, 128, sbo_a);
+        const uint64_t bd = smem_desc(b_addr + ks * 256, 128, sbo_b);
+        mma_f16(tmem, ad, bd, idesc, ks > 0 ? 1u : 0u);
+      }
+      mma_commit(mbar);
+    }
+    long long it = 0;
+    while (!mbar_try_wait(mbar, parity)) {
+      if (++it > kWaitLimit) {
+        s.abort = 1;
+        break;
+      }
+    }
+    parity ^= 1u;
+    fence_after();
+    __syncthreads();
+    return s.abort == 0;
+  };
+
+  // hidden epilogue: row tid of the accumulator -> tanh(. + b) -> bf16 -> act (core layout)
+  auto hidden_epilogue = [&](const float* b) {
+#pragma unroll 1
+    for (int c0 = 0; c0 < NH; c0 += 16) {
+      float v[16];
+      tmem_ld16(tmem + lane_base + (uint32_t)c0, v);
+      __align__(16) __nv_bfloat16 o[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) o[i] = __float2bfloat16_rn(tanhf(v[i] + b[c0 + i]));
+      *reinterpret_cast<int4*>(&s.act[cm_index(tid, c0, NH)]) = *reinterpret_cast<const int4*>(&o[0]);
+      *reinterpret_cast<int4*>(&s.act[cm_index(tid, c0 + 8, NH)]) = *reinterpret_cast<const int4*>(&o[8]);
+    }
+  };
+
+  bool ok = true;
+  for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+    const int p = tile * TM + tid;
+    {
+      __align__(16) __nv_bfloat16 f[16];
+#pragma unroll
+      for (int k = 0; k < 16; ++k) f[k] = __float2bfloat16_rn((k < NIN && p < P) ? F[(size_t)p * NIN + k] : 0.f);
+      *reinterpret_cast<int4*>(&s.a1[cm_index(tid, 0, K1)]) = *reinterpret_cast<const int4*>(&f[0]);
+      *reinterpret_cast<int4*>(&s.a1[cm_index(tid, 8, K1)]) = *reinterpret_cast<const int4*>(&f[8]);
+    }
+    ok = run_layer(a1_addr, K1, w_addr + 2 * PW1, id_hidden);
+    if (!ok) break;
+    hidden_epilogue(s.bias);
+    ok = run_layer(act_addr, NH, w_addr + 2 * PW2, id_hidden);
+    if (!ok) break;
+    hidden_epilogue(s.bias + NH);
+    ok = run_layer(act_addr, NH, w_addr + 2 * PW3, id_hidden);
+    if (!ok) break;
+    hidden_epilogue(s.bias + 2 * NH);
+    ok = run_layer(act_addr, NH, w_addr + 2 * PW4, id_out);
+    if (!ok) break;
+    float o[16];
+    tmem_ld16(tmem + lane_base, o);
+    if (p < P) {
+      const float* b4 = s.bias + 3 * NH;
+      float y[NOUT];
+#pragma unroll
+      for (int c = 0; c < NOUT; ++c) y[c] = o[c] + b4[c];
+      float* dst = out + (size_t)p * NOUT;
+      if (FR != nullptr) {
+        const float* fr = FR + (size_t)p * 9;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          dst[i] = y[0] * fr[i] + y[1] * fr[3 + i] + y[2] * fr[6 + i];
+          dst[3 + i] = y[3] * fr[i] + y[4] * fr[3 + i] + y[5] * fr[6 + i];
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < NOUT; ++c) dst[c] = y[c];
+      }
+    }
+  }
+  if (!ok) {
+    // a chain that did not signal in time may still be running: wait once more (bounded)
+    // before the tensor memory it writes is released
+    long long it = 0;
+    while (!mbar_try_wait(mbar, parity ^ 1u) && ++it <= kWaitLimit) {
+    }
+    if (tid == 0) atomicExch(err, 1);
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(128) : "memory");
+}
+
+}  // namespace
+
+size_t packed_tc_bytes() { return sizeof(__nv_bfloat16) * PWEND + sizeof(float) * PBIAS; }
+
+cudaError_t pack_weights_tc(const float* theta, void* packed, cudaStream_t st) {
+  k_pack_tc<<<(NH * NH + 255) / 256, 256, 0, st>>>(theta, static_cast<__nv_bfloat16*>(packed));
+  return cudaGetLastError();
+}
+
+cudaError_t infer_tc(int P, const float* F, const float* FR, const void* packed, float* out, int* err, int num_sms,
+                     cudaStream_t st) {
+  if (P <= 0) return cudaSuccess;
+  const size_t smem = sizeof(TcSmem);
+  cudaError_t e = cudaFuncSetAttribute(k_infer_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
+  const int ntiles = (P + TM - 1) / TM;
+  const int grid = ntiles < 2 * num_sms ? ntiles : 2 * num_sms;
+  k_infer_tc<<<grid, 128, smem, st>>>(P, F, FR, static_cast<const __nv_bfloat16*>(packed), out, err);
+  return cudaGetLastError();
+}
+
+}  // namespace mlpk
+}  // namespace gbi

@@ -101,12 +101,14 @@ def test_features_match_oracle(ctx, gbi):
     np.testing.assert_allclose(FR.cpu().numpy().reshape(-1, 3, 3), FRo, atol=2e-5, rtol=0)
 
 
-@pytest.mark.parametrize("P", [1, 63, 64, 1000])
-def test_tensor_core_forward_matches_oracle(ctx, gbi, P):
+@pytest.mark.parametrize("engine", [0, 1])
+@pytest.mark.parametrize("P", [1, 63, 64, 127, 128, 1000])
+def test_tensor_core_forward_matches_oracle(ctx, gbi, P, engine):
     from paper_1411_0278_gb300 import nearfield
     th = nearfield.init_theta(7)
     th[omlp.NPARAM - 6:] = [0.1, -0.2, 0.3, 0.0, 0.05, -0.05]
     ctx.mlp_set(th, 4.0)
+    ctx.mlp_set_engine(engine)
     R, p, tg, sr = _random_pairs(P, 5 + P)
     Fo, FRo = omlp.features_for_pairs(R, p, 1.0, tg, sr)
     Fd = dev(Fo, torch.float32)
@@ -116,6 +118,21 @@ def test_tensor_core_forward_matches_oracle(ctx, gbi, P):
     assert np.abs(out - ref).max() <= 1e-2 * scale
     lab = ctx.mlp_forward(Fd, dev(FRo.reshape(-1, 9), torch.float32)).cpu().numpy()
     np.testing.assert_allclose(lab, omlp.rotate_out(ref, FRo), atol=1e-2 * scale, rtol=0)
+
+
+def test_engines_agree(ctx, gbi):
+    """Both inference engines multiply the same bf16 values; only FP32 summation order and
+    an occasional bf16 rounding of an activation differ."""
+    from paper_1411_0278_gb300 import nearfield
+    ctx.mlp_set(nearfield.init_theta(9), 1.0)
+    R, p, tg, sr = _random_pairs(5000, 12)
+    F, FR = ctx.mlp_features(dev(R), dev(p), dev(tg, torch.int32), dev(sr, torch.int32), 1.0)
+    ctx.mlp_set_engine(0)
+    a = ctx.mlp_forward(F).cpu().numpy()
+    ctx.mlp_set_engine(1)
+    b = ctx.mlp_forward(F).cpu().numpy()
+    assert np.abs(a - b).max() <= 1e-2 * np.abs(a).max()
+    assert np.median(np.abs(a - b)) <= 1e-4 * np.abs(a).max()
 
 
 def test_training_gradient_matches_oracle(ctx, gbi):
@@ -156,11 +173,13 @@ def test_adam_matches_oracle(ctx, gbi):
     np.testing.assert_allclose(got, t, atol=1e-6, rtol=1e-5)
 
 
-def test_correct_adds_scaled_sums(ctx, gbi):
+@pytest.mark.parametrize("engine", [0, 1])
+def test_correct_adds_scaled_sums(ctx, gbi, engine):
     from paper_1411_0278_gb300 import nearfield
     s = workloads.suspension(400, 0.1, 2.05, workloads.SEED_BASE + 77)
     th = nearfield.init_theta(5)
     ctx.mlp_set(th, 8.0)
+    ctx.mlp_set_engine(engine)
     R, p = dev(s["R"]), dev(s["p"])
     V0 = torch.randn(400, 3, dtype=torch.float64, device="cuda")
     O0 = torch.randn(400, 3, dtype=torch.float64, device="cuda")
