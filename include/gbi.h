@@ -271,10 +271,12 @@ gbi_status gbi_mlp_features(gbi_ctx* ctx, int P, const double* R, const double* 
 gbi_status gbi_mlp_forward(gbi_ctx* ctx, int P, const float* F, const float* FR, float* out);
 /* Inference engine of gbi_mlp_forward / gbi_mlp_correct: 0 = warp-level mma.sync
  * m16n8k16 (64 pairs per tile), 1 = tcgen05.mma with the accumulator in tensor memory
- * (128 pairs per tile; synchronizes the stream to read its completion status and
- * returns GBI_ERR_TIMEOUT if an MMA completion wait gave up).  Both multiply the same
- * bf16 values with FP32 accumulation. */
+ * (128 pairs per tile; default).  Both multiply the same bf16 values with FP32
+ * accumulation.  The tcgen05 kernel bounds its completion waits; if one gave up it
+ * records it on the device and gbi_mlp_status (synchronizes the stream) returns
+ * GBI_ERR_TIMEOUT once and clears the record; outputs of that call are not valid. */
 gbi_status gbi_mlp_set_engine(gbi_ctx* ctx, int engine);
+gbi_status gbi_mlp_status(gbi_ctx* ctx);
 gbi_status gbi_mlp_correct(gbi_ctx* ctx, int N, const double* R, const double* p, double a, double s0, int nsys,
                            const int* offsets_host, double* V, double* Omega, int* npairs);
 gbi_status gbi_mlp_labels(gbi_ctx* ctx, int N, double s0, const double* Vx, const double* Ox, const double* Vs,

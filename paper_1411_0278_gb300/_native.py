@@ -77,6 +77,7 @@ _SIGS = {
     "gbi_mlp_features": (_I, [_VP, _I, _VP, _VP, _VP, _VP, _D, _VP, _VP]),
     "gbi_mlp_forward": (_I, [_VP, _I, _VP, _VP, _VP]),
     "gbi_mlp_set_engine": (_I, [_VP, _I]),
+    "gbi_mlp_status": (_I, [_VP]),
     "gbi_mlp_correct": (_I, [_VP, _I, _VP, _VP, _D, _D, _I, ctypes.POINTER(ctypes.c_int), _VP, _VP,
                              ctypes.POINTER(ctypes.c_int)]),
     "gbi_mlp_labels": (_I, [_VP, _I, _D, _VP, _VP, _VP, _VP, c_double_p, _VP]),
@@ -374,6 +375,10 @@ class Context:
     def mlp_set_engine(self, engine):
         """0: mma.sync inference kernel, 1: tcgen05 (tensor memory) inference kernel."""
         self._check(lib().gbi_mlp_set_engine(self._h, int(engine)), "gbi_mlp_set_engine")
+
+    def mlp_status(self):
+        """gbi_mlp_status: raises GbiError if a tensor-core completion wait gave up."""
+        self._check(lib().gbi_mlp_status(self._h), "gbi_mlp_status")
 
     def mlp_correct(self, R, p, a, s0, V, Om, offsets=None):
         nsys, offs = self._offs(offsets)

@@ -63,6 +63,18 @@ __host__ __device__ __forceinline__ df& operator+=(df& a, df b) {
   return a;
 }
 
+// a * b + c with a single renormalisation: the product's rounding error terms are
+// folded into the sum (15 FP32 operations instead of 18 for a separate * and +)
+__host__ __device__ __forceinline__ df df_fma(df a, df b, df c) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  const df s = df_two_sum(p, c.hi);
+  const float t = s.lo + (e + c.lo);
+  return df_fast_two_sum(s.hi, t);
+}
+
 __host__ __device__ __forceinline__ bool operator>(df a, df b) {
   return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo);
 }
@@ -89,3 +101,9 @@ __device__ __forceinline__ df df_shfl_xor(df v, int o) {
 #endif
 
 }  // namespace gbi
+
+// a * b + c in the arithmetic of T (fused where the type has a fused form); the
+// generated pair-frame code chains its sums of products through this
+__host__ __device__ __forceinline__ float gbi_fmac(float a, float b, float c) { return fmaf(a, b, c); }
+__host__ __device__ __forceinline__ double gbi_fmac(double a, double b, double c) { return fma(a, b, c); }
+__host__ __device__ __forceinline__ gbi::df gbi_fmac(gbi::df a, gbi::df b, gbi::df c) { return gbi::df_fma(a, b, c); }

@@ -94,7 +94,7 @@ struct gbi_ctx {
   // copy (training), padded bf16 copy (inference), gradient; neighbour lists; pair
   // features, outputs and training scratch
   Buf mlp_th, mlp_m, mlp_v, mlp_thq, mlp_pk, mlp_grad, mlp_pk_tc, mlp_err;
-  int mlp_engine = 0;                          // inference: 0 mma.sync, 1 tcgen05
+  int mlp_engine = 1;                          // inference: 0 mma.sync, 1 tcgen05
   double mlp_sigma = 0.0;
   int mlp_step = 0;
   bool mlp_ready = false;
@@ -1516,19 +1516,12 @@ int sm_count(gbi_ctx* ctx) {
   return ctx->num_sms;
 }
 
-// Network inference with the selected engine; the tcgen05 kernel reports a wait that
-// gave up through a device flag, read back here (synchronizes the stream).
+// Network inference with the selected engine.  The tcgen05 kernel reports a wait that
+// gave up through a device flag that gbi_mlp_status reads back.
 gbi_status mlp_infer(gbi_ctx* ctx, int np_, const float* F, const float* FR, float* out) {
   if (ctx->mlp_engine == 1) {
     GBI_CHECK(mlpk::infer_tc(np_, F, FR, ctx->mlp_pk_tc.p, out, P<int>(ctx->mlp_err), sm_count(ctx), ctx->stream));
     ++ctx->launches;
-    int e = 0;
-    GBI_CHECK(cudaMemcpyAsync(&e, ctx->mlp_err.p, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-    GBI_CHECK(cudaStreamSynchronize(ctx->stream));
-    if (e) {
-      ctx->err = "tensor-core inference: an MMA completion wait gave up";
-      return GBI_ERR_TIMEOUT;
-    }
     return GBI_OK;
   }
   GBI_CHECK(mlpk::infer(np_, F, FR, ctx->mlp_pk.p, out, sm_count(ctx), ctx->stream));
@@ -1923,6 +1916,20 @@ gbi_status gbi_mlp_forward(gbi_ctx* ctx, int P, const float* F, const float* FR,
   return mlp_infer(ctx, P, F, FR, out);
 }
 
+gbi_status gbi_mlp_status(gbi_ctx* ctx) {
+  if (!ctx) return GBI_ERR_ARG;
+  GBI_TRY(mlp_require(ctx));
+  int e = 0;
+  GBI_CHECK(cudaMemcpyAsync(&e, ctx->mlp_err.p, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  GBI_CHECK(cudaStreamSynchronize(ctx->stream));
+  if (e) {
+    GBI_CHECK(cudaMemsetAsync(ctx->mlp_err.p, 0, sizeof(int), ctx->stream));
+    ctx->err = "tensor-core inference: an MMA completion wait gave up";
+    return GBI_ERR_TIMEOUT;
+  }
+  return GBI_OK;
+}
+
 gbi_status gbi_mlp_set_engine(gbi_ctx* ctx, int engine) {
   if (!ctx || engine < 0 || engine > 1) return GBI_ERR_ARG;
   ctx->mlp_engine = engine;
@@ -1976,8 +1983,8 @@ gbi_status gbi_mlp_adam(gbi_ctx* ctx, const float* grad, double lr) {
   GBI_TRY(mlp_require(ctx));
   ++ctx->mlp_step;
   GBI_CHECK(mlpk::adam(P<float>(ctx->mlp_th), P<float>(ctx->mlp_m), P<float>(ctx->mlp_v), grad, ctx->mlp_step, lr,
-                       P<float>(ctx->mlp_thq), ctx->mlp_pk.p, ctx->stream));
-  ctx->launches += 2;
+                       P<float>(ctx->mlp_thq), ctx->mlp_pk.p, ctx->mlp_pk_tc.p, ctx->stream));
+  ctx->launches += 3;
   return GBI_OK;
 }
 
@@ -2050,8 +2057,8 @@ gbi_status gbi_mlp_train(gbi_ctx* ctx, int N, const double* R, const double* p, 
       ++ctx->mlp_step;
       GBI_CHECK(mlpk::adam(P<float>(ctx->mlp_th), P<float>(ctx->mlp_m), P<float>(ctx->mlp_v),
                            P<float>(ctx->mlp_grad), ctx->mlp_step, lr, P<float>(ctx->mlp_thq), ctx->mlp_pk.p,
-                           ctx->stream));
-      ctx->launches += 7;
+                           ctx->mlp_pk_tc.p, ctx->stream));
+      ctx->launches += 8;
     }
     GBI_CHECK(cudaMemcpyAsync(hl.data(), lstep, sizeof(double) * nbatch, cudaMemcpyDeviceToHost, ctx->stream));
     GBI_CHECK(cudaStreamSynchronize(ctx->stream));

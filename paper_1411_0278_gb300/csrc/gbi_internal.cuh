@@ -130,7 +130,7 @@ cudaError_t train_batch(const float* thq, const float* F, const float* FR, const
                         int p_begin, int p_end, int n_begin, int n_end, int ns_total, float* lab, float* dO,
                         float* part, double* loss_part, float* grad, cudaStream_t st);
 cudaError_t adam(float* th, float* m, float* v, const float* g, int t, double lr, float* thq, void* packed,
-                 cudaStream_t st);
+                 void* packed_tc, cudaStream_t st);
 cudaError_t sum_into(const double* parts, int n, double* dst, cudaStream_t st);
 // tcgen05 inference (mlp_tc.cu): own packed layout; *err is set if a wait gave up
 size_t packed_tc_bytes();

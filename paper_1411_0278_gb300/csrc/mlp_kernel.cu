@@ -787,13 +787,15 @@ __global__ void k_adam(float* __restrict__ th, float* __restrict__ m, float* __r
 }
 
 cudaError_t adam(float* th, float* m, float* v, const float* g, int t, double lr, float* thq, void* packed,
-                 cudaStream_t st) {
+                 void* packed_tc, cudaStream_t st) {
   const double b1 = 0.9, b2 = 0.999;
   const float c1 = float(1.0 - pow(b1, t)), c2 = float(1.0 - pow(b2, t));
   k_adam<<<(NPARAM + 255) / 256, 256, 0, st>>>(th, m, v, g, float(lr), c1, c2, float(b1), float(b2), 1e-8f);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  return pack_weights(th, thq, packed, st);
+  e = pack_weights(th, thq, packed, st);   // every inference copy follows the new weights
+  if (e != cudaSuccess) return e;
+  return pack_weights_tc(th, packed_tc, st);
 }
 
 // ---------------------------------------------------------------------------------

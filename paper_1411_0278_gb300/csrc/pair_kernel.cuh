@@ -90,8 +90,8 @@ __host__ __device__ __forceinline__ void to_pair_frame(const T* x, T* xs, const 
 #pragma unroll
     for (int mm = 1; mm <= k; ++mm) {
       const T xp = x[o + k + mm], xn = x[o + k - mm];
-      t[k + mm] = cm[mm] * xp + sm[mm] * xn;
-      t[k - mm] = cm[mm] * xn - sm[mm] * xp;
+      t[k + mm] = gbi_fmac(cm[mm], xp, sm[mm] * xn);
+      t[k - mm] = gbi_fmac(cm[mm], xn, -(sm[mm] * xp));
     }
     dapply<k, T>(dm, t, u);
 #pragma unroll
@@ -117,8 +117,8 @@ __host__ __device__ __forceinline__ void from_pair_frame(const T* yy, T* acc, co
 #pragma unroll
     for (int mm = 1; mm <= k; ++mm) {
       const T tp = t[k + mm], tn = t[k - mm];
-      acc[o - R0 + k + mm] += cm[mm] * tp - sm[mm] * tn;
-      acc[o - R0 + k - mm] += sm[mm] * tp + cm[mm] * tn;
+      acc[o - R0 + k + mm] = gbi_fmac(cm[mm], tp, gbi_fmac(-sm[mm], tn, acc[o - R0 + k + mm]));
+      acc[o - R0 + k - mm] = gbi_fmac(sm[mm], tp, gbi_fmac(cm[mm], tn, acc[o - R0 + k - mm]));
     }
     from_pair_frame<TR, T, M + 1, MEND, R0>(yy, acc, cm, sm, dm, ep);
   }
@@ -192,8 +192,8 @@ __host__ __device__ __forceinline__ void pair_body(T dx, T dy, T dz, T a, const 
   cm[1] = cphi; sm[1] = sphi;
 #pragma unroll
   for (int mm = 2; mm <= MAXK; ++mm) {
-    cm[mm] = cm[mm - 1] * cphi - sm[mm - 1] * sphi;
-    sm[mm] = sm[mm - 1] * cphi + cm[mm - 1] * sphi;
+    cm[mm] = gbi_fmac(cm[mm - 1], cphi, -(sm[mm - 1] * sphi));
+    sm[mm] = gbi_fmac(sm[mm - 1], cphi, cm[mm - 1] * sphi);
   }
   // rotation about y by -theta: cos = ct, sin = -st
   DMats<T> dm;

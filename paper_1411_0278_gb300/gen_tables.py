@@ -396,6 +396,18 @@ def fmt(v):
     return repr(float(v))
 
 
+def fma_chain(terms):
+    """C++ expression for the sum of products [(a, b), ...] as a chain of gbi_fmac calls:
+    the first product is a plain multiply, every later one is fused into the sum."""
+    if not terms:
+        return "T(0)"
+    a0, b0 = terms[0]
+    expr = a0 if b0 is None else "%s * %s" % (a0, b0)
+    for a, b in terms[1:]:
+        expr = "(%s + %s)" % (expr, a) if b is None else "gbi_fmac(%s, %s, %s)" % (a, b, expr)
+    return expr
+
+
 def emit(path):
     lines = []
     w = lines.append
@@ -403,6 +415,8 @@ def emit(path):
     w("// Pair-frame single-layer Galerkin couplings, packed-basis rotations and")
     w("// self scalars for the truncations l<=2, 3, 4 (mode sets 1s 2a | 2s 3t | 3a 3s 4t | 4a 4s 5t).")
     w("#pragma once")
+    w("")
+    w("#include \"df.cuh\"   // gbi_fmac: a * b + c in the arithmetic of T")
     w("")
     maxk = 4
     check_tables(maxk)
@@ -419,10 +433,18 @@ def emit(path):
         w("template <typename T> __host__ __device__ __forceinline__ void gbi_dmat%d(T c, T s, T* __restrict__ dm) {" % k)
         w("  const T c2 = c * c; const T c3 = c2 * c; const T c4 = c2 * c2;")
         w("  const T cp[5] = {T(1), c, c2, c3, c4}; (void)cp;")
+        w("  const T sp[5] = {s, c * s, c2 * s, c3 * s, c4 * s}; (void)sp;")
         for e, ((mu, nu), poly) in enumerate(entries):
-            expr = " + ".join("T(%s)%s%s" % (fmt(v), "" if i == 0 else " * cp[%d]" % i, " * s" if j == 1 else "")
-                              for (i, j), v in sorted(poly.items()))
-            w("  dm[%d] = %s;   // (mu=%d, nu=%d)" % (e, expr, mu, nu))
+            terms = []
+            for (i, j), v in sorted(poly.items()):
+                mono = ("sp[%d]" % i) if j == 1 else (None if i == 0 else "cp[%d]" % i)
+                if mono is not None and v in (1, -1):      # unit coefficient: no multiply
+                    terms.append((mono if v == 1 else "(-%s)" % mono, None))
+                else:
+                    terms.append(("T(%s)" % fmt(v), mono))
+            # put a constant term (no monomial) first, so that the chain starts from it
+            terms.sort(key=lambda t: t[1] is not None)
+            w("  dm[%d] = %s;   // (mu=%d, nu=%d)" % (e, fma_chain(terms), mu, nu))
         w("}")
         for transpose in (False, True):
             nm = "gbi_dapply%s%d" % ("T" if transpose else "", k)
@@ -435,7 +457,7 @@ def emit(path):
                     rows.setdefault(mu, []).append((e, nu))
             for o in range(-k, k + 1):
                 terms = rows.get(o, [])
-                w("  out[%d] = %s;" % (o + k, " + ".join("dm[%d] * in[%d]" % (e, i + k) for e, i in terms) or "T(0)"))
+                w("  out[%d] = %s;" % (o + k, fma_chain([("dm[%d]" % e, "in[%d]" % (i + k)) for e, i in terms])))
             w("}")
     w("")
     # packing helpers for the trap inputs: U_mu . v^2 (mu = -2..2) and the Cartesian
@@ -507,9 +529,12 @@ def emit(path):
                     if not terms:
                         w("  y[%d] = T(0);" % p)
                         continue
-                    ea = " + ".join("T(%s) * xs[%d]" % (fmt(al), q) for q, al, be in terms if al != 0.0) or "T(0)"
-                    eb = " + ".join("T(%s) * xs[%d]" % (fmt(be), q) for q, al, be in terms if be != 0.0) or "T(0)"
-                    w("  y[%d] = (%s) + e2 * (%s);" % (p, ea, eb))
+                    ta = [("T(%s)" % fmt(al), "xs[%d]" % q) for q, al, be in terms if al != 0.0]
+                    tb = [("T(%s)" % fmt(be), "xs[%d]" % q) for q, al, be in terms if be != 0.0]
+                    if tb:
+                        w("  y[%d] = gbi_fmac(e2, %s, %s);" % (p, fma_chain(tb), fma_chain(ta)))
+                    else:
+                        w("  y[%d] = %s;" % (p, fma_chain(ta)))
                 w("}")
         nnz = len(cpl)
         w("static constexpr int gbi_t%d_nnz = %d;   // pair-frame nonzeros (all rows, all columns)" % (trunc, nnz))

@@ -118,6 +118,7 @@ def test_tensor_core_forward_matches_oracle(ctx, gbi, P, engine):
     assert np.abs(out - ref).max() <= 1e-2 * scale
     lab = ctx.mlp_forward(Fd, dev(FRo.reshape(-1, 9), torch.float32)).cpu().numpy()
     np.testing.assert_allclose(lab, omlp.rotate_out(ref, FRo), atol=1e-2 * scale, rtol=0)
+    ctx.mlp_status()
 
 
 def test_engines_agree(ctx, gbi):
@@ -131,6 +132,7 @@ def test_engines_agree(ctx, gbi):
     a = ctx.mlp_forward(F).cpu().numpy()
     ctx.mlp_set_engine(1)
     b = ctx.mlp_forward(F).cpu().numpy()
+    ctx.mlp_status()
     assert np.abs(a - b).max() <= 1e-2 * np.abs(a).max()
     assert np.median(np.abs(a - b)) <= 1e-4 * np.abs(a).max()
 
@@ -164,6 +166,17 @@ def test_adam_matches_oracle(ctx, gbi):
     ctx.mlp_adam(dev(g1, torch.float32), 1e-3)
     ctx.mlp_adam(dev(g2, torch.float32), 5e-4)
     got, sig = ctx.mlp_get()
+    # both inference engines follow the updated weights
+    R, p, tg, sr = _random_pairs(300, 21)
+    F = dev(omlp.features_for_pairs(R, p, 1.0, tg, sr)[0], torch.float32)
+    outs = []
+    for engine in (0, 1):
+        ctx.mlp_set_engine(engine)
+        outs.append(ctx.mlp_forward(F).cpu().numpy())
+    ctx.mlp_status()
+    ref, _ = omlp.forward(got.astype(np.float64), F.cpu().numpy().astype(np.float64), bf16=True)
+    for o in outs:
+        assert np.abs(o - ref).max() <= 1e-2 * np.abs(ref).max()
     assert sig == 1.0
     t = th.astype(np.float64)
     m = np.zeros_like(t)
