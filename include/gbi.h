@@ -232,8 +232,10 @@ gbi_status gbi_solve_static(void* stream, const gbi_params* params, int N,
  * Flat parameters (GBI_MLP_NPARAM floats): W1[128][9], b1[128], W2[128][128], b2[128],
  * W3[128][128], b3[128], W4[6][128], b4[6].
  * Inference multiplies BF16 weights and BF16 layer inputs on the tensor cores with
- * FP32 accumulation; training (FP32 CUDA cores) multiplies the same rounded values
- * and updates FP32 master weights with Adam (beta1 0.9, beta2 0.999, eps 1e-8).
+ * FP32 accumulation and evaluates tanh with the hardware approximation (relative
+ * error about 2^-11, below the bf16 rounding of the activation); training (FP32 CUDA
+ * cores, tanh to FP32 accuracy) multiplies the same rounded values and updates FP32
+ * master weights with Adam (beta1 0.9, beta2 0.999, eps 1e-8).
  *
  * gbi_pairs: ordered pairs (n, m), n != m, of the same system with |R_n - R_m| < rcut a
  * (decided in FP64 as (dx dx + dy dy) + dz dz), grouped by n and sorted by m; systems

@@ -103,6 +103,15 @@ int trap_splits(int N);
 
 // Learned near-field correction (mlp_kernel.cu).  Layout and definitions: gbi.h.
 namespace mlpk {
+#ifdef __CUDACC__
+// tanh of the inference kernels: the hardware approximation (PTX tanh.approx.f32, relative
+// error about 2^-11), below the bf16 rounding that every activation receives next
+__device__ __forceinline__ float tanh_act(float x) {
+  float y;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+#endif
 constexpr int NIN = 9, NH = 128, NOUT = 6;
 constexpr int NPARAM = NH * NIN + NH + 2 * (NH * NH + NH) + NOUT * NH + NOUT;   // 35078
 size_t scan_scratch_ints(int n);

@@ -421,8 +421,8 @@ __device__ __forceinline__ void hidden_layer(const __nv_bfloat16* in, const __nv
 #pragma unroll
   for (int t = 0; t < 16; ++t) {
     const int col = t * 8 + c2;
-    const float v0 = tanhf(acc[t][0] + b[col]), v1 = tanhf(acc[t][1] + b[col + 1]);
-    const float v2 = tanhf(acc[t][2] + b[col]), v3 = tanhf(acc[t][3] + b[col + 1]);
+    const float v0 = tanh_act(acc[t][0] + b[col]), v1 = tanh_act(acc[t][1] + b[col + 1]);
+    const float v2 = tanh_act(acc[t][2] + b[col]), v3 = tanh_act(acc[t][3] + b[col + 1]);
     *reinterpret_cast<uint32_t*>(out + g * LDA + col) = pack_bf16x2(v0, v1);
     *reinterpret_cast<uint32_t*>(out + (g + 8) * LDA + col) = pack_bf16x2(v2, v3);
   }

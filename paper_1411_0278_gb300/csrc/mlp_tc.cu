@@ -1,7 +1,7 @@
 // Near-field network inference on the 5th-generation tensor cores (tcgen05).
 //
 // Same network and numerics as k_infer in mlp_kernel.cu (bf16 weights and layer
-// inputs, FP32 accumulation, tanh in FP32): one 128-pair tile per step, each layer
+// inputs, FP32 accumulation, hardware tanh approximation): one 128-pair tile per step, each layer
 // one chain of tcgen05.mma.cta_group::1.kind::f16 (M = 128 pairs, N = 128 neurons or 16
 // outputs, K = 16 per instruction) issued by a single thread, operands in shared
 // memory in the no-swizzle K-major core-matrix layout (8 rows x 16 bytes per core
@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(128) k_infer_tc(int P, const float* __restrict
       tmem_ld16(tmem + lane_base + (uint32_t)c0, v);
       __align__(16) __nv_bfloat16 o[16];
 #pragma unroll
-      for (int i = 0; i < 16; ++i) o[i] = __float2bfloat16_rn(tanhf(v[i] + b[c0 + i]));
+      for (int i = 0; i < 16; ++i) o[i] = __float2bfloat16_rn(tanh_act(v[i] + b[c0 + i]));
       *reinterpret_cast<int4*>(&s.act[cm_index(tid, c0, NH)]) = *reinterpret_cast<const int4*>(&o[0]);
       *reinterpret_cast<int4*>(&s.act[cm_index(tid, c0 + 8, NH)]) = *reinterpret_cast<const int4*>(&o[8]);
     }
