@@ -214,9 +214,12 @@ def learned_nearfield(ctx, gbi, dev, stream, peaks):
     t0 = time.time()
     hist = nearfield.train(ctx, dtr, epochs=epochs, batch_systems=1024, lr0=3e-3, lr1=3e-5, seed=1)
     t_train = time.time() - t0
-    te = workloads.nearfield_systems(1000, 1000, k=21)
-    dte = nearfield.make_dataset(ctx, T(te["R"]), T(te["p"]), te["offsets"], a, eta, vs, s0, sigma=dtr["sigma"])
-    held = nearfield.evaluate(ctx, dte)
+    held = {}
+    for name, n2, n3 in (("two_body", 1000, 0), ("three_body", 0, 1000)):
+        te = workloads.nearfield_systems(n2, n3, k=21)
+        dte = nearfield.make_dataset(ctx, T(te["R"]), T(te["p"]), te["offsets"], a, eta, vs, s0,
+                                     sigma=dtr["sigma"])
+        held[name] = nearfield.evaluate(ctx, dte)
 
     # dense suspension: plain l <= 4 solve against superposition (+ network)
     ss = workloads.suspension(2000, 0.1, 2.05, workloads.SEED_BASE + 5200)
@@ -282,7 +285,7 @@ def learned_nearfield(ctx, gbi, dev, stream, peaks):
             "training": {"systems": len(tr["offsets"]) - 1, "spheres": len(tr["R"]), "label_s": t_label,
                          "train_s": t_train, "epochs": epochs, "loss_first": hist[0], "loss_last": hist[-1],
                          "sigma": dtr["sigma"]},
-            "heldout_2_3_body": held, "dense_suspension": dense,
+            "heldout": held, "dense_suspension": dense,
             "note": "errors are relative to the plain l<=4 Galerkin solve: ||V - Vx|| / ||Vx - Va||, "
                     "||Omega - Ox|| / ||Ox||"}
 
@@ -355,7 +358,9 @@ def run_ours(args):
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
 
-    def run_steps(k):
+    step_stats = {"iters": 0, "refinements": 0, "matvecs_f32": 0, "matvecs_hp": 0, "max_residual": 0.0}
+
+    def run_steps(k, stats=None):
         ms, pr = 0.0, 0
         for _ in range(k):
             flush.fill_(1.0)                    # evict the L2 between timed steps
@@ -365,10 +370,16 @@ def run_ours(args):
             ev1.synchronize()
             ms += ev0.elapsed_time(ev1)
             pr += info.pair_interactions
+            if stats is not None:
+                stats["iters"] += info.iters
+                stats["refinements"] += info.refinements
+                stats["matvecs_f32"] += info.matvecs_f32
+                stats["matvecs_hp"] += info.matvecs_f64
+                stats["max_residual"] = max(stats["max_residual"], info.rel_residual)
         return ms, pr
 
     barrier()
-    total_ms, pairs = run_steps(args.steps)
+    total_ms, pairs = run_steps(args.steps, step_stats)
     barrier()
     launches = ctx.kernel_launches() - launches0
     clocks = sampler.stop()
@@ -453,7 +464,8 @@ def run_ours(args):
     h2d = 8 * N * (5 * 3 + h)
     d2h = 8 * N * (2 * 3 + h)
     e2e = {"value": e_pairs / e_t, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-           "solves_per_s": args.steps / e_t, "call": "gbi_solve_host (pinned host buffers, one solve per step)"}
+           "solves_per_s": args.steps / e_t, "call": "gbi_solve_host (pinned host buffers, one solve per step)",
+           "start": "cold (zero initial guess) every call, the N=1024 initial suspension"}
 
     # ---- secondary: superposition trap pass at N = 10^4 (closed-form kernel, FP32)
     c3 = workloads.config3()
@@ -536,7 +548,14 @@ def run_ours(args):
                            "step": "trap inputs + full Galerkin solve + Euler update",
                            "l2": "flushed (256 MB write) before every timed step",
                            "parallelism": "replicas" if world > 1 else "single GPU"},
-                "solves_per_s": solves_per_s, "error_vs_fp64": err, "roofline": roofline,
+                "solves_per_s": solves_per_s, "error_vs_fp64": err,
+                "per_step": {"gmres_iters": step_stats["iters"] / args.steps,
+                             "refinements": step_stats["refinements"] / args.steps,
+                             "fp32_passes": step_stats["matvecs_f32"] / args.steps,
+                             "high_precision_passes": step_stats["matvecs_hp"] / args.steps,
+                             "max_rel_residual": step_stats["max_residual"],
+                             "start": "cold (zero initial guess) every step: mixed precision"},
+                "roofline": roofline,
                 "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
                 "superposition": superposition, "batched": batched, "learned_nearfield": learned,
                 "tuned_wpt": dict(zip(TUNED_PASSES, tuned))}

@@ -63,7 +63,8 @@ typedef struct {
   int restart;       /* GMRES restart length (Krylov vectors per cycle), 1..128          */
   int max_iter;      /* cap on inner GMRES iterations over the whole solve               */
   int max_refine;    /* cap on refinement sweeps (precision = 1)                         */
-  double inner_rtol; /* relative tolerance of each inner FP32 solve (precision = 1)      */
+  double inner_rtol; /* relative tolerance of each inner FP32 solve (precision 1, 2);    */
+                     /*    loosened to 0.1 rtol |b| / |r| when that is larger           */
   double min_sep;    /* overlap guard: reject pairs closer than min_sep * a (0 = off)    */
 } gbi_params;
 
@@ -185,7 +186,12 @@ gbi_status gbi_trap_inputs(gbi_ctx* ctx, int N, int trunc, double k_trap, double
  *     R <- R + dt V,  p <- normalise(p + dt Omega x p),
  * with F^e = -k_trap R, T^e = 0, V^a = vs p, Omega^a = 0, V^(2s) = s0 (pp - I/3),
  * V^(3t) = d0 p and every other higher mode zero, V and Omega re-evaluated every
- * step by gbi_superpose (superposition != 0) or gbi_solve (warm-started).
+ * step by gbi_superpose (superposition != 0) or gbi_solve (superposition == 0).  With
+ * params.precision 0 each solve starts from the previous step's traction coefficients
+ * Q^H, also across calls on the same context with the same N and truncation (the first
+ * call, or one after a failed solve, starts from zero); mixed-precision solves start
+ * from zero (a warm start would cost one more high-precision residual pass and save no
+ * refinement sweep).  Results differ only within the solve tolerance.
  * R, p: [N][3] device arrays updated in place.  info (may be NULL) accumulates
  * over the steps.  Synchronous when superposition == 0. */
 gbi_status gbi_trap_step(gbi_ctx* ctx, const gbi_params* params, int N, double dt, double k_trap,

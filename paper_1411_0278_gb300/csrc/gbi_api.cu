@@ -70,11 +70,12 @@ struct gbi_ctx {
   std::vector<char> hbatch;                    // host copy of the per-system solver states
   bool allow_graphs = true;                    // replay Arnoldi chunks from a CUDA graph
   bool fixed = false;                          // buffers bound to static storage: never reallocate
-  cudaGraphExec_t chunk_exec = nullptr;        // captured chunk of Arnoldi iterations
+  cudaGraphExec_t chunk_exec = nullptr;        // device-looped Arnoldi steps of one GMRES cycle
   const void* chunk_key[8] = {};
   long long chunk_ikey[6] = {};
   int chunk_nodes = 0;
   Buf tFe, tTe, tVa, tOa, tVH, tV, tOm, tQH;   // trap-step / host-call staging
+  int tqh_N = -1, tqh_trunc = -1;              // tQH holds the last trap-step solution of this size
   Buf hR, hVa, hOa, hVH, hFe, hTe, hV, hOm, hQH;
   double* hbuf = nullptr;                      // pinned scalars read back by GMRES
   long long launches = 0;                      // kernels launched by this context
@@ -513,6 +514,7 @@ struct GPtr {     // per-system views into the gstate buffer
   GDev* st;
   double *H, *cs, *sn, *g, *y, *nrm;
   double *h1p, *h2p, *nrmp;   // per-chunk partial sums of the dot products and the norm
+  int* nact;                  // systems still active after the current Arnoldi step
   int S, m, CH;
 };
 
@@ -541,7 +543,8 @@ GPtr gptrs(void* base, int m, int S, int CH) {
   p.nrm = d; d += (size_t)S;
   p.h1p = d; d += (size_t)S * (m + 1) * CH;
   p.h2p = d; d += (size_t)S * (m + 1) * CH;
-  p.nrmp = d;
+  p.nrmp = d; d += (size_t)S * CH;
+  p.nact = reinterpret_cast<int*>(d);
   return p;
 }
 
@@ -705,6 +708,7 @@ __global__ void bk_finalize(GPtr p) {
     } else {
       st->inv_hn = 1.0 / hn;
       st->j = j + 1;
+      atomicAdd(p.nact, 1);
     }
   }
   __syncthreads();
@@ -746,9 +750,18 @@ __global__ void bk_scale(double* V, size_t n, const double* __restrict__ w, int 
   write_src(src, Ntot, gridDim.y, blockIdx.y, p, v);
 }
 
+// End of one device-looped Arnoldi step: keep looping while any system is still active
+// (the WHILE node of the cycle graph reads the value set here), and reset the count.
+__global__ void bk_continue(GPtr p, cudaGraphConditionalHandle h) {
+  const int v = *p.nact;
+  *p.nact = 0;
+  cudaGraphSetConditional(h, v > 0 ? 1u : 0u);
+}
+
 // start of a GMRES cycle for every enabled system: beta = |V_0|, g = (beta, 0, ...)
 __global__ void bk_init_cycle(GPtr p, int first) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s == 0) *p.nact = 0;
   if (s >= p.S) return;
   GDev* st = p.st + s;
   const int m = p.m;
@@ -853,7 +866,7 @@ __global__ void bk_axpy_enabled(const double* __restrict__ d, int Ntot, const in
 // systems' small states once per chunk.
 gbi_status gmres_batch(gbi_ctx* ctx, const Setup& s, const Batch& B, int precision, const double* rhs, double* u,
                        bool u_is_zero, double tol, int restart, int max_iter, gbi_info* info, int& iters,
-                       double& relres, std::vector<GDev>& hst);
+                       double& relres, std::vector<GDev>& hst, double outer_rtol = 0.0);
 
 // Where the kernels producing V_j put the next pair pass's source (see SrcOut).
 SrcOut src_out(const Setup& s, int precision, void* xsrc) {
@@ -897,11 +910,15 @@ gbi_status launch_chunk(gbi_ctx* ctx, const Setup& s, const Batch& B, int precis
   return GBI_OK;
 }
 
-__global__ void bk_setup(GPtr p, double tol, int max_iter) {
+// Per-system GMRES set-up.  With outer_rtol > 0 (an inner solve of the refinement) the
+// tolerance relative to the current residual r is loosened to 0.1 outer_rtol |b| / |r|
+// when that is larger than tol: the solve only has to bring |r| a decade below the
+// target, so a refinement sweep that starts close to it needs few iterations.
+__global__ void bk_setup(GPtr p, double tol, int max_iter, double outer_rtol) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= p.S) return;
   GDev* st = p.st + s;
-  st->tol = tol;
+  st->tol = outer_rtol > 0 ? fmax(tol, 0.1 * outer_rtol / fmax(st->rel, 1e-300)) : tol;
   st->max_iter = max_iter;
   st->m = p.m;
   st->active = 0;
@@ -911,7 +928,7 @@ __global__ void bk_setup(GPtr p, double tol, int max_iter) {
 
 gbi_status gmres_batch(gbi_ctx* ctx, const Setup& s, const Batch& B, int precision, const double* rhs, double* u,
                        bool u_is_zero, double tol, int restart, int max_iter, gbi_info* info, int& iters,
-                       double& relres, std::vector<GDev>& hst) {
+                       double& relres, std::vector<GDev>& hst, double outer_rtol) {
   constexpr int kChunk = 6;
   const int S = B.S, Ntot = B.Ntot, h = s.h;
   const size_t n = (size_t)Ntot * h;
@@ -929,9 +946,12 @@ gbi_status gmres_batch(gbi_ctx* ctx, const Setup& s, const Batch& B, int precisi
   const int sblk = (S + 127) / 128;
   iters = 0;
   relres = 0.0;
-  bk_setup<<<sblk, 128, 0, ctx->stream>>>(gp, tol, std::max(0, max_iter));
+  bk_setup<<<sblk, 128, 0, ctx->stream>>>(gp, tol, std::max(0, max_iter), outer_rtol);
   ++ctx->launches;
-  // chunk graph: captured once per buffer set, replayed afterwards
+  // cycle graph: a WHILE node whose body is one Arnoldi step of every active system
+  // followed by bk_continue; the loop runs on the device until no system is active, so a
+  // GMRES cycle costs one graph launch and one read of the per-system states.  Built
+  // once per buffer set and replayed afterwards.
   const bool graphs = ctx->allow_graphs && ctx->stream != nullptr && !ctx->prof;
   if (graphs) {
     const void* key[8] = {Vb, w, xsrc, ctx->gstate.p, B.sys, B.off, s.pos.hi, s.pos.p64};
@@ -942,18 +962,36 @@ gbi_status gmres_batch(gbi_ctx* ctx, const Setup& s, const Batch& B, int precisi
     if (!same) {
       if (ctx->chunk_exec) cudaGraphExecDestroy(ctx->chunk_exec);
       ctx->chunk_exec = nullptr;
-      const long long saved = ctx->launches;
       cudaGraph_t graph = nullptr;
-      GBI_CHECK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-      gbi_status st = launch_chunk(ctx, s, B, precision, gp, m, Vb, w, xsrc, kChunk);
-      cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
+      GBI_CHECK(cudaGraphCreate(&graph, 0));
+      cudaGraphConditionalHandle handle;
+      cudaError_t e = cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault);
+      cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+      cp.conditional.handle = handle;
+      cp.conditional.type = cudaGraphCondTypeWhile;
+      cp.conditional.size = 1;
+      cudaGraphNode_t node = nullptr;
+      if (e == cudaSuccess) e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp);
+      const long long saved = ctx->launches;
+      gbi_status st = GBI_OK;
+      if (e == cudaSuccess) {
+        e = cudaStreamBeginCaptureToGraph(ctx->stream, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+          st = launch_chunk(ctx, s, B, precision, gp, m, Vb, w, xsrc, 1);
+          bk_continue<<<1, 1, 0, ctx->stream>>>(gp, handle);
+          ++ctx->launches;
+          cudaGraph_t body = nullptr;
+          const cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &body);
+          if (e == cudaSuccess) e = e2;
+        }
+      }
+      ctx->chunk_nodes = int(ctx->launches - saved);   // kernels per loop iteration
+      ctx->launches = saved;
+      if (st == GBI_OK && e == cudaSuccess) e = cudaGraphInstantiate(&ctx->chunk_exec, graph, 0);
+      cudaGraphDestroy(graph);
       if (st != GBI_OK) return st;
       GBI_CHECK(e);
-      e = cudaGraphInstantiate(&ctx->chunk_exec, graph, 0);
-      cudaGraphDestroy(graph);
-      GBI_CHECK(e);
-      ctx->chunk_nodes = int(ctx->launches - saved);
-      ctx->launches = saved;
       for (int i = 0; i < 8; ++i) ctx->chunk_key[i] = key[i];
       for (int i = 0; i < 6; ++i) ctx->chunk_ikey[i] = ikey[i];
     }
@@ -983,43 +1021,52 @@ gbi_status gmres_batch(gbi_ctx* ctx, const Setup& s, const Batch& B, int precisi
     bk_scale0<<<g2, 256, 0, ctx->stream>>>(Vb, Ntot, B.sys, gp.st, src_out(s, precision, xsrc));
     ctx->launches += 4;
     GBI_CHECK(cudaGetLastError());
+    if (first)
+      for (int q = 0; q < S; ++q) before[q] = 0;      // bk_init_cycle restarts the counters
+    else
+      for (int q = 0; q < S; ++q) before[q] = hst[q].iters;
     first = false;
-    for (int q = 0; q < S; ++q) before[q] = hst[q].iters;
-    // Arnoldi iterations in chunks, one host check per chunk
-    bool any = true;
-    {
-      // iteration counters at cycle start (bk_init_cycle keeps them across restarts)
+    auto account = [&](int nsteps) {
+      // states after the launched steps: pair work of the systems that took them
+      int live = 0;
+      for (int q = 0; q < S; ++q) {
+        const int d = hst[q].iters - before[q];
+        before[q] = hst[q].iters;
+        live = std::max(live, d);
+        if (info) info->pair_interactions += (long long)d * (B.h_off[q + 1] - B.h_off[q]) * (B.h_off[q + 1] - B.h_off[q] - 1);
+      }
+      if (info) (precision == 1 ? info->matvecs_f32 : info->matvecs_f64) += live;
+      ctx->stat_dead[precision * 9 + SET_H * 3 + SET_H] += std::max(0, nsteps - live);
+      return live;
+    };
+    auto read_states = [&]() -> gbi_status {
       ctx->hbatch.resize(sizeof(GDev) * S);
       GBI_CHECK(cudaMemcpyAsync(ctx->hbatch.data(), gp.st, sizeof(GDev) * S, cudaMemcpyDeviceToHost, ctx->stream));
       GBI_CHECK(cudaStreamSynchronize(ctx->stream));
       std::memcpy(hst.data(), ctx->hbatch.data(), sizeof(GDev) * S);
-      any = false;
-      for (int q = 0; q < S; ++q) {
-        before[q] = hst[q].iters;
-        any = any || hst[q].active;
-      }
-    }
-    while (any) {
-      if (graphs) {
-        GBI_CHECK(cudaGraphLaunch(ctx->chunk_exec, ctx->stream));
-        ctx->launches += ctx->chunk_nodes;
-      } else {
+      return GBI_OK;
+    };
+    if (graphs) {
+      // the whole cycle's Arnoldi steps in one launch; the loop ran max(1, most steps) times
+      GBI_CHECK(cudaGraphLaunch(ctx->chunk_exec, ctx->stream));
+      GBI_TRY(read_states());
+      int most = 0;
+      for (int q = 0; q < S; ++q) most = std::max(most, hst[q].iters - before[q]);
+      const int steps = std::max(1, most);
+      ctx->launches += (long long)steps * ctx->chunk_nodes;
+      account(steps);
+    } else {
+      // host-driven: chunks of kChunk steps with a state read after each
+      GBI_TRY(read_states());
+      bool any = false;
+      for (int q = 0; q < S; ++q) any = any || hst[q].active;
+      while (any) {
         GBI_TRY(launch_chunk(ctx, s, B, precision, gp, m, Vb, w, xsrc, kChunk));
+        GBI_TRY(read_states());
+        account(kChunk);
+        any = false;
+        for (int q = 0; q < S; ++q) any = any || hst[q].active;
       }
-      GBI_CHECK(cudaMemcpyAsync(ctx->hbatch.data(), gp.st, sizeof(GDev) * S, cudaMemcpyDeviceToHost, ctx->stream));
-      GBI_CHECK(cudaStreamSynchronize(ctx->stream));
-      std::vector<GDev> prev = hst;
-      std::memcpy(hst.data(), ctx->hbatch.data(), sizeof(GDev) * S);
-      int live = 0;
-      any = false;
-      for (int q = 0; q < S; ++q) {
-        const int d = hst[q].iters - prev[q].iters;
-        live = std::max(live, d);
-        any = any || hst[q].active;
-        if (info) info->pair_interactions += (long long)d * (B.h_off[q + 1] - B.h_off[q]) * (B.h_off[q + 1] - B.h_off[q] - 1);
-      }
-      if (info) (precision == 1 ? info->matvecs_f32 : info->matvecs_f64) += live;
-      ctx->stat_dead[precision * 9 + SET_H * 3 + SET_H] += kChunk - live;
     }
     bk_solve_y<<<S, 128, 0, ctx->stream>>>(gp);
     bk_update<<<g2, 256, 0, ctx->stream>>>(Vb, n, Ntot, B.sys, gp, s.minv, u);
@@ -1182,7 +1229,7 @@ gbi_status solve_core(gbi_ctx* ctx, const gbi_params* prm, const Batch& B, const
         inf->matvecs_f64 += 1;
         inf->pair_interactions += pairs_enabled();
         bk_norm_part<<<dim3(S, gp.CH), 256, 0, ctx->stream>>>(r, N, h, B.off, gp.st, 1, gp.CH, gp.nrmp);
-    bk_norm_sum<<<(S + 127) / 128, 128, 0, ctx->stream>>>(gp.nrmp, gp.st, S, 1, gp.CH, gp.nrm);
+        bk_norm_sum<<<(S + 127) / 128, 128, 0, ctx->stream>>>(gp.nrmp, gp.st, S, 1, gp.CH, gp.nrm);
         bk_refine<<<sblk, 128, 0, ctx->stream>>>(gp, 1, rtol);
         ctx->launches += 3;
       }
@@ -1194,7 +1241,8 @@ gbi_status solve_core(gbi_ctx* ctx, const gbi_params* prm, const Batch& B, const
       int it = 0;
       double rr = 0.0;
       GBI_CHECK(cudaMemsetAsync(dl, 0, sizeof(double) * nh, ctx->stream));
-      GBI_TRY(gmres_batch(ctx, s, B, 1, r, dl, true, inner, restart, max_iter - inf->iters, inf, it, rr, hst));
+      GBI_TRY(gmres_batch(ctx, s, B, 1, r, dl, true, inner, restart, max_iter - inf->iters, inf, it, rr, hst,
+                          rtol));
       inf->iters += it;
       bool any = false;
       for (int q = 0; q < S; ++q) any = any || hst[q].enabled;
@@ -1781,9 +1829,19 @@ gbi_status gbi_trap_step(gbi_ctx* ctx, const gbi_params* prm, int N, double dt, 
       (prm->precision == 1 ? total.matvecs_f32 : total.matvecs_f64) += 1;
     } else {
       gbi_info one{};
+      // FP64 solves warm-start from the previous step's traction coefficients (also across
+      // calls with the same N and truncation on this context).  Mixed-precision solves start
+      // from zero: a warm start costs one more high-precision residual pass, and the FP32
+      // inner solves cannot reach the target from it in fewer sweeps.
+      const bool warm = prm->precision == 0 && (step > 0 || (ctx->tqh_N == N && ctx->tqh_trunc == prm->trunc));
+      ctx->tqh_N = -1;
       st = gbi_solve(ctx, prm, N, R, P<double>(ctx->tVa), P<double>(ctx->tOa), P<double>(ctx->tVH),
                      P<double>(ctx->tFe), P<double>(ctx->tTe), P<double>(ctx->tV), P<double>(ctx->tOm),
-                     P<double>(ctx->tQH), step > 0 ? 1 : 0, &one);
+                     P<double>(ctx->tQH), warm ? 1 : 0, &one);
+      if (st == GBI_OK) {
+        ctx->tqh_N = N;
+        ctx->tqh_trunc = prm->trunc;
+      }
       total.iters += one.iters;
       total.refinements += one.refinements;
       total.matvecs_f32 += one.matvecs_f32;
