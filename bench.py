@@ -291,6 +291,19 @@ def learned_nearfield(ctx, gbi, dev, stream, peaks):
 
 
 
+def job_totals(t_local, pairs_local, world, device):
+    """Whole-job time (the slowest rank) and work (summed over ranks) of a timed region."""
+    if world <= 1:
+        return t_local, float(pairs_local)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([t_local], dtype=torch.float64, device=device)
+    w = torch.tensor([float(pairs_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(w, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(w[0])
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -393,15 +406,7 @@ def run_ours(args):
     stats = {cls: ctx.kernel_stats(cls) for cls in range(gbi._native.N_KERNEL_CLASSES)}
     ctx.set_profiling(False)
 
-    t_local = total_ms / 1e3
-    if world > 1:
-        tt = torch.tensor([t_local, float(pairs)], dtype=torch.float64, device=dev)
-        tmax = tt.clone()
-        torch.distributed.all_reduce(tmax[:1], op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(tt[1:], op=torch.distributed.ReduceOp.SUM)
-        t_job, pairs_job = float(tmax[0]), float(tt[1])
-    else:
-        t_job, pairs_job = t_local, float(pairs)
+    t_job, pairs_job = job_totals(total_ms / 1e3, pairs, world, dev)
     value = pairs_job / t_job
     solves_per_s = world * args.steps / t_job
 

@@ -515,8 +515,13 @@ struct GPtr {     // per-system views into the gstate buffer
   double *H, *cs, *sn, *g, *y, *nrm;
   double *h1p, *h2p, *nrmp;   // per-chunk partial sums of the dot products and the norm
   int* nact;                  // systems still active after the current Arnoldi step
+  unsigned int* bar;          // grid barrier of the fused single-system step: count, generation, error
+  double* fp;                 // its per-block partial sums (two dot-product sets and the norm)
   int S, m, CH;
 };
+
+// blocks of the fused single-system Arnoldi step (each holds a slice of the vectors)
+constexpr int kFusedBlocks = 64;
 
 // Row chunks per system of the Arnoldi reductions: a few systems get one block per
 // component row (so that a single suspension still spreads over many SMs), large
@@ -525,7 +530,7 @@ int arnoldi_chunks(int S, int h) { return S >= 64 ? 1 : h; }
 
 size_t gstate_doubles(int m, int S, int CH) {
   return (size_t)S * (sizeof(GDev) / sizeof(double) + 1) + (size_t)S * ((size_t)(m + 1) * m + 5 * (size_t)(m + 1) + 1) +
-         (size_t)S * CH * (2 * (size_t)(m + 1) + 1) + 16;
+         (size_t)S * CH * (2 * (size_t)(m + 1) + 1) + (size_t)kFusedBlocks * (2 * (size_t)(m + 1) + 1) + 24;
 }
 
 GPtr gptrs(void* base, int m, int S, int CH) {
@@ -545,6 +550,10 @@ GPtr gptrs(void* base, int m, int S, int CH) {
   p.h2p = d; d += (size_t)S * (m + 1) * CH;
   p.nrmp = d; d += (size_t)S * CH;
   p.nact = reinterpret_cast<int*>(d);
+  d += 1;
+  p.bar = reinterpret_cast<unsigned int*>(d);
+  d += 2;
+  p.fp = d;
   return p;
 }
 
@@ -654,33 +663,21 @@ __global__ void bk_norm_sum(const double* __restrict__ part, const GDev* __restr
 // Hessenberg column j_s, Givens rotations, residual estimate and stopping test of one
 // system per block (parallel loads to shared memory, one thread sweeps the rotations).
 constexpr int kGmMaxM = 128;
-__global__ void bk_finalize(GPtr p) {
-  const int s = blockIdx.x;
+// Hessenberg column j of system s (col[0..j] = the two Gram-Schmidt coefficient sums,
+// in shared memory, overwritten), new norm hn: apply the previous rotations, form the
+// new one, update g, the residual estimate and the stopping test, store the column.
+// Called by one block per system; thread 0 does the serial part.
+__device__ void givens_step(const GPtr& p, int s, int j, double hn, double* col, double* scs, double* ssn) {
   GDev* st = p.st + s;
-  if (!st->active) return;
-  __shared__ double col[kGmMaxM + 1], scs[kGmMaxM], ssn[kGmMaxM];
-  const int j = st->j, m = p.m;
+  const int m = p.m;
   const size_t o1 = (size_t)s * (m + 1);
   const int tid = threadIdx.x;
-  for (int i = tid; i <= j; i += blockDim.x) {
-    const double* a1 = p.h1p + (o1 + i) * p.CH;
-    const double* a2 = p.h2p + (o1 + i) * p.CH;
-    double c1 = 0.0, c2 = 0.0;
-    for (int c = 0; c < p.CH; ++c) {
-      c1 += a1[c];
-      c2 += a2[c];
-    }
-    col[i] = c1 + c2;
-  }
   for (int i = tid; i < j; i += blockDim.x) {
     scs[i] = p.cs[o1 + i];
     ssn[i] = p.sn[o1 + i];
   }
   __syncthreads();
   if (tid == 0) {
-    double nrm = 0.0;
-    for (int c = 0; c < p.CH; ++c) nrm += p.nrmp[(size_t)s * p.CH + c];
-    const double hn = sqrt(fmax(0.0, nrm));
     for (int i = 0; i < j; ++i) {
       const double t1 = col[i], t2 = col[i + 1];
       col[i] = scs[i] * t1 + ssn[i] * t2;
@@ -716,6 +713,33 @@ __global__ void bk_finalize(GPtr p) {
   for (int i = tid; i <= j + 1; i += blockDim.x) H[(size_t)i * m + j] = col[i];
 }
 
+__global__ void bk_finalize(GPtr p) {
+  const int s = blockIdx.x;
+  GDev* st = p.st + s;
+  if (!st->active) return;
+  __shared__ double col[kGmMaxM + 1], scs[kGmMaxM], ssn[kGmMaxM];
+  const int j = st->j, m = p.m;
+  const size_t o1 = (size_t)s * (m + 1);
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+    const double* a1 = p.h1p + (o1 + i) * p.CH;
+    const double* a2 = p.h2p + (o1 + i) * p.CH;
+    double c1 = 0.0, c2 = 0.0;
+    for (int c = 0; c < p.CH; ++c) {
+      c1 += a1[c];
+      c2 += a2[c];
+    }
+    col[i] = c1 + c2;
+  }
+  __shared__ double s_hn;
+  if (threadIdx.x == 0) {
+    double nrm = 0.0;
+    for (int c = 0; c < p.CH; ++c) nrm += p.nrmp[(size_t)s * p.CH + c];
+    s_hn = sqrt(fmax(0.0, nrm));
+  }
+  __syncthreads();
+  givens_step(p, s, j, s_hn, col, scs, ssn);
+}
+
 // Arnoldi source of the next pair pass, written by the kernels that produce V_j:
 // FP32 records (PairArgs::x32, ncp floats per sphere, zero padding) or FP64
 // component-major, both scaled by the column multipliers minv.
@@ -748,6 +772,146 @@ __global__ void bk_scale(double* V, size_t n, const double* __restrict__ w, int 
   const double v = w[t] * g.inv_hn;
   V[(size_t)g.j * n + t] = v;
   write_src(src, Ntot, gridDim.y, blockIdx.y, p, v);
+}
+
+// ---------------------------------------------------------------------------------
+// Fused Arnoldi step of a single system: both Gram-Schmidt rounds, the norm, the
+// Givens update and V_{j+1} (with its pair-pass source) in one kernel of kFusedBlocks
+// blocks, each owning a contiguous slice of the vectors, separated by three grid-wide
+// barriers.  Partial sums are combined in block order by every block (identical
+// results everywhere), so the result does not depend on timing.  The blocks must be
+// co-resident: 64 blocks of 256 threads on a 152-SM GPU that runs nothing else in the
+// stream meanwhile.  Each barrier wait is bounded; a block that gives up records an
+// error (bar[2]) and returns, and the host reports GBI_ERR_TIMEOUT.
+// ---------------------------------------------------------------------------------
+
+constexpr long long kBarrierLimit = 1ll << 22;   // polling rounds (with back-off) per barrier
+
+__device__ bool grid_barrier(unsigned int* bar, int* s_ok) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned int g = atomicAdd(&bar[1], 0u);   // generation before arriving
+    __threadfence();
+    int ok = 1;
+    if (atomicAdd(&bar[0], 1u) == gridDim.x - 1) {
+      atomicExch(&bar[0], 0u);
+      __threadfence();
+      atomicAdd(&bar[1], 1u);
+    } else {
+      long long it = 0;
+      while (atomicAdd(&bar[1], 0u) == g) {
+        if (++it > kBarrierLimit) {
+          atomicExch(&bar[2], 1u);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    *s_ok = ok;
+  }
+  __syncthreads();
+  return *s_ok != 0;
+}
+
+// sum over the block in a fixed order; the leading barrier makes back-to-back calls safe
+__device__ __forceinline__ double block_sum_ordered(double v, double* sh) {
+  __syncthreads();
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  return sh[0];
+}
+
+// part[i G + b] = V_i . w over [t0, t1) for i <= j: warp k of the block takes
+// i = k, k + nwarps, ...; lanes stride the slice and a shuffle tree sums them (fixed order)
+__device__ __forceinline__ void slice_dots(const double* __restrict__ V, size_t n, const double* __restrict__ w,
+                                           int j, size_t t0, size_t t1, double* part, int G, int b) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = warp; i <= j; i += nw) {
+    const double* v = V + (size_t)i * n;
+    double acc = 0.0;
+    for (size_t t = t0 + lane; t < t1; t += 32) acc += v[t] * w[t];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) part[(size_t)i * G + b] = acc;
+  }
+}
+
+__global__ void __launch_bounds__(256) bk_step_fused(double* V, size_t n, double* w, int Ntot, int h, GPtr p,
+                                                     SrcOut so) {
+  __shared__ double sh[256];
+  __shared__ double c1[kGmMaxM + 1], c2[kGmMaxM + 1], scs[kGmMaxM], ssn[kGmMaxM];
+  __shared__ double s_hn;
+  __shared__ int s_ok;
+  const GDev* st = p.st;
+  if (!st->active) return;   // the same decision in every block: nothing writes the state yet
+  const int j = st->j, m = p.m;
+  const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
+  const size_t L = (n + G - 1) / G;
+  const size_t t0 = (size_t)b * L, t1 = min(n, t0 + L);
+  double* part1 = p.fp;
+  double* part2 = p.fp + (size_t)(m + 1) * G;
+  double* partn = p.fp + 2 * (size_t)(m + 1) * G;
+  // (A) partial V_i . w: warp w of the block takes i = w, w + 8, ... (no block barrier)
+  slice_dots(V, n, w, j, t0, t1, part1, G, b);
+  if (!grid_barrier(p.bar, &s_ok)) return;
+  // (B) w1 = w - sum c1_i V_i on the slice, then partial V_i . w1
+  for (int i = tid; i <= j; i += blockDim.x) {
+    double c = 0.0;
+    for (int q = 0; q < G; ++q) c += part1[(size_t)i * G + q];
+    c1[i] = c;
+  }
+  __syncthreads();
+  for (size_t t = t0 + tid; t < t1; t += blockDim.x) {
+    double a = w[t];
+    for (int i = 0; i <= j; ++i) a -= c1[i] * V[(size_t)i * n + t];
+    w[t] = a;
+  }
+  __syncthreads();
+  slice_dots(V, n, w, j, t0, t1, part2, G, b);
+  if (!grid_barrier(p.bar, &s_ok)) return;
+  // (C) w2 = w1 - sum c2_i V_i, partial |w2|^2
+  for (int i = tid; i <= j; i += blockDim.x) {
+    double c = 0.0;
+    for (int q = 0; q < G; ++q) c += part2[(size_t)i * G + q];
+    c2[i] = c;
+  }
+  __syncthreads();
+  double nacc = 0.0;
+  for (size_t t = t0 + tid; t < t1; t += blockDim.x) {
+    double a = w[t];
+    for (int i = 0; i <= j; ++i) a -= c2[i] * V[(size_t)i * n + t];
+    w[t] = a;
+    nacc += a * a;
+  }
+  nacc = block_sum_ordered(nacc, sh);
+  if (tid == 0) partn[b] = nacc;
+  if (!grid_barrier(p.bar, &s_ok)) return;
+  // (D) h_{j+1,j} = |w2|, V_{j+1} = w2 / h and its source; block 0 updates the rotations
+  if (tid == 0) {
+    double nrm = 0.0;
+    for (int q = 0; q < G; ++q) nrm += partn[q];
+    s_hn = sqrt(fmax(0.0, nrm));
+  }
+  __syncthreads();
+  const double hn = s_hn;
+  const double inv = hn > 1e-300 ? 1.0 / hn : 0.0;
+  for (size_t t = t0 + tid; t < t1; t += blockDim.x) {
+    const double v = w[t] * inv;
+    V[(size_t)(j + 1) * n + t] = v;
+    const int q = int(t / (size_t)Ntot);
+    write_src(so, Ntot, h, q, int(t - (size_t)q * Ntot), v);
+  }
+  if (b == 0) {
+    for (int i = tid; i <= j; i += blockDim.x) c1[i] += c2[i];
+    __syncthreads();
+    givens_step(p, 0, j, hn, c1, scs, ssn);
+  }
 }
 
 // End of one device-looped Arnoldi step: keep looping while any system is still active
@@ -880,9 +1044,13 @@ SrcOut src_out(const Setup& s, int precision, void* xsrc) {
 
 // kChunk Arnoldi iterations of every active system: pair pass on the source of V_j
 // (written by the previous bk_scale / bk_scale0), two rounds of classical Gram-Schmidt,
-// norm, Givens update and V_{j+1} with its source -- eight kernels per iteration.
+// norm, Givens update and V_{j+1} with its source -- eight kernels per iteration.  With
+// fused set and a single system the seven kernels after the pair pass are replaced by
+// bk_step_fused; that is faster for direct launches, while inside the cycle graph the
+// separate kernels (graph launch overhead about a microsecond each) measured faster than
+// the fused kernel's three grid barriers.
 gbi_status launch_chunk(gbi_ctx* ctx, const Setup& s, const Batch& B, int precision, const GPtr& gp, int m,
-                        double* Vb, double* w, void* xsrc, int kChunk) {
+                        double* Vb, double* w, void* xsrc, int kChunk, bool fused) {
   const int S = B.S, Ntot = B.Ntot, h = s.h;
   const size_t n = (size_t)Ntot * h;
   const dim3 g2((Ntot + 255) / 256, h);
@@ -897,6 +1065,12 @@ gbi_status launch_chunk(gbi_ctx* ctx, const Setup& s, const Batch& B, int precis
   const dim3 gd(S, m + 1, gp.CH);
   for (int c = 0; c < kChunk; ++c) {
     GBI_CHECK(run_pairs(ctx, s.trunc, SET_H, SET_H, precision, pa));
+    if (fused && S == 1) {
+      // a single system launched step by step: the whole orthogonalisation in one kernel
+      bk_step_fused<<<kFusedBlocks, 256, 0, ctx->stream>>>(Vb, n, w, Ntot, h, gp, so);
+      ++ctx->launches;
+      continue;
+    }
     bk_dots<<<gd, 256, 0, ctx->stream>>>(Vb, n, w, Ntot, h, B.off, gp.st, m, gp.CH, gp.h1p);
     bk_sub<<<g2, 256, 0, ctx->stream>>>(Vb, n, w, Ntot, B.sys, gp.st, m, gp.CH, gp.h1p);
     bk_dots<<<gd, 256, 0, ctx->stream>>>(Vb, n, w, Ntot, h, B.off, gp.st, m, gp.CH, gp.h2p);
@@ -918,6 +1092,10 @@ __global__ void bk_setup(GPtr p, double tol, int max_iter, double outer_rtol) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= p.S) return;
   GDev* st = p.st + s;
+  if (s == 0) {
+    p.bar[0] = 0u;   // arrivals
+    p.bar[2] = 0u;   // error flag
+  }
   st->tol = outer_rtol > 0 ? fmax(tol, 0.1 * outer_rtol / fmax(st->rel, 1e-300)) : tol;
   st->max_iter = max_iter;
   st->m = p.m;
@@ -978,7 +1156,7 @@ gbi_status gmres_batch(gbi_ctx* ctx, const Setup& s, const Batch& B, int precisi
         e = cudaStreamBeginCaptureToGraph(ctx->stream, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
                                           cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-          st = launch_chunk(ctx, s, B, precision, gp, m, Vb, w, xsrc, 1);
+          st = launch_chunk(ctx, s, B, precision, gp, m, Vb, w, xsrc, 1, false);
           bk_continue<<<1, 1, 0, ctx->stream>>>(gp, handle);
           ++ctx->launches;
           cudaGraph_t body = nullptr;
@@ -1040,10 +1218,18 @@ gbi_status gmres_batch(gbi_ctx* ctx, const Setup& s, const Batch& B, int precisi
       return live;
     };
     auto read_states = [&]() -> gbi_status {
-      ctx->hbatch.resize(sizeof(GDev) * S);
+      ctx->hbatch.resize(sizeof(GDev) * S + sizeof(unsigned int) * 3);
       GBI_CHECK(cudaMemcpyAsync(ctx->hbatch.data(), gp.st, sizeof(GDev) * S, cudaMemcpyDeviceToHost, ctx->stream));
+      GBI_CHECK(cudaMemcpyAsync(ctx->hbatch.data() + sizeof(GDev) * S, gp.bar, sizeof(unsigned int) * 3,
+                                cudaMemcpyDeviceToHost, ctx->stream));
       GBI_CHECK(cudaStreamSynchronize(ctx->stream));
       std::memcpy(hst.data(), ctx->hbatch.data(), sizeof(GDev) * S);
+      unsigned int bar[3];
+      std::memcpy(bar, ctx->hbatch.data() + sizeof(GDev) * S, sizeof(bar));
+      if (bar[2] != 0u) {
+        ctx->err = "fused Arnoldi step: a grid barrier wait gave up";
+        return GBI_ERR_TIMEOUT;
+      }
       return GBI_OK;
     };
     if (graphs) {
@@ -1061,7 +1247,7 @@ gbi_status gmres_batch(gbi_ctx* ctx, const Setup& s, const Batch& B, int precisi
       bool any = false;
       for (int q = 0; q < S; ++q) any = any || hst[q].active;
       while (any) {
-        GBI_TRY(launch_chunk(ctx, s, B, precision, gp, m, Vb, w, xsrc, kChunk));
+        GBI_TRY(launch_chunk(ctx, s, B, precision, gp, m, Vb, w, xsrc, kChunk, true));
         GBI_TRY(read_states());
         account(kChunk);
         any = false;
@@ -2226,7 +2412,8 @@ constexpr size_t kOffX32 = kOffMin + 256;
 constexpr size_t kOffGs = kOffX32 + al256(sizeof(float) * 2 * (kStaticMaxND + 3 * kStaticMaxN));
 constexpr size_t kOffBoff = kOffGs + al256(sizeof(double) * (64 + (kStaticMaxRestart + 1) * kStaticMaxRestart +
                                                               8 * (kStaticMaxRestart + 1) +
-                                                              48 * (2 * (kStaticMaxRestart + 1) + 1)));
+                                                              48 * (2 * (kStaticMaxRestart + 1) + 1) +
+                                                              kFusedBlocks * (2 * (kStaticMaxRestart + 1) + 1) + 24));
 constexpr size_t kOffBsys = kOffBoff + 256;
 constexpr size_t kStaticBytes = kOffBsys + al256(sizeof(int) * kStaticMaxN);
 
