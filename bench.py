@@ -546,7 +546,9 @@ def run_ours(args):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "precision": {0: "FP64 throughout", 1: "FP32 pair sums in GMRES; FP64 RHS, residuals, outputs; FP64 "
                               "Arnoldi/Givens", 2: "FP32 pair sums in GMRES; double-float (FP32-pipe, ~48-bit) RHS, "
-                              "residuals, outputs; FP64 Arnoldi/Givens"}[args.precision],
+                              "residuals, outputs; FP64 Arnoldi/Givens",
+                              3: "FP32 pair sums in GMRES, RHS and outputs; double-float refinement residuals; "
+                              "FP64 Arnoldi/Givens"}[args.precision],
                 "data": "synthetic",
                 "config": {"workload": c["name"], "N": N, "trunc": trunc, "h": h, "volume_fraction": 0.05,
                            "min_sep_a": 2.5, "rtol": 1e-10, "restart": 40, "inner_rtol": 1e-5,
@@ -576,8 +578,9 @@ def main():
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", type=int, default=2, choices=[0, 1, 2],
-                    help="0 all FP64; 1 FP32 GMRES + FP64 refinement; 2 FP32 GMRES + double-float refinement")
+    ap.add_argument("--precision", type=int, default=3, choices=[0, 1, 2, 3],
+                    help="0 all FP64; 1 FP32 GMRES + FP64 refinement; 2 FP32 GMRES + double-float refinement, "
+                         "RHS and outputs; 3 as 2 with FP32 RHS and outputs")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

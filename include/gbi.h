@@ -58,7 +58,11 @@ typedef struct {
                      /*    FP64 right-hand side, residuals and outputs (iterative         */
                      /*    refinement); 2: as 1 but those FP64 passes run in double-float */
                      /*    arithmetic (pairs of floats, ~48-bit significand) on the FP32  */
-                     /*    pipe.  Arnoldi, Givens and the solution update stay FP64.      */
+                     /*    pipe; 3: as 2 but the right-hand side and the output pass in   */
+                     /*    FP32 too (only the refinement residual in double-float), so    */
+                     /*    V and Omega carry FP32 pair-sum rounding (~1e-7 relative) while */
+                     /*    the traction solve still meets rtol for that right-hand side. */
+                     /*    Arnoldi, Givens and the solution update stay FP64.             */
   double rtol;       /* target relative residual ||b - A q|| / ||b|| of the traction solve */
   int restart;       /* GMRES restart length (Krylov vectors per cycle), 1..128          */
   int max_iter;      /* cap on inner GMRES iterations over the whole solve               */
@@ -160,8 +164,8 @@ gbi_status gbi_solve_host(gbi_ctx* ctx, const gbi_params* params, int N,
  * remains.  params.trunc = 2 uses the closed-form trap kernel (Stokeslet/RPY,
  * rotlet, stresslet and potential dipole with their finite-size terms);
  * trunc 3, 4 use the general pair operator.  Arguments as gbi_solve (no QH).
- * params.precision selects FP32 (1) or FP64 (0) pair arithmetic; 2 selects FP64 for the
- * closed-form kernel and double-float for the general one.  Asynchronous. */
+ * params.precision selects FP32 (1 or 3) or FP64 (0) pair arithmetic; 2 selects FP64 for
+ * the closed-form kernel and double-float for the general one.  Asynchronous. */
 gbi_status gbi_superpose(gbi_ctx* ctx, const gbi_params* params, int N,
                          const double* R, const double* Va, const double* Oa, const double* VH,
                          const double* Fe, const double* Te, double* V, double* Omega);

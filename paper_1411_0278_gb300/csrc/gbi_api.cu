@@ -1276,7 +1276,7 @@ bool valid_params(const gbi_params* p) {
   if (!p) return false;
   if (!(p->a > 0) || !(p->eta > 0)) return false;
   if (p->trunc < 2 || p->trunc > 4) return false;
-  if (p->precision < 0 || p->precision > 2) return false;
+  if (p->precision < 0 || p->precision > 3) return false;
   return true;
 }
 
@@ -1298,8 +1298,10 @@ gbi_status solve_core(gbi_ctx* ctx, const gbi_params* prm, const Batch& B, const
   const size_t nh = (size_t)N * h;
   const dim3 g2((N + 255) / 256, h);
   const int sblk = (S + 127) / 128;
-  // arithmetic of the passes that need more than FP32: FP64, or double-float (precision 2)
-  const int hp = prm->precision == 2 ? 2 : 0;
+  // arithmetic of the refinement residual (FP64, or double-float for precision 2 and 3)
+  // and of the right-hand-side and output passes (the same, or FP32 for precision 3)
+  const int hp = prm->precision >= 2 ? 2 : 0;
+  const int io = prm->precision == 3 ? 1 : hp;
   const int restart = std::max(1, std::min(prm->restart > 0 ? prm->restart : 40, kMaxRestart));
   GBI_TRY(ensure(ctx, ctx->xQ, sizeof(double) * (size_t)N * D));
   GBI_TRY(ensure(ctx, ctx->xVH, sizeof(double) * nh));
@@ -1339,8 +1341,8 @@ gbi_status solve_core(gbi_ctx* ctx, const gbi_params* prm, const Batch& B, const
   {
     PairArgs p = batched(pair_args(s, xF, b, -1.0, 1.0, 0, s.ones, 0), nullptr);
     p.min_r2_bits = P<unsigned int>(ctx->minr2);
-    GBI_CHECK(run_pairs(ctx, s.trunc, SET_H, SET_L, hp, p));
-    inf->matvecs_f64 += 1;
+    GBI_CHECK(run_pairs(ctx, s.trunc, SET_H, SET_L, io, p));
+    (io == 1 ? inf->matvecs_f32 : inf->matvecs_f64) += 1;
     inf->pair_interactions += pairs_all;
   }
   if (prm->min_sep > 0) {
@@ -1449,8 +1451,8 @@ gbi_status solve_core(gbi_ctx* ctx, const gbi_params* prm, const Batch& B, const
     PairArgs p = batched(pair_args(s, P<double>(ctx->xQ), P<double>(ctx->xVL), -1.0 / (8.0 * kPi * s.eta), 0.0, 1,
                                    s.ones, 0),
                          nullptr);
-    GBI_CHECK(run_pairs(ctx, s.trunc, SET_L, SET_ALL, hp, p));
-    inf->matvecs_f64 += 1;
+    GBI_CHECK(run_pairs(ctx, s.trunc, SET_L, SET_ALL, io, p));
+    (io == 1 ? inf->matvecs_f32 : inf->matvecs_f64) += 1;
     inf->pair_interactions += pairs_all;
   }
   k_finalize_lower<<<grid1(N), 256, 0, ctx->stream>>>(N, s.a, c2a, P<double>(ctx->xVL), Va, Oa, V, Omega);
@@ -1928,7 +1930,7 @@ gbi_status gbi_batch_superpose(gbi_ctx* ctx, const gbi_params* prm, int nsys, co
                          0);
   p.sys_of = B.sys;
   p.sys_off = B.off;
-  GBI_CHECK(run_pairs(ctx, s.trunc, SET_L, SET_ALL, prm->precision, p));
+  GBI_CHECK(run_pairs(ctx, s.trunc, SET_L, SET_ALL, prm->precision == 3 ? 1 : prm->precision, p));
   k_finalize_lower<<<grid1(N), 256, 0, ctx->stream>>>(N, s.a, s.scale.v[3], P<double>(ctx->xVL), Va, Oa, V,
                                                       Omega);
   ++ctx->launches;
@@ -1957,7 +1959,7 @@ gbi_status gbi_superpose(gbi_ctx* ctx, const gbi_params* prm, int N, const doubl
     t.Oa = Oa;
     t.V = V;
     t.Om = Omega;
-    GBI_CHECK(run_trap(ctx, t, prm->precision));
+    GBI_CHECK(run_trap(ctx, t, prm->precision == 3 ? 1 : prm->precision));
     return GBI_OK;
   }
   const int D = s.D, h = s.h;
@@ -1974,7 +1976,7 @@ gbi_status gbi_superpose(gbi_ctx* ctx, const gbi_params* prm, int N, const doubl
   ++ctx->launches;
   PairArgs p = pair_args(s, P<double>(ctx->xQ), P<double>(ctx->xVL), -1.0 / (8.0 * kPi * s.eta), 0.0, 1, s.ones,
                          0);
-  GBI_CHECK(run_pairs(ctx, s.trunc, SET_L, SET_ALL, prm->precision, p));
+  GBI_CHECK(run_pairs(ctx, s.trunc, SET_L, SET_ALL, prm->precision == 3 ? 1 : prm->precision, p));
   k_finalize_lower<<<grid1(N), 256, 0, ctx->stream>>>(N, s.a, s.scale.v[3], P<double>(ctx->xVL), Va, Oa, V,
                                                       Omega);
   ++ctx->launches;
@@ -2012,7 +2014,7 @@ gbi_status gbi_trap_step(gbi_ctx* ctx, const gbi_params* prm, int N, double dt, 
       GBI_TRY(gbi_superpose(ctx, prm, N, R, P<double>(ctx->tVa), P<double>(ctx->tOa), P<double>(ctx->tVH),
                             P<double>(ctx->tFe), P<double>(ctx->tTe), P<double>(ctx->tV), P<double>(ctx->tOm)));
       total.pair_interactions += (long long)N * (N - 1);
-      (prm->precision == 1 ? total.matvecs_f32 : total.matvecs_f64) += 1;
+      (prm->precision == 1 || prm->precision == 3 ? total.matvecs_f32 : total.matvecs_f64) += 1;
     } else {
       gbi_info one{};
       // FP64 solves warm-start from the previous step's traction coefficients (also across

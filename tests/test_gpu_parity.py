@@ -198,20 +198,24 @@ def _solve_case(gbi, ctx, R, p, s, trunc, precision, d0=0.02, Te_scale=0.01, rto
 
 
 @pytest.mark.parametrize("trunc,N", [(2, 64), (3, 40), (4, 24)])
-@pytest.mark.parametrize("precision", [0, 1, 2])
+@pytest.mark.parametrize("precision", [0, 1, 2, 3])
 def test_solve_matches_dense_lu(ctx, gbi, trunc, N, precision):
+    """Precision 3 sums the right-hand side and the outputs in FP32: V, Omega and Q^H then
+    carry FP32 pair-sum rounding, bounded here by the 1e-5 pair-velocity bar (the
+    residual of the solve for that right-hand side still meets 1e-10)."""
     R, p, s = cloud(N, 20 + trunc)
     inp, V, Om, QH, info = _solve_case(gbi, ctx, R, p, s, trunc, precision)
     Vr, Omr, QHr = galerkin.solve(R, inp["Va"], inp["Oa"], inp["VH"], inp["Fe"], inp["Te"], s["a"], s["eta"], trunc)
+    tol_v, tol_q = (1e-5, 1e-5) if precision == 3 else (1e-9, 1e-8)
     assert info.rel_residual <= 1e-10
-    assert relerr(V, Vr) < 1e-9
-    assert relerr(Om, Omr) < 1e-9
+    assert relerr(V, Vr) < tol_v
+    assert relerr(Om, Omr) < tol_v
     # per mode: every H block of Q^H against the oracle
     MB = tensors.ModeBasis(trunc)
     off = 0
     for (name, L, sig) in MB.hmodes:
         k = 2 * (L - sig) + 1
-        assert relerr(QH[:, off:off + k], QHr[:, off:off + k]) < 1e-8, name
+        assert relerr(QH[:, off:off + k], QHr[:, off:off + k]) < tol_q, name
         off += k
     assert info.pair_interactions == (info.matvecs_f32 + info.matvecs_f64) * N * (N - 1)
     if precision >= 1:
