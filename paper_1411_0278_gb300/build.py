@@ -1,6 +1,6 @@
 """Build step: regenerate the pair-frame tables and compile libgbi.so for sm_103a.
 
-The four translation units are compiled in parallel with nvcc (one -gencode,
+The translation units are compiled in parallel with nvcc (one -gencode,
 sm_103a only) and linked into ``_build/libgbi.so`` inside the package, where the
 binding loads it.  Nothing is installed outside the source tree.
 """
@@ -14,7 +14,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libgbi.so")
-SOURCES = ["gbi_api.cu", "trap_kernel.cu", "mlp_kernel.cu", "mlp_tc.cu"] + ["pairs_%s_%d.cu" % (p, t) for p in ("f32", "f64", "df") for t in (2, 3, 4)]
+SOURCES = ["gbi_api.cu", "common.cu", "solver.cu", "nearfield_api.cu", "trap_kernel.cu", "mlp_kernel.cu",
+           "mlp_tc.cu"] + ["pairs_%s_%d.cu" % (p, t) for p in ("f32", "f64", "df") for t in (2, 3, 4)]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wno-deprecated-declarations",
          "-diag-suppress", "177"]

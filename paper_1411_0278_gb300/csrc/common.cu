@@ -1,0 +1,367 @@
+// Shared parts of libgbi: pair-pass dispatch and bookkeeping, workspace management,
+// input packing kernels, per-call set-up and batch layouts.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "ctx.cuh"
+
+namespace gbi {
+#define GBI_DECL(P)                                                                       \
+  cudaError_t launch_pairs_##P##_2(int, int, const PairArgs&, cudaStream_t);              \
+  cudaError_t launch_pairs_##P##_3(int, int, const PairArgs&, cudaStream_t);              \
+  cudaError_t launch_pairs_##P##_4(int, int, const PairArgs&, cudaStream_t);
+GBI_DECL(f32)
+GBI_DECL(f64)
+GBI_DECL(df)
+#undef GBI_DECL
+
+// precision: 0 = FP64, 1 = FP32, 2 = double-float on the FP32 pipe
+cudaError_t launch_pairs(int trunc, int rows, int cols, int precision, const PairArgs& args,
+                         cudaStream_t stream) {
+#define GBI_DISPATCH(P)                                                   \
+  if (trunc == 2) return launch_pairs_##P##_2(rows, cols, args, stream);  \
+  if (trunc == 3) return launch_pairs_##P##_3(rows, cols, args, stream);  \
+  if (trunc == 4) return launch_pairs_##P##_4(rows, cols, args, stream);  \
+  return cudaErrorInvalidValue;
+  if (precision == 1) { GBI_DISPATCH(f32) }
+  if (precision == 2) { GBI_DISPATCH(df) }
+  GBI_DISPATCH(f64)
+#undef GBI_DISPATCH
+}
+
+double pair_flops(int trunc, int rows, int cols) {
+  if (rows < 0 || rows > 2 || cols < 0 || cols > 2) return 0.0;
+  if (trunc == 2) return gbi_t2_flops[rows][cols];
+  if (trunc == 3) return gbi_t3_flops[rows][cols];
+  if (trunc == 4) return gbi_t4_flops[rows][cols];
+  return 0.0;
+}
+}  // namespace gbi
+
+namespace gbi {
+
+gbi_status fail(gbi_ctx* c, cudaError_t e, const char* where) {
+  if (e == cudaSuccess) return GBI_OK;
+  // the allocation-free entry point keeps no message (it has no handle to read it from)
+  if (!c->fixed) c->err = std::string(where) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? GBI_ERR_NOMEM : GBI_ERR_CUDA;
+}
+
+gbi_status host_scratch(gbi_ctx* ctx, size_t bytes) {
+  if (bytes <= ctx->hs_cap) return GBI_OK;
+  if (ctx->fixed) return GBI_ERR_NOMEM;   // static storage: never reallocated
+  ctx->hs_own.resize(bytes);
+  ctx->hs = ctx->hs_own.data();
+  ctx->hs_cap = bytes;
+  return GBI_OK;
+}
+
+gbi_status ensure(gbi_ctx* ctx, Buf& b, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (b.bytes >= bytes) return GBI_OK;
+  if (ctx->fixed) return GBI_ERR_NOMEM;   // static storage: never reallocated
+  if (b.p) {
+    GBI_CHECK(cudaStreamSynchronize(ctx->stream));
+    GBI_CHECK(cudaFree(b.p));
+    b.p = nullptr;
+    b.bytes = 0;
+  }
+  GBI_CHECK(cudaMalloc(&b.p, bytes));
+  b.bytes = bytes;
+  return GBI_OK;
+}
+
+cudaEvent_t take_event(gbi_ctx* ctx) {
+  if (!ctx->pool.empty()) {
+    cudaEvent_t e = ctx->pool.back();
+    ctx->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Resolve recorded event pairs into per-class totals (blocks on the last one).
+void drain_profile(gbi_ctx* ctx) {
+  for (auto& r : ctx->pending) {
+    cudaEventSynchronize(r.b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, r.a, r.b);
+    ctx->stat_ms[r.cls] += ms;
+    ctx->stat_flops[r.cls] += r.flops;
+    ctx->stat_n[r.cls] += 1;
+    ctx->pool.push_back(r.a);
+    ctx->pool.push_back(r.b);
+  }
+  ctx->pending.clear();
+}
+
+// Source records of the FP32 / double-float passes (see PairArgs::x32): from the
+// component-major [nc][N] block x (optionally device-indexed; skipped when the
+// device-side solver has stopped), rec[m] = float(x[.][m] * cs) padded with zeros to
+// ncp floats (double-float: then the lo block).  One block per 32 spheres, transposed
+// through shared memory so that both the reads and the writes are coalesced.
+template <bool DFL>
+__global__ void k_records(int N, int nc, int ncp, const double* __restrict__ x, const int* xi, size_t xs,
+                          const int* active, ColScale cs, float* __restrict__ rec) {
+  extern __shared__ float tile[];   // [32][rf + 1]
+  if (active != nullptr && *active == 0) return;
+  if (xi != nullptr) x += (size_t)(*xi) * xs;
+  const int rf = DFL ? 2 * ncp : ncp;
+  const int m0 = blockIdx.x * 32;
+  const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int m = m0 + lane;
+  for (int q = wy; q < ncp; q += nw) {
+    float h = 0.f, l = 0.f;
+    if (q < nc && m < N) {
+      const double v = x[(size_t)q * N + m] * cs.v[q];
+      h = float(v);
+      l = float(v - double(h));
+    }
+    tile[lane * (rf + 1) + q] = h;
+    if (DFL) tile[lane * (rf + 1) + ncp + q] = l;
+  }
+  __syncthreads();
+  const int cnt = min(32, N - m0);
+  for (int i = threadIdx.x; i < cnt * rf; i += blockDim.x) {
+    const int r = i / rf, c = i - r * rf;
+    rec[(size_t)(m0 + r) * rf + c] = tile[r * (rf + 1) + c];
+  }
+}
+
+cudaError_t launch_records(bool dfl, int N, int nc, const double* x, const int* xi, size_t xs, const int* active,
+                           const ColScale& cs, float* rec, cudaStream_t stream) {
+  const int ncp = (nc + 3) & ~3;
+  const int rf = dfl ? 2 * ncp : ncp;
+  const size_t smem = sizeof(float) * 32 * (rf + 1);
+  const dim3 grid((N + 31) / 32), block(256);
+  if (dfl) k_records<true><<<grid, block, smem, stream>>>(N, nc, ncp, x, xi, xs, active, cs, rec);
+  else k_records<false><<<grid, block, smem, stream>>>(N, nc, ncp, x, xi, xs, active, cs, rec);
+  return cudaGetLastError();
+}
+
+int ncols_of(int trunc, int cols) {
+  const int D = trunc == 2 ? GbiTrunc2::D : trunc == 3 ? GbiTrunc3::D : GbiTrunc4::D;
+  return cols == SET_L ? 6 : cols == SET_H ? D - 6 : D;
+}
+
+cudaError_t run_pairs(gbi_ctx* ctx, int trunc, int rows, int cols, int precision, const PairArgs& args_in) {
+  const double flops = pair_flops(trunc, rows, cols) * double(args_in.N) * double(args_in.N - 1);
+  PairArgs args = args_in;
+  int extra = 0;
+  if (args.wpt == 0)
+    args.wpt = ctx->force_wpt > 0 ? ctx->force_wpt
+                                  : ctx->tuned_wpt(trunc, rows, cols, precision, args.N, args.sys_of != nullptr);
+  if (precision == 2 || (precision == 1 && args.x32 == nullptr)) {
+    // per-sphere source records (FP32, or the double-float hi/lo pair), once per pass,
+    // so that the pair loop touches no FP64
+    const int nc = ncols_of(trunc, cols);
+    const size_t bytes = sizeof(float) * rec_floats(nc, precision == 2) * (size_t)args.N;
+    if (ensure(ctx, ctx->x32, bytes) != GBI_OK) return cudaErrorMemoryAllocation;
+    ColScale cs;
+    const int c0 = cols == SET_H ? 6 : 0;
+    for (int i = 0; i < 54; ++i) cs.v[i] = (i < nc) ? args.colscale[c0 + i] : 1.0;
+    const cudaError_t e = launch_records(precision == 2, args.N, nc, args.x, args.x_index, args.x_stride,
+                                         args.active, cs, P<float>(ctx->x32), ctx->stream);
+    if (e != cudaSuccess) return e;
+    args.x32 = P<float>(ctx->x32);
+    extra = 1;
+  }
+  return timed(ctx, precision * 9 + rows * 3 + cols, flops, 1 + extra,
+               [&] { return launch_pairs(trunc, rows, cols, precision, args, ctx->stream); });
+}
+
+cudaError_t run_trap(gbi_ctx* ctx, const TrapArgs& t, int precision) {
+  const double flops = trap_flops() * double(t.N) * double(t.N - 1);
+  if (ensure(ctx, ctx->trapbuf, trap_scratch_bytes(t.N, precision)) != GBI_OK) return cudaErrorMemoryAllocation;
+  return timed(ctx, precision == 1 ? 28 : 27, flops, 3,
+               [&] { return launch_trap(t, precision, ctx->trapbuf.p, ctx->stream); });
+}
+
+int d_of(int trunc) { return trunc == 2 ? GbiTrunc2::D : trunc == 3 ? GbiTrunc3::D : trunc == 4 ? GbiTrunc4::D : -1; }
+const double* scale_tab(int trunc) { return trunc == 2 ? gbi_t2_scale : trunc == 3 ? gbi_t3_scale : gbi_t4_scale; }
+const double* self_tab(int trunc) { return trunc == 2 ? gbi_t2_self : trunc == 3 ? gbi_t3_self : gbi_t4_self; }
+
+// ---------------------------------------------------------------------------------
+// small kernels
+// ---------------------------------------------------------------------------------
+
+__global__ void k_positions(int N, const double* __restrict__ R, float4* hi, float4* lo, dpos4* p64) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const double x = R[3 * n], y = R[3 * n + 1], z = R[3 * n + 2];
+  const float hx = float(x), hy = float(y), hz = float(z);
+  hi[n] = make_float4(hx, hy, hz, 0.f);
+  lo[n] = make_float4(float(x - double(hx)), float(y - double(hy)), float(z - double(hz)), 0.f);
+  p64[n] = dpos4{x, y, z, 0.0};
+}
+
+// F^(1) = -F^e and F^(21) = -T^e/a in internal coordinates: xF[6][N]
+__global__ void k_pack_lower(int N, double a, double c2a, const double* __restrict__ Fe,
+                             const double* __restrict__ Te, double* xF) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const double* f = Fe + 3 * n;
+  const double* t = Te + 3 * n;
+  xF[0 * N + n] = -f[1];
+  xF[1 * N + n] = -f[2];
+  xF[2 * N + n] = -f[0];
+  xF[3 * N + n] = -c2a * t[1] / a;
+  xF[4 * N + n] = -c2a * t[2] / a;
+  xF[5 * N + n] = -c2a * t[0] / a;
+}
+
+// packed [N][h] -> internal component-major [h][N] times scale * mult
+__global__ void k_pack_higher(int N, int h, const double* __restrict__ VH, Scales sc, double mult,
+                              double* out) {
+  const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i >= (size_t)N * h) return;
+  const int n = int(i / h), p = int(i - (size_t)n * h);
+  out[(size_t)p * N + n] = mult * sc.v[p] * VH[i];
+}
+
+// internal [h][N] -> packed [N][h] divided by scale
+__global__ void k_unpack_higher(int N, int h, const double* __restrict__ x, Scales sc, double* QH) {
+  const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i >= (size_t)N * h) return;
+  const int n = int(i / h), p = int(i - (size_t)n * h);
+  QH[i] = x[(size_t)p * N + n] / sc.v[p];
+}
+
+// V = V^a + (1s part), Omega = Omega^a + (2a part)/(c_2a 2a)
+__global__ void k_finalize_lower(int N, double a, double c2a, const double* __restrict__ xVL,
+                                 const double* __restrict__ Va, const double* __restrict__ Oa,
+                                 double* V, double* Om) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const double f = 1.0 / (c2a * 2.0 * a);
+  V[3 * n + 0] = Va[3 * n + 0] + xVL[2 * N + n];
+  V[3 * n + 1] = Va[3 * n + 1] + xVL[0 * N + n];
+  V[3 * n + 2] = Va[3 * n + 2] + xVL[1 * N + n];
+  Om[3 * n + 0] = Oa[3 * n + 0] + f * xVL[5 * N + n];
+  Om[3 * n + 1] = Oa[3 * n + 1] + f * xVL[3 * N + n];
+  Om[3 * n + 2] = Oa[3 * n + 2] + f * xVL[4 * N + n];
+}
+
+// ---------------------------------------------------------------------------------
+// solver state for one call
+// ---------------------------------------------------------------------------------
+
+gbi_status setup_call(gbi_ctx* ctx, Setup& s, int N, int trunc, double a, double eta, const double* R) {
+  s.N = N;
+  s.trunc = trunc;
+  s.D = d_of(trunc);
+  s.h = s.D - 6;
+  s.a = a;
+  s.eta = eta;
+  const double* sc = scale_tab(trunc);
+  const double* sg = self_tab(trunc);
+  for (int i = 0; i < 54; ++i) {
+    s.scale.v[i] = i < s.D ? sc[i] : 1.0;
+    s.selfg.v[i] = i < s.D ? sg[i] : 0.0;
+    s.ones.v[i] = 1.0;
+    s.minv.v[i] = (i < s.h) ? a / sg[6 + i] : 1.0;
+  }
+  s.pairs_per_pass = (long long)N * (N - 1);
+  GBI_TRY(ensure(ctx, ctx->pos_hi, sizeof(float4) * N));
+  GBI_TRY(ensure(ctx, ctx->pos_lo, sizeof(float4) * N));
+  GBI_TRY(ensure(ctx, ctx->pos64, sizeof(dpos4) * N));
+  k_positions<<<grid1(N), 256, 0, ctx->stream>>>(N, R, P<float4>(ctx->pos_hi), P<float4>(ctx->pos_lo),
+                                                 P<dpos4>(ctx->pos64));
+  ++ctx->launches;
+  GBI_CHECK(cudaGetLastError());
+  s.pos = Positions{P<float4>(ctx->pos_hi), P<float4>(ctx->pos_lo), P<dpos4>(ctx->pos64)};
+  return GBI_OK;
+}
+
+PairArgs pair_args(const Setup& s, const double* x, double* y, double alpha, double beta, int add_self,
+                   const Scales& colscale, int col0) {
+  PairArgs p;
+  p.N = s.N;
+  p.a = s.a;
+  p.pos = s.pos;
+  p.x = x;
+  p.x32 = nullptr;
+  p.x32lo = nullptr;
+  p.wpt = 0;
+  p.y = y;
+  p.alpha = alpha;
+  p.beta = beta;
+  p.add_self = add_self;
+  for (int i = 0; i < 54; ++i) {
+    // colscale is indexed by absolute component; callers pass H-relative scales with col0 = 6
+    const int src = i - col0;
+    p.colscale[i] = (src >= 0 && src < 54) ? colscale.v[src] : 1.0;
+    p.selfg[i] = s.selfg.v[i];
+  }
+  p.min_r2_bits = nullptr;
+  p.x_index = nullptr;
+  p.x_stride = 0;
+  p.active = nullptr;
+  p.sys_of = nullptr;
+  p.sys_off = nullptr;
+  p.sys_flag = nullptr;
+  p.sys_flag_stride = 0;
+  return p;
+}
+
+// S = 1 batch over the spheres [0, N): offsets and system ids in the context workspace
+gbi_status single_batch(gbi_ctx* ctx, int N, Batch& B) {
+  GBI_TRY(ensure(ctx, ctx->boff, sizeof(int) * 2));
+  GBI_TRY(ensure(ctx, ctx->bsys, sizeof(int) * (size_t)std::max(N, 1)));
+  const int off[2] = {0, N};
+  GBI_CHECK(cudaMemcpyAsync(ctx->boff.p, off, sizeof(off), cudaMemcpyHostToDevice, ctx->stream));
+  GBI_CHECK(cudaMemsetAsync(ctx->bsys.p, 0, sizeof(int) * (size_t)N, ctx->stream));
+  B.S = 1;
+  B.Ntot = N;
+  B.off = P<int>(ctx->boff);
+  B.sys = P<int>(ctx->bsys);
+  B.one[0] = 0;
+  B.one[1] = N;
+  B.h_off = B.one;
+  return GBI_OK;
+}
+
+__global__ void k_fill_sys(int S, const int* __restrict__ off, int* sys) {
+  const int s = blockIdx.x;
+  for (int p = off[s] + threadIdx.x; p < off[s + 1]; p += blockDim.x) sys[p] = s;
+}
+
+bool valid_offsets(int nsys, const int* off) {
+  if (off[0] != 0) return false;
+  for (int q = 0; q < nsys; ++q)
+    if (off[q + 1] < off[q]) return false;
+  return true;
+}
+
+// Device copies of a batch layout (system offsets and the system of every sphere).
+gbi_status make_batch(gbi_ctx* ctx, int nsys, const int* offsets_host, Batch& B) {
+  const int N = offsets_host[nsys];
+  GBI_TRY(ensure(ctx, ctx->boff, sizeof(int) * (size_t)(nsys + 1)));
+  GBI_TRY(ensure(ctx, ctx->bsys, sizeof(int) * (size_t)N));
+  GBI_CHECK(cudaMemcpyAsync(ctx->boff.p, offsets_host, sizeof(int) * (size_t)(nsys + 1), cudaMemcpyHostToDevice,
+                            ctx->stream));
+  k_fill_sys<<<nsys, 256, 0, ctx->stream>>>(nsys, P<int>(ctx->boff), P<int>(ctx->bsys));
+  ++ctx->launches;
+  GBI_CHECK(cudaGetLastError());
+  B.S = nsys;
+  B.Ntot = N;
+  B.off = P<int>(ctx->boff);
+  B.sys = P<int>(ctx->bsys);
+  B.h_off = offsets_host;
+  return GBI_OK;
+}
+
+bool valid_params(const gbi_params* p) {
+  if (!p) return false;
+  if (!(p->a > 0) || !(p->eta > 0)) return false;
+  if (p->trunc < 2 || p->trunc > 4) return false;
+  if (p->precision < 0 || p->precision > 3) return false;
+  return true;
+}
+
+}  // namespace gbi

@@ -1,0 +1,996 @@
+// Device-side GMRES for one or many independent systems and the mixed-precision
+// refinement around it: per-system state, Gram-Schmidt, Givens rotations and stopping
+// tests in kernels, the Arnoldi steps of a cycle replayed from a CUDA graph with a
+// device-side WHILE loop, and the solve sequence (right-hand side, refinement sweeps,
+// output pass).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "ctx.cuh"
+
+namespace gbi {
+
+// ---------------------------------------------------------------------------------
+// Batched GMRES with its control on the device
+// ---------------------------------------------------------------------------------
+//
+// S independent systems (suspensions) share one launch per pass: every vector is
+// component-major over all spheres [h][Ntot], sphere n belongs to system sys[n] with
+// spheres [off[s], off[s+1]).  Each system has its own Krylov state, Hessenberg
+// matrix, Givens rotations, tolerance test and refinement flag; a system that has
+// stopped is skipped by every kernel.  A single suspension is the case S = 1.
+
+// Device-resident state of one system's GMRES / refinement.
+struct GDev {
+  int j;          // Arnoldi index of the vector being expanded
+  int active;     // 1 while the current cycle continues
+  int iters;      // inner iterations of the current inner solve
+  int kdim;       // Krylov dimension reached in the current cycle
+  int converged;  // relative residual estimate <= tol
+  int breakdown;  // happy breakdown (exact solution in the Krylov space)
+  int max_iter, m;
+  int enabled;    // refinement: this system still needs a correction
+  int pad;
+  double bnorm, tol, res, beta, inv_hn;
+  double nb;      // |b_s| (reference of the refinement residual)
+  double rel;     // |b_s - A q_s| / |b_s|
+  double pad2;
+};
+
+struct GPtr {     // per-system views into the gstate buffer
+  GDev* st;
+  double *H, *cs, *sn, *g, *y, *nrm;
+  double *h1p, *h2p, *nrmp;   // per-chunk partial sums of the dot products and the norm
+  int* nact;                  // systems still active after the current Arnoldi step
+  unsigned int* bar;          // grid barrier of the fused single-system step: count, generation, error
+  double* fp;                 // its per-block partial sums (two dot-product sets and the norm)
+  int S, m, CH;
+};
+
+// blocks of the fused single-system Arnoldi step (each holds a slice of the vectors)
+
+// Row chunks per system of the Arnoldi reductions: a few systems get one block per
+// component row (so that a single suspension still spreads over many SMs), large
+// batches one block per system.
+int arnoldi_chunks(int S, int h) { return S >= 64 ? 1 : h; }
+
+size_t gstate_doubles(int m, int S, int CH) {
+  return (size_t)S * (sizeof(GDev) / sizeof(double) + 1) + (size_t)S * ((size_t)(m + 1) * m + 5 * (size_t)(m + 1) + 1) +
+         (size_t)S * CH * (2 * (size_t)(m + 1) + 1) + (size_t)kFusedBlocks * (2 * (size_t)(m + 1) + 1) + 24;
+}
+
+GPtr gptrs(void* base, int m, int S, int CH) {
+  GPtr p;
+  p.S = S;
+  p.m = m;
+  p.CH = CH;
+  p.st = reinterpret_cast<GDev*>(base);
+  double* d = reinterpret_cast<double*>(base) + (size_t)S * (sizeof(GDev) / sizeof(double) + 1);
+  p.H = d; d += (size_t)S * (m + 1) * m;
+  p.cs = d; d += (size_t)S * (m + 1);
+  p.sn = d; d += (size_t)S * (m + 1);
+  p.g = d; d += (size_t)S * (m + 1);
+  p.y = d; d += (size_t)S * (m + 1);
+  p.nrm = d; d += (size_t)S;
+  p.h1p = d; d += (size_t)S * (m + 1) * CH;
+  p.h2p = d; d += (size_t)S * (m + 1) * CH;
+  p.nrmp = d; d += (size_t)S * CH;
+  p.nact = reinterpret_cast<int*>(d);
+  d += 1;
+  p.bar = reinterpret_cast<unsigned int*>(d);
+  d += 2;
+  p.fp = d;
+  return p;
+}
+
+__device__ __forceinline__ double block_sum_256(double v) {
+  __shared__ double sh[256];
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  return sh[0];
+}
+
+// part[(s (m+1) + i) CH + c] = V_i . w over the component rows of chunk c of system s,
+// for i <= j_s (block (s, i, c); fixed-order block reduction)
+__global__ void bk_dots(const double* __restrict__ V, size_t n, const double* __restrict__ w, int Ntot, int h,
+                        const int* __restrict__ off, const GDev* __restrict__ st, int m, int CH, double* part) {
+  const int s = blockIdx.x, i = blockIdx.y, c = blockIdx.z;
+  const GDev& g = st[s];
+  if (!g.active || i > g.j) return;
+  const double* v = V + (size_t)i * n;
+  const int lo = off[s], hi = off[s + 1];
+  const int q0 = c * h / CH, q1 = (c + 1) * h / CH;
+  double acc = 0.0;
+  for (int q = q0; q < q1; ++q) {
+    const size_t b = (size_t)q * Ntot;
+    for (int p = lo + threadIdx.x; p < hi; p += blockDim.x) acc += v[b + p] * w[b + p];
+  }
+  const double t = block_sum_256(acc);
+  if (threadIdx.x == 0) part[((size_t)s * (m + 1) + i) * CH + c] = t;
+}
+
+// w -= sum_{i <= j_s} coef[s][i] V_i with coef[s][i] = sum over the CH chunk partials (in
+// order).  A block whose spheres all belong to one system sums the partials once into
+// shared memory; otherwise every thread sums them for its own system.
+__global__ void bk_sub(const double* __restrict__ V, size_t n, double* w, int Ntot, const int* __restrict__ sys,
+                       const GDev* __restrict__ st, int m, int CH, const double* __restrict__ part) {
+  __shared__ double sc[kMaxRestart + 1];
+  const int p0 = blockIdx.x * blockDim.x;
+  const int pl = min(Ntot - 1, p0 + (int)blockDim.x - 1);
+  const int sb = sys[p0];
+  const bool uniform = sys[pl] == sb;
+  if (uniform) {
+    const GDev& g = st[sb];
+    if (!g.active) return;
+    for (int i = threadIdx.x; i <= g.j; i += blockDim.x) {
+      const double* q = part + ((size_t)sb * (m + 1) + i) * CH;
+      double acc = 0.0;
+      for (int c = 0; c < CH; ++c) acc += q[c];
+      sc[i] = acc;
+    }
+    __syncthreads();
+  }
+  const int p = p0 + threadIdx.x;
+  if (p >= Ntot) return;
+  const int s = sys[p];
+  const GDev& g = st[s];
+  if (!g.active) return;
+  const size_t t = (size_t)blockIdx.y * Ntot + p;
+  double acc = w[t];
+  for (int i = 0; i <= g.j; ++i) {
+    double c;
+    if (uniform) {
+      c = sc[i];
+    } else {
+      const double* q = part + ((size_t)s * (m + 1) + i) * CH;
+      c = 0.0;
+      for (int k = 0; k < CH; ++k) c += q[k];
+    }
+    acc -= c * V[(size_t)i * n + t];
+  }
+  w[t] = acc;
+}
+
+__device__ __forceinline__ bool norm_wanted(const GDev& g, int mode) {
+  return !((mode == 0 && !g.active) || (mode == 1 && !g.enabled));
+}
+
+// part[s CH + c] = |x_s|^2 over the rows of chunk c (block (s, c)); mode 0: active
+// systems, 1: enabled, 2: all
+__global__ void bk_norm_part(const double* __restrict__ x, int Ntot, int h, const int* __restrict__ off,
+                             const GDev* __restrict__ st, int mode, int CH, double* part) {
+  const int s = blockIdx.x, c = blockIdx.y;
+  if (!norm_wanted(st[s], mode)) return;
+  const int lo = off[s], hi = off[s + 1];
+  const int q0 = c * h / CH, q1 = (c + 1) * h / CH;
+  double acc = 0.0;
+  for (int q = q0; q < q1; ++q) {
+    const size_t b = (size_t)q * Ntot;
+    for (int p = lo + threadIdx.x; p < hi; p += blockDim.x) acc += x[b + p] * x[b + p];
+  }
+  const double t = block_sum_256(acc);
+  if (threadIdx.x == 0) part[(size_t)s * CH + c] = t;
+}
+
+// out[s] = sum of the chunk partials in order
+__global__ void bk_norm_sum(const double* __restrict__ part, const GDev* __restrict__ st, int S, int mode, int CH,
+                            double* __restrict__ out) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= S || !norm_wanted(st[s], mode)) return;
+  double acc = 0.0;
+  for (int c = 0; c < CH; ++c) acc += part[(size_t)s * CH + c];
+  out[s] = acc;
+}
+
+// Hessenberg column j_s, Givens rotations, residual estimate and stopping test of one
+// system per block (parallel loads to shared memory, one thread sweeps the rotations).
+constexpr int kGmMaxM = 128;
+// Hessenberg column j of system s (col[0..j] = the two Gram-Schmidt coefficient sums,
+// in shared memory, overwritten), new norm hn: apply the previous rotations, form the
+// new one, update g, the residual estimate and the stopping test, store the column.
+// Called by one block per system; thread 0 does the serial part.
+__device__ void givens_step(const GPtr& p, int s, int j, double hn, double* col, double* scs, double* ssn) {
+  GDev* st = p.st + s;
+  const int m = p.m;
+  const size_t o1 = (size_t)s * (m + 1);
+  const int tid = threadIdx.x;
+  for (int i = tid; i < j; i += blockDim.x) {
+    scs[i] = p.cs[o1 + i];
+    ssn[i] = p.sn[o1 + i];
+  }
+  __syncthreads();
+  if (tid == 0) {
+    for (int i = 0; i < j; ++i) {
+      const double t1 = col[i], t2 = col[i + 1];
+      col[i] = scs[i] * t1 + ssn[i] * t2;
+      col[i + 1] = -ssn[i] * t1 + scs[i] * t2;
+    }
+    col[j + 1] = hn;
+    const double hjj = col[j], hj1 = hn;
+    const double den = hypot(hjj, hj1);
+    const double c = den > 0 ? hjj / den : 1.0, sg = den > 0 ? hj1 / den : 0.0;
+    p.cs[o1 + j] = c;
+    p.sn[o1 + j] = sg;
+    col[j] = den;
+    col[j + 1] = 0.0;
+    const double gj = p.g[o1 + j];
+    p.g[o1 + j + 1] = -sg * gj;
+    p.g[o1 + j] = c * gj;
+    st->iters += 1;
+    st->kdim = j + 1;
+    st->res = fabs(p.g[o1 + j + 1]) / st->bnorm;
+    st->converged = st->res <= st->tol;
+    st->breakdown = hn <= 1e-300;
+    const bool stop = st->converged || st->breakdown || st->iters >= st->max_iter || j + 1 >= m;
+    if (stop) {
+      st->active = 0;
+    } else {
+      st->inv_hn = 1.0 / hn;
+      st->j = j + 1;
+      atomicAdd(p.nact, 1);
+    }
+  }
+  __syncthreads();
+  double* H = p.H + (size_t)s * (m + 1) * m;
+  for (int i = tid; i <= j + 1; i += blockDim.x) H[(size_t)i * m + j] = col[i];
+}
+
+__global__ void bk_finalize(GPtr p) {
+  const int s = blockIdx.x;
+  GDev* st = p.st + s;
+  if (!st->active) return;
+  __shared__ double col[kGmMaxM + 1], scs[kGmMaxM], ssn[kGmMaxM];
+  const int j = st->j, m = p.m;
+  const size_t o1 = (size_t)s * (m + 1);
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+    const double* a1 = p.h1p + (o1 + i) * p.CH;
+    const double* a2 = p.h2p + (o1 + i) * p.CH;
+    double c1 = 0.0, c2 = 0.0;
+    for (int c = 0; c < p.CH; ++c) {
+      c1 += a1[c];
+      c2 += a2[c];
+    }
+    col[i] = c1 + c2;
+  }
+  __shared__ double s_hn;
+  if (threadIdx.x == 0) {
+    double nrm = 0.0;
+    for (int c = 0; c < p.CH; ++c) nrm += p.nrmp[(size_t)s * p.CH + c];
+    s_hn = sqrt(fmax(0.0, nrm));
+  }
+  __syncthreads();
+  givens_step(p, s, j, s_hn, col, scs, ssn);
+}
+
+// Arnoldi source of the next pair pass, written by the kernels that produce V_j:
+// FP32 records (PairArgs::x32, ncp floats per sphere, zero padding) or FP64
+// component-major, both scaled by the column multipliers minv.
+struct SrcOut {
+  float* rec;
+  double* dbl;
+  int ncp;
+  Scales minv;
+};
+
+__device__ __forceinline__ void write_src(const SrcOut& o, int Ntot, int h, int q, int p, double v) {
+  if (o.rec != nullptr) {
+    float* r = o.rec + (size_t)p * o.ncp;
+    r[q] = float(v * o.minv.v[q]);
+    if (q == 0)
+      for (int k = h; k < o.ncp; ++k) r[k] = 0.f;
+  } else if (o.dbl != nullptr) {
+    o.dbl[(size_t)q * Ntot + p] = v * o.minv.v[q];
+  }
+}
+
+// V_{j_s} = w / h for the newly advanced j_s (and its Arnoldi source)
+__global__ void bk_scale(double* V, size_t n, const double* __restrict__ w, int Ntot, const int* __restrict__ sys,
+                         const GDev* __restrict__ st, SrcOut src) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= Ntot) return;
+  const GDev& g = st[sys[p]];
+  if (!g.active) return;
+  const size_t t = (size_t)blockIdx.y * Ntot + p;
+  const double v = w[t] * g.inv_hn;
+  V[(size_t)g.j * n + t] = v;
+  write_src(src, Ntot, gridDim.y, blockIdx.y, p, v);
+}
+
+// ---------------------------------------------------------------------------------
+// Fused Arnoldi step of a single system: both Gram-Schmidt rounds, the norm, the
+// Givens update and V_{j+1} (with its pair-pass source) in one kernel of kFusedBlocks
+// blocks, each owning a contiguous slice of the vectors, separated by three grid-wide
+// barriers.  Partial sums are combined in block order by every block (identical
+// results everywhere), so the result does not depend on timing.  The blocks must be
+// co-resident: 64 blocks of 256 threads on a 152-SM GPU that runs nothing else in the
+// stream meanwhile.  Each barrier wait is bounded; a block that gives up records an
+// error (bar[2]) and returns, and the host reports GBI_ERR_TIMEOUT.
+// ---------------------------------------------------------------------------------
+
+constexpr long long kBarrierLimit = 1ll << 22;   // polling rounds (with back-off) per barrier
+
+__device__ bool grid_barrier(unsigned int* bar, int* s_ok) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned int g = atomicAdd(&bar[1], 0u);   // generation before arriving
+    __threadfence();
+    int ok = 1;
+    if (atomicAdd(&bar[0], 1u) == gridDim.x - 1) {
+      atomicExch(&bar[0], 0u);
+      __threadfence();
+      atomicAdd(&bar[1], 1u);
+    } else {
+      long long it = 0;
+      while (atomicAdd(&bar[1], 0u) == g) {
+        if (++it > kBarrierLimit) {
+          atomicExch(&bar[2], 1u);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    *s_ok = ok;
+  }
+  __syncthreads();
+  return *s_ok != 0;
+}
+
+// sum over the block in a fixed order; the leading barrier makes back-to-back calls safe
+__device__ __forceinline__ double block_sum_ordered(double v, double* sh) {
+  __syncthreads();
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  return sh[0];
+}
+
+// part[i G + b] = V_i . w over [t0, t1) for i <= j: warp k of the block takes
+// i = k, k + nwarps, ...; lanes stride the slice and a shuffle tree sums them (fixed order)
+__device__ __forceinline__ void slice_dots(const double* __restrict__ V, size_t n, const double* __restrict__ w,
+                                           int j, size_t t0, size_t t1, double* part, int G, int b) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = warp; i <= j; i += nw) {
+    const double* v = V + (size_t)i * n;
+    double acc = 0.0;
+    for (size_t t = t0 + lane; t < t1; t += 32) acc += v[t] * w[t];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) part[(size_t)i * G + b] = acc;
+  }
+}
+
+__global__ void __launch_bounds__(256) bk_step_fused(double* V, size_t n, double* w, int Ntot, int h, GPtr p,
+                                                     SrcOut so) {
+  __shared__ double sh[256];
+  __shared__ double c1[kGmMaxM + 1], c2[kGmMaxM + 1], scs[kGmMaxM], ssn[kGmMaxM];
+  __shared__ double s_hn;
+  __shared__ int s_ok;
+  const GDev* st = p.st;
+  if (!st->active) return;   // the same decision in every block: nothing writes the state yet
+  const int j = st->j, m = p.m;
+  const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
+  const size_t L = (n + G - 1) / G;
+  const size_t t0 = (size_t)b * L, t1 = min(n, t0 + L);
+  double* part1 = p.fp;
+  double* part2 = p.fp + (size_t)(m + 1) * G;
+  double* partn = p.fp + 2 * (size_t)(m + 1) * G;
+  // (A) partial V_i . w: warp w of the block takes i = w, w + 8, ... (no block barrier)
+  slice_dots(V, n, w, j, t0, t1, part1, G, b);
+  if (!grid_barrier(p.bar, &s_ok)) return;
+  // (B) w1 = w - sum c1_i V_i on the slice, then partial V_i . w1
+  for (int i = tid; i <= j; i += blockDim.x) {
+    double c = 0.0;
+    for (int q = 0; q < G; ++q) c += part1[(size_t)i * G + q];
+    c1[i] = c;
+  }
+  __syncthreads();
+  for (size_t t = t0 + tid; t < t1; t += blockDim.x) {
+    double a = w[t];
+    for (int i = 0; i <= j; ++i) a -= c1[i] * V[(size_t)i * n + t];
+    w[t] = a;
+  }
+  __syncthreads();
+  slice_dots(V, n, w, j, t0, t1, part2, G, b);
+  if (!grid_barrier(p.bar, &s_ok)) return;
+  // (C) w2 = w1 - sum c2_i V_i, partial |w2|^2
+  for (int i = tid; i <= j; i += blockDim.x) {
+    double c = 0.0;
+    for (int q = 0; q < G; ++q) c += part2[(size_t)i * G + q];
+    c2[i] = c;
+  }
+  __syncthreads();
+  double nacc = 0.0;
+  for (size_t t = t0 + tid; t < t1; t += blockDim.x) {
+    double a = w[t];
+    for (int i = 0; i <= j; ++i) a -= c2[i] * V[(size_t)i * n + t];
+    w[t] = a;
+    nacc += a * a;
+  }
+  nacc = block_sum_ordered(nacc, sh);
+  if (tid == 0) partn[b] = nacc;
+  if (!grid_barrier(p.bar, &s_ok)) return;
+  // (D) h_{j+1,j} = |w2|, V_{j+1} = w2 / h and its source; block 0 updates the rotations
+  if (tid == 0) {
+    double nrm = 0.0;
+    for (int q = 0; q < G; ++q) nrm += partn[q];
+    s_hn = sqrt(fmax(0.0, nrm));
+  }
+  __syncthreads();
+  const double hn = s_hn;
+  const double inv = hn > 1e-300 ? 1.0 / hn : 0.0;
+  for (size_t t = t0 + tid; t < t1; t += blockDim.x) {
+    const double v = w[t] * inv;
+    V[(size_t)(j + 1) * n + t] = v;
+    const int q = int(t / (size_t)Ntot);
+    write_src(so, Ntot, h, q, int(t - (size_t)q * Ntot), v);
+  }
+  if (b == 0) {
+    for (int i = tid; i <= j; i += blockDim.x) c1[i] += c2[i];
+    __syncthreads();
+    givens_step(p, 0, j, hn, c1, scs, ssn);
+  }
+}
+
+// End of one device-looped Arnoldi step: keep looping while any system is still active
+// (the WHILE node of the cycle graph reads the value set here), and reset the count.
+__global__ void bk_continue(GPtr p, cudaGraphConditionalHandle h) {
+  const int v = *p.nact;
+  *p.nact = 0;
+  cudaGraphSetConditional(h, v > 0 ? 1u : 0u);
+}
+
+// start of a GMRES cycle for every enabled system: beta = |V_0|, g = (beta, 0, ...)
+__global__ void bk_init_cycle(GPtr p, int first) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s == 0) *p.nact = 0;
+  if (s >= p.S) return;
+  GDev* st = p.st + s;
+  const int m = p.m;
+  if (first) st->iters = 0;
+  st->j = 0;
+  st->kdim = 0;
+  st->breakdown = 0;
+  if (!st->enabled || (!first && st->converged)) {
+    st->active = 0;
+    return;
+  }
+  const double beta = sqrt(fmax(0.0, p.nrm[s]));
+  if (first) st->bnorm = beta;
+  st->beta = beta;
+  double* g = p.g + (size_t)s * (m + 1);
+  for (int i = 0; i <= m; ++i) g[i] = 0.0;
+  g[0] = beta;
+  st->res = st->bnorm > 0 ? beta / st->bnorm : 0.0;
+  st->converged = st->res <= st->tol;
+  st->active = (!st->converged && st->iters < st->max_iter && beta > 0) ? 1 : 0;
+  st->inv_hn = beta > 0 ? 1.0 / beta : 0.0;
+}
+
+__global__ void bk_scale0(double* V0, int Ntot, const int* __restrict__ sys, const GDev* __restrict__ st,
+                          SrcOut src) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= Ntot) return;
+  const GDev& g = st[sys[p]];
+  if (!g.active) return;
+  const size_t t = (size_t)blockIdx.y * Ntot + p;
+  const double v = V0[t] * g.inv_hn;
+  V0[t] = v;
+  write_src(src, Ntot, gridDim.y, blockIdx.y, p, v);
+}
+
+// y_s = H_s^-1 g_s on the kdim leading rows (column-oriented back substitution)
+__global__ void bk_solve_y(GPtr p) {
+  const int s = blockIdx.x;
+  const GDev* st = p.st + s;
+  const int k = st->kdim, m = p.m;
+  if (k == 0) return;
+  const double* H = p.H + (size_t)s * (m + 1) * m;
+  const size_t o1 = (size_t)s * (m + 1);
+  __shared__ double rhs[kGmMaxM], yv[kGmMaxM];
+  for (int i = threadIdx.x; i < k; i += blockDim.x) rhs[i] = p.g[o1 + i];
+  __syncthreads();
+  for (int i = k - 1; i >= 0; --i) {
+    if (threadIdx.x == 0) yv[i] = rhs[i] / H[(size_t)i * m + i];
+    __syncthreads();
+    for (int r = threadIdx.x; r < i; r += blockDim.x) rhs[r] -= H[(size_t)r * m + i] * yv[i];
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < k; i += blockDim.x) p.y[o1 + i] = yv[i];
+}
+
+// u += minv * sum_{i < kdim_s} y_s[i] V_i  (systems whose cycle ran)
+__global__ void bk_update(const double* __restrict__ V, size_t n, int Ntot, const int* __restrict__ sys, GPtr p,
+                          Scales minv, double* u) {
+  const int pp = blockIdx.x * blockDim.x + threadIdx.x;
+  if (pp >= Ntot) return;
+  const int s = sys[pp];
+  const int k = p.st[s].kdim;
+  if (k == 0) return;
+  const size_t t = (size_t)blockIdx.y * Ntot + pp;
+  const double* y = p.y + (size_t)s * (p.m + 1);
+  double acc = 0.0;
+  for (int i = 0; i < k; ++i) acc += y[i] * V[(size_t)i * n + t];
+  u[t] += minv.v[blockIdx.y] * acc;
+}
+
+// refinement bookkeeping: mode 0 stores |b_s| (from nrm), mode 1 sets rel and enabled
+__global__ void bk_refine(GPtr p, int mode, double rtol) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= p.S) return;
+  GDev* st = p.st + s;
+  const double v = sqrt(fmax(0.0, p.nrm[s]));
+  if (mode == 0) {
+    st->nb = v;
+    st->enabled = v > 0 ? 1 : 0;
+    st->rel = v > 0 ? 1.0 : 0.0;
+  } else if (st->enabled) {
+    st->rel = st->nb > 0 ? v / st->nb : 0.0;
+    st->enabled = st->rel > rtol ? 1 : 0;
+  }
+}
+
+// x += d on enabled systems
+__global__ void bk_axpy_enabled(const double* __restrict__ d, int Ntot, const int* __restrict__ sys,
+                                const GDev* __restrict__ st, double* x) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= Ntot) return;
+  if (!st[sys[p]].enabled) return;
+  const size_t t = (size_t)blockIdx.y * Ntot + p;
+  x[t] += d[t];
+}
+
+// Restarted right-preconditioned GMRES(m) on every active system of the batch for
+// G^HH u = rhs (internal coordinates).  u holds the initial guess (zero or warm).
+// Arnoldi (classical Gram-Schmidt twice), Givens rotations, the stopping tests and
+// the triangular solves run on the device in FP64; the host launches the iterations
+// in chunks (replayed from a CUDA graph when the stream allows capture) and reads the
+// systems' small states once per chunk.
+gbi_status gmres_batch(gbi_ctx* ctx, const Setup& s, const Batch& B, int precision, const double* rhs, double* u,
+                       bool u_is_zero, double tol, int restart, int max_iter, gbi_info* info, int& iters,
+                       double& relres, GDev* hst, int* before, unsigned int* bar, double outer_rtol = 0.0);
+
+// Where the kernels producing V_j put the next pair pass's source (see SrcOut).
+SrcOut src_out(const Setup& s, int precision, void* xsrc) {
+  SrcOut o;
+  o.rec = precision == 1 ? static_cast<float*>(xsrc) : nullptr;
+  o.dbl = precision == 1 ? nullptr : static_cast<double*>(xsrc);
+  o.ncp = (s.h + 3) & ~3;
+  o.minv = s.minv;
+  return o;
+}
+
+// kChunk Arnoldi iterations of every active system: pair pass on the source of V_j
+// (written by the previous bk_scale / bk_scale0), two rounds of classical Gram-Schmidt,
+// norm, Givens update and V_{j+1} with its source -- eight kernels per iteration.  With
+// fused set and a single system the seven kernels after the pair pass are replaced by
+// bk_step_fused; that is faster for direct launches, while inside the cycle graph the
+// separate kernels (graph launch overhead about a microsecond each) measured faster than
+// the fused kernel's three grid barriers.
+gbi_status launch_chunk(gbi_ctx* ctx, const Setup& s, const Batch& B, int precision, const GPtr& gp, int m,
+                        double* Vb, double* w, void* xsrc, int kChunk, bool fused) {
+  const int S = B.S, Ntot = B.Ntot, h = s.h;
+  const size_t n = (size_t)Ntot * h;
+  const dim3 g2((Ntot + 255) / 256, h);
+  PairArgs pa = pair_args(s, precision == 1 ? nullptr : static_cast<const double*>(xsrc), w, 1.0, 0.0, 1, s.ones,
+                          6);
+  if (precision == 1) pa.x32 = static_cast<const float*>(xsrc);
+  pa.sys_of = B.sys;
+  pa.sys_off = B.off;
+  pa.sys_flag = &gp.st[0].active;
+  pa.sys_flag_stride = int(sizeof(GDev) / sizeof(int));
+  const SrcOut so = src_out(s, precision, xsrc);
+  const dim3 gd(S, m + 1, gp.CH);
+  for (int c = 0; c < kChunk; ++c) {
+    GBI_CHECK(run_pairs(ctx, s.trunc, SET_H, SET_H, precision, pa));
+    if (fused && S == 1) {
+      // a single system launched step by step: the whole orthogonalisation in one kernel
+      bk_step_fused<<<kFusedBlocks, 256, 0, ctx->stream>>>(Vb, n, w, Ntot, h, gp, so);
+      ++ctx->launches;
+      continue;
+    }
+    bk_dots<<<gd, 256, 0, ctx->stream>>>(Vb, n, w, Ntot, h, B.off, gp.st, m, gp.CH, gp.h1p);
+    bk_sub<<<g2, 256, 0, ctx->stream>>>(Vb, n, w, Ntot, B.sys, gp.st, m, gp.CH, gp.h1p);
+    bk_dots<<<gd, 256, 0, ctx->stream>>>(Vb, n, w, Ntot, h, B.off, gp.st, m, gp.CH, gp.h2p);
+    bk_sub<<<g2, 256, 0, ctx->stream>>>(Vb, n, w, Ntot, B.sys, gp.st, m, gp.CH, gp.h2p);
+    bk_norm_part<<<dim3(S, gp.CH), 256, 0, ctx->stream>>>(w, Ntot, h, B.off, gp.st, 0, gp.CH, gp.nrmp);
+    bk_finalize<<<S, 128, 0, ctx->stream>>>(gp);
+    bk_scale<<<g2, 256, 0, ctx->stream>>>(Vb, n, w, Ntot, B.sys, gp.st, so);
+    ctx->launches += 7;
+  }
+  GBI_CHECK(cudaGetLastError());
+  return GBI_OK;
+}
+
+// Per-system GMRES set-up.  With outer_rtol > 0 (an inner solve of the refinement) the
+// tolerance relative to the current residual r is loosened to 0.1 outer_rtol |b| / |r|
+// when that is larger than tol: the solve only has to bring |r| a decade below the
+// target, so a refinement sweep that starts close to it needs few iterations.
+__global__ void bk_setup(GPtr p, double tol, int max_iter, double outer_rtol) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= p.S) return;
+  GDev* st = p.st + s;
+  if (s == 0) {
+    p.bar[0] = 0u;   // arrivals
+    p.bar[2] = 0u;   // error flag
+  }
+  st->tol = outer_rtol > 0 ? fmax(tol, 0.1 * outer_rtol / fmax(st->rel, 1e-300)) : tol;
+  st->max_iter = max_iter;
+  st->m = p.m;
+  st->active = 0;
+  st->converged = 0;
+  st->iters = 0;
+}
+
+gbi_status gmres_batch(gbi_ctx* ctx, const Setup& s, const Batch& B, int precision, const double* rhs, double* u,
+                       bool u_is_zero, double tol, int restart, int max_iter, gbi_info* info, int& iters,
+                       double& relres, GDev* hst, int* before, unsigned int* bar, double outer_rtol) {
+  constexpr int kChunk = 6;
+  const int S = B.S, Ntot = B.Ntot, h = s.h;
+  const size_t n = (size_t)Ntot * h;
+  const int m = std::max(1, std::min(restart, kMaxRestart));
+  GBI_TRY(ensure(ctx, ctx->krylov, sizeof(double) * n * (m + 1)));
+  GBI_TRY(ensure(ctx, ctx->w, sizeof(double) * n));
+  GBI_TRY(ensure(ctx, ctx->gstate, sizeof(double) * gstate_doubles(m, S, arnoldi_chunks(S, h))));
+  // gathered Arnoldi source: FP64 component-major, or FP32 records of round4(h) floats
+  GBI_TRY(ensure(ctx, ctx->x32, std::max(sizeof(double) * n, sizeof(float) * (size_t)Ntot * ((h + 3) & ~3))));
+  double* Vb = P<double>(ctx->krylov);
+  double* w = P<double>(ctx->w);
+  void* xsrc = ctx->x32.p;
+  const GPtr gp = gptrs(ctx->gstate.p, m, S, arnoldi_chunks(S, h));
+  const dim3 g2((Ntot + 255) / 256, h);
+  const int sblk = (S + 127) / 128;
+  iters = 0;
+  relres = 0.0;
+  bk_setup<<<sblk, 128, 0, ctx->stream>>>(gp, tol, std::max(0, max_iter), outer_rtol);
+  ++ctx->launches;
+  // cycle graph: a WHILE node whose body is one Arnoldi step of every active system
+  // followed by bk_continue; the loop runs on the device until no system is active, so a
+  // GMRES cycle costs one graph launch and one read of the per-system states.  Built
+  // once per buffer set and replayed afterwards.
+  const bool graphs = ctx->allow_graphs && ctx->stream != nullptr && !ctx->prof;
+  if (graphs) {
+    const void* key[8] = {Vb, w, xsrc, ctx->gstate.p, B.sys, B.off, s.pos.hi, s.pos.p64};
+    const long long ikey[6] = {(long long)n, S, m, precision, s.trunc, Ntot};
+    bool same = ctx->chunk_exec != nullptr;
+    for (int i = 0; i < 8 && same; ++i) same = ctx->chunk_key[i] == key[i];
+    for (int i = 0; i < 6 && same; ++i) same = ctx->chunk_ikey[i] == ikey[i];
+    if (!same) {
+      if (ctx->chunk_exec) cudaGraphExecDestroy(ctx->chunk_exec);
+      ctx->chunk_exec = nullptr;
+      cudaGraph_t graph = nullptr;
+      GBI_CHECK(cudaGraphCreate(&graph, 0));
+      cudaGraphConditionalHandle handle;
+      cudaError_t e = cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault);
+      cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+      cp.conditional.handle = handle;
+      cp.conditional.type = cudaGraphCondTypeWhile;
+      cp.conditional.size = 1;
+      cudaGraphNode_t node = nullptr;
+      if (e == cudaSuccess) e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp);
+      const long long saved = ctx->launches;
+      gbi_status st = GBI_OK;
+      if (e == cudaSuccess) {
+        e = cudaStreamBeginCaptureToGraph(ctx->stream, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+          st = launch_chunk(ctx, s, B, precision, gp, m, Vb, w, xsrc, 1, false);
+          bk_continue<<<1, 1, 0, ctx->stream>>>(gp, handle);
+          ++ctx->launches;
+          cudaGraph_t body = nullptr;
+          const cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &body);
+          if (e == cudaSuccess) e = e2;
+        }
+      }
+      ctx->chunk_nodes = int(ctx->launches - saved);   // kernels per loop iteration
+      ctx->launches = saved;
+      if (st == GBI_OK && e == cudaSuccess) e = cudaGraphInstantiate(&ctx->chunk_exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (st != GBI_OK) return st;
+      GBI_CHECK(e);
+      for (int i = 0; i < 8; ++i) ctx->chunk_key[i] = key[i];
+      for (int i = 0; i < 6; ++i) ctx->chunk_ikey[i] = ikey[i];
+    }
+  }
+  bool first = true;
+  for (int q = 0; q < S; ++q) before[q] = 0;
+  while (true) {
+    // V_0 = rhs - A u on the enabled systems, beta_s = |V_0,s|
+    GBI_CHECK(cudaMemcpyAsync(Vb, rhs, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+    if (!(first && u_is_zero)) {
+      PairArgs pr = pair_args(s, u, Vb, -1.0, 1.0, 1, s.ones, 6);
+      pr.sys_of = B.sys;
+      pr.sys_off = B.off;
+      pr.sys_flag = &gp.st[0].enabled;
+      pr.sys_flag_stride = int(sizeof(GDev) / sizeof(int));
+      GBI_CHECK(run_pairs(ctx, s.trunc, SET_H, SET_H, precision, pr));
+      if (info) {
+        (precision == 1 ? info->matvecs_f32 : info->matvecs_f64) += 1;
+        for (int q = 0; q < S; ++q)
+          if (hst[q].enabled) info->pair_interactions += (long long)(B.h_off[q + 1] - B.h_off[q]) * (B.h_off[q + 1] - B.h_off[q] - 1);
+      }
+    }
+    bk_norm_part<<<dim3(S, gp.CH), 256, 0, ctx->stream>>>(Vb, Ntot, h, B.off, gp.st, 1, gp.CH, gp.nrmp);
+    bk_norm_sum<<<(S + 127) / 128, 128, 0, ctx->stream>>>(gp.nrmp, gp.st, S, 1, gp.CH, gp.nrm);
+    bk_init_cycle<<<sblk, 128, 0, ctx->stream>>>(gp, first ? 1 : 0);
+    bk_scale0<<<g2, 256, 0, ctx->stream>>>(Vb, Ntot, B.sys, gp.st, src_out(s, precision, xsrc));
+    ctx->launches += 4;
+    GBI_CHECK(cudaGetLastError());
+    if (first)
+      for (int q = 0; q < S; ++q) before[q] = 0;      // bk_init_cycle restarts the counters
+    else
+      for (int q = 0; q < S; ++q) before[q] = hst[q].iters;
+    first = false;
+    auto account = [&](int nsteps) {
+      // states after the launched steps: pair work of the systems that took them
+      int live = 0;
+      for (int q = 0; q < S; ++q) {
+        const int d = hst[q].iters - before[q];
+        before[q] = hst[q].iters;
+        live = std::max(live, d);
+        if (info) info->pair_interactions += (long long)d * (B.h_off[q + 1] - B.h_off[q]) * (B.h_off[q + 1] - B.h_off[q] - 1);
+      }
+      if (info) (precision == 1 ? info->matvecs_f32 : info->matvecs_f64) += live;
+      ctx->stat_dead[precision * 9 + SET_H * 3 + SET_H] += std::max(0, nsteps - live);
+      return live;
+    };
+    auto read_states = [&]() -> gbi_status {
+      GBI_CHECK(cudaMemcpyAsync(hst, gp.st, sizeof(GDev) * S, cudaMemcpyDeviceToHost, ctx->stream));
+      GBI_CHECK(cudaMemcpyAsync(bar, gp.bar, sizeof(unsigned int) * 3, cudaMemcpyDeviceToHost, ctx->stream));
+      GBI_CHECK(cudaStreamSynchronize(ctx->stream));
+      if (bar[2] != 0u) {
+        ctx->err = "fused Arnoldi step: a grid barrier wait gave up";
+        return GBI_ERR_TIMEOUT;
+      }
+      return GBI_OK;
+    };
+    if (graphs) {
+      // the whole cycle's Arnoldi steps in one launch; the loop ran max(1, most steps) times
+      GBI_CHECK(cudaGraphLaunch(ctx->chunk_exec, ctx->stream));
+      GBI_TRY(read_states());
+      int most = 0;
+      for (int q = 0; q < S; ++q) most = std::max(most, hst[q].iters - before[q]);
+      const int steps = std::max(1, most);
+      ctx->launches += (long long)steps * ctx->chunk_nodes;
+      account(steps);
+    } else {
+      // host-driven: chunks of kChunk steps with a state read after each
+      GBI_TRY(read_states());
+      bool any = false;
+      for (int q = 0; q < S; ++q) any = any || hst[q].active;
+      while (any) {
+        GBI_TRY(launch_chunk(ctx, s, B, precision, gp, m, Vb, w, xsrc, kChunk, true));
+        GBI_TRY(read_states());
+        account(kChunk);
+        any = false;
+        for (int q = 0; q < S; ++q) any = any || hst[q].active;
+      }
+    }
+    bk_solve_y<<<S, 128, 0, ctx->stream>>>(gp);
+    bk_update<<<g2, 256, 0, ctx->stream>>>(Vb, n, Ntot, B.sys, gp, s.minv, u);
+    ctx->launches += 2;
+    GBI_CHECK(cudaGetLastError());
+    bool restart_any = false;
+    for (int q = 0; q < S; ++q) {
+      const GDev& g = hst[q];
+      iters = std::max(iters, g.iters);
+      if (g.enabled && g.kdim > 0 && !g.converged && !g.breakdown && g.iters < g.max_iter) restart_any = true;
+    }
+    if (!restart_any) break;
+  }
+  relres = 0.0;
+  for (int q = 0; q < S; ++q)
+    if (hst[q].enabled) relres = std::max(relres, hst[q].res);
+  return GBI_OK;
+}
+
+// The full solve for a batch of independent suspensions (S = 1: one suspension).
+// Inputs and outputs are concatenated over the systems ([Ntot][3], [Ntot][h]).
+gbi_status solve_core(gbi_ctx* ctx, const gbi_params* prm, const Batch& B, const double* R, const double* Va,
+                      const double* Oa, const double* VH, const double* Fe, const double* Te, double* V,
+                      double* Omega, double* QH, int warm_start, gbi_info* inf) {
+  const int N = B.Ntot, S = B.S;
+  Setup s;
+  GBI_TRY(setup_call(ctx, s, N, prm->trunc, prm->a, prm->eta, R));
+  long long pairs_all = 0;
+  for (int q = 0; q < S; ++q) {
+    const long long ns = B.h_off[q + 1] - B.h_off[q];
+    pairs_all += ns * (ns - 1);
+  }
+  s.pairs_per_pass = pairs_all;
+  const int D = s.D, h = s.h;
+  const size_t nh = (size_t)N * h;
+  const dim3 g2((N + 255) / 256, h);
+  const int sblk = (S + 127) / 128;
+  // arithmetic of the refinement residual (FP64, or double-float for precision 2 and 3)
+  // and of the right-hand-side and output passes (the same, or FP32 for precision 3)
+  const int hp = prm->precision >= 2 ? 2 : 0;
+  const int io = prm->precision == 3 ? 1 : hp;
+  const int restart = std::max(1, std::min(prm->restart > 0 ? prm->restart : 40, kMaxRestart));
+  GBI_TRY(ensure(ctx, ctx->xQ, sizeof(double) * (size_t)N * D));
+  GBI_TRY(ensure(ctx, ctx->b, sizeof(double) * nh));
+  GBI_TRY(ensure(ctx, ctx->r, sizeof(double) * nh));
+  GBI_TRY(ensure(ctx, ctx->delta, sizeof(double) * nh));
+  GBI_TRY(ensure(ctx, ctx->xVL, sizeof(double) * 6 * N));
+  GBI_TRY(ensure(ctx, ctx->minr2, sizeof(unsigned int)));
+  GBI_TRY(ensure(ctx, ctx->gstate, sizeof(double) * gstate_doubles(restart, S, arnoldi_chunks(S, h))));
+  double* xF = P<double>(ctx->xQ);              // rows 0..5 of the full vector
+  double* xQH = P<double>(ctx->xQ) + (size_t)6 * N;
+  double* b = P<double>(ctx->b);
+  double* r = P<double>(ctx->r);
+  double* dl = P<double>(ctx->delta);
+  const GPtr gp = gptrs(ctx->gstate.p, restart, S, arnoldi_chunks(S, h));
+  const double c2a = s.scale.v[3];
+  Scales hscale;
+  for (int i = 0; i < 54; ++i) hscale.v[i] = (i < h) ? s.scale.v[6 + i] : 1.0;
+  auto batched = [&](PairArgs p, const int* flag) {
+    p.sys_of = B.sys;
+    p.sys_off = B.off;
+    p.sys_flag = flag;
+    p.sys_flag_stride = int(sizeof(GDev) / sizeof(int));
+    return p;
+  };
+  // host copies of the per-system states, the barrier words and per-system counters
+  const size_t hs_states = (sizeof(GDev) * (size_t)S + 15) & ~size_t(15);
+  GBI_TRY(host_scratch(ctx, hs_states + 16 + sizeof(int) * (size_t)S));
+  GDev* hst = reinterpret_cast<GDev*>(ctx->hs);
+  unsigned int* hbar = reinterpret_cast<unsigned int*>(ctx->hs + hs_states);
+  int* hbefore = reinterpret_cast<int*>(ctx->hs + hs_states + 16);
+
+  // inputs -> internal coordinates
+  k_pack_lower<<<grid1(N), 256, 0, ctx->stream>>>(N, s.a, c2a, Fe, Te, xF);
+  // b = -8 pi eta V^H
+  k_pack_higher<<<grid1(nh), 256, 0, ctx->stream>>>(N, h, VH, hscale, -8.0 * kPi * s.eta, b);
+  ctx->launches += 2;
+  GBI_CHECK(cudaGetLastError());
+  // b -= G^HL F^L, with the overlap scan
+  const unsigned int init_bits = 0x7f7fffffu;
+  GBI_CHECK(cudaMemcpyAsync(ctx->minr2.p, &init_bits, sizeof(unsigned int), cudaMemcpyHostToDevice, ctx->stream));
+  {
+    PairArgs p = batched(pair_args(s, xF, b, -1.0, 1.0, 0, s.ones, 0), nullptr);
+    p.min_r2_bits = P<unsigned int>(ctx->minr2);
+    GBI_CHECK(run_pairs(ctx, s.trunc, SET_H, SET_L, io, p));
+    (io == 1 ? inf->matvecs_f32 : inf->matvecs_f64) += 1;
+    inf->pair_interactions += pairs_all;
+  }
+  if (prm->min_sep > 0) {
+    unsigned int bits = 0;
+    GBI_CHECK(cudaMemcpyAsync(&bits, ctx->minr2.p, sizeof(unsigned int), cudaMemcpyDeviceToHost, ctx->stream));
+    GBI_CHECK(cudaStreamSynchronize(ctx->stream));
+    float mr2;
+    std::memcpy(&mr2, &bits, sizeof(float));
+    inf->min_separation = pairs_all > 0 ? std::sqrt(double(mr2)) / s.a : 0.0;
+    if (pairs_all > 0 && inf->min_separation < prm->min_sep) return GBI_ERR_OVERLAP;
+  }
+
+  // initial guess
+  bool zero = true;
+  if (warm_start) {
+    k_pack_higher<<<grid1(nh), 256, 0, ctx->stream>>>(N, h, QH, hscale, 1.0, xQH);
+    ++ctx->launches;
+    zero = false;
+  } else {
+    GBI_CHECK(cudaMemsetAsync(xQH, 0, sizeof(double) * nh, ctx->stream));
+  }
+  const int max_iter = prm->max_iter > 0 ? prm->max_iter : 1000;
+  const double rtol = prm->rtol > 0 ? prm->rtol : 1e-10;
+  // |b_s| per system
+  bk_norm_part<<<dim3(S, gp.CH), 256, 0, ctx->stream>>>(b, N, h, B.off, gp.st, 2, gp.CH, gp.nrmp);
+  bk_norm_sum<<<(S + 127) / 128, 128, 0, ctx->stream>>>(gp.nrmp, gp.st, S, 2, gp.CH, gp.nrm);
+  bk_refine<<<sblk, 128, 0, ctx->stream>>>(gp, 0, rtol);
+  ctx->launches += 3;
+  auto read_state = [&]() -> gbi_status {
+    GBI_CHECK(cudaMemcpyAsync(hst, gp.st, sizeof(GDev) * S, cudaMemcpyDeviceToHost, ctx->stream));
+    GBI_CHECK(cudaStreamSynchronize(ctx->stream));
+    return GBI_OK;
+  };
+  auto pairs_enabled = [&]() {
+    long long c = 0;
+    for (int q = 0; q < S; ++q)
+      if (hst[q].enabled) {
+        const long long ns = B.h_off[q + 1] - B.h_off[q];
+        c += ns * (ns - 1);
+      }
+    return c;
+  };
+  GBI_TRY(read_state());
+  bool converged = false;
+  if (prm->precision == 0) {
+    int it = 0;
+    double rr = 0.0;
+    GBI_TRY(gmres_batch(ctx, s, B, 0, b, xQH, zero, rtol, restart, max_iter, inf, it, rr, hst, hbefore, hbar));
+    inf->iters += it;
+    // true FP64 residual per system
+    GBI_CHECK(cudaMemcpyAsync(r, b, sizeof(double) * nh, cudaMemcpyDeviceToDevice, ctx->stream));
+    PairArgs p = batched(pair_args(s, xQH, r, -1.0, 1.0, 1, s.ones, 6), &gp.st[0].enabled);
+    GBI_CHECK(run_pairs(ctx, s.trunc, SET_H, SET_H, 0, p));
+    inf->matvecs_f64 += 1;
+    inf->pair_interactions += pairs_enabled();
+    bk_norm_part<<<dim3(S, gp.CH), 256, 0, ctx->stream>>>(r, N, h, B.off, gp.st, 1, gp.CH, gp.nrmp);
+    bk_norm_sum<<<(S + 127) / 128, 128, 0, ctx->stream>>>(gp.nrmp, gp.st, S, 1, gp.CH, gp.nrm);
+    bk_refine<<<sblk, 128, 0, ctx->stream>>>(gp, 1, rtol);
+    ctx->launches += 3;
+    GBI_TRY(read_state());
+  } else {
+    // mixed precision: r = b - A_hp x; A_32 d = r (FP32 pair sums, FP64 Arnoldi); x += d
+    const double inner = prm->inner_rtol > 0 ? prm->inner_rtol : 1e-5;
+    const int max_refine = prm->max_refine > 0 ? prm->max_refine : 8;
+    for (int sweep = 0;; ++sweep) {
+      GBI_CHECK(cudaMemcpyAsync(r, b, sizeof(double) * nh, cudaMemcpyDeviceToDevice, ctx->stream));
+      if (!(zero && sweep == 0)) {
+        PairArgs p = batched(pair_args(s, xQH, r, -1.0, 1.0, 1, s.ones, 6), &gp.st[0].enabled);
+        GBI_CHECK(run_pairs(ctx, s.trunc, SET_H, SET_H, hp, p));
+        inf->matvecs_f64 += 1;
+        inf->pair_interactions += pairs_enabled();
+        bk_norm_part<<<dim3(S, gp.CH), 256, 0, ctx->stream>>>(r, N, h, B.off, gp.st, 1, gp.CH, gp.nrmp);
+        bk_norm_sum<<<(S + 127) / 128, 128, 0, ctx->stream>>>(gp.nrmp, gp.st, S, 1, gp.CH, gp.nrm);
+        bk_refine<<<sblk, 128, 0, ctx->stream>>>(gp, 1, rtol);
+        ctx->launches += 3;
+      }
+      if (sweep > 0) inf->refinements += 1;
+      if (sweep >= max_refine || inf->iters >= max_iter) {
+        GBI_TRY(read_state());
+        break;
+      }
+      int it = 0;
+      double rr = 0.0;
+      GBI_CHECK(cudaMemsetAsync(dl, 0, sizeof(double) * nh, ctx->stream));
+      GBI_TRY(gmres_batch(ctx, s, B, 1, r, dl, true, inner, restart, max_iter - inf->iters, inf, it, rr, hst, hbefore, hbar,
+                          rtol));
+      inf->iters += it;
+      bool any = false;
+      for (int q = 0; q < S; ++q) any = any || hst[q].enabled;
+      if (!any) break;       // every system met the tolerance at this sweep's residual
+      bk_axpy_enabled<<<g2, 256, 0, ctx->stream>>>(dl, N, B.sys, gp.st, xQH);
+      ++ctx->launches;
+      GBI_CHECK(cudaGetLastError());
+    }
+  }
+  converged = true;
+  inf->rel_residual = 0.0;
+  for (int q = 0; q < S; ++q) {
+    inf->rel_residual = std::max(inf->rel_residual, hst[q].rel);
+    if (hst[q].rel > rtol) converged = false;
+  }
+  // outputs: 8 pi eta x^{V,L} = -(G^LL F^L + G^LH Q^H) incl. self
+  {
+    PairArgs p = batched(pair_args(s, P<double>(ctx->xQ), P<double>(ctx->xVL), -1.0 / (8.0 * kPi * s.eta), 0.0, 1,
+                                   s.ones, 0),
+                         nullptr);
+    GBI_CHECK(run_pairs(ctx, s.trunc, SET_L, SET_ALL, io, p));
+    (io == 1 ? inf->matvecs_f32 : inf->matvecs_f64) += 1;
+    inf->pair_interactions += pairs_all;
+  }
+  k_finalize_lower<<<grid1(N), 256, 0, ctx->stream>>>(N, s.a, c2a, P<double>(ctx->xVL), Va, Oa, V, Omega);
+  ++ctx->launches;
+  if (QH) {
+    k_unpack_higher<<<grid1(nh), 256, 0, ctx->stream>>>(N, h, xQH, hscale, QH);
+    ++ctx->launches;
+  }
+  GBI_CHECK(cudaGetLastError());
+  if (prm->min_sep <= 0) {
+    unsigned int bits = 0;
+    GBI_CHECK(cudaMemcpyAsync(&bits, ctx->minr2.p, sizeof(unsigned int), cudaMemcpyDeviceToHost, ctx->stream));
+    GBI_CHECK(cudaStreamSynchronize(ctx->stream));
+    float mr2;
+    std::memcpy(&mr2, &bits, sizeof(float));
+    inf->min_separation = pairs_all > 0 ? std::sqrt(double(mr2)) / s.a : 0.0;
+  } else {
+    GBI_CHECK(cudaStreamSynchronize(ctx->stream));
+  }
+  return converged ? GBI_OK : GBI_ERR_NOT_CONVERGED;
+}
+
+}  // namespace gbi

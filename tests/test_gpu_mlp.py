@@ -249,3 +249,27 @@ def test_trained_network_beats_superposition(ctx, gbi):
     dsus = nearfield.make_dataset(ctx, dev(s["R"]), dev(s["p"]), [0, 300], a, eta, vs, s0, sigma=dtr["sigma"])
     ev2 = nearfield.evaluate(ctx, dsus)
     assert ev2["with_network"]["V"] < ev2["superposition"]["V"], ev2
+
+
+def test_nearfield_edge_cases(ctx, gbi):
+    """Empty input, a single sphere, spheres farther apart than the cut-off, and a batch
+    whose systems have no pairs: no pairs, nothing added."""
+    from paper_1411_0278_gb300 import nearfield
+    ctx.mlp_set(nearfield.init_theta(2), 1.0)
+    R0 = torch.zeros((0, 3), dtype=torch.float64, device="cuda")
+    assert ctx.mlp_correct(R0, R0, 1.0, 0.05, R0, R0) == 0
+    tg, sr = ctx.pairs(R0, 1.0, 4.0)
+    assert tg.numel() == 0
+    for R in ([[0.0, 0.0, 0.0]], [[0.0, 0.0, 0.0], [4.0, 0.0, 0.0], [0.0, 9.0, 0.0]]):
+        Rd = dev(R)
+        p = dev(workloads.unit_vectors(len(R), np.random.default_rng(0)))
+        V = torch.ones((len(R), 3), dtype=torch.float64, device="cuda")
+        O = torch.ones_like(V)
+        assert ctx.mlp_correct(Rd, p, 1.0, 0.05, V, O) == 0
+        assert float((V - 1).abs().max()) == 0.0 and float((O - 1).abs().max()) == 0.0
+    # two systems of two spheres each, pairs only inside each system
+    R = dev([[0.0, 0, 0], [3.0, 0, 0], [0.5, 0, 0], [10.0, 0, 0]])
+    tg, sr = ctx.pairs(R, 1.0, 4.0, [0, 2, 4])
+    assert list(zip(tg.cpu().tolist(), sr.cpu().tolist())) == [(0, 1), (1, 0)]
+    with pytest.raises(gbi.GbiError):
+        ctx.pairs(R, 1.0, 4.0, [0, 2, 3])          # offsets must end at N
