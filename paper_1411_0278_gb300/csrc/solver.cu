@@ -99,13 +99,15 @@ __device__ __forceinline__ double block_sum_256(double v) {
 }
 
 // part[(s (m+1) + i) CH + c] = V_i . w over the component rows of chunk c of system s,
-// for i <= j_s (block (s, i, c); fixed-order block reduction)
+// for i <= j_s (block (s, i, c); fixed-order block reduction).  With with_norm set, slot
+// i = j_s + 1 receives w . w (the one-reduction step below).
 __global__ void bk_dots(const double* __restrict__ V, size_t n, const double* __restrict__ w, int Ntot, int h,
-                        const int* __restrict__ off, const GDev* __restrict__ st, int m, int CH, double* part) {
+                        const int* __restrict__ off, const GDev* __restrict__ st, int m, int CH, double* part,
+                        int with_norm) {
   const int s = blockIdx.x, i = blockIdx.y, c = blockIdx.z;
   const GDev& g = st[s];
-  if (!g.active || i > g.j) return;
-  const double* v = V + (size_t)i * n;
+  if (!g.active || i > g.j + with_norm) return;
+  const double* v = i > g.j ? w : V + (size_t)i * n;
   const int lo = off[s], hi = off[s + 1];
   const int q0 = c * h / CH, q1 = (c + 1) * h / CH;
   double acc = 0.0;
@@ -243,27 +245,39 @@ __device__ void givens_step(const GPtr& p, int s, int j, double hn, double* col,
   for (int i = tid; i <= j + 1; i += blockDim.x) H[(size_t)i * m + j] = col[i];
 }
 
-__global__ void bk_finalize(GPtr p) {
+// Column j of the Hessenberg matrix from the Gram-Schmidt partial sums and the new
+// norm, then the Givens step.  two_pass: coefficients of both rounds (h1p + h2p) and
+// the norm of the twice-orthogonalised vector (nrmp).  Otherwise one round: h1p holds
+// c_i = V_i . w for i <= j and |w|^2 in slot j + 1, and with orthonormal V_i
+// |w - sum c_i V_i|^2 = |w|^2 - sum c_i^2 (clamped at zero).
+__global__ void bk_finalize(GPtr p, int two_pass) {
   const int s = blockIdx.x;
   GDev* st = p.st + s;
   if (!st->active) return;
   __shared__ double col[kGmMaxM + 1], scs[kGmMaxM], ssn[kGmMaxM];
   const int j = st->j, m = p.m;
   const size_t o1 = (size_t)s * (m + 1);
-  for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+  const int top = two_pass ? j : j + 1;
+  for (int i = threadIdx.x; i <= top; i += blockDim.x) {
     const double* a1 = p.h1p + (o1 + i) * p.CH;
-    const double* a2 = p.h2p + (o1 + i) * p.CH;
     double c1 = 0.0, c2 = 0.0;
-    for (int c = 0; c < p.CH; ++c) {
-      c1 += a1[c];
-      c2 += a2[c];
+    for (int c = 0; c < p.CH; ++c) c1 += a1[c];
+    if (two_pass) {
+      const double* a2 = p.h2p + (o1 + i) * p.CH;
+      for (int c = 0; c < p.CH; ++c) c2 += a2[c];
     }
     col[i] = c1 + c2;
   }
   __shared__ double s_hn;
+  __syncthreads();
   if (threadIdx.x == 0) {
     double nrm = 0.0;
-    for (int c = 0; c < p.CH; ++c) nrm += p.nrmp[(size_t)s * p.CH + c];
+    if (two_pass) {
+      for (int c = 0; c < p.CH; ++c) nrm += p.nrmp[(size_t)s * p.CH + c];
+    } else {
+      nrm = col[j + 1];
+      for (int i = 0; i <= j; ++i) nrm -= col[i] * col[i];
+    }
     s_hn = sqrt(fmax(0.0, nrm));
   }
   __syncthreads();
@@ -300,6 +314,51 @@ __global__ void bk_scale(double* V, size_t n, const double* __restrict__ w, int 
   if (!g.active) return;
   const size_t t = (size_t)blockIdx.y * Ntot + p;
   const double v = w[t] * g.inv_hn;
+  V[(size_t)g.j * n + t] = v;
+  write_src(src, Ntot, gridDim.y, blockIdx.y, p, v);
+}
+
+// One-reduction step, after bk_finalize advanced j_s: V_{j_s} = (w - sum_{i < j_s} c_i V_i)
+// / h_{j_s, j_s - 1} with the coefficients summed from the h1p partials (once per block
+// into shared memory when the block's spheres all belong to one system), and its source.
+__global__ void bk_sub_scale(double* V, size_t n, const double* __restrict__ w, int Ntot,
+                             const int* __restrict__ sys, const GDev* __restrict__ st, int m, int CH,
+                             const double* __restrict__ part, SrcOut src) {
+  __shared__ double sc[kMaxRestart + 1];
+  const int p0 = blockIdx.x * blockDim.x;
+  const int pl = min(Ntot - 1, p0 + (int)blockDim.x - 1);
+  const int sb = sys[p0];
+  const bool uniform = sys[pl] == sb;
+  if (uniform) {
+    const GDev& g = st[sb];
+    if (!g.active) return;
+    for (int i = threadIdx.x; i < g.j; i += blockDim.x) {
+      const double* q = part + ((size_t)sb * (m + 1) + i) * CH;
+      double acc = 0.0;
+      for (int c = 0; c < CH; ++c) acc += q[c];
+      sc[i] = acc;
+    }
+    __syncthreads();
+  }
+  const int p = p0 + threadIdx.x;
+  if (p >= Ntot) return;
+  const int s = sys[p];
+  const GDev& g = st[s];
+  if (!g.active) return;
+  const size_t t = (size_t)blockIdx.y * Ntot + p;
+  double acc = w[t];
+  for (int i = 0; i < g.j; ++i) {
+    double c;
+    if (uniform) {
+      c = sc[i];
+    } else {
+      const double* q = part + ((size_t)s * (m + 1) + i) * CH;
+      c = 0.0;
+      for (int k = 0; k < CH; ++k) c += q[k];
+    }
+    acc -= c * V[(size_t)i * n + t];
+  }
+  const double v = acc * g.inv_hn;
   V[(size_t)g.j * n + t] = v;
   write_src(src, Ntot, gridDim.y, blockIdx.y, p, v);
 }
@@ -357,13 +416,14 @@ __device__ __forceinline__ double block_sum_ordered(double v, double* sh) {
   return sh[0];
 }
 
-// part[i G + b] = V_i . w over [t0, t1) for i <= j: warp k of the block takes
-// i = k, k + nwarps, ...; lanes stride the slice and a shuffle tree sums them (fixed order)
+// part[i G + b] = V_i . w over [t0, t1) for i <= j (and w . w for i = top = j + 1):
+// warp k of the block takes i = k, k + nwarps, ...; lanes stride the slice and a
+// shuffle tree sums them (fixed order)
 __device__ __forceinline__ void slice_dots(const double* __restrict__ V, size_t n, const double* __restrict__ w,
-                                           int j, size_t t0, size_t t1, double* part, int G, int b) {
+                                           int j, int top, size_t t0, size_t t1, double* part, int G, int b) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int i = warp; i <= j; i += nw) {
-    const double* v = V + (size_t)i * n;
+  for (int i = warp; i <= top; i += nw) {
+    const double* v = i > j ? w : V + (size_t)i * n;
     double acc = 0.0;
     for (size_t t = t0 + lane; t < t1; t += 32) acc += v[t] * w[t];
 #pragma unroll
@@ -373,7 +433,7 @@ __device__ __forceinline__ void slice_dots(const double* __restrict__ V, size_t 
 }
 
 __global__ void __launch_bounds__(256) bk_step_fused(double* V, size_t n, double* w, int Ntot, int h, GPtr p,
-                                                     SrcOut so) {
+                                                     SrcOut so, int two_pass) {
   __shared__ double sh[256];
   __shared__ double c1[kGmMaxM + 1], c2[kGmMaxM + 1], scs[kGmMaxM], ssn[kGmMaxM];
   __shared__ double s_hn;
@@ -388,8 +448,35 @@ __global__ void __launch_bounds__(256) bk_step_fused(double* V, size_t n, double
   double* part2 = p.fp + (size_t)(m + 1) * G;
   double* partn = p.fp + 2 * (size_t)(m + 1) * G;
   // (A) partial V_i . w: warp w of the block takes i = w, w + 8, ... (no block barrier)
-  slice_dots(V, n, w, j, t0, t1, part1, G, b);
+  slice_dots(V, n, w, j, two_pass ? j : j + 1, t0, t1, part1, G, b);
   if (!grid_barrier(p.bar, &s_ok)) return;
+  if (!two_pass) {
+    // one round: h_{j+1,j}^2 = |w|^2 - sum c_i^2, V_{j+1} = (w - sum c_i V_i) / h_{j+1,j}
+    for (int i = tid; i <= j + 1; i += blockDim.x) {
+      double c = 0.0;
+      for (int q = 0; q < G; ++q) c += part1[(size_t)i * G + q];
+      c1[i] = c;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double nrm = c1[j + 1];
+      for (int i = 0; i <= j; ++i) nrm -= c1[i] * c1[i];
+      s_hn = sqrt(fmax(0.0, nrm));
+    }
+    __syncthreads();
+    const double hn = s_hn;
+    const double inv = hn > 1e-300 ? 1.0 / hn : 0.0;
+    for (size_t t = t0 + tid; t < t1; t += blockDim.x) {
+      double a = w[t];
+      for (int i = 0; i <= j; ++i) a -= c1[i] * V[(size_t)i * n + t];
+      const double v = a * inv;
+      V[(size_t)(j + 1) * n + t] = v;
+      const int q = int(t / (size_t)Ntot);
+      write_src(so, Ntot, h, q, int(t - (size_t)q * Ntot), v);
+    }
+    if (b == 0) givens_step(p, 0, j, hn, c1, scs, ssn);
+    return;
+  }
   // (B) w1 = w - sum c1_i V_i on the slice, then partial V_i . w1
   for (int i = tid; i <= j; i += blockDim.x) {
     double c = 0.0;
@@ -403,7 +490,7 @@ __global__ void __launch_bounds__(256) bk_step_fused(double* V, size_t n, double
     w[t] = a;
   }
   __syncthreads();
-  slice_dots(V, n, w, j, t0, t1, part2, G, b);
+  slice_dots(V, n, w, j, j, t0, t1, part2, G, b);
   if (!grid_barrier(p.bar, &s_ok)) return;
   // (C) w2 = w1 - sum c2_i V_i, partial |w2|^2
   for (int i = tid; i <= j; i += blockDim.x) {
@@ -572,9 +659,19 @@ SrcOut src_out(const Setup& s, int precision, void* xsrc) {
   return o;
 }
 
+// Gram-Schmidt of the Arnoldi step.  The FP64 solve (precision 0) orthogonalises twice
+// (CGS2) and takes the norm of the result.  The FP32 inner solves of the refinement
+// orthogonalise once and take the norm from |w|^2 - sum c_i^2, so that the dot products
+// and the norm share one reduction: the inner solve only has to cut the residual by a
+// few decades, its FP32 pair sums already limit the Arnoldi relation to about 1e-7, and
+// the residual of every refinement sweep is recomputed from scratch in FP64 or
+// double-float, so a lost digit there costs at most an extra sweep, never accuracy.
+int two_pass_gs(int precision) { return precision == 0 ? 1 : 0; }
+
 // kChunk Arnoldi iterations of every active system: pair pass on the source of V_j
-// (written by the previous bk_scale / bk_scale0), two rounds of classical Gram-Schmidt,
-// norm, Givens update and V_{j+1} with its source -- eight kernels per iteration.  With
+// (written by the previous bk_scale / bk_scale0 / bk_sub_scale), classical Gram-Schmidt
+// (see two_pass_gs), Givens update and V_{j+1} with its source -- eight kernels per
+// iteration with two rounds, four with one.  With
 // fused set and a single system the seven kernels after the pair pass are replaced by
 // bk_step_fused; that is faster for direct launches, while inside the cycle graph the
 // separate kernels (graph launch overhead about a microsecond each) measured faster than
@@ -593,22 +690,30 @@ gbi_status launch_chunk(gbi_ctx* ctx, const Setup& s, const Batch& B, int precis
   pa.sys_flag_stride = int(sizeof(GDev) / sizeof(int));
   const SrcOut so = src_out(s, precision, xsrc);
   const dim3 gd(S, m + 1, gp.CH);
+  const int two = two_pass_gs(precision);
   for (int c = 0; c < kChunk; ++c) {
     GBI_CHECK(run_pairs(ctx, s.trunc, SET_H, SET_H, precision, pa));
     if (fused && S == 1) {
       // a single system launched step by step: the whole orthogonalisation in one kernel
-      bk_step_fused<<<kFusedBlocks, 256, 0, ctx->stream>>>(Vb, n, w, Ntot, h, gp, so);
+      bk_step_fused<<<kFusedBlocks, 256, 0, ctx->stream>>>(Vb, n, w, Ntot, h, gp, so, two);
       ++ctx->launches;
       continue;
     }
-    bk_dots<<<gd, 256, 0, ctx->stream>>>(Vb, n, w, Ntot, h, B.off, gp.st, m, gp.CH, gp.h1p);
-    bk_sub<<<g2, 256, 0, ctx->stream>>>(Vb, n, w, Ntot, B.sys, gp.st, m, gp.CH, gp.h1p);
-    bk_dots<<<gd, 256, 0, ctx->stream>>>(Vb, n, w, Ntot, h, B.off, gp.st, m, gp.CH, gp.h2p);
-    bk_sub<<<g2, 256, 0, ctx->stream>>>(Vb, n, w, Ntot, B.sys, gp.st, m, gp.CH, gp.h2p);
-    bk_norm_part<<<dim3(S, gp.CH), 256, 0, ctx->stream>>>(w, Ntot, h, B.off, gp.st, 0, gp.CH, gp.nrmp);
-    bk_finalize<<<S, 128, 0, ctx->stream>>>(gp);
-    bk_scale<<<g2, 256, 0, ctx->stream>>>(Vb, n, w, Ntot, B.sys, gp.st, so);
-    ctx->launches += 7;
+    if (two) {
+      bk_dots<<<gd, 256, 0, ctx->stream>>>(Vb, n, w, Ntot, h, B.off, gp.st, m, gp.CH, gp.h1p, 0);
+      bk_sub<<<g2, 256, 0, ctx->stream>>>(Vb, n, w, Ntot, B.sys, gp.st, m, gp.CH, gp.h1p);
+      bk_dots<<<gd, 256, 0, ctx->stream>>>(Vb, n, w, Ntot, h, B.off, gp.st, m, gp.CH, gp.h2p, 0);
+      bk_sub<<<g2, 256, 0, ctx->stream>>>(Vb, n, w, Ntot, B.sys, gp.st, m, gp.CH, gp.h2p);
+      bk_norm_part<<<dim3(S, gp.CH), 256, 0, ctx->stream>>>(w, Ntot, h, B.off, gp.st, 0, gp.CH, gp.nrmp);
+      bk_finalize<<<S, 128, 0, ctx->stream>>>(gp, 1);
+      bk_scale<<<g2, 256, 0, ctx->stream>>>(Vb, n, w, Ntot, B.sys, gp.st, so);
+      ctx->launches += 7;
+    } else {
+      bk_dots<<<gd, 256, 0, ctx->stream>>>(Vb, n, w, Ntot, h, B.off, gp.st, m, gp.CH, gp.h1p, 1);
+      bk_finalize<<<S, 128, 0, ctx->stream>>>(gp, 0);
+      bk_sub_scale<<<g2, 256, 0, ctx->stream>>>(Vb, n, w, Ntot, B.sys, gp.st, m, gp.CH, gp.h1p, so);
+      ctx->launches += 3;
+    }
   }
   GBI_CHECK(cudaGetLastError());
   return GBI_OK;
