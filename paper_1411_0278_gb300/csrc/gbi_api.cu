@@ -579,7 +579,7 @@ constexpr size_t kOffGs = kOffX32 + al256(sizeof(float) * 2 * (kStaticMaxND + 3 
 constexpr size_t kOffBoff = kOffGs + al256(sizeof(double) * (64 + (kStaticMaxRestart + 1) * kStaticMaxRestart +
                                                               8 * (kStaticMaxRestart + 1) +
                                                               48 * (2 * (kStaticMaxRestart + 1) + 1) +
-                                                              kFusedBlocks * (2 * (kStaticMaxRestart + 1) + 1) + 24));
+                                                              kFusedBlocks * (2 * (kStaticMaxRestart + 1) + 1) + 24 + 2));
 constexpr size_t kOffBsys = kOffBoff + 256;
 constexpr size_t kStaticBytes = kOffBsys + al256(sizeof(int) * kStaticMaxN);
 

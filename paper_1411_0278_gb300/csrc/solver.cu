@@ -48,6 +48,7 @@ struct GPtr {     // per-system views into the gstate buffer
   int* nact;                  // systems still active after the current Arnoldi step
   unsigned int* bar;          // grid barrier of the fused single-system step: count, generation, error
   double* fp;                 // its per-block partial sums (two dot-product sets and the norm)
+  unsigned int* cnt;          // per system: blocks of bk_dots_fin done in the current step
   int S, m, CH;
 };
 
@@ -60,7 +61,8 @@ int arnoldi_chunks(int S, int h) { return S >= 64 ? 1 : h; }
 
 size_t gstate_doubles(int m, int S, int CH) {
   return (size_t)S * (sizeof(GDev) / sizeof(double) + 1) + (size_t)S * ((size_t)(m + 1) * m + 5 * (size_t)(m + 1) + 1) +
-         (size_t)S * CH * (2 * (size_t)(m + 1) + 1) + (size_t)kFusedBlocks * (2 * (size_t)(m + 1) + 1) + 24;
+         (size_t)S * CH * (2 * (size_t)(m + 1) + 1) + (size_t)kFusedBlocks * (2 * (size_t)(m + 1) + 1) + 24 +
+         ((size_t)S + 1) / 2 + 1;
 }
 
 GPtr gptrs(void* base, int m, int S, int CH) {
@@ -84,6 +86,8 @@ GPtr gptrs(void* base, int m, int S, int CH) {
   p.bar = reinterpret_cast<unsigned int*>(d);
   d += 2;
   p.fp = d;
+  d += 21 + (size_t)kFusedBlocks * (2 * (size_t)(m + 1) + 1);
+  p.cnt = reinterpret_cast<unsigned int*>(d);
   return p;
 }
 
@@ -250,30 +254,27 @@ __device__ void givens_step(const GPtr& p, int s, int j, double hn, double* col,
 // the norm of the twice-orthogonalised vector (nrmp).  Otherwise one round: h1p holds
 // c_i = V_i . w for i <= j and |w|^2 in slot j + 1, and with orthonormal V_i
 // |w - sum c_i V_i|^2 = |w|^2 - sum c_i^2 (clamped at zero).
-__global__ void bk_finalize(GPtr p, int two_pass) {
-  const int s = blockIdx.x;
-  GDev* st = p.st + s;
-  if (!st->active) return;
+__device__ void finalize_column(const GPtr& p, int s, int j, int two_pass) {
   __shared__ double col[kGmMaxM + 1], scs[kGmMaxM], ssn[kGmMaxM];
-  const int j = st->j, m = p.m;
-  const size_t o1 = (size_t)s * (m + 1);
+  __shared__ double s_hn;
+  const size_t o1 = (size_t)s * (p.m + 1);
   const int top = two_pass ? j : j + 1;
   for (int i = threadIdx.x; i <= top; i += blockDim.x) {
+    // L2 loads: the partials may come from other blocks of the same kernel
     const double* a1 = p.h1p + (o1 + i) * p.CH;
     double c1 = 0.0, c2 = 0.0;
-    for (int c = 0; c < p.CH; ++c) c1 += a1[c];
+    for (int c = 0; c < p.CH; ++c) c1 += __ldcg(a1 + c);
     if (two_pass) {
       const double* a2 = p.h2p + (o1 + i) * p.CH;
-      for (int c = 0; c < p.CH; ++c) c2 += a2[c];
+      for (int c = 0; c < p.CH; ++c) c2 += __ldcg(a2 + c);
     }
     col[i] = c1 + c2;
   }
-  __shared__ double s_hn;
   __syncthreads();
   if (threadIdx.x == 0) {
     double nrm = 0.0;
     if (two_pass) {
-      for (int c = 0; c < p.CH; ++c) nrm += p.nrmp[(size_t)s * p.CH + c];
+      for (int c = 0; c < p.CH; ++c) nrm += __ldcg(p.nrmp + (size_t)s * p.CH + c);
     } else {
       nrm = col[j + 1];
       for (int i = 0; i <= j; ++i) nrm -= col[i] * col[i];
@@ -282,6 +283,50 @@ __global__ void bk_finalize(GPtr p, int two_pass) {
   }
   __syncthreads();
   givens_step(p, s, j, s_hn, col, scs, ssn);
+}
+
+__global__ void bk_finalize(GPtr p, int two_pass) {
+  const int s = blockIdx.x;
+  const GDev* st = p.st + s;
+  if (!st->active) return;
+  finalize_column(p, s, st->j, two_pass);
+}
+
+// One-reduction Arnoldi step, first half, for fewer than 64 systems: block (s, i, c)
+// forms V_i . w (w . w for i = j_s + 1) over the component rows of chunk c of system s,
+// as bk_dots does.  Every block of an active system, with a slot or without, counts
+// itself in cnt[s] after its partial is stored; the last one sums the partials (chunk
+// order) and runs the Givens step.  All blocks read j_s and the active flag before they
+// count, so none can see the state the last block writes.
+__global__ void __launch_bounds__(256) bk_dots_fin(const double* __restrict__ V, size_t n,
+                                                   const double* __restrict__ w, int Ntot, int h,
+                                                   const int* __restrict__ off, GPtr p) {
+  const int s = blockIdx.x, i = blockIdx.y, c = blockIdx.z;
+  const GDev* st = p.st + s;
+  if (!st->active) return;
+  const int j = st->j, CH = p.CH;
+  if (i <= j + 1) {
+    const double* v = i > j ? w : V + (size_t)i * n;
+    const int lo = off[s], hi = off[s + 1];
+    const int q0 = c * h / CH, q1 = (c + 1) * h / CH;
+    double acc = 0.0;
+    for (int q = q0; q < q1; ++q) {
+      const size_t b = (size_t)q * Ntot;
+      for (int t = lo + threadIdx.x; t < hi; t += blockDim.x) acc += v[b + t] * w[b + t];
+    }
+    const double tot = block_sum_256(acc);
+    if (threadIdx.x == 0) p.h1p[((size_t)s * (p.m + 1) + i) * CH + c] = tot;
+  }
+  __shared__ int s_last;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(p.cnt + s, 1u) == gridDim.y * gridDim.z - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (threadIdx.x == 0) p.cnt[s] = 0u;
+  finalize_column(p, s, j, 0);
 }
 
 // Arnoldi source of the next pair pass, written by the kernels that produce V_j:
@@ -305,9 +350,27 @@ __device__ __forceinline__ void write_src(const SrcOut& o, int Ntot, int h, int 
   }
 }
 
+// End of one device-looped Arnoldi step: inside the cycle graph the step's last kernel
+// keeps the loop going while any system is still active (the WHILE node reads the value
+// set here) and resets the count; its first thread does it before any block can leave.
+struct LoopCtl {
+  int* nact;
+  cudaGraphConditionalHandle h;
+  int on;
+};
+
+__device__ __forceinline__ void loop_continue(const LoopCtl& lc) {
+  if (lc.on && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+    const int v = *lc.nact;
+    *lc.nact = 0;
+    cudaGraphSetConditional(lc.h, v > 0 ? 1u : 0u);
+  }
+}
+
 // V_{j_s} = w / h for the newly advanced j_s (and its Arnoldi source)
 __global__ void bk_scale(double* V, size_t n, const double* __restrict__ w, int Ntot, const int* __restrict__ sys,
-                         const GDev* __restrict__ st, SrcOut src) {
+                         const GDev* __restrict__ st, SrcOut src, LoopCtl lc) {
+  loop_continue(lc);
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= Ntot) return;
   const GDev& g = st[sys[p]];
@@ -323,7 +386,8 @@ __global__ void bk_scale(double* V, size_t n, const double* __restrict__ w, int 
 // into shared memory when the block's spheres all belong to one system), and its source.
 __global__ void bk_sub_scale(double* V, size_t n, const double* __restrict__ w, int Ntot,
                              const int* __restrict__ sys, const GDev* __restrict__ st, int m, int CH,
-                             const double* __restrict__ part, SrcOut src) {
+                             const double* __restrict__ part, SrcOut src, LoopCtl lc) {
+  loop_continue(lc);
   __shared__ double sc[kMaxRestart + 1];
   const int p0 = blockIdx.x * blockDim.x;
   const int pl = min(Ntot - 1, p0 + (int)blockDim.x - 1);
@@ -531,14 +595,6 @@ __global__ void __launch_bounds__(256) bk_step_fused(double* V, size_t n, double
   }
 }
 
-// End of one device-looped Arnoldi step: keep looping while any system is still active
-// (the WHILE node of the cycle graph reads the value set here), and reset the count.
-__global__ void bk_continue(GPtr p, cudaGraphConditionalHandle h) {
-  const int v = *p.nact;
-  *p.nact = 0;
-  cudaGraphSetConditional(h, v > 0 ? 1u : 0u);
-}
-
 // start of a GMRES cycle for every enabled system: beta = |V_0|, g = (beta, 0, ...)
 __global__ void bk_init_cycle(GPtr p, int first) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -677,7 +733,7 @@ int two_pass_gs(int precision) { return precision == 0 ? 1 : 0; }
 // separate kernels (graph launch overhead about a microsecond each) measured faster than
 // the fused kernel's three grid barriers.
 gbi_status launch_chunk(gbi_ctx* ctx, const Setup& s, const Batch& B, int precision, const GPtr& gp, int m,
-                        double* Vb, double* w, void* xsrc, int kChunk, bool fused) {
+                        double* Vb, double* w, void* xsrc, int kChunk, bool fused, LoopCtl lc = LoopCtl{}) {
   const int S = B.S, Ntot = B.Ntot, h = s.h;
   const size_t n = (size_t)Ntot * h;
   const dim3 g2((Ntot + 255) / 256, h);
@@ -706,13 +762,20 @@ gbi_status launch_chunk(gbi_ctx* ctx, const Setup& s, const Batch& B, int precis
       bk_sub<<<g2, 256, 0, ctx->stream>>>(Vb, n, w, Ntot, B.sys, gp.st, m, gp.CH, gp.h2p);
       bk_norm_part<<<dim3(S, gp.CH), 256, 0, ctx->stream>>>(w, Ntot, h, B.off, gp.st, 0, gp.CH, gp.nrmp);
       bk_finalize<<<S, 128, 0, ctx->stream>>>(gp, 1);
-      bk_scale<<<g2, 256, 0, ctx->stream>>>(Vb, n, w, Ntot, B.sys, gp.st, so);
+      bk_scale<<<g2, 256, 0, ctx->stream>>>(Vb, n, w, Ntot, B.sys, gp.st, so, lc);
       ctx->launches += 7;
     } else {
-      bk_dots<<<gd, 256, 0, ctx->stream>>>(Vb, n, w, Ntot, h, B.off, gp.st, m, gp.CH, gp.h1p, 1);
-      bk_finalize<<<S, 128, 0, ctx->stream>>>(gp, 0);
-      bk_sub_scale<<<g2, 256, 0, ctx->stream>>>(Vb, n, w, Ntot, B.sys, gp.st, m, gp.CH, gp.h1p, so);
-      ctx->launches += 3;
+      if (S < 64) {
+        // dot products, norm and Givens step in one kernel
+        bk_dots_fin<<<gd, 256, 0, ctx->stream>>>(Vb, n, w, Ntot, h, B.off, gp);
+        ++ctx->launches;
+      } else {
+        bk_dots<<<gd, 256, 0, ctx->stream>>>(Vb, n, w, Ntot, h, B.off, gp.st, m, gp.CH, gp.h1p, 1);
+        bk_finalize<<<S, 128, 0, ctx->stream>>>(gp, 0);
+        ctx->launches += 2;
+      }
+      bk_sub_scale<<<g2, 256, 0, ctx->stream>>>(Vb, n, w, Ntot, B.sys, gp.st, m, gp.CH, gp.h1p, so, lc);
+      ++ctx->launches;
     }
   }
   GBI_CHECK(cudaGetLastError());
@@ -731,6 +794,7 @@ __global__ void bk_setup(GPtr p, double tol, int max_iter, double outer_rtol) {
     p.bar[0] = 0u;   // arrivals
     p.bar[2] = 0u;   // error flag
   }
+  p.cnt[s] = 0u;
   st->tol = outer_rtol > 0 ? fmax(tol, 0.1 * outer_rtol / fmax(st->rel, 1e-300)) : tol;
   st->max_iter = max_iter;
   st->m = p.m;
@@ -761,10 +825,10 @@ gbi_status gmres_batch(gbi_ctx* ctx, const Setup& s, const Batch& B, int precisi
   relres = 0.0;
   bk_setup<<<sblk, 128, 0, ctx->stream>>>(gp, tol, std::max(0, max_iter), outer_rtol);
   ++ctx->launches;
-  // cycle graph: a WHILE node whose body is one Arnoldi step of every active system
-  // followed by bk_continue; the loop runs on the device until no system is active, so a
-  // GMRES cycle costs one graph launch and one read of the per-system states.  Built
-  // once per buffer set and replayed afterwards.
+  // cycle graph: a WHILE node whose body is one Arnoldi step of every active system, the
+  // step's last kernel setting the loop condition; the loop runs on the device until no
+  // system is active, so a GMRES cycle costs one graph launch and one read of the
+  // per-system states.  Built once per buffer set and replayed afterwards.
   const bool graphs = ctx->allow_graphs && ctx->stream != nullptr && !ctx->prof;
   if (graphs) {
     const void* key[8] = {Vb, w, xsrc, ctx->gstate.p, B.sys, B.off, s.pos.hi, s.pos.p64};
@@ -791,9 +855,7 @@ gbi_status gmres_batch(gbi_ctx* ctx, const Setup& s, const Batch& B, int precisi
         e = cudaStreamBeginCaptureToGraph(ctx->stream, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
                                           cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-          st = launch_chunk(ctx, s, B, precision, gp, m, Vb, w, xsrc, 1, false);
-          bk_continue<<<1, 1, 0, ctx->stream>>>(gp, handle);
-          ++ctx->launches;
+          st = launch_chunk(ctx, s, B, precision, gp, m, Vb, w, xsrc, 1, false, LoopCtl{gp.nact, handle, 1});
           cudaGraph_t body = nullptr;
           const cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &body);
           if (e == cudaSuccess) e = e2;
