@@ -335,6 +335,15 @@ int gbi_pass_wpt(gbi_ctx* ctx, int trunc, int rows, int cols, int precision, int
  * 27 = closed-form trap pass in FP64, 28 = in FP32.  gbi_kernel_stats synchronizes
  * on the recorded events. */
 long long gbi_kernel_launches(gbi_ctx* ctx);
+/* Number of solves this context has run as one replayed CUDA graph (-1 for a NULL
+ * context).  A mixed-precision solve (precision 1..3, zero initial guess) on a
+ * non-default stream, with profiling off, is captured as one graph the second time a
+ * call repeats the previous call's sizes, parameters, tuning and workspace, and
+ * replayed while they stay the same; the refinement sweeps, GMRES restarts and Arnoldi
+ * steps then loop on the device (nested conditional graph nodes) and the call waits for
+ * the GPU once.  Results are identical to the host-driven sequence.  No counterpart in
+ * the paper. */
+long long gbi_solve_graph_replays(gbi_ctx* ctx);
 gbi_status gbi_set_profiling(gbi_ctx* ctx, int on);
 gbi_status gbi_kernel_stats(gbi_ctx* ctx, int kernel_class, double* total_ms, long long* launches,
                             double* flops);

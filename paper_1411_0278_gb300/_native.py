@@ -86,6 +86,7 @@ _SIGS = {
     "gbi_mlp_train": (_I, [_VP, _I, _VP, _VP, _D, _I, ctypes.POINTER(ctypes.c_int), _VP, _I, _I, _D, _D,
                            c_double_p]),
     "gbi_kernel_launches": (ctypes.c_longlong, [_VP]),
+    "gbi_solve_graph_replays": (ctypes.c_longlong, [_VP]),
     "gbi_set_profiling": (_I, [_VP, _I]),
     "gbi_kernel_stats": (_I, [_VP, _I, c_double_p, ctypes.POINTER(ctypes.c_longlong), c_double_p]),
 }
@@ -418,6 +419,9 @@ class Context:
 
     def kernel_launches(self):
         return int(lib().gbi_kernel_launches(self._h))
+
+    def solve_graph_replays(self):
+        return int(lib().gbi_solve_graph_replays(self._h))
 
     def set_profiling(self, on):
         self._check(lib().gbi_set_profiling(self._h, int(bool(on))), "gbi_set_profiling")

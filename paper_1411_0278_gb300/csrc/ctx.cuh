@@ -18,6 +18,8 @@ struct Buf {
   void* p = nullptr;
   size_t bytes = 0;
 };
+// nesting depth of the conditional bodies in the solve graph (one capture stream each)
+constexpr int kCapLevels = 4;
 }  // namespace gbi
 
 struct gbi_ctx {
@@ -36,6 +38,15 @@ struct gbi_ctx {
   const void* chunk_key[8] = {};                 // buffers and sizes the graph was built for
   long long chunk_ikey[6] = {};
   int chunk_nodes = 0;                           // kernels per loop iteration
+  // the whole mixed-precision solve as one graph: built when a call repeats the previous
+  // call's key (buffers, sizes, parameters, tuning), replayed while the key stays
+  cudaGraphExec_t solve_exec = nullptr;
+  std::vector<long long> solve_key, solve_prev, solve_failed;
+  long long solve_own[5] = {};                   // kernels: top level, per sweep, inner solve, cycle, step
+  cudaStream_t cap[gbi::kCapLevels] = {};        // capture streams of the nested bodies
+  gbi::Buf dsolve;                               // its device-side counters
+  long long wpt_gen = 0;                         // bumped whenever the warps-per-target choice changes
+  long long solve_replays = 0;                   // solves run from solve_exec
   gbi::Buf tFe, tTe, tVa, tOa, tVH, tV, tOm, tQH;  // trap-step staging
   int tqh_N = -1, tqh_trunc = -1;                // tQH holds the last trap-step solution of this size
   gbi::Buf hR, hVa, hOa, hVH, hFe, hTe, hV, hOm, hQH;  // gbi_solve_host staging

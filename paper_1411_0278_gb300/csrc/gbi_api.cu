@@ -164,6 +164,7 @@ gbi_status tune_impl(gbi_ctx* ctx, int trunc, int nsys, const int* offsets, int 
       break;
     }
     ctx->wpt_table[gbi_ctx::wpt_key(trunc, ps.rows, ps.cols, ps.precision, Ntot, batched)] = best;
+    ++ctx->wpt_gen;
     if (chosen) chosen[k] = best;
   }
   ctx->pool.push_back(e0);
@@ -203,12 +204,15 @@ gbi_status gbi_destroy(gbi_ctx* ctx) {
                  &ctx->hOm, &ctx->hQH, &ctx->mlp_th, &ctx->mlp_m, &ctx->mlp_v, &ctx->mlp_thq, &ctx->mlp_pk,
                  &ctx->mlp_grad, &ctx->mlp_pk_tc, &ctx->mlp_err, &ctx->nb_cnt, &ctx->nb_start, &ctx->nb_tg, &ctx->nb_sr, &ctx->nb_scan,
                  &ctx->cell_of, &ctx->cell_cnt, &ctx->cell_start, &ctx->cell_fill, &ctx->cell_items, &ctx->nb_aux,
-                 &ctx->mf_F, &ctx->mf_FR, &ctx->mf_lab, &ctx->mf_dO, &ctx->mf_part, &ctx->mf_loss};
+                 &ctx->mf_F, &ctx->mf_FR, &ctx->mf_lab, &ctx->mf_dO, &ctx->mf_part, &ctx->mf_loss, &ctx->dsolve};
   for (Buf* b : bufs)
     if (b->p) cudaFree(b->p);
   drain_profile(ctx);
   for (cudaEvent_t e : ctx->pool) cudaEventDestroy(e);
   if (ctx->chunk_exec) cudaGraphExecDestroy(ctx->chunk_exec);
+  if (ctx->solve_exec) cudaGraphExecDestroy(ctx->solve_exec);
+  for (cudaStream_t cs : ctx->cap)
+    if (cs) cudaStreamDestroy(cs);
   delete ctx;
   return GBI_OK;
 }
@@ -473,6 +477,7 @@ gbi_status gbi_tune(gbi_ctx* ctx, int trunc, int nsys, const int* offsets, int r
 gbi_status gbi_set_wpt(gbi_ctx* ctx, int wpt) {
   if (!ctx || !(wpt == 0 || wpt == 2 || wpt == 4 || wpt == 8 || wpt == 16)) return GBI_ERR_ARG;
   ctx->force_wpt = wpt;
+  ++ctx->wpt_gen;
   return GBI_OK;
 }
 
@@ -510,6 +515,8 @@ gbi_status gbi_kernel_stats(gbi_ctx* ctx, int kernel_class, double* total_ms, lo
 }
 
 long long gbi_kernel_launches(gbi_ctx* ctx) { return ctx ? ctx->launches : -1; }
+
+long long gbi_solve_graph_replays(gbi_ctx* ctx) { return ctx ? ctx->solve_replays : -1; }
 
 gbi_status gbi_solve_host(gbi_ctx* ctx, const gbi_params* prm, int N, const double* R, const double* Va,
                           const double* Oa, const double* VH, const double* Fe, const double* Te, double* V,

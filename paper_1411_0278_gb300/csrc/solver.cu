@@ -34,7 +34,7 @@ struct GDev {
   int breakdown;  // happy breakdown (exact solution in the Krylov space)
   int max_iter, m;
   int enabled;    // refinement: this system still needs a correction
-  int pad;
+  int it0;        // iterations already counted (device-decided solve)
   double bnorm, tol, res, beta, inv_hn;
   double nb;      // |b_s| (reference of the refinement residual)
   double rel;     // |b_s - A q_s| / |b_s|
@@ -52,7 +52,23 @@ struct GPtr {     // per-system views into the gstate buffer
   int S, m, CH;
 };
 
-// blocks of the fused single-system Arnoldi step (each holds a slice of the vectors)
+// Counters of the device-decided solve (one record per call, read back at the end):
+// what the host-driven sequence accumulates in gbi_info, plus the number of times each
+// loop body of the solve graph ran.
+struct DSolve {
+  long long iters;        // inner GMRES iterations over the whole solve
+  long long mv32, mv64;   // pair passes decided on the device
+  long long pairs;        // their ordered pairs
+  long long steps;        // Arnoldi loop iterations
+  long long cycles;       // GMRES cycles
+  int refinements;        // refinement sweeps after the first
+  int ifs;                // sweeps that ran an inner solve
+  int first, notfirst;    // the current inner solve is in its first cycle / past it
+  int overlap;            // the overlap guard stopped the solve
+  int pad;
+  double rel_max;         // largest final relative residual over the systems
+};
+
 
 // Row chunks per system of the Arnoldi reductions: a few systems get one block per
 // component row (so that a single suspension still spreads over many SMs), large
@@ -357,12 +373,14 @@ struct LoopCtl {
   int* nact;
   cudaGraphConditionalHandle h;
   int on;
+  long long* steps;   // optional count of loop iterations
 };
 
 __device__ __forceinline__ void loop_continue(const LoopCtl& lc) {
   if (lc.on && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
     const int v = *lc.nact;
     *lc.nact = 0;
+    if (lc.steps != nullptr) *lc.steps += 1;
     cudaGraphSetConditional(lc.h, v > 0 ? 1u : 0u);
   }
 }
@@ -596,13 +614,24 @@ __global__ void __launch_bounds__(256) bk_step_fused(double* V, size_t n, double
 }
 
 // start of a GMRES cycle for every enabled system: beta = |V_0|, g = (beta, 0, ...)
-__global__ void bk_init_cycle(GPtr p, int first) {
+// In the solve graph (d set) `first` comes from the device record and the Arnoldi
+// loop's condition is reset to 1, so that its body runs at least once, as it does when
+// the cycle graph is launched.
+__global__ void bk_init_cycle(GPtr p, int first, const DSolve* d = nullptr,
+                              cudaGraphConditionalHandle ha = 0) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s == 0) *p.nact = 0;
+  if (d != nullptr) first = d->first;
+  if (s == 0) {
+    *p.nact = 0;
+    if (d != nullptr) cudaGraphSetConditional(ha, 1u);
+  }
   if (s >= p.S) return;
   GDev* st = p.st + s;
   const int m = p.m;
-  if (first) st->iters = 0;
+  if (first) {
+    st->iters = 0;
+    st->it0 = 0;
+  }
   st->j = 0;
   st->kdim = 0;
   st->breakdown = 0;
@@ -786,13 +815,22 @@ gbi_status launch_chunk(gbi_ctx* ctx, const Setup& s, const Batch& B, int precis
 // tolerance relative to the current residual r is loosened to 0.1 outer_rtol |b| / |r|
 // when that is larger than tol: the solve only has to bring |r| a decade below the
 // target, so a refinement sweep that starts close to it needs few iterations.
-__global__ void bk_setup(GPtr p, double tol, int max_iter, double outer_rtol) {
+// In the solve graph (d set) the iteration cap is what the whole solve has left, the
+// record marks the first cycle and the restart loop's condition starts at 1.
+__global__ void bk_setup(GPtr p, double tol, int max_iter, double outer_rtol, DSolve* d = nullptr,
+                         cudaGraphConditionalHandle hr = 0) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= p.S) return;
   GDev* st = p.st + s;
+  if (d != nullptr) max_iter = (int)max(0ll, (long long)max_iter - d->iters);
   if (s == 0) {
     p.bar[0] = 0u;   // arrivals
     p.bar[2] = 0u;   // error flag
+    if (d != nullptr) {
+      d->first = 1;
+      d->notfirst = 0;
+      cudaGraphSetConditional(hr, 1u);
+    }
   }
   p.cnt[s] = 0u;
   st->tol = outer_rtol > 0 ? fmax(tol, 0.1 * outer_rtol / fmax(st->rel, 1e-300)) : tol;
@@ -963,6 +1001,274 @@ gbi_status gmres_batch(gbi_ctx* ctx, const Setup& s, const Batch& B, int precisi
   return GBI_OK;
 }
 
+// ---------------------------------------------------------------------------------
+// The whole mixed-precision solve as one CUDA graph
+// ---------------------------------------------------------------------------------
+//
+// Every decision that solve_core's host-driven sequence takes between kernels is taken on
+// the device instead: the refinement sweeps, the GMRES cycles of an inner solve and the
+// Arnoldi steps of a cycle are nested WHILE nodes (an IF node skips the inner solve of a
+// sweep that has met the tolerance), and the counters of gbi_info live in a DSolve record
+// read back once.  The kernels and their order are those of the host-driven sequence, so
+// the results are the same bit for bit.
+
+// one-block reductions over the systems
+__device__ __forceinline__ long long sys_pairs(const int* __restrict__ off, int s) {
+  const long long n = off[s + 1] - off[s];
+  return n * (n - 1);
+}
+
+__global__ void gk_copy(double* __restrict__ dst, const double* __restrict__ src, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    dst[i] = src[i];
+}
+
+__global__ void gk_zero(double* __restrict__ dst, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    dst[i] = 0.0;
+}
+
+// overlap guard: a centre distance below min_sep a stops every system (the host reports
+// GBI_ERR_OVERLAP after the graph)
+__global__ void gk_overlap(GPtr p, const unsigned int* __restrict__ minr2, double a, double min_sep, DSolve* d) {
+  const float mr2 = __uint_as_float(*minr2);
+  if (!(sqrt(double(mr2)) / a < min_sep)) return;
+  for (int s = threadIdx.x; s < p.S; s += blockDim.x) p.st[s].enabled = 0;
+  if (threadIdx.x == 0) d->overlap = 1;
+}
+
+// the sweep loop runs while some system still needs a correction
+__global__ void gk_sweep_start(GPtr p, cudaGraphConditionalHandle hsw) {
+  int any = 0;
+  for (int s = threadIdx.x; s < p.S; s += blockDim.x) any |= p.st[s].enabled;
+  any = __syncthreads_or(any);
+  if (threadIdx.x == 0) cudaGraphSetConditional(hsw, any ? 1u : 0u);
+}
+
+// a residual pass over the enabled systems has run
+__global__ void gk_count_pass(GPtr p, const int* __restrict__ off, DSolve* d) {
+  __shared__ unsigned long long sp;
+  if (threadIdx.x == 0) sp = 0ull;
+  __syncthreads();
+  unsigned long long c = 0;
+  for (int s = threadIdx.x; s < p.S; s += blockDim.x)
+    if (p.st[s].enabled) c += (unsigned long long)sys_pairs(off, s);
+  atomicAdd(&sp, c);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    d->mv64 += 1;
+    d->pairs += (long long)sp;
+  }
+}
+
+// after the residual of sweep k >= 1: run its inner solve (and come back for sweep k + 1)
+// while some system needs a correction and neither cap is reached
+__global__ void gk_sweep_decide(GPtr p, DSolve* d, int max_refine, int max_iter, cudaGraphConditionalHandle hsw,
+                                cudaGraphConditionalHandle hif) {
+  int any = 0;
+  for (int s = threadIdx.x; s < p.S; s += blockDim.x) any |= p.st[s].enabled;
+  any = __syncthreads_or(any);
+  if (threadIdx.x == 0) {
+    d->refinements += 1;
+    const int go = any && d->refinements < max_refine && d->iters < max_iter;
+    d->ifs += go;
+    cudaGraphSetConditional(hif, go ? 1u : 0u);
+    cudaGraphSetConditional(hsw, go ? 1u : 0u);
+  }
+}
+
+// end of a GMRES cycle: count its pair passes, decide the restart
+__global__ void gk_cycle_end(GPtr p, const int* __restrict__ off, DSolve* d, cudaGraphConditionalHandle hr) {
+  __shared__ unsigned long long sp;
+  __shared__ int slive;
+  if (threadIdx.x == 0) {
+    sp = 0ull;
+    slive = 0;
+  }
+  __syncthreads();
+  const int v0_ran = d->notfirst;
+  unsigned long long c = 0;
+  int live = 0, any = 0;
+  for (int s = threadIdx.x; s < p.S; s += blockDim.x) {
+    GDev* st = p.st + s;
+    const unsigned long long np = (unsigned long long)sys_pairs(off, s);
+    if (v0_ran && st->enabled) c += np;
+    const int dd = st->iters - st->it0;
+    st->it0 = st->iters;
+    c += (unsigned long long)dd * np;
+    live = max(live, dd);
+    if (st->enabled && st->kdim > 0 && !st->converged && !st->breakdown && st->iters < st->max_iter) any = 1;
+  }
+  atomicAdd(&sp, c);
+  atomicMax(&slive, live);
+  any = __syncthreads_or(any);
+  if (threadIdx.x == 0) {
+    d->pairs += (long long)sp;
+    d->mv32 += slive + (v0_ran ? 1 : 0);
+    d->cycles += 1;
+    d->first = 0;
+    d->notfirst = 1;
+    cudaGraphSetConditional(hr, any ? 1u : 0u);
+  }
+}
+
+// end of an inner solve: its iterations are the most any system took
+__global__ void gk_gmres_end(GPtr p, DSolve* d) {
+  __shared__ int smax;
+  if (threadIdx.x == 0) smax = 0;
+  __syncthreads();
+  int mx = 0;
+  for (int s = threadIdx.x; s < p.S; s += blockDim.x) mx = max(mx, p.st[s].iters);
+  atomicMax(&smax, mx);
+  __syncthreads();
+  if (threadIdx.x == 0) d->iters += smax;
+}
+
+__global__ void gk_summary(GPtr p, DSolve* d) {
+  __shared__ double sm[256];
+  double mx = 0.0;
+  for (int s = threadIdx.x; s < p.S; s += blockDim.x) mx = fmax(mx, p.st[s].rel);
+  sm[threadIdx.x] = mx;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sm[threadIdx.x] = fmax(sm[threadIdx.x], sm[threadIdx.x + o]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) d->rel_max = sm[0];
+}
+
+// Building the graph by stream capture: a conditional node is added to the graph that
+// the current stream is capturing, and its body is captured on a stream of its own
+// (one per nesting level) while the library's launches are pointed at that stream.
+struct GraphBuild {
+  gbi_ctx* ctx;
+  cudaError_t err = cudaSuccess;
+  int nopen = 0;                   // bodies being captured
+  long long nested[kCapLevels + 1] = {};   // launches inside nested bodies, per depth (0: top)
+  long long own[4] = {};           // launches per execution of a body kind (see BodyKind)
+
+  bool ok(cudaError_t e) {
+    if (e != cudaSuccess && err == cudaSuccess) err = e;
+    return err == cudaSuccess;
+  }
+  cudaGraph_t capturing() {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaGraph_t g = nullptr;
+    if (!ok(cudaStreamGetCaptureInfo(ctx->stream, &cs, nullptr, &g, nullptr, nullptr, nullptr))) return nullptr;
+    if (cs != cudaStreamCaptureStatusActive) {
+      ok(cudaErrorStreamCaptureInvalidated);
+      return nullptr;
+    }
+    return g;
+  }
+  cudaGraphConditionalHandle handle() {
+    cudaGraphConditionalHandle h = 0;
+    cudaGraph_t g = capturing();
+    if (g != nullptr) ok(cudaGraphConditionalHandleCreate(&h, g, 0, 0));
+    return h;
+  }
+  // a conditional node after everything captured so far on the current stream
+  cudaGraph_t node(cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    if (!ok(cudaStreamGetCaptureInfo(ctx->stream, &cs, nullptr, &g, &deps, nullptr, &nd))) return nullptr;
+    cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+    cp.conditional.handle = h;
+    cp.conditional.type = type;
+    cp.conditional.size = 1;
+    cudaGraphNode_t nodeh = nullptr;
+    if (!ok(cudaGraphAddNode(&nodeh, g, deps, nullptr, nd, &cp))) return nullptr;
+    if (!ok(cudaStreamUpdateCaptureDependencies(ctx->stream, &nodeh, nullptr, 1, cudaStreamSetCaptureDependencies)))
+      return nullptr;
+    return cp.conditional.phGraph_out[0];
+  }
+  // capture emit() into body on the next level's stream; kind: which own[] it fills
+  template <typename F>
+  gbi_status body(cudaGraph_t g, int kind, F&& emit) {
+    const int k = nopen + 1;   // nesting depth of the new body
+    if (g == nullptr || err != cudaSuccess || k > kCapLevels) return GBI_ERR_CUDA;
+    cudaStream_t cs = ctx->cap[k - 1];
+    if (!ok(cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)))
+      return GBI_ERR_CUDA;
+    cudaStream_t outer = ctx->stream;
+    nested[k] = 0;
+    nopen = k;
+    ctx->stream = cs;
+    const long long before = ctx->launches;
+    const gbi_status st = emit();
+    ctx->stream = outer;
+    nopen = k - 1;
+    cudaGraph_t out = nullptr;
+    ok(cudaStreamEndCapture(cs, &out));
+    const long long total = ctx->launches - before;
+    own[kind] = total - nested[k];
+    nested[k - 1] += total;
+    if (st != GBI_OK) return st;
+    return err == cudaSuccess ? GBI_OK : GBI_ERR_CUDA;
+  }
+};
+
+enum BodyKind { kBodySweep = 0, kBodyIf = 1, kBodyCycle = 2, kBodyStep = 3 };
+
+gbi_status gmres_reserve(gbi_ctx* ctx, const Setup& s, const Batch& B, int m) {
+  const size_t n = (size_t)B.Ntot * s.h;
+  GBI_TRY(ensure(ctx, ctx->krylov, sizeof(double) * n * (m + 1)));
+  GBI_TRY(ensure(ctx, ctx->w, sizeof(double) * n));
+  GBI_TRY(ensure(ctx, ctx->gstate, sizeof(double) * gstate_doubles(m, B.S, arnoldi_chunks(B.S, s.h))));
+  GBI_TRY(ensure(ctx, ctx->x32, std::max(sizeof(double) * n, sizeof(float) * (size_t)B.Ntot * ((s.h + 3) & ~3))));
+  return GBI_OK;
+}
+
+// Inner FP32 GMRES of one sweep in the solve graph: set-up, then a WHILE node over the
+// cycles whose body is one cycle of gmres_batch (V_0 = rhs - A u, norms, cycle start,
+// the Arnoldi WHILE node, triangular solve, update, restart decision).
+gbi_status emit_gmres(GraphBuild& gb, const Setup& s, const Batch& B, const GPtr& gp, int m, const double* rhs,
+                      double* u, double tol, int max_iter, double outer_rtol, DSolve* d) {
+  gbi_ctx* ctx = gb.ctx;
+  const int S = B.S, Ntot = B.Ntot, h = s.h;
+  const size_t n = (size_t)Ntot * h;
+  double* Vb = P<double>(ctx->krylov);
+  double* w = P<double>(ctx->w);
+  void* xsrc = ctx->x32.p;
+  const dim3 g2((Ntot + 255) / 256, h);
+  const int sblk = (S + 127) / 128;
+  const cudaGraphConditionalHandle hr = gb.handle();
+  bk_setup<<<sblk, 128, 0, ctx->stream>>>(gp, tol, max_iter, outer_rtol, d, hr);
+  ++ctx->launches;
+  GBI_TRY(gb.body(gb.node(hr, cudaGraphCondTypeWhile), kBodyCycle, [&]() -> gbi_status {
+    gk_copy<<<grid1(n), 256, 0, ctx->stream>>>(Vb, rhs, n);
+    ++ctx->launches;
+    PairArgs pr = pair_args(s, u, Vb, -1.0, 1.0, 1, s.ones, 6);
+    pr.sys_of = B.sys;
+    pr.sys_off = B.off;
+    pr.sys_flag = &gp.st[0].enabled;
+    pr.sys_flag_stride = int(sizeof(GDev) / sizeof(int));
+    pr.active = &d->notfirst;   // u is zero in the first cycle
+    GBI_CHECK(run_pairs(ctx, s.trunc, SET_H, SET_H, 1, pr));
+    bk_norm_part<<<dim3(S, gp.CH), 256, 0, ctx->stream>>>(Vb, Ntot, h, B.off, gp.st, 1, gp.CH, gp.nrmp);
+    bk_norm_sum<<<(S + 127) / 128, 128, 0, ctx->stream>>>(gp.nrmp, gp.st, S, 1, gp.CH, gp.nrm);
+    const cudaGraphConditionalHandle ha = gb.handle();
+    bk_init_cycle<<<sblk, 128, 0, ctx->stream>>>(gp, 0, d, ha);
+    bk_scale0<<<g2, 256, 0, ctx->stream>>>(Vb, Ntot, B.sys, gp.st, src_out(s, 1, xsrc));
+    ctx->launches += 4;
+    GBI_TRY(gb.body(gb.node(ha, cudaGraphCondTypeWhile), kBodyStep, [&]() -> gbi_status {
+      return launch_chunk(ctx, s, B, 1, gp, m, Vb, w, xsrc, 1, false, LoopCtl{gp.nact, ha, 1, &d->steps});
+    }));
+    bk_solve_y<<<S, 128, 0, ctx->stream>>>(gp);
+    bk_update<<<g2, 256, 0, ctx->stream>>>(Vb, n, Ntot, B.sys, gp, s.minv, u);
+    gk_cycle_end<<<1, 256, 0, ctx->stream>>>(gp, B.off, d, hr);
+    ctx->launches += 3;
+    GBI_CHECK(cudaGetLastError());
+    return GBI_OK;
+  }));
+  gk_gmres_end<<<1, 256, 0, ctx->stream>>>(gp, d);
+  ++ctx->launches;
+  GBI_CHECK(cudaGetLastError());
+  return GBI_OK;
+}
+
 // The full solve for a batch of independent suspensions (S = 1: one suspension).
 // Inputs and outputs are concatenated over the systems ([Ntot][3], [Ntot][h]).
 gbi_status solve_core(gbi_ctx* ctx, const gbi_params* prm, const Batch& B, const double* R, const double* Va,
@@ -1009,29 +1315,213 @@ gbi_status solve_core(gbi_ctx* ctx, const gbi_params* prm, const Batch& B, const
     p.sys_flag_stride = int(sizeof(GDev) / sizeof(int));
     return p;
   };
-  // host copies of the per-system states, the barrier words and per-system counters
+  // host copies of the per-system states, the barrier words, per-system counters and
+  // the solve graph's record with the smallest-distance word
   const size_t hs_states = (sizeof(GDev) * (size_t)S + 15) & ~size_t(15);
-  GBI_TRY(host_scratch(ctx, hs_states + 16 + sizeof(int) * (size_t)S));
+  const size_t hs_rec = hs_states + 16 + ((sizeof(int) * (size_t)S + 15) & ~size_t(15));
+  GBI_TRY(host_scratch(ctx, hs_rec + sizeof(DSolve) + 16));
   GDev* hst = reinterpret_cast<GDev*>(ctx->hs);
   unsigned int* hbar = reinterpret_cast<unsigned int*>(ctx->hs + hs_states);
   int* hbefore = reinterpret_cast<int*>(ctx->hs + hs_states + 16);
+  DSolve* hrec = reinterpret_cast<DSolve*>(ctx->hs + hs_rec);
+  unsigned int* hbits = reinterpret_cast<unsigned int*>(ctx->hs + hs_rec + sizeof(DSolve));
 
-  // inputs -> internal coordinates
-  k_pack_lower<<<grid1(N), 256, 0, ctx->stream>>>(N, s.a, c2a, Fe, Te, xF);
-  // b = -8 pi eta V^H
-  k_pack_higher<<<grid1(nh), 256, 0, ctx->stream>>>(N, h, VH, hscale, -8.0 * kPi * s.eta, b);
-  ctx->launches += 2;
-  GBI_CHECK(cudaGetLastError());
+  // the caller's inputs -> internal coordinates: F^L and b = -8 pi eta V^H
+  auto pack_inputs = [&]() -> gbi_status {
+    k_pack_lower<<<grid1(N), 256, 0, ctx->stream>>>(N, s.a, c2a, Fe, Te, xF);
+    k_pack_higher<<<grid1(nh), 256, 0, ctx->stream>>>(N, h, VH, hscale, -8.0 * kPi * s.eta, b);
+    ctx->launches += 2;
+    GBI_CHECK(cudaGetLastError());
+    return GBI_OK;
+  };
   // b -= G^HL F^L, with the overlap scan
-  const unsigned int init_bits = 0x7f7fffffu;
-  GBI_CHECK(cudaMemcpyAsync(ctx->minr2.p, &init_bits, sizeof(unsigned int), cudaMemcpyHostToDevice, ctx->stream));
-  {
+  auto rhs_pass = [&]() -> gbi_status {
+    GBI_CHECK(cudaMemsetAsync(ctx->minr2.p, 0x7f, sizeof(unsigned int), ctx->stream));   // a huge float
     PairArgs p = batched(pair_args(s, xF, b, -1.0, 1.0, 0, s.ones, 0), nullptr);
     p.min_r2_bits = P<unsigned int>(ctx->minr2);
     GBI_CHECK(run_pairs(ctx, s.trunc, SET_H, SET_L, io, p));
-    (io == 1 ? inf->matvecs_f32 : inf->matvecs_f64) += 1;
-    inf->pair_interactions += pairs_all;
+    return GBI_OK;
+  };
+  // 8 pi eta x^{V,L} = -(G^LL F^L + G^LH Q^H) incl. self
+  auto output_pass = [&]() -> gbi_status {
+    PairArgs p = batched(pair_args(s, P<double>(ctx->xQ), P<double>(ctx->xVL), -1.0 / (8.0 * kPi * s.eta), 0.0, 1,
+                                   s.ones, 0),
+                         nullptr);
+    GBI_CHECK(run_pairs(ctx, s.trunc, SET_L, SET_ALL, io, p));
+    return GBI_OK;
+  };
+  // internal coordinates -> the caller's V, Omega (and Q^H)
+  auto unpack_outputs = [&]() -> gbi_status {
+    k_finalize_lower<<<grid1(N), 256, 0, ctx->stream>>>(N, s.a, c2a, P<double>(ctx->xVL), Va, Oa, V, Omega);
+    ++ctx->launches;
+    if (QH) {
+      k_unpack_higher<<<grid1(nh), 256, 0, ctx->stream>>>(N, h, xQH, hscale, QH);
+      ++ctx->launches;
+    }
+    GBI_CHECK(cudaGetLastError());
+    return GBI_OK;
+  };
+  const int max_iter = prm->max_iter > 0 ? prm->max_iter : 1000;
+  const double rtol = prm->rtol > 0 ? prm->rtol : 1e-10;
+  const double inner = prm->inner_rtol > 0 ? prm->inner_rtol : 1e-5;
+  const int max_refine = prm->max_refine > 0 ? prm->max_refine : 8;
+
+  // ---- the mixed-precision solve as one graph (see GraphBuild): every device step of
+  // the sequence below, the decisions taken by kernels instead of the host
+  if (prm->precision >= 1 && !warm_start && ctx->allow_graphs && ctx->stream != nullptr && !ctx->prof) {
+    auto bits = [](double v) {
+      long long b;
+      std::memcpy(&b, &v, sizeof(b));
+      return b;
+    };
+    // the graph reads and writes only the context's own buffers (the caller's arrays are
+    // packed before it and unpacked after it), so the key holds none of the caller's
+    // every buffer the graph touches at its final size first (a repeated call then
+    // allocates nothing): the Krylov workspace, the device record, and the source
+    // records of every FP32 / double-float pass (right-hand side, residual, outputs)
+    GBI_TRY(gmres_reserve(ctx, s, B, restart));
+    GBI_TRY(ensure(ctx, ctx->dsolve, sizeof(DSolve)));
+    {
+      size_t x32b = ctx->x32.bytes;
+      const int pass_cols[3] = {SET_L, SET_H, SET_ALL};
+      const int pass_prec[3] = {io, hp, io};
+      for (int i = 0; i < 3; ++i)
+        if (pass_prec[i] >= 1)
+          x32b = std::max(x32b, sizeof(float) * (size_t)rec_floats(ncols_of(s.trunc, pass_cols[i]), pass_prec[i] == 2) *
+                                    (size_t)N);
+      GBI_TRY(ensure(ctx, ctx->x32, x32b));
+    }
+    const void* ptrs[] = {B.sys, B.off, ctx->pos_hi.p, ctx->pos_lo.p, ctx->pos64.p, ctx->xQ.p, ctx->b.p, ctx->r.p, ctx->delta.p, ctx->xVL.p, ctx->minr2.p,
+                          ctx->krylov.p, ctx->w.p, ctx->x32.p, ctx->gstate.p, ctx->dsolve.p};
+    std::vector<long long> key = {N, S, pairs_all, prm->trunc, prm->precision, restart, max_iter, max_refine,
+                                  bits(rtol), bits(inner), bits(prm->min_sep), bits(prm->a), bits(prm->eta),
+                                  ctx->wpt_gen, ctx->force_wpt};
+    for (const void* q : ptrs) key.push_back((long long)(uintptr_t)q);
+    const bool ready = ctx->solve_exec != nullptr && key == ctx->solve_key;
+    const bool build = !ready && key == ctx->solve_prev && key != ctx->solve_failed;
+    ctx->solve_prev = key;
+    if (build) {
+      // a repeated call: its buffers already have their sizes, so nothing below allocates
+      bool built = false;
+      {
+        bool streams = true;
+        for (int i = 0; i < kCapLevels && streams; ++i)
+          if (!ctx->cap[i]) streams = cudaStreamCreateWithFlags(&ctx->cap[i], cudaStreamNonBlocking) == cudaSuccess;
+        if (streams) {
+          if (ctx->solve_exec) cudaGraphExecDestroy(ctx->solve_exec);
+          ctx->solve_exec = nullptr;
+          DSolve* d = P<DSolve>(ctx->dsolve);
+          GraphBuild gb{ctx};
+          const long long saved = ctx->launches;
+          gbi_status st = GBI_ERR_CUDA;
+          cudaGraph_t graph = nullptr;
+          if (cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            st = [&]() -> gbi_status {
+              GBI_CHECK(cudaMemsetAsync(d, 0, sizeof(DSolve), ctx->stream));
+              GBI_TRY(rhs_pass());
+              GBI_CHECK(cudaMemsetAsync(xQH, 0, sizeof(double) * nh, ctx->stream));
+              bk_norm_part<<<dim3(S, gp.CH), 256, 0, ctx->stream>>>(b, N, h, B.off, gp.st, 2, gp.CH, gp.nrmp);
+              bk_norm_sum<<<(S + 127) / 128, 128, 0, ctx->stream>>>(gp.nrmp, gp.st, S, 2, gp.CH, gp.nrm);
+              bk_refine<<<sblk, 128, 0, ctx->stream>>>(gp, 0, rtol);
+              ctx->launches += 3;
+              if (prm->min_sep > 0 && pairs_all > 0) {
+                gk_overlap<<<1, 256, 0, ctx->stream>>>(gp, P<unsigned int>(ctx->minr2), s.a, prm->min_sep, d);
+                ++ctx->launches;
+              }
+              // sweep 0: the residual is b
+              GBI_CHECK(cudaMemcpyAsync(r, b, sizeof(double) * nh, cudaMemcpyDeviceToDevice, ctx->stream));
+              GBI_CHECK(cudaMemsetAsync(dl, 0, sizeof(double) * nh, ctx->stream));
+              GBI_TRY(emit_gmres(gb, s, B, gp, restart, r, dl, inner, max_iter, rtol, d));
+              bk_axpy_enabled<<<g2, 256, 0, ctx->stream>>>(dl, N, B.sys, gp.st, xQH);
+              ++ctx->launches;
+              // sweeps 1, 2, ...: residual in the high precision, refinement test, inner solve
+              const cudaGraphConditionalHandle hsw = gb.handle();
+              gk_sweep_start<<<1, 256, 0, ctx->stream>>>(gp, hsw);
+              ++ctx->launches;
+              GBI_TRY(gb.body(gb.node(hsw, cudaGraphCondTypeWhile), kBodySweep, [&]() -> gbi_status {
+                gk_copy<<<grid1(nh), 256, 0, ctx->stream>>>(r, b, nh);
+                ++ctx->launches;
+                PairArgs p = batched(pair_args(s, xQH, r, -1.0, 1.0, 1, s.ones, 6), &gp.st[0].enabled);
+                GBI_CHECK(run_pairs(ctx, s.trunc, SET_H, SET_H, hp, p));
+                gk_count_pass<<<1, 256, 0, ctx->stream>>>(gp, B.off, d);
+                bk_norm_part<<<dim3(S, gp.CH), 256, 0, ctx->stream>>>(r, N, h, B.off, gp.st, 1, gp.CH, gp.nrmp);
+                bk_norm_sum<<<(S + 127) / 128, 128, 0, ctx->stream>>>(gp.nrmp, gp.st, S, 1, gp.CH, gp.nrm);
+                bk_refine<<<sblk, 128, 0, ctx->stream>>>(gp, 1, rtol);
+                const cudaGraphConditionalHandle hif = gb.handle();
+                gk_sweep_decide<<<1, 256, 0, ctx->stream>>>(gp, d, max_refine, max_iter, hsw, hif);
+                ctx->launches += 5;
+                GBI_CHECK(cudaGetLastError());
+                return gb.body(gb.node(hif, cudaGraphCondTypeIf), kBodyIf, [&]() -> gbi_status {
+                  gk_zero<<<grid1(nh), 256, 0, ctx->stream>>>(dl, nh);
+                  ++ctx->launches;
+                  GBI_TRY(emit_gmres(gb, s, B, gp, restart, r, dl, inner, max_iter, rtol, d));
+                  bk_axpy_enabled<<<g2, 256, 0, ctx->stream>>>(dl, N, B.sys, gp.st, xQH);
+                  ++ctx->launches;
+                  GBI_CHECK(cudaGetLastError());
+                  return GBI_OK;
+                });
+              }));
+              gk_summary<<<1, 256, 0, ctx->stream>>>(gp, d);
+              ++ctx->launches;
+              return output_pass();
+            }();
+            const cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
+            if (st == GBI_OK && (e != cudaSuccess || gb.err != cudaSuccess)) st = GBI_ERR_CUDA;
+          }
+          const long long total = ctx->launches - saved;
+          ctx->launches = saved;
+          if (st == GBI_OK && cudaGraphInstantiate(&ctx->solve_exec, graph, 0) != cudaSuccess) {
+            ctx->solve_exec = nullptr;
+            st = GBI_ERR_CUDA;
+          }
+          if (graph) cudaGraphDestroy(graph);
+          if (st == GBI_OK) {
+            built = true;
+            ctx->solve_key = key;
+            ctx->solve_prev = key;
+            ctx->solve_own[0] = total - gb.nested[0];
+            for (int i = 0; i < 4; ++i) ctx->solve_own[1 + i] = gb.own[i];
+          }
+        }
+      }
+      if (!built) {
+        // the graph could not be built here: the host-driven sequence serves this key
+        cudaGetLastError();
+        ctx->solve_failed = key;
+      }
+    }
+    if (ctx->solve_exec != nullptr && key == ctx->solve_key) {
+      DSolve* d = P<DSolve>(ctx->dsolve);
+      GBI_TRY(pack_inputs());
+      GBI_CHECK(cudaGraphLaunch(ctx->solve_exec, ctx->stream));
+      ++ctx->solve_replays;
+      GBI_TRY(unpack_outputs());
+      GBI_CHECK(cudaMemcpyAsync(hrec, d, sizeof(DSolve), cudaMemcpyDeviceToHost, ctx->stream));
+      GBI_CHECK(cudaMemcpyAsync(hbits, ctx->minr2.p, sizeof(unsigned int), cudaMemcpyDeviceToHost, ctx->stream));
+      GBI_CHECK(cudaStreamSynchronize(ctx->stream));
+      const DSolve& hd = *hrec;
+      ctx->launches += ctx->solve_own[0] + (long long)hd.refinements * ctx->solve_own[1] +
+                       (long long)hd.ifs * ctx->solve_own[2] + hd.cycles * ctx->solve_own[3] +
+                       hd.steps * ctx->solve_own[4];
+      // the right-hand-side and output passes are the two the host knows of
+      inf->iters = (int)hd.iters;
+      inf->refinements = hd.refinements;
+      inf->matvecs_f32 = (int)hd.mv32 + (io == 1 ? 2 : 0);
+      inf->matvecs_f64 = (int)hd.mv64 + (io == 1 ? 0 : 2);
+      inf->pair_interactions = hd.pairs + 2 * pairs_all;
+      inf->rel_residual = hd.rel_max;
+      float mr2;
+      std::memcpy(&mr2, hbits, sizeof(float));
+      inf->min_separation = pairs_all > 0 ? std::sqrt(double(mr2)) / s.a : 0.0;
+      if (hd.overlap) return GBI_ERR_OVERLAP;
+      return hd.rel_max <= rtol ? GBI_OK : GBI_ERR_NOT_CONVERGED;
+    }
   }
+
+  GBI_TRY(pack_inputs());
+  GBI_TRY(rhs_pass());
+  (io == 1 ? inf->matvecs_f32 : inf->matvecs_f64) += 1;
+  inf->pair_interactions += pairs_all;
   if (prm->min_sep > 0) {
     unsigned int bits = 0;
     GBI_CHECK(cudaMemcpyAsync(&bits, ctx->minr2.p, sizeof(unsigned int), cudaMemcpyDeviceToHost, ctx->stream));
@@ -1051,8 +1541,6 @@ gbi_status solve_core(gbi_ctx* ctx, const gbi_params* prm, const Batch& B, const
   } else {
     GBI_CHECK(cudaMemsetAsync(xQH, 0, sizeof(double) * nh, ctx->stream));
   }
-  const int max_iter = prm->max_iter > 0 ? prm->max_iter : 1000;
-  const double rtol = prm->rtol > 0 ? prm->rtol : 1e-10;
   // |b_s| per system
   bk_norm_part<<<dim3(S, gp.CH), 256, 0, ctx->stream>>>(b, N, h, B.off, gp.st, 2, gp.CH, gp.nrmp);
   bk_norm_sum<<<(S + 127) / 128, 128, 0, ctx->stream>>>(gp.nrmp, gp.st, S, 2, gp.CH, gp.nrm);
@@ -1092,8 +1580,6 @@ gbi_status solve_core(gbi_ctx* ctx, const gbi_params* prm, const Batch& B, const
     GBI_TRY(read_state());
   } else {
     // mixed precision: r = b - A_hp x; A_32 d = r (FP32 pair sums, FP64 Arnoldi); x += d
-    const double inner = prm->inner_rtol > 0 ? prm->inner_rtol : 1e-5;
-    const int max_refine = prm->max_refine > 0 ? prm->max_refine : 8;
     for (int sweep = 0;; ++sweep) {
       GBI_CHECK(cudaMemcpyAsync(r, b, sizeof(double) * nh, cudaMemcpyDeviceToDevice, ctx->stream));
       if (!(zero && sweep == 0)) {
@@ -1131,22 +1617,10 @@ gbi_status solve_core(gbi_ctx* ctx, const gbi_params* prm, const Batch& B, const
     inf->rel_residual = std::max(inf->rel_residual, hst[q].rel);
     if (hst[q].rel > rtol) converged = false;
   }
-  // outputs: 8 pi eta x^{V,L} = -(G^LL F^L + G^LH Q^H) incl. self
-  {
-    PairArgs p = batched(pair_args(s, P<double>(ctx->xQ), P<double>(ctx->xVL), -1.0 / (8.0 * kPi * s.eta), 0.0, 1,
-                                   s.ones, 0),
-                         nullptr);
-    GBI_CHECK(run_pairs(ctx, s.trunc, SET_L, SET_ALL, io, p));
-    (io == 1 ? inf->matvecs_f32 : inf->matvecs_f64) += 1;
-    inf->pair_interactions += pairs_all;
-  }
-  k_finalize_lower<<<grid1(N), 256, 0, ctx->stream>>>(N, s.a, c2a, P<double>(ctx->xVL), Va, Oa, V, Omega);
-  ++ctx->launches;
-  if (QH) {
-    k_unpack_higher<<<grid1(nh), 256, 0, ctx->stream>>>(N, h, xQH, hscale, QH);
-    ++ctx->launches;
-  }
-  GBI_CHECK(cudaGetLastError());
+  GBI_TRY(output_pass());
+  GBI_TRY(unpack_outputs());
+  (io == 1 ? inf->matvecs_f32 : inf->matvecs_f64) += 1;
+  inf->pair_interactions += pairs_all;
   if (prm->min_sep <= 0) {
     unsigned int bits = 0;
     GBI_CHECK(cudaMemcpyAsync(&bits, ctx->minr2.p, sizeof(unsigned int), cudaMemcpyDeviceToHost, ctx->stream));

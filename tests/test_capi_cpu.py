@@ -58,6 +58,8 @@ def test_tuning_calls_validate_without_a_device(gbi):
     assert L.gbi_tune(None, 2, 1, offs, 1, None) == gbi.GBI_ERR_ARG
     assert L.gbi_set_wpt(None, 4) == gbi.GBI_ERR_ARG
     assert L.gbi_pass_wpt(None, 2, 2, 2, 1, 100, 0) == -1
+    assert L.gbi_solve_graph_replays(None) == -1
+    assert L.gbi_kernel_launches(None) == -1
 
 
 def test_nearfield_calls_validate_without_a_device(gbi):
