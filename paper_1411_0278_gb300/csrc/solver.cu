@@ -369,6 +369,8 @@ __device__ __forceinline__ void write_src(const SrcOut& o, int Ntot, int h, int 
 // End of one device-looped Arnoldi step: inside the cycle graph the step's last kernel
 // keeps the loop going while any system is still active (the WHILE node reads the value
 // set here) and resets the count; its first thread does it before any block can leave.
+// When the loop body holds several Arnoldi steps, the steps before the last only reset
+// the count (on = 1); the last one (on = 2) also sets the condition and counts the trip.
 struct LoopCtl {
   int* nact;
   cudaGraphConditionalHandle h;
@@ -380,8 +382,10 @@ __device__ __forceinline__ void loop_continue(const LoopCtl& lc) {
   if (lc.on && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
     const int v = *lc.nact;
     *lc.nact = 0;
-    if (lc.steps != nullptr) *lc.steps += 1;
-    cudaGraphSetConditional(lc.h, v > 0 ? 1u : 0u);
+    if (lc.on == 2) {
+      if (lc.steps != nullptr) *lc.steps += 1;
+      cudaGraphSetConditional(lc.h, v > 0 ? 1u : 0u);
+    }
   }
 }
 
@@ -753,6 +757,11 @@ SrcOut src_out(const Setup& s, int precision, void* xsrc) {
 // double-float, so a lost digit there costs at most an extra sweep, never accuracy.
 int two_pass_gs(int precision) { return precision == 0 ? 1 : 0; }
 
+// Arnoldi steps per trip of a device-side loop: a trip costs about 4.5 us of conditional
+// node overhead on GB300 besides its kernels, a step after its system has stopped about
+// 4 us (its kernels return at once), so several steps a trip pay off.
+constexpr int kArnoldiUnroll = 4;
+
 // kChunk Arnoldi iterations of every active system: pair pass on the source of V_j
 // (written by the previous bk_scale / bk_scale0 / bk_sub_scale), classical Gram-Schmidt
 // (see two_pass_gs), Givens update and V_{j+1} with its source -- eight kernels per
@@ -777,6 +786,8 @@ gbi_status launch_chunk(gbi_ctx* ctx, const Setup& s, const Batch& B, int precis
   const dim3 gd(S, m + 1, gp.CH);
   const int two = two_pass_gs(precision);
   for (int c = 0; c < kChunk; ++c) {
+    LoopCtl lcs = lc;
+    if (lc.on) lcs.on = c + 1 < kChunk ? 1 : 2;
     GBI_CHECK(run_pairs(ctx, s.trunc, SET_H, SET_H, precision, pa));
     if (fused && S == 1) {
       // a single system launched step by step: the whole orthogonalisation in one kernel
@@ -791,7 +802,7 @@ gbi_status launch_chunk(gbi_ctx* ctx, const Setup& s, const Batch& B, int precis
       bk_sub<<<g2, 256, 0, ctx->stream>>>(Vb, n, w, Ntot, B.sys, gp.st, m, gp.CH, gp.h2p);
       bk_norm_part<<<dim3(S, gp.CH), 256, 0, ctx->stream>>>(w, Ntot, h, B.off, gp.st, 0, gp.CH, gp.nrmp);
       bk_finalize<<<S, 128, 0, ctx->stream>>>(gp, 1);
-      bk_scale<<<g2, 256, 0, ctx->stream>>>(Vb, n, w, Ntot, B.sys, gp.st, so, lc);
+      bk_scale<<<g2, 256, 0, ctx->stream>>>(Vb, n, w, Ntot, B.sys, gp.st, so, lcs);
       ctx->launches += 7;
     } else {
       if (S < 64) {
@@ -803,7 +814,7 @@ gbi_status launch_chunk(gbi_ctx* ctx, const Setup& s, const Batch& B, int precis
         bk_finalize<<<S, 128, 0, ctx->stream>>>(gp, 0);
         ctx->launches += 2;
       }
-      bk_sub_scale<<<g2, 256, 0, ctx->stream>>>(Vb, n, w, Ntot, B.sys, gp.st, m, gp.CH, gp.h1p, so, lc);
+      bk_sub_scale<<<g2, 256, 0, ctx->stream>>>(Vb, n, w, Ntot, B.sys, gp.st, m, gp.CH, gp.h1p, so, lcs);
       ++ctx->launches;
     }
   }
@@ -893,7 +904,8 @@ gbi_status gmres_batch(gbi_ctx* ctx, const Setup& s, const Batch& B, int precisi
         e = cudaStreamBeginCaptureToGraph(ctx->stream, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
                                           cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-          st = launch_chunk(ctx, s, B, precision, gp, m, Vb, w, xsrc, 1, false, LoopCtl{gp.nact, handle, 1});
+          st = launch_chunk(ctx, s, B, precision, gp, m, Vb, w, xsrc, kArnoldiUnroll, false,
+                            LoopCtl{gp.nact, handle, 1, nullptr});
           cudaGraph_t body = nullptr;
           const cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &body);
           if (e == cudaSuccess) e = e2;
@@ -967,9 +979,9 @@ gbi_status gmres_batch(gbi_ctx* ctx, const Setup& s, const Batch& B, int precisi
       GBI_TRY(read_states());
       int most = 0;
       for (int q = 0; q < S; ++q) most = std::max(most, hst[q].iters - before[q]);
-      const int steps = std::max(1, most);
-      ctx->launches += (long long)steps * ctx->chunk_nodes;
-      account(steps);
+      const int trips = std::max(1, (most + kArnoldiUnroll - 1) / kArnoldiUnroll);
+      ctx->launches += (long long)trips * ctx->chunk_nodes;
+      account(trips * kArnoldiUnroll);
     } else {
       // host-driven: chunks of kChunk steps with a state read after each
       GBI_TRY(read_states());
@@ -1254,7 +1266,7 @@ gbi_status emit_gmres(GraphBuild& gb, const Setup& s, const Batch& B, const GPtr
     bk_scale0<<<g2, 256, 0, ctx->stream>>>(Vb, Ntot, B.sys, gp.st, src_out(s, 1, xsrc));
     ctx->launches += 4;
     GBI_TRY(gb.body(gb.node(ha, cudaGraphCondTypeWhile), kBodyStep, [&]() -> gbi_status {
-      return launch_chunk(ctx, s, B, 1, gp, m, Vb, w, xsrc, 1, false, LoopCtl{gp.nact, ha, 1, &d->steps});
+      return launch_chunk(ctx, s, B, 1, gp, m, Vb, w, xsrc, kArnoldiUnroll, false, LoopCtl{gp.nact, ha, 1, &d->steps});
     }));
     bk_solve_y<<<S, 128, 0, ctx->stream>>>(gp);
     bk_update<<<g2, 256, 0, ctx->stream>>>(Vb, n, Ntot, B.sys, gp, s.minv, u);
