@@ -155,7 +155,8 @@ cudaError_t run_pairs(gbi_ctx* ctx, int trunc, int rows, int cols, int precision
   int extra = 0;
   if (args.wpt == 0)
     args.wpt = ctx->force_wpt > 0 ? ctx->force_wpt
-                                  : ctx->tuned_wpt(trunc, rows, cols, precision, args.N, args.sys_of != nullptr);
+                                  : ctx->tuned_wpt(trunc, rows, cols, precision, args.N,
+                                                   args.sys_of != nullptr && args.nsys > 1);
   if (precision == 2 || (precision == 1 && args.x32 == nullptr)) {
     // per-sphere source records (FP32, or the double-float hi/lo pair), once per pass,
     // so that the pair loop touches no FP64
@@ -174,6 +175,7 @@ cudaError_t run_pairs(gbi_ctx* ctx, int trunc, int rows, int cols, int precision
   return timed(ctx, precision * 9 + rows * 3 + cols, flops, 1 + extra,
                [&] { return launch_pairs(trunc, rows, cols, precision, args, ctx->stream); });
 }
+
 
 cudaError_t run_trap(gbi_ctx* ctx, const TrapArgs& t, int precision) {
   const double flops = trap_flops() * double(t.N) * double(t.N - 1);
@@ -306,16 +308,36 @@ PairArgs pair_args(const Setup& s, const double* x, double* y, double alpha, dou
   p.sys_off = nullptr;
   p.sys_flag = nullptr;
   p.sys_flag_stride = 0;
+  p.nsys = 1;
   return p;
+}
+
+// streaming multiprocessors of the context's device (cached)
+int sm_count(gbi_ctx* ctx) {
+  if (ctx->num_sms == 0) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess || v <= 0) v = 152;
+    ctx->num_sms = v;
+  }
+  return ctx->num_sms;
 }
 
 // S = 1 batch over the spheres [0, N): offsets and system ids in the context workspace
 gbi_status single_batch(gbi_ctx* ctx, int N, Batch& B) {
   GBI_TRY(ensure(ctx, ctx->boff, sizeof(int) * 2));
   GBI_TRY(ensure(ctx, ctx->bsys, sizeof(int) * (size_t)std::max(N, 1)));
-  const int off[2] = {0, N};
-  GBI_CHECK(cudaMemcpyAsync(ctx->boff.p, off, sizeof(off), cudaMemcpyHostToDevice, ctx->stream));
-  GBI_CHECK(cudaMemsetAsync(ctx->bsys.p, 0, sizeof(int) * (size_t)N, ctx->stream));
+  // the arrays already describe one system of N spheres unless a batch call or a
+  // reallocation changed them since
+  if (ctx->single_N != N || ctx->single_off != ctx->boff.p || ctx->single_sys != ctx->bsys.p) {
+    ctx->single_N = N;
+    ctx->single_off = ctx->boff.p;
+    ctx->single_sys = ctx->bsys.p;
+    ctx->single_off_host[0] = 0;
+    ctx->single_off_host[1] = N;
+    GBI_CHECK(cudaMemcpyAsync(ctx->boff.p, ctx->single_off_host, sizeof(int) * 2, cudaMemcpyHostToDevice,
+                              ctx->stream));
+    GBI_CHECK(cudaMemsetAsync(ctx->bsys.p, 0, sizeof(int) * (size_t)N, ctx->stream));
+  }
   B.S = 1;
   B.Ntot = N;
   B.off = P<int>(ctx->boff);
@@ -340,6 +362,7 @@ bool valid_offsets(int nsys, const int* off) {
 
 // Device copies of a batch layout (system offsets and the system of every sphere).
 gbi_status make_batch(gbi_ctx* ctx, int nsys, const int* offsets_host, Batch& B) {
+  ctx->single_N = -1;   // the batch arrays are rewritten below
   const int N = offsets_host[nsys];
   GBI_TRY(ensure(ctx, ctx->boff, sizeof(int) * (size_t)(nsys + 1)));
   GBI_TRY(ensure(ctx, ctx->bsys, sizeof(int) * (size_t)N));

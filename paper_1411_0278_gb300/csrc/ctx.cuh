@@ -29,6 +29,10 @@ struct gbi_ctx {
   gbi::Buf pos_hi, pos_lo, pos64;                // centres: hi / lo floats, FP64 copy
   gbi::Buf b, xQ, r, delta, krylov, w, xVL, minr2, x32, trapbuf, gstate;   // solve workspace
   gbi::Buf boff, bsys;                           // system offsets / ids of the current batch
+  int single_N = -1;                             // boff / bsys hold one system of this many spheres
+  const void* single_off = nullptr;              // ... in these buffers
+  const void* single_sys = nullptr;
+  int single_off_host[2] = {0, 0};               // source of that upload (outlives the async copy)
   char* hs = nullptr;                            // host scratch: per-system solver states, counters
   size_t hs_cap = 0;
   std::vector<char> hs_own;                      // its storage (a static array for gbi_solve_static)
@@ -116,6 +120,7 @@ gbi_status ensure(gbi_ctx* ctx, Buf& b, size_t bytes);
 template <typename T> T* P(Buf& b) { return reinterpret_cast<T*>(b.p); }
 
 cudaEvent_t take_event(gbi_ctx* ctx);
+int sm_count(gbi_ctx* ctx);
 // Resolve recorded event pairs into per-class totals (blocks on the last one).
 void drain_profile(gbi_ctx* ctx);
 

@@ -135,6 +135,7 @@ gbi_status tune_impl(gbi_ctx* ctx, int trunc, int nsys, const int* offsets, int 
     if (batched) {
       pa.sys_of = sys_of;
       pa.sys_off = sys_off;
+      pa.nsys = nsys;
     }
     const int nc = ncols_of(trunc, ps.cols);
     ColScale cs;
@@ -336,6 +337,7 @@ gbi_status gbi_batch_superpose(gbi_ctx* ctx, const gbi_params* prm, int nsys, co
                          0);
   p.sys_of = B.sys;
   p.sys_off = B.off;
+  p.nsys = B.S;
   GBI_CHECK(run_pairs(ctx, s.trunc, SET_L, SET_ALL, prm->precision == 3 ? 1 : prm->precision, p));
   k_finalize_lower<<<grid1(N), 256, 0, ctx->stream>>>(N, s.a, s.scale.v[3], P<double>(ctx->xVL), Va, Oa, V,
                                                       Omega);

@@ -57,6 +57,7 @@ struct PairArgs {
   const int* sys_off;
   const int* sys_flag;
   int sys_flag_stride;
+  int nsys;              // systems in the batch (<= 1: every target's sources are [0, N))
   int wpt;               // warps per target of the FP32 / double-float kernel (0: default)
 };
 

@@ -118,14 +118,6 @@ gbi_status mlp_prepare(gbi_ctx* ctx, int N, const double* R, const double* p, do
   return GBI_OK;
 }
 
-int sm_count(gbi_ctx* ctx) {
-  if (ctx->num_sms == 0) {
-    int v = 0;
-    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess || v <= 0) v = 152;
-    ctx->num_sms = v;
-  }
-  return ctx->num_sms;
-}
 
 // Network inference with the selected engine.  The tcgen05 kernel reports a wait that
 // gave up through a device flag that gbi_mlp_status reads back.

@@ -399,19 +399,74 @@ __device__ __forceinline__ void warp_transpose_sum(const T* v, T* out) {
   }
 }
 
+// One source m (not the target) of target n, centre th + tl, in the streaming forms:
+// the pair body on m's record, accumulated into acc; min_r2 keeps the smallest r^2.
+template <int TR, int ROWS, int COLS, typename T>
+__device__ __forceinline__ void stream_source(const PairArgs& args, const float4* __restrict__ rec, float4 th,
+                                              float4 tl, int m, T a, T* acc, float& min_r2) {
+  using S = PassShape<TR, ROWS, COLS>;
+  constexpr int D = S::D;
+  constexpr int C0 = S::C0;
+  constexpr int NC = S::NC;
+  constexpr bool DF = std::is_same<T, df>::value;
+  constexpr int NCP = RecShape<NC>::NCP;
+  constexpr int NV = RecShape<NC>::NV;
+  constexpr int RECV = DF ? 2 * NV : NV;
+  const float4 sh = __ldg(args.pos.hi + m), sl = __ldg(args.pos.lo + m);
+  float4 r4[RECV];
+#pragma unroll
+  for (int i = 0; i < RECV; ++i) r4[i] = __ldg(rec + (size_t)m * RECV + i);
+  T dx, dy, dz;
+  if constexpr (DF) {
+    // exact difference of the hi parts, plus the (tiny) difference of the lo parts
+    dx = df_two_sum(th.x, -sh.x) + df(tl.x - sl.x, 0.f);
+    dy = df_two_sum(th.y, -sh.y) + df(tl.y - sl.y, 0.f);
+    dz = df_two_sum(th.z, -sh.z) + df(tl.z - sl.z, 0.f);
+  } else {
+    dx = (th.x - sh.x) + (tl.x - sl.x);
+    dy = (th.y - sh.y) + (tl.y - sl.y);
+    dz = (th.z - sh.z) + (tl.z - sl.z);
+  }
+  min_r2 = fminf(min_r2, float(dx * dx + dy * dy + dz * dz));
+  T xl[D];
+#pragma unroll
+  for (int q = 0; q < NC; ++q) {
+    if constexpr (DF) xl[C0 + q] = df(f4c(r4, q), f4c(r4, NCP + q));
+    else xl[C0 + q] = f4c(r4, q);
+  }
+  pair_body<TR, ROWS, COLS, T>(dx, dy, dz, a, xl, acc);
+}
+
+// Row p (counted from the pass's first row) of target n in the streaming forms: the
+// pair sum (units 1/a), the self term, then y = alpha v + beta y.
+template <int TR, int ROWS, int COLS, typename T>
+__device__ __forceinline__ void store_target(const PairArgs& args, int n, int p, double sum) {
+  using S = PassShape<TR, ROWS, COLS>;
+  constexpr int R0 = S::R0;
+  constexpr int C0 = S::C0;
+  constexpr int NC = S::NC;
+  constexpr bool DF = std::is_same<T, df>::value;
+  constexpr int RECV = DF ? 2 * RecShape<NC>::NV : RecShape<NC>::NV;
+  const double inva = 1.0 / args.a;
+  double v = sum * inva;
+  if (args.add_self) {
+    // FP32 passes use the rounded source the pair terms saw; double-float the FP64 one
+    const int q = R0 - C0 + p;
+    const double* xsrc = args.x_index ? args.x + (size_t)(*args.x_index) * args.x_stride : args.x;
+    const double xs = DF ? xsrc[(size_t)q * args.N + n] * args.colscale[R0 + p]
+                         : double(args.x32[(size_t)n * (RECV * 4) + q]);
+    v += args.selfg[R0 + p] * inva * xs;
+  }
+  double* dst = args.y + (size_t)p * args.N + n;
+  *dst = args.alpha * v + (args.beta != 0.0 ? args.beta * (*dst) : 0.0);
+}
+
 template <int TR, int ROWS, int COLS, typename T, int WPT, int MINB>
 __global__ void __launch_bounds__(WPT * 32, MINB) pair_stream_kernel(const PairArgs args) {
   using S = PassShape<TR, ROWS, COLS>;
-  constexpr int D = S::D;
-  constexpr int R0 = S::R0;
-  constexpr int C0 = S::C0;
   constexpr int NR = S::NR;
-  constexpr int NC = S::NC;
   constexpr bool DF = std::is_same<T, df>::value;
   static_assert(DF || std::is_same<T, float>::value, "streaming pass is FP32 or double-float");
-  constexpr int NCP = RecShape<NC>::NCP;
-  constexpr int NV = RecShape<NC>::NV;
-  constexpr int RECV = DF ? 2 * NV : NV;       // float4 per source record
   constexpr int NRC = (NR + 31) / 32;
   __shared__ T red[WPT > 1 ? WPT : 1][NRC * 32];
 
@@ -437,30 +492,8 @@ __global__ void __launch_bounds__(WPT * 32, MINB) pair_stream_kernel(const PairA
   float min_r2 = 3.0e38f;
 
   for (int m = src_lo + warp * 32 + lane; m < src_hi; m += WPT * 32) {
-    const float4 sh = __ldg(args.pos.hi + m), sl = __ldg(args.pos.lo + m);
-    float4 r4[RECV];
-#pragma unroll
-    for (int i = 0; i < RECV; ++i) r4[i] = __ldg(rec + (size_t)m * RECV + i);
     if (m == n) continue;
-    T dx, dy, dz;
-    if constexpr (DF) {
-      // exact difference of the hi parts, plus the (tiny) difference of the lo parts
-      dx = df_two_sum(th.x, -sh.x) + df(tl.x - sl.x, 0.f);
-      dy = df_two_sum(th.y, -sh.y) + df(tl.y - sl.y, 0.f);
-      dz = df_two_sum(th.z, -sh.z) + df(tl.z - sl.z, 0.f);
-    } else {
-      dx = (th.x - sh.x) + (tl.x - sl.x);
-      dy = (th.y - sh.y) + (tl.y - sl.y);
-      dz = (th.z - sh.z) + (tl.z - sl.z);
-    }
-    min_r2 = fminf(min_r2, float(dx * dx + dy * dy + dz * dz));
-    T xl[D];
-#pragma unroll
-    for (int q = 0; q < NC; ++q) {
-      if constexpr (DF) xl[C0 + q] = df(f4c(r4, q), f4c(r4, NCP + q));
-      else xl[C0 + q] = f4c(r4, q);
-    }
-    pair_body<TR, ROWS, COLS, T>(dx, dy, dz, a, xl, acc);
+    stream_source<TR, ROWS, COLS, T>(args, rec, th, tl, m, a, acc, min_r2);
   }
 
   T tot[NRC];
@@ -483,22 +516,10 @@ __global__ void __launch_bounds__(WPT * 32, MINB) pair_stream_kernel(const PairA
       tot[c] = v;
     }
   }
-  const double inva = 1.0 / args.a;
 #pragma unroll
   for (int c = 0; c < NRC; ++c) {
     const int p = 32 * c + lane;
-    if (p >= NR) continue;
-    double v = gbi_to_double(tot[c]) * inva;
-    if (args.add_self) {
-      // FP32 passes use the rounded source the pair terms saw; double-float the FP64 one
-      const int q = R0 - C0 + p;
-      const double* xsrc = args.x_index ? args.x + (size_t)(*args.x_index) * args.x_stride : args.x;
-      const double xs = DF ? xsrc[(size_t)q * args.N + n] * args.colscale[R0 + p]
-                           : double(args.x32[(size_t)n * (RECV * 4) + q]);
-      v += args.selfg[R0 + p] * inva * xs;
-    }
-    double* dst = args.y + (size_t)p * args.N + n;
-    *dst = args.alpha * v + (args.beta != 0.0 ? args.beta * (*dst) : 0.0);
+    if (p < NR) store_target<TR, ROWS, COLS, T>(args, n, p, gbi_to_double(tot[c]));
   }
 }
 

@@ -779,6 +779,7 @@ gbi_status launch_chunk(gbi_ctx* ctx, const Setup& s, const Batch& B, int precis
                           6);
   if (precision == 1) pa.x32 = static_cast<const float*>(xsrc);
   pa.sys_of = B.sys;
+  pa.nsys = B.S;
   pa.sys_off = B.off;
   pa.sys_flag = &gp.st[0].active;
   pa.sys_flag_stride = int(sizeof(GDev) / sizeof(int));
@@ -929,6 +930,7 @@ gbi_status gmres_batch(gbi_ctx* ctx, const Setup& s, const Batch& B, int precisi
     if (!(first && u_is_zero)) {
       PairArgs pr = pair_args(s, u, Vb, -1.0, 1.0, 1, s.ones, 6);
       pr.sys_of = B.sys;
+      pr.nsys = B.S;
       pr.sys_off = B.off;
       pr.sys_flag = &gp.st[0].enabled;
       pr.sys_flag_stride = int(sizeof(GDev) / sizeof(int));
@@ -1254,6 +1256,7 @@ gbi_status emit_gmres(GraphBuild& gb, const Setup& s, const Batch& B, const GPtr
     ++ctx->launches;
     PairArgs pr = pair_args(s, u, Vb, -1.0, 1.0, 1, s.ones, 6);
     pr.sys_of = B.sys;
+    pr.nsys = B.S;
     pr.sys_off = B.off;
     pr.sys_flag = &gp.st[0].enabled;
     pr.sys_flag_stride = int(sizeof(GDev) / sizeof(int));
@@ -1322,6 +1325,7 @@ gbi_status solve_core(gbi_ctx* ctx, const gbi_params* prm, const Batch& B, const
   for (int i = 0; i < 54; ++i) hscale.v[i] = (i < h) ? s.scale.v[6 + i] : 1.0;
   auto batched = [&](PairArgs p, const int* flag) {
     p.sys_of = B.sys;
+    p.nsys = B.S;
     p.sys_off = B.off;
     p.sys_flag = flag;
     p.sys_flag_stride = int(sizeof(GDev) / sizeof(int));
