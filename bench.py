@@ -178,7 +178,7 @@ def run_reference(args):
 
 
 # passes timed by gbi_tune, in the order of its result
-TUNED_PASSES = ["HH_f32", "HH_df", "HL_df", "Lall_df"]
+TUNED_PASSES = ["HH_f32", "HH_df", "HL_df", "Lall_df", "HL_f32", "Lall_f32"]
 
 
 def learned_nearfield(ctx, gbi, dev, stream, peaks):

@@ -304,8 +304,9 @@ gbi_status gbi_mlp_train(gbi_ctx* ctx, int N, const double* R, const double* p, 
  * and double-float pair passes run one block per target sphere whose WPT warps split
  * the sources; WPT in {2, 4, 8, 16} (8 at most for trunc 4 and double-float) trades
  * parallelism at small N against per-target reduction work.
- * gbi_tune times every WPT for the four passes of a mixed-precision solve -- rows H /
- * columns H in FP32 and in double-float, H/L and L/all in double-float -- on synthetic
+ * gbi_tune times every WPT for the six FP32 / double-float passes of the mixed-precision
+ * solves -- rows H / columns H in FP32 and in double-float, H/L and L/all in
+ * double-float, H/L and L/all in FP32 -- on synthetic
  * input of the given layout: nsys systems, system s holding spheres
  * [offsets[s], offsets[s+1]) (host array of nsys + 1 increasing ints, offsets[0] = 0;
  * nsys = 1 describes one suspension, nsys > 1 a gbi_batch_solve batch).  Spheres sit
@@ -313,7 +314,7 @@ gbi_status gbi_mlp_train(gbi_ctx* ctx, int N, const double* R, const double* p, 
  * times (reps = 0 selects 5) between CUDA events on the context's stream.  The fastest
  * WPT is kept in the context for every later pass of the same truncation, pass,
  * precision, batching and floor(log2(total spheres)).  chosen (host, may be NULL)
- * receives the 4 choices in the order above.  Allocates and frees its own device
+ * receives the 6 choices in the order above.  Allocates and frees its own device
  * buffers and synchronizes the stream (not capturable).
  * gbi_set_wpt forces one WPT for every later pass (0 = back to tuned/default).
  * gbi_pass_wpt returns the WPT a pass with these parameters would use (0 for the

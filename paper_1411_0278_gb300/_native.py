@@ -312,9 +312,10 @@ class Context:
 
     def tune(self, trunc, offsets, reps=0):
         """gbi_tune: time each warps-per-target choice of the pair passes on synthetic
-        input with the sphere layout ``offsets`` (nsys + 1 ints); returns the 4 choices."""
+        input with the sphere layout ``offsets`` (nsys + 1 ints); returns the 6 choices
+        (H/H FP32, H/H double-float, H/L and L/all double-float, H/L and L/all FP32)."""
         off = (ctypes.c_int * len(offsets))(*[int(v) for v in offsets])
-        out = (ctypes.c_int * 4)()
+        out = (ctypes.c_int * 6)()
         self._check(lib().gbi_tune(self._h, int(trunc), len(offsets) - 1, off, int(reps), out), "gbi_tune")
         return list(out)
 

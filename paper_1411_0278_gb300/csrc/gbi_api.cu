@@ -83,6 +83,8 @@ __global__ void k_tune_fill(int Ntot, int nsys, const int* __restrict__ off, int
   for (int q = 0; q < D; ++q) x[(size_t)q * Ntot + i] = 1e-3;
 }
 
+constexpr int kTunedPasses = 6;
+
 struct TuneBufs {
   void* p[7] = {};
   ~TuneBufs() {
@@ -119,9 +121,12 @@ gbi_status tune_impl(gbi_ctx* ctx, int trunc, int nsys, const int* offsets, int 
   struct Pass {
     int rows, cols, precision;
   };
-  const Pass passes[4] = {{SET_H, SET_H, 1}, {SET_H, SET_H, 2}, {SET_H, SET_L, 2}, {SET_L, SET_ALL, 2}};
+  // the FP32 and double-float passes of the mixed-precision solves (the right-hand-side
+  // and output passes run in FP32 for precision 3, in double-float for precision 2)
+  const Pass passes[kTunedPasses] = {{SET_H, SET_H, 1}, {SET_H, SET_H, 2}, {SET_H, SET_L, 2},
+                                     {SET_L, SET_ALL, 2}, {SET_H, SET_L, 1}, {SET_L, SET_ALL, 1}};
   gbi_status st = GBI_OK;
-  for (int k = 0; k < 4 && st == GBI_OK; ++k) {
+  for (int k = 0; k < kTunedPasses && st == GBI_OK; ++k) {
     const Pass& ps = passes[k];
     PairArgs pa;
     std::memset(&pa, 0, sizeof(pa));

@@ -70,6 +70,12 @@ struct DSolve {
 };
 
 
+// ordered pairs of system s
+__device__ __forceinline__ long long sys_pairs(const int* __restrict__ off, int s) {
+  const long long n = off[s + 1] - off[s];
+  return n * (n - 1);
+}
+
 // Row chunks per system of the Arnoldi reductions: a few systems get one block per
 // component row (so that a single suspension still spreads over many SMs), large
 // batches one block per system.
@@ -621,15 +627,7 @@ __global__ void __launch_bounds__(256) bk_step_fused(double* V, size_t n, double
 // In the solve graph (d set) `first` comes from the device record and the Arnoldi
 // loop's condition is reset to 1, so that its body runs at least once, as it does when
 // the cycle graph is launched.
-__global__ void bk_init_cycle(GPtr p, int first, const DSolve* d = nullptr,
-                              cudaGraphConditionalHandle ha = 0) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (d != nullptr) first = d->first;
-  if (s == 0) {
-    *p.nact = 0;
-    if (d != nullptr) cudaGraphSetConditional(ha, 1u);
-  }
-  if (s >= p.S) return;
+__device__ void init_cycle_sys(const GPtr& p, int s, int first) {
   GDev* st = p.st + s;
   const int m = p.m;
   if (first) {
@@ -655,6 +653,12 @@ __global__ void bk_init_cycle(GPtr p, int first, const DSolve* d = nullptr,
   st->inv_hn = beta > 0 ? 1.0 / beta : 0.0;
 }
 
+__global__ void bk_init_cycle(GPtr p, int first) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s == 0) *p.nact = 0;
+  if (s < p.S) init_cycle_sys(p, s, first);
+}
+
 __global__ void bk_scale0(double* V0, int Ntot, const int* __restrict__ sys, const GDev* __restrict__ st,
                           SrcOut src) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -667,24 +671,77 @@ __global__ void bk_scale0(double* V0, int Ntot, const int* __restrict__ sys, con
   write_src(src, Ntot, gridDim.y, blockIdx.y, p, v);
 }
 
-// y_s = H_s^-1 g_s on the kdim leading rows (column-oriented back substitution)
-__global__ void bk_solve_y(GPtr p) {
+// End of a GMRES cycle in the solve graph, once every system's cycle is over: count the
+// cycle's pair passes (the V_0 pass when it ran, the Arnoldi steps each system took) and
+// keep the restart loop going while some system needs another cycle.  One block.
+__device__ void cycle_end_all(const GPtr& p, const int* __restrict__ off, DSolve* d, cudaGraphConditionalHandle hr) {
+  __shared__ unsigned long long sp;
+  __shared__ int slive;
+  if (threadIdx.x == 0) {
+    sp = 0ull;
+    slive = 0;
+  }
+  __syncthreads();
+  const int v0_ran = d->notfirst;
+  unsigned long long c = 0;
+  int live = 0, any = 0;
+  for (int s = threadIdx.x; s < p.S; s += blockDim.x) {
+    GDev* st = p.st + s;
+    const unsigned long long np = (unsigned long long)sys_pairs(off, s);
+    const int iters = __ldcg(&st->iters);
+    if (v0_ran && st->enabled) c += np;
+    const int dd = iters - st->it0;
+    st->it0 = iters;
+    c += (unsigned long long)dd * np;
+    live = max(live, dd);
+    if (st->enabled && st->kdim > 0 && !st->converged && !st->breakdown && iters < st->max_iter) any = 1;
+  }
+  atomicAdd(&sp, c);
+  atomicMax(&slive, live);
+  any = __syncthreads_or(any);
+  if (threadIdx.x == 0) {
+    d->pairs += (long long)sp;
+    d->mv32 += slive + (v0_ran ? 1 : 0);
+    d->cycles += 1;
+    d->first = 0;
+    d->notfirst = 1;
+    cudaGraphSetConditional(hr, any ? 1u : 0u);
+  }
+}
+
+// y_s = H_s^-1 g_s on the kdim leading rows (column-oriented back substitution).  In the
+// solve graph (d set) the last system's block (counted in cnt[S]) then ends the cycle
+// (cycle_end_all).
+__global__ void bk_solve_y(GPtr p, DSolve* d = nullptr, const int* __restrict__ off = nullptr,
+                           cudaGraphConditionalHandle hr = 0) {
   const int s = blockIdx.x;
   const GDev* st = p.st + s;
   const int k = st->kdim, m = p.m;
-  if (k == 0) return;
-  const double* H = p.H + (size_t)s * (m + 1) * m;
-  const size_t o1 = (size_t)s * (m + 1);
-  __shared__ double rhs[kGmMaxM], yv[kGmMaxM];
-  for (int i = threadIdx.x; i < k; i += blockDim.x) rhs[i] = p.g[o1 + i];
-  __syncthreads();
-  for (int i = k - 1; i >= 0; --i) {
-    if (threadIdx.x == 0) yv[i] = rhs[i] / H[(size_t)i * m + i];
+  if (k > 0) {
+    const double* H = p.H + (size_t)s * (m + 1) * m;
+    const size_t o1 = (size_t)s * (m + 1);
+    __shared__ double rhs[kGmMaxM], yv[kGmMaxM];
+    for (int i = threadIdx.x; i < k; i += blockDim.x) rhs[i] = p.g[o1 + i];
     __syncthreads();
-    for (int r = threadIdx.x; r < i; r += blockDim.x) rhs[r] -= H[(size_t)r * m + i] * yv[i];
-    __syncthreads();
+    for (int i = k - 1; i >= 0; --i) {
+      if (threadIdx.x == 0) yv[i] = rhs[i] / H[(size_t)i * m + i];
+      __syncthreads();
+      for (int r = threadIdx.x; r < i; r += blockDim.x) rhs[r] -= H[(size_t)r * m + i] * yv[i];
+      __syncthreads();
+    }
+    for (int i = threadIdx.x; i < k; i += blockDim.x) p.y[o1 + i] = yv[i];
   }
-  for (int i = threadIdx.x; i < k; i += blockDim.x) p.y[o1 + i] = yv[i];
+  if (d == nullptr) return;
+  __shared__ int s_last;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(p.cnt + p.S, 1u) == (unsigned int)p.S - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (threadIdx.x == 0) p.cnt[p.S] = 0u;
+  cycle_end_all(p, off, d, hr);
 }
 
 // u += minv * sum_{i < kdim_s} y_s[i] V_i  (systems whose cycle ran)
@@ -703,9 +760,7 @@ __global__ void bk_update(const double* __restrict__ V, size_t n, int Ntot, cons
 }
 
 // refinement bookkeeping: mode 0 stores |b_s| (from nrm), mode 1 sets rel and enabled
-__global__ void bk_refine(GPtr p, int mode, double rtol) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= p.S) return;
+__device__ void refine_sys(const GPtr& p, int s, int mode, double rtol) {
   GDev* st = p.st + s;
   const double v = sqrt(fmax(0.0, p.nrm[s]));
   if (mode == 0) {
@@ -715,6 +770,103 @@ __global__ void bk_refine(GPtr p, int mode, double rtol) {
   } else if (st->enabled) {
     st->rel = st->nb > 0 ? v / st->nb : 0.0;
     st->enabled = st->rel > rtol ? 1 : 0;
+  }
+}
+
+__global__ void bk_refine(GPtr p, int mode, double rtol) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < p.S) refine_sys(p, s, mode, rtol);
+}
+
+// What follows the norms of bk_norm_then, per system (see there).
+enum NormFollow : int { kFollowNone = 0, kFollowCycle = 1, kFollowRefine0 = 2, kFollowRefine1 = 3, kFollowSweep = 4 };
+
+struct NormCtl {
+  int follow;                        // NormFollow
+  int first;                         // kFollowCycle: first cycle of the solve (when d is null)
+  double rtol;                       // refinement tolerance
+  DSolve* d;                         // solve graph record, or null
+  cudaGraphConditionalHandle ha;     // kFollowCycle in the graph: the Arnoldi loop
+  cudaGraphConditionalHandle hsw;    // kFollowSweep: the sweep loop and the inner-solve IF
+  cudaGraphConditionalHandle hif;
+  int max_refine, max_iter;
+};
+
+// |x_s|^2 per system with the partials and the summation order of bk_norm_part and
+// bk_norm_sum, followed in the same kernel by what uses it: every block (s, c) counts
+// itself in cnt[s] once its partial is stored, and the last one of system s forms nrm[s]
+// and runs the follow-up of s -- the start of a GMRES cycle (bk_init_cycle), the
+// refinement bookkeeping (bk_refine mode 0 or 1), or, in the solve graph, the
+// bookkeeping of a sweep: bk_refine mode 1, the residual pass's counters and, in the last
+// system to finish (counted in cnt[S]), the decision to run the sweep's inner solve.
+// All blocks of s read the state they depend on before counting, so none sees the
+// follow-up's writes.  The counters are zero between launches.
+__global__ void __launch_bounds__(256) bk_norm_then(const double* __restrict__ x, int Ntot, int h,
+                                                    const int* __restrict__ off, GPtr p, int mode, NormCtl nc) {
+  const int s = blockIdx.x, c = blockIdx.y, CH = p.CH;
+  if (nc.follow == kFollowCycle && s == 0 && c == 0 && threadIdx.x == 0) {
+    *p.nact = 0;
+    if (nc.d != nullptr) cudaGraphSetConditional(nc.ha, 1u);
+  }
+  const GDev* st = p.st + s;
+  const bool want = norm_wanted(*st, mode);
+  const int enabled0 = st->enabled;
+  if (want) {
+    const int lo = off[s], hi = off[s + 1];
+    const int q0 = c * h / CH, q1 = (c + 1) * h / CH;
+    double acc = 0.0;
+    for (int q = q0; q < q1; ++q) {
+      const size_t b = (size_t)q * Ntot;
+      for (int t = lo + threadIdx.x; t < hi; t += blockDim.x) acc += x[b + t] * x[b + t];
+    }
+    const double t = block_sum_256(acc);
+    if (threadIdx.x == 0) p.nrmp[(size_t)s * CH + c] = t;
+  }
+  __shared__ int s_last, s_glob;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(p.cnt + s, 1u) == (unsigned int)CH - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (threadIdx.x == 0) {
+    p.cnt[s] = 0u;
+    if (want) {
+      double acc = 0.0;
+      for (int k = 0; k < CH; ++k) acc += __ldcg(p.nrmp + (size_t)s * CH + k);
+      p.nrm[s] = acc;
+    }
+    switch (nc.follow) {
+      case kFollowCycle: init_cycle_sys(p, s, nc.d != nullptr ? nc.d->first : nc.first); break;
+      case kFollowRefine0: refine_sys(p, s, 0, nc.rtol); break;
+      case kFollowRefine1:
+      case kFollowSweep: refine_sys(p, s, 1, nc.rtol); break;
+      default: break;
+    }
+    s_glob = 0;
+    if (nc.follow == kFollowSweep) {
+      if (enabled0) atomicAdd(reinterpret_cast<unsigned long long*>(&nc.d->pairs), (unsigned long long)sys_pairs(off, s));
+      __threadfence();
+      s_glob = atomicAdd(p.cnt + p.S, 1u) == (unsigned int)p.S - 1;
+    }
+  }
+  __syncthreads();
+  if (!s_glob) return;
+  // the sweep decision, once every system's refinement flag is final
+  __threadfence();
+  int any = 0;
+  for (int q = threadIdx.x; q < p.S; q += blockDim.x) any |= __ldcg(&p.st[q].enabled);
+  any = __syncthreads_or(any);
+  if (threadIdx.x == 0) {
+    p.cnt[p.S] = 0u;
+    DSolve* d = nc.d;
+    d->mv64 += 1;
+    d->refinements += 1;
+    const int go = any && d->refinements < nc.max_refine && d->iters < nc.max_iter;
+    d->ifs += go;
+    cudaGraphSetConditional(nc.hif, go ? 1u : 0u);
+    cudaGraphSetConditional(nc.hsw, go ? 1u : 0u);
   }
 }
 
@@ -941,11 +1093,14 @@ gbi_status gmres_batch(gbi_ctx* ctx, const Setup& s, const Batch& B, int precisi
           if (hst[q].enabled) info->pair_interactions += (long long)(B.h_off[q + 1] - B.h_off[q]) * (B.h_off[q + 1] - B.h_off[q] - 1);
       }
     }
-    bk_norm_part<<<dim3(S, gp.CH), 256, 0, ctx->stream>>>(Vb, Ntot, h, B.off, gp.st, 1, gp.CH, gp.nrmp);
-    bk_norm_sum<<<(S + 127) / 128, 128, 0, ctx->stream>>>(gp.nrmp, gp.st, S, 1, gp.CH, gp.nrm);
-    bk_init_cycle<<<sblk, 128, 0, ctx->stream>>>(gp, first ? 1 : 0);
+    {
+      NormCtl nc{};
+      nc.follow = kFollowCycle;
+      nc.first = first ? 1 : 0;
+      bk_norm_then<<<dim3(S, gp.CH), 256, 0, ctx->stream>>>(Vb, Ntot, h, B.off, gp, 1, nc);
+    }
     bk_scale0<<<g2, 256, 0, ctx->stream>>>(Vb, Ntot, B.sys, gp.st, src_out(s, precision, xsrc));
-    ctx->launches += 4;
+    ctx->launches += 2;
     GBI_CHECK(cudaGetLastError());
     if (first)
       for (int q = 0; q < S; ++q) before[q] = 0;      // bk_init_cycle restarts the counters
@@ -1026,11 +1181,6 @@ gbi_status gmres_batch(gbi_ctx* ctx, const Setup& s, const Batch& B, int precisi
 // read back once.  The kernels and their order are those of the host-driven sequence, so
 // the results are the same bit for bit.
 
-// one-block reductions over the systems
-__device__ __forceinline__ long long sys_pairs(const int* __restrict__ off, int s) {
-  const long long n = off[s + 1] - off[s];
-  return n * (n - 1);
-}
 
 __global__ void gk_copy(double* __restrict__ dst, const double* __restrict__ src, size_t n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
@@ -1057,73 +1207,6 @@ __global__ void gk_sweep_start(GPtr p, cudaGraphConditionalHandle hsw) {
   for (int s = threadIdx.x; s < p.S; s += blockDim.x) any |= p.st[s].enabled;
   any = __syncthreads_or(any);
   if (threadIdx.x == 0) cudaGraphSetConditional(hsw, any ? 1u : 0u);
-}
-
-// a residual pass over the enabled systems has run
-__global__ void gk_count_pass(GPtr p, const int* __restrict__ off, DSolve* d) {
-  __shared__ unsigned long long sp;
-  if (threadIdx.x == 0) sp = 0ull;
-  __syncthreads();
-  unsigned long long c = 0;
-  for (int s = threadIdx.x; s < p.S; s += blockDim.x)
-    if (p.st[s].enabled) c += (unsigned long long)sys_pairs(off, s);
-  atomicAdd(&sp, c);
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    d->mv64 += 1;
-    d->pairs += (long long)sp;
-  }
-}
-
-// after the residual of sweep k >= 1: run its inner solve (and come back for sweep k + 1)
-// while some system needs a correction and neither cap is reached
-__global__ void gk_sweep_decide(GPtr p, DSolve* d, int max_refine, int max_iter, cudaGraphConditionalHandle hsw,
-                                cudaGraphConditionalHandle hif) {
-  int any = 0;
-  for (int s = threadIdx.x; s < p.S; s += blockDim.x) any |= p.st[s].enabled;
-  any = __syncthreads_or(any);
-  if (threadIdx.x == 0) {
-    d->refinements += 1;
-    const int go = any && d->refinements < max_refine && d->iters < max_iter;
-    d->ifs += go;
-    cudaGraphSetConditional(hif, go ? 1u : 0u);
-    cudaGraphSetConditional(hsw, go ? 1u : 0u);
-  }
-}
-
-// end of a GMRES cycle: count its pair passes, decide the restart
-__global__ void gk_cycle_end(GPtr p, const int* __restrict__ off, DSolve* d, cudaGraphConditionalHandle hr) {
-  __shared__ unsigned long long sp;
-  __shared__ int slive;
-  if (threadIdx.x == 0) {
-    sp = 0ull;
-    slive = 0;
-  }
-  __syncthreads();
-  const int v0_ran = d->notfirst;
-  unsigned long long c = 0;
-  int live = 0, any = 0;
-  for (int s = threadIdx.x; s < p.S; s += blockDim.x) {
-    GDev* st = p.st + s;
-    const unsigned long long np = (unsigned long long)sys_pairs(off, s);
-    if (v0_ran && st->enabled) c += np;
-    const int dd = st->iters - st->it0;
-    st->it0 = st->iters;
-    c += (unsigned long long)dd * np;
-    live = max(live, dd);
-    if (st->enabled && st->kdim > 0 && !st->converged && !st->breakdown && st->iters < st->max_iter) any = 1;
-  }
-  atomicAdd(&sp, c);
-  atomicMax(&slive, live);
-  any = __syncthreads_or(any);
-  if (threadIdx.x == 0) {
-    d->pairs += (long long)sp;
-    d->mv32 += slive + (v0_ran ? 1 : 0);
-    d->cycles += 1;
-    d->first = 0;
-    d->notfirst = 1;
-    cudaGraphSetConditional(hr, any ? 1u : 0u);
-  }
 }
 
 // end of an inner solve: its iterations are the most any system took
@@ -1262,19 +1345,22 @@ gbi_status emit_gmres(GraphBuild& gb, const Setup& s, const Batch& B, const GPtr
     pr.sys_flag_stride = int(sizeof(GDev) / sizeof(int));
     pr.active = &d->notfirst;   // u is zero in the first cycle
     GBI_CHECK(run_pairs(ctx, s.trunc, SET_H, SET_H, 1, pr));
-    bk_norm_part<<<dim3(S, gp.CH), 256, 0, ctx->stream>>>(Vb, Ntot, h, B.off, gp.st, 1, gp.CH, gp.nrmp);
-    bk_norm_sum<<<(S + 127) / 128, 128, 0, ctx->stream>>>(gp.nrmp, gp.st, S, 1, gp.CH, gp.nrm);
     const cudaGraphConditionalHandle ha = gb.handle();
-    bk_init_cycle<<<sblk, 128, 0, ctx->stream>>>(gp, 0, d, ha);
+    {
+      NormCtl nc{};
+      nc.follow = kFollowCycle;
+      nc.d = d;
+      nc.ha = ha;
+      bk_norm_then<<<dim3(S, gp.CH), 256, 0, ctx->stream>>>(Vb, Ntot, h, B.off, gp, 1, nc);
+    }
     bk_scale0<<<g2, 256, 0, ctx->stream>>>(Vb, Ntot, B.sys, gp.st, src_out(s, 1, xsrc));
-    ctx->launches += 4;
+    ctx->launches += 2;
     GBI_TRY(gb.body(gb.node(ha, cudaGraphCondTypeWhile), kBodyStep, [&]() -> gbi_status {
       return launch_chunk(ctx, s, B, 1, gp, m, Vb, w, xsrc, kArnoldiUnroll, false, LoopCtl{gp.nact, ha, 1, &d->steps});
     }));
-    bk_solve_y<<<S, 128, 0, ctx->stream>>>(gp);
+    bk_solve_y<<<S, 128, 0, ctx->stream>>>(gp, d, B.off, hr);
     bk_update<<<g2, 256, 0, ctx->stream>>>(Vb, n, Ntot, B.sys, gp, s.minv, u);
-    gk_cycle_end<<<1, 256, 0, ctx->stream>>>(gp, B.off, d, hr);
-    ctx->launches += 3;
+    ctx->launches += 2;
     GBI_CHECK(cudaGetLastError());
     return GBI_OK;
   }));
@@ -1301,7 +1387,6 @@ gbi_status solve_core(gbi_ctx* ctx, const gbi_params* prm, const Batch& B, const
   const int D = s.D, h = s.h;
   const size_t nh = (size_t)N * h;
   const dim3 g2((N + 255) / 256, h);
-  const int sblk = (S + 127) / 128;
   // arithmetic of the refinement residual (FP64, or double-float for precision 2 and 3)
   // and of the right-hand-side and output passes (the same, or FP32 for precision 3)
   const int hp = prm->precision >= 2 ? 2 : 0;
@@ -1434,12 +1519,16 @@ gbi_status solve_core(gbi_ctx* ctx, const gbi_params* prm, const Batch& B, const
           if (cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
             st = [&]() -> gbi_status {
               GBI_CHECK(cudaMemsetAsync(d, 0, sizeof(DSolve), ctx->stream));
+              GBI_CHECK(cudaMemsetAsync(gp.cnt, 0, sizeof(unsigned int) * (S + 2), ctx->stream));
               GBI_TRY(rhs_pass());
               GBI_CHECK(cudaMemsetAsync(xQH, 0, sizeof(double) * nh, ctx->stream));
-              bk_norm_part<<<dim3(S, gp.CH), 256, 0, ctx->stream>>>(b, N, h, B.off, gp.st, 2, gp.CH, gp.nrmp);
-              bk_norm_sum<<<(S + 127) / 128, 128, 0, ctx->stream>>>(gp.nrmp, gp.st, S, 2, gp.CH, gp.nrm);
-              bk_refine<<<sblk, 128, 0, ctx->stream>>>(gp, 0, rtol);
-              ctx->launches += 3;
+              {
+                NormCtl nc{};
+                nc.follow = kFollowRefine0;
+                nc.rtol = rtol;
+                bk_norm_then<<<dim3(S, gp.CH), 256, 0, ctx->stream>>>(b, N, h, B.off, gp, 2, nc);
+                ++ctx->launches;
+              }
               if (prm->min_sep > 0 && pairs_all > 0) {
                 gk_overlap<<<1, 256, 0, ctx->stream>>>(gp, P<unsigned int>(ctx->minr2), s.a, prm->min_sep, d);
                 ++ctx->launches;
@@ -1459,13 +1548,19 @@ gbi_status solve_core(gbi_ctx* ctx, const gbi_params* prm, const Batch& B, const
                 ++ctx->launches;
                 PairArgs p = batched(pair_args(s, xQH, r, -1.0, 1.0, 1, s.ones, 6), &gp.st[0].enabled);
                 GBI_CHECK(run_pairs(ctx, s.trunc, SET_H, SET_H, hp, p));
-                gk_count_pass<<<1, 256, 0, ctx->stream>>>(gp, B.off, d);
-                bk_norm_part<<<dim3(S, gp.CH), 256, 0, ctx->stream>>>(r, N, h, B.off, gp.st, 1, gp.CH, gp.nrmp);
-                bk_norm_sum<<<(S + 127) / 128, 128, 0, ctx->stream>>>(gp.nrmp, gp.st, S, 1, gp.CH, gp.nrm);
-                bk_refine<<<sblk, 128, 0, ctx->stream>>>(gp, 1, rtol);
                 const cudaGraphConditionalHandle hif = gb.handle();
-                gk_sweep_decide<<<1, 256, 0, ctx->stream>>>(gp, d, max_refine, max_iter, hsw, hif);
-                ctx->launches += 5;
+                {
+                  NormCtl nc{};
+                  nc.follow = kFollowSweep;
+                  nc.rtol = rtol;
+                  nc.d = d;
+                  nc.hsw = hsw;
+                  nc.hif = hif;
+                  nc.max_refine = max_refine;
+                  nc.max_iter = max_iter;
+                  bk_norm_then<<<dim3(S, gp.CH), 256, 0, ctx->stream>>>(r, N, h, B.off, gp, 1, nc);
+                  ++ctx->launches;
+                }
                 GBI_CHECK(cudaGetLastError());
                 return gb.body(gb.node(hif, cudaGraphCondTypeIf), kBodyIf, [&]() -> gbi_status {
                   gk_zero<<<grid1(nh), 256, 0, ctx->stream>>>(dl, nh);
@@ -1558,10 +1653,15 @@ gbi_status solve_core(gbi_ctx* ctx, const gbi_params* prm, const Batch& B, const
     GBI_CHECK(cudaMemsetAsync(xQH, 0, sizeof(double) * nh, ctx->stream));
   }
   // |b_s| per system
-  bk_norm_part<<<dim3(S, gp.CH), 256, 0, ctx->stream>>>(b, N, h, B.off, gp.st, 2, gp.CH, gp.nrmp);
-  bk_norm_sum<<<(S + 127) / 128, 128, 0, ctx->stream>>>(gp.nrmp, gp.st, S, 2, gp.CH, gp.nrm);
-  bk_refine<<<sblk, 128, 0, ctx->stream>>>(gp, 0, rtol);
-  ctx->launches += 3;
+  GBI_CHECK(cudaMemsetAsync(gp.cnt, 0, sizeof(unsigned int) * (S + 2), ctx->stream));
+  auto norm_refine = [&](const double* x, int mode, int follow) {
+    NormCtl nc{};
+    nc.follow = follow;
+    nc.rtol = rtol;
+    bk_norm_then<<<dim3(S, gp.CH), 256, 0, ctx->stream>>>(x, N, h, B.off, gp, mode, nc);
+    ++ctx->launches;
+  };
+  norm_refine(b, 2, kFollowRefine0);
   auto read_state = [&]() -> gbi_status {
     GBI_CHECK(cudaMemcpyAsync(hst, gp.st, sizeof(GDev) * S, cudaMemcpyDeviceToHost, ctx->stream));
     GBI_CHECK(cudaStreamSynchronize(ctx->stream));
@@ -1589,10 +1689,7 @@ gbi_status solve_core(gbi_ctx* ctx, const gbi_params* prm, const Batch& B, const
     GBI_CHECK(run_pairs(ctx, s.trunc, SET_H, SET_H, 0, p));
     inf->matvecs_f64 += 1;
     inf->pair_interactions += pairs_enabled();
-    bk_norm_part<<<dim3(S, gp.CH), 256, 0, ctx->stream>>>(r, N, h, B.off, gp.st, 1, gp.CH, gp.nrmp);
-    bk_norm_sum<<<(S + 127) / 128, 128, 0, ctx->stream>>>(gp.nrmp, gp.st, S, 1, gp.CH, gp.nrm);
-    bk_refine<<<sblk, 128, 0, ctx->stream>>>(gp, 1, rtol);
-    ctx->launches += 3;
+    norm_refine(r, 1, kFollowRefine1);
     GBI_TRY(read_state());
   } else {
     // mixed precision: r = b - A_hp x; A_32 d = r (FP32 pair sums, FP64 Arnoldi); x += d
@@ -1603,10 +1700,7 @@ gbi_status solve_core(gbi_ctx* ctx, const gbi_params* prm, const Batch& B, const
         GBI_CHECK(run_pairs(ctx, s.trunc, SET_H, SET_H, hp, p));
         inf->matvecs_f64 += 1;
         inf->pair_interactions += pairs_enabled();
-        bk_norm_part<<<dim3(S, gp.CH), 256, 0, ctx->stream>>>(r, N, h, B.off, gp.st, 1, gp.CH, gp.nrmp);
-        bk_norm_sum<<<(S + 127) / 128, 128, 0, ctx->stream>>>(gp.nrmp, gp.st, S, 1, gp.CH, gp.nrm);
-        bk_refine<<<sblk, 128, 0, ctx->stream>>>(gp, 1, rtol);
-        ctx->launches += 3;
+        norm_refine(r, 1, kFollowRefine1);
       }
       if (sweep > 0) inf->refinements += 1;
       if (sweep >= max_refine || inf->iters >= max_iter) {

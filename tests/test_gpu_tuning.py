@@ -100,11 +100,17 @@ def test_tune_picks_valid_choices_and_keeps_results(ctx, gbi):
     V0, O0, _, i0, _ = ctx.solve(prm, R, *args)
     V0, O0 = V0.cpu().numpy(), O0.cpu().numpy()
     chosen = ctx.tune(trunc, [0, N], reps=2)
-    assert len(chosen) == 4
-    assert chosen[0] in (2, 4, 8, 16)
-    assert all(w in (2, 4, 8) for w in chosen[1:])
+    assert len(chosen) == 6
+    fp32_cap = 8 if trunc == 4 else 16
+    assert chosen[0] in (2, 4, 8, 16) and chosen[0] <= fp32_cap
+    assert all(w in (2, 4, 8) for w in chosen[1:4])
+    assert all(w in (2, 4, 8, 16) and w <= fp32_cap for w in chosen[4:])
     assert ctx.pass_wpt(trunc, 2, 2, 1, N) == chosen[0]
     assert ctx.pass_wpt(trunc, 2, 2, 2, N) == chosen[1]
+    assert ctx.pass_wpt(trunc, 2, 1, 2, N) == chosen[2]
+    assert ctx.pass_wpt(trunc, 1, 0, 2, N) == chosen[3]
+    assert ctx.pass_wpt(trunc, 2, 1, 1, N) == chosen[4]
+    assert ctx.pass_wpt(trunc, 1, 0, 1, N) == chosen[5]
     assert ctx.pass_wpt(trunc, 2, 2, 0, N) == 0
     V1, O1, _, i1, _ = ctx.solve(prm, R, *args)
     assert i1.rel_residual <= 1e-10
@@ -118,7 +124,7 @@ def test_tune_batched_layout(ctx, gbi):
     for n in sizes:
         offs.append(offs[-1] + n)
     chosen = ctx.tune(2, offs, reps=1)
-    assert len(chosen) == 4 and all(w in (2, 4, 8, 16) for w in chosen)
+    assert len(chosen) == 6 and all(w in (2, 4, 8, 16) for w in chosen)
     assert ctx.pass_wpt(2, 2, 2, 1, offs[-1], batched=True) == chosen[0]
 
 
