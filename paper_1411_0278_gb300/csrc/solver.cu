@@ -38,12 +38,26 @@ struct GDev {
   double bnorm, tol, res, beta, inv_hn;
   double nb;      // |b_s| (reference of the refinement residual)
   double rel;     // |b_s - A q_s| / |b_s|
-  double pad2;
+  double inv_bnorm, inv_nb;   // 1 / bnorm, 1 / nb (0 for a zero norm)
 };
+
+// sqrt(q) and 1 / sqrt(q) for q >= 0 (0 and 0 for q <= 0) from one reciprocal square root:
+// on GB300 a dependent FP64 sqrt or division costs ~650 cycles, rsqrt ~430 and an FMA 64,
+// and the Arnoldi step's scalar work runs on one thread between grid-wide phases
+__device__ __forceinline__ void root_and_inverse(double q, double& r, double& inv) {
+  if (q > 0.0) {
+    inv = rsqrt(q);
+    r = q * inv;
+  } else {
+    inv = 0.0;
+    r = 0.0;
+  }
+}
 
 struct GPtr {     // per-system views into the gstate buffer
   GDev* st;
   double *H, *cs, *sn, *g, *y, *nrm;
+  double* cf;                 // Gram-Schmidt coefficients c_i of the current step (one round)
   double *h1p, *h2p, *nrmp;   // per-chunk partial sums of the dot products and the norm
   int* nact;                  // systems still active after the current Arnoldi step
   unsigned int* bar;          // grid barrier of the fused single-system step: count, generation, error
@@ -82,7 +96,7 @@ __device__ __forceinline__ long long sys_pairs(const int* __restrict__ off, int 
 int arnoldi_chunks(int S, int h) { return S >= 64 ? 1 : h; }
 
 size_t gstate_doubles(int m, int S, int CH) {
-  return (size_t)S * (sizeof(GDev) / sizeof(double) + 1) + (size_t)S * ((size_t)(m + 1) * m + 5 * (size_t)(m + 1) + 1) +
+  return (size_t)S * (sizeof(GDev) / sizeof(double) + 1) + (size_t)S * ((size_t)(m + 1) * m + 6 * (size_t)(m + 1) + 1) +
          (size_t)S * CH * (2 * (size_t)(m + 1) + 1) + (size_t)kFusedBlocks * (2 * (size_t)(m + 1) + 1) + 24 +
          ((size_t)S + 1) / 2 + 1;
 }
@@ -99,6 +113,7 @@ GPtr gptrs(void* base, int m, int S, int CH) {
   p.sn = d; d += (size_t)S * (m + 1);
   p.g = d; d += (size_t)S * (m + 1);
   p.y = d; d += (size_t)S * (m + 1);
+  p.cf = d; d += (size_t)S * (m + 1);
   p.nrm = d; d += (size_t)S;
   p.h1p = d; d += (size_t)S * (m + 1) * CH;
   p.h2p = d; d += (size_t)S * (m + 1) * CH;
@@ -208,16 +223,6 @@ __global__ void bk_norm_part(const double* __restrict__ x, int Ntot, int h, cons
   if (threadIdx.x == 0) part[(size_t)s * CH + c] = t;
 }
 
-// out[s] = sum of the chunk partials in order
-__global__ void bk_norm_sum(const double* __restrict__ part, const GDev* __restrict__ st, int S, int mode, int CH,
-                            double* __restrict__ out) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= S || !norm_wanted(st[s], mode)) return;
-  double acc = 0.0;
-  for (int c = 0; c < CH; ++c) acc += part[(size_t)s * CH + c];
-  out[s] = acc;
-}
-
 // Hessenberg column j_s, Givens rotations, residual estimate and stopping test of one
 // system per block (parallel loads to shared memory, one thread sweeps the rotations).
 constexpr int kGmMaxM = 128;
@@ -225,43 +230,60 @@ constexpr int kGmMaxM = 128;
 // in shared memory, overwritten), new norm hn: apply the previous rotations, form the
 // new one, update g, the residual estimate and the stopping test, store the column.
 // Called by one block per system; thread 0 does the serial part.
-__device__ void givens_step(const GPtr& p, int s, int j, double hn, double* col, double* scs, double* ssn) {
+__device__ void givens_step(const GPtr& p, int s, int j, double hn, double inv_hn, double* col, double* scs,
+                            double* ssn) {
   GDev* st = p.st + s;
   const int m = p.m;
   const size_t o1 = (size_t)s * (m + 1);
   const int tid = threadIdx.x;
+  // every value the serial part reads, loaded by many threads at once: a chain of
+  // dependent global loads on one thread would cost an L2 round trip per link
+  __shared__ double s_gj, s_ibnorm, s_tol;
+  __shared__ int s_iters, s_maxit;
   for (int i = tid; i < j; i += blockDim.x) {
     scs[i] = p.cs[o1 + i];
     ssn[i] = p.sn[o1 + i];
   }
+  if (tid == 32) s_gj = p.g[o1 + j];   // blocks here have 128 or 256 threads
+  if (tid == 33) s_ibnorm = st->inv_bnorm;
+  if (tid == 34) s_tol = st->tol;
+  if (tid == 35) s_iters = st->iters;
+  if (tid == 36) s_maxit = st->max_iter;
   __syncthreads();
   if (tid == 0) {
+    // the previous rotations, the carried entry in a register
+    double carry = col[0];
     for (int i = 0; i < j; ++i) {
-      const double t1 = col[i], t2 = col[i + 1];
-      col[i] = scs[i] * t1 + ssn[i] * t2;
-      col[i + 1] = -ssn[i] * t1 + scs[i] * t2;
+      const double t2 = col[i + 1];
+      col[i] = scs[i] * carry + ssn[i] * t2;
+      carry = -ssn[i] * carry + scs[i] * t2;
     }
-    col[j + 1] = hn;
-    const double hjj = col[j], hj1 = hn;
-    const double den = hypot(hjj, hj1);
-    const double c = den > 0 ? hjj / den : 1.0, sg = den > 0 ? hj1 / den : 0.0;
-    p.cs[o1 + j] = c;
-    p.sn[o1 + j] = sg;
+    const double hjj = carry, hj1 = hn;
+    double den, inv;
+    root_and_inverse(hjj * hjj + hj1 * hj1, den, inv);
+    const double c = den > 0 ? hjj * inv : 1.0, sg = den > 0 ? hj1 * inv : 0.0;
     col[j] = den;
     col[j + 1] = 0.0;
-    const double gj = p.g[o1 + j];
-    p.g[o1 + j + 1] = -sg * gj;
+    const double gj = s_gj;
+    const double g1 = -sg * gj;
+    const int iters = s_iters + 1;
+    const double res = fabs(g1) * s_ibnorm;
+    const int conv = res <= s_tol;
+    const int brk = hn <= 1e-300;
+    const bool stop = conv || brk || iters >= s_maxit || j + 1 >= m;
+    p.cs[o1 + j] = c;
+    p.sn[o1 + j] = sg;
+    p.g[o1 + j + 1] = g1;
     p.g[o1 + j] = c * gj;
-    st->iters += 1;
+    st->iters = iters;
     st->kdim = j + 1;
-    st->res = fabs(p.g[o1 + j + 1]) / st->bnorm;
-    st->converged = st->res <= st->tol;
-    st->breakdown = hn <= 1e-300;
-    const bool stop = st->converged || st->breakdown || st->iters >= st->max_iter || j + 1 >= m;
+    st->res = res;
+    st->converged = conv;
+    st->breakdown = brk;
     if (stop) {
       st->active = 0;
     } else {
-      st->inv_hn = 1.0 / hn;
+      st->inv_hn = inv_hn;
       st->j = j + 1;
       atomicAdd(p.nact, 1);
     }
@@ -276,35 +298,45 @@ __device__ void givens_step(const GPtr& p, int s, int j, double hn, double* col,
 // the norm of the twice-orthogonalised vector (nrmp).  Otherwise one round: h1p holds
 // c_i = V_i . w for i <= j and |w|^2 in slot j + 1, and with orthonormal V_i
 // |w - sum c_i V_i|^2 = |w|^2 - sum c_i^2 (clamped at zero).
+// Sum of CH chunk partials by one warp: lane c loads chunks c, c + 32, ... (all loads in
+// flight together) and a fixed shuffle tree adds the lanes.  L2 loads: the partials may
+// come from other blocks of the same kernel.
+__device__ __forceinline__ double warp_chunk_sum(const double* a, int CH) {
+  const int lane = threadIdx.x & 31;
+  double v = 0.0;
+  for (int c = lane; c < CH; c += 32) v += __ldcg(a + c);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
 __device__ void finalize_column(const GPtr& p, int s, int j, int two_pass) {
   __shared__ double col[kGmMaxM + 1], scs[kGmMaxM], ssn[kGmMaxM];
-  __shared__ double s_hn;
+  __shared__ double s_hn, s_ihn;
   const size_t o1 = (size_t)s * (p.m + 1);
   const int top = two_pass ? j : j + 1;
-  for (int i = threadIdx.x; i <= top; i += blockDim.x) {
-    // L2 loads: the partials may come from other blocks of the same kernel
-    const double* a1 = p.h1p + (o1 + i) * p.CH;
-    double c1 = 0.0, c2 = 0.0;
-    for (int c = 0; c < p.CH; ++c) c1 += __ldcg(a1 + c);
-    if (two_pass) {
-      const double* a2 = p.h2p + (o1 + i) * p.CH;
-      for (int c = 0; c < p.CH; ++c) c2 += __ldcg(a2 + c);
-    }
-    col[i] = c1 + c2;
+  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  // one warp per slot
+  for (int i = warp; i <= top; i += nw) {
+    double v = warp_chunk_sum(p.h1p + (o1 + i) * p.CH, p.CH);
+    if (two_pass) v += warp_chunk_sum(p.h2p + (o1 + i) * p.CH, p.CH);
+    if ((threadIdx.x & 31) == 0) col[i] = v;
   }
+  double nrm2 = 0.0;
+  if (two_pass && warp == 0) nrm2 = warp_chunk_sum(p.nrmp + (size_t)s * p.CH, p.CH);
   __syncthreads();
   if (threadIdx.x == 0) {
-    double nrm = 0.0;
-    if (two_pass) {
-      for (int c = 0; c < p.CH; ++c) nrm += __ldcg(p.nrmp + (size_t)s * p.CH + c);
-    } else {
+    double nrm = nrm2;
+    if (!two_pass) {
       nrm = col[j + 1];
       for (int i = 0; i <= j; ++i) nrm -= col[i] * col[i];
     }
-    s_hn = sqrt(fmax(0.0, nrm));
+    root_and_inverse(nrm, s_hn, s_ihn);
   }
+  // the coefficients before the rotations act on them (one-round step: bk_sub_scale)
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) p.cf[o1 + i] = col[i];
   __syncthreads();
-  givens_step(p, s, j, s_hn, col, scs, ssn);
+  givens_step(p, s, j, s_hn, s_ihn, col, scs, ssn);
 }
 
 __global__ void bk_finalize(GPtr p, int two_pass) {
@@ -336,8 +368,17 @@ __global__ void __launch_bounds__(256) bk_dots_fin(const double* __restrict__ V,
       const size_t b = (size_t)q * Ntot;
       for (int t = lo + threadIdx.x; t < hi; t += blockDim.x) acc += v[b + t] * w[b + t];
     }
-    const double tot = block_sum_256(acc);
-    if (threadIdx.x == 0) p.h1p[((size_t)s * (p.m + 1) + i) * CH + c] = tot;
+    // lanes by a shuffle tree, then the warps in order
+    __shared__ double s_w[8];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double tot = s_w[0];
+      for (int k = 1; k < (int)(blockDim.x >> 5); ++k) tot += s_w[k];
+      p.h1p[((size_t)s * (p.m + 1) + i) * CH + c] = tot;
+    }
   }
   __shared__ int s_last;
   if (threadIdx.x == 0) {
@@ -409,12 +450,13 @@ __global__ void bk_scale(double* V, size_t n, const double* __restrict__ w, int 
   write_src(src, Ntot, gridDim.y, blockIdx.y, p, v);
 }
 
-// One-reduction step, after bk_finalize advanced j_s: V_{j_s} = (w - sum_{i < j_s} c_i V_i)
-// / h_{j_s, j_s - 1} with the coefficients summed from the h1p partials (once per block
-// into shared memory when the block's spheres all belong to one system), and its source.
+// One-reduction step, after the Givens step advanced j_s: V_{j_s} = (w - sum_{i < j_s}
+// c_i V_i) / h_{j_s, j_s - 1} with the coefficients cf the Givens step stored (copied
+// once per block into shared memory when the block's spheres all belong to one system),
+// and its source.
 __global__ void bk_sub_scale(double* V, size_t n, const double* __restrict__ w, int Ntot,
-                             const int* __restrict__ sys, const GDev* __restrict__ st, int m, int CH,
-                             const double* __restrict__ part, SrcOut src, LoopCtl lc) {
+                             const int* __restrict__ sys, const GDev* __restrict__ st, int m,
+                             const double* __restrict__ cf, SrcOut src, LoopCtl lc) {
   loop_continue(lc);
   __shared__ double sc[kMaxRestart + 1];
   const int p0 = blockIdx.x * blockDim.x;
@@ -424,12 +466,7 @@ __global__ void bk_sub_scale(double* V, size_t n, const double* __restrict__ w, 
   if (uniform) {
     const GDev& g = st[sb];
     if (!g.active) return;
-    for (int i = threadIdx.x; i < g.j; i += blockDim.x) {
-      const double* q = part + ((size_t)sb * (m + 1) + i) * CH;
-      double acc = 0.0;
-      for (int c = 0; c < CH; ++c) acc += q[c];
-      sc[i] = acc;
-    }
+    for (int i = threadIdx.x; i < g.j; i += blockDim.x) sc[i] = cf[(size_t)sb * (m + 1) + i];
     __syncthreads();
   }
   const int p = p0 + threadIdx.x;
@@ -439,15 +476,9 @@ __global__ void bk_sub_scale(double* V, size_t n, const double* __restrict__ w, 
   if (!g.active) return;
   const size_t t = (size_t)blockIdx.y * Ntot + p;
   double acc = w[t];
+#pragma unroll 8
   for (int i = 0; i < g.j; ++i) {
-    double c;
-    if (uniform) {
-      c = sc[i];
-    } else {
-      const double* q = part + ((size_t)s * (m + 1) + i) * CH;
-      c = 0.0;
-      for (int k = 0; k < CH; ++k) c += q[k];
-    }
+    const double c = uniform ? sc[i] : cf[(size_t)s * (m + 1) + i];
     acc -= c * V[(size_t)i * n + t];
   }
   const double v = acc * g.inv_hn;
@@ -528,7 +559,7 @@ __global__ void __launch_bounds__(256) bk_step_fused(double* V, size_t n, double
                                                      SrcOut so, int two_pass) {
   __shared__ double sh[256];
   __shared__ double c1[kGmMaxM + 1], c2[kGmMaxM + 1], scs[kGmMaxM], ssn[kGmMaxM];
-  __shared__ double s_hn;
+  __shared__ double s_hn, s_ihn;
   __shared__ int s_ok;
   const GDev* st = p.st;
   if (!st->active) return;   // the same decision in every block: nothing writes the state yet
@@ -553,11 +584,11 @@ __global__ void __launch_bounds__(256) bk_step_fused(double* V, size_t n, double
     if (tid == 0) {
       double nrm = c1[j + 1];
       for (int i = 0; i <= j; ++i) nrm -= c1[i] * c1[i];
-      s_hn = sqrt(fmax(0.0, nrm));
+      root_and_inverse(nrm, s_hn, s_ihn);
     }
     __syncthreads();
     const double hn = s_hn;
-    const double inv = hn > 1e-300 ? 1.0 / hn : 0.0;
+    const double inv = hn > 1e-300 ? s_ihn : 0.0;
     for (size_t t = t0 + tid; t < t1; t += blockDim.x) {
       double a = w[t];
       for (int i = 0; i <= j; ++i) a -= c1[i] * V[(size_t)i * n + t];
@@ -566,7 +597,7 @@ __global__ void __launch_bounds__(256) bk_step_fused(double* V, size_t n, double
       const int q = int(t / (size_t)Ntot);
       write_src(so, Ntot, h, q, int(t - (size_t)q * Ntot), v);
     }
-    if (b == 0) givens_step(p, 0, j, hn, c1, scs, ssn);
+    if (b == 0) givens_step(p, 0, j, hn, s_ihn, c1, scs, ssn);
     return;
   }
   // (B) w1 = w - sum c1_i V_i on the slice, then partial V_i . w1
@@ -605,11 +636,11 @@ __global__ void __launch_bounds__(256) bk_step_fused(double* V, size_t n, double
   if (tid == 0) {
     double nrm = 0.0;
     for (int q = 0; q < G; ++q) nrm += partn[q];
-    s_hn = sqrt(fmax(0.0, nrm));
+    root_and_inverse(nrm, s_hn, s_ihn);
   }
   __syncthreads();
   const double hn = s_hn;
-  const double inv = hn > 1e-300 ? 1.0 / hn : 0.0;
+  const double inv = hn > 1e-300 ? s_ihn : 0.0;
   for (size_t t = t0 + tid; t < t1; t += blockDim.x) {
     const double v = w[t] * inv;
     V[(size_t)(j + 1) * n + t] = v;
@@ -619,7 +650,7 @@ __global__ void __launch_bounds__(256) bk_step_fused(double* V, size_t n, double
   if (b == 0) {
     for (int i = tid; i <= j; i += blockDim.x) c1[i] += c2[i];
     __syncthreads();
-    givens_step(p, 0, j, hn, c1, scs, ssn);
+    givens_step(p, 0, j, hn, s_ihn, c1, scs, ssn);
   }
 }
 
@@ -641,16 +672,20 @@ __device__ void init_cycle_sys(const GPtr& p, int s, int first) {
     st->active = 0;
     return;
   }
-  const double beta = sqrt(fmax(0.0, p.nrm[s]));
-  if (first) st->bnorm = beta;
+  double beta, ibeta;
+  root_and_inverse(p.nrm[s], beta, ibeta);
+  if (first) {
+    st->bnorm = beta;
+    st->inv_bnorm = ibeta;
+  }
   st->beta = beta;
   double* g = p.g + (size_t)s * (m + 1);
   for (int i = 0; i <= m; ++i) g[i] = 0.0;
   g[0] = beta;
-  st->res = st->bnorm > 0 ? beta / st->bnorm : 0.0;
+  st->res = beta * st->inv_bnorm;
   st->converged = st->res <= st->tol;
   st->active = (!st->converged && st->iters < st->max_iter && beta > 0) ? 1 : 0;
-  st->inv_hn = beta > 0 ? 1.0 / beta : 0.0;
+  st->inv_hn = ibeta;
 }
 
 __global__ void bk_init_cycle(GPtr p, int first) {
@@ -709,6 +744,8 @@ __device__ void cycle_end_all(const GPtr& p, const int* __restrict__ off, DSolve
   }
 }
 
+constexpr int kSolveSmemK = 48;   // Krylov dimensions whose triangle bk_solve_y stages in shared memory
+
 // y_s = H_s^-1 g_s on the kdim leading rows (column-oriented back substitution).  In the
 // solve graph (d set) the last system's block (counted in cnt[S]) then ends the cycle
 // (cycle_end_all).
@@ -717,14 +754,40 @@ __global__ void bk_solve_y(GPtr p, DSolve* d = nullptr, const int* __restrict__ 
   const int s = blockIdx.x;
   const GDev* st = p.st + s;
   const int k = st->kdim, m = p.m;
-  if (k > 0) {
-    const double* H = p.H + (size_t)s * (m + 1) * m;
-    const size_t o1 = (size_t)s * (m + 1);
-    __shared__ double rhs[kGmMaxM], yv[kGmMaxM];
+  const double* H = p.H + (size_t)s * (m + 1) * m;
+  const size_t o1 = (size_t)s * (m + 1);
+  __shared__ double rhs[kGmMaxM], yv[kGmMaxM];
+  if (k > 0 && k <= kSolveSmemK) {
+    // the k x k triangle in shared memory (all its loads in flight together), then the
+    // substitution on the first warp
+    __shared__ double Hs[kSolveSmemK * kSolveSmemK];
+    for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+      const int r = e / k, c = e - r * k;
+      if (c >= r) Hs[e] = H[(size_t)r * m + c];
+    }
+    __shared__ double idg[kSolveSmemK];
+    for (int i = threadIdx.x; i < k; i += blockDim.x) rhs[i] = p.g[o1 + i];
+    __syncthreads();
+    // the reciprocals of the diagonal all at once, off the serial chain
+    for (int i = threadIdx.x; i < k; i += blockDim.x) idg[i] = 1.0 / Hs[i * k + i];
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      const int lane = threadIdx.x;
+      for (int i = k - 1; i >= 0; --i) {
+        if (lane == 0) yv[i] = rhs[i] * idg[i];
+        __syncwarp();
+        const double yi = yv[i];
+        for (int r = lane; r < i; r += 32) rhs[r] -= Hs[r * k + i] * yi;
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < k; i += blockDim.x) p.y[o1 + i] = yv[i];
+  } else if (k > 0) {
     for (int i = threadIdx.x; i < k; i += blockDim.x) rhs[i] = p.g[o1 + i];
     __syncthreads();
     for (int i = k - 1; i >= 0; --i) {
-      if (threadIdx.x == 0) yv[i] = rhs[i] / H[(size_t)i * m + i];
+      if (threadIdx.x == 0) yv[i] = rhs[i] * (1.0 / H[(size_t)i * m + i]);
       __syncthreads();
       for (int r = threadIdx.x; r < i; r += blockDim.x) rhs[r] -= H[(size_t)r * m + i] * yv[i];
       __syncthreads();
@@ -762,13 +825,15 @@ __global__ void bk_update(const double* __restrict__ V, size_t n, int Ntot, cons
 // refinement bookkeeping: mode 0 stores |b_s| (from nrm), mode 1 sets rel and enabled
 __device__ void refine_sys(const GPtr& p, int s, int mode, double rtol) {
   GDev* st = p.st + s;
-  const double v = sqrt(fmax(0.0, p.nrm[s]));
+  double v, iv;
+  root_and_inverse(p.nrm[s], v, iv);
   if (mode == 0) {
     st->nb = v;
+    st->inv_nb = iv;
     st->enabled = v > 0 ? 1 : 0;
     st->rel = v > 0 ? 1.0 : 0.0;
   } else if (st->enabled) {
-    st->rel = st->nb > 0 ? v / st->nb : 0.0;
+    st->rel = v * st->inv_nb;
     st->enabled = st->rel > rtol ? 1 : 0;
   }
 }
@@ -830,13 +895,12 @@ __global__ void __launch_bounds__(256) bk_norm_then(const double* __restrict__ x
   __syncthreads();
   if (!s_last) return;
   __threadfence();
+  if (threadIdx.x < 32) {
+    const double v = want ? warp_chunk_sum(p.nrmp + (size_t)s * CH, CH) : 0.0;
+    if (threadIdx.x == 0 && want) p.nrm[s] = v;
+  }
   if (threadIdx.x == 0) {
     p.cnt[s] = 0u;
-    if (want) {
-      double acc = 0.0;
-      for (int k = 0; k < CH; ++k) acc += __ldcg(p.nrmp + (size_t)s * CH + k);
-      p.nrm[s] = acc;
-    }
     switch (nc.follow) {
       case kFollowCycle: init_cycle_sys(p, s, nc.d != nullptr ? nc.d->first : nc.first); break;
       case kFollowRefine0: refine_sys(p, s, 0, nc.rtol); break;
@@ -967,7 +1031,7 @@ gbi_status launch_chunk(gbi_ctx* ctx, const Setup& s, const Batch& B, int precis
         bk_finalize<<<S, 128, 0, ctx->stream>>>(gp, 0);
         ctx->launches += 2;
       }
-      bk_sub_scale<<<g2, 256, 0, ctx->stream>>>(Vb, n, w, Ntot, B.sys, gp.st, m, gp.CH, gp.h1p, so, lcs);
+      bk_sub_scale<<<g2, 256, 0, ctx->stream>>>(Vb, n, w, Ntot, B.sys, gp.st, m, gp.cf, so, lcs);
       ++ctx->launches;
     }
   }
