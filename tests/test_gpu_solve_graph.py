@@ -95,6 +95,23 @@ def test_replay_matches_host_sequence(gbi, batched, sizes, trunc, precision):
         fresh.close()
 
 
+@pytest.mark.parametrize("precision", [1, 3])
+def test_replay_matches_host_sequence_many_systems(gbi, precision):
+    """64 systems or more take the separate dot-product and Givens kernels."""
+    sizes = [int(n) for n in np.random.default_rng(5).integers(2, 14, size=70)]
+    R, t, offs = inputs(sizes, 2, seed=60)
+    prm = gbi.params(a=1.0, eta=workloads.ETA_DEFAULT, trunc=2, precision=precision, rtol=1e-10)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        ctx = gbi.Context(0, stream=stream)
+        first = run(gbi, ctx, prm, R, t, offs, True)
+        for k in range(2):
+            same(run(gbi, ctx, prm, R, t, offs, True), first)
+            assert ctx.solve_graph_replays() == k + 1
+        assert first[3]["rel_residual"] <= 1e-10
+        ctx.close()
+
+
 def test_key_change_and_launch_count(gbi):
     R, t, offs = inputs([48], 3, seed=7)
     prm = gbi.params(a=1.0, eta=workloads.ETA_DEFAULT, trunc=3, precision=3, rtol=1e-10)
