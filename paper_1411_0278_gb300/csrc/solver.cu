@@ -654,10 +654,8 @@ __global__ void __launch_bounds__(256) bk_step_fused(double* V, size_t n, double
   }
 }
 
-// start of a GMRES cycle for every enabled system: beta = |V_0|, g = (beta, 0, ...)
-// In the solve graph (d set) `first` comes from the device record and the Arnoldi
-// loop's condition is reset to 1, so that its body runs at least once, as it does when
-// the cycle graph is launched.
+// start of a GMRES cycle for system s (enabled systems): beta = |V_0|, g = (beta, 0, ...);
+// `first` marks the first cycle of an inner solve (the counters restart)
 __device__ void init_cycle_sys(const GPtr& p, int s, int first) {
   GDev* st = p.st + s;
   const int m = p.m;
@@ -688,11 +686,6 @@ __device__ void init_cycle_sys(const GPtr& p, int s, int first) {
   st->inv_hn = ibeta;
 }
 
-__global__ void bk_init_cycle(GPtr p, int first) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s == 0) *p.nact = 0;
-  if (s < p.S) init_cycle_sys(p, s, first);
-}
 
 __global__ void bk_scale0(double* V0, int Ntot, const int* __restrict__ sys, const GDev* __restrict__ st,
                           SrcOut src) {
@@ -822,7 +815,8 @@ __global__ void bk_update(const double* __restrict__ V, size_t n, int Ntot, cons
   u[t] += minv.v[blockIdx.y] * acc;
 }
 
-// refinement bookkeeping: mode 0 stores |b_s| (from nrm), mode 1 sets rel and enabled
+// refinement bookkeeping of system s: mode 0 stores |b_s| (from nrm), mode 1 sets rel and
+// enabled
 __device__ void refine_sys(const GPtr& p, int s, int mode, double rtol) {
   GDev* st = p.st + s;
   double v, iv;
@@ -838,10 +832,6 @@ __device__ void refine_sys(const GPtr& p, int s, int mode, double rtol) {
   }
 }
 
-__global__ void bk_refine(GPtr p, int mode, double rtol) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s < p.S) refine_sys(p, s, mode, rtol);
-}
 
 // What follows the norms of bk_norm_then, per system (see there).
 enum NormFollow : int { kFollowNone = 0, kFollowCycle = 1, kFollowRefine0 = 2, kFollowRefine1 = 3, kFollowSweep = 4 };
@@ -857,15 +847,16 @@ struct NormCtl {
   int max_refine, max_iter;
 };
 
-// |x_s|^2 per system with the partials and the summation order of bk_norm_part and
-// bk_norm_sum, followed in the same kernel by what uses it: every block (s, c) counts
+// |x_s|^2 per system (partials per row chunk as bk_norm_part forms them, added by one warp
+// in a fixed order), followed in the same kernel by what uses it: every block (s, c) counts
 // itself in cnt[s] once its partial is stored, and the last one of system s forms nrm[s]
-// and runs the follow-up of s -- the start of a GMRES cycle (bk_init_cycle), the
-// refinement bookkeeping (bk_refine mode 0 or 1), or, in the solve graph, the
-// bookkeeping of a sweep: bk_refine mode 1, the residual pass's counters and, in the last
-// system to finish (counted in cnt[S]), the decision to run the sweep's inner solve.
-// All blocks of s read the state they depend on before counting, so none sees the
-// follow-up's writes.  The counters are zero between launches.
+// and runs the follow-up of s -- the start of a GMRES cycle (init_cycle_sys; in the solve
+// graph `first` comes from the device record and the Arnoldi loop's condition is reset to 1
+// so that its body runs at least once), the refinement bookkeeping (refine_sys mode 0 or 1),
+// or, in the solve graph, the bookkeeping of a sweep: refine_sys mode 1, the residual pass's
+// counters and, in the last system to finish (counted in cnt[S]), the decision to run the
+// sweep's inner solve.  All blocks of s read the state they depend on before counting, so
+// none sees the follow-up's writes.  The counters are zero between launches.
 __global__ void __launch_bounds__(256) bk_norm_then(const double* __restrict__ x, int Ntot, int h,
                                                     const int* __restrict__ off, GPtr p, int mode, NormCtl nc) {
   const int s = blockIdx.x, c = blockIdx.y, CH = p.CH;
@@ -1167,7 +1158,7 @@ gbi_status gmres_batch(gbi_ctx* ctx, const Setup& s, const Batch& B, int precisi
     ctx->launches += 2;
     GBI_CHECK(cudaGetLastError());
     if (first)
-      for (int q = 0; q < S; ++q) before[q] = 0;      // bk_init_cycle restarts the counters
+      for (int q = 0; q < S; ++q) before[q] = 0;      // the first cycle restarts the counters
     else
       for (int q = 0; q < S; ++q) before[q] = hst[q].iters;
     first = false;
