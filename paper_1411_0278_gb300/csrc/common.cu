@@ -253,7 +253,8 @@ __global__ void k_finalize_lower(int N, double a, double c2a, const double* __re
 // solver state for one call
 // ---------------------------------------------------------------------------------
 
-gbi_status setup_call(gbi_ctx* ctx, Setup& s, int N, int trunc, double a, double eta, const double* R) {
+gbi_status setup_call(gbi_ctx* ctx, Setup& s, int N, int trunc, double a, double eta, const double* R,
+                      bool launch) {
   s.N = N;
   s.trunc = trunc;
   s.D = d_of(trunc);
@@ -272,11 +273,16 @@ gbi_status setup_call(gbi_ctx* ctx, Setup& s, int N, int trunc, double a, double
   GBI_TRY(ensure(ctx, ctx->pos_hi, sizeof(float4) * N));
   GBI_TRY(ensure(ctx, ctx->pos_lo, sizeof(float4) * N));
   GBI_TRY(ensure(ctx, ctx->pos64, sizeof(dpos4) * N));
-  k_positions<<<grid1(N), 256, 0, ctx->stream>>>(N, R, P<float4>(ctx->pos_hi), P<float4>(ctx->pos_lo),
-                                                 P<dpos4>(ctx->pos64));
+  s.pos = Positions{P<float4>(ctx->pos_hi), P<float4>(ctx->pos_lo), P<dpos4>(ctx->pos64)};
+  if (launch) GBI_TRY(launch_positions(ctx, s, R));
+  return GBI_OK;
+}
+
+gbi_status launch_positions(gbi_ctx* ctx, const Setup& s, const double* R) {
+  k_positions<<<grid1(s.N), 256, 0, ctx->stream>>>(s.N, R, P<float4>(ctx->pos_hi), P<float4>(ctx->pos_lo),
+                                                   P<dpos4>(ctx->pos64));
   ++ctx->launches;
   GBI_CHECK(cudaGetLastError());
-  s.pos = Positions{P<float4>(ctx->pos_hi), P<float4>(ctx->pos_lo), P<dpos4>(ctx->pos64)};
   return GBI_OK;
 }
 

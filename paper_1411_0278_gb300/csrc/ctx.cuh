@@ -5,6 +5,7 @@
 
 #include <cuda_runtime.h>
 
+#include <functional>
 #include <map>
 #include <string>
 #include <vector>
@@ -184,7 +185,10 @@ struct Setup {
   long long pairs_per_pass;
 };
 
-gbi_status setup_call(gbi_ctx* ctx, Setup& s, int N, int trunc, double a, double eta, const double* R);
+gbi_status setup_call(gbi_ctx* ctx, Setup& s, int N, int trunc, double a, double eta, const double* R,
+                      bool launch_positions = true);
+// the centres of R as float hi / lo and FP64 copies (what setup_call launches)
+gbi_status launch_positions(gbi_ctx* ctx, const Setup& s, const double* R);
 PairArgs pair_args(const Setup& s, const double* x, double* y, double alpha, double beta, int add_self,
                    const Scales& colscale, int col0);
 
@@ -205,8 +209,36 @@ bool valid_params(const gbi_params* p);
 bool valid_offsets(int nsys, const int* off);
 gbi_status make_batch(gbi_ctx* ctx, int nsys, const int* offsets_host, Batch& B);
 gbi_status single_batch(gbi_ctx* ctx, int N, Batch& B);
+// Counters of the device-decided solve (one record per call, read back at the end):
+// what the host-driven sequence accumulates in gbi_info, plus the number of times each
+// loop body of the solve graph ran.
+struct DSolve {
+  long long iters;        // inner GMRES iterations over the whole solve
+  long long mv32, mv64;   // pair passes decided on the device
+  long long pairs;        // their ordered pairs
+  long long steps;        // Arnoldi loop iterations
+  long long cycles;       // GMRES cycles
+  int refinements;        // refinement sweeps after the first
+  int ifs;                // sweeps that ran an inner solve
+  int first, notfirst;    // the current inner solve is in its first cycle / past it
+  int overlap;            // the overlap guard stopped the solve
+  int pad;
+  double rel_max;         // largest final relative residual over the systems
+};
+
+// Work a caller wraps around one solve (a trap step: the inputs from (R, p) before, the
+// Euler update after).  solve_core launches `before` ahead of its own packing and `after`
+// once the solve has succeeded; in a replayed solve graph both are captured with the solve
+// (the caller's arrays then belong to the graph's key) and `after` receives the device
+// record, so that its kernels can skip the update of a solve that failed.
+struct StepHooks {
+  std::function<gbi_status()> before;
+  std::function<gbi_status(const DSolve* rec)> after;   // rec: device record, or null
+  std::vector<long long> key;                           // values the hooks' launches depend on
+};
+
 gbi_status solve_core(gbi_ctx* ctx, const gbi_params* prm, const Batch& B, const double* R, const double* Va,
                       const double* Oa, const double* VH, const double* Fe, const double* Te, double* V,
-                      double* Omega, double* QH, int warm_start, gbi_info* inf);
+                      double* Omega, double* QH, int warm_start, gbi_info* inf, const StepHooks* hooks = nullptr);
 
 }  // namespace gbi

@@ -40,8 +40,12 @@ __global__ void k_trap_inputs(int N, double k_trap, double vs, double s0, double
   vh[7] = d0 * px;
 }
 
+// With rec set (a trap step replayed inside the solve graph) the update is skipped when
+// that solve failed: an overlap, or a residual above rtol -- the cases in which the
+// host-driven step stops before its update.
 __global__ void k_euler(int N, double dt, const double* __restrict__ V, const double* __restrict__ Om,
-                        double* R, double* p) {
+                        double* R, double* p, const DSolve* __restrict__ rec = nullptr, double rtol = 0.0) {
+  if (rec != nullptr && (rec->overlap || !(rec->rel_max <= rtol))) return;
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
   const double px = p[3 * n], py = p[3 * n + 1], pz = p[3 * n + 2];
@@ -417,17 +421,42 @@ gbi_status gbi_trap_step(gbi_ctx* ctx, const gbi_params* prm, int N, double dt, 
   GBI_TRY(ensure(ctx, ctx->tOm, sizeof(double) * 3 * N));
   GBI_TRY(ensure(ctx, ctx->tQH, sizeof(double) * (size_t)h * N));
   gbi_status st = GBI_OK;
-  for (int step = 0; step < nsteps; ++step) {
+  auto trap_inputs = [&]() -> gbi_status {
     k_trap_inputs<<<grid1(N), 256, 0, ctx->stream>>>(N, k_trap, vs, s0, d0, h, R, p, P<double>(ctx->tFe),
                                                      P<double>(ctx->tTe), P<double>(ctx->tVa), P<double>(ctx->tOa),
                                                      P<double>(ctx->tVH));
     ++ctx->launches;
     GBI_CHECK(cudaGetLastError());
+    return GBI_OK;
+  };
+  const double rtol = prm->rtol > 0 ? prm->rtol : 1e-10;
+  auto euler = [&](const DSolve* rec) -> gbi_status {
+    k_euler<<<grid1(N), 256, 0, ctx->stream>>>(N, dt, P<double>(ctx->tV), P<double>(ctx->tOm), R, p, rec, rtol);
+    ++ctx->launches;
+    GBI_CHECK(cudaGetLastError());
+    return GBI_OK;
+  };
+  // the solve's work around it: inputs from (R, p) before, the update after (captured
+  // with a replayed solve graph)
+  StepHooks hooks;
+  hooks.before = trap_inputs;
+  hooks.after = euler;
+  {
+    double pr[5] = {dt, k_trap, vs, s0, d0};
+    long long b[5];
+    std::memcpy(b, pr, sizeof(pr));
+    hooks.key.assign(b, b + 5);
+    hooks.key.push_back((long long)(uintptr_t)R);
+    hooks.key.push_back((long long)(uintptr_t)p);
+  }
+  for (int step = 0; step < nsteps; ++step) {
     if (superposition) {
+      GBI_TRY(trap_inputs());
       GBI_TRY(gbi_superpose(ctx, prm, N, R, P<double>(ctx->tVa), P<double>(ctx->tOa), P<double>(ctx->tVH),
                             P<double>(ctx->tFe), P<double>(ctx->tTe), P<double>(ctx->tV), P<double>(ctx->tOm)));
       total.pair_interactions += (long long)N * (N - 1);
       (prm->precision == 1 || prm->precision == 3 ? total.matvecs_f32 : total.matvecs_f64) += 1;
+      GBI_TRY(euler(nullptr));
     } else {
       gbi_info one{};
       // FP64 solves warm-start from the previous step's traction coefficients (also across
@@ -436,9 +465,11 @@ gbi_status gbi_trap_step(gbi_ctx* ctx, const gbi_params* prm, int N, double dt, 
       // inner solves cannot reach the target from it in fewer sweeps.
       const bool warm = prm->precision == 0 && (step > 0 || (ctx->tqh_N == N && ctx->tqh_trunc == prm->trunc));
       ctx->tqh_N = -1;
-      st = gbi_solve(ctx, prm, N, R, P<double>(ctx->tVa), P<double>(ctx->tOa), P<double>(ctx->tVH),
-                     P<double>(ctx->tFe), P<double>(ctx->tTe), P<double>(ctx->tV), P<double>(ctx->tOm),
-                     P<double>(ctx->tQH), warm ? 1 : 0, &one);
+      Batch B;
+      GBI_TRY(single_batch(ctx, N, B));
+      st = solve_core(ctx, prm, B, R, P<double>(ctx->tVa), P<double>(ctx->tOa), P<double>(ctx->tVH),
+                      P<double>(ctx->tFe), P<double>(ctx->tTe), P<double>(ctx->tV), P<double>(ctx->tOm),
+                      P<double>(ctx->tQH), warm ? 1 : 0, &one, &hooks);
       if (st == GBI_OK) {
         ctx->tqh_N = N;
         ctx->tqh_trunc = prm->trunc;
@@ -450,11 +481,8 @@ gbi_status gbi_trap_step(gbi_ctx* ctx, const gbi_params* prm, int N, double dt, 
       total.pair_interactions += one.pair_interactions;
       total.rel_residual = std::max(total.rel_residual, one.rel_residual);
       total.min_separation = step == 0 ? one.min_separation : std::min(total.min_separation, one.min_separation);
-      if (st != GBI_OK) break;
+      if (st != GBI_OK) break;   // the update ran only for a successful solve
     }
-    k_euler<<<grid1(N), 256, 0, ctx->stream>>>(N, dt, P<double>(ctx->tV), P<double>(ctx->tOm), R, p);
-    ++ctx->launches;
-    GBI_CHECK(cudaGetLastError());
   }
   if (info) *info = total;
   return st;

@@ -66,22 +66,6 @@ struct GPtr {     // per-system views into the gstate buffer
   int S, m, CH;
 };
 
-// Counters of the device-decided solve (one record per call, read back at the end):
-// what the host-driven sequence accumulates in gbi_info, plus the number of times each
-// loop body of the solve graph ran.
-struct DSolve {
-  long long iters;        // inner GMRES iterations over the whole solve
-  long long mv32, mv64;   // pair passes decided on the device
-  long long pairs;        // their ordered pairs
-  long long steps;        // Arnoldi loop iterations
-  long long cycles;       // GMRES cycles
-  int refinements;        // refinement sweeps after the first
-  int ifs;                // sweeps that ran an inner solve
-  int first, notfirst;    // the current inner solve is in its first cycle / past it
-  int overlap;            // the overlap guard stopped the solve
-  int pad;
-  double rel_max;         // largest final relative residual over the systems
-};
 
 
 // ordered pairs of system s
@@ -1429,10 +1413,10 @@ gbi_status emit_gmres(GraphBuild& gb, const Setup& s, const Batch& B, const GPtr
 // Inputs and outputs are concatenated over the systems ([Ntot][3], [Ntot][h]).
 gbi_status solve_core(gbi_ctx* ctx, const gbi_params* prm, const Batch& B, const double* R, const double* Va,
                       const double* Oa, const double* VH, const double* Fe, const double* Te, double* V,
-                      double* Omega, double* QH, int warm_start, gbi_info* inf) {
+                      double* Omega, double* QH, int warm_start, gbi_info* inf, const StepHooks* hooks) {
   const int N = B.Ntot, S = B.S;
   Setup s;
-  GBI_TRY(setup_call(ctx, s, N, prm->trunc, prm->a, prm->eta, R));
+  GBI_TRY(setup_call(ctx, s, N, prm->trunc, prm->a, prm->eta, R, false));
   long long pairs_all = 0;
   for (int q = 0; q < S; ++q) {
     const long long ns = B.h_off[q + 1] - B.h_off[q];
@@ -1553,6 +1537,13 @@ gbi_status solve_core(gbi_ctx* ctx, const gbi_params* prm, const Batch& B, const
                                   bits(rtol), bits(inner), bits(prm->min_sep), bits(prm->a), bits(prm->eta),
                                   ctx->wpt_gen, ctx->force_wpt};
     for (const void* q : ptrs) key.push_back((long long)(uintptr_t)q);
+    if (hooks != nullptr) {
+      // the caller's work and arrays go into the graph as well
+      const void* io[] = {R, Va, Oa, VH, Fe, Te, V, Omega, QH};
+      key.push_back(-1);
+      for (const void* q : io) key.push_back((long long)(uintptr_t)q);
+      key.insert(key.end(), hooks->key.begin(), hooks->key.end());
+    }
     const bool ready = ctx->solve_exec != nullptr && key == ctx->solve_key;
     const bool build = !ready && key == ctx->solve_prev && key != ctx->solve_failed;
     ctx->solve_prev = key;
@@ -1575,6 +1566,11 @@ gbi_status solve_core(gbi_ctx* ctx, const gbi_params* prm, const Batch& B, const
             st = [&]() -> gbi_status {
               GBI_CHECK(cudaMemsetAsync(d, 0, sizeof(DSolve), ctx->stream));
               GBI_CHECK(cudaMemsetAsync(gp.cnt, 0, sizeof(unsigned int) * (S + 2), ctx->stream));
+              if (hooks != nullptr) {
+                GBI_TRY(hooks->before());
+                GBI_TRY(launch_positions(ctx, s, R));
+                GBI_TRY(pack_inputs());
+              }
               GBI_TRY(rhs_pass());
               GBI_CHECK(cudaMemsetAsync(xQH, 0, sizeof(double) * nh, ctx->stream));
               {
@@ -1629,7 +1625,12 @@ gbi_status solve_core(gbi_ctx* ctx, const gbi_params* prm, const Batch& B, const
               }));
               gk_summary<<<1, 256, 0, ctx->stream>>>(gp, d);
               ++ctx->launches;
-              return output_pass();
+              GBI_TRY(output_pass());
+              if (hooks != nullptr) {
+                GBI_TRY(unpack_outputs());
+                GBI_TRY(hooks->after(d));
+              }
+              return GBI_OK;
             }();
             const cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
             if (st == GBI_OK && (e != cudaSuccess || gb.err != cudaSuccess)) st = GBI_ERR_CUDA;
@@ -1658,10 +1659,13 @@ gbi_status solve_core(gbi_ctx* ctx, const gbi_params* prm, const Batch& B, const
     }
     if (ctx->solve_exec != nullptr && key == ctx->solve_key) {
       DSolve* d = P<DSolve>(ctx->dsolve);
-      GBI_TRY(pack_inputs());
+      if (hooks == nullptr) {
+        GBI_TRY(launch_positions(ctx, s, R));
+        GBI_TRY(pack_inputs());
+      }
       GBI_CHECK(cudaGraphLaunch(ctx->solve_exec, ctx->stream));
       ++ctx->solve_replays;
-      GBI_TRY(unpack_outputs());
+      if (hooks == nullptr) GBI_TRY(unpack_outputs());
       GBI_CHECK(cudaMemcpyAsync(hrec, d, sizeof(DSolve), cudaMemcpyDeviceToHost, ctx->stream));
       GBI_CHECK(cudaMemcpyAsync(hbits, ctx->minr2.p, sizeof(unsigned int), cudaMemcpyDeviceToHost, ctx->stream));
       GBI_CHECK(cudaStreamSynchronize(ctx->stream));
@@ -1684,6 +1688,8 @@ gbi_status solve_core(gbi_ctx* ctx, const gbi_params* prm, const Batch& B, const
     }
   }
 
+  if (hooks != nullptr) GBI_TRY(hooks->before());
+  GBI_TRY(launch_positions(ctx, s, R));
   GBI_TRY(pack_inputs());
   GBI_TRY(rhs_pass());
   (io == 1 ? inf->matvecs_f32 : inf->matvecs_f64) += 1;
@@ -1784,6 +1790,7 @@ gbi_status solve_core(gbi_ctx* ctx, const gbi_params* prm, const Batch& B, const
   }
   GBI_TRY(output_pass());
   GBI_TRY(unpack_outputs());
+  if (converged && hooks != nullptr) GBI_TRY(hooks->after(nullptr));
   (io == 1 ? inf->matvecs_f32 : inf->matvecs_f64) += 1;
   inf->pair_interactions += pairs_all;
   if (prm->min_sep <= 0) {

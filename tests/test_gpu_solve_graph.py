@@ -168,3 +168,53 @@ def test_overlap_guard_in_the_graph(gbi):
                 run(gbi, ctx, prm, R, t, offs, False)
         assert ctx.solve_graph_replays() == 2
         ctx.close()
+
+
+def _trap_case(gbi, precision, max_iter=1000):
+    c = workloads.config1()
+    prm = gbi.params(a=c["a"], eta=c["eta"], trunc=3, precision=precision, rtol=1e-10, max_iter=max_iter)
+    return c, prm
+
+
+@pytest.mark.parametrize("precision", [2, 3])
+def test_trap_steps_replayed_with_their_inputs_and_update(gbi, precision):
+    """A trap step replays its inputs, solve and Euler update as one graph: every replayed
+    step equals a host-driven step taken from the same state on a fresh context."""
+    c, prm = _trap_case(gbi, precision)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        ctx = gbi.Context(0, stream=stream)
+        R = dev(c["R"])
+        p = dev(c["p"])
+        for k in range(4):
+            R0, p0 = R.clone(), p.clone()
+            info = ctx.trap_step(prm, R, p, 0.05, c["k"], c["vs"], c["s0"], c["d0"], False, 1)
+            stream.synchronize()
+            assert info.rel_residual <= 1e-10
+            ref = gbi.Context(0, stream=stream)
+            R1, p1 = R0.clone(), p0.clone()
+            ref.trap_step(prm, R1, p1, 0.05, c["k"], c["vs"], c["s0"], c["d0"], False, 1)
+            stream.synchronize()
+            assert ref.solve_graph_replays() == 0
+            assert torch.equal(R1, R) and torch.equal(p1, p), k
+            ref.close()
+        # steps 1 and 2 repeat step 0's key only in sizes: R moved, but its buffer did not
+        assert ctx.solve_graph_replays() >= 2
+        ctx.close()
+
+
+def test_failed_trap_step_leaves_the_state_in_the_graph(gbi):
+    c, prm = _trap_case(gbi, 3, max_iter=3)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        ctx = gbi.Context(0, stream=stream)
+        R = dev(c["R"])
+        p = dev(c["p"])
+        R0, p0 = R.clone(), p.clone()
+        for _ in range(3):
+            with pytest.raises(gbi.GbiError):
+                ctx.trap_step(prm, R, p, 0.05, c["k"], c["vs"], c["s0"], c["d0"], False, 1)
+            stream.synchronize()
+            assert torch.equal(R, R0) and torch.equal(p, p0)
+        assert ctx.solve_graph_replays() == 2
+        ctx.close()
