@@ -315,6 +315,7 @@ PairArgs pair_args(const Setup& s, const double* x, double* y, double alpha, dou
   p.sys_flag = nullptr;
   p.sys_flag_stride = 0;
   p.nsys = 1;
+  p.pdl = 0;
   return p;
 }
 

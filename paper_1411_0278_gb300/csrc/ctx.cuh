@@ -52,6 +52,7 @@ struct gbi_ctx {
   gbi::Buf dsolve;                               // its device-side counters
   long long wpt_gen = 0;                         // bumped whenever the warps-per-target choice changes
   long long solve_replays = 0;                   // solves run from solve_exec
+  bool pdl = true;                               // programmatic dependent launch in the Arnoldi steps
   gbi::Buf tFe, tTe, tVa, tOa, tVH, tV, tOm, tQH;  // trap-step staging
   int tqh_N = -1, tqh_trunc = -1;                // tQH holds the last trap-step solution of this size
   gbi::Buf hR, hVa, hOa, hVH, hFe, hTe, hV, hOm, hQH;  // gbi_solve_host staging

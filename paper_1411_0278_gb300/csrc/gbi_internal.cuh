@@ -59,7 +59,32 @@ struct PairArgs {
   int sys_flag_stride;
   int nsys;              // systems in the batch (<= 1: every target's sources are [0, N))
   int wpt;               // warps per target of the FP32 / double-float kernel (0: default)
+  int pdl;               // launch with programmatic dependent launch (see launch_pdl)
 };
+
+// Programmatic dependent launch: with pdl set the kernel's blocks may be scheduled while
+// the previous kernel in the stream is still finishing (its launch latency overlaps that
+// kernel's last blocks).  Every kernel launched this way starts with pdl_wait(), which
+// returns once all the previous kernel's memory operations are visible, so only block
+// scheduling overlaps, never computation.
+template <typename... K, typename... A>
+inline cudaError_t launch_pdl(bool pdl, dim3 grid, dim3 block, cudaStream_t st, void (*kernel)(K...), A&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = pdl ? at : nullptr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<A&&>(args)...);
+}
+
+#ifdef __CUDACC__
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+#endif
 
 // Floats per source record of a pass reading NC columns (see PairArgs::x32).
 inline int rec_floats(int nc, bool df) { return ((nc + 3) & ~3) * (df ? 2 : 1); }

@@ -470,6 +470,7 @@ __global__ void __launch_bounds__(WPT * 32, MINB) pair_stream_kernel(const PairA
   constexpr int NRC = (NR + 31) / 32;
   __shared__ T red[WPT > 1 ? WPT : 1][NRC * 32];
 
+  pdl_wait();
   if (args.active != nullptr && *args.active == 0) return;   // device-side GMRES has stopped
   const int n = blockIdx.x;
   const int warp = threadIdx.x >> 5;

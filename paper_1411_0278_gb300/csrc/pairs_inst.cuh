@@ -38,8 +38,8 @@ cudaError_t launch_pairs_tt(int rows, int cols, const PairArgs& args, cudaStream
 #define GBI_S(RV, CV, WPT)                                                                         \
   if (rows == RV && cols == CV && wpt == WPT) {                                                    \
     constexpr int MINB = WARPS_SM / WPT > 0 ? WARPS_SM / WPT : 1;                                  \
-    pair_stream_kernel<TRN, RV, CV, T, WPT, MINB><<<dim3(N), dim3(WPT * 32), 0, stream>>>(args);   \
-    return cudaGetLastError();                                                                     \
+    return launch_pdl(args.pdl != 0, dim3(N), dim3(WPT * 32), stream,                              \
+                      pair_stream_kernel<TRN, RV, CV, T, WPT, MINB>, args);                        \
   }
 #define GBI_SW(RV, CV) \
   GBI_S(RV, CV, 2) GBI_S(RV, CV, 4) GBI_S(RV, CV, 8) if constexpr (WARPS_SM >= 16) { GBI_S(RV, CV, 16) }

@@ -339,6 +339,7 @@ __global__ void bk_finalize(GPtr p, int two_pass) {
 __global__ void __launch_bounds__(256) bk_dots_fin(const double* __restrict__ V, size_t n,
                                                    const double* __restrict__ w, int Ntot, int h,
                                                    const int* __restrict__ off, GPtr p) {
+  pdl_wait();
   const int s = blockIdx.x, i = blockIdx.y, c = blockIdx.z;
   const GDev* st = p.st + s;
   if (!st->active) return;
@@ -441,6 +442,7 @@ __global__ void bk_scale(double* V, size_t n, const double* __restrict__ w, int 
 __global__ void bk_sub_scale(double* V, size_t n, const double* __restrict__ w, int Ntot,
                              const int* __restrict__ sys, const GDev* __restrict__ st, int m,
                              const double* __restrict__ cf, SrcOut src, LoopCtl lc) {
+  pdl_wait();
   loop_continue(lc);
   __shared__ double sc[kMaxRestart + 1];
   const int p0 = blockIdx.x * blockDim.x;
@@ -977,9 +979,13 @@ gbi_status launch_chunk(gbi_ctx* ctx, const Setup& s, const Batch& B, int precis
   const SrcOut so = src_out(s, precision, xsrc);
   const dim3 gd(S, m + 1, gp.CH);
   const int two = two_pass_gs(precision);
+  // programmatic dependent launch inside the one-reduction step, between kernels of the
+  // same sequence (the first pair pass of a chunk follows other work)
+  const bool pdl = ctx->pdl && !two;
   for (int c = 0; c < kChunk; ++c) {
     LoopCtl lcs = lc;
     if (lc.on) lcs.on = c + 1 < kChunk ? 1 : 2;
+    pa.pdl = pdl && c > 0;
     GBI_CHECK(run_pairs(ctx, s.trunc, SET_H, SET_H, precision, pa));
     if (fused && S == 1) {
       // a single system launched step by step: the whole orthogonalisation in one kernel
@@ -999,14 +1005,15 @@ gbi_status launch_chunk(gbi_ctx* ctx, const Setup& s, const Batch& B, int precis
     } else {
       if (S < 64) {
         // dot products, norm and Givens step in one kernel
-        bk_dots_fin<<<gd, 256, 0, ctx->stream>>>(Vb, n, w, Ntot, h, B.off, gp);
+        GBI_CHECK(launch_pdl(pdl, gd, dim3(256), ctx->stream, bk_dots_fin, Vb, n, w, Ntot, h, B.off, gp));
         ++ctx->launches;
       } else {
         bk_dots<<<gd, 256, 0, ctx->stream>>>(Vb, n, w, Ntot, h, B.off, gp.st, m, gp.CH, gp.h1p, 1);
         bk_finalize<<<S, 128, 0, ctx->stream>>>(gp, 0);
         ctx->launches += 2;
       }
-      bk_sub_scale<<<g2, 256, 0, ctx->stream>>>(Vb, n, w, Ntot, B.sys, gp.st, m, gp.cf, so, lcs);
+      GBI_CHECK(launch_pdl(pdl && S < 64, g2, dim3(256), ctx->stream, bk_sub_scale, Vb, n, w, Ntot, B.sys, gp.st,
+                           m, gp.cf, so, lcs));
       ++ctx->launches;
     }
   }
