@@ -179,6 +179,20 @@ def test_self_scalars_against_one_body_laws():
         assert abs(g[name] - 2 * math.factorial(l) * tensors.dfact(2 * l - 1) / a) < 1e-9
 
 
+def test_self_scalars_against_the_papers_coefficient_table():
+    """The sigma = 0 single-layer entries of the paper's table of C_lsigma
+    (tests/golden/one_body_coefficients.txt) give the self scalars of those modes."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "one_body_coefficients.txt")
+    rows = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    assert len(rows) == 2
+    g = _g_by_mode(3, A)
+    for name, mode, num, den, power in rows:
+        l = int(name[1])
+        C = float(num) / float(den) * math.pi * ETA * A ** int(power)
+        assert abs(g[mode] - 8 * math.pi * ETA * A ** (2 * l - 2) / C) < 1e-12 * g[mode], name
+
+
 def test_self_elements_from_exterior_flow():
     """Self elements equal the Galerkin projection of the exterior flow formula (App. B)
     evaluated on the surface, an independent route to Eq. single_layer_yl_matrix_element."""
