@@ -278,6 +278,44 @@ def test_solve_full_size_sampled_rows(ctx, gbi, precision):
     assert relerr(Om[tgt], Om_o) < 1e-10
 
 
+def test_solve_full_size_graph_replay_sampled_rows(gbi):
+    """The bench's configuration: N = 1024, l <= 3, precision 3 on a user stream, where a
+    repeated solve is replayed as one CUDA graph; the replayed solution against sampled
+    rows of the oracle's system (FP32 right-hand side and output passes: the 1e-5 bar)."""
+    c = workloads.config2()
+    R, p = c["R"], c["p"]
+    N = len(R)
+    prm_o = dict(a=c["a"], eta=c["eta"], k=c["k"], vs=c["vs"], s0=c["s0"], d0=0.0)
+    inp = dynamics.trap_inputs(R, p, prm_o, 3)
+    prm = gbi.params(a=c["a"], eta=c["eta"], trunc=3, precision=3, rtol=1e-10)
+    t = {k: dev(v) for k, v in inp.items()}
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        gctx = gbi.Context(0, stream=stream)
+        gctx.tune(3, [0, N])
+        Rd = dev(R)
+        for _ in range(3):
+            V, Om, QH, info, _ = gctx.solve(prm, Rd, t["Va"], t["Oa"], t["VH"], t["Fe"], t["Te"])
+        stream.synchronize()
+        assert gctx.solve_graph_replays() == 2
+        gctx.close()
+    assert info.rel_residual <= 1e-10
+    V, Om, QH = V.cpu().numpy(), Om.cpu().numpy(), QH.cpu().numpy()
+    MB = tensors.ModeBasis(3)
+    tgt = np.random.default_rng(5).choice(N, size=6, replace=False)
+    rows = _oracle_rows(R, tgt, c["a"], 3)
+    xF = galerkin.lower_trial(inp["Fe"], inp["Te"], c["a"], MB)
+    x = np.concatenate([xF, QH * MB.scale[6:]], axis=1)
+    eta = c["eta"]
+    Ax = np.einsum("kpmq,mq->kp", rows, x)
+    xVH = inp["VH"] * MB.scale[6:]
+    res = Ax[:, 6:] + 8 * np.pi * eta * xVH[tgt]
+    assert np.abs(res).max() / np.abs(8 * np.pi * eta * xVH).max() < FP32_TOL
+    V_o, Om_o = galerkin.lower_velocity(-Ax[:, :6] / (8 * np.pi * eta), inp["Va"][tgt], inp["Oa"][tgt], c["a"], MB)
+    assert relerr(V[tgt], V_o) < FP32_TOL
+    assert relerr(Om[tgt], Om_o) < FP32_TOL
+
+
 @pytest.mark.parametrize("precision", [1, 2])
 def test_mixed_matches_fp64_gpu(ctx, gbi, precision):
     R, p, s = cloud(200, 31)
