@@ -6,10 +6,11 @@
 // outputs, K = 16 per instruction) issued by a single thread, operands in shared
 // memory in the no-swizzle K-major core-matrix layout (8 rows x 16 bytes per core
 // matrix), the FP32 accumulator in tensor memory (128 lanes x 128 columns) read back
-// with tcgen05.ld by the four warps (warp w owns lanes 32w..32w+31 = pairs of the
-// tile).  Completion of each MMA chain is signalled through an mbarrier
-// (tcgen05.commit); every wait has an iteration limit after which the kernel records
-// an error, releases its tensor memory and returns.
+// with tcgen05.ld by eight warps: a warp may only read the lane quarter of its warp
+// index mod 4, so warps w and w + 4 share lanes 32 (w mod 4) .. + 31 (pairs of the tile)
+// and each takes half of the 128 columns of the epilogue.  Completion of each MMA chain
+// is signalled through an mbarrier (tcgen05.commit); every wait has an iteration limit
+// after which the kernel records an error, releases its tensor memory and returns.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -144,12 +145,16 @@ struct TcSmem {
   int abort;
 };
 
-__global__ void __launch_bounds__(128) k_infer_tc(int P, const float* __restrict__ F, const float* __restrict__ FR,
+constexpr int kTcThreads = 256;   // eight warps: two per tensor-memory lane quarter
+
+__global__ void __launch_bounds__(kTcThreads) k_infer_tc(int P, const float* __restrict__ F, const float* __restrict__ FR,
                                                    const __nv_bfloat16* __restrict__ pk, float* __restrict__ out,
                                                    int* __restrict__ err) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   TcSmem& s = *reinterpret_cast<TcSmem*>(smem_raw);
   const int tid = threadIdx.x, warp = tid >> 5;
+  const int row = tid & (TM - 1);          // the pair of the tile (accumulator lane) this thread reads
+  const int half = warp >> 2;              // which 64 of the 128 hidden columns it handles
   {
     const int4* src = reinterpret_cast<const int4*>(pk);
     int4* dst = reinterpret_cast<int4*>(s.w);
@@ -173,7 +178,7 @@ __global__ void __launch_bounds__(128) k_infer_tc(int P, const float* __restrict
   __syncthreads();
   fence_after();
   const uint32_t tmem = s.tmem_base;
-  const uint32_t lane_base = (uint32_t)(warp * 32) << 16;   // this warp's TMEM lanes
+  const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;   // this warp's TMEM lane quarter
   const uint32_t a1_addr = saddr(s.a1), act_addr = saddr(s.act), w_addr = saddr(s.w);
   const uint32_t id_hidden = instr_desc(TM, NH), id_out = instr_desc(TM, N4);
   uint32_t parity = 0;
@@ -208,29 +213,30 @@ __global__ void __launch_bounds__(128) k_infer_tc(int P, const float* __restrict
     return s.abort == 0;
   };
 
-  // hidden epilogue: row tid of the accumulator -> tanh(. + b) -> bf16 -> act (core layout)
+  // hidden epilogue: row `row`, columns [64 half, 64 half + 64) of the accumulator ->
+  // tanh(. + b) -> bf16 -> act (core layout)
   auto hidden_epilogue = [&](const float* b) {
 #pragma unroll 1
-    for (int c0 = 0; c0 < NH; c0 += 16) {
+    for (int c0 = half * (NH / 2); c0 < (half + 1) * (NH / 2); c0 += 16) {
       float v[16];
       tmem_ld16(tmem + lane_base + (uint32_t)c0, v);
       __align__(16) __nv_bfloat16 o[16];
 #pragma unroll
       for (int i = 0; i < 16; ++i) o[i] = __float2bfloat16_rn(tanh_act(v[i] + b[c0 + i]));
-      *reinterpret_cast<int4*>(&s.act[cm_index(tid, c0, NH)]) = *reinterpret_cast<const int4*>(&o[0]);
-      *reinterpret_cast<int4*>(&s.act[cm_index(tid, c0 + 8, NH)]) = *reinterpret_cast<const int4*>(&o[8]);
+      *reinterpret_cast<int4*>(&s.act[cm_index(row, c0, NH)]) = *reinterpret_cast<const int4*>(&o[0]);
+      *reinterpret_cast<int4*>(&s.act[cm_index(row, c0 + 8, NH)]) = *reinterpret_cast<const int4*>(&o[8]);
     }
   };
 
   bool ok = true;
   for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-    const int p = tile * TM + tid;
-    {
+    const int p = tile * TM + row;
+    if (half == 0) {
       __align__(16) __nv_bfloat16 f[16];
 #pragma unroll
       for (int k = 0; k < 16; ++k) f[k] = __float2bfloat16_rn((k < NIN && p < P) ? F[(size_t)p * NIN + k] : 0.f);
-      *reinterpret_cast<int4*>(&s.a1[cm_index(tid, 0, K1)]) = *reinterpret_cast<const int4*>(&f[0]);
-      *reinterpret_cast<int4*>(&s.a1[cm_index(tid, 8, K1)]) = *reinterpret_cast<const int4*>(&f[8]);
+      *reinterpret_cast<int4*>(&s.a1[cm_index(row, 0, K1)]) = *reinterpret_cast<const int4*>(&f[0]);
+      *reinterpret_cast<int4*>(&s.a1[cm_index(row, 8, K1)]) = *reinterpret_cast<const int4*>(&f[8]);
     }
     ok = run_layer(a1_addr, K1, w_addr + 2 * PW1, id_hidden);
     if (!ok) break;
@@ -243,6 +249,7 @@ __global__ void __launch_bounds__(128) k_infer_tc(int P, const float* __restrict
     hidden_epilogue(s.bias + 2 * NH);
     ok = run_layer(act_addr, NH, w_addr + 2 * PW4, id_out);
     if (!ok) break;
+    if (half != 0) continue;   // the 16 output columns: the first warp of each lane quarter
     float o[16];
     tmem_ld16(tmem + lane_base, o);
     if (p < P) {
@@ -294,7 +301,7 @@ cudaError_t infer_tc(int P, const float* F, const float* FR, const void* packed,
   if (e != cudaSuccess) return e;
   const int ntiles = (P + TM - 1) / TM;
   const int grid = ntiles < 2 * num_sms ? ntiles : 2 * num_sms;
-  k_infer_tc<<<grid, 128, smem, st>>>(P, F, FR, static_cast<const __nv_bfloat16*>(packed), out, err);
+  k_infer_tc<<<grid, kTcThreads, smem, st>>>(P, F, FR, static_cast<const __nv_bfloat16*>(packed), out, err);
   return cudaGetLastError();
 }
 
