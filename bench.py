@@ -157,7 +157,7 @@ def run_reference(args):
         return
     import workloads
     c = workloads.config2()
-    npairs = 3000
+    npairs = 1500
     for _ in range(args.warmup):
         oracle_pair_rate(c["R"], 3, c["a"], 200)
     total_pairs, total_t = 0, 0.0
@@ -575,7 +575,7 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", type=int, default=3, choices=[0, 1, 2, 3],
