@@ -179,6 +179,7 @@ def run_reference(args):
 
 # passes timed by gbi_tune, in the order of its result
 TUNED_PASSES = ["HH_f32", "HH_df", "HL_df", "Lall_df", "HL_f32", "Lall_f32"]
+RESET_EVERY = 20     # timed trap steps between returns to the initial suspension
 
 
 def learned_nearfield(ctx, gbi, dev, stream, peaks):
@@ -375,7 +376,12 @@ def run_ours(args):
 
     def run_steps(k, stats=None):
         ms, pr = 0.0, 0
-        for _ in range(k):
+        for i in range(k):
+            if i > 0 and i % RESET_EVERY == 0:
+                # back to the initial suspension (outside the timed interval): every step
+                # then starts within RESET_EVERY steps of it, whatever the step count
+                R.copy_(R0)
+                p.copy_(p0)
             flush.fill_(1.0)                    # evict the L2 between timed steps
             ev0.record(stream)
             info = step()
@@ -553,6 +559,7 @@ def run_ours(args):
                 "config": {"workload": c["name"], "N": N, "trunc": trunc, "h": h, "volume_fraction": 0.05,
                            "min_sep_a": 2.5, "rtol": 1e-10, "restart": 40, "inner_rtol": 1e-5,
                            "step": "trap inputs + full Galerkin solve + Euler update",
+                           "trajectory": "from the initial suspension, reset to it every %d steps" % RESET_EVERY,
                            "l2": "flushed (256 MB write) before every timed step",
                            "parallelism": "replicas" if world > 1 else "single GPU"},
                 "solves_per_s": solves_per_s, "error_vs_fp64": err,
