@@ -180,6 +180,10 @@ def run_reference(args):
 # passes timed by gbi_tune, in the order of its result
 TUNED_PASSES = ["HH_f32", "HH_df", "HL_df", "Lall_df", "HL_f32", "Lall_f32"]
 RESET_EVERY = 20     # timed trap steps between returns to the initial suspension
+# DRAM bytes (read + write) per launch of a pass class on this workload, from an ncu capture
+# of the current kernel (profiles/pair_stream_kernel_l3_HH_f32_N1024.md, 1024 targets, l <= 3):
+# class 17 = FP32 rows H / columns H.  Reported as roofline.traffic when that class dominates.
+NCU_TRAFFIC_BYTES = {17: 169728}
 
 
 def learned_nearfield(ctx, gbi, dev, stream, peaks):
@@ -435,7 +439,9 @@ def run_ours(args):
     kernel_share = {names.get(k, "class%d" % k): round(v["ms"] / max(1e-9, sum(s["ms"] for s in stats.values())), 4)
                     for k, v in stats.items() if v["launches"]}
     roofline = {"bound": "alu", "kernel": names.get(dom, "class%d" % dom), "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": NCU_TRAFFIC_BYTES.get(dom),
+                "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum, "
+                                "profiles/pair_stream_kernel_l3_HH_f32_N1024.md)",
                 "peak_source": ("FP32 CUDA-core peak 152 SMs x 128 lanes x 2 x %.0f MHz (sm_max_mhz of %s "
                                 "MEASURED_PEAKS.json)" % (sm_max, peak_src)) if is_f32 else
                                "GB300 FP64 nominal 1.25 TFLOP/s",
