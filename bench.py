@@ -330,8 +330,9 @@ def run_ours(args):
     c = workloads.config2()
     N, trunc = len(c["R"]), c["trunc"]
     dt = 0.1
+    # min_sep: the overlap guard (centres closer than 2a fail the step instead of being timed)
     prm = gbi.params(a=c["a"], eta=c["eta"], trunc=trunc, precision=args.precision, rtol=1e-10, restart=40,
-                     inner_rtol=1e-5)
+                     inner_rtol=1e-5, min_sep=2.0)
     R0 = torch.tensor(c["R"], dtype=torch.float64, device=dev)
     p0 = torch.tensor(c["p"], dtype=torch.float64, device=dev)
     R, p = R0.clone(), p0.clone()
@@ -563,7 +564,8 @@ def run_ours(args):
                               "FP64 Arnoldi/Givens"}[args.precision],
                 "data": "synthetic",
                 "config": {"workload": c["name"], "N": N, "trunc": trunc, "h": h, "volume_fraction": 0.05,
-                           "min_sep_a": 2.5, "rtol": 1e-10, "restart": 40, "inner_rtol": 1e-5,
+                           "min_sep_a": 2.5, "overlap_guard_a": 2.0, "rtol": 1e-10, "restart": 40,
+                           "inner_rtol": 1e-5,
                            "step": "trap inputs + full Galerkin solve + Euler update",
                            "trajectory": "from the initial suspension, reset to it every %d steps" % RESET_EVERY,
                            "l2": "flushed (256 MB write) before every timed step",
