@@ -112,6 +112,25 @@ def test_replay_matches_host_sequence_many_systems(gbi, precision):
         ctx.close()
 
 
+@pytest.mark.parametrize("restart", [2, 64])
+def test_replay_with_short_and_long_restarts(gbi, restart):
+    """Restart 2: many GMRES cycles per inner solve (the restart loop of the graph);
+    restart 64: Krylov dimensions past the triangular solve's shared-memory stage."""
+    R, t, offs = inputs([96], 3, seed=70)
+    # an inner tolerance below the FP32 floor makes every cycle run its full length
+    prm = gbi.params(a=1.0, eta=workloads.ETA_DEFAULT, trunc=3, precision=2, rtol=1e-10, restart=restart,
+                     max_iter=4000, max_refine=30, inner_rtol=1e-5 if restart == 2 else 1e-12)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        ctx = gbi.Context(0, stream=stream)
+        first = run(gbi, ctx, prm, R, t, offs, False)
+        for k in range(2):
+            same(run(gbi, ctx, prm, R, t, offs, False), first)
+        assert ctx.solve_graph_replays() == 2
+        assert first[3]["rel_residual"] <= 1e-10
+        ctx.close()
+
+
 def test_key_change_and_launch_count(gbi):
     R, t, offs = inputs([48], 3, seed=7)
     prm = gbi.params(a=1.0, eta=workloads.ETA_DEFAULT, trunc=3, precision=3, rtol=1e-10)
