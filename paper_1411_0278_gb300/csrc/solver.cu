@@ -377,6 +377,47 @@ __global__ void __launch_bounds__(256) bk_dots_fin(const double* __restrict__ V,
   finalize_column(p, s, j, 0);
 }
 
+// One-reduction Arnoldi step, first half, for batches of many small systems: one block
+// per system, its warp k taking the slots i = k, k + 8, ... <= j_s + 1 (V_i . w, and w . w
+// for i = j_s + 1) over the system's whole vector (lanes stride its elements, a shuffle
+// tree adds them), then the Hessenberg column and the Givens step in the same block -- one
+// block per system instead of one per (system, slot), and no counting across blocks.
+__global__ void __launch_bounds__(256) bk_dots_sys(const double* __restrict__ V, size_t n,
+                                                   const double* __restrict__ w, int Ntot, int h,
+                                                   const int* __restrict__ off, GPtr p) {
+  const int s = blockIdx.x;
+  const GDev* st = p.st + s;
+  if (!st->active) return;
+  const int j = st->j;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int lo = off[s], ns = off[s + 1] - lo;
+  const int len = ns * h;
+  __shared__ double col[kGmMaxM + 1], scs[kGmMaxM], ssn[kGmMaxM];
+  __shared__ double s_hn, s_ihn;
+  for (int i = warp; i <= j + 1; i += nw) {
+    const double* v = i > j ? w : V + (size_t)i * n;
+    double acc = 0.0;
+    for (int e = lane; e < len; e += 32) {
+      const int q = e / ns;
+      const size_t t = (size_t)q * Ntot + lo + (e - q * ns);
+      acc += v[t] * w[t];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) col[i] = acc;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double nrm = col[j + 1];
+    for (int i = 0; i <= j; ++i) nrm -= col[i] * col[i];
+    root_and_inverse(nrm, s_hn, s_ihn);
+  }
+  const size_t o1 = (size_t)s * (p.m + 1);
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) p.cf[o1 + i] = col[i];
+  __syncthreads();
+  givens_step(p, s, j, s_hn, s_ihn, col, scs, ssn);
+}
+
 // Arnoldi source of the next pair pass, written by the kernels that produce V_j:
 // FP32 records (PairArgs::x32, ncp floats per sphere, zero padding) or FP64
 // component-major, both scaled by the column multipliers minv.
@@ -941,6 +982,15 @@ SrcOut src_out(const Setup& s, int precision, void* xsrc) {
   return o;
 }
 
+// Largest system of a batch (spheres), and the vector length up to which the one-round
+// step gives each system a single block (bk_dots_sys)
+int max_system(const Batch& B) {
+  int mx = 0;
+  for (int q = 0; q < B.S; ++q) mx = std::max(mx, B.h_off[q + 1] - B.h_off[q]);
+  return mx;
+}
+constexpr long long kSysBlockElems = 4096;
+
 // Gram-Schmidt of the Arnoldi step.  The FP64 solve (precision 0) orthogonalises twice
 // (CGS2) and takes the norm of the result.  The FP32 inner solves of the refinement
 // orthogonalise once and take the norm from |w|^2 - sum c_i^2, so that the dot products
@@ -1006,6 +1056,10 @@ gbi_status launch_chunk(gbi_ctx* ctx, const Setup& s, const Batch& B, int precis
       if (S < 64) {
         // dot products, norm and Givens step in one kernel
         GBI_CHECK(launch_pdl(pdl, gd, dim3(256), ctx->stream, bk_dots_fin, Vb, n, w, Ntot, h, B.off, gp));
+        ++ctx->launches;
+      } else if ((long long)max_system(B) * h <= kSysBlockElems) {
+        // many small systems: one block each
+        bk_dots_sys<<<S, 256, 0, ctx->stream>>>(Vb, n, w, Ntot, h, B.off, gp);
         ++ctx->launches;
       } else {
         bk_dots<<<gd, 256, 0, ctx->stream>>>(Vb, n, w, Ntot, h, B.off, gp.st, m, gp.CH, gp.h1p, 1);
@@ -1540,7 +1594,8 @@ gbi_status solve_core(gbi_ctx* ctx, const gbi_params* prm, const Batch& B, const
     }
     const void* ptrs[] = {B.sys, B.off, ctx->pos_hi.p, ctx->pos_lo.p, ctx->pos64.p, ctx->xQ.p, ctx->b.p, ctx->r.p, ctx->delta.p, ctx->xVL.p, ctx->minr2.p,
                           ctx->krylov.p, ctx->w.p, ctx->x32.p, ctx->gstate.p, ctx->dsolve.p};
-    std::vector<long long> key = {N, S, pairs_all, prm->trunc, prm->precision, restart, max_iter, max_refine,
+    std::vector<long long> key = {N, S, pairs_all, max_system(B), prm->trunc, prm->precision, restart, max_iter,
+                                  max_refine,
                                   bits(rtol), bits(inner), bits(prm->min_sep), bits(prm->a), bits(prm->eta),
                                   ctx->wpt_gen, ctx->force_wpt};
     for (const void* q : ptrs) key.push_back((long long)(uintptr_t)q);
