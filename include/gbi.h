@@ -130,7 +130,12 @@ gbi_status gbi_apply(gbi_ctx* ctx, int N, int trunc, double a, int rows, int col
  * with F^(1) = -F^e and F^(21) = -T^e / a.
  * Inputs R, Va, Oa, Fe, Te: [N][3]; VH: [N][h] packed.  Outputs V, Omega: [N][3];
  * QH: [N][h] packed (may be NULL unless warm_start).  If warm_start != 0, QH is
- * also read as the initial guess.  info may be NULL.  Synchronous. */
+ * also read as the initial guess.  info may be NULL.  Synchronous.
+ * On a non-default stream with profiling off, a mixed-precision solve (precision 1..3)
+ * without warm start is captured as one CUDA graph the second time a call repeats the
+ * previous call's sizes, parameters, tuning and workspace, and replayed afterwards (see
+ * gbi_solve_graph_replays); the caller's arrays are copied in and out around the graph,
+ * so they may differ from call to call.  Results are identical either way. */
 gbi_status gbi_solve(gbi_ctx* ctx, const gbi_params* params, int N,
                      const double* R, const double* Va, const double* Oa, const double* VH,
                      const double* Fe, const double* Te,
@@ -197,7 +202,11 @@ gbi_status gbi_trap_inputs(gbi_ctx* ctx, int N, int trunc, double k_trap, double
  * from zero (a warm start would cost one more high-precision residual pass and save no
  * refinement sweep).  Results differ only within the solve tolerance.
  * R, p: [N][3] device arrays updated in place.  info (may be NULL) accumulates
- * over the steps.  Synchronous when superposition == 0. */
+ * over the steps.  A step whose solve fails (overlap guard, tolerance not met) leaves
+ * R and p as they were and ends the call with that status.  Synchronous when
+ * superposition == 0.  When the solve is replayed as a graph (see gbi_solve), the
+ * step's input evaluation and update are captured with it; the graph then also depends
+ * on R, p, dt and the trap parameters. */
 gbi_status gbi_trap_step(gbi_ctx* ctx, const gbi_params* params, int N, double dt, double k_trap,
                          double vs, double s0, double d0, int superposition, int nsteps,
                          double* R, double* p, gbi_info* info);
