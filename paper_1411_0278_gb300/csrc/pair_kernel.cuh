@@ -76,8 +76,17 @@ __host__ __device__ __forceinline__ void dapplyT(const DMats<T>& dm, const T* in
   if constexpr (K == 4) gbi_dapplyT4<T>(dm.d4, in, out);
 }
 
+// v scaled by (a/r)^j = ep[j]; j = 0 leaves v untouched (no multiply by one).
+template <int J, typename T>
+__host__ __device__ __forceinline__ T eps_pow(const T* ep, T v) {
+  if constexpr (J == 0) return v;
+  else return ep[J] * v;
+}
+
 // Rotate the column modes [M, MEND) of x (absolute component index) into the pair
-// frame and scale by (a/r)^l: xs = (a/r)^l D_y Z x.
+// frame and scale by (a/r)^l: xs = (a/r)^l D_y Z x.  The scaling rides on the z
+// rotation: its cos/sin factors are taken times (a/r)^l (products shared by every mode
+// with the same l), so no separate multiply per component is needed.
 template <int TR, typename T, int M, int MEND>
 __host__ __device__ __forceinline__ void to_pair_frame(const T* x, T* xs, const T* cm, const T* sm,
                                               const DMats<T>& dm, const T* ep) {
@@ -85,23 +94,23 @@ __host__ __device__ __forceinline__ void to_pair_frame(const T* x, T* xs, const 
     constexpr int k = Tab<TR>::k(M);
     constexpr int o = Tab<TR>::off(M);
     constexpr int l = Tab<TR>::L(M) - 1;
-    T t[2 * k + 1], u[2 * k + 1];
-    t[k] = x[o + k];
+    T t[2 * k + 1];
+    t[k] = eps_pow<l>(ep, x[o + k]);
 #pragma unroll
     for (int mm = 1; mm <= k; ++mm) {
+      const T c = eps_pow<l>(ep, cm[mm]), s = eps_pow<l>(ep, sm[mm]);
       const T xp = x[o + k + mm], xn = x[o + k - mm];
-      t[k + mm] = gbi_fmac(cm[mm], xp, sm[mm] * xn);
-      t[k - mm] = gbi_fmac(cm[mm], xn, -(sm[mm] * xp));
+      t[k + mm] = gbi_fmac(c, xp, s * xn);
+      t[k - mm] = gbi_fmac(c, xn, -(s * xp));
     }
-    dapply<k, T>(dm, t, u);
-#pragma unroll
-    for (int i = 0; i < 2 * k + 1; ++i) xs[o + i] = ep[l] * u[i];
+    dapply<k, T>(dm, t, xs + o);
     to_pair_frame<TR, T, M + 1, MEND>(x, xs, cm, sm, dm, ep);
   }
 }
 
 // Rotate the row modes [M, MEND) of the pair-frame result back and accumulate:
 // acc += Z^T D_y^T (a/r)^(l+1) yy.  acc is indexed from the first row component R0.
+// As above, (a/r)^(l+1) multiplies the z rotation's cos/sin instead of yy.
 template <int TR, typename T, int M, int MEND, int R0>
 __host__ __device__ __forceinline__ void from_pair_frame(const T* yy, T* acc, const T* cm, const T* sm,
                                                 const DMats<T>& dm, const T* ep) {
@@ -109,16 +118,15 @@ __host__ __device__ __forceinline__ void from_pair_frame(const T* yy, T* acc, co
     constexpr int k = Tab<TR>::k(M);
     constexpr int o = Tab<TR>::off(M);
     constexpr int l = Tab<TR>::L(M) - 1;
-    T u[2 * k + 1], t[2 * k + 1];
-#pragma unroll
-    for (int i = 0; i < 2 * k + 1; ++i) u[i] = ep[l + 1] * yy[o + i];
-    dapplyT<k, T>(dm, u, t);
-    acc[o - R0 + k] += t[k];
+    T t[2 * k + 1];
+    dapplyT<k, T>(dm, yy + o, t);
+    acc[o - R0 + k] = gbi_fmac(ep[l + 1], t[k], acc[o - R0 + k]);
 #pragma unroll
     for (int mm = 1; mm <= k; ++mm) {
+      const T c = ep[l + 1] * cm[mm], s = ep[l + 1] * sm[mm];
       const T tp = t[k + mm], tn = t[k - mm];
-      acc[o - R0 + k + mm] = gbi_fmac(cm[mm], tp, gbi_fmac(-sm[mm], tn, acc[o - R0 + k + mm]));
-      acc[o - R0 + k - mm] = gbi_fmac(sm[mm], tp, gbi_fmac(cm[mm], tn, acc[o - R0 + k - mm]));
+      acc[o - R0 + k + mm] = gbi_fmac(c, tp, gbi_fmac(-s, tn, acc[o - R0 + k + mm]));
+      acc[o - R0 + k - mm] = gbi_fmac(s, tp, gbi_fmac(c, tn, acc[o - R0 + k - mm]));
     }
     from_pair_frame<TR, T, M + 1, MEND, R0>(yy, acc, cm, sm, dm, ep);
   }

@@ -550,9 +550,20 @@ def emit(path):
                 f += 7                                           # powers of a/r
                 for kk in range(1, maxk_used + 1):               # rotation matrices about y
                     f += 6 + 2 * dm_terms[kk]
-                for m in cmodes + rmodes:                        # z and y rotations per block
-                    kk = MODES[m][1] - MODES[m][2]
-                    f += 6 * kk + 2 * dm_nnz[kk] + (2 * kk + 1)
+                # z and y rotations per block; the (a/r)^j scalings ride on the z rotation's
+                # cos/sin factors (2 products per multiple angle and power j, shared by the
+                # modes), plus one multiply (columns, l > 0) or FMA (rows) for the centre entry
+                kmax_pow = {}
+                for m in cmodes:
+                    kk, j = MODES[m][1] - MODES[m][2], MODES[m][1] - 1
+                    f += 6 * kk + 2 * dm_nnz[kk] + (1 if j > 0 else 0)
+                    if j > 0:
+                        kmax_pow[j] = max(kmax_pow.get(j, 0), kk)
+                for m in rmodes:
+                    kk, j = MODES[m][1] - MODES[m][2], MODES[m][1]
+                    f += 6 * kk + 2 * dm_nnz[kk] + 1
+                    kmax_pow[j] = max(kmax_pow.get(j, 0), kk)
+                f += sum(2 * kk for kk in kmax_pow.values())
                 for (p, q, al, be) in cpl:
                     if p in rows and q in cols:
                         f += (2 if al != 0.0 else 0) + (2 if be != 0.0 else 0)
