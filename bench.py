@@ -183,7 +183,7 @@ RESET_EVERY = 20     # timed trap steps between returns to the initial suspensio
 # DRAM bytes (read + write) per launch of a pass class on this workload, from an ncu capture
 # of the current kernel (profiles/pair_stream_kernel_l3_HH_f32_N1024.md, 1024 targets, l <= 3):
 # class 17 = FP32 rows H / columns H.  Reported as roofline.traffic when that class dominates.
-NCU_TRAFFIC_BYTES = {17: 169728}
+NCU_TRAFFIC_BYTES = {17: 168704}
 
 
 def learned_nearfield(ctx, gbi, dev, stream, peaks):
@@ -362,6 +362,28 @@ def run_ours(args):
     err = {"V_rel": rel(V1, V0), "Omega_rel": rel(O1, O0), "QH_rel": rel(Q1, Q0),
            "mixed_residual": i1.rel_residual, "fp64_residual": i0.rel_residual,
            "mixed_iters": i1.iters, "mixed_refinements": i1.refinements, "fp64_iters": i0.iters}
+
+    # ---- the same solve in plain FP64 GMRES (precision 0) against the mixed form: solves/s
+    # on this GPU at the same tolerance, the mixed V within V_rel of the FP64 one (outside
+    # the timed region; CUDA events on the library stream, each solve after an L2 flush)
+    sv0, sv1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def solve_ms(pr, reps):
+        tot = 0.0
+        for _ in range(reps):
+            flush.fill_(1.0)
+            sv0.record(stream)
+            ctx.solve(pr, R0, inp["Va"], inp["Oa"], inp["VH"], inp["Fe"], inp["Te"])
+            sv1.record(stream)
+            sv1.synchronize()
+            tot += sv0.elapsed_time(sv1)
+        return tot / reps
+    ms64 = solve_ms(prm64, 3)
+    ms_mixed = solve_ms(prm, 10)
+    vs_fp64 = {"fp64_solves_per_s": 1e3 / ms64, "mixed_solves_per_s": 1e3 / ms_mixed,
+               "fp64_ms_per_solve": ms64, "mixed_ms_per_solve": ms_mixed, "speedup": ms64 / ms_mixed,
+               "mixed_V_rel_vs_fp64": err["V_rel"], "rtol": 1e-10,
+               "note": "same input (the initial N=1024 suspension), cold start, solve only (no trap step)"}
 
     # ---- warm-up
     for _ in range(max(3, args.warmup)):
@@ -570,7 +592,7 @@ def run_ours(args):
                            "trajectory": "from the initial suspension, reset to it every %d steps" % RESET_EVERY,
                            "l2": "flushed (256 MB write) before every timed step",
                            "parallelism": "replicas" if world > 1 else "single GPU"},
-                "solves_per_s": solves_per_s, "error_vs_fp64": err,
+                "solves_per_s": solves_per_s, "error_vs_fp64": err, "vs_fp64_gmres": vs_fp64,
                 "per_step": {"gmres_iters": step_stats["iters"] / args.steps,
                              "refinements": step_stats["refinements"] / args.steps,
                              "fp32_passes": step_stats["matvecs_f32"] / args.steps,
