@@ -443,6 +443,37 @@ def test_batch_solve_matches_oracle_per_system(ctx, gbi, trunc, precision):
     assert 2 * pairs <= info.pair_interactions <= (info.iters + 8) * 3 * pairs
 
 
+@pytest.mark.parametrize("precision", [1, 3])
+def test_batch_with_empty_systems(ctx, gbi, precision):
+    """Offsets may repeat: systems with no spheres (in the middle and at the end) take no
+    part in the solve or the superposition, and the others equal the oracle's solve and
+    superposition of each system alone."""
+    sizes = [3, 0, 12, 1, 0, 7, 0]
+    R, inp, offs = _batch_inputs(sizes, 2, seed=5)
+    t = {k: dev(v) for k, v in inp.items()}
+    prm = gbi.params(a=1.0, eta=workloads.ETA_DEFAULT, trunc=2, precision=precision, rtol=1e-10)
+    V, Om, QH, info, st = ctx.batch_solve(prm, offs, dev(R), t["Va"], t["Oa"], t["VH"], t["Fe"], t["Te"])
+    Vs, Oms = ctx.batch_superpose(prm, offs, dev(R), t["Va"], t["Oa"], t["VH"], t["Fe"], t["Te"])
+    torch.cuda.synchronize()
+    assert st == gbi.GBI_OK and info.rel_residual <= 1e-10
+    V, Om, Vs, Oms = V.cpu().numpy(), Om.cpu().numpy(), Vs.cpu().numpy(), Oms.cpu().numpy()
+    assert V.shape == (sum(sizes), 3)
+    # precision 3 runs the right-hand side and output in FP32
+    tol = 1e-9 if precision < 3 else FP32_TOL
+    for k, n in enumerate(sizes):
+        if n == 0:
+            continue
+        sl = slice(offs[k], offs[k + 1])
+        args = (R[sl], inp["Va"][sl], inp["Oa"][sl], inp["VH"][sl], inp["Fe"][sl], inp["Te"][sl], 1.0,
+                workloads.ETA_DEFAULT, 2)
+        Vr, Omr, _ = galerkin.solve(*args)
+        assert relerr(V[sl], Vr) < tol, k
+        assert relerr(Om[sl], Omr) < tol, k
+        Vsr, Omsr = galerkin.superpose(*args)
+        assert relerr(Vs[sl], Vsr) < FP32_TOL, k
+        assert relerr(Oms[sl], Omsr) < FP32_TOL, k
+
+
 def test_batch_graph_replay_matches_direct(gbi):
     """Arnoldi chunks replayed from a CUDA graph (non-default stream) give the same
     solution as direct launches on the default stream."""
