@@ -296,6 +296,18 @@ def learned_nearfield(ctx, gbi, dev, stream, peaks):
 
 
 
+def h_mode_slices(trunc):
+    """(name, first column, width) of every higher mode l-sigma in the packed [N][h] layout of
+    V^H and Q^H: the modes after 1s and 2a, each 2(l - sigma) + 1 wide."""
+    from paper_1411_0278_gb300 import gen_tables
+    out, off = [], 0
+    for name, L, sig in gen_tables.MODES[2:gen_tables.NMODES[trunc]]:
+        k = 2 * (L - sig) + 1
+        out.append((name, off, k))
+        off += k
+    return out
+
+
 def job_totals(t_local, pairs_local, world, device):
     """Whole-job time (the slowest rank) and work (summed over ranks) of a timed region."""
     if world <= 1:
@@ -359,7 +371,12 @@ def run_ours(args):
 
     def rel(a, b):
         return float((a - b).abs().max() / b.abs().max())
+
+    def rel_rows(a, b):   # max_n |a_n - b_n| / max_n |b_n| (per-sphere 2-norms)
+        return float((a - b).norm(dim=1).max() / b.norm(dim=1).max())
     err = {"V_rel": rel(V1, V0), "Omega_rel": rel(O1, O0), "QH_rel": rel(Q1, Q0),
+           "V_rel_per_particle": rel_rows(V1, V0), "Omega_rel_per_particle": rel_rows(O1, O0),
+           "QH_rel_per_mode": {name: rel(Q1[:, o:o + k], Q0[:, o:o + k]) for name, o, k in h_mode_slices(trunc)},
            "mixed_residual": i1.rel_residual, "fp64_residual": i0.rel_residual,
            "mixed_iters": i1.iters, "mixed_refinements": i1.refinements, "fp64_iters": i0.iters}
 
