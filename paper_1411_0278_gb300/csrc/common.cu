@@ -294,7 +294,6 @@ PairArgs pair_args(const Setup& s, const double* x, double* y, double alpha, dou
   p.pos = s.pos;
   p.x = x;
   p.x32 = nullptr;
-  p.x32lo = nullptr;
   p.wpt = 0;
   p.y = y;
   p.alpha = alpha;

@@ -38,7 +38,6 @@ struct PairArgs {
   // padded to a multiple of 4 (double-float: that hi block, then the lo block
   // float(x * colscale - hi)).  The FP64 pass reads x itself.
   const float* x32;
-  const float* x32lo;    // unused (kept zero)
   double* y;             // component-major, first component of the row set
   double alpha, beta;
   int add_self;
