@@ -66,9 +66,9 @@ typedef struct {
   double rtol;       /* target relative residual ||b - A q|| / ||b|| of the traction solve */
   int restart;       /* GMRES restart length (Krylov vectors per cycle), 1..128          */
   int max_iter;      /* cap on inner GMRES iterations over the whole solve               */
-  int max_refine;    /* cap on refinement sweeps (precision = 1)                         */
-  double inner_rtol; /* relative tolerance of each inner FP32 solve (precision 1, 2);    */
-                     /*    loosened to 0.1 rtol |b| / |r| when that is larger           */
+  int max_refine;    /* cap on refinement sweeps (precision 1..3; 0 = 8)                 */
+  double inner_rtol; /* relative tolerance of each inner FP32 solve (precision 1..3;     */
+                     /*    0 = 1e-5); loosened to 0.1 rtol |b| / |r| when that is larger */
   double min_sep;    /* overlap guard: reject pairs closer than min_sep * a (0 = off)    */
 } gbi_params;
 
