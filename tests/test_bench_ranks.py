@@ -1,4 +1,5 @@
-"""Host logic of bench.py's multi-rank (replica) mode, on CPU with the gloo backend.
+"""Host logic of bench.py on CPU: the multi-rank (replica) mode with the gloo backend,
+and the column layout of its per-mode error report.
 
 Replicas share nothing on the data path; the only cross-rank step is the job total:
 the slowest rank's time (max) and the work of all ranks (sum).
@@ -47,3 +48,20 @@ def test_job_totals_single_rank():
     sys.path.insert(0, ROOT)
     import bench
     assert bench.job_totals(1.5, 7, 1, None) == (1.5, 7.0)
+
+
+def test_h_mode_slices_follow_the_packed_mode_order():
+    """The per-mode error columns of the bench line: each higher mode's block of the
+    packed [N][h] layout, in the oracle's mode order and widths."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from oracle import tensors
+    for trunc in (2, 3, 4):
+        MB = tensors.ModeBasis(trunc)
+        expect, off = [], 0
+        for name, L, sig in MB.hmodes:
+            k = 2 * (L - sig) + 1
+            expect.append((name, off, k))
+            off += k
+        assert bench.h_mode_slices(trunc) == expect
+        assert off == MB.h
