@@ -417,3 +417,98 @@ def test_trap_opposite_pair_does_not_rotate():
     for sup in (True, False):
         _, Om = dynamics.velocities(R, p, prm, 2, sup)
         assert np.abs(Om).max() < 1e-16
+
+
+# ---------------------------------------------------------------- active modes and kinematics
+
+def _curl_and_laplacian(u, x, h=1e-2):
+    """Fourth-order central differences of a closed-form field u at x."""
+    e = np.eye(3)
+    J = np.zeros((3, 3))                                  # J[i, j] = d u_i / d x_j
+    lap = np.zeros(3)
+    for j in range(3):
+        f = [u(x + k * h * e[j]) for k in (-2, -1, 0, 1, 2)]
+        J[:, j] = (f[0] - 8 * f[1] + 8 * f[3] - f[4]) / (12 * h)
+        lap += (-f[0] + 16 * f[1] - 30 * f[2] + 16 * f[3] - f[4]) / (12 * h * h)
+    curl = np.array([J[2, 1] - J[1, 2], J[0, 2] - J[2, 0], J[1, 0] - J[0, 1]])
+    return curl, lap
+
+
+@pytest.mark.parametrize("trunc", [2, 3])
+def test_active_strain_mode_drives_passive_partner(trunc):
+    """``active_modes`` with s0 != 0 only: V^(2s) = s0 (pp - I/3) = a E (Sec. V trap
+    parametrisation; Sec. III, v = V^(2).Y^(1) on the surface).  The exterior flow of
+    that sphere is the classical strain solution u_E; a passive, force- and torque-free
+    partner in the superposition approximation moves with the Faxen laws
+    V = (1 + a^2/6 lap) u_E and Omega = curl(u_E)/2 at its centre (Sec. IV, first
+    terms of the superposition mobility).  A wrong sign, slot or scale of s0 fails."""
+    s0 = 0.07
+    p = np.array([[0.36, -0.48, 0.8]])
+    E = s0 * (np.outer(p[0], p[0]) - np.eye(3) / 3) / A
+
+    def u_E(x):
+        r = np.linalg.norm(x)
+        xEx = x @ E @ x
+        return 2.5 * A ** 3 * xEx * x / r ** 5 + A ** 5 * (E @ x / r ** 5 - 2.5 * xEx * x / r ** 7)
+
+    MB = tensors.ModeBasis(trunc)
+    VH = np.zeros((2, MB.h))
+    VH[:1] = galerkin.active_modes(p, s0, 0.0, trunc)
+    z = np.zeros((2, 3))
+    for x2 in (np.array([5.0, 2.0, -1.5]) * A, np.array([-1.0, 3.0, 4.0]) * A):
+        R = np.array([np.zeros(3), x2])
+        V, Om = galerkin.superpose(R, z, z, VH, z, z, A, ETA, trunc)
+        curl, lap = _curl_and_laplacian(u_E, x2)
+        np.testing.assert_allclose(V[1], u_E(x2) + A ** 2 / 6 * lap, rtol=1e-7, atol=1e-12)
+        np.testing.assert_allclose(Om[1], curl / 2, rtol=1e-7, atol=1e-12)
+        np.testing.assert_allclose(V[0], 0.0, atol=1e-16)
+        np.testing.assert_allclose(Om[0], 0.0, atol=1e-16)
+
+
+@pytest.mark.parametrize("trunc", [2, 3])
+def test_active_dipole_mode_drives_passive_partner(trunc):
+    """``active_modes`` with d0 != 0 only: V^(3t) = d0 p, the trace part of V^(3) with the
+    embedding coefficient 3/5 (Sec. III, Eq. irred_velocity_coefficients_inverse), so the
+    surface velocity (1/3!!2!) V^(3):Y^(2) is v = (3 nn - I).d/10 (Sec. III expansion of v).
+    Its exterior flow is the potential dipole u = (d0/10)(a/r)^3 (3 (p.r^) r^ - p), harmonic,
+    so a passive partner moves with exactly u and does not rotate."""
+    d0 = -0.09
+    p = np.array([[0.0, 0.6, -0.8]])
+    MB = tensors.ModeBasis(trunc)
+    VH = np.zeros((2, MB.h))
+    VH[:1] = galerkin.active_modes(p, 0.0, d0, trunc)
+    z = np.zeros((2, 3))
+    for x2 in (np.array([4.0, -2.0, 1.0]) * A, np.array([0.5, 1.0, -6.0]) * A):
+        R = np.array([np.zeros(3), x2])
+        V, Om = galerkin.superpose(R, z, z, VH, z, z, A, ETA, trunc)
+        r = np.linalg.norm(x2)
+        n = x2 / r
+        u = d0 / 10 * (A / r) ** 3 * (3 * (p[0] @ n) * n - p[0])
+        np.testing.assert_allclose(V[1], u, rtol=1e-12, atol=1e-16)
+        np.testing.assert_allclose(Om[1], 0.0, atol=1e-16)
+
+
+def test_euler_turns_orientation_about_the_torque():
+    """One sphere under a force F and a torque T perpendicular to p: V = F/(6 pi eta a),
+    Omega = T/(8 pi eta a^3) (Stokes laws, Sec. IV).  Forward Euler on dp/dt = Omega x p
+    (Sec. II kinematics) followed by renormalisation turns p about T, in the right-handed
+    sense, by exactly atan(dt |Omega|) per step, and moves R by dt V."""
+    F = np.array([[0.2, -0.1, 0.05]])
+    T = np.array([[0.0, 0.0, 0.9]])
+    R = np.array([[1.0, 2.0, -3.0]])
+    p = np.array([[0.8, 0.6, 0.0]])
+    dt = 0.3
+    z = np.zeros((1, 3))
+    for _ in range(5):
+        V, Om, _ = galerkin.solve(R, z, z, np.zeros((1, 8)), F, T, A, ETA, 2)
+        Rn, pn = dynamics.euler(R, p, V, Om, dt)
+        w = T[0, 2] / (8 * np.pi * ETA * A ** 3)
+        ang = math.atan(dt * w)
+        np.testing.assert_allclose(Rn, R + dt * F / (6 * np.pi * ETA * A), rtol=1e-14)
+        np.testing.assert_allclose(np.linalg.norm(pn[0]), 1.0, rtol=1e-15)
+        # counter-clockwise about +z: p_new = Rz(ang) p
+        c, s = math.cos(ang), math.sin(ang)
+        expect = np.array([c * p[0, 0] - s * p[0, 1], s * p[0, 0] + c * p[0, 1], 0.0])
+        np.testing.assert_allclose(pn[0], expect, atol=1e-14)
+        assert np.cross(p[0], pn[0])[2] > 0
+        R, p = Rn, pn
