@@ -310,9 +310,14 @@ gbi_status gbi_mlp_train(gbi_ctx* ctx, int N, const double* R, const double* p, 
                          double lr1, double* loss_hist);
 
 /* Tuning of the pair kernel (engineering; the paper has no counterpart).  The FP32
- * and double-float pair passes run one block per target sphere whose WPT warps split
- * the sources; WPT in {2, 4, 8, 16} (8 at most for trunc 4 and double-float) trades
- * parallelism at small N against per-target reduction work.
+ * and double-float pair passes run in one of two forms.  Streaming: one block per
+ * target sphere whose WPT warps split the sources; WPT in {2, 4, 8, 16} (8 at most for
+ * trunc 4 and double-float) trades parallelism at small N against per-target
+ * reduction work.  Tiled (code WPT = 1, one system only, not batches): lanes are 32
+ * target spheres, source records are staged in shared memory by the TMA unit and read
+ * by all lanes at once, and the (targets, source) work is split evenly over one block
+ * per SM; the blocks' partial sums are added in a fixed order, so results do not
+ * depend on timing.  Both forms sum the same pairs (in different fixed orders).
  * gbi_tune times every WPT for the six FP32 / double-float passes of the mixed-precision
  * solves -- rows H / columns H in FP32 and in double-float, H/L and L/all in
  * double-float, H/L and L/all in FP32 -- on synthetic
@@ -331,6 +336,19 @@ gbi_status gbi_mlp_train(gbi_ctx* ctx, int N, const double* R, const double* p, 
 gbi_status gbi_tune(gbi_ctx* ctx, int trunc, int nsys, const int* offsets, int reps, int* chosen);
 gbi_status gbi_set_wpt(gbi_ctx* ctx, int wpt);
 int gbi_pass_wpt(gbi_ctx* ctx, int trunc, int rows, int cols, int precision, int N, int batched);
+
+/* Bounded waits of the tiled pair passes (engineering; the paper has no counterpart).
+ * Each wait of a tiled pass for its shared-memory stage gives up after `rounds`
+ * mbarrier try_wait rounds (default 2^24, far beyond any copy's latency); the pass
+ * then records the failure on the device, waits with the default bound for the copies
+ * it has in flight and returns without storing.  gbi_solve and the calls built on it
+ * read the record after the solve and return GBI_ERR_TIMEOUT (outputs not valid); the
+ * context stays usable.  gbi_set_wait_limit(ctx, r): r >= 0 sets the bound (0 makes
+ * every such wait give up at once: a test of this path), r = -1 restores the default.
+ * gbi_pass_status synchronizes the stream and returns GBI_ERR_TIMEOUT once if a pair
+ * pass launched since the last check (gbi_apply included) gave up, else GBI_OK. */
+gbi_status gbi_set_wait_limit(gbi_ctx* ctx, long long rounds);
+gbi_status gbi_pass_status(gbi_ctx* ctx);
 
 /* Instrumentation.  gbi_kernel_launches: number of CUDA kernels this context has
  * launched since creation.  gbi_set_profiling(ctx, 1) resets the per-class

@@ -70,6 +70,8 @@ _SIGS = {
     "gbi_tune": (_I, [_VP, _I, _I, ctypes.POINTER(ctypes.c_int), _I, ctypes.POINTER(ctypes.c_int)]),
     "gbi_set_wpt": (_I, [_VP, _I]),
     "gbi_pass_wpt": (_I, [_VP, _I, _I, _I, _I, _I, _I]),
+    "gbi_set_wait_limit": (_I, [_VP, ctypes.c_longlong]),
+    "gbi_pass_status": (_I, [_VP]),
     "gbi_pairs": (_I, [_VP, _I, _VP, _D, _D, _I, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "gbi_pairs_get": (_I, [_VP, _VP, _VP]),
     "gbi_mlp_set": (_I, [_VP, _VP, _D]),
@@ -321,6 +323,13 @@ class Context:
 
     def set_wpt(self, wpt):
         self._check(lib().gbi_set_wpt(self._h, int(wpt)), "gbi_set_wpt")
+
+    def set_wait_limit(self, rounds):
+        self._check(lib().gbi_set_wait_limit(self._h, int(rounds)), "gbi_set_wait_limit")
+
+    def pass_status(self):
+        """gbi_pass_status: the status code (GBI_OK or GBI_ERR_TIMEOUT), not raised."""
+        return lib().gbi_pass_status(self._h)
 
     def pass_wpt(self, trunc, rows, cols, precision, N, batched=False):
         return lib().gbi_pass_wpt(self._h, int(trunc), int(rows), int(cols), int(precision), int(N), int(batched))

@@ -7,6 +7,7 @@
 #include <cstring>
 
 #include "ctx.cuh"
+#include "pair_tile.cuh"
 
 namespace gbi {
 #define GBI_DECL(P)                                                                       \
@@ -149,6 +150,60 @@ int ncols_of(int trunc, int cols) {
   return cols == SET_L ? 6 : cols == SET_H ? D - 6 : D;
 }
 
+gbi_status status_words(gbi_ctx* ctx) {
+  const void* old = ctx->minr2.p;
+  GBI_TRY(ensure(ctx, ctx->minr2, 4 * sizeof(unsigned int)));
+  if (ctx->minr2.p != old) GBI_CHECK(cudaMemsetAsync(ctx->minr2.p, 0, 4 * sizeof(unsigned int), ctx->stream));
+  return GBI_OK;
+}
+
+int* pass_error_word(gbi_ctx* ctx) { return P<int>(ctx->minr2) + 1; }
+int* input_error_word(gbi_ctx* ctx) { return P<int>(ctx->minr2) + 2; }
+
+gbi_status tile_reserve(gbi_ctx* ctx, int trunc, int rows, int precision, int N, TilePlan* out) {
+  const TilePlan t = tile_plan(N, sm_count(ctx), 1);
+  if (t.P <= 0) return GBI_ERR_ARG;
+  const int D = d_of(trunc);
+  const int nr = rows == SET_L ? 6 : (rows == SET_H ? D - 6 : D);
+  GBI_TRY(ensure(ctx, ctx->tile, tile_part_bytes(t, nr, precision == 2 ? sizeof(df) : sizeof(float))));
+  const void* old = ctx->tilecnt.p;
+  GBI_TRY(ensure(ctx, ctx->tilecnt, sizeof(unsigned int) * (size_t)t.G));
+  // counters start at zero and every launch leaves them so; a new buffer is cleared
+  if (ctx->tilecnt.p != old) GBI_CHECK(cudaMemsetAsync(ctx->tilecnt.p, 0, ctx->tilecnt.bytes, ctx->stream));
+  GBI_TRY(status_words(ctx));
+  if (out) *out = t;
+  return GBI_OK;
+}
+
+gbi_status pass_error_reset(gbi_ctx* ctx) {
+  GBI_CHECK(cudaMemsetAsync(pass_error_word(ctx), 0, sizeof(int), ctx->stream));
+  if (ctx->tilecnt.p) GBI_CHECK(cudaMemsetAsync(ctx->tilecnt.p, 0, ctx->tilecnt.bytes, ctx->stream));
+  return GBI_OK;
+}
+
+// The tiled form for this pass if the caller's (or the tuned) choice asks for it and its
+// scratch can be had (a context bound to static storage may not have it): fills the
+// plan and scratch fields of a; otherwise a's wpt is set back to a streaming choice.
+void tile_select(gbi_ctx* ctx, int trunc, int rows, int precision, PairArgs& a) {
+  const bool batched = a.sys_of != nullptr && a.nsys > 1;
+  if (precision == 0 || !balanced_form(a.wpt) || batched || a.N <= 1) {
+    if (balanced_form(a.wpt)) a.wpt = 0;
+    return;
+  }
+  TilePlan t;
+  if (tile_reserve(ctx, trunc, rows, precision, a.N, &t) != GBI_OK) {
+    a.wpt = 0;
+    return;
+  }
+  a.tile_part = ctx->tile.p;
+  a.tile_cnt = P<unsigned int>(ctx->tilecnt);
+  a.tile_P = t.P;
+  a.tile_G = t.G;
+  a.tile_maxseg = t.maxseg;
+  a.err = pass_error_word(ctx);
+  a.wait_limit = ctx->wait_limit;
+}
+
 cudaError_t run_pairs(gbi_ctx* ctx, int trunc, int rows, int cols, int precision, const PairArgs& args_in) {
   const double flops = pair_flops(trunc, rows, cols) * double(args_in.N) * double(args_in.N - 1);
   PairArgs args = args_in;
@@ -157,6 +212,7 @@ cudaError_t run_pairs(gbi_ctx* ctx, int trunc, int rows, int cols, int precision
     args.wpt = ctx->force_wpt > 0 ? ctx->force_wpt
                                   : ctx->tuned_wpt(trunc, rows, cols, precision, args.N,
                                                    args.sys_of != nullptr && args.nsys > 1);
+  tile_select(ctx, trunc, rows, precision, args);
   if (precision == 2 || (precision == 1 && args.x32 == nullptr)) {
     // per-sphere source records (FP32, or the double-float hi/lo pair), once per pass,
     // so that the pair loop touches no FP64
@@ -192,10 +248,16 @@ const double* self_tab(int trunc) { return trunc == 2 ? gbi_t2_self : trunc == 3
 // small kernels
 // ---------------------------------------------------------------------------------
 
-__global__ void k_positions(int N, const double* __restrict__ R, float4* hi, float4* lo, dpos4* p64) {
+// non-finite inputs: any NaN or infinity among v0..v2 sets *bad (if given)
+__device__ __forceinline__ void flag_nonfinite(int* bad, double v0, double v1, double v2) {
+  if (bad != nullptr && !(isfinite(v0) && isfinite(v1) && isfinite(v2))) atomicOr(bad, 1);
+}
+
+__global__ void k_positions(int N, const double* __restrict__ R, float4* hi, float4* lo, dpos4* p64, int* bad) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
   const double x = R[3 * n], y = R[3 * n + 1], z = R[3 * n + 2];
+  flag_nonfinite(bad, x, y, z);
   const float hx = float(x), hy = float(y), hz = float(z);
   hi[n] = make_float4(hx, hy, hz, 0.f);
   lo[n] = make_float4(float(x - double(hx)), float(y - double(hy)), float(z - double(hz)), 0.f);
@@ -204,11 +266,13 @@ __global__ void k_positions(int N, const double* __restrict__ R, float4* hi, flo
 
 // F^(1) = -F^e and F^(21) = -T^e/a in internal coordinates: xF[6][N]
 __global__ void k_pack_lower(int N, double a, double c2a, const double* __restrict__ Fe,
-                             const double* __restrict__ Te, double* xF) {
+                             const double* __restrict__ Te, double* xF, int* bad) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
   const double* f = Fe + 3 * n;
   const double* t = Te + 3 * n;
+  flag_nonfinite(bad, f[0], f[1], f[2]);
+  flag_nonfinite(bad, t[0], t[1], t[2]);
   xF[0 * N + n] = -f[1];
   xF[1 * N + n] = -f[2];
   xF[2 * N + n] = -f[0];
@@ -219,10 +283,11 @@ __global__ void k_pack_lower(int N, double a, double c2a, const double* __restri
 
 // packed [N][h] -> internal component-major [h][N] times scale * mult
 __global__ void k_pack_higher(int N, int h, const double* __restrict__ VH, Scales sc, double mult,
-                              double* out) {
+                              double* out, int* bad) {
   const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (i >= (size_t)N * h) return;
   const int n = int(i / h), p = int(i - (size_t)n * h);
+  flag_nonfinite(bad, VH[i], 0.0, 0.0);
   out[(size_t)p * N + n] = mult * sc.v[p] * VH[i];
 }
 
@@ -237,9 +302,11 @@ __global__ void k_unpack_higher(int N, int h, const double* __restrict__ x, Scal
 // V = V^a + (1s part), Omega = Omega^a + (2a part)/(c_2a 2a)
 __global__ void k_finalize_lower(int N, double a, double c2a, const double* __restrict__ xVL,
                                  const double* __restrict__ Va, const double* __restrict__ Oa,
-                                 double* V, double* Om) {
+                                 double* V, double* Om, int* bad) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
+  flag_nonfinite(bad, Va[3 * n], Va[3 * n + 1], Va[3 * n + 2]);
+  flag_nonfinite(bad, Oa[3 * n], Oa[3 * n + 1], Oa[3 * n + 2]);
   const double f = 1.0 / (c2a * 2.0 * a);
   V[3 * n + 0] = Va[3 * n + 0] + xVL[2 * N + n];
   V[3 * n + 1] = Va[3 * n + 1] + xVL[0 * N + n];
@@ -278,9 +345,9 @@ gbi_status setup_call(gbi_ctx* ctx, Setup& s, int N, int trunc, double a, double
   return GBI_OK;
 }
 
-gbi_status launch_positions(gbi_ctx* ctx, const Setup& s, const double* R) {
+gbi_status launch_positions(gbi_ctx* ctx, const Setup& s, const double* R, int* bad) {
   k_positions<<<grid1(s.N), 256, 0, ctx->stream>>>(s.N, R, P<float4>(ctx->pos_hi), P<float4>(ctx->pos_lo),
-                                                   P<dpos4>(ctx->pos64));
+                                                   P<dpos4>(ctx->pos64), bad);
   ++ctx->launches;
   GBI_CHECK(cudaGetLastError());
   return GBI_OK;
@@ -315,6 +382,11 @@ PairArgs pair_args(const Setup& s, const double* x, double* y, double alpha, dou
   p.sys_flag_stride = 0;
   p.nsys = 1;
   p.pdl = 0;
+  p.tile_part = nullptr;
+  p.tile_cnt = nullptr;
+  p.tile_P = p.tile_G = p.tile_maxseg = 0;
+  p.err = nullptr;
+  p.wait_limit = 0;
   return p;
 }
 

@@ -30,6 +30,9 @@ struct gbi_ctx {
   gbi::Buf pos_hi, pos_lo, pos64;                // centres: hi / lo floats, FP64 copy
   gbi::Buf b, xQ, r, delta, krylov, w, xVL, minr2, x32, trapbuf, gstate;   // solve workspace
   gbi::Buf boff, bsys;                           // system offsets / ids of the current batch
+  gbi::Buf tile, tilecnt;                        // tiled pair passes: partial sums, arrival counters
+  long long wait_limit = 1ll << 24;              // try_wait rounds of a tiled pass's stage waits
+                                                 // (kTileWaitLimit; gbi_set_wait_limit)
   int single_N = -1;                             // boff / bsys hold one system of this many spheres
   const void* single_off = nullptr;              // ... in these buffers
   const void* single_sys = nullptr;
@@ -154,6 +157,18 @@ cudaError_t launch_records(bool dfl, int N, int nc, const double* x, const int* 
                            const ColScale& cs, float* rec, cudaStream_t stream);
 int ncols_of(int trunc, int cols);
 cudaError_t run_pairs(gbi_ctx* ctx, int trunc, int rows, int cols, int precision, const PairArgs& args_in);
+// ctx->minr2 holds four words: [0] smallest r^2 (float bits) of the overlap guard, [1] set
+// by a tiled pair pass whose stage wait gave up, [2] non-finite solve input.  Allocated
+// (cleared) on first use.
+gbi_status status_words(gbi_ctx* ctx);
+int* pass_error_word(gbi_ctx* ctx);
+// [2]: set by the input-packing kernels of a solve when an input is NaN or infinite
+int* input_error_word(gbi_ctx* ctx);
+// clear the error word and the tiled passes' counters after a pass gave up
+gbi_status pass_error_reset(gbi_ctx* ctx);
+struct TilePlan;
+// scratch of a tiled pass over N spheres with these rows in this precision
+gbi_status tile_reserve(gbi_ctx* ctx, int trunc, int rows, int precision, int N, TilePlan* out);
 cudaError_t run_trap(gbi_ctx* ctx, const TrapArgs& t, int precision);
 int d_of(int trunc);
 const double* scale_tab(int trunc);
@@ -164,13 +179,13 @@ struct Scales {
 };
 
 __global__ void k_pack_lower(int N, double a, double c2a, const double* __restrict__ Fe,
-                             const double* __restrict__ Te, double* xF);
+                             const double* __restrict__ Te, double* xF, int* bad);
 __global__ void k_pack_higher(int N, int h, const double* __restrict__ VH, Scales sc, double mult,
-                              double* out);
+                              double* out, int* bad);
 __global__ void k_unpack_higher(int N, int h, const double* __restrict__ x, Scales sc, double* QH);
 __global__ void k_finalize_lower(int N, double a, double c2a, const double* __restrict__ xVL,
                                  const double* __restrict__ Va, const double* __restrict__ Oa,
-                                 double* V, double* Om);
+                                 double* V, double* Om, int* bad);
 
 inline unsigned grid1(size_t n, int bs = 256) { return unsigned((n + bs - 1) / bs); }
 
@@ -189,7 +204,7 @@ struct Setup {
 gbi_status setup_call(gbi_ctx* ctx, Setup& s, int N, int trunc, double a, double eta, const double* R,
                       bool launch_positions = true);
 // the centres of R as float hi / lo and FP64 copies (what setup_call launches)
-gbi_status launch_positions(gbi_ctx* ctx, const Setup& s, const double* R);
+gbi_status launch_positions(gbi_ctx* ctx, const Setup& s, const double* R, int* bad = nullptr);
 PairArgs pair_args(const Setup& s, const double* x, double* y, double alpha, double beta, int add_self,
                    const Scales& colscale, int col0);
 
@@ -223,7 +238,7 @@ struct DSolve {
   int ifs;                // sweeps that ran an inner solve
   int first, notfirst;    // the current inner solve is in its first cycle / past it
   int overlap;            // the overlap guard stopped the solve
-  int pad;
+  int bad_input;          // an input was NaN or infinite: the solve stopped
   double rel_max;         // largest final relative residual over the systems
 };
 

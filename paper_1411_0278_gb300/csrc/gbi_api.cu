@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "ctx.cuh"
+#include "pair_tile.cuh"
 
 namespace gbi {
 namespace {
@@ -153,8 +154,25 @@ gbi_status tune_impl(gbi_ctx* ctx, int trunc, int nsys, const int* offsets, int 
     pa.x32 = rec;
     int best = 0;
     float best_ms = 0.f;
-    for (int w = 2; w <= max_wpt(trunc, ps.precision) && e == cudaSuccess; w *= 2) {
+    // candidates: the tiled form (1, one system only) and 2, 4, ... warps per target of
+    // the streaming form
+    std::vector<int> cand;
+    if (!batched) cand.push_back(kFormTile);
+    for (int w = 2; w <= max_wpt(trunc, ps.precision); w *= 2) cand.push_back(w);
+    for (const int w : cand) {
+      if (e != cudaSuccess) break;
       pa.wpt = w;
+      if (balanced_form(w)) {
+        TilePlan t;
+        if (tile_reserve(ctx, trunc, ps.rows, ps.precision, Ntot, &t) != GBI_OK) continue;
+        pa.tile_part = ctx->tile.p;
+        pa.tile_cnt = P<unsigned int>(ctx->tilecnt);
+        pa.tile_P = t.P;
+        pa.tile_G = t.G;
+        pa.tile_maxseg = t.maxseg;
+        pa.err = pass_error_word(ctx);
+        pa.wait_limit = ctx->wait_limit;
+      }
       e = launch_pairs(trunc, ps.rows, ps.cols, ps.precision, pa, ctx->stream);   // warm-up
       if (e == cudaSuccess) e = cudaEventRecord(e0, ctx->stream);
       for (int r = 0; r < reps && e == cudaSuccess; ++r)
@@ -214,7 +232,8 @@ gbi_status gbi_destroy(gbi_ctx* ctx) {
                  &ctx->hOm, &ctx->hQH, &ctx->mlp_th, &ctx->mlp_m, &ctx->mlp_v, &ctx->mlp_thq, &ctx->mlp_pk,
                  &ctx->mlp_grad, &ctx->mlp_pk_tc, &ctx->mlp_err, &ctx->nb_cnt, &ctx->nb_start, &ctx->nb_tg, &ctx->nb_sr, &ctx->nb_scan,
                  &ctx->cell_of, &ctx->cell_cnt, &ctx->cell_start, &ctx->cell_fill, &ctx->cell_items, &ctx->nb_aux,
-                 &ctx->mf_F, &ctx->mf_FR, &ctx->mf_lab, &ctx->mf_dO, &ctx->mf_part, &ctx->mf_loss, &ctx->dsolve};
+                 &ctx->mf_F, &ctx->mf_FR, &ctx->mf_lab, &ctx->mf_dO, &ctx->mf_part, &ctx->mf_loss, &ctx->dsolve,
+                 &ctx->tile, &ctx->tilecnt};
   for (Buf* b : bufs)
     if (b->p) cudaFree(b->p);
   drain_profile(ctx);
@@ -338,9 +357,9 @@ gbi_status gbi_batch_superpose(gbi_ctx* ctx, const gbi_params* prm, int nsys, co
   double* xQH = P<double>(ctx->xQ) + (size_t)6 * N;
   Scales oneb;   // one-body Q^H = -8 pi eta a V^H / g, in internal coordinates
   for (int i = 0; i < 54; ++i) oneb.v[i] = (i < h) ? s.scale.v[6 + i] * s.a / s.selfg.v[6 + i] : 1.0;
-  k_pack_lower<<<grid1(N), 256, 0, ctx->stream>>>(N, s.a, s.scale.v[3], Fe, Te, xF);
+  k_pack_lower<<<grid1(N), 256, 0, ctx->stream>>>(N, s.a, s.scale.v[3], Fe, Te, xF, nullptr);
   ++ctx->launches;
-  k_pack_higher<<<grid1(nh), 256, 0, ctx->stream>>>(N, h, VH, oneb, -8.0 * kPi * s.eta, xQH);
+  k_pack_higher<<<grid1(nh), 256, 0, ctx->stream>>>(N, h, VH, oneb, -8.0 * kPi * s.eta, xQH, nullptr);
   ++ctx->launches;
   PairArgs p = pair_args(s, P<double>(ctx->xQ), P<double>(ctx->xVL), -1.0 / (8.0 * kPi * s.eta), 0.0, 1, s.ones,
                          0);
@@ -349,7 +368,7 @@ gbi_status gbi_batch_superpose(gbi_ctx* ctx, const gbi_params* prm, int nsys, co
   p.nsys = B.S;
   GBI_CHECK(run_pairs(ctx, s.trunc, SET_L, SET_ALL, prm->precision == 3 ? 1 : prm->precision, p));
   k_finalize_lower<<<grid1(N), 256, 0, ctx->stream>>>(N, s.a, s.scale.v[3], P<double>(ctx->xVL), Va, Oa, V,
-                                                      Omega);
+                                                      Omega, nullptr);
   ++ctx->launches;
   GBI_CHECK(cudaGetLastError());
   return GBI_OK;
@@ -387,15 +406,15 @@ gbi_status gbi_superpose(gbi_ctx* ctx, const gbi_params* prm, int N, const doubl
   double* xQH = P<double>(ctx->xQ) + (size_t)6 * N;
   Scales oneb;   // one-body Q^H = -8 pi eta a V^H / g, in internal coordinates
   for (int i = 0; i < 54; ++i) oneb.v[i] = (i < h) ? s.scale.v[6 + i] * s.a / s.selfg.v[6 + i] : 1.0;
-  k_pack_lower<<<grid1(N), 256, 0, ctx->stream>>>(N, s.a, s.scale.v[3], Fe, Te, xF);
+  k_pack_lower<<<grid1(N), 256, 0, ctx->stream>>>(N, s.a, s.scale.v[3], Fe, Te, xF, nullptr);
   ++ctx->launches;
-  k_pack_higher<<<grid1(nh), 256, 0, ctx->stream>>>(N, h, VH, oneb, -8.0 * kPi * s.eta, xQH);
+  k_pack_higher<<<grid1(nh), 256, 0, ctx->stream>>>(N, h, VH, oneb, -8.0 * kPi * s.eta, xQH, nullptr);
   ++ctx->launches;
   PairArgs p = pair_args(s, P<double>(ctx->xQ), P<double>(ctx->xVL), -1.0 / (8.0 * kPi * s.eta), 0.0, 1, s.ones,
                          0);
   GBI_CHECK(run_pairs(ctx, s.trunc, SET_L, SET_ALL, prm->precision == 3 ? 1 : prm->precision, p));
   k_finalize_lower<<<grid1(N), 256, 0, ctx->stream>>>(N, s.a, s.scale.v[3], P<double>(ctx->xVL), Va, Oa, V,
-                                                      Omega);
+                                                      Omega, nullptr);
   ++ctx->launches;
   GBI_CHECK(cudaGetLastError());
   return GBI_OK;
@@ -510,10 +529,32 @@ gbi_status gbi_tune(gbi_ctx* ctx, int trunc, int nsys, const int* offsets, int r
 }
 
 gbi_status gbi_set_wpt(gbi_ctx* ctx, int wpt) {
-  if (!ctx || !(wpt == 0 || wpt == 2 || wpt == 4 || wpt == 8 || wpt == 16)) return GBI_ERR_ARG;
+  if (!ctx || !(wpt == 0 || wpt == 1 || wpt == 2 || wpt == 4 || wpt == 8 || wpt == 16)) return GBI_ERR_ARG;
   ctx->force_wpt = wpt;
   ++ctx->wpt_gen;
   return GBI_OK;
+}
+
+gbi_status gbi_set_wait_limit(gbi_ctx* ctx, long long rounds) {
+  if (!ctx || rounds < -1) return GBI_ERR_ARG;
+  ctx->wait_limit = rounds == -1 ? kTileWaitLimit : rounds;
+  return GBI_OK;
+}
+
+gbi_status gbi_pass_status(gbi_ctx* ctx) {
+  if (!ctx) return GBI_ERR_ARG;
+  cudaSetDevice(ctx->device);
+  if (ctx->minr2.p == nullptr) {
+    GBI_CHECK(cudaStreamSynchronize(ctx->stream));
+    return GBI_OK;
+  }
+  int word = 0;
+  GBI_CHECK(cudaMemcpyAsync(&word, pass_error_word(ctx), sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  GBI_CHECK(cudaStreamSynchronize(ctx->stream));
+  if (word == 0) return GBI_OK;
+  GBI_TRY(pass_error_reset(ctx));
+  GBI_CHECK(cudaStreamSynchronize(ctx->stream));
+  return GBI_ERR_TIMEOUT;
 }
 
 int gbi_pass_wpt(gbi_ctx* ctx, int trunc, int rows, int cols, int precision, int N, int batched) {
@@ -521,7 +562,7 @@ int gbi_pass_wpt(gbi_ctx* ctx, int trunc, int rows, int cols, int precision, int
   if (precision == 0) return 0;
   if (precision != 1 && precision != 2) return -1;
   const int req = ctx->force_wpt > 0 ? ctx->force_wpt : ctx->tuned_wpt(trunc, rows, cols, precision, N, batched != 0);
-  return stream_wpt(trunc, precision, N, req);
+  return stream_wpt(trunc, precision, N, req, batched != 0);
 }
 
 gbi_status gbi_set_profiling(gbi_ctx* ctx, int on) {

@@ -57,8 +57,17 @@ struct PairArgs {
   const int* sys_flag;
   int sys_flag_stride;
   int nsys;              // systems in the batch (<= 1: every target's sources are [0, N))
-  int wpt;               // warps per target of the FP32 / double-float kernel (0: default)
+  int wpt;               // warps per target of the FP32 / double-float kernel (0: default;
+                         // 1: the tiled form of pair_tile.cuh, single systems only)
   int pdl;               // launch with programmatic dependent launch (see launch_pdl)
+  // tiled form: partial row blocks, one arrival counter per group of 32 targets (zero
+  // between launches), the plan (blocks, groups, partial slots per block), the word that
+  // records a stage wait that gave up, and the limit of that wait in try_wait rounds
+  void* tile_part;
+  unsigned int* tile_cnt;
+  int tile_P, tile_G, tile_maxseg;
+  int* err;
+  long long wait_limit;
 };
 
 // Programmatic dependent launch: with pdl set the kernel's blocks may be scheduled while
@@ -67,11 +76,12 @@ struct PairArgs {
 // returns once all the previous kernel's memory operations are visible, so only block
 // scheduling overlaps, never computation.
 template <typename... K, typename... A>
-inline cudaError_t launch_pdl(bool pdl, dim3 grid, dim3 block, cudaStream_t st, void (*kernel)(K...), A&&... args) {
+inline cudaError_t launch_pdl_smem(bool pdl, dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                                   void (*kernel)(K...), A&&... args) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = grid;
   cfg.blockDim = block;
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -79,6 +89,10 @@ inline cudaError_t launch_pdl(bool pdl, dim3 grid, dim3 block, cudaStream_t st, 
   cfg.attrs = pdl ? at : nullptr;
   cfg.numAttrs = pdl ? 1 : 0;
   return cudaLaunchKernelEx(&cfg, kernel, static_cast<A&&>(args)...);
+}
+template <typename... K, typename... A>
+inline cudaError_t launch_pdl(bool pdl, dim3 grid, dim3 block, cudaStream_t st, void (*kernel)(K...), A&&... args) {
+  return launch_pdl_smem(pdl, grid, block, 0, st, kernel, static_cast<A&&>(args)...);
 }
 
 #ifdef __CUDACC__
@@ -92,12 +106,18 @@ inline int rec_floats(int nc, bool df) { return ((nc + 3) & ~3) * (df ? 2 : 1); 
 // would cap the heavier forms (l <= 4, double-float) at 128 registers and spill.
 inline int max_wpt(int trunc, int precision) { return (trunc == 4 || precision == 2) ? 8 : 16; }
 
+// Code of the tiled form of pair_tile.cuh (lanes are targets; single systems only).
+constexpr int kFormTile = 1;
+inline bool balanced_form(int w) { return w == kFormTile; }
+
 // Warps per target of the FP32 / double-float pair kernel: the requested value (2, 4,
-// 8 or 16), else enough warps to cover 152 SMs at small N and fewer (less reduction
-// work per target) once the N targets alone fill the GPU; capped by max_wpt.
-inline int stream_wpt(int trunc, int precision, int N, int requested) {
+// 8 or 16; 1 selects the tiled form, which serves one system only), else
+// enough warps to cover 152 SMs at small N and fewer (less reduction work per target)
+// once the N targets alone fill the GPU; capped by max_wpt.
+inline int stream_wpt(int trunc, int precision, int N, int requested, bool batched = false) {
   const int d = N >= 8192 ? 2 : (N >= 4096 ? 4 : (N >= 1024 ? 8 : 16));
-  const int w = requested > 0 ? requested : d;
+  if (balanced_form(requested) && !batched && N > 1) return requested;
+  const int w = (requested > 1 && !balanced_form(requested)) ? requested : d;
   const int cap = max_wpt(trunc, precision);
   return w < cap ? w : cap;
 }

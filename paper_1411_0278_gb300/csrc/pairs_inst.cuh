@@ -2,6 +2,7 @@
 #pragma once
 
 #include "pair_kernel.cuh"
+#include "pair_tile.cuh"
 
 namespace gbi {
 
@@ -34,6 +35,31 @@ cudaError_t launch_pairs_tt(int rows, int cols, const PairArgs& args, cudaStream
     // cap), 8 for l <= 4 and double-float; stream_wpt keeps WPT within the same bound
     constexpr bool DF = std::is_same<T, df>::value;
     constexpr int WARPS_SM = (TRN == 4 || DF) ? 8 : 16;
+    if (args.wpt == kFormTile) {
+      // tiled form (pair_tile.cuh): the caller filled the plan and scratch of PairArgs
+#define GBI_T(RV, CV)                                                                              \
+  if (rows == RV && cols == CV) {                                                                  \
+    constexpr size_t smem = tile_smem_bytes<TRN, RV, CV, T>();                                     \
+    static bool attr = false;                                                                      \
+    if (!attr) {                                                                                   \
+      const cudaError_t ea = cudaFuncSetAttribute(pair_tile_kernel<TRN, RV, CV, T>,                \
+                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,     \
+                                                  int(smem));                                      \
+      if (ea != cudaSuccess) return ea;                                                            \
+      attr = true;                                                                                 \
+    }                                                                                              \
+    return launch_pdl_smem(args.pdl != 0, dim3(args.tile_P), dim3(TileShape<T, TRN>::WARPS * 32), smem, \
+                           stream, pair_tile_kernel<TRN, RV, CV, T>, args);                        \
+  }
+      GBI_T(SET_H, SET_L)
+      GBI_T(SET_H, SET_H)
+      GBI_T(SET_L, SET_ALL)
+      if constexpr (FULL) {
+        GBI_T(SET_ALL, SET_ALL)
+      }
+#undef GBI_T
+      return cudaErrorInvalidValue;
+    }
     const int wpt = stream_wpt(TRN, DF ? 2 : 1, N, args.wpt);
 #define GBI_S(RV, CV, WPT)                                                                         \
   if (rows == RV && cols == CV && wpt == WPT) {                                                    \

@@ -1292,13 +1292,19 @@ __global__ void gk_zero(double* __restrict__ dst, size_t n) {
     dst[i] = 0.0;
 }
 
-// overlap guard: a centre distance below min_sep a stops every system (the host reports
-// GBI_ERR_OVERLAP after the graph)
-__global__ void gk_overlap(GPtr p, const unsigned int* __restrict__ minr2, double a, double min_sep, DSolve* d) {
+// input guard: a centre distance below min_sep a (min_sep > 0) or a NaN / infinite input
+// stops every system (the host reports GBI_ERR_OVERLAP or GBI_ERR_ARG after the graph)
+__global__ void gk_guard(GPtr p, const unsigned int* __restrict__ minr2, const int* __restrict__ bad, double a,
+                         double min_sep, DSolve* d) {
   const float mr2 = __uint_as_float(*minr2);
-  if (!(sqrt(double(mr2)) / a < min_sep)) return;
+  const bool ov = min_sep > 0 && sqrt(double(mr2)) / a < min_sep;
+  const bool bi = *bad != 0;
+  if (!ov && !bi) return;
   for (int s = threadIdx.x; s < p.S; s += blockDim.x) p.st[s].enabled = 0;
-  if (threadIdx.x == 0) d->overlap = 1;
+  if (threadIdx.x == 0) {
+    if (ov) d->overlap = 1;
+    if (bi) d->bad_input = 1;
+  }
 }
 
 // the sweep loop runs while some system still needs a correction
@@ -1497,7 +1503,7 @@ gbi_status solve_core(gbi_ctx* ctx, const gbi_params* prm, const Batch& B, const
   GBI_TRY(ensure(ctx, ctx->r, sizeof(double) * nh));
   GBI_TRY(ensure(ctx, ctx->delta, sizeof(double) * nh));
   GBI_TRY(ensure(ctx, ctx->xVL, sizeof(double) * 6 * N));
-  GBI_TRY(ensure(ctx, ctx->minr2, sizeof(unsigned int)));
+  GBI_TRY(status_words(ctx));
   GBI_TRY(ensure(ctx, ctx->gstate, sizeof(double) * gstate_doubles(restart, S, arnoldi_chunks(S, h))));
   double* xF = P<double>(ctx->xQ);              // rows 0..5 of the full vector
   double* xQH = P<double>(ctx->xQ) + (size_t)6 * N;
@@ -1528,9 +1534,14 @@ gbi_status solve_core(gbi_ctx* ctx, const gbi_params* prm, const Batch& B, const
   unsigned int* hbits = reinterpret_cast<unsigned int*>(ctx->hs + hs_rec + sizeof(DSolve));
 
   // the caller's inputs -> internal coordinates: F^L and b = -8 pi eta V^H
+  int* bad_in = input_error_word(ctx);
+  // centres and packed inputs; a NaN or infinite value in R, V^H, F^e or T^e (or V^a,
+  // Omega^a, read at the end) sets the input word, cleared here first
   auto pack_inputs = [&]() -> gbi_status {
-    k_pack_lower<<<grid1(N), 256, 0, ctx->stream>>>(N, s.a, c2a, Fe, Te, xF);
-    k_pack_higher<<<grid1(nh), 256, 0, ctx->stream>>>(N, h, VH, hscale, -8.0 * kPi * s.eta, b);
+    GBI_CHECK(cudaMemsetAsync(bad_in, 0, sizeof(int), ctx->stream));
+    GBI_TRY(launch_positions(ctx, s, R, bad_in));
+    k_pack_lower<<<grid1(N), 256, 0, ctx->stream>>>(N, s.a, c2a, Fe, Te, xF, bad_in);
+    k_pack_higher<<<grid1(nh), 256, 0, ctx->stream>>>(N, h, VH, hscale, -8.0 * kPi * s.eta, b, bad_in);
     ctx->launches += 2;
     GBI_CHECK(cudaGetLastError());
     return GBI_OK;
@@ -1553,7 +1564,7 @@ gbi_status solve_core(gbi_ctx* ctx, const gbi_params* prm, const Batch& B, const
   };
   // internal coordinates -> the caller's V, Omega (and Q^H)
   auto unpack_outputs = [&]() -> gbi_status {
-    k_finalize_lower<<<grid1(N), 256, 0, ctx->stream>>>(N, s.a, c2a, P<double>(ctx->xVL), Va, Oa, V, Omega);
+    k_finalize_lower<<<grid1(N), 256, 0, ctx->stream>>>(N, s.a, c2a, P<double>(ctx->xVL), Va, Oa, V, Omega, bad_in);
     ++ctx->launches;
     if (QH) {
       k_unpack_higher<<<grid1(nh), 256, 0, ctx->stream>>>(N, h, xQH, hscale, QH);
@@ -1593,7 +1604,7 @@ gbi_status solve_core(gbi_ctx* ctx, const gbi_params* prm, const Batch& B, const
       GBI_TRY(ensure(ctx, ctx->x32, x32b));
     }
     const void* ptrs[] = {B.sys, B.off, ctx->pos_hi.p, ctx->pos_lo.p, ctx->pos64.p, ctx->xQ.p, ctx->b.p, ctx->r.p, ctx->delta.p, ctx->xVL.p, ctx->minr2.p,
-                          ctx->krylov.p, ctx->w.p, ctx->x32.p, ctx->gstate.p, ctx->dsolve.p};
+                          ctx->krylov.p, ctx->w.p, ctx->x32.p, ctx->gstate.p, ctx->dsolve.p, ctx->tile.p, ctx->tilecnt.p};
     std::vector<long long> key = {N, S, pairs_all, max_system(B), prm->trunc, prm->precision, restart, max_iter,
                                   max_refine,
                                   bits(rtol), bits(inner), bits(prm->min_sep), bits(prm->a), bits(prm->eta),
@@ -1630,7 +1641,6 @@ gbi_status solve_core(gbi_ctx* ctx, const gbi_params* prm, const Batch& B, const
               GBI_CHECK(cudaMemsetAsync(gp.cnt, 0, sizeof(unsigned int) * (S + 2), ctx->stream));
               if (hooks != nullptr) {
                 GBI_TRY(hooks->before());
-                GBI_TRY(launch_positions(ctx, s, R));
                 GBI_TRY(pack_inputs());
               }
               GBI_TRY(rhs_pass());
@@ -1642,10 +1652,9 @@ gbi_status solve_core(gbi_ctx* ctx, const gbi_params* prm, const Batch& B, const
                 bk_norm_then<<<dim3(S, gp.CH), 256, 0, ctx->stream>>>(b, N, h, B.off, gp, 2, nc);
                 ++ctx->launches;
               }
-              if (prm->min_sep > 0 && pairs_all > 0) {
-                gk_overlap<<<1, 256, 0, ctx->stream>>>(gp, P<unsigned int>(ctx->minr2), s.a, prm->min_sep, d);
-                ++ctx->launches;
-              }
+              gk_guard<<<1, 256, 0, ctx->stream>>>(gp, P<unsigned int>(ctx->minr2), bad_in, s.a,
+                                                   pairs_all > 0 ? prm->min_sep : 0.0, d);
+              ++ctx->launches;
               // sweep 0: the residual is b
               GBI_CHECK(cudaMemcpyAsync(r, b, sizeof(double) * nh, cudaMemcpyDeviceToDevice, ctx->stream));
               GBI_CHECK(cudaMemsetAsync(dl, 0, sizeof(double) * nh, ctx->stream));
@@ -1722,15 +1731,19 @@ gbi_status solve_core(gbi_ctx* ctx, const gbi_params* prm, const Batch& B, const
     if (ctx->solve_exec != nullptr && key == ctx->solve_key) {
       DSolve* d = P<DSolve>(ctx->dsolve);
       if (hooks == nullptr) {
-        GBI_TRY(launch_positions(ctx, s, R));
         GBI_TRY(pack_inputs());
       }
       GBI_CHECK(cudaGraphLaunch(ctx->solve_exec, ctx->stream));
       ++ctx->solve_replays;
       if (hooks == nullptr) GBI_TRY(unpack_outputs());
       GBI_CHECK(cudaMemcpyAsync(hrec, d, sizeof(DSolve), cudaMemcpyDeviceToHost, ctx->stream));
-      GBI_CHECK(cudaMemcpyAsync(hbits, ctx->minr2.p, sizeof(unsigned int), cudaMemcpyDeviceToHost, ctx->stream));
+      GBI_CHECK(cudaMemcpyAsync(hbits, ctx->minr2.p, 3 * sizeof(unsigned int), cudaMemcpyDeviceToHost, ctx->stream));
       GBI_CHECK(cudaStreamSynchronize(ctx->stream));
+      if (hbits[1] != 0) {
+        GBI_TRY(pass_error_reset(ctx));
+        return GBI_ERR_TIMEOUT;
+      }
+      if (hbits[2] != 0 || hrec->bad_input) return GBI_ERR_ARG;
       const DSolve& hd = *hrec;
       ctx->launches += ctx->solve_own[0] + (long long)hd.refinements * ctx->solve_own[1] +
                        (long long)hd.ifs * ctx->solve_own[2] + hd.cycles * ctx->solve_own[3] +
@@ -1751,17 +1764,27 @@ gbi_status solve_core(gbi_ctx* ctx, const gbi_params* prm, const Batch& B, const
   }
 
   if (hooks != nullptr) GBI_TRY(hooks->before());
-  GBI_TRY(launch_positions(ctx, s, R));
   GBI_TRY(pack_inputs());
   GBI_TRY(rhs_pass());
   (io == 1 ? inf->matvecs_f32 : inf->matvecs_f64) += 1;
   inf->pair_interactions += pairs_all;
+  {
+    // inputs checked (and, with the guard on, the smallest distance) before the GMRES
+    unsigned int bits[3] = {0, 0, 0};
+    GBI_CHECK(cudaMemcpyAsync(bits, ctx->minr2.p, 3 * sizeof(unsigned int), cudaMemcpyDeviceToHost, ctx->stream));
+    GBI_CHECK(cudaStreamSynchronize(ctx->stream));
+    if (bits[1] != 0) {
+      GBI_TRY(pass_error_reset(ctx));
+      return GBI_ERR_TIMEOUT;
+    }
+    if (bits[2] != 0) return GBI_ERR_ARG;
+  }
   if (prm->min_sep > 0) {
-    unsigned int bits = 0;
-    GBI_CHECK(cudaMemcpyAsync(&bits, ctx->minr2.p, sizeof(unsigned int), cudaMemcpyDeviceToHost, ctx->stream));
+    unsigned int bits[2] = {0, 0};
+    GBI_CHECK(cudaMemcpyAsync(bits, ctx->minr2.p, sizeof(unsigned int), cudaMemcpyDeviceToHost, ctx->stream));
     GBI_CHECK(cudaStreamSynchronize(ctx->stream));
     float mr2;
-    std::memcpy(&mr2, &bits, sizeof(float));
+    std::memcpy(&mr2, &bits[0], sizeof(float));
     inf->min_separation = pairs_all > 0 ? std::sqrt(double(mr2)) / s.a : 0.0;
     if (pairs_all > 0 && inf->min_separation < prm->min_sep) return GBI_ERR_OVERLAP;
   }
@@ -1769,7 +1792,7 @@ gbi_status solve_core(gbi_ctx* ctx, const gbi_params* prm, const Batch& B, const
   // initial guess
   bool zero = true;
   if (warm_start) {
-    k_pack_higher<<<grid1(nh), 256, 0, ctx->stream>>>(N, h, QH, hscale, 1.0, xQH);
+    k_pack_higher<<<grid1(nh), 256, 0, ctx->stream>>>(N, h, QH, hscale, 1.0, xQH, bad_in);
     ++ctx->launches;
     zero = false;
   } else {
@@ -1855,15 +1878,18 @@ gbi_status solve_core(gbi_ctx* ctx, const gbi_params* prm, const Batch& B, const
   if (converged && hooks != nullptr) GBI_TRY(hooks->after(nullptr));
   (io == 1 ? inf->matvecs_f32 : inf->matvecs_f64) += 1;
   inf->pair_interactions += pairs_all;
+  unsigned int bits[3] = {0, 0, 0};
+  GBI_CHECK(cudaMemcpyAsync(bits, ctx->minr2.p, 3 * sizeof(unsigned int), cudaMemcpyDeviceToHost, ctx->stream));
+  GBI_CHECK(cudaStreamSynchronize(ctx->stream));
+  if (bits[1] != 0) {
+    GBI_TRY(pass_error_reset(ctx));
+    return GBI_ERR_TIMEOUT;
+  }
+  if (bits[2] != 0) return GBI_ERR_ARG;
   if (prm->min_sep <= 0) {
-    unsigned int bits = 0;
-    GBI_CHECK(cudaMemcpyAsync(&bits, ctx->minr2.p, sizeof(unsigned int), cudaMemcpyDeviceToHost, ctx->stream));
-    GBI_CHECK(cudaStreamSynchronize(ctx->stream));
     float mr2;
-    std::memcpy(&mr2, &bits, sizeof(float));
+    std::memcpy(&mr2, &bits[0], sizeof(float));
     inf->min_separation = pairs_all > 0 ? std::sqrt(double(mr2)) / s.a : 0.0;
-  } else {
-    GBI_CHECK(cudaStreamSynchronize(ctx->stream));
   }
   return converged ? GBI_OK : GBI_ERR_NOT_CONVERGED;
 }

@@ -21,6 +21,7 @@
 // terms, in FP64.
 #include <type_traits>
 
+#include "df.cuh"
 #include "gbi_generated.cuh"
 #include "gbi_internal.cuh"
 
@@ -56,7 +57,8 @@ __global__ void trap_pack(const TrapArgs args, T* __restrict__ rec) {
   for (int i = 0; i < 6; ++i) r[12 + i] = T(sf * s6[i]);
   // V^(32) packed (y, z, x)
   r[18] = T(df * vh[7]); r[19] = T(df * vh[5]); r[20] = T(df * vh[6]);
-  r[21] = 0; r[22] = 0; r[23] = 0;
+  // -T/2 (divided by 8 pi eta) for the rotlet-dipole term of Omega
+  r[21] = T(-0.5 * Tq[0] * inv8pe); r[22] = T(-0.5 * Tq[1] * inv8pe); r[23] = T(-0.5 * Tq[2] * inv8pe);
 }
 
 template <typename T> struct Vec4;
@@ -67,6 +69,71 @@ template <typename T>
 __device__ __forceinline__ T trap_rsqrt(T v) {
   if constexpr (std::is_same<T, float>::value) return rsqrtf(v);
   else return rsqrt(v);
+}
+
+// The pair terms of source j of the tile (sphere m) for the thread's TI targets n0 + t.
+// SELF: the tile may hold one of those targets, which is then skipped.  Each sum is an
+// FMA chain: the rotlet and potential dipole share ri3 (T x rho - d), the torque's own
+// rotlet-dipole term rides on the force rotlet (F x rho - T/2, with -T/2 in the record).
+template <typename T, int TI, bool SELF>
+__device__ __forceinline__ void trap_source(const T* __restrict__ s_rec, int j, int m, int n0, const T* px,
+                                            const T* py, const T* pz, const T* lx, const T* ly, const T* lz, T a2,
+                                            T* v0, T* v1, T* v2, T* w0, T* w1, T* w2) {
+  constexpr bool F32 = std::is_same<T, float>::value;
+  using V4 = typename Vec4<T>::type;
+  const V4* r4 = reinterpret_cast<const V4*>(s_rec + j * kRec);
+  const V4 q0 = r4[0], q1 = r4[1], q2 = r4[2], q3 = r4[3], q4 = r4[4], q5 = r4[5];
+  const T sx = q0.x, sy = q0.y, sz = q0.z, slx = q0.w, sly = q1.x, slz = q1.y;
+  const T Fx = q1.z, Fy = q1.w, Fz = q2.x;
+  const T Tx = q2.y, Ty = q2.z, Tz = q2.w;
+  const T Sxx = q3.x, Sxy = q3.y, Sxz = q3.z, Syy = q3.w, Syz = q4.x, Szz = q4.y;
+  const T dx = q4.z, dy = q4.w, dz = q5.x;
+  const T hx = q5.y, hy = q5.z, hz = q5.w;   // -T/2
+  const T c23 = T(2.0 / 3.0) * a2, c2a = T(-2) * a2, c8a = T(8) * a2, c165 = T(-16.0 / 5.0) * a2;
+#pragma unroll
+  for (int t = 0; t < TI; ++t) {
+    if (SELF && m == n0 + t) continue;
+    T x, y, z;
+    if constexpr (F32) {
+      x = (px[t] - sx) + (lx[t] - slx);
+      y = (py[t] - sy) + (ly[t] - sly);
+      z = (pz[t] - sz) + (lz[t] - slz);
+    } else {
+      x = px[t] - sx;
+      y = py[t] - sy;
+      z = pz[t] - sz;
+    }
+    const T r2 = gbi_fmac(z, z, gbi_fmac(y, y, x * x));
+    const T ri = trap_rsqrt(r2);
+    const T ri2 = ri * ri, ri3 = ri * ri2, ri5 = ri3 * ri2, ri7 = ri5 * ri2;
+    const T rF = gbi_fmac(z, Fz, gbi_fmac(y, Fy, x * Fx));
+    const T Sx = gbi_fmac(Sxz, z, gbi_fmac(Sxy, y, Sxx * x));
+    const T Sy = gbi_fmac(Syz, z, gbi_fmac(Syy, y, Sxy * x));
+    const T Sz = gbi_fmac(Szz, z, gbi_fmac(Syz, y, Sxz * x));
+    const T rSr = gbi_fmac(z, Sz, gbi_fmac(y, Sy, x * Sx));
+    const T rd = gbi_fmac(z, dz, gbi_fmac(y, dy, x * dx));
+    const T rT = gbi_fmac(z, Tz, gbi_fmac(y, Ty, x * Tx));
+    const T c1 = gbi_fmac(c23, ri3, ri);
+    const T t3 = T(3) * ri5;
+    // common radial coefficient of rho in V: RPY + stresslet + dipole
+    const T cx = gbi_fmac(gbi_fmac(c2a, ri5, ri3), rF, gbi_fmac(gbi_fmac(c8a, ri7, -t3), rSr, t3 * rd));
+    const T cs2 = c165 * ri5;
+    // (T x rho - d) and (F x rho - T/2)
+    const T u0 = gbi_fmac(Ty, z, gbi_fmac(-Tz, y, -dx));
+    const T u1 = gbi_fmac(Tz, x, gbi_fmac(-Tx, z, -dy));
+    const T u2 = gbi_fmac(Tx, y, gbi_fmac(-Ty, x, -dz));
+    v0[t] = gbi_fmac(ri3, u0, gbi_fmac(cs2, Sx, gbi_fmac(cx, x, gbi_fmac(c1, Fx, v0[t]))));
+    v1[t] = gbi_fmac(ri3, u1, gbi_fmac(cs2, Sy, gbi_fmac(cx, y, gbi_fmac(c1, Fy, v1[t]))));
+    v2[t] = gbi_fmac(ri3, u2, gbi_fmac(cs2, Sz, gbi_fmac(cx, z, gbi_fmac(c1, Fz, v2[t]))));
+    const T e0 = gbi_fmac(Fy, z, gbi_fmac(-Fz, y, hx));
+    const T e1 = gbi_fmac(Fz, x, gbi_fmac(-Fx, z, hy));
+    const T e2 = gbi_fmac(Fx, y, gbi_fmac(-Fy, x, hz));
+    const T ct = (T(1.5) * ri5) * rT;
+    const T tx = t3 * x, ty = t3 * y, tz = t3 * z;
+    w0[t] = gbi_fmac(ty, Sz, gbi_fmac(-tz, Sy, gbi_fmac(ct, x, gbi_fmac(ri3, e0, w0[t]))));
+    w1[t] = gbi_fmac(tz, Sx, gbi_fmac(-tx, Sz, gbi_fmac(ct, y, gbi_fmac(ri3, e1, w1[t]))));
+    w2[t] = gbi_fmac(tx, Sy, gbi_fmac(-ty, Sx, gbi_fmac(ct, z, gbi_fmac(ri3, e2, w2[t]))));
+  }
 }
 
 // partial[split][n][6] = sum over this split's sources of the pair terms for target n
@@ -81,6 +148,7 @@ __global__ void __launch_bounds__(THREADS) trap_pairs(const TrapArgs args, const
   const int m_begin = blockIdx.y * chunk;
   const int m_end = min(N, m_begin + chunk);
   const T a2 = T(args.a * args.a);
+  const int blk_n0 = blockIdx.x * THREADS * TI, blk_n1 = blk_n0 + THREADS * TI;
 
   T px[TI], py[TI], pz[TI], lx[TI], ly[TI], lz[TI];
   T v0[TI], v1[TI], v2[TI], w0[TI], w1[TI], w2[TI];
@@ -106,52 +174,14 @@ __global__ void __launch_bounds__(THREADS) trap_pairs(const TrapArgs args, const
       for (int i = threadIdx.x; i < len * (kRec / 4); i += THREADS) dst[i] = src[i];
     }
     __syncthreads();
-    for (int j = 0; j < len; ++j) {
-      const V4* r4 = reinterpret_cast<const V4*>(s_rec + j * kRec);
-      const V4 q0 = r4[0], q1 = r4[1], q2 = r4[2], q3 = r4[3], q4 = r4[4], q5 = r4[5];
-      const T sx = q0.x, sy = q0.y, sz = q0.z, slx = q0.w, sly = q1.x, slz = q1.y;
-      const T Fx = q1.z, Fy = q1.w, Fz = q2.x;
-      const T Tx = q2.y, Ty = q2.z, Tz = q2.w;
-      const T Sxx = q3.x, Sxy = q3.y, Sxz = q3.z, Syy = q3.w, Syz = q4.x, Szz = q4.y;
-      const T dx = q4.z, dy = q4.w, dz = q5.x;
-      const int m = base + j;
-#pragma unroll
-      for (int t = 0; t < TI; ++t) {
-        if (m == n0 + t) continue;
-        T x, y, z;
-        if constexpr (F32) {
-          x = (px[t] - sx) + (lx[t] - slx);
-          y = (py[t] - sy) + (ly[t] - sly);
-          z = (pz[t] - sz) + (lz[t] - slz);
-        } else {
-          x = px[t] - sx;
-          y = py[t] - sy;
-          z = pz[t] - sz;
-        }
-        const T r2 = x * x + y * y + z * z;
-        const T ri = trap_rsqrt(r2);
-        const T ri2 = ri * ri, ri3 = ri * ri2, ri5 = ri3 * ri2, ri7 = ri5 * ri2;
-        const T rF = x * Fx + y * Fy + z * Fz;
-        const T c1 = ri + T(2.0 / 3.0) * a2 * ri3;
-        const T c2 = (ri3 - T(2) * a2 * ri5) * rF;
-        const T Sx = Sxx * x + Sxy * y + Sxz * z;
-        const T Sy = Sxy * x + Syy * y + Syz * z;
-        const T Sz = Sxz * x + Syz * y + Szz * z;
-        const T rSr = x * Sx + y * Sy + z * Sz;
-        const T rd = x * dx + y * dy + z * dz;
-        const T rT = x * Tx + y * Ty + z * Tz;
-        // common radial coefficient of rho in V: RPY + stresslet + dipole
-        const T cx = c2 + (T(8) * a2 * ri7 - T(3) * ri5) * rSr + T(3) * ri5 * rd;
-        const T cs2 = T(-16.0 / 5.0) * a2 * ri5;
-        v0[t] += c1 * Fx + cx * x + (Ty * z - Tz * y) * ri3 + cs2 * Sx - ri3 * dx;
-        v1[t] += c1 * Fy + cx * y + (Tz * x - Tx * z) * ri3 + cs2 * Sy - ri3 * dy;
-        v2[t] += c1 * Fz + cx * z + (Tx * y - Ty * x) * ri3 + cs2 * Sz - ri3 * dz;
-        const T ct = T(1.5) * ri5 * rT;
-        const T t3 = T(3) * ri5;
-        w0[t] += (Fy * z - Fz * y) * ri3 + ct * x - T(0.5) * ri3 * Tx + t3 * (y * Sz - z * Sy);
-        w1[t] += (Fz * x - Fx * z) * ri3 + ct * y - T(0.5) * ri3 * Ty + t3 * (z * Sx - x * Sz);
-        w2[t] += (Fx * y - Fy * x) * ri3 + ct * z - T(0.5) * ri3 * Tz + t3 * (x * Sy - y * Sx);
-      }
+    // only a tile that holds one of this block's targets can hold a thread's own sphere
+    const bool self_tile = base < blk_n1 && base + len > blk_n0;
+    if (self_tile) {
+      for (int j = 0; j < len; ++j) trap_source<T, TI, true>(s_rec, j, base + j, n0, px, py, pz, lx, ly, lz, a2, v0, v1, v2,
+                                                            w0, w1, w2);
+    } else {
+      for (int j = 0; j < len; ++j) trap_source<T, TI, false>(s_rec, j, base + j, n0, px, py, pz, lx, ly, lz, a2, v0, v1, v2,
+                                                             w0, w1, w2);
     }
   }
 #pragma unroll

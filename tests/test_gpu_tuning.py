@@ -63,7 +63,7 @@ def _case(N, trunc, seed):
 @pytest.mark.parametrize("trunc,N", [(2, 333), (3, 150), (4, 61)])
 @pytest.mark.parametrize("rows,cols", [(2, 2), (2, 1), (1, 0)])
 @pytest.mark.parametrize("precision", [1, 2])
-@pytest.mark.parametrize("wpt", [2, 4, 8, 16])
+@pytest.mark.parametrize("wpt", [1, 2, 4, 8, 16])
 def test_every_wpt_matches_oracle(ctx, gbi, trunc, N, rows, cols, precision, wpt):
     R, A4, d = _case(N, trunc, 70 + trunc)
     g = galerkin.self_scalars(trunc, 1.0)
@@ -81,7 +81,7 @@ def test_every_wpt_matches_oracle(ctx, gbi, trunc, N, rows, cols, precision, wpt
     ref = 1.3 * ref + 0.5 * y0
     ctx.set_wpt(wpt)
     used = ctx.pass_wpt(trunc, rows, cols, precision, N)
-    assert used == min(wpt, 8 if (trunc == 4 or precision == 2) else 16)
+    assert used == (1 if wpt == 1 else min(wpt, 8 if (trunc == 4 or precision == 2) else 16))
     yd = dev(y0)
     ctx.apply(N, trunc, 1.0, rows, cols, precision, dev(R), dev(x), yd, 1.3, 0.5, add_self)
     torch.cuda.synchronize()
@@ -102,9 +102,9 @@ def test_tune_picks_valid_choices_and_keeps_results(ctx, gbi):
     chosen = ctx.tune(trunc, [0, N], reps=2)
     assert len(chosen) == 6
     fp32_cap = 8 if trunc == 4 else 16
-    assert chosen[0] in (2, 4, 8, 16) and chosen[0] <= fp32_cap
-    assert all(w in (2, 4, 8) for w in chosen[1:4])
-    assert all(w in (2, 4, 8, 16) and w <= fp32_cap for w in chosen[4:])
+    assert chosen[0] in (1, 2, 4, 8, 16) and chosen[0] <= fp32_cap
+    assert all(w in (1, 2, 4, 8) for w in chosen[1:4])
+    assert all(w in (1, 2, 4, 8, 16) and w <= fp32_cap for w in chosen[4:])
     assert ctx.pass_wpt(trunc, 2, 2, 1, N) == chosen[0]
     assert ctx.pass_wpt(trunc, 2, 2, 2, N) == chosen[1]
     assert ctx.pass_wpt(trunc, 2, 1, 2, N) == chosen[2]
@@ -134,3 +134,52 @@ def test_tune_rejects_bad_layouts(ctx, gbi):
             ctx.tune(2, offs)
     with pytest.raises(gbi.GbiError):
         ctx.set_wpt(3)
+
+
+@pytest.mark.parametrize("trunc,N", [(2, 2), (2, 33), (3, 64), (3, 97), (2, 1024), (3, 517), (3, 1300)])
+@pytest.mark.parametrize("precision", [1, 2])
+def test_tiled_form_partitions(ctx, gbi, trunc, N, precision):
+    """The tiled form splits (group of 32 targets, source) units evenly over the blocks;
+    whatever the number of groups, partial groups and block ranges that cross groups, it
+    sums the same pairs as the streaming form (to rounding) on three launches in a row
+    (its arrival counters must be back at zero after each)."""
+    s = workloads.small_cloud(N, 90 + N, phi=0.05)
+    R = dev(s["R"])
+    d = tensors.ModeBasis(trunc).d
+    h = d - 6
+    rng = np.random.default_rng(N)
+    x = dev(rng.normal(size=(h, N)))
+    ctx.set_wpt(4)
+    y_ref = torch.zeros((h, N), dtype=torch.float64, device="cuda")
+    ctx.apply(N, trunc, 1.0, 2, 2, precision, R, x, y_ref, 1.0, 0.0, True)
+    ctx.set_wpt(1)
+    assert ctx.pass_wpt(trunc, 2, 2, precision, N) == 1
+    for _ in range(3):
+        y = torch.full((h, N), 7.0, dtype=torch.float64, device="cuda")
+        ctx.apply(N, trunc, 1.0, 2, 2, precision, R, x, y, 1.0, 0.0, True)
+        torch.cuda.synchronize()
+        assert relerr(y.cpu().numpy(), y_ref.cpu().numpy()) < (2e-6 if precision == 1 else 1e-12)
+    ctx.set_wpt(0)
+
+
+def test_tiled_form_full_size_sampled_rows(ctx, gbi):
+    """N = 1024 at l <= 3 (the solve workload), FP32 H/H pass in the tiled form, against
+    the oracle's dense pair blocks for sampled target spheres."""
+    c = workloads.config2()
+    R = c["R"]
+    N, trunc = len(R), 3
+    d = tensors.ModeBasis(trunc).d
+    h = d - 6
+    rng = np.random.default_rng(5)
+    x = rng.normal(size=(h, N))
+    ctx.set_wpt(1)
+    y = torch.zeros((h, N), dtype=torch.float64, device="cuda")
+    ctx.apply(N, trunc, c["a"], 2, 2, 1, dev(R), dev(x), y, 1.0, 0.0, False)
+    torch.cuda.synchronize()
+    ctx.set_wpt(0)
+    tg = np.array([0, 31, 32, 511, 700, 1023])
+    xf = np.zeros((N, d))
+    xf[:, 6:] = x.T
+    ref = galerkin.apply_offdiag(R, xf, c["a"], trunc, rows=slice(6, d), targets=tg)
+    got = y.cpu().numpy()[:, tg].T
+    assert relerr(got, ref) < 1e-5
