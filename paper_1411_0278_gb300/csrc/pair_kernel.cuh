@@ -500,23 +500,7 @@ __global__ void __launch_bounds__(WPT * 32, MINB) pair_stream_kernel(const PairA
   for (int p = 0; p < NR; ++p) acc[p] = T(0);
   float min_r2 = 3.0e38f;
 
-  constexpr int RECF = 4 * (DF ? 2 * RecShape<S::NC>::NV : RecShape<S::NC>::NV);   // floats per record
   for (int m = src_lo + warp * 32 + lane; m < src_hi; m += WPT * 32) {
-#ifdef GBI_TOUCH
-    {
-      // bring the next iteration's record and centres into L1 while this one computes:
-      // one 4-byte load per 128-byte line they occupy (results unused)
-      const int mn = m + WPT * 32;
-      if (mn < src_hi) {
-        const float* r = args.x32 + (size_t)mn * RECF;
-        float t0, t1, t2, t3;
-        asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(t0) : "l"(r));
-        asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(t1) : "l"(r + RECF - 1));
-        asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(t2) : "l"(&args.pos.hi[mn].x));
-        asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(t3) : "l"(&args.pos.lo[mn].x));
-      }
-    }
-#endif
     if (m == n) continue;
     stream_source<TR, ROWS, COLS, T>(args, rec, th, tl, m, a, acc, min_r2);
   }
