@@ -4,15 +4,17 @@
 Workload (default): N = 1024 active spheres at volume fraction 0.05, truncation
 l <= 3 (25 higher components per sphere), harmonic trap k = 0.01, V^a = 0.1 p,
 V^(2s) = 0.05 (pp - I/3).  One step = trap inputs from (R, p), the full
-traction solve (FP64 right-hand-side pass, restarted GMRES with FP32 pair sums
-and FP64 Arnoldi, FP64 iterative refinement to ||b - A q|| / ||b|| <= 1e-10,
-FP64 output pass) and one forward-Euler update, all inside libgbi.
+traction solve (right-hand-side pass, restarted GMRES with FP32 pair sums and
+FP64 Arnoldi, iterative refinement to ||b - A q|| / ||b|| <= 1e-10, output pass)
+and one forward-Euler update, all inside libgbi.
 
 Metric: pair-interactions/s (ordered pairs summed over every pair pass of the
-step) and solves/s.  Also reported: the roofline of the dominant kernel (event
-timed live in the timed region), the end-to-end number through the host-pointer
-C-ABI call, the N = 10^4 superposition pass, and the FP64 CPU oracle timed on
-a bounded sample on this machine's cores.
+step) and solves/s.  Also reported: the roofline of the dominant kernel, the
+end-to-end number through the host-pointer C-ABI call, every precision mode of
+the same solve with its residual against the FP64 system, the N = 64 FP64
+trajectory (100 re-solved Euler steps), the N = 10^4 superposition trajectory
+(10^4 steps and its steady convective flux), the batched and learned workloads,
+and the FP64 CPU oracle timed on bounded samples on this machine's cores.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun (N > 1) every rank solves its own replica of the workload.
@@ -34,7 +36,7 @@ if ROOT not in sys.path:
 METRIC = "pair-interactions/s & Galerkin solves/s at stated error vs FP64; % FP32 peak"
 UNIT = "pair-interactions/s"
 FP64_NOMINAL_TFLOPS = 1.25          # GB300 FP64 (recipe's nominal figure)
-SMS, FP32_LANES = 152, 128
+FP32_LANES = 128                    # FP32 lanes per SM (Blackwell)
 
 
 def load_peaks():
@@ -46,8 +48,29 @@ def load_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def fp32_alu_peak_tflops(sm_mhz):
-    return SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
+def fp32_alu_peak_tflops(sm_mhz, sms):
+    """FP32 CUDA-core peak: SMs x 128 lanes x 2 flops (FMA) x clock."""
+    return sms * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith("model name"):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -130,6 +153,58 @@ def oracle_pair_rate(R, trunc, a, npairs, seed=0):
     return npairs / dt, dt
 
 
+def oracle_baselines(c1, c2, c3, npairs=12000):
+    """The FP64 oracle, as it stands, on bounded samples of three workloads, on this host's
+    cores: dense pair blocks (the unit of the headline metric), a whole N = 64 dense solve,
+    the N = 1024 dense solve extrapolated from its parts, and the N = 10^4 superposition sum
+    for sampled spheres."""
+    import numpy as np
+
+    from oracle import dynamics, galerkin
+    rate3, dt3 = oracle_pair_rate(c2["R"], c2["trunc"], c2["a"], npairs)
+    trap = lambda c: dict(a=c["a"], eta=c["eta"], k=c["k"], vs=c["vs"], s0=c["s0"], d0=c["d0"])
+    # N = 64, l <= 2: assemble the dense system, LU, outputs
+    dynamics.velocities(c1["R"][:4], c1["p"][:4], trap(c1), c1["trunc"], False)
+    t0 = time.perf_counter()
+    dynamics.velocities(c1["R"], c1["p"], trap(c1), c1["trunc"], False)
+    t1 = time.perf_counter() - t0
+    # N = 1024, l <= 3: N(N-1) dense pair blocks at the sampled rate, plus the LU of the
+    # n = N h system scaled as n^3 from a timed LU of a smaller dense system
+    N2 = len(c2["R"])
+    n2 = N2 * 25
+    ns = 2400
+    rng = np.random.default_rng(0)
+    M = rng.normal(size=(ns, ns))
+    M = M @ M.T + ns * np.eye(ns)
+    rhs = rng.normal(size=ns)
+    t0 = time.perf_counter()
+    np.linalg.solve(M, rhs)
+    t_lu_s = time.perf_counter() - t0
+    t_asm2 = N2 * (N2 - 1) / rate3
+    t_lu2 = t_lu_s * (n2 / ns) ** 3
+    # N = 10^4, l <= 2 superposition: the oracle's pair sum for sampled target spheres
+    N3 = len(c3["R"])
+    tg = np.arange(0, N3, N3 // 6)[:6]
+    inp3 = dynamics.trap_inputs(c3["R"], c3["p"], trap(c3), 2)
+    t0 = time.perf_counter()
+    galerkin.superpose(c3["R"], inp3["Va"], inp3["Oa"], inp3["VH"], inp3["Fe"], inp3["Te"], c3["a"], c3["eta"], 2,
+                       targets=tg)
+    t3 = time.perf_counter() - t0
+    rate_sup = len(tg) * (N3 - 1) / t3
+    return {"value": rate3, "unit": UNIT, "cores": blas_threads(), "kind": "oracle", "cpu_model": cpu_model(),
+            "sample": "%d random ordered pairs of the N=1024 l<=3 suspension, dense FP64 31x31 pair blocks + "
+                      "apply (%.1f s)" % (npairs, dt3),
+            "solve_N64_l2": {"solves_per_s": 1.0 / t1, "s_per_solve": t1, "how": "whole dense assembly + LU + "
+                             "outputs of the N=64 l<=2 suspension (n = 512 unknowns), timed"},
+            "solve_N1024_l3": {"solves_per_s": 1.0 / (t_asm2 + t_lu2), "s_per_solve": t_asm2 + t_lu2,
+                               "assembly_s": t_asm2, "lu_s": t_lu2,
+                               "how": "extrapolated: N(N-1) pair blocks at the sampled rate, plus LU of n = %d "
+                                      "scaled as n^3 from a timed LU of n = %d (%.2f s)" % (n2, ns, t_lu_s)},
+            "superposition_N10000": {"pairs_per_s": rate_sup, "s_per_step": N3 * (N3 - 1) / rate_sup,
+                                     "how": "oracle superposition sum for %d sampled spheres against all N-1 "
+                                            "sources (%.1f s), extrapolated to one step of all N" % (len(tg), t3)}}
+
+
 def blas_threads():
     try:
         from threadpoolctl import threadpool_info
@@ -172,7 +247,8 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": c["name"], "N": 1024, "trunc": 3},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                             "cpu_model": cpu_model()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -180,10 +256,7 @@ def run_reference(args):
 # passes timed by gbi_tune, in the order of its result
 TUNED_PASSES = ["HH_f32", "HH_df", "HL_df", "Lall_df", "HL_f32", "Lall_f32"]
 RESET_EVERY = 20     # timed trap steps between returns to the initial suspension
-# DRAM bytes (read + write) per launch of a pass class on this workload, from an ncu capture
-# of the current kernel (profiles/pair_stream_kernel_l3_HH_f32_N1024.md, 1024 targets, l <= 3):
-# class 17 = FP32 rows H / columns H.  Reported as roofline.traffic when that class dominates.
-NCU_TRAFFIC_BYTES = {17: 168704}
+CLASS_PASS = {"H": 2, "L": 1, "all": 0}
 
 
 def learned_nearfield(ctx, gbi, dev, stream, peaks):
@@ -321,6 +394,187 @@ def job_totals(t_local, pairs_local, world, device):
     return float(t[0]), float(w[0])
 
 
+def fp64_system_residual(ctx, gbi, N, trunc, a, eta, R, inp, QH):
+    """||b - A q|| / ||b|| of the FP64 system for a solution Q^H: b = -8 pi eta V^H - G^HL F^L
+    and A = G^HH (pair and self terms), both evaluated by the FP64 pair kernel, in the
+    solver's internal coordinates (x = c y per component)."""
+    import torch
+    sc = torch.tensor(gbi.component_scales(trunc), dtype=torch.float64, device=R.device)
+    h = len(sc) - 6
+    xV = (inp["VH"] * sc[6:]).T.contiguous()
+    xQ = (QH * sc[6:]).T.contiguous()
+    F, T, c2a = inp["Fe"], inp["Te"], float(sc[3])
+    xF = torch.stack([-F[:, 1], -F[:, 2], -F[:, 0], -c2a * T[:, 1] / a, -c2a * T[:, 2] / a,
+                      -c2a * T[:, 0] / a]).contiguous()
+    y1 = torch.zeros((h, N), dtype=torch.float64, device=R.device)
+    y2 = torch.zeros_like(y1)
+    ctx.apply(N, trunc, a, gbi.SET_H, gbi.SET_L, 0, R, xF, y1, 1.0, 0.0, False)
+    ctx.apply(N, trunc, a, gbi.SET_H, gbi.SET_H, 0, R, xQ, y2, 1.0, 0.0, True)
+    b = -8.0 * math.pi * eta * xV - y1
+    return float((b - y2).norm() / b.norm())
+
+
+def pass_launch_time(ctx, gbi, N, trunc, a, R, cls, reps=40):
+    """Average duration of one launch of pair-pass class cls (precision * 9 + rows * 3 + cols)
+    with the tuned form: reps back-to-back launches through gbi_apply, CUDA events around each
+    pair kernel on the library stream (the host runs ahead, so no launch gap is timed)."""
+    import torch
+    prec, rows, cols = cls // 9, (cls % 9) // 3, cls % 3
+    D = gbi.d(trunc)
+    nr = {0: D, 1: 6, 2: D - 6}[rows]
+    nc = {0: D, 1: 6, 2: D - 6}[cols]
+    x = torch.randn((nc, N), dtype=torch.float64, device=R.device)
+    y = torch.zeros((nr, N), dtype=torch.float64, device=R.device)
+    self_ok = rows == cols or (rows == 1 and cols == 0)
+    for _ in range(3):
+        ctx.apply(N, trunc, a, rows, cols, prec, R, x, y, 1.0, 0.0, self_ok)
+    ctx.set_profiling(True)
+    for _ in range(reps):
+        ctx.apply(N, trunc, a, rows, cols, prec, R, x, y, 1.0, 0.0, self_ok)
+    st = ctx.kernel_stats(cls)
+    ctx.set_profiling(False)
+    return st["ms"] / max(1, st["launches"]), st["flops"] / max(1, st["launches"])
+
+
+def precision_lines(ctx, gbi, c, R0, inp, flush, stream):
+    """The headline solve (N = 1024, l <= 3, cold start, rtol 1e-10) in every precision mode:
+    ms per solve and solves/s (CUDA events, L2 flushed before each solve), the residual
+    against the FP64 system, and V, Omega, Q^H (per mode) against the all-FP64 solve."""
+    import torch
+    N, trunc = len(c["R"]), c["trunc"]
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    args = (inp["Va"], inp["Oa"], inp["VH"], inp["Fe"], inp["Te"])
+    sols, out = {}, {}
+    names = {0: "FP64 throughout", 1: "FP32 pair sums in GMRES; FP64 right-hand side, refinement residuals, "
+             "outputs", 2: "FP32 pair sums in GMRES; double-float right-hand side, refinement residuals, outputs",
+             3: "FP32 pair sums in GMRES, right-hand side and outputs; double-float refinement residuals"}
+    for pr in (0, 1, 2, 3):
+        prm = gbi.params(a=c["a"], eta=c["eta"], trunc=trunc, precision=pr, rtol=1e-10, restart=40, inner_rtol=1e-5,
+                         min_sep=2.0)
+        for _ in range(2):
+            ctx.solve(prm, R0, *args)
+        reps = 3 if pr == 0 else 10
+        tot = 0.0
+        for _ in range(reps):
+            flush.fill_(1.0)
+            ev0.record(stream)
+            V, O, Q, info, _ = ctx.solve(prm, R0, *args)
+            ev1.record(stream)
+            ev1.synchronize()
+            tot += ev0.elapsed_time(ev1)
+        sols[pr] = (V.clone(), O.clone(), Q.clone(), info)
+        out["p%d" % pr] = {"precision": names[pr], "ms_per_solve": tot / reps, "solves_per_s": 1e3 * reps / tot,
+                           "iters": info.iters, "refinements": info.refinements,
+                           "solver_rel_residual": info.rel_residual,
+                           "residual_vs_fp64_system": fp64_system_residual(ctx, gbi, N, trunc, c["a"], c["eta"], R0,
+                                                                           inp, Q)}
+
+    def rel(x, y):
+        return float((x - y).abs().max() / y.abs().max())
+    V0, O0, Q0, _ = sols[0]
+    for pr in (1, 2, 3):
+        V, O, Q, _ = sols[pr]
+        out["p%d" % pr].update({"V_rel_vs_fp64": rel(V, V0), "Omega_rel_vs_fp64": rel(O, O0),
+                                "QH_rel_vs_fp64": rel(Q, Q0),
+                                "QH_rel_per_mode": {nm: rel(Q[:, o:o + k], Q0[:, o:o + k])
+                                                    for nm, o, k in h_mode_slices(trunc)},
+                                "speedup_vs_fp64": out["p0"]["ms_per_solve"] / out["p%d" % pr]["ms_per_solve"]})
+    out["note"] = ("residual_vs_fp64_system = ||b - A q|| / ||b|| with b and A of the FP64 system (FP64 pair "
+                   "kernel); solver_rel_residual is the solver's own refinement residual, whose right-hand side "
+                   "is FP32-summed in precision 3")
+    return out
+
+
+def trajectory_n64(ctx, gbi, dev, stream):
+    """N = 64, l <= 2: one FP64 solve to 1e-10, then 100 forward-Euler steps of dt = 0.1, each
+    re-solved in FP64 (warm-started from the previous step's Q^H), through gbi_trap_step."""
+    import torch
+    import workloads
+    c = workloads.config1()
+    N = len(c["R"])
+    prm = gbi.params(a=c["a"], eta=c["eta"], trunc=c["trunc"], precision=0, rtol=c["rtol"], restart=40)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    R0 = torch.tensor(c["R"], dtype=torch.float64, device=dev)
+    p0 = torch.tensor(c["p"], dtype=torch.float64, device=dev)
+    inp = ctx.trap_inputs(N, c["trunc"], c["k"], c["vs"], c["s0"], c["d0"], R0, p0)
+    for _ in range(2):
+        ctx.solve(prm, R0, inp["Va"], inp["Oa"], inp["VH"], inp["Fe"], inp["Te"])
+    ev0.record(stream)
+    _, _, _, i0, _ = ctx.solve(prm, R0, inp["Va"], inp["Oa"], inp["VH"], inp["Fe"], inp["Te"])
+    ev1.record(stream)
+    ev1.synchronize()
+    ms_solve = ev0.elapsed_time(ev1)
+    R, p = R0.clone(), p0.clone()
+    ev0.record(stream)
+    info = ctx.trap_step(prm, R, p, c["dt"], c["k"], c["vs"], c["s0"], c["d0"], False, c["steps"])
+    ev1.record(stream)
+    ev1.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    d = torch.cdist(R, R) + torch.eye(N, dtype=torch.float64, device=dev) * 1e9
+    return {"workload": c["name"], "N": N, "trunc": c["trunc"], "precision": "FP64 throughout", "dt": c["dt"],
+            "first_solve_ms": ms_solve, "first_solve_iters": i0.iters, "first_solve_rel_residual": i0.rel_residual,
+            "steps": c["steps"], "ms_total": ms, "steps_per_s": 1e3 * c["steps"] / ms,
+            "solves_per_s": 1e3 * c["steps"] / ms, "gmres_iters_per_step": info.iters / c["steps"],
+            "max_rel_residual": info.rel_residual, "pair_interactions_per_s": info.pair_interactions / (ms / 1e3),
+            "min_separation_a_final": float(d.min()) / c["a"],
+            "start": "each step warm-started from the previous step's Q^H"}
+
+
+def trajectory_trap(ctx, gbi, dev, stream, R_init, p_init, k_trap, steps, dt, tail=0.2, every=10, vs=0.1, s0=0.05):
+    """Superposition trap dynamics (closed-form l <= 2 pair sum in FP32, forward Euler): the
+    first (1 - tail) of the steps in one gbi_trap_step call (timed), then the tail in short
+    calls that sample the convective flux: <v . e> over the spheres inside R*/2, e the unit
+    mean orientation of those spheres, v = (R_{k+1} - R_k) / dt (exact for forward Euler),
+    averaged over the samples."""
+    import torch
+    import workloads
+    a, eta = 1.0, workloads.ETA_DEFAULT
+    N = len(R_init)
+    Rstar = 6 * math.pi * eta * vs * a / k_trap
+    prm = gbi.params(a=a, eta=eta, trunc=2, precision=1)
+    R = torch.tensor(R_init, dtype=torch.float64, device=dev)
+    p = torch.tensor(p_init, dtype=torch.float64, device=dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ctx.trap_step(prm, R.clone(), p.clone(), dt, k_trap, vs, s0, 0.0, True, 3)     # warm-up on a copy
+    n_main = int(round(steps * (1 - tail)))
+    ev0.record(stream)
+    ctx.trap_step(prm, R, p, dt, k_trap, vs, s0, 0.0, True, n_main)
+    ev1.record(stream)
+    ev1.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    flux, inner = [], []
+    done = n_main
+    while done < steps:
+        Rk = R.clone()
+        pk = p.clone()
+        ctx.trap_step(prm, R, p, dt, k_trap, vs, s0, 0.0, True, 1)
+        v = (R - Rk) / dt
+        sel = Rk.norm(dim=1) < Rstar / 2
+        if int(sel.sum()) > 0:
+            e = pk[sel].mean(dim=0)
+            if float(e.norm()) > 0:
+                e = e / e.norm()
+                flux.append(float((v[sel] @ e).mean()))
+                inner.append(int(sel.sum()))
+        n = min(every - 1, steps - done - 1)
+        if n > 0:
+            ctx.trap_step(prm, R, p, dt, k_trap, vs, s0, 0.0, True, n)
+        done += 1 + max(n, 0)
+    torch.cuda.synchronize(dev)
+    r = R.norm(dim=1)
+    return {"N": N, "dt": dt, "k_trap": k_trap, "R_star_a": Rstar / a, "steps": steps,
+            "timed_steps": n_main, "ms_timed": ms, "steps_per_s": 1e3 * n_main / ms,
+            "value": n_main * N * (N - 1) / (ms / 1e3), "unit": UNIT,
+            "steady_convective_flux": (sum(flux) / len(flux)) if flux else None,
+            "flux_samples": len(flux), "mean_inner_spheres": (sum(inner) / len(inner)) if inner else 0,
+            "radius_median_a": float(r.median()) / a, "radius_max_a": float(r.max()) / a,
+            "escaped_fraction": float((r > 10 * Rstar).double().mean()),
+            "overlaps_note": "the superposition model has no contact force (as in the paper's trap model): "
+                             "spheres may overlap, where the far-field pair formulas give large velocities",
+            "flux_definition": "<v . e> over spheres with |R| < R*/2, e = unit mean orientation of those spheres, "
+                               "sampled every %d steps over the last %d%% of steps" % (every, int(100 * tail))}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -334,7 +588,8 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    # a non-default stream lets the library replay its Arnoldi chunks from CUDA graphs
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    # a non-default stream lets the library replay its solves from CUDA graphs
     stream = torch.cuda.Stream(dev)
     torch.cuda.set_stream(stream)
     ctx = gbi.Context(local, stream=stream)
@@ -359,46 +614,20 @@ def run_ours(args):
     def step():
         return ctx.trap_step(prm, R, p, dt, c["k"], c["vs"], c["s0"], c["d0"], False, 1)
 
-    # ---- pair-kernel tuning (warps per target of each pass), outside the timed region
+    # ---- pair-kernel tuning (form and warps per target of each pass), outside the timed region
     tuned = ctx.tune(trunc, [0, N])
 
-    # ---- accuracy statement (outside the timed region): mixed vs all-FP64 on the GPU
+    # ---- accuracy and speed of every precision mode (outside the timed region)
     inp = ctx.trap_inputs(N, trunc, c["k"], c["vs"], c["s0"], c["d0"], R0, p0)
-    V1, O1, Q1, i1, _ = ctx.solve(prm, R0, inp["Va"], inp["Oa"], inp["VH"], inp["Fe"], inp["Te"])
-    prm64 = gbi.params(a=c["a"], eta=c["eta"], trunc=trunc, precision=0, rtol=1e-10, restart=40)
-    V0, O0, Q0, i0, _ = ctx.solve(prm64, R0, inp["Va"], inp["Oa"], inp["VH"], inp["Fe"], inp["Te"])
-    torch.cuda.synchronize(dev)
-
-    def rel(a, b):
-        return float((a - b).abs().max() / b.abs().max())
-
-    def rel_rows(a, b):   # max_n |a_n - b_n| / max_n |b_n| (per-sphere 2-norms)
-        return float((a - b).norm(dim=1).max() / b.norm(dim=1).max())
-    err = {"V_rel": rel(V1, V0), "Omega_rel": rel(O1, O0), "QH_rel": rel(Q1, Q0),
-           "V_rel_per_particle": rel_rows(V1, V0), "Omega_rel_per_particle": rel_rows(O1, O0),
-           "QH_rel_per_mode": {name: rel(Q1[:, o:o + k], Q0[:, o:o + k]) for name, o, k in h_mode_slices(trunc)},
-           "mixed_residual": i1.rel_residual, "fp64_residual": i0.rel_residual,
-           "mixed_iters": i1.iters, "mixed_refinements": i1.refinements, "fp64_iters": i0.iters}
-
-    # ---- the same solve in plain FP64 GMRES (precision 0) against the mixed form: solves/s
-    # on this GPU at the same tolerance, the mixed V within V_rel of the FP64 one (outside
-    # the timed region; CUDA events on the library stream, each solve after an L2 flush)
-    sv0, sv1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-
-    def solve_ms(pr, reps):
-        tot = 0.0
-        for _ in range(reps):
-            flush.fill_(1.0)
-            sv0.record(stream)
-            ctx.solve(pr, R0, inp["Va"], inp["Oa"], inp["VH"], inp["Fe"], inp["Te"])
-            sv1.record(stream)
-            sv1.synchronize()
-            tot += sv0.elapsed_time(sv1)
-        return tot / reps
-    ms64 = solve_ms(prm64, 3)
-    ms_mixed = solve_ms(prm, 10)
-    vs_fp64 = {"fp64_solves_per_s": 1e3 / ms64, "mixed_solves_per_s": 1e3 / ms_mixed,
-               "fp64_ms_per_solve": ms64, "mixed_ms_per_solve": ms_mixed, "speedup": ms64 / ms_mixed,
+    modes = precision_lines(ctx, gbi, c, R0, inp, flush, stream)
+    head = modes["p%d" % args.precision]
+    err = {"V_rel": head.get("V_rel_vs_fp64", 0.0), "Omega_rel": head.get("Omega_rel_vs_fp64", 0.0),
+           "QH_rel": head.get("QH_rel_vs_fp64", 0.0), "QH_rel_per_mode": head.get("QH_rel_per_mode", {}),
+           "solver_rel_residual": head["solver_rel_residual"],
+           "residual_vs_fp64_system": head["residual_vs_fp64_system"]}
+    vs_fp64 = {"fp64_solves_per_s": modes["p0"]["solves_per_s"], "mixed_solves_per_s": head["solves_per_s"],
+               "fp64_ms_per_solve": modes["p0"]["ms_per_solve"], "mixed_ms_per_solve": head["ms_per_solve"],
+               "speedup": modes["p0"]["ms_per_solve"] / head["ms_per_solve"],
                "mixed_V_rel_vs_fp64": err["V_rel"], "rtol": 1e-10,
                "note": "same input (the initial N=1024 suspension), cold start, solve only (no trap step)"}
 
@@ -446,7 +675,8 @@ def run_ours(args):
     barrier()
     launches = ctx.kernel_launches() - launches0
     clocks = sampler.stop()
-    # ---- the same steps again with CUDA events around every pair pass (direct launches)
+    # ---- the same steps again with CUDA events around every pair pass (direct launches):
+    # which pass class dominates the step, and its share
     R.copy_(R0)
     p.copy_(p0)
     for _ in range(2):
@@ -460,39 +690,44 @@ def run_ours(args):
     value = pairs_job / t_job
     solves_per_s = world * args.steps / t_job
 
-    # ---- dominant kernel and its roofline
+    # ---- dominant kernel and its roofline: its launch timed back to back with the tuned form
     peaks, peak_src = load_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = fp32_alu_peak_tflops(sm_max, sms)
     tname = {0: "double", 1: "float", 2: "double-float"}
     sname = {0: "all", 1: "L", 2: "H"}
-    names = {pr * 9 + r * 3 + cc: "pair_kernel<l3, %s, %s, %s>" % (sname[r], sname[cc], tname[pr])
+    names = {pr * 9 + r * 3 + cc: "pair pass <l%d, rows %s, cols %s, %s>" % (trunc, sname[r], sname[cc], tname[pr])
              for pr in range(3) for r in range(3) for cc in range(3)}
     names[27] = "trap pass FP64"
     names[28] = "trap pass FP32"
+    total_pass_ms = sum(v["ms"] for v in stats.values())
     dom = max(stats, key=lambda k: stats[k]["ms"])
-    st = stats[dom]
-    avg_ms = st["ms"] / max(1, st["launches"])
-    flops_per_launch = st["flops"] / max(1, st["launches"])
+    in_step_ms = stats[dom]["ms"] / max(1, stats[dom]["launches"])
+    avg_ms, flops_per_launch = pass_launch_time(ctx, gbi, N, trunc, c["a"], R0, dom)
     achieved = flops_per_launch / (avg_ms * 1e-3) / 1e12
     is_f32 = dom == 28 or (9 <= dom < 27)       # FP32 and double-float classes run on the FP32 pipe
-    peak = fp32_alu_peak_tflops(sm_max) if is_f32 else FP64_NOMINAL_TFLOPS
-    kernel_share = {names.get(k, "class%d" % k): round(v["ms"] / max(1e-9, sum(s["ms"] for s in stats.values())), 4)
+    peak = fp32_peak if is_f32 else FP64_NOMINAL_TFLOPS
+    prec_d, rows_d, cols_d = dom // 9, (dom % 9) // 3, dom % 3
+    form = ctx.pass_wpt(trunc, rows_d, cols_d, prec_d, N)
+    kernel_share = {names.get(k, "class%d" % k): round(v["ms"] / max(1e-9, total_pass_ms), 4)
                     for k, v in stats.items() if v["launches"]}
-    roofline = {"bound": "alu", "kernel": names.get(dom, "class%d" % dom), "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": NCU_TRAFFIC_BYTES.get(dom),
-                "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum, "
-                                "profiles/pair_stream_kernel_l3_HH_f32_N1024.md)",
-                "peak_source": ("FP32 CUDA-core peak 152 SMs x 128 lanes x 2 x %.0f MHz (sm_max_mhz of %s "
-                                "MEASURED_PEAKS.json)" % (sm_max, peak_src)) if is_f32 else
+    roofline = {"bound": "alu", "kernel": names.get(dom, "class%d" % dom),
+                "form": "tiled (lanes = targets, TMA-staged sources)" if form == 1 else
+                        "streaming, %d warps per target" % form,
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None,
+                "traffic_note": "DRAM bytes per launch are not counted in this run; they come from an ncu capture "
+                                "of the same kernel (sources L1/L2-resident: a few hundred KB per launch)",
+                "peak_source": ("FP32 CUDA-core peak %d SMs x 128 lanes x 2 x %.0f MHz (sm_max_mhz of %s "
+                                "MEASURED_PEAKS.json)" % (sms, sm_max, peak_src)) if is_f32 else
                                "GB300 FP64 nominal 1.25 TFLOP/s",
                 "flop_convention": "algorithmic flops of the pair formula (FMA = 2); double-float passes count "
                                    "the same formula although each flop costs ~10-20 FP32 instructions",
-                "timing": "CUDA events around every pair pass on the library stream, in a replay of the same "
-                          "steps right after the timed region (per-pass events need direct launches; the timed "
-                          "region replays Arnoldi chunks from CUDA graphs)",
-                "profiled_ms_per_step": prof_ms / args.steps,
-                "flops_per_launch": flops_per_launch, "avg_launch_ms": avg_ms, "launches": st["launches"],
-                "time_share": kernel_share}
+                "timing": "CUDA events around each of 40 back-to-back launches of this pass on the library stream "
+                          "(same N, positions, tuned form), right after the timed region",
+                "in_step_avg_launch_ms": in_step_ms, "in_step_frac": flops_per_launch / (in_step_ms * 1e-3) / 1e12 /
+                peak, "profiled_ms_per_step": prof_ms / args.steps,
+                "flops_per_launch": flops_per_launch, "avg_launch_ms": avg_ms, "time_share": kernel_share}
 
     # ---- end to end through the host-pointer C ABI (H2D + solve + D2H per step)
     h = gbi.h(trunc)
@@ -549,11 +784,29 @@ def run_ours(args):
     ach3 = s3["flops"] / (s3["ms"] * 1e-3) / 1e12
     superposition = {"workload": c3["name"], "N": N3, "value": n3 * N3 * (N3 - 1) / t3, "unit": UNIT,
                      "ms_per_pass": 1e3 * t3 / n3,
-                     "roofline": {"bound": "alu", "kernel": "trap superposition pass (pack + trap_pairs<float> + finish)", "achieved": ach3,
-                                  "peak": fp32_alu_peak_tflops(sm_max), "unit": "TFLOP/s",
-                                  "frac": ach3 / fp32_alu_peak_tflops(sm_max), "traffic": None,
-                                  "avg_launch_ms": s3["ms"] / max(1, s3["launches"])},
+                     "roofline": {"bound": "alu", "kernel": "trap superposition pass (pack + trap_pairs<float> + finish)",
+                                  "achieved": ach3, "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach3 / fp32_peak,
+                                  "traffic": None, "avg_launch_ms": s3["ms"] / max(1, s3["launches"])},
                      "note": "inputs resident (L2-sized), not flushed"}
+
+    # ---- trajectories: N = 64 FP64 re-solved steps; N = 10^4 superposition trap (10^4 steps)
+    try:
+        traj64 = trajectory_n64(ctx, gbi, dev, stream)
+    except gbi.GbiError as e:
+        traj64 = {"status": str(e)}
+    traj3 = trajectory_trap(ctx, gbi, dev, stream, c3["R"], c3["p"], c3["k"], c3["steps"], c3["dt"])
+    traj3.update({"workload": c3["name"], "initial": "Gaussian cloud sigma = 20a about the trap centre"})
+    # the paper's geometry: 10^4 squirmers uniform on the sphere of radius R* = 1256.6a
+    rng = np.random.default_rng(workloads.SEED_BASE + 33)
+    u = rng.normal(size=(N3, 3))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    Rp = 1256.6
+    kp = 6 * math.pi * workloads.ETA_DEFAULT * 0.1 / Rp
+    trajp = trajectory_trap(ctx, gbi, dev, stream, Rp * u, u.copy(), kp, 2000, c3["dt"])
+    trajp.update({"workload": "N10000_trap_paper_geometry",
+                  "initial": "uniform on the sphere of radius R* = 1256.6a, orientations radial",
+                  "note": "short run (%.0f time units); the paper's snapshots reach 8 tau_r = %.3g time units"
+                          % (2000 * c3["dt"], 8 * 8 * math.pi * workloads.ETA_DEFAULT / kp)})
 
     # ---- secondary: 256 independent suspensions (N log-uniform in [32, 4096]) in one batched solve
     c4 = workloads.config4()
@@ -579,28 +832,34 @@ def run_ours(args):
         ev1.synchronize()
         b_ms += ev0.elapsed_time(ev1)
         b_pairs += i4.pair_interactions
+    # its dominant pass class, event-timed per launch inside one more batched solve
+    ctx.set_profiling(True)
+    ctx.batch_solve(prm4, offs, R4, in4["Va"], in4["Oa"], in4["VH"], in4["Fe"], in4["Te"])
+    st4 = {cls: ctx.kernel_stats(cls) for cls in range(gbi._native.N_KERNEL_CLASSES)}
+    ctx.set_profiling(False)
+    dom4 = max(st4, key=lambda k: st4[k]["ms"])
+    ach4 = st4[dom4]["flops"] / (st4[dom4]["ms"] * 1e-3) / 1e12
     batched = {"workload": c4["name"], "systems": len(c4["systems"]), "spheres": len(R4), "trunc": 2,
                "value": b_pairs / (b_ms / 1e3), "unit": UNIT, "ms_per_batch_solve": b_ms / n4,
                "systems_per_s": n4 * len(c4["systems"]) / (b_ms / 1e3), "lockstep_iters": i4.iters,
-               "rel_residual": i4.rel_residual, "tuned_wpt": dict(zip(TUNED_PASSES, tuned4))}
+               "rel_residual": i4.rel_residual, "tuned_wpt": dict(zip(TUNED_PASSES, tuned4)),
+               "roofline": {"bound": "alu", "kernel": names.get(dom4, "class%d" % dom4).replace("l%d" % trunc, "l2"),
+                            "achieved": ach4, "peak": fp32_peak if (9 <= dom4 < 27) else FP64_NOMINAL_TFLOPS,
+                            "unit": "TFLOP/s",
+                            "frac": ach4 / (fp32_peak if (9 <= dom4 < 27) else FP64_NOMINAL_TFLOPS),
+                            "traffic": None, "avg_launch_ms": st4[dom4]["ms"] / max(1, st4[dom4]["launches"]),
+                            "timing": "CUDA events around every pass of one batched solve (direct launches)"}}
 
     # ---- secondary: learned near-field correction (training, errors, N = 10^5 evaluation)
     learned = learned_nearfield(ctx, gbi, dev, stream, load_peaks()[0])
 
     if rank == 0:
-        # ---- CPU baseline: the oracle on a bounded sample, this machine's cores
-        rate, dtc = oracle_pair_rate(c["R"], trunc, c["a"], 12000)
-        cpu = {"value": rate, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
-               "sample": "12000 random ordered pairs of the N=1024 l<=3 suspension, dense FP64 31x31 pair "
-                         "blocks + apply (%.1f s)" % dtc}
+        # ---- CPU baseline: the oracle on bounded samples, this machine's cores
+        cpu = oracle_baselines(workloads.config1(), c, c3)
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-                "precision": {0: "FP64 throughout", 1: "FP32 pair sums in GMRES; FP64 RHS, residuals, outputs; FP64 "
-                              "Arnoldi/Givens", 2: "FP32 pair sums in GMRES; double-float (FP32-pipe, ~48-bit) RHS, "
-                              "residuals, outputs; FP64 Arnoldi/Givens",
-                              3: "FP32 pair sums in GMRES, RHS and outputs; double-float refinement residuals; "
-                              "FP64 Arnoldi/Givens"}[args.precision],
+                "precision": modes["p%d" % args.precision]["precision"] + "; FP64 Arnoldi/Givens",
                 "data": "synthetic",
                 "config": {"workload": c["name"], "N": N, "trunc": trunc, "h": h, "volume_fraction": 0.05,
                            "min_sep_a": 2.5, "overlap_guard_a": 2.0, "rtol": 1e-10, "restart": 40,
@@ -608,8 +867,9 @@ def run_ours(args):
                            "step": "trap inputs + full Galerkin solve + Euler update",
                            "trajectory": "from the initial suspension, reset to it every %d steps" % RESET_EVERY,
                            "l2": "flushed (256 MB write) before every timed step",
-                           "parallelism": "replicas" if world > 1 else "single GPU"},
-                "solves_per_s": solves_per_s, "error_vs_fp64": err, "vs_fp64_gmres": vs_fp64,
+                           "parallelism": "replicas" if world > 1 else "single GPU", "sms": sms},
+                "solves_per_s": solves_per_s, "residual_vs_fp64_system": err["residual_vs_fp64_system"],
+                "error_vs_fp64": err, "vs_fp64_gmres": vs_fp64, "precision_modes": modes,
                 "per_step": {"gmres_iters": step_stats["iters"] / args.steps,
                              "refinements": step_stats["refinements"] / args.steps,
                              "fp32_passes": step_stats["matvecs_f32"] / args.steps,
@@ -618,7 +878,8 @@ def run_ours(args):
                              "start": "cold (zero initial guess) every step: mixed precision"},
                 "roofline": roofline,
                 "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
-                "superposition": superposition, "batched": batched, "learned_nearfield": learned,
+                "superposition": superposition, "config1_trajectory": traj64, "config3_trajectory": traj3,
+                "config3_paper_geometry": trajp, "batched": batched, "learned_nearfield": learned,
                 "tuned_wpt": dict(zip(TUNED_PASSES, tuned))}
         print(json.dumps(line), flush=True)
     ctx.close()

@@ -205,7 +205,8 @@ void tile_select(gbi_ctx* ctx, int trunc, int rows, int precision, PairArgs& a) 
 }
 
 cudaError_t run_pairs(gbi_ctx* ctx, int trunc, int rows, int cols, int precision, const PairArgs& args_in) {
-  const double flops = pair_flops(trunc, rows, cols) * double(args_in.N) * double(args_in.N - 1);
+  const double pairs = args_in.npairs > 0 ? double(args_in.npairs) : double(args_in.N) * double(args_in.N - 1);
+  const double flops = pair_flops(trunc, rows, cols) * pairs;
   PairArgs args = args_in;
   int extra = 0;
   if (args.wpt == 0)
@@ -381,6 +382,7 @@ PairArgs pair_args(const Setup& s, const double* x, double* y, double alpha, dou
   p.sys_flag = nullptr;
   p.sys_flag_stride = 0;
   p.nsys = 1;
+  p.npairs = 0;
   p.pdl = 0;
   p.tile_part = nullptr;
   p.tile_cnt = nullptr;
@@ -429,6 +431,15 @@ gbi_status single_batch(gbi_ctx* ctx, int N, Batch& B) {
 __global__ void k_fill_sys(int S, const int* __restrict__ off, int* sys) {
   const int s = blockIdx.x;
   for (int p = off[s] + threadIdx.x; p < off[s + 1]; p += blockDim.x) sys[p] = s;
+}
+
+long long batch_pairs(const Batch& B) {
+  long long c = 0;
+  for (int q = 0; q < B.S; ++q) {
+    const long long n = B.h_off[q + 1] - B.h_off[q];
+    c += n * (n - 1);
+  }
+  return c;
 }
 
 bool valid_offsets(int nsys, const int* off) {

@@ -222,6 +222,8 @@ struct Batch {
 };
 
 bool valid_params(const gbi_params* p);
+// ordered pairs of a batch, sum over its systems of n (n - 1)
+long long batch_pairs(const Batch& B);
 bool valid_offsets(int nsys, const int* off);
 gbi_status make_batch(gbi_ctx* ctx, int nsys, const int* offsets_host, Batch& B);
 gbi_status single_batch(gbi_ctx* ctx, int N, Batch& B);

@@ -366,6 +366,7 @@ gbi_status gbi_batch_superpose(gbi_ctx* ctx, const gbi_params* prm, int nsys, co
   p.sys_of = B.sys;
   p.sys_off = B.off;
   p.nsys = B.S;
+  p.npairs = batch_pairs(B);
   GBI_CHECK(run_pairs(ctx, s.trunc, SET_L, SET_ALL, prm->precision == 3 ? 1 : prm->precision, p));
   k_finalize_lower<<<grid1(N), 256, 0, ctx->stream>>>(N, s.a, s.scale.v[3], P<double>(ctx->xVL), Va, Oa, V,
                                                       Omega, nullptr);

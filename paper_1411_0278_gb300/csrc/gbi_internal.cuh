@@ -57,6 +57,7 @@ struct PairArgs {
   const int* sys_flag;
   int sys_flag_stride;
   int nsys;              // systems in the batch (<= 1: every target's sources are [0, N))
+  long long npairs;      // ordered pairs the pass evaluates, for the flop accounting (0: N(N-1))
   int wpt;               // warps per target of the FP32 / double-float kernel (0: default;
                          // 1: the tiled form of pair_tile.cuh, single systems only)
   int pdl;               // launch with programmatic dependent launch (see launch_pdl)

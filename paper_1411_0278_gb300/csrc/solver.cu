@@ -1023,6 +1023,7 @@ gbi_status launch_chunk(gbi_ctx* ctx, const Setup& s, const Batch& B, int precis
   if (precision == 1) pa.x32 = static_cast<const float*>(xsrc);
   pa.sys_of = B.sys;
   pa.nsys = B.S;
+  pa.npairs = batch_pairs(B);
   pa.sys_off = B.off;
   pa.sys_flag = &gp.st[0].active;
   pa.sys_flag_stride = int(sizeof(GDev) / sizeof(int));
@@ -1183,6 +1184,7 @@ gbi_status gmres_batch(gbi_ctx* ctx, const Setup& s, const Batch& B, int precisi
       PairArgs pr = pair_args(s, u, Vb, -1.0, 1.0, 1, s.ones, 6);
       pr.sys_of = B.sys;
       pr.nsys = B.S;
+      pr.npairs = batch_pairs(B);
       pr.sys_off = B.off;
       pr.sys_flag = &gp.st[0].enabled;
       pr.sys_flag_stride = int(sizeof(GDev) / sizeof(int));
@@ -1446,6 +1448,7 @@ gbi_status emit_gmres(GraphBuild& gb, const Setup& s, const Batch& B, const GPtr
     PairArgs pr = pair_args(s, u, Vb, -1.0, 1.0, 1, s.ones, 6);
     pr.sys_of = B.sys;
     pr.nsys = B.S;
+    pr.npairs = batch_pairs(B);
     pr.sys_off = B.off;
     pr.sys_flag = &gp.st[0].enabled;
     pr.sys_flag_stride = int(sizeof(GDev) / sizeof(int));
@@ -1517,6 +1520,7 @@ gbi_status solve_core(gbi_ctx* ctx, const gbi_params* prm, const Batch& B, const
   auto batched = [&](PairArgs p, const int* flag) {
     p.sys_of = B.sys;
     p.nsys = B.S;
+    p.npairs = batch_pairs(B);
     p.sys_off = B.off;
     p.sys_flag = flag;
     p.sys_flag_stride = int(sizeof(GDev) / sizeof(int));
