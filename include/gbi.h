@@ -216,15 +216,16 @@ gbi_status gbi_trap_step(gbi_ctx* ctx, const gbi_params* params, int N, double d
  * loop that forbids cudaMalloc/cudaFree, or a host that pre-plans its memory -- this
  * entry point performs the same solve as gbi_solve (same arguments and results) but
  * takes every scratch buffer from one static device array of the library (about
- * 3 MB, held by every GPU that loads the library until the process exits) and its
- * read-back scalars from a static host array.  It needs no context: work is queued
+ * 2.9 MB, held by every GPU that loads the library until the process exits) and its
+ * read-back scalars from a static host array (one per device).  It needs no context: work is queued
  * on `stream` (a cudaStream_t, NULL = default stream) of the current device.
  * The paper has no counterpart; it is an engineering entry point.
  * Limits: N <= 1024, N * gbi_h(trunc) <= 8192, params.restart <= 32 (a value <= 0
  * selects 32); anything larger returns GBI_ERR_ARG before any work.
  * The first call on a device looks up the array's device address (set-up); make that
- * first call before any stream capture on the device.  All calls share the array:
- * calls that overlap on the GPU (other threads or streams) race, and each call
+ * first call before any stream capture on the device.  All calls on one device share
+ * that device's array and read-back area: two calls on the same device that overlap
+ * (other threads or streams) race; calls on different devices do not.  Each call
  * re-initialises whatever must start at zero.  Synchronous. */
 gbi_status gbi_solve_static(void* stream, const gbi_params* params, int N,
                             const double* R, const double* Va, const double* Oa, const double* VH,

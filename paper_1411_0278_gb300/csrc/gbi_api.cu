@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -12,6 +13,7 @@
 #include <vector>
 
 #include "ctx.cuh"
+#include "gstate.cuh"
 #include "pair_tile.cuh"
 
 namespace gbi {
@@ -659,21 +661,30 @@ constexpr size_t kOffKry = kOffXVL + al256(sizeof(double) * 6 * kStaticMaxN);
 constexpr size_t kOffW = kOffKry + al256(sizeof(double) * (size_t)(kStaticMaxRestart + 1) * kStaticMaxNH);
 constexpr size_t kOffMin = kOffW + al256(sizeof(double) * kStaticMaxNH);
 constexpr size_t kOffX32 = kOffMin + 256;
-constexpr size_t kOffGs = kOffX32 + al256(sizeof(float) * 2 * (kStaticMaxND + 3 * kStaticMaxN));
-constexpr size_t kOffBoff = kOffGs + al256(sizeof(double) * (64 + (kStaticMaxRestart + 1) * kStaticMaxRestart +
-                                                              8 * (kStaticMaxRestart + 1) +
-                                                              48 * (2 * (kStaticMaxRestart + 1) + 1) +
-                                                              kFusedBlocks * (2 * (kStaticMaxRestart + 1) + 1) + 24 + 2));
+constexpr int kStaticMaxH = 48;           // the largest gbi_h (trunc 4)
+// x32: per-sphere source records of a double-float pass over every column, rec_floats(D, df)
+// = 2 round4(h + 6) <= 2 (h + 9) floats per sphere, within the limits above
+constexpr size_t kStaticX32Floats = 2 * ((size_t)kStaticMaxNH + 9 * (size_t)kStaticMaxN);
+constexpr size_t kOffGs = kOffX32 + al256(sizeof(float) * kStaticX32Floats);
+// solver state of one system: restart <= 32, at most kStaticMaxH Arnoldi chunks
+constexpr size_t kStaticGsDoubles = gstate_doubles(kStaticMaxRestart, 1, kStaticMaxH, kFusedBlocks);
+constexpr size_t kOffBoff = kOffGs + al256(sizeof(double) * kStaticGsDoubles);
 constexpr size_t kOffBsys = kOffBoff + 256;
 constexpr size_t kStaticBytes = kOffBsys + al256(sizeof(int) * kStaticMaxN);
+static_assert(arnoldi_chunks(1, kStaticMaxH) == kStaticMaxH, "one system: one chunk per higher component");
+static_assert(kStaticBytes < 3u * 1024u * 1024u, "the static scratch stays below 3 MB");
+static_assert(((sizeof(GDev) + 15) & ~size_t(15)) + 32 + sizeof(DSolve) + 16 <= 4096,
+              "the read-back area holds one system's state, the counters and the device record");
 
-// The scratch itself (about 2.6 MB).  Every device that loads the library holds it
+// The scratch itself (about 2.9 MB).  Every device that loads the library holds it
 // until the process exits.  Host code must not use this symbol as an address.
 __device__ __align__(256) unsigned char g_solve_scratch[kStaticBytes];
 
 constexpr int kStaticMaxDevices = 64;
-void* g_scratch_addr[kStaticMaxDevices] = {nullptr};   // device address, per device ordinal
-alignas(64) char g_static_host[4096];                    // host copies of the solver state (pageable)
+// device address of the array, per device ordinal, published once looked up
+std::atomic<void*> g_scratch_addr[kStaticMaxDevices];
+// host copies of the solver state read back by a call (pageable), per device ordinal
+alignas(64) char g_static_host[kStaticMaxDevices][4096];
 
 }  // namespace
 
@@ -687,18 +698,19 @@ extern "C" gbi_status gbi_solve_static(void* stream, const gbi_params* prm, int 
   if (prm->restart > kStaticMaxRestart) return GBI_ERR_ARG;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kStaticMaxDevices) return GBI_ERR_CUDA;
-  if (g_scratch_addr[dev] == nullptr) {
-    // one-time set-up on this device: the device address of the static array
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_solve_scratch) != cudaSuccess || p == nullptr) return GBI_ERR_CUDA;
-    g_scratch_addr[dev] = p;
+  void* addr = g_scratch_addr[dev].load(std::memory_order_acquire);
+  if (addr == nullptr) {
+    // set-up on this device: the device address of the static array (two threads that
+    // race here look up the same address)
+    if (cudaGetSymbolAddress(&addr, g_solve_scratch) != cudaSuccess || addr == nullptr) return GBI_ERR_CUDA;
+    g_scratch_addr[dev].store(addr, std::memory_order_release);
   }
-  unsigned char* base = static_cast<unsigned char*>(g_scratch_addr[dev]);
+  unsigned char* base = static_cast<unsigned char*>(addr);
   gbi_ctx c;
   c.device = dev;
   c.stream = reinterpret_cast<cudaStream_t>(stream);
-  c.hs = g_static_host;
-  c.hs_cap = sizeof(g_static_host);
+  c.hs = g_static_host[dev];
+  c.hs_cap = sizeof(g_static_host[dev]);
   c.allow_graphs = false;      // graph instantiation could allocate
   c.fixed = true;
   auto bind = [&](Buf& b, size_t off, size_t bytes) {

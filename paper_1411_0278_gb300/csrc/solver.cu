@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "ctx.cuh"
+#include "gstate.cuh"
 
 namespace gbi {
 
@@ -25,21 +26,6 @@ namespace gbi {
 // stopped is skipped by every kernel.  A single suspension is the case S = 1.
 
 // Device-resident state of one system's GMRES / refinement.
-struct GDev {
-  int j;          // Arnoldi index of the vector being expanded
-  int active;     // 1 while the current cycle continues
-  int iters;      // inner iterations of the current inner solve
-  int kdim;       // Krylov dimension reached in the current cycle
-  int converged;  // relative residual estimate <= tol
-  int breakdown;  // happy breakdown (exact solution in the Krylov space)
-  int max_iter, m;
-  int enabled;    // refinement: this system still needs a correction
-  int it0;        // iterations already counted (device-decided solve)
-  double bnorm, tol, res, beta, inv_hn;
-  double nb;      // |b_s| (reference of the refinement residual)
-  double rel;     // |b_s - A q_s| / |b_s|
-  double inv_bnorm, inv_nb;   // 1 / bnorm, 1 / nb (0 for a zero norm)
-};
 
 // sqrt(q) and 1 / sqrt(q) for q >= 0 (0 and 0 for q <= 0) from one reciprocal square root:
 // on GB300 a dependent FP64 sqrt or division costs ~650 cycles, rsqrt ~430 and an FMA 64,
@@ -77,13 +63,6 @@ __device__ __forceinline__ long long sys_pairs(const int* __restrict__ off, int 
 // Row chunks per system of the Arnoldi reductions: a few systems get one block per
 // component row (so that a single suspension still spreads over many SMs), large
 // batches one block per system.
-int arnoldi_chunks(int S, int h) { return S >= 64 ? 1 : h; }
-
-size_t gstate_doubles(int m, int S, int CH) {
-  return (size_t)S * (sizeof(GDev) / sizeof(double) + 1) + (size_t)S * ((size_t)(m + 1) * m + 6 * (size_t)(m + 1) + 1) +
-         (size_t)S * CH * (2 * (size_t)(m + 1) + 1) + (size_t)kFusedBlocks * (2 * (size_t)(m + 1) + 1) + 24 +
-         ((size_t)S + 1) / 2 + 1;
-}
 
 GPtr gptrs(void* base, int m, int S, int CH) {
   GPtr p;
@@ -1115,7 +1094,7 @@ gbi_status gmres_batch(gbi_ctx* ctx, const Setup& s, const Batch& B, int precisi
   const int m = std::max(1, std::min(restart, kMaxRestart));
   GBI_TRY(ensure(ctx, ctx->krylov, sizeof(double) * n * (m + 1)));
   GBI_TRY(ensure(ctx, ctx->w, sizeof(double) * n));
-  GBI_TRY(ensure(ctx, ctx->gstate, sizeof(double) * gstate_doubles(m, S, arnoldi_chunks(S, h))));
+  GBI_TRY(ensure(ctx, ctx->gstate, sizeof(double) * gstate_doubles(m, S, arnoldi_chunks(S, h), kFusedBlocks)));
   // gathered Arnoldi source: FP64 component-major, or FP32 records of round4(h) floats
   GBI_TRY(ensure(ctx, ctx->x32, std::max(sizeof(double) * n, sizeof(float) * (size_t)Ntot * ((h + 3) & ~3))));
   double* Vb = P<double>(ctx->krylov);
@@ -1421,7 +1400,7 @@ gbi_status gmres_reserve(gbi_ctx* ctx, const Setup& s, const Batch& B, int m) {
   const size_t n = (size_t)B.Ntot * s.h;
   GBI_TRY(ensure(ctx, ctx->krylov, sizeof(double) * n * (m + 1)));
   GBI_TRY(ensure(ctx, ctx->w, sizeof(double) * n));
-  GBI_TRY(ensure(ctx, ctx->gstate, sizeof(double) * gstate_doubles(m, B.S, arnoldi_chunks(B.S, s.h))));
+  GBI_TRY(ensure(ctx, ctx->gstate, sizeof(double) * gstate_doubles(m, B.S, arnoldi_chunks(B.S, s.h), kFusedBlocks)));
   GBI_TRY(ensure(ctx, ctx->x32, std::max(sizeof(double) * n, sizeof(float) * (size_t)B.Ntot * ((s.h + 3) & ~3))));
   return GBI_OK;
 }
@@ -1507,7 +1486,7 @@ gbi_status solve_core(gbi_ctx* ctx, const gbi_params* prm, const Batch& B, const
   GBI_TRY(ensure(ctx, ctx->delta, sizeof(double) * nh));
   GBI_TRY(ensure(ctx, ctx->xVL, sizeof(double) * 6 * N));
   GBI_TRY(status_words(ctx));
-  GBI_TRY(ensure(ctx, ctx->gstate, sizeof(double) * gstate_doubles(restart, S, arnoldi_chunks(S, h))));
+  GBI_TRY(ensure(ctx, ctx->gstate, sizeof(double) * gstate_doubles(restart, S, arnoldi_chunks(S, h), kFusedBlocks)));
   double* xF = P<double>(ctx->xQ);              // rows 0..5 of the full vector
   double* xQH = P<double>(ctx->xQ) + (size_t)6 * N;
   double* b = P<double>(ctx->b);
