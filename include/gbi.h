@@ -211,6 +211,31 @@ gbi_status gbi_trap_step(gbi_ctx* ctx, const gbi_params* params, int N, double d
                          double vs, double s0, double d0, int superposition, int nsteps,
                          double* R, double* p, gbi_info* info);
 
+/* Flow field (Sec. III, Eq. flow_expression / galerkin_representation_flow_yl): the
+ * velocity at M points X [M][3] in the fluid around a solved suspension,
+ *   v(x) = -(1/(8 pi eta)) sum_m [F^l' grad^(l') G](x - R_m) . Q_m,   Q^L = F^L,
+ * the single-layer flow of every sphere's modes with its flow coefficients (F^(1s) =
+ * -F^e, F^(2a) from -T^e; Q^H as returned by gbi_solve for the same R, F^e, T^e and
+ * truncation).  R, Fe, Te: [N][3]; QH: [N][gbi_h(trunc)]; U: [M][3] output.  The
+ * representation holds in the fluid: a point inside a sphere (|x - R_m| < a) gets NaN
+ * and is counted in *n_inside (host pointer, may be NULL; when given the call
+ * synchronizes the stream to return it).  params: a, eta, trunc; precision 0 evaluates
+ * in FP64, any other value in FP32 (two-float centres).  Asynchronous otherwise. */
+gbi_status gbi_flow(gbi_ctx* ctx, const gbi_params* params, int N, const double* R, const double* Fe,
+                    const double* Te, const double* QH, int M, const double* X, double* U, int* n_inside);
+
+/* gbi_trap_step for a batch of independent suspensions (the layout of gbi_batch_solve:
+ * system s holds spheres [offsets_host[s], offsets_host[s+1]); each system has its own
+ * trap centred at the origin of the coordinates).  Every step evaluates all systems
+ * together (gbi_batch_superpose, or one lock-step gbi_batch_solve); a repeated
+ * mixed-precision call on a non-default stream runs each step -- trap inputs, the whole
+ * batched solve and the Euler update of every system -- as one replayed CUDA graph.  A
+ * step in which any system's solve fails updates no system and ends the call with that
+ * status.  Same arguments otherwise; R, p: [offsets_host[nsys]][3]. */
+gbi_status gbi_batch_trap_step(gbi_ctx* ctx, const gbi_params* params, int nsys, const int* offsets_host,
+                               double dt, double k_trap, double vs, double s0, double d0, int superposition,
+                               int nsteps, double* R, double* p, gbi_info* info);
+
 /* gbi_solve without any allocation.  For callers that cannot allocate device memory
  * while they run -- code inside a framework that owns every allocation, a real-time
  * loop that forbids cudaMalloc/cudaFree, or a host that pre-plans its memory -- this
@@ -361,7 +386,8 @@ gbi_status gbi_pass_status(gbi_ctx* ctx);
  * counted as launches; their few microseconds stay in the summed time.  Class ids:
  * precision * 9 + rows * 3 + cols for gbi_apply-style passes (precision 0 = FP64,
  * 1 = FP32, 2 = double-float; rows/cols 0 = all, 1 = rigid-body, 2 = higher),
- * 27 = closed-form trap pass in FP64, 28 = in FP32.  gbi_kernel_stats synchronizes
+ * 27 = closed-form trap pass in FP64, 28 = in FP32, 29 = flow field (gbi_flow) in FP64,
+ * 30 = in FP32.  gbi_kernel_stats synchronizes
  * on the recorded events. */
 long long gbi_kernel_launches(gbi_ctx* ctx);
 /* Number of solves this context has run as one replayed CUDA graph (-1 for a NULL

@@ -63,6 +63,10 @@ _SIGS = {
     "gbi_trap_inputs": (_I, [_VP, _I, _I, _D, _D, _D, _D] + [_VP] * 7),
     "gbi_trap_step": (_I, [_VP, ctypes.POINTER(gbi_params), _I, _D, _D, _D, _D, _D, _I, _I, _VP, _VP,
                            ctypes.POINTER(gbi_info)]),
+    "gbi_flow": (_I, [_VP, ctypes.POINTER(gbi_params), _I, _VP, _VP, _VP, _VP, _I, _VP, _VP,
+                      ctypes.POINTER(ctypes.c_int)]),
+    "gbi_batch_trap_step": (_I, [_VP, ctypes.POINTER(gbi_params), _I, ctypes.POINTER(ctypes.c_int), _D, _D, _D, _D,
+                                 _D, _I, _I, _VP, _VP, ctypes.POINTER(gbi_info)]),
     "gbi_batch_solve": (_I, [_VP, ctypes.POINTER(gbi_params), _I, ctypes.POINTER(ctypes.c_int)] + [_VP] * 9 +
                         [_I, ctypes.POINTER(gbi_info)]),
     "gbi_batch_superpose": (_I, [_VP, ctypes.POINTER(gbi_params), _I, ctypes.POINTER(ctypes.c_int)] + [_VP] * 8),
@@ -99,8 +103,9 @@ def kernel_class(precision, rows, cols):
 
 
 TRAP_F64, TRAP_F32 = 27, 28
+FLOW_F64, FLOW_F32 = 29, 30
 MLP_NPARAM = 35078
-N_KERNEL_CLASSES = 30
+N_KERNEL_CLASSES = 31
 
 
 def lib():
@@ -443,6 +448,27 @@ class Context:
         self._check(lib().gbi_kernel_stats(self._h, int(cls), ctypes.byref(ms), ctypes.byref(n), ctypes.byref(fl)),
                     "gbi_kernel_stats")
         return dict(ms=ms.value, launches=n.value, flops=fl.value)
+
+    def flow(self, prm, R, Fe, Te, QH, X, U=None):
+        """gbi_flow: the flow at points X [M][3] of a solved suspension; returns (U, inside count)."""
+        import torch
+        M = X.shape[0]
+        if U is None:
+            U = torch.empty((M, 3), dtype=torch.float64, device=X.device)
+        n_in = ctypes.c_int(0)
+        N = R.shape[0]
+        self._check(lib().gbi_flow(self._h, ctypes.byref(prm), int(N), _ptr(R), _ptr(Fe), _ptr(Te), _ptr(QH),
+                                   int(M), _ptr(X), _ptr(U), ctypes.byref(n_in)), "gbi_flow")
+        return U, n_in.value
+
+    def batch_trap_step(self, prm, offsets, R, p, dt, k_trap, vs, s0, d0, superposition, nsteps):
+        info = gbi_info()
+        nsys, off = self._offs(offsets)
+        st = lib().gbi_batch_trap_step(self._h, ctypes.byref(prm), nsys, off, float(dt), float(k_trap),
+                                       float(vs), float(s0), float(d0), int(bool(superposition)), int(nsteps),
+                                       _ptr(R), _ptr(p), ctypes.byref(info))
+        self._check(st, "gbi_batch_trap_step")
+        return info
 
     def trap_step(self, prm, R, p, dt, k_trap, vs, s0, d0, superposition, nsteps):
         info = gbi_info()

@@ -235,7 +235,7 @@ gbi_status gbi_destroy(gbi_ctx* ctx) {
                  &ctx->mlp_grad, &ctx->mlp_pk_tc, &ctx->mlp_err, &ctx->nb_cnt, &ctx->nb_start, &ctx->nb_tg, &ctx->nb_sr, &ctx->nb_scan,
                  &ctx->cell_of, &ctx->cell_cnt, &ctx->cell_start, &ctx->cell_fill, &ctx->cell_items, &ctx->nb_aux,
                  &ctx->mf_F, &ctx->mf_FR, &ctx->mf_lab, &ctx->mf_dO, &ctx->mf_part, &ctx->mf_loss, &ctx->dsolve,
-                 &ctx->tile, &ctx->tilecnt};
+                 &ctx->tile, &ctx->tilecnt, &ctx->flowx, &ctx->flowrec, &ctx->flowcnt};
   for (Buf* b : bufs)
     if (b->p) cudaFree(b->p);
   drain_profile(ctx);
@@ -423,9 +423,17 @@ gbi_status gbi_superpose(gbi_ctx* ctx, const gbi_params* prm, int N, const doubl
   return GBI_OK;
 }
 
-gbi_status gbi_trap_step(gbi_ctx* ctx, const gbi_params* prm, int N, double dt, double k_trap, double vs,
-                         double s0, double d0, int superposition, int nsteps, double* R, double* p,
-                         gbi_info* info) {
+}  // extern "C"
+
+namespace gbi {
+namespace {
+
+// Forward-Euler trap steps of one suspension (nsys = 1, offsets NULL) or of a batch of
+// independent ones (system s = spheres [offsets[s], offsets[s+1]), each with its own trap
+// centred at the origin of the coordinates).
+gbi_status trap_steps(gbi_ctx* ctx, const gbi_params* prm, int nsys, const int* offsets, int N, double dt,
+                      double k_trap, double vs, double s0, double d0, int superposition, int nsteps, double* R,
+                      double* p, gbi_info* info) {
   if (!ctx || !valid_params(prm) || N < 0 || nsteps < 0) return GBI_ERR_ARG;
   gbi_info total{};
   if (N == 0 || nsteps == 0) {
@@ -474,9 +482,19 @@ gbi_status gbi_trap_step(gbi_ctx* ctx, const gbi_params* prm, int N, double dt, 
   for (int step = 0; step < nsteps; ++step) {
     if (superposition) {
       GBI_TRY(trap_inputs());
-      GBI_TRY(gbi_superpose(ctx, prm, N, R, P<double>(ctx->tVa), P<double>(ctx->tOa), P<double>(ctx->tVH),
-                            P<double>(ctx->tFe), P<double>(ctx->tTe), P<double>(ctx->tV), P<double>(ctx->tOm)));
-      total.pair_interactions += (long long)N * (N - 1);
+      if (offsets == nullptr) {
+        GBI_TRY(gbi_superpose(ctx, prm, N, R, P<double>(ctx->tVa), P<double>(ctx->tOa), P<double>(ctx->tVH),
+                              P<double>(ctx->tFe), P<double>(ctx->tTe), P<double>(ctx->tV), P<double>(ctx->tOm)));
+        total.pair_interactions += (long long)N * (N - 1);
+      } else {
+        GBI_TRY(gbi_batch_superpose(ctx, prm, nsys, offsets, R, P<double>(ctx->tVa), P<double>(ctx->tOa),
+                                    P<double>(ctx->tVH), P<double>(ctx->tFe), P<double>(ctx->tTe), P<double>(ctx->tV),
+                                    P<double>(ctx->tOm)));
+        for (int q = 0; q < nsys; ++q) {
+          const long long n = offsets[q + 1] - offsets[q];
+          total.pair_interactions += n * (n - 1);
+        }
+      }
       (prm->precision == 1 || prm->precision == 3 ? total.matvecs_f32 : total.matvecs_f64) += 1;
       GBI_TRY(euler(nullptr));
     } else {
@@ -488,7 +506,8 @@ gbi_status gbi_trap_step(gbi_ctx* ctx, const gbi_params* prm, int N, double dt, 
       const bool warm = prm->precision == 0 && (step > 0 || (ctx->tqh_N == N && ctx->tqh_trunc == prm->trunc));
       ctx->tqh_N = -1;
       Batch B;
-      GBI_TRY(single_batch(ctx, N, B));
+      if (offsets == nullptr) GBI_TRY(single_batch(ctx, N, B));
+      else GBI_TRY(make_batch(ctx, nsys, offsets, B));
       st = solve_core(ctx, prm, B, R, P<double>(ctx->tVa), P<double>(ctx->tOa), P<double>(ctx->tVH),
                       P<double>(ctx->tFe), P<double>(ctx->tTe), P<double>(ctx->tV), P<double>(ctx->tOm),
                       P<double>(ctx->tQH), warm ? 1 : 0, &one, &hooks);
@@ -508,6 +527,25 @@ gbi_status gbi_trap_step(gbi_ctx* ctx, const gbi_params* prm, int N, double dt, 
   }
   if (info) *info = total;
   return st;
+}
+
+}  // namespace
+}  // namespace gbi
+
+extern "C" {
+
+gbi_status gbi_trap_step(gbi_ctx* ctx, const gbi_params* prm, int N, double dt, double k_trap, double vs,
+                         double s0, double d0, int superposition, int nsteps, double* R, double* p,
+                         gbi_info* info) {
+  return trap_steps(ctx, prm, 1, nullptr, N, dt, k_trap, vs, s0, d0, superposition, nsteps, R, p, info);
+}
+
+gbi_status gbi_batch_trap_step(gbi_ctx* ctx, const gbi_params* prm, int nsys, const int* offsets_host, double dt,
+                               double k_trap, double vs, double s0, double d0, int superposition, int nsteps,
+                               double* R, double* p, gbi_info* info) {
+  if (!ctx || nsys < 1 || !offsets_host || !valid_offsets(nsys, offsets_host)) return GBI_ERR_ARG;
+  return trap_steps(ctx, prm, nsys, offsets_host, offsets_host[nsys], dt, k_trap, vs, s0, d0, superposition, nsteps,
+                    R, p, info);
 }
 
 gbi_status gbi_trap_inputs(gbi_ctx* ctx, int N, int trunc, double k_trap, double vs, double s0, double d0,
@@ -583,7 +621,7 @@ gbi_status gbi_set_profiling(gbi_ctx* ctx, int on) {
 
 gbi_status gbi_kernel_stats(gbi_ctx* ctx, int kernel_class, double* total_ms, long long* launches,
                             double* flops) {
-  if (!ctx || kernel_class < 0 || kernel_class >= 30) return GBI_ERR_ARG;
+  if (!ctx || kernel_class < 0 || kernel_class >= 31) return GBI_ERR_ARG;
   drain_profile(ctx);
   if (total_ms) *total_ms = ctx->stat_ms[kernel_class];
   const long long live = ctx->stat_n[kernel_class] - (ctx->prof ? ctx->stat_dead[kernel_class] : 0);

@@ -110,3 +110,55 @@ def test_fp32_superposition_trajectory_n10000(ctx, gbi):
                                     targets=tg)
         assert rel_rows(Vg[tg], Vr) < 1e-5
         assert rel_rows(Og[tg], Or) < 1e-5
+
+
+@pytest.mark.parametrize("superposition,precision", [(True, 1), (False, 3), (False, 0)])
+def test_batched_trap_steps_match_per_system_steps(ctx, gbi, superposition, precision):
+    """gbi_batch_trap_step on three suspensions of uneven size (each with its own trap at
+    its origin) against gbi_trap_step on each system alone: the same trajectories, to the
+    solve tolerance (lock-step batched GMRES sums in another order)."""
+    sizes = [17, 40, 9]
+    cs = [workloads.small_cloud(n, 300 + i) for i, n in enumerate(sizes)]
+    offs = [0]
+    for n in sizes:
+        offs.append(offs[-1] + n)
+    R = np.concatenate([c["R"] for c in cs])
+    p = np.concatenate([c["p"] for c in cs])
+    c = cs[0]
+    prm = gbi.params(a=c["a"], eta=c["eta"], trunc=2, precision=precision, rtol=1e-10)
+    Rb, pb = dev(R), dev(p)
+    ctx.batch_trap_step(prm, offs, Rb, pb, 0.1, c["k"], c["vs"], c["s0"], 0.02, superposition, 3)
+    torch.cuda.synchronize()
+    for q in range(len(sizes)):
+        Rs, ps = dev(R[offs[q]:offs[q + 1]]), dev(p[offs[q]:offs[q + 1]])
+        one = gbi.Context(0)
+        one.trap_step(prm, Rs, ps, 0.1, c["k"], c["vs"], c["s0"], 0.02, superposition, 3)
+        torch.cuda.synchronize()
+        one.close()
+        Rr, pr = Rs.cpu().numpy(), ps.cpu().numpy()
+        tol = 1e-6 if precision in (1, 3) else 1e-11
+        assert np.abs(Rb.cpu().numpy()[offs[q]:offs[q + 1]] - Rr).max() < tol * np.abs(Rr).max()
+        assert np.abs(pb.cpu().numpy()[offs[q]:offs[q + 1]] - pr).max() < tol
+
+
+def test_batched_trap_step_replays_one_graph_per_step(gbi):
+    """On a non-default stream a repeated mixed-precision batched step is one CUDA graph:
+    trap inputs, the batched solve and the update of every system."""
+    sizes = [30, 64, 12]
+    cs = [workloads.small_cloud(n, 310 + i) for i, n in enumerate(sizes)]
+    offs = [0]
+    for n in sizes:
+        offs.append(offs[-1] + n)
+    R = dev(np.concatenate([c["R"] for c in cs]))
+    p = dev(np.concatenate([c["p"] for c in cs]))
+    c = cs[0]
+    prm = gbi.params(a=c["a"], eta=c["eta"], trunc=2, precision=3, rtol=1e-10)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        bctx = gbi.Context(0, stream=stream)
+        for _ in range(4):
+            bctx.batch_trap_step(prm, offs, R, p, 0.05, c["k"], c["vs"], c["s0"], 0.0, False, 1)
+        stream.synchronize()
+        assert bctx.solve_graph_replays() >= 2
+        bctx.close()
+    assert np.all(np.isfinite(R.cpu().numpy()))
