@@ -789,6 +789,31 @@ def run_ours(args):
                                   "traffic": None, "avg_launch_ms": s3["ms"] / max(1, s3["launches"])},
                      "note": "inputs resident (L2-sized), not flushed"}
 
+    # ---- flow field after the solve: a 64^3 grid through the N = 1024 suspension (FP32)
+    V2, O2, Q2, _, _ = ctx.solve(prm, R0, inp["Va"], inp["Oa"], inp["VH"], inp["Fe"], inp["Te"])
+    side = float(c["side"])
+    g1 = torch.linspace(-side / 2, side / 2, 64, dtype=torch.float64, device=dev)
+    Xg = torch.stack(torch.meshgrid(g1, g1, g1, indexing="ij"), -1).reshape(-1, 3).contiguous()
+    prmf = gbi.params(a=c["a"], eta=c["eta"], trunc=trunc, precision=1)
+    Ug = torch.empty_like(Xg)
+    ctx.flow(prmf, R0, inp["Fe"], inp["Te"], Q2, Xg, Ug)
+    ctx.set_profiling(True)
+    nfl = 5
+    n_inside = 0
+    for _ in range(nfl):
+        _, n_inside = ctx.flow(prmf, R0, inp["Fe"], inp["Te"], Q2, Xg, Ug)
+    sf = ctx.kernel_stats(gbi._native.FLOW_F32)
+    ctx.set_profiling(False)
+    fl_ms = sf["ms"] / max(1, sf["launches"])
+    ach_f = sf["flops"] / (sf["ms"] * 1e-3) / 1e12
+    flowline = {"points": int(Xg.shape[0]), "spheres": N, "trunc": trunc, "points_inside_spheres": n_inside,
+                "ms_per_evaluation": fl_ms, "points_per_s": Xg.shape[0] / (fl_ms / 1e3),
+                "point_sphere_terms_per_s": Xg.shape[0] * N / (fl_ms / 1e3),
+                "roofline": {"bound": "alu", "kernel": "k_flow<l3, float> (1s rows of a zero-radius target)",
+                             "achieved": ach_f, "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach_f / fp32_peak,
+                             "traffic": None},
+                "grid": "64^3 points on the suspension's cube (side %.1f a)" % side}
+
     # ---- trajectories: N = 64 FP64 re-solved steps; N = 10^4 superposition trap (10^4 steps)
     try:
         traj64 = trajectory_n64(ctx, gbi, dev, stream)
@@ -901,7 +926,7 @@ def run_ours(args):
                              "start": "cold (zero initial guess) every step: mixed precision"},
                 "roofline": roofline,
                 "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
-                "superposition": superposition, "config1_trajectory": traj64, "config3_trajectory": traj3,
+                "superposition": superposition, "flow_field": flowline, "config1_trajectory": traj64, "config3_trajectory": traj3,
                 "config3_paper_geometry": trajp, "batched": batched, "learned_nearfield": learned,
                 "tuned_wpt": dict(zip(TUNED_PASSES, tuned))}
         print(json.dumps(line), flush=True)

@@ -9,8 +9,9 @@ Modules: ``tensors`` (STF projectors, tensorial harmonics, packed basis, mode
 embeddings), ``taylor`` (exact truncated Taylor series of |rho|^nu),
 ``galerkin`` (pair and self elements, dense system, LU solve, superposition),
 ``quadrature`` (brute-force surface integrals used only to pin the above),
-``dynamics`` (forward-Euler trap update), ``mlp`` (features, network, loss,
-gradient and Adam step of the learned near-field correction).
+``dynamics`` (forward-Euler trap update), ``flow`` (the flow field of the Galerkin
+representation at points in the fluid, by surface quadrature), ``mlp`` (features,
+network, loss, gradient and Adam step of the learned near-field correction).
 
 Parity status: every function is pinned by tests/test_oracle_pins.py and
 tests/test_oracle_mlp_pins.py against

@@ -31,6 +31,7 @@ struct gbi_ctx {
   gbi::Buf b, xQ, r, delta, krylov, w, xVL, minr2, x32, trapbuf, gstate;   // solve workspace
   gbi::Buf boff, bsys;                           // system offsets / ids of the current batch
   gbi::Buf tile, tilecnt;                        // tiled pair passes: partial sums, arrival counters
+  gbi::Buf flowx, flowrec, flowcnt;              // gbi_flow: coefficients, FP32 records, inside count
   long long wait_limit = 1ll << 24;              // try_wait rounds of a tiled pass's stage waits
                                                  // (kTileWaitLimit; gbi_set_wait_limit)
   int single_N = -1;                             // boff / bsys hold one system of this many spheres
@@ -68,10 +69,10 @@ struct gbi_ctx {
   };
   std::vector<Rec> pending;
   std::vector<cudaEvent_t> pool;
-  double stat_ms[30] = {0};
-  double stat_flops[30] = {0};
-  long long stat_n[30] = {0};
-  long long stat_dead[30] = {0};
+  double stat_ms[32] = {0};
+  double stat_flops[32] = {0};
+  long long stat_n[32] = {0};
+  long long stat_dead[32] = {0};
   // learned near-field correction: FP32 master weights, Adam moments, bf16-rounded
   // copy (training), padded bf16 copy (inference), gradient; neighbour lists; pair
   // features, outputs and training scratch
@@ -131,7 +132,8 @@ void drain_profile(gbi_ctx* ctx);
 
 // One pair pass with launch counting and optional event timing.
 // Class: precision * 9 + rows * 3 + cols for the generic operator (precision 0 FP64,
-// 1 FP32, 2 double-float), 27/28 for the closed-form trap kernel in FP64/FP32.
+// 1 FP32, 2 double-float), 27/28 for the closed-form trap kernel in FP64/FP32, 29/30 for
+// the flow-field kernel in FP64/FP32.
 template <typename F>
 cudaError_t timed(gbi_ctx* ctx, int cls, double flops, int nlaunch, F&& launch) {
   cudaEvent_t a = nullptr, b = nullptr;

@@ -26,7 +26,8 @@ struct Positions {
 };
 
 // Which components a pair pass reads (cols) and writes (rows).
-enum CompSet : int { SET_ALL = 0, SET_L = 1, SET_H = 2 };
+// SET_P (rows only): the 1s rows of a point target of radius zero (flow field evaluation).
+enum CompSet : int { SET_ALL = 0, SET_L = 1, SET_H = 2, SET_P = 3 };
 
 struct PairArgs {
   int N;

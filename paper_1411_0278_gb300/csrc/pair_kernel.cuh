@@ -50,6 +50,9 @@ __host__ __device__ __forceinline__ void couple(T e2, const T* xs, T* y) {
   GBI_C3(2)
   GBI_C3(3)
   GBI_C3(4)
+  GBI_C(2, P, all, 3, 0)
+  GBI_C(3, P, all, 3, 0)
+  GBI_C(4, P, all, 3, 0)
 #undef GBI_C3
 #undef GBI_C
 }
@@ -160,16 +163,16 @@ __host__ __device__ __forceinline__ double gbi_to_double(df v) { return df_to_do
 template <int TR, int ROWS, int COLS> struct PassShape {
   static constexpr int D = Tab<TR>::D;
   static constexpr int R0 = ROWS == SET_H ? 6 : 0;
-  static constexpr int R1 = ROWS == SET_L ? 6 : D;
+  static constexpr int R1 = ROWS == SET_P ? 3 : (ROWS == SET_L ? 6 : D);
   static constexpr int C0 = COLS == SET_H ? 6 : 0;
   static constexpr int C1 = COLS == SET_L ? 6 : D;
   static constexpr int NR = R1 - R0;
   static constexpr int NC = C1 - C0;
   static constexpr int MR0 = ROWS == SET_H ? 2 : 0;
-  static constexpr int MR1 = ROWS == SET_L ? 2 : Tab<TR>::NMODE;
+  static constexpr int MR1 = ROWS == SET_P ? 1 : (ROWS == SET_L ? 2 : Tab<TR>::NMODE);
   static constexpr int MC0 = COLS == SET_H ? 2 : 0;
   static constexpr int MC1 = COLS == SET_L ? 2 : Tab<TR>::NMODE;
-  static constexpr int MAXK_R = ROWS == SET_L ? 1 : Tab<TR>::MAXK;
+  static constexpr int MAXK_R = (ROWS == SET_L || ROWS == SET_P) ? 1 : Tab<TR>::MAXK;
   static constexpr int MAXK_C = COLS == SET_L ? 1 : Tab<TR>::MAXK;
   static constexpr int MAXK = MAXK_R > MAXK_C ? MAXK_R : MAXK_C;
 };

@@ -272,6 +272,22 @@ def couplings(trunc):
     return comps, out
 
 
+def point_couplings(trunc):
+    """(p, q, alpha, beta) of the 1s rows (p < 3) for a point target: the target has no
+    radius, so only the source's finite-size operator F^l' = 1 + a^2/(4l'+6) lap remains
+    in the beta term (the beta of couplings() carries both radii: its factor
+    1/6 + 1/(4l'+6) becomes 1/(4l'+6))."""
+    comps, cpl = couplings(trunc)
+    out = []
+    for (p, q, al, be) in cpl:
+        if p >= 3:
+            continue
+        lq = comps[q].L - 1
+        bp = be * (1.0 / (4 * lq + 6)) / (1.0 / 6 + 1.0 / (4 * lq + 6))
+        out.append((p, q, al, bp))
+    return comps, out
+
+
 def sphere_mono(n):
     """int x^a y^b z^c dOmega / (4 pi), exact."""
     if any(v % 2 for v in n):
@@ -536,6 +552,22 @@ def emit(path):
                     else:
                         w("  y[%d] = %s;" % (p, fma_chain(ta)))
                 w("}")
+        # the flow at a point (a target of radius zero): the 1s rows from every column
+        _, pcpl = point_couplings(trunc)
+        w("template <typename T> __host__ __device__ __forceinline__ void gbi_t%d_couple_P_all(T e2, const T* __restrict__ xs, T* __restrict__ y) {" % trunc)
+        w("  // point target: 1s rows only, beta from the source's finite-size operator alone")
+        by_p = {}
+        for (p, q, al, be) in pcpl:
+            by_p.setdefault(p, []).append((q, al, be))
+        for p in range(3):
+            terms = by_p.get(p, [])
+            ta = [("T(%s)" % fmt(al), "xs[%d]" % q) for q, al, be in terms if al != 0.0]
+            tb = [("T(%s)" % fmt(be), "xs[%d]" % q) for q, al, be in terms if be != 0.0]
+            if tb:
+                w("  y[%d] = gbi_fmac(e2, %s, %s);" % (p, fma_chain(tb), fma_chain(ta)))
+            else:
+                w("  y[%d] = %s;" % (p, fma_chain(ta)))
+        w("}")
         nnz = len(cpl)
         w("static constexpr int gbi_t%d_nnz = %d;   // pair-frame nonzeros (all rows, all columns)" % (trunc, nnz))
         # algorithmic flops per ordered pair of the pair-frame evaluation (FMA = 2, rsqrt = 1)
@@ -569,6 +601,26 @@ def emit(path):
                         f += (2 if al != 0.0 else 0) + (2 if be != 0.0 else 0)
                 f += 2 * len(rows) + len(rows)                  # combine alpha/beta, accumulate
                 flops[(rn, cn)] = f
+        # the point rows (1s from every column): same count with the 1s row mode and the
+        # point couplings
+        cmodes = sorted({c.mode for c in comps})
+        maxk_used = max(MODES[m][1] - MODES[m][2] for m in cmodes)
+        fp = 9 + 5 + 1 + 3 + 3 + 1 + 2 + 2 + 2 + 6 * max(0, maxk_used - 1) + 7
+        for kk in range(1, maxk_used + 1):
+            fp += 6 + 2 * dm_terms[kk]
+        kmax_pow = {}
+        for m in cmodes:
+            kk, j = MODES[m][1] - MODES[m][2], MODES[m][1] - 1
+            fp += 6 * kk + 2 * dm_nnz[kk] + (1 if j > 0 else 0)
+            if j > 0:
+                kmax_pow[j] = max(kmax_pow.get(j, 0), kk)
+        fp += 6 * 1 + 2 * dm_nnz[1] + 1
+        kmax_pow[1] = max(kmax_pow.get(1, 0), 1)
+        fp += sum(2 * kk for kk in kmax_pow.values())
+        for (p, q, al, be) in pcpl:
+            fp += (2 if al != 0.0 else 0) + (2 if be != 0.0 else 0)
+        fp += 2 * 3 + 3
+        w("static constexpr int gbi_t%d_flops_point = %d;   // per (point, sphere): 1s rows from all columns" % (trunc, fp))
         w("// algorithmic flops per ordered pair, [rows][cols] with 0 = all, 1 = L, 2 = H")
         w("static constexpr int gbi_t%d_flops[3][3] = {%s};" % (trunc, ", ".join(
             "{%s}" % ", ".join(str(flops[(rn, cn)]) for cn in ("all", "L", "H")) for rn in ("all", "L", "H"))))

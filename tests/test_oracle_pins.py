@@ -512,3 +512,63 @@ def test_euler_turns_orientation_about_the_torque():
         np.testing.assert_allclose(pn[0], expect, atol=1e-14)
         assert np.cross(p[0], pn[0])[2] > 0
         R, p = Rn, pn
+
+
+# ---------------------------------------------------------------- flow field
+
+def _exterior_points(R0, rng, n, rmin, rmax):
+    d = rng.normal(size=(n, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    return R0 + d * rng.uniform(rmin, rmax, size=(n, 1)) * A
+
+
+def test_flow_of_translating_and_rotating_sphere():
+    """One sphere under a force F and a torque T: the flow of the Galerkin representation
+    is the exact exterior Stokes solution, F.[(1/r + a^2/3r^3) I + (1/r^3 - a^2/r^5) rho rho]
+    / (8 pi eta) (translation) plus T x rho / (8 pi eta r^3) (rotation)."""
+    from oracle import flow
+    rng = np.random.default_rng(21)
+    R0 = np.array([[0.4, -1.0, 2.0]])
+    F = np.array([[0.3, -0.7, 0.2]])
+    T = np.array([[-0.2, 0.5, 0.9]])
+    z = np.zeros((1, 3))
+    _, _, QH = galerkin.solve(R0, z, z, np.zeros((1, 25)), F, T, A, ETA, 3)
+    X = _exterior_points(R0[0], rng, 12, 2.0, 6.0)
+    U = flow.flow(X, R0, flow.internal_coefficients(F, T, QH, A, 3), A, ETA, 3)
+    rho = X - R0
+    r = np.linalg.norm(rho, axis=1)[:, None]
+    exact = (F * (1 / r + A ** 2 / (3 * r ** 3)) + rho * np.sum(rho * F, axis=1, keepdims=True)
+             * (1 / r ** 3 - A ** 2 / r ** 5)) / (8 * np.pi * ETA) + np.cross(T, rho) / (8 * np.pi * ETA * r ** 3)
+    np.testing.assert_allclose(U, exact, rtol=1e-11, atol=1e-14)
+
+
+def test_flow_of_strain_and_dipole_modes():
+    """One force-free sphere with only the strain mode V^(2s) = a E, then only the dipole
+    mode V^(3t) = d: its flow is the classical strain solution, then the potential dipole
+    (d/10)(a/r)^3 (3 (d.r^) r^ - d) (both derived from the surface velocity v = V^(l+1).Y^(l)
+    / (l!(2l-1)!!) of Sec. III)."""
+    from oracle import flow
+    rng = np.random.default_rng(22)
+    R0 = np.zeros((1, 3))
+    z = np.zeros((1, 3))
+    E = rng.normal(size=(3, 3))
+    E = (E + E.T) / 2
+    E -= np.trace(E) / 3 * np.eye(3)
+    d = rng.normal(size=3)
+    for which in ("strain", "dipole"):
+        VH = np.zeros((1, 8))
+        if which == "strain":
+            VH[0, :5] = tensors.pack_stf(A * E)
+        else:
+            VH[0, 5:8] = galerkin.vec_to_packed(d)
+        _, _, QH = galerkin.solve(R0, z, z, VH, z, z, A, ETA, 2)
+        X = _exterior_points(R0[0], rng, 10, 1.6, 5.0)
+        U = flow.flow(X, R0, flow.internal_coefficients(z, z, QH, A, 2), A, ETA, 2)
+        r = np.linalg.norm(X, axis=1)[:, None]
+        if which == "strain":
+            xEx = np.einsum("mi,ij,mj->m", X, E, X)[:, None]
+            exact = 2.5 * A ** 3 * xEx * X / r ** 5 + A ** 5 * (X @ E.T / r ** 5 - 2.5 * xEx * X / r ** 7)
+        else:
+            n = X / r
+            exact = (A / r) ** 3 * (3 * (n @ d)[:, None] * n - d) / 10
+        np.testing.assert_allclose(U, exact, rtol=1e-10, atol=1e-14)
