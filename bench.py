@@ -575,6 +575,51 @@ def trajectory_trap(ctx, gbi, dev, stream, R_init, p_init, k_trap, steps, dt, ta
                                "sampled every %d steps over the last %d%% of steps" % (every, int(100 * tail))}
 
 
+def squirmer_pair_orbits(ctx, gbi, dev, stream):
+    """Two squirmers in a harmonic trap (Sec. V, two-particle discussion): both on the sphere
+    R* = 12.56 a, pointing outwards, the second at theta0 from the first; superposition
+    dynamics (l <= 2, FP32) for 40 rotational times tau_r = 8 pi eta a / k.  Reported per
+    theta0: the range of the angle between the particles, their largest change of
+    orientation (zero for the frozen theta0 = 180 degrees) and how often the angle turns."""
+    import torch
+    import workloads
+    B1, B2, Rs = 0.15, -1.0 / 12.0, 12.56
+    eta = workloads.ETA_DEFAULT
+    k = 6 * math.pi * eta * (2 * B1 / 3) / Rs
+    tau_r = 8 * math.pi * eta / k
+    dt = 0.5
+    every = 50
+    nsteps = int(40 * tau_r / dt) // every * every
+    prm = gbi.params(a=1.0, eta=eta, trunc=2, precision=1)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {"B1": B1, "B2": B2, "R_star_a": Rs, "k_trap": k, "tau_r": tau_r, "dt": dt, "steps": nsteps}
+    total_ms = 0.0
+    for th in (180.0, 115.0, 190.0, 260.0):
+        t = math.radians(th)
+        u = [[0.0, 0.0, 1.0], [math.sin(t), 0.0, math.cos(t)]]
+        R = torch.tensor(u, dtype=torch.float64, device=dev) * Rs
+        p = torch.tensor(u, dtype=torch.float64, device=dev)
+        p0 = p.clone()
+        angles, rot = [], 0.0
+        for _ in range(nsteps // every):
+            ev0.record(stream)
+            ctx.squirmer_step(prm, R, p, dt, k, B1, B2, True, every)
+            ev1.record(stream)
+            ev1.synchronize()
+            total_ms += ev0.elapsed_time(ev1)
+            c = float((R[0] @ R[1]) / (R[0].norm() * R[1].norm()))
+            angles.append(math.degrees(math.acos(max(-1.0, min(1.0, c)))))
+            rot = max(rot, float((p - p0).abs().max()))
+        d = [b - a for a, b in zip(angles, angles[1:])]
+        turns = sum(1 for a, b in zip(d, d[1:]) if a * b < 0)
+        out["theta0_%d" % int(th)] = {"angle_min_deg": min(angles), "angle_max_deg": max(angles),
+                                      "angle_final_deg": angles[-1], "max_orientation_change": rot,
+                                      "angle_turning_points": turns,
+                                      "radius_final_a": [float(R[0].norm()), float(R[1].norm())]}
+    out["steps_per_s"] = 4 * nsteps / (total_ms / 1e3)
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -814,6 +859,9 @@ def run_ours(args):
                              "traffic": None},
                 "grid": "64^3 points on the suspension's cube (side %.1f a)" % side}
 
+    # ---- two squirmers in a trap: the frozen opposite pair and the orbits of other angles
+    pair_orbits = squirmer_pair_orbits(ctx, gbi, dev, stream)
+
     # ---- trajectories: N = 64 FP64 re-solved steps; N = 10^4 superposition trap (10^4 steps)
     try:
         traj64 = trajectory_n64(ctx, gbi, dev, stream)
@@ -927,7 +975,7 @@ def run_ours(args):
                 "roofline": roofline,
                 "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
                 "superposition": superposition, "flow_field": flowline, "config1_trajectory": traj64, "config3_trajectory": traj3,
-                "config3_paper_geometry": trajp, "batched": batched, "learned_nearfield": learned,
+                "config3_paper_geometry": trajp, "squirmer_pair_orbits": pair_orbits, "batched": batched, "learned_nearfield": learned,
                 "tuned_wpt": dict(zip(TUNED_PASSES, tuned))}
         print(json.dumps(line), flush=True)
     ctx.close()

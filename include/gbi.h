@@ -211,6 +211,21 @@ gbi_status gbi_trap_step(gbi_ctx* ctx, const gbi_params* params, int N, double d
                          double vs, double s0, double d0, int superposition, int nsteps,
                          double* R, double* p, gbi_info* info);
 
+/* Squirmers (Sec. V, Lighthill-Blake slip with the first two modes): the active slip
+ * v^a = (nn - I).[B1 p + B2 (pp - I/3).n] has the tensorial-harmonic coefficients
+ * V^a = 2 B1 p / 3, V^(2s) = -3/5 B2 (pp - I/3), V^(3t) = 10/3 B1 p and
+ * V^(4t) = 7 B2 (pp - I/3) (every other mode zero; 4t is kept for trunc >= 3).
+ * gbi_squirmer_inputs writes them with the trap forcing F^e = -k_trap R, T^e = 0,
+ * Omega^a = 0 (layouts as gbi_trap_inputs); gbi_squirmer_step is gbi_trap_step with
+ * these inputs re-evaluated from (R, p) at every step.  The paper prints 15/2 V^a and
+ * 140/3 B2 for the 3t and 4t coefficients; the values here are the projection of the
+ * printed slip onto the modes as this library normalises them. */
+gbi_status gbi_squirmer_inputs(gbi_ctx* ctx, int N, int trunc, double k_trap, double B1, double B2,
+                               const double* R, const double* p, double* Fe, double* Te, double* Va, double* Oa,
+                               double* VH);
+gbi_status gbi_squirmer_step(gbi_ctx* ctx, const gbi_params* params, int N, double dt, double k_trap, double B1,
+                             double B2, int superposition, int nsteps, double* R, double* p, gbi_info* info);
+
 /* Flow field (Sec. III, Eq. flow_expression / galerkin_representation_flow_yl): the
  * velocity at M points X [M][3] in the fluid around a solved suspension,
  *   v(x) = -(1/(8 pi eta)) sum_m [F^l' grad^(l') G](x - R_m) . Q_m,   Q^L = F^L,

@@ -63,6 +63,9 @@ _SIGS = {
     "gbi_trap_inputs": (_I, [_VP, _I, _I, _D, _D, _D, _D] + [_VP] * 7),
     "gbi_trap_step": (_I, [_VP, ctypes.POINTER(gbi_params), _I, _D, _D, _D, _D, _D, _I, _I, _VP, _VP,
                            ctypes.POINTER(gbi_info)]),
+    "gbi_squirmer_inputs": (_I, [_VP, _I, _I, _D, _D, _D] + [_VP] * 7),
+    "gbi_squirmer_step": (_I, [_VP, ctypes.POINTER(gbi_params), _I, _D, _D, _D, _D, _I, _I, _VP, _VP,
+                               ctypes.POINTER(gbi_info)]),
     "gbi_flow": (_I, [_VP, ctypes.POINTER(gbi_params), _I, _VP, _VP, _VP, _VP, _I, _VP, _VP,
                       ctypes.POINTER(ctypes.c_int)]),
     "gbi_batch_trap_step": (_I, [_VP, ctypes.POINTER(gbi_params), _I, ctypes.POINTER(ctypes.c_int), _D, _D, _D, _D,
@@ -448,6 +451,23 @@ class Context:
         self._check(lib().gbi_kernel_stats(self._h, int(cls), ctypes.byref(ms), ctypes.byref(n), ctypes.byref(fl)),
                     "gbi_kernel_stats")
         return dict(ms=ms.value, launches=n.value, flops=fl.value)
+
+    def squirmer_inputs(self, N, trunc, k_trap, B1, B2, R, p):
+        import torch
+        z = lambda *shape: torch.empty(shape, dtype=torch.float64, device=R.device)
+        out = dict(Fe=z(N, 3), Te=z(N, 3), Va=z(N, 3), Oa=z(N, 3), VH=z(N, max(h(trunc), 1)))
+        self._check(lib().gbi_squirmer_inputs(self._h, int(N), int(trunc), float(k_trap), float(B1), float(B2),
+                                              _ptr(R), _ptr(p), _ptr(out["Fe"]), _ptr(out["Te"]), _ptr(out["Va"]),
+                                              _ptr(out["Oa"]), _ptr(out["VH"])), "gbi_squirmer_inputs")
+        return out
+
+    def squirmer_step(self, prm, R, p, dt, k_trap, B1, B2, superposition, nsteps):
+        info = gbi_info()
+        st = lib().gbi_squirmer_step(self._h, ctypes.byref(prm), int(R.shape[0]), float(dt), float(k_trap),
+                                     float(B1), float(B2), int(bool(superposition)), int(nsteps), _ptr(R), _ptr(p),
+                                     ctypes.byref(info))
+        self._check(st, "gbi_squirmer_step")
+        return info
 
     def flow(self, prm, R, Fe, Te, QH, X, U=None):
         """gbi_flow: the flow at points X [M][3] of a solved suspension; returns (U, inside count)."""

@@ -19,7 +19,7 @@
 namespace gbi {
 namespace {
 
-__global__ void k_trap_inputs(int N, double k_trap, double vs, double s0, double d0, int h,
+__global__ void k_trap_inputs(int N, double k_trap, double vs, double s0, double d0, double q0, int h,
                               const double* __restrict__ R, const double* __restrict__ p, double* Fe,
                               double* Te, double* Va, double* Oa, double* VH) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
@@ -41,6 +41,19 @@ __global__ void k_trap_inputs(int N, double k_trap, double vs, double s0, double
   vh[5] = d0 * py;
   vh[6] = d0 * pz;
   vh[7] = d0 * px;
+  // V^(4t) = q0 (pp - I/3): the degenerate octupole of a squirmer (trunc >= 3)
+  if (h >= 25 && q0 != 0.0)
+    for (int i = 0; i < 5; ++i) vh[20 + i] = q0 * q[i];
+}
+
+// Modes of a squirmer with the Lighthill-Blake slip of Sec. V, B1 and B2: from the slip's
+// tensorial-harmonic coefficients, V^a = 2 B1 p / 3, V^(2s) = -3/5 B2 (pp - I/3),
+// V^(3t) = 10/3 B1 p and V^(4t) = 7 B2 (pp - I/3) (the trap parameters vs, s0, d0, q0).
+struct SquirmerModes {
+  double vs, s0, d0, q0;
+};
+inline SquirmerModes squirmer_modes(double B1, double B2) {
+  return SquirmerModes{2.0 * B1 / 3.0, -0.6 * B2, 10.0 * B1 / 3.0, 7.0 * B2};
 }
 
 // With rec set (a trap step replayed inside the solve graph) the update is skipped when
@@ -432,8 +445,8 @@ namespace {
 // independent ones (system s = spheres [offsets[s], offsets[s+1]), each with its own trap
 // centred at the origin of the coordinates).
 gbi_status trap_steps(gbi_ctx* ctx, const gbi_params* prm, int nsys, const int* offsets, int N, double dt,
-                      double k_trap, double vs, double s0, double d0, int superposition, int nsteps, double* R,
-                      double* p, gbi_info* info) {
+                      double k_trap, double vs, double s0, double d0, double q0, int superposition, int nsteps,
+                      double* R, double* p, gbi_info* info) {
   if (!ctx || !valid_params(prm) || N < 0 || nsteps < 0) return GBI_ERR_ARG;
   gbi_info total{};
   if (N == 0 || nsteps == 0) {
@@ -452,7 +465,7 @@ gbi_status trap_steps(gbi_ctx* ctx, const gbi_params* prm, int nsys, const int* 
   GBI_TRY(ensure(ctx, ctx->tQH, sizeof(double) * (size_t)h * N));
   gbi_status st = GBI_OK;
   auto trap_inputs = [&]() -> gbi_status {
-    k_trap_inputs<<<grid1(N), 256, 0, ctx->stream>>>(N, k_trap, vs, s0, d0, h, R, p, P<double>(ctx->tFe),
+    k_trap_inputs<<<grid1(N), 256, 0, ctx->stream>>>(N, k_trap, vs, s0, d0, q0, h, R, p, P<double>(ctx->tFe),
                                                      P<double>(ctx->tTe), P<double>(ctx->tVa), P<double>(ctx->tOa),
                                                      P<double>(ctx->tVH));
     ++ctx->launches;
@@ -472,10 +485,10 @@ gbi_status trap_steps(gbi_ctx* ctx, const gbi_params* prm, int nsys, const int* 
   hooks.before = trap_inputs;
   hooks.after = euler;
   {
-    double pr[5] = {dt, k_trap, vs, s0, d0};
-    long long b[5];
+    double pr[6] = {dt, k_trap, vs, s0, d0, q0};
+    long long b[6];
     std::memcpy(b, pr, sizeof(pr));
-    hooks.key.assign(b, b + 5);
+    hooks.key.assign(b, b + 6);
     hooks.key.push_back((long long)(uintptr_t)R);
     hooks.key.push_back((long long)(uintptr_t)p);
   }
@@ -537,15 +550,22 @@ extern "C" {
 gbi_status gbi_trap_step(gbi_ctx* ctx, const gbi_params* prm, int N, double dt, double k_trap, double vs,
                          double s0, double d0, int superposition, int nsteps, double* R, double* p,
                          gbi_info* info) {
-  return trap_steps(ctx, prm, 1, nullptr, N, dt, k_trap, vs, s0, d0, superposition, nsteps, R, p, info);
+  return trap_steps(ctx, prm, 1, nullptr, N, dt, k_trap, vs, s0, d0, 0.0, superposition, nsteps, R, p, info);
+}
+
+gbi_status gbi_squirmer_step(gbi_ctx* ctx, const gbi_params* prm, int N, double dt, double k_trap, double B1,
+                             double B2, int superposition, int nsteps, double* R, double* p, gbi_info* info) {
+  const SquirmerModes m = squirmer_modes(B1, B2);
+  return trap_steps(ctx, prm, 1, nullptr, N, dt, k_trap, m.vs, m.s0, m.d0, m.q0, superposition, nsteps, R, p,
+                    info);
 }
 
 gbi_status gbi_batch_trap_step(gbi_ctx* ctx, const gbi_params* prm, int nsys, const int* offsets_host, double dt,
                                double k_trap, double vs, double s0, double d0, int superposition, int nsteps,
                                double* R, double* p, gbi_info* info) {
   if (!ctx || nsys < 1 || !offsets_host || !valid_offsets(nsys, offsets_host)) return GBI_ERR_ARG;
-  return trap_steps(ctx, prm, nsys, offsets_host, offsets_host[nsys], dt, k_trap, vs, s0, d0, superposition, nsteps,
-                    R, p, info);
+  return trap_steps(ctx, prm, nsys, offsets_host, offsets_host[nsys], dt, k_trap, vs, s0, d0, 0.0, superposition,
+                    nsteps, R, p, info);
 }
 
 gbi_status gbi_trap_inputs(gbi_ctx* ctx, int N, int trunc, double k_trap, double vs, double s0, double d0,
@@ -554,7 +574,22 @@ gbi_status gbi_trap_inputs(gbi_ctx* ctx, int N, int trunc, double k_trap, double
   if (!ctx || N < 0 || d_of(trunc) < 0) return GBI_ERR_ARG;
   if (N == 0) return GBI_OK;
   if (!R || !p || !Fe || !Te || !Va || !Oa || !VH) return GBI_ERR_ARG;
-  k_trap_inputs<<<grid1(N), 256, 0, ctx->stream>>>(N, k_trap, vs, s0, d0, gbi_h(trunc), R, p, Fe, Te, Va, Oa, VH);
+  k_trap_inputs<<<grid1(N), 256, 0, ctx->stream>>>(N, k_trap, vs, s0, d0, 0.0, gbi_h(trunc), R, p, Fe, Te, Va, Oa,
+                                                   VH);
+  ++ctx->launches;
+  GBI_CHECK(cudaGetLastError());
+  return GBI_OK;
+}
+
+gbi_status gbi_squirmer_inputs(gbi_ctx* ctx, int N, int trunc, double k_trap, double B1, double B2,
+                               const double* R, const double* p, double* Fe, double* Te, double* Va, double* Oa,
+                               double* VH) {
+  if (!ctx || N < 0 || d_of(trunc) < 0) return GBI_ERR_ARG;
+  if (N == 0) return GBI_OK;
+  if (!R || !p || !Fe || !Te || !Va || !Oa || !VH) return GBI_ERR_ARG;
+  const SquirmerModes m = squirmer_modes(B1, B2);
+  k_trap_inputs<<<grid1(N), 256, 0, ctx->stream>>>(N, k_trap, m.vs, m.s0, m.d0, m.q0, gbi_h(trunc), R, p, Fe, Te,
+                                                   Va, Oa, VH);
   ++ctx->launches;
   GBI_CHECK(cudaGetLastError());
   return GBI_OK;

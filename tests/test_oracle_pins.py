@@ -572,3 +572,40 @@ def test_flow_of_strain_and_dipole_modes():
             n = X / r
             exact = (A / r) ** 3 * (3 * (n @ d)[:, None] * n - d) / 10
         np.testing.assert_allclose(U, exact, rtol=1e-10, atol=1e-14)
+
+
+# ---------------------------------------------------------------- squirmer
+
+def test_squirmer_modes_from_the_slip():
+    """Squirmer slip v^a = (nn - I).[B1 p + B2 (pp - I/3).n] (Sec. V): its tensorial-harmonic
+    coefficients give the printed V^a = 2 B1 p / 3 and V^(20) = -3/5 B2 (pp - I/3), no
+    rotation, the potential dipole V^(32) = 10/3 B1 p and the degenerate octupole
+    V^(42) = 7 B2 (pp - I/3) in the oracle's embedding (the slip's l = 2 and l = 3 parts,
+    (B1/3) Y^(2).p and (B2/15)(pp - I/3):Y^(3)), and nothing else; the expansion
+    sum_l V^(l+1).Y^(l) / (l!(2l-1)!!) rebuilds the slip."""
+    from oracle.tensors import dfact, tsh
+    rng = np.random.default_rng(31)
+    p = rng.normal(size=3)
+    p /= np.linalg.norm(p)
+    B1, B2 = 0.21, -0.37
+    S = np.outer(p, p) - np.eye(3) / 3
+    Va, Oa, VH = dynamics.squirmer_modes(p, B1, B2, 3)
+    np.testing.assert_allclose(Va, 2 * B1 / 3 * p, atol=1e-14)
+    np.testing.assert_allclose(Oa, 0.0, atol=1e-14)
+    np.testing.assert_allclose(VH[0:5], tensors.pack_stf(-0.6 * B2 * S), atol=1e-14)
+    np.testing.assert_allclose(VH[5:8], galerkin.vec_to_packed(10 / 3 * B1 * p), atol=1e-14)
+    np.testing.assert_allclose(VH[8:20], 0.0, atol=1e-14)                 # 3a, 3s
+    np.testing.assert_allclose(VH[20:25], tensors.pack_stf(7 * B2 * S), atol=1e-13)
+    # rebuild the slip from the reducible coefficients of the truncation (l <= 3)
+    MB = tensors.ModeBasis(3)
+    y = np.concatenate([galerkin.vec_to_packed(-Va), np.zeros(3), VH])
+    n = rng.normal(size=(6, 3))
+    n /= np.linalg.norm(n, axis=1, keepdims=True)
+    v = np.zeros((6, 3))
+    for L in (1, 2, 3, 4):
+        l = L - 1
+        T = sum(y[i] * MB.scale[i] * e for i, e in enumerate(MB.vectors) if MB.rank[i] == L)
+        for k in range(6):
+            Y = tsh(l, n[k])
+            v[k] += (np.tensordot(T, Y, axes=l) if l > 0 else T * Y) / (math.factorial(l) * dfact(2 * l - 1))
+    np.testing.assert_allclose(v, dynamics.squirmer_slip(p, B1, B2, n), atol=1e-13)
