@@ -218,12 +218,19 @@ def embed(L, sigma, T):
 MODES = [("1s", 1, 0), ("2a", 2, 1),
          ("2s", 2, 0), ("3t", 3, 2),
          ("3a", 3, 1), ("3s", 3, 0), ("4t", 4, 2),
-         ("4a", 4, 1), ("4s", 4, 0), ("5t", 5, 2)]
-N_HMODES = {2: 2, 3: 5, 4: 8}     # truncation l<=L keeps MODES[2 : 2 + N_HMODES[L]]
+         ("4a", 4, 1), ("4s", 4, 0), ("5t", 5, 2),
+         ("5a", 5, 1), ("5s", 5, 0), ("6t", 6, 2),
+         ("6a", 6, 1), ("6s", 6, 0), ("7t", 7, 2)]
+# truncation l<=L keeps MODES[2 : 2 + N_HMODES[L]] as higher modes: the nested sets
+# {1s, 2a} + {ks, ka, (k+1)t : 2 <= k <= L}.  MINIMAL (code 40) is the paper's minimal
+# truncation of Sec. III: every mode of rank <= 4 (Y^(0..3)), 47 components per sphere
+# (l <= 4 without 5t).
+MINIMAL = 40
+N_HMODES = {2: 2, 3: 5, 4: 8, 5: 11, 6: 14, MINIMAL: 7}
 
 
 def modes_for(trunc):
-    """(L modes, H modes) lists of (name, L, sigma) for truncation l <= trunc."""
+    """(L modes, H modes) lists of (name, L, sigma) for truncation l <= trunc (or MINIMAL)."""
     return MODES[:2], MODES[2:2 + N_HMODES[trunc]]
 
 

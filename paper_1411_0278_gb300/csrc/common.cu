@@ -18,6 +18,8 @@ GBI_DECL(f32)
 GBI_DECL(f64)
 GBI_DECL(df)
 #undef GBI_DECL
+cudaError_t launch_pairs_f64_5(int, int, const PairArgs&, cudaStream_t);
+cudaError_t launch_pairs_f64_40(int, int, const PairArgs&, cudaStream_t);
 
 // precision: 0 = FP64, 1 = FP32, 2 = double-float on the FP32 pipe
 cudaError_t launch_pairs(int trunc, int rows, int cols, int precision, const PairArgs& args,
@@ -27,6 +29,11 @@ cudaError_t launch_pairs(int trunc, int rows, int cols, int precision, const Pai
   if (trunc == 3) return launch_pairs_##P##_3(rows, cols, args, stream);  \
   if (trunc == 4) return launch_pairs_##P##_4(rows, cols, args, stream);  \
   return cudaErrorInvalidValue;
+  // l <= 5 and the minimal set: FP64 passes only
+  if (fp64_only(trunc)) {
+    if (precision != 0) return cudaErrorInvalidValue;
+    return trunc == 5 ? launch_pairs_f64_5(rows, cols, args, stream) : launch_pairs_f64_40(rows, cols, args, stream);
+  }
   if (precision == 1) { GBI_DISPATCH(f32) }
   if (precision == 2) { GBI_DISPATCH(df) }
   GBI_DISPATCH(f64)
@@ -38,6 +45,8 @@ double pair_flops(int trunc, int rows, int cols) {
   if (trunc == 2) return gbi_t2_flops[rows][cols];
   if (trunc == 3) return gbi_t3_flops[rows][cols];
   if (trunc == 4) return gbi_t4_flops[rows][cols];
+  if (trunc == 5) return gbi_t5_flops[rows][cols];
+  if (trunc == 40) return gbi_t40_flops[rows][cols];
   return 0.0;
 }
 }  // namespace gbi
@@ -146,7 +155,7 @@ cudaError_t launch_records(bool dfl, int N, int nc, const double* x, const int* 
 }
 
 int ncols_of(int trunc, int cols) {
-  const int D = trunc == 2 ? GbiTrunc2::D : trunc == 3 ? GbiTrunc3::D : GbiTrunc4::D;
+  const int D = d_of(trunc);
   return cols == SET_L ? 6 : cols == SET_H ? D - 6 : D;
 }
 
@@ -222,7 +231,7 @@ cudaError_t run_pairs(gbi_ctx* ctx, int trunc, int rows, int cols, int precision
     if (ensure(ctx, ctx->x32, bytes) != GBI_OK) return cudaErrorMemoryAllocation;
     ColScale cs;
     const int c0 = cols == SET_H ? 6 : 0;
-    for (int i = 0; i < 54; ++i) cs.v[i] = (i < nc) ? args.colscale[c0 + i] : 1.0;
+    for (int i = 0; i < kMaxD; ++i) cs.v[i] = (i < nc) ? args.colscale[c0 + i] : 1.0;
     const cudaError_t e = launch_records(precision == 2, args.N, nc, args.x, args.x_index, args.x_stride,
                                          args.active, cs, P<float>(ctx->x32), ctx->stream);
     if (e != cudaSuccess) return e;
@@ -241,9 +250,34 @@ cudaError_t run_trap(gbi_ctx* ctx, const TrapArgs& t, int precision) {
                [&] { return launch_trap(t, precision, ctx->trapbuf.p, ctx->stream); });
 }
 
-int d_of(int trunc) { return trunc == 2 ? GbiTrunc2::D : trunc == 3 ? GbiTrunc3::D : trunc == 4 ? GbiTrunc4::D : -1; }
-const double* scale_tab(int trunc) { return trunc == 2 ? gbi_t2_scale : trunc == 3 ? gbi_t3_scale : gbi_t4_scale; }
-const double* self_tab(int trunc) { return trunc == 2 ? gbi_t2_self : trunc == 3 ? gbi_t3_self : gbi_t4_self; }
+int d_of(int trunc) {
+  switch (trunc) {
+    case 2: return GbiTrunc2::D;
+    case 3: return GbiTrunc3::D;
+    case 4: return GbiTrunc4::D;
+    case 5: return GbiTrunc5::D;
+    case 40: return GbiTrunc40::D;
+    default: return -1;
+  }
+}
+const double* scale_tab(int trunc) {
+  switch (trunc) {
+    case 2: return gbi_t2_scale;
+    case 3: return gbi_t3_scale;
+    case 4: return gbi_t4_scale;
+    case 5: return gbi_t5_scale;
+    default: return gbi_t40_scale;
+  }
+}
+const double* self_tab(int trunc) {
+  switch (trunc) {
+    case 2: return gbi_t2_self;
+    case 3: return gbi_t3_self;
+    case 4: return gbi_t4_self;
+    case 5: return gbi_t5_self;
+    default: return gbi_t40_self;
+  }
+}
 
 // ---------------------------------------------------------------------------------
 // small kernels
@@ -331,7 +365,7 @@ gbi_status setup_call(gbi_ctx* ctx, Setup& s, int N, int trunc, double a, double
   s.eta = eta;
   const double* sc = scale_tab(trunc);
   const double* sg = self_tab(trunc);
-  for (int i = 0; i < 54; ++i) {
+  for (int i = 0; i < kMaxD; ++i) {
     s.scale.v[i] = i < s.D ? sc[i] : 1.0;
     s.selfg.v[i] = i < s.D ? sg[i] : 0.0;
     s.ones.v[i] = 1.0;
@@ -367,10 +401,10 @@ PairArgs pair_args(const Setup& s, const double* x, double* y, double alpha, dou
   p.alpha = alpha;
   p.beta = beta;
   p.add_self = add_self;
-  for (int i = 0; i < 54; ++i) {
+  for (int i = 0; i < kMaxD; ++i) {
     // colscale is indexed by absolute component; callers pass H-relative scales with col0 = 6
     const int src = i - col0;
-    p.colscale[i] = (src >= 0 && src < 54) ? colscale.v[src] : 1.0;
+    p.colscale[i] = (src >= 0 && src < kMaxD) ? colscale.v[src] : 1.0;
     p.selfg[i] = s.selfg.v[i];
   }
   p.min_r2_bits = nullptr;
@@ -471,8 +505,9 @@ gbi_status make_batch(gbi_ctx* ctx, int nsys, const int* offsets_host, Batch& B)
 bool valid_params(const gbi_params* p) {
   if (!p) return false;
   if (!(p->a > 0) || !(p->eta > 0)) return false;
-  if (p->trunc < 2 || p->trunc > 4) return false;
+  if (d_of(p->trunc) < 0) return false;
   if (p->precision < 0 || p->precision > 3) return false;
+  if (fp64_only(p->trunc) && p->precision != 0) return false;
   return true;
 }
 

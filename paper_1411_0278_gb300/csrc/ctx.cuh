@@ -152,7 +152,7 @@ cudaError_t timed(gbi_ctx* ctx, int cls, double flops, int nlaunch, F&& launch) 
 }
 
 struct ColScale {
-  double v[54];
+  double v[kMaxD];
 };
 
 cudaError_t launch_records(bool dfl, int N, int nc, const double* x, const int* xi, size_t xs, const int* active,
@@ -177,7 +177,7 @@ const double* scale_tab(int trunc);
 const double* self_tab(int trunc);
 
 struct Scales {
-  double v[54];
+  double v[kMaxD];
 };
 
 __global__ void k_pack_lower(int N, double a, double c2a, const double* __restrict__ Fe,

@@ -125,9 +125,25 @@ __global__ void __launch_bounds__(kFlowThreads) k_flow(const FlowArgs f) {
 template <int TR>
 cudaError_t launch_flow_t(bool fp32, const FlowArgs& f, cudaStream_t st) {
   const dim3 grid((f.M + kFlowThreads - 1) / kFlowThreads);
-  if (fp32) k_flow<TR, float><<<grid, kFlowThreads, 0, st>>>(f);
-  else k_flow<TR, double><<<grid, kFlowThreads, 0, st>>>(f);
+  if constexpr (TR == 5 || TR == 40) {
+    // l <= 5 and the minimal set: FP64 only
+    if (fp32) return cudaErrorInvalidValue;
+    k_flow<TR, double><<<grid, kFlowThreads, 0, st>>>(f);
+  } else {
+    if (fp32) k_flow<TR, float><<<grid, kFlowThreads, 0, st>>>(f);
+    else k_flow<TR, double><<<grid, kFlowThreads, 0, st>>>(f);
+  }
   return cudaGetLastError();
+}
+
+double flops_point(int trunc) {
+  switch (trunc) {
+    case 2: return gbi_t2_flops_point;
+    case 3: return gbi_t3_flops_point;
+    case 4: return gbi_t4_flops_point;
+    case 5: return gbi_t5_flops_point;
+    default: return gbi_t40_flops_point;
+  }
 }
 
 }  // namespace
@@ -165,7 +181,7 @@ extern "C" gbi_status gbi_flow(gbi_ctx* ctx, const gbi_params* prm, int N, const
   if (N > 0) {
     // F^L and Q^H in internal coordinates, component-major [D][N]
     Scales hscale;
-    for (int i = 0; i < 54; ++i) hscale.v[i] = (i < h) ? s.scale.v[6 + i] : 1.0;
+    for (int i = 0; i < kMaxD; ++i) hscale.v[i] = (i < h) ? s.scale.v[6 + i] : 1.0;
     k_pack_lower<<<grid1(N), 256, 0, ctx->stream>>>(N, s.a, s.scale.v[3], Fe, Te, x, nullptr);
     k_pack_higher<<<grid1((size_t)N * h), 256, 0, ctx->stream>>>(N, h, QH, hscale, 1.0, x + (size_t)6 * N, nullptr);
     ctx->launches += 2;
@@ -173,19 +189,21 @@ extern "C" gbi_status gbi_flow(gbi_ctx* ctx, const gbi_params* prm, int N, const
     if (fp32) {
       GBI_TRY(ensure(ctx, ctx->flowrec, sizeof(float) * rec_floats(D, false) * (size_t)N));
       ColScale cs;
-      for (int i = 0; i < 54; ++i) cs.v[i] = 1.0;
+      for (int i = 0; i < kMaxD; ++i) cs.v[i] = 1.0;
       GBI_CHECK(launch_records(false, N, D, x, nullptr, 0, nullptr, cs, P<float>(ctx->flowrec), ctx->stream));
       ++ctx->launches;
       f.rec = P<float>(ctx->flowrec);
     }
   }
-  const double flops = double(prm->trunc == 2 ? gbi_t2_flops_point : prm->trunc == 3 ? gbi_t3_flops_point
-                                                                                      : gbi_t4_flops_point) *
-                       double(N) * double(M);
+  const double flops = flops_point(prm->trunc) * double(N) * double(M);
   cudaError_t e = timed(ctx, fp32 ? 30 : 29, flops, 1, [&] {
-    if (prm->trunc == 2) return launch_flow_t<2>(fp32, f, ctx->stream);
-    if (prm->trunc == 3) return launch_flow_t<3>(fp32, f, ctx->stream);
-    return launch_flow_t<4>(fp32, f, ctx->stream);
+    switch (prm->trunc) {
+      case 2: return launch_flow_t<2>(fp32, f, ctx->stream);
+      case 3: return launch_flow_t<3>(fp32, f, ctx->stream);
+      case 4: return launch_flow_t<4>(fp32, f, ctx->stream);
+      case 5: return launch_flow_t<5>(fp32, f, ctx->stream);
+      default: return launch_flow_t<40>(fp32, f, ctx->stream);
+    }
   });
   GBI_CHECK(e);
   if (n_inside) {

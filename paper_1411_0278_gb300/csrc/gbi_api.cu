@@ -156,7 +156,7 @@ gbi_status tune_impl(gbi_ctx* ctx, int trunc, int nsys, const int* offsets, int 
     pa.x = x;
     pa.y = y;
     pa.alpha = 1.0;
-    for (int i = 0; i < 54; ++i) pa.colscale[i] = 1.0;
+    for (int i = 0; i < kMaxD; ++i) pa.colscale[i] = 1.0;
     if (batched) {
       pa.sys_of = sys_of;
       pa.sys_off = sys_off;
@@ -164,7 +164,7 @@ gbi_status tune_impl(gbi_ctx* ctx, int trunc, int nsys, const int* offsets, int 
     }
     const int nc = ncols_of(trunc, ps.cols);
     ColScale cs;
-    for (int i = 0; i < 54; ++i) cs.v[i] = 1.0;
+    for (int i = 0; i < kMaxD; ++i) cs.v[i] = 1.0;
     cudaError_t e = launch_records(ps.precision == 2, Ntot, nc, x, nullptr, 0, nullptr, cs, rec, ctx->stream);
     pa.x32 = rec;
     int best = 0;
@@ -306,6 +306,7 @@ gbi_status gbi_self_scalars(int trunc, double* out_host) {
 gbi_status gbi_apply(gbi_ctx* ctx, int N, int trunc, double a, int rows, int cols, int precision,
                      const double* R, const double* x, double* y, double alpha, double beta, int add_self) {
   if (!ctx || N < 0 || d_of(trunc) < 0 || !(a > 0) || precision < 0 || precision > 2) return GBI_ERR_ARG;
+  if (fp64_only(trunc) && precision != 0) return GBI_ERR_ARG;
   if (N == 0) return GBI_OK;
   if (!R || !x || !y) return GBI_ERR_ARG;
   const bool supported = (rows == SET_H && cols == SET_L) || (rows == SET_H && cols == SET_H) ||
@@ -371,7 +372,7 @@ gbi_status gbi_batch_superpose(gbi_ctx* ctx, const gbi_params* prm, int nsys, co
   double* xF = P<double>(ctx->xQ);
   double* xQH = P<double>(ctx->xQ) + (size_t)6 * N;
   Scales oneb;   // one-body Q^H = -8 pi eta a V^H / g, in internal coordinates
-  for (int i = 0; i < 54; ++i) oneb.v[i] = (i < h) ? s.scale.v[6 + i] * s.a / s.selfg.v[6 + i] : 1.0;
+  for (int i = 0; i < kMaxD; ++i) oneb.v[i] = (i < h) ? s.scale.v[6 + i] * s.a / s.selfg.v[6 + i] : 1.0;
   k_pack_lower<<<grid1(N), 256, 0, ctx->stream>>>(N, s.a, s.scale.v[3], Fe, Te, xF, nullptr);
   ++ctx->launches;
   k_pack_higher<<<grid1(nh), 256, 0, ctx->stream>>>(N, h, VH, oneb, -8.0 * kPi * s.eta, xQH, nullptr);
@@ -421,7 +422,7 @@ gbi_status gbi_superpose(gbi_ctx* ctx, const gbi_params* prm, int N, const doubl
   double* xF = P<double>(ctx->xQ);
   double* xQH = P<double>(ctx->xQ) + (size_t)6 * N;
   Scales oneb;   // one-body Q^H = -8 pi eta a V^H / g, in internal coordinates
-  for (int i = 0; i < 54; ++i) oneb.v[i] = (i < h) ? s.scale.v[6 + i] * s.a / s.selfg.v[6 + i] : 1.0;
+  for (int i = 0; i < kMaxD; ++i) oneb.v[i] = (i < h) ? s.scale.v[6 + i] * s.a / s.selfg.v[6 + i] : 1.0;
   k_pack_lower<<<grid1(N), 256, 0, ctx->stream>>>(N, s.a, s.scale.v[3], Fe, Te, xF, nullptr);
   ++ctx->launches;
   k_pack_higher<<<grid1(nh), 256, 0, ctx->stream>>>(N, h, VH, oneb, -8.0 * kPi * s.eta, xQH, nullptr);
@@ -596,7 +597,7 @@ gbi_status gbi_squirmer_inputs(gbi_ctx* ctx, int N, int trunc, double k_trap, do
 }
 
 gbi_status gbi_tune(gbi_ctx* ctx, int trunc, int nsys, const int* offsets, int reps, int* chosen) {
-  if (!ctx || d_of(trunc) < 0 || nsys < 1 || !offsets || reps < 0) return GBI_ERR_ARG;
+  if (!ctx || d_of(trunc) < 0 || fp64_only(trunc) || nsys < 1 || !offsets || reps < 0) return GBI_ERR_ARG;
   if (offsets[0] != 0) return GBI_ERR_ARG;
   for (int s = 0; s < nsys; ++s)
     if (offsets[s + 1] <= offsets[s]) return GBI_ERR_ARG;
@@ -636,7 +637,7 @@ gbi_status gbi_pass_status(gbi_ctx* ctx) {
 int gbi_pass_wpt(gbi_ctx* ctx, int trunc, int rows, int cols, int precision, int N, int batched) {
   if (!ctx || d_of(trunc) < 0 || rows < 0 || rows > 2 || cols < 0 || cols > 2 || N < 1) return -1;
   if (precision == 0) return 0;
-  if (precision != 1 && precision != 2) return -1;
+  if ((precision != 1 && precision != 2) || fp64_only(trunc)) return -1;
   const int req = ctx->force_wpt > 0 ? ctx->force_wpt : ctx->tuned_wpt(trunc, rows, cols, precision, N, batched != 0);
   return stream_wpt(trunc, precision, N, req, batched != 0);
 }
@@ -645,7 +646,7 @@ gbi_status gbi_set_profiling(gbi_ctx* ctx, int on) {
   if (!ctx) return GBI_ERR_ARG;
   drain_profile(ctx);
   ctx->prof = on != 0;
-  for (int i = 0; i < 30; ++i) {
+  for (int i = 0; i < 32; ++i) {
     ctx->stat_dead[i] = 0;
     ctx->stat_ms[i] = 0.0;
     ctx->stat_flops[i] = 0.0;
@@ -734,7 +735,7 @@ constexpr size_t kOffKry = kOffXVL + al256(sizeof(double) * 6 * kStaticMaxN);
 constexpr size_t kOffW = kOffKry + al256(sizeof(double) * (size_t)(kStaticMaxRestart + 1) * kStaticMaxNH);
 constexpr size_t kOffMin = kOffW + al256(sizeof(double) * kStaticMaxNH);
 constexpr size_t kOffX32 = kOffMin + 256;
-constexpr int kStaticMaxH = 48;           // the largest gbi_h (trunc 4)
+constexpr int kStaticMaxH = 48;           // the largest gbi_h taken here (trunc 4)
 // x32: per-sphere source records of a double-float pass over every column, rec_floats(D, df)
 // = 2 round4(h + 6) <= 2 (h + 9) floats per sphere, within the limits above
 constexpr size_t kStaticX32Floats = 2 * ((size_t)kStaticMaxNH + 9 * (size_t)kStaticMaxN);
@@ -767,7 +768,7 @@ extern "C" gbi_status gbi_solve_static(void* stream, const gbi_params* prm, int 
                                        gbi_info* info) {
   if (!valid_params(prm) || N < 0) return GBI_ERR_ARG;
   const int h = gbi_h(prm->trunc);
-  if (N > kStaticMaxN || (long long)N * h > kStaticMaxNH) return GBI_ERR_ARG;
+  if (h > kStaticMaxH || N > kStaticMaxN || (long long)N * h > kStaticMaxNH) return GBI_ERR_ARG;
   if (prm->restart > kStaticMaxRestart) return GBI_ERR_ARG;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kStaticMaxDevices) return GBI_ERR_CUDA;

@@ -11,6 +11,11 @@
 namespace gbi {
 
 constexpr double kPi = 3.14159265358979323846;
+// components per sphere of the largest truncation (l <= 5: 83), rounded up; sizes the
+// per-component tables passed to kernels by value
+constexpr int kMaxD = 84;
+// truncations whose pair passes exist in FP64 only: l <= 5 and the minimal set (code 40)
+inline bool fp64_only(int trunc) { return trunc == 5 || trunc == 40; }
 
 // Position layouts built once per call from the caller's [N][3] doubles:
 //   hi[n] = (float)R, lo[n] = (float)(R - hi)   -> rho = (hi_n - hi_m) + (lo_n - lo_m) in FP32
@@ -42,8 +47,8 @@ struct PairArgs {
   double* y;             // component-major, first component of the row set
   double alpha, beta;
   int add_self;
-  double colscale[54];   // per-column multiplier applied to x (preconditioner / unit scaling)
-  double selfg[54];      // one-body self scalars g (units 1/a) per component, for add_self
+  double colscale[kMaxD];   // per-column multiplier applied to x (preconditioner / unit scaling)
+  double selfg[kMaxD];    // one-body self scalars g (units 1/a) per component, for add_self
   unsigned int* min_r2_bits;   // optional: atomicMin of the smallest r^2 (float bits), may be null
   // device-side indexing (GMRES on the device): if x_index is set, the kernel reads
   // x + (*x_index) * x_stride; if active is set and *active == 0 the pass does nothing

@@ -35,6 +35,8 @@ template <int TR> struct Tab;
 GBI_TAB(2)
 GBI_TAB(3)
 GBI_TAB(4)
+GBI_TAB(5)
+GBI_TAB(40)
 #undef GBI_TAB
 
 template <int TR, int ROWS, int COLS, typename T>
@@ -50,9 +52,13 @@ __host__ __device__ __forceinline__ void couple(T e2, const T* xs, T* y) {
   GBI_C3(2)
   GBI_C3(3)
   GBI_C3(4)
+  GBI_C3(5)
+  GBI_C3(40)
   GBI_C(2, P, all, 3, 0)
   GBI_C(3, P, all, 3, 0)
   GBI_C(4, P, all, 3, 0)
+  GBI_C(5, P, all, 3, 0)
+  GBI_C(40, P, all, 3, 0)
 #undef GBI_C3
 #undef GBI_C
 }
@@ -62,6 +68,7 @@ template <typename T> struct DMats {
   T d2[gbi_dm2_n];
   T d3[gbi_dm3_n];
   T d4[gbi_dm4_n];
+  T d5[gbi_dm5_n];   // l <= 5 only (6t); unused members cost nothing once inlined
 };
 
 template <int K, typename T>
@@ -70,6 +77,7 @@ __host__ __device__ __forceinline__ void dapply(const DMats<T>& dm, const T* in,
   if constexpr (K == 2) gbi_dapply2<T>(dm.d2, in, out);
   if constexpr (K == 3) gbi_dapply3<T>(dm.d3, in, out);
   if constexpr (K == 4) gbi_dapply4<T>(dm.d4, in, out);
+  if constexpr (K == 5) gbi_dapply5<T>(dm.d5, in, out);
 }
 template <int K, typename T>
 __host__ __device__ __forceinline__ void dapplyT(const DMats<T>& dm, const T* in, T* out) {
@@ -77,6 +85,7 @@ __host__ __device__ __forceinline__ void dapplyT(const DMats<T>& dm, const T* in
   if constexpr (K == 2) gbi_dapplyT2<T>(dm.d2, in, out);
   if constexpr (K == 3) gbi_dapplyT3<T>(dm.d3, in, out);
   if constexpr (K == 4) gbi_dapplyT4<T>(dm.d4, in, out);
+  if constexpr (K == 5) gbi_dapplyT5<T>(dm.d5, in, out);
 }
 
 // v scaled by (a/r)^j = ep[j]; j = 0 leaves v untouched (no multiply by one).
@@ -212,6 +221,7 @@ __host__ __device__ __forceinline__ void pair_body(T dx, T dy, T dz, T a, const 
   if constexpr (MAXK >= 2) gbi_dmat2<T>(ct, -st, dm.d2);
   if constexpr (MAXK >= 3) gbi_dmat3<T>(ct, -st, dm.d3);
   if constexpr (MAXK >= 4) gbi_dmat4<T>(ct, -st, dm.d4);
+  if constexpr (MAXK >= 5) gbi_dmat5<T>(ct, -st, dm.d5);
   T ep[7];
   ep[0] = T(1);
 #pragma unroll

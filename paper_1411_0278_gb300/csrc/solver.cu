@@ -1495,7 +1495,7 @@ gbi_status solve_core(gbi_ctx* ctx, const gbi_params* prm, const Batch& B, const
   const GPtr gp = gptrs(ctx->gstate.p, restart, S, arnoldi_chunks(S, h));
   const double c2a = s.scale.v[3];
   Scales hscale;
-  for (int i = 0; i < 54; ++i) hscale.v[i] = (i < h) ? s.scale.v[6 + i] : 1.0;
+  for (int i = 0; i < kMaxD; ++i) hscale.v[i] = (i < h) ? s.scale.v[6 + i] : 1.0;
   auto batched = [&](PairArgs p, const int* flag) {
     p.sys_of = B.sys;
     p.nsys = B.S;

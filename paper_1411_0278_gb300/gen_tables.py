@@ -155,8 +155,12 @@ def solid_harmonic(k, mu):
 # ----------------------------------------------------------------------------
 
 MODES = [("1s", 1, 0), ("2a", 2, 1), ("2s", 2, 0), ("3t", 3, 2), ("3a", 3, 1), ("3s", 3, 0),
-         ("4t", 4, 2), ("4a", 4, 1), ("4s", 4, 0), ("5t", 5, 2)]
-NMODES = {2: 4, 3: 7, 4: 10}
+         ("4t", 4, 2), ("4a", 4, 1), ("4s", 4, 0), ("5t", 5, 2), ("5a", 5, 1), ("5s", 5, 0), ("6t", 6, 2)]
+# truncation l <= L keeps the first NMODES[L] modes; code 40 is the paper's minimal
+# truncation of Sec. III (every mode of rank <= 4, 47 components: l <= 4 without 5t)
+MINIMAL = 40
+NMODES = {2: 4, 3: 7, 4: 10, 5: 13, MINIMAL: 9}
+TRUNCS = (2, 3, 4, 5, MINIMAL)
 
 
 class Comp:
@@ -429,12 +433,13 @@ def emit(path):
     w = lines.append
     w("// Generated by paper_1411_0278_gb300/gen_tables.py -- do not edit.")
     w("// Pair-frame single-layer Galerkin couplings, packed-basis rotations and")
-    w("// self scalars for the truncations l<=2, 3, 4 (mode sets 1s 2a | 2s 3t | 3a 3s 4t | 4a 4s 5t).")
+    w("// self scalars for the truncations l<=2, 3, 4, 5 (mode sets 1s 2a | 2s 3t | 3a 3s 4t | 4a 4s 5t |")
+    w("// 5a 5s 6t) and the minimal truncation 40 (every mode of rank <= 4: l<=4 without 5t).")
     w("#pragma once")
     w("")
     w("#include \"df.cuh\"   // gbi_fmac: a * b + c in the arithmetic of T")
     w("")
-    maxk = 4
+    maxk = 5
     check_tables(maxk)
     # rotation about y: gbi_dmat<k>(c, s, dm) fills the nonzero entries of D^k(R_y(beta))
     # (c = cos beta, s = sin beta); gbi_dapply<k>/gbi_dapplyT<k> apply it or its transpose.
@@ -447,9 +452,14 @@ def emit(path):
         dm_nnz[k] = len(entries)
         w("static constexpr int gbi_dm%d_n = %d;" % (k, len(entries)))
         w("template <typename T> __host__ __device__ __forceinline__ void gbi_dmat%d(T c, T s, T* __restrict__ dm) {" % k)
-        w("  const T c2 = c * c; const T c3 = c2 * c; const T c4 = c2 * c2;")
-        w("  const T cp[5] = {T(1), c, c2, c3, c4}; (void)cp;")
-        w("  const T sp[5] = {s, c * s, c2 * s, c3 * s, c4 * s}; (void)sp;")
+        if k <= 4:
+            w("  const T c2 = c * c; const T c3 = c2 * c; const T c4 = c2 * c2;")
+            w("  const T cp[5] = {T(1), c, c2, c3, c4}; (void)cp;")
+            w("  const T sp[5] = {s, c * s, c2 * s, c3 * s, c4 * s}; (void)sp;")
+        else:
+            w("  const T c2 = c * c; const T c3 = c2 * c; const T c4 = c2 * c2; const T c5 = c4 * c;")
+            w("  const T cp[6] = {T(1), c, c2, c3, c4, c5}; (void)cp;")
+            w("  const T sp[6] = {s, c * s, c2 * s, c3 * s, c4 * s, c5 * s}; (void)sp;")
         for e, ((mu, nu), poly) in enumerate(entries):
             terms = []
             for (i, j), v in sorted(poly.items()):
@@ -501,11 +511,14 @@ def emit(path):
         w("  s6[%d] = %s;" % (idx, " + ".join(terms) or "T(0)"))
     w("}")
     w("")
-    for trunc in (2, 3, 4):
+    for trunc in TRUNCS:
         comps, cpl = couplings(trunc)
         d = len(comps)
         modes = MODES[:NMODES[trunc]]
-        w("// ---------------- truncation l <= %d: %d components per sphere" % (trunc, d))
+        if trunc == MINIMAL:
+            w("// ---------------- minimal truncation (every mode of rank <= 4): %d components per sphere" % d)
+        else:
+            w("// ---------------- truncation l <= %d: %d components per sphere" % (trunc, d))
         w("struct GbiTrunc%d {" % trunc)
         w("  static constexpr int D = %d;      // components per sphere (L + H)" % d)
         w("  static constexpr int NL = 6;")

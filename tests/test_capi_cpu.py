@@ -42,9 +42,9 @@ def test_every_declared_symbol_is_exported(gbi):
 
 
 def test_host_calls(gbi):
-    assert [gbi.h(t) for t in (2, 3, 4)] == [8, 25, 48]
-    assert [gbi.d(t) for t in (2, 3, 4)] == [14, 31, 54]
-    assert gbi.h(5) == -1
+    assert [gbi.h(t) for t in (2, 3, 4, 5, 40)] == [8, 25, 48, 77, 41]
+    assert [gbi.d(t) for t in (2, 3, 4, 5, 40)] == [14, 31, 54, 83, 47]
+    assert gbi.h(6) == -1 and gbi.h(1) == -1
     assert gbi.status_string(gbi.GBI_ERR_OVERLAP).startswith("spheres overlap")
     with pytest.raises(gbi.GbiError):
         gbi.component_scales(7)
@@ -78,7 +78,7 @@ def test_nearfield_calls_validate_without_a_device(gbi):
 
 def test_generated_tables_agree_with_oracle(gbi):
     from oracle import galerkin, tensors
-    for trunc in (2, 3, 4):
+    for trunc in (2, 3, 4, 5, tensors.MINIMAL):
         MB = tensors.ModeBasis(trunc)
         np.testing.assert_allclose(gbi.component_scales(trunc), MB.scale, rtol=1e-13)
         np.testing.assert_allclose(gbi.self_scalars(trunc), galerkin.self_scalars(trunc, 1.0), rtol=1e-11)

@@ -75,13 +75,22 @@ def _sl(code, d):
     return slice(0, d) if code == 0 else (slice(0, 6) if code == 1 else slice(6, d))
 
 
-@pytest.mark.parametrize("trunc,N", [(2, 150), (3, 150), (4, 70)])
+# l <= 5 and the paper's minimal truncation (every mode of rank <= 4) run in FP64 only
+FP64_ONLY = (5, tensors.MINIMAL)
+
+
+@pytest.mark.parametrize("trunc,N", [(2, 150), (3, 150), (4, 70), (5, 40), (tensors.MINIMAL, 70)])
 @pytest.mark.parametrize("rows,cols", [(2, 1), (2, 2), (1, 0), (0, 0)])
 @pytest.mark.parametrize("precision", [0, 1, 2])
 def test_apply_matches_dense_oracle(ctx, gbi, trunc, N, rows, cols, precision):
     if precision == 2 and rows == 0 and cols == 0:
         pytest.skip("double-float is instantiated for the solver passes only")
     R, _, s = cloud(N, 11 + trunc)
+    if trunc in FP64_ONLY and precision != 0:
+        z = torch.zeros((1, N), dtype=torch.float64, device="cuda")
+        with pytest.raises(gbi.GbiError):
+            ctx.apply(N, trunc, 1.0, rows, cols, precision, dev(R), z, z)
+        return
     a = 1.0
     A = assembled(N, 11 + trunc, trunc, a)
     MB = tensors.ModeBasis(trunc)
@@ -197,13 +206,18 @@ def _solve_case(gbi, ctx, R, p, s, trunc, precision, d0=0.02, Te_scale=0.01, rto
     return inp, V.cpu().numpy(), Om.cpu().numpy(), QH.cpu().numpy(), info
 
 
-@pytest.mark.parametrize("trunc,N", [(2, 64), (3, 40), (4, 24)])
+@pytest.mark.parametrize("trunc,N", [(2, 64), (3, 40), (4, 24), (5, 16), (tensors.MINIMAL, 24)])
 @pytest.mark.parametrize("precision", [0, 1, 2, 3])
 def test_solve_matches_dense_lu(ctx, gbi, trunc, N, precision):
     """Precision 3 sums the right-hand side and the outputs in FP32: V, Omega and Q^H then
     carry FP32 pair-sum rounding, bounded here by the 1e-5 pair-velocity bar (the
-    residual of the solve for that right-hand side still meets 1e-10)."""
+    residual of the solve for that right-hand side still meets 1e-10).  l <= 5 and the
+    minimal truncation take FP64 only: the mixed modes are refused."""
     R, p, s = cloud(N, 20 + trunc)
+    if trunc in FP64_ONLY and precision != 0:
+        with pytest.raises(gbi.GbiError):
+            _solve_case(gbi, ctx, R, p, s, trunc, precision)
+        return
     inp, V, Om, QH, info = _solve_case(gbi, ctx, R, p, s, trunc, precision)
     Vr, Omr, QHr = galerkin.solve(R, inp["Va"], inp["Oa"], inp["VH"], inp["Fe"], inp["Te"], s["a"], s["eta"], trunc)
     tol_v, tol_q = (1e-5, 1e-5) if precision == 3 else (1e-9, 1e-8)
@@ -220,6 +234,24 @@ def test_solve_matches_dense_lu(ctx, gbi, trunc, N, precision):
     assert info.pair_interactions == (info.matvecs_f32 + info.matvecs_f64) * N * (N - 1)
     if precision >= 1:
         assert info.matvecs_f32 > info.matvecs_f64
+
+
+def test_truncation_convergence_on_the_gpu(ctx, gbi):
+    """N = 96 spheres of the trap cloud (volume fraction 0.1), FP64 solves at l <= 3, 4, 5
+    and the minimal truncation: successive truncations move the velocities less and
+    less, and the minimal set (every mode of rank <= 4) is closer to l <= 5 than l <= 3
+    is (the convergence the oracle pins for pairs and triangles, at a size it does not
+    solve in seconds at l <= 5)."""
+    R, p, s = cloud(96, 41, phi=0.1)
+    V = {}
+    for trunc in (3, 4, 5, tensors.MINIMAL):
+        _, V[trunc], _, _, info = _solve_case(gbi, ctx, R, p, s, trunc, 0, rtol=1e-11)
+        assert info.rel_residual <= 1e-11
+    scale = np.abs(V[5]).max()
+    d34 = np.abs(V[4] - V[3]).max() / scale
+    d45 = np.abs(V[5] - V[4]).max() / scale
+    assert d45 < d34, (d34, d45)
+    assert np.abs(V[tensors.MINIMAL] - V[5]).max() < np.abs(V[3] - V[5]).max()
 
 
 def test_solve_config1_and_single_sphere(ctx, gbi):

@@ -363,14 +363,26 @@ def test_invariance_translation_rotation_permutation():
     np.testing.assert_allclose(Om5, Om[perm], atol=1e-14)
 
 
-def test_truncation_convergence():
-    R = np.array([[0.0, 0.0, 0.0], [2.6, 0.3, -0.2], [0.4, 2.7, 0.5]]) * A
-    p = np.array([[0, 0, 1.0], [1.0, 0, 0], [0, 0.6, 0.8]])
-    prm = dict(a=A, eta=ETA, k=0.05, vs=0.1, s0=0.05, d0=0.02)
-    out = {}
-    for tr in (2, 3, 4):
-        out[tr] = np.concatenate(dynamics.velocities(R, p, prm, tr, False), axis=1)
-    assert np.linalg.norm(out[4] - out[3]) < np.linalg.norm(out[3] - out[2])
+@pytest.mark.parametrize("case", ["pair", "triangle"])
+def test_truncation_convergence(case):
+    """Two and three active spheres in the trap at centre distances 2.05a, 2.5a, 3a, 4a:
+    the change of (V, Omega) from one truncation to the next, l <= 2, 3, 4, 5, 6, decreases
+    monotonically, and the paper's minimal truncation (every mode of rank <= 4, 47
+    components per sphere, Sec. III) is closer to l <= 6 than l <= 3 is."""
+    prm = dict(a=A, eta=ETA, k=0.01, vs=0.1, s0=0.05, d0=0.02)
+    for r in (2.05, 2.5, 3.0, 4.0):
+        if case == "pair":
+            R = np.array([[0.0, 0.0, 0.0], [r, 0.0, 0.0]]) * A
+            p = np.array([[0.0, 0.6, 0.8], [1.0, 0.0, 0.0]])
+        else:
+            R = np.array([[0.0, 0.0, 0.0], [r, 0.0, 0.0], [r / 2, r * math.sqrt(3) / 2, 0.0]]) * A
+            p = np.array([[0.0, 0.6, 0.8], [1.0, 0.0, 0.0], [0.0, 0.0, 1.0]])
+        out = {tr: np.concatenate(dynamics.velocities(R, p, prm, tr, False), axis=1).ravel()
+               for tr in (2, 3, 4, 5, 6, tensors.MINIMAL)}
+        steps = [np.linalg.norm(out[b] - out[a]) for a, b in ((2, 3), (3, 4), (4, 5), (5, 6))]
+        assert all(y < x for x, y in zip(steps, steps[1:])), (r, steps)
+        assert np.linalg.norm(out[tensors.MINIMAL] - out[6]) < np.linalg.norm(out[3] - out[6])
+    assert tensors.ModeBasis(tensors.MINIMAL).d == 47
 
 
 def test_superposition_is_dilute_limit():
