@@ -223,7 +223,7 @@ MODES = [("1s", 1, 0), ("2a", 2, 1),
          ("6a", 6, 1), ("6s", 6, 0), ("7t", 7, 2)]
 # truncation l<=L keeps MODES[2 : 2 + N_HMODES[L]] as higher modes: the nested sets
 # {1s, 2a} + {ks, ka, (k+1)t : 2 <= k <= L}.  MINIMAL (code 40) is the paper's minimal
-# truncation of Sec. III: every mode of rank <= 4 (Y^(0..3)), 47 components per sphere
+# truncation of Sec. IV: every mode of rank <= 4 (Y^(0..3)), 47 components per sphere
 # (l <= 4 without 5t).
 MINIMAL = 40
 N_HMODES = {2: 2, 3: 5, 4: 8, 5: 11, 6: 14, MINIMAL: 7}

@@ -157,7 +157,7 @@ def solid_harmonic(k, mu):
 MODES = [("1s", 1, 0), ("2a", 2, 1), ("2s", 2, 0), ("3t", 3, 2), ("3a", 3, 1), ("3s", 3, 0),
          ("4t", 4, 2), ("4a", 4, 1), ("4s", 4, 0), ("5t", 5, 2), ("5a", 5, 1), ("5s", 5, 0), ("6t", 6, 2)]
 # truncation l <= L keeps the first NMODES[L] modes; code 40 is the paper's minimal
-# truncation of Sec. III (every mode of rank <= 4, 47 components: l <= 4 without 5t)
+# truncation of Sec. IV (every mode of rank <= 4, 47 components: l <= 4 without 5t)
 MINIMAL = 40
 NMODES = {2: 4, 3: 7, 4: 10, 5: 13, MINIMAL: 9}
 TRUNCS = (2, 3, 4, 5, MINIMAL)

@@ -368,7 +368,7 @@ def test_truncation_convergence(case):
     """Two and three active spheres in the trap at centre distances 2.05a, 2.5a, 3a, 4a:
     the change of (V, Omega) from one truncation to the next, l <= 2, 3, 4, 5, 6, decreases
     monotonically, and the paper's minimal truncation (every mode of rank <= 4, 47
-    components per sphere, Sec. III) is closer to l <= 6 than l <= 3 is."""
+    components per sphere, Sec. IV) is closer to l <= 6 than l <= 3 is."""
     prm = dict(a=A, eta=ETA, k=0.01, vs=0.1, s0=0.05, d0=0.02)
     for r in (2.05, 2.5, 3.0, 4.0):
         if case == "pair":
