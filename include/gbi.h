@@ -175,6 +175,13 @@ gbi_status gbi_superpose(gbi_ctx* ctx, const gbi_params* params, int N,
                          const double* R, const double* Va, const double* Oa, const double* VH,
                          const double* Fe, const double* Te, double* V, double* Omega);
 
+/* One-body flow coefficients of the higher modes, the Q^H of the superposition
+ * approximation (Sec. IV): QH = -8 pi eta a VH / g per component (g the self scalars
+ * of the truncation, gbi_self_scalars, for a unit sphere).  VH, QH are [N][h] device
+ * arrays (QH may not alias VH).  Used as a warm start of gbi_solve, alone or with the
+ * learned correction (gbi_mlp_correct_qh).  Asynchronous. */
+gbi_status gbi_qh_onebody(gbi_ctx* ctx, const gbi_params* params, int N, const double* VH, double* QH);
+
 /* Superposition approximation of gbi_superpose for a batch of independent
  * suspensions laid out as in gbi_batch_solve (system s = spheres [offsets_host[s],
  * offsets_host[s+1])); pairs are summed within each system only.  Every truncation
@@ -321,7 +328,22 @@ gbi_status gbi_solve_static(void* stream, const gbi_params* params, int N,
  * gbi_mlp_train: epochs passes over the systems in order, minibatches of batch_systems
  * consecutive systems (loss normalised per minibatch), learning rate geometric from
  * lr0 to lr1 over all steps; loss_hist (host, may be NULL) receives each epoch's mean
- * minibatch loss.  Synchronous. */
+ * minibatch loss.  Synchronous.
+ *
+ * Second head (gbi_mlp_set_head, per context; 0 = the velocity head above, the default):
+ * head 1 predicts the correction of the strain-mode flow coefficient Q^(2s) of sphere n
+ * (the first five packed components of Q^H, Sec. III Eq. generalized_Qlsigma) beyond its
+ * one-body value (gbi_qh_onebody).  Outputs o_0..4 are the packed symmetric traceless
+ * tensor S' in the pair frame, taken to the lab as sum_kl S'_kl e_k e_l and packed
+ * again (the same orthonormal packing as V^H); o_5 is trained toward zero and unused.
+ * Forward, loss, gradient and training take the head of the context.  The guess it
+ * gives, Q^H = one-body + (s0/sigma) sum_m rotated o, is a warm start of gbi_solve:
+ * the solve, not the network, decides the result.
+ * gbi_mlp_correct_qh: builds the 4a pairs of R and ADDS the head-1 correction to
+ * QH[n][0..4] (rows of h >= 5 doubles, device).  gbi_mlp_correct needs head 0 and
+ * gbi_mlp_correct_qh head 1 (GBI_ERR_ARG otherwise).
+ * gbi_mlp_labels_qh: labels [N][6] = sigma/s0 (QHx - QH1)[n][0..4], 0, from the solve's
+ * (x) and the one-body (1) Q^H (rows of h); sigma as for gbi_mlp_labels. */
 #define GBI_MLP_NPARAM 35078
 gbi_status gbi_pairs(gbi_ctx* ctx, int N, const double* R, double a, double rcut, int nsys, const int* offsets_host,
                      int* npairs);
@@ -349,6 +371,11 @@ gbi_status gbi_mlp_adam(gbi_ctx* ctx, const float* grad, double lr);
 gbi_status gbi_mlp_train(gbi_ctx* ctx, int N, const double* R, const double* p, double a, int nsys,
                          const int* offsets_host, const double* labels, int epochs, int batch_systems, double lr0,
                          double lr1, double* loss_hist);
+gbi_status gbi_mlp_set_head(gbi_ctx* ctx, int head);
+gbi_status gbi_mlp_correct_qh(gbi_ctx* ctx, int N, const double* R, const double* p, double a, double s0, int nsys,
+                              const int* offsets_host, int h, double* QH, int* npairs);
+gbi_status gbi_mlp_labels_qh(gbi_ctx* ctx, int N, int h, double s0, const double* QHx, const double* QH1,
+                             double* sigma, double* labels);
 
 /* Tuning of the pair kernel (engineering; the paper has no counterpart).  The FP32
  * and double-float pair passes run in one of two forms.  Streaming: one block per

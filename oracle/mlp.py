@@ -27,6 +27,14 @@ s0 the strain amplitude of the workload and sigma the label scale of the model.
 Flat parameter layout (shared with the C ABI): W1[128][9], b1[128], W2[128][128],
 b2[128], W3[128][128], b3[128], W4[6][128], b4[6]  (35 078 numbers).
 
+Second head (head = 1): the six outputs of a pair are instead o_0..4 = the packed
+coordinates of a symmetric traceless tensor S' in the pair frame (the orthonormal STF
+packing of tensors.pack_stf) and o_5, trained toward zero and unused.  Its lab-frame
+contribution is pack(sum_kl S'_kl e_k e_l), and the per-sphere sum predicts the
+correction of the strain-mode flow coefficient Q^(2s) (the first five packed components
+of Q^H, Sec. III Eq. generalized_Qlsigma) beyond its one-body value
+(galerkin.one_body_QH):  labels_n = sigma/s0 (Q^(2s)_solve - Q^(2s)_one-body, 0).
+
 Loss over a set of spheres with labels L_n (6 numbers, already scaled by sigma/s0):
     loss = sum_n |P_n - L_n|^2 / (6 Ns),   P_n = sum over n's pairs of the rotated o.
 Adam: Kingma & Ba (2015), bias-corrected first and second moments.
@@ -144,23 +152,46 @@ def forward(theta, F, bf16=False):
     return o, (x0, h1, h2, h3)
 
 
-def rotate_out(o, FR):
-    """Lab-frame (dV, dOmega) [P, 6] from pair-frame outputs: sum_c o_c e_c."""
-    v = np.einsum("pc,pci->pi", o[:, :3], FR)
-    w = np.einsum("pc,pci->pi", o[:, 3:], FR)
-    return np.concatenate([v, w], axis=1)
+def rotate_out(o, FR, head=0):
+    """Lab-frame contributions [P, 6] from pair-frame outputs: head 0, (dV, dOmega) =
+    sum_c o_c e_c for each triple; head 1, pack(sum_kl S'_kl e_k e_l) with
+    S' = unpack(o_0..4), and o_5 unchanged."""
+    o = np.asarray(o, float)
+    if head == 0:
+        v = np.einsum("pc,pci->pi", o[:, :3], FR)
+        w = np.einsum("pc,pci->pi", o[:, 3:], FR)
+        return np.concatenate([v, w], axis=1)
+    from .tensors import pack_stf, unpack_stf
+    out = np.zeros_like(o)
+    for k in range(len(o)):
+        S = unpack_stf(o[k, :5], 2)                  # pair-frame coordinates
+        out[k, :5] = pack_stf(FR[k].T @ S @ FR[k])   # sum_kl S_kl e_k e_l (rows e_k of FR)
+        out[k, 5] = o[k, 5]
+    return out
 
 
-def predict(theta, F, FR, tg, Ns, bf16=False):
+def head_matrices(FR, head=0):
+    """The linear map of rotate_out for every pair, [P, 6, 6] (lab = M o), built by
+    applying rotate_out to the unit outputs."""
+    P = len(FR)
+    M = np.zeros((P, NOUT, NOUT))
+    for c in range(NOUT):
+        e = np.zeros((P, NOUT))
+        e[:, c] = 1.0
+        M[:, :, c] = rotate_out(e, FR, head)
+    return M
+
+
+def predict(theta, F, FR, tg, Ns, bf16=False, head=0):
     """Per-sphere sums P_n [Ns, 6] (label units)."""
     o, _ = forward(theta, F, bf16)
-    lab = rotate_out(o, FR)
+    lab = rotate_out(o, FR, head)
     out = np.zeros((Ns, NOUT))
     np.add.at(out, tg, lab)
     return out
 
 
-def loss_and_grad(theta, F, FR, tg, labels, bf16=False):
+def loss_and_grad(theta, F, FR, tg, labels, bf16=False, head=0):
     """Loss over the spheres that carry labels (all Ns rows of `labels`) and its
     gradient with respect to the flat parameters (plain backpropagation; with bf16
     the rounded values are used in the products and the gradient flows straight
@@ -169,16 +200,16 @@ def loss_and_grad(theta, F, FR, tg, labels, bf16=False):
     P = unflatten(theta)
     rd = bf16_round if bf16 else (lambda v: v)
     o, (x0, h1, h2, h3) = forward(theta, F, bf16)
-    lab = rotate_out(o, FR)
+    M = head_matrices(FR, head)
+    lab = np.einsum("pij,pj->pi", M, o)
     pred = np.zeros((Ns, NOUT))
     np.add.at(pred, tg, lab)
     diff = pred - labels
     loss = float((diff ** 2).sum() / (6.0 * Ns))
     dpred = 2.0 * diff / (6.0 * Ns)
     dlab = dpred[tg]
-    # lab_i = sum_c o_c FR[c, i]  =>  do_c = sum_i FR[c, i] dlab_i
-    do = np.concatenate([np.einsum("pci,pi->pc", FR, dlab[:, :3]), np.einsum("pci,pi->pc", FR, dlab[:, 3:])],
-                        axis=1)
+    # lab = M o  =>  do = M^T dlab
+    do = np.einsum("pij,pi->pj", M, dlab)
     g = {}
     g["W4"] = do.T @ rd(h3)
     g["b4"] = do.sum(0)
@@ -201,3 +232,10 @@ def adam_step(theta, grad, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
     mh = m / (1.0 - beta1 ** t)
     vh = v / (1.0 - beta2 ** t)
     return theta - lr * mh / (np.sqrt(vh) + eps), m, v
+
+
+def labels_qstrain(QH_solve, QH_onebody, s0, sigma):
+    """Labels [N, 6] of the strain-mode head: sigma/s0 (Q^(2s) of the solve - one-body), 0."""
+    out = np.zeros((len(QH_solve), NOUT))
+    out[:, :5] = sigma / s0 * (np.asarray(QH_solve, float)[:, :5] - np.asarray(QH_onebody, float)[:, :5])
+    return out

@@ -94,6 +94,11 @@ _SIGS = {
     "gbi_mlp_adam": (_I, [_VP, _VP, _D]),
     "gbi_mlp_train": (_I, [_VP, _I, _VP, _VP, _D, _I, ctypes.POINTER(ctypes.c_int), _VP, _I, _I, _D, _D,
                            c_double_p]),
+    "gbi_mlp_set_head": (_I, [_VP, _I]),
+    "gbi_mlp_correct_qh": (_I, [_VP, _I, _VP, _VP, _D, _D, _I, ctypes.POINTER(ctypes.c_int), _I, _VP,
+                                ctypes.POINTER(ctypes.c_int)]),
+    "gbi_mlp_labels_qh": (_I, [_VP, _I, _I, _D, _VP, _VP, c_double_p, _VP]),
+    "gbi_qh_onebody": (_I, [_VP, ctypes.POINTER(gbi_params), _I, _VP, _VP]),
     "gbi_kernel_launches": (ctypes.c_longlong, [_VP]),
     "gbi_solve_graph_replays": (ctypes.c_longlong, [_VP]),
     "gbi_set_profiling": (_I, [_VP, _I]),
@@ -414,6 +419,33 @@ class Context:
         self._check(lib().gbi_mlp_labels(self._h, N, float(s0), _ptr(Vx), _ptr(Ox), _ptr(Vs), _ptr(Os),
                                          ctypes.byref(sig), _ptr(lab)), "gbi_mlp_labels")
         return lab, sig.value
+
+    def mlp_set_head(self, head):
+        """0: velocity-correction head, 1: strain-mode Q^(2s) head (warm start of the solve)."""
+        self._check(lib().gbi_mlp_set_head(self._h, int(head)), "gbi_mlp_set_head")
+
+    def mlp_correct_qh(self, R, p, a, s0, QH, offsets=None):
+        nsys, offs = self._offs(offsets)
+        n = ctypes.c_int()
+        self._check(lib().gbi_mlp_correct_qh(self._h, int(R.shape[0]), _ptr(R), _ptr(p), float(a), float(s0), nsys,
+                                             offs, int(QH.shape[1]), _ptr(QH), ctypes.byref(n)), "gbi_mlp_correct_qh")
+        return n.value
+
+    def mlp_labels_qh(self, s0, QHx, QH1, sigma=0.0):
+        import torch
+        N = int(QHx.shape[0])
+        lab = torch.empty((N, 6), dtype=torch.float64, device=QHx.device)
+        sig = ctypes.c_double(float(sigma))
+        self._check(lib().gbi_mlp_labels_qh(self._h, N, int(QHx.shape[1]), float(s0), _ptr(QHx), _ptr(QH1),
+                                            ctypes.byref(sig), _ptr(lab)), "gbi_mlp_labels_qh")
+        return lab, sig.value
+
+    def qh_onebody(self, prm, VH):
+        import torch
+        QH = torch.empty_like(VH)
+        self._check(lib().gbi_qh_onebody(self._h, ctypes.byref(prm), int(VH.shape[0]), _ptr(VH), _ptr(QH)),
+                    "gbi_qh_onebody")
+        return QH
 
     def mlp_loss_grad(self, R, p, a, labels, offsets=None):
         import torch

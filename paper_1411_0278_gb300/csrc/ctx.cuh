@@ -78,6 +78,7 @@ struct gbi_ctx {
   // features, outputs and training scratch
   gbi::Buf mlp_th, mlp_m, mlp_v, mlp_thq, mlp_pk, mlp_grad, mlp_pk_tc, mlp_err;
   int mlp_engine = 1;                            // inference: 0 mma.sync, 1 tcgen05
+  int mlp_head = 0;                              // what the outputs are (mlpk::HEAD_*)
   double mlp_sigma = 0.0;
   int mlp_step = 0;
   bool mlp_ready = false;

@@ -46,6 +46,16 @@ __global__ void k_trap_inputs(int N, double k_trap, double vs, double s0, double
     for (int i = 0; i < 5; ++i) vh[20 + i] = q0 * q[i];
 }
 
+// One-body flow coefficients of the higher modes (Sec. IV: an isolated sphere's traction
+// from its own active velocity, the self elements alone): Q^H = -8 pi eta a V^H / g, g the
+// self scalars of a unit sphere.  [N][h] in and out.
+__global__ void k_qh_onebody(int N, int h, const double* __restrict__ VH, Scales ginv, double mult,
+                             double* __restrict__ QH) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (size_t)N * h) return;
+  QH[i] = mult * VH[i] * ginv.v[i % h];
+}
+
 // Modes of a squirmer with the Lighthill-Blake slip of Sec. V, B1 and B2: from the slip's
 // tensorial-harmonic coefficients, V^a = 2 B1 p / 3, V^(2s) = -3/5 B2 (pp - I/3),
 // V^(3t) = 10/3 B1 p and V^(4t) = 7 B2 (pp - I/3) (the trap parameters vs, s0, d0, q0).
@@ -386,6 +396,21 @@ gbi_status gbi_batch_superpose(gbi_ctx* ctx, const gbi_params* prm, int nsys, co
   GBI_CHECK(run_pairs(ctx, s.trunc, SET_L, SET_ALL, prm->precision == 3 ? 1 : prm->precision, p));
   k_finalize_lower<<<grid1(N), 256, 0, ctx->stream>>>(N, s.a, s.scale.v[3], P<double>(ctx->xVL), Va, Oa, V,
                                                       Omega, nullptr);
+  ++ctx->launches;
+  GBI_CHECK(cudaGetLastError());
+  return GBI_OK;
+}
+
+gbi_status gbi_qh_onebody(gbi_ctx* ctx, const gbi_params* prm, int N, const double* VH, double* QH) {
+  if (!ctx || !valid_params(prm) || N < 0) return GBI_ERR_ARG;
+  if (N == 0) return GBI_OK;
+  if (!VH || !QH) return GBI_ERR_ARG;
+  cudaSetDevice(ctx->device);
+  const int h = gbi_h(prm->trunc);
+  const double* sg = self_tab(prm->trunc);
+  Scales ginv;   // 1 / g of every higher component (self scalars of a unit sphere)
+  for (int i = 0; i < kMaxD; ++i) ginv.v[i] = i < h ? 1.0 / sg[6 + i] : 0.0;
+  k_qh_onebody<<<grid1((size_t)N * h), 256, 0, ctx->stream>>>(N, h, VH, ginv, -8.0 * kPi * prm->eta * prm->a, QH);
   ++ctx->launches;
   GBI_CHECK(cudaGetLastError());
   return GBI_OK;

@@ -166,6 +166,82 @@ __device__ __forceinline__ float tanh_act(float x) {
 #endif
 constexpr int NIN = 9, NH = 128, NOUT = 6;
 constexpr int NPARAM = NH * NIN + NH + 2 * (NH * NH + NH) + NOUT * NH + NOUT;   // 35078
+// What the six outputs of a pair are (gbi_mlp_set_head): 0 = the velocity and angular
+// velocity corrections of the target (two vectors in the pair frame); 1 = the correction
+// of its strain-mode flow coefficient Q^(2s) (outputs 0..4: the packed symmetric
+// traceless tensor in the pair frame; output 5 is trained toward zero and not used).
+constexpr int HEAD_VELOCITY = 0, HEAD_QSTRAIN = 1;
+#ifdef __CUDACC__
+// Packed coordinates of a symmetric traceless 3x3 tensor in the orthonormal basis of the
+// mode layout (components sqrt2 xy, sqrt2 yz, (2zz - xx - yy)/sqrt6, sqrt2 xz, (xx - yy)/sqrt2).
+__device__ __forceinline__ void stf2_unpack(const float* q, float S[3][3]) {
+  const float r2 = 0.70710678118654752f, r6 = 0.40824829046386302f;
+  S[0][0] = -r6 * q[2] + r2 * q[4];
+  S[1][1] = -r6 * q[2] - r2 * q[4];
+  S[2][2] = 2.0f * r6 * q[2];
+  S[0][1] = S[1][0] = r2 * q[0];
+  S[1][2] = S[2][1] = r2 * q[1];
+  S[0][2] = S[2][0] = r2 * q[3];
+}
+__device__ __forceinline__ void stf2_pack(const float T[3][3], float* q) {
+  const float s2 = 1.41421356237309505f, r2 = 0.70710678118654752f, r6 = 0.40824829046386302f;
+  q[0] = s2 * T[0][1];
+  q[1] = s2 * T[1][2];
+  q[2] = r6 * (2.0f * T[2][2] - T[0][0] - T[1][1]);
+  q[3] = s2 * T[0][2];
+  q[4] = r2 * (T[0][0] - T[1][1]);
+}
+// The rank-2 tensor with pair-frame coordinates q, in lab coordinates (to_lab: sum_kl
+// S_kl e_k e_l), or the lab tensor q in pair-frame coordinates (e_k . S . e_l).  fr holds
+// the rows e_x, e_y, e_z.
+__device__ __forceinline__ void stf2_rotate(const float* fr, const float* q, float* out, bool to_lab) {
+  float S[3][3], T[3][3];
+  stf2_unpack(q, S);
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      float acc = 0.f;
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int l = 0; l < 3; ++l) {
+          const float a = to_lab ? fr[3 * k + i] : fr[3 * i + k];
+          const float b = to_lab ? fr[3 * l + j] : fr[3 * j + l];
+          acc = fmaf(a * b, S[k][l], acc);
+        }
+      T[i][j] = acc;
+    }
+  stf2_pack(T, out);
+}
+// Lab-frame per-pair contribution dst[6] from the pair-frame outputs y[6].
+__device__ __forceinline__ void pair_out_to_lab(int head, const float* fr, const float* y, float* dst) {
+  if (head == HEAD_QSTRAIN) {
+    stf2_rotate(fr, y, dst, true);
+    dst[5] = y[5];
+    return;
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    dst[i] = y[0] * fr[i] + y[1] * fr[3 + i] + y[2] * fr[6 + i];
+    dst[3 + i] = y[3] * fr[i] + y[4] * fr[3 + i] + y[5] * fr[6 + i];
+  }
+}
+// Gradient with respect to the pair-frame outputs from the gradient dp[6] with respect to
+// the lab-frame contribution (the transpose of pair_out_to_lab, itself orthogonal).
+__device__ __forceinline__ void lab_grad_to_pair(int head, const float* fr, const float* dp, float* g) {
+  if (head == HEAD_QSTRAIN) {
+    stf2_rotate(fr, dp, g, false);
+    g[5] = dp[5];
+    return;
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    g[c] = fr[3 * c] * dp[0] + fr[3 * c + 1] * dp[1] + fr[3 * c + 2] * dp[2];
+    g[3 + c] = fr[3 * c] * dp[3] + fr[3 * c + 1] * dp[4] + fr[3 * c + 2] * dp[5];
+  }
+}
+#endif
 size_t scan_scratch_ints(int n);
 cudaError_t exclusive_scan(const int* in, int* out, int n, int* scratch, cudaStream_t st);
 cudaError_t bbox(int N, const double* R, double* part_dev, double* out_host, cudaStream_t st);
@@ -182,14 +258,17 @@ cudaError_t features(int P, const double* R, const double* p, const int* tg, con
                      float* FR, cudaStream_t st);
 size_t packed_bytes();
 cudaError_t pack_weights(const float* theta, float* thq, void* packed, cudaStream_t st);
-cudaError_t infer(int P, const float* F, const float* FR, const void* packed, float* out, int num_sms,
+cudaError_t infer(int P, const float* F, const float* FR, const void* packed, float* out, int num_sms, int head,
                   cudaStream_t st);
 cudaError_t sphere_sums(int N, const int* start, const float* lab, double scale, double* V, double* Om,
                         cudaStream_t st);
+// QH[n][0..4] (rows of h) += scale * the sums of n's pairs' first five outputs
+cudaError_t sphere_sums_q(int N, const int* start, const float* lab, double scale, double* QH, int h,
+                          cudaStream_t st);
 size_t train_part_floats(int max_pairs);
 cudaError_t train_batch(const float* thq, const float* F, const float* FR, const int* start, const double* labels,
                         int p_begin, int p_end, int n_begin, int n_end, int ns_total, float* lab, float* dO,
-                        float* part, double* loss_part, float* grad, cudaStream_t st);
+                        float* part, double* loss_part, float* grad, int head, cudaStream_t st);
 cudaError_t adam(float* th, float* m, float* v, const float* g, int t, double lr, float* thq, void* packed,
                  void* packed_tc, cudaStream_t st);
 cudaError_t sum_into(const double* parts, int n, double* dst, cudaStream_t st);
@@ -197,9 +276,12 @@ cudaError_t sum_into(const double* parts, int n, double* dst, cudaStream_t st);
 size_t packed_tc_bytes();
 cudaError_t pack_weights_tc(const float* theta, void* packed, cudaStream_t st);
 cudaError_t infer_tc(int P, const float* F, const float* FR, const void* packed, float* out, int* err, int num_sms,
-                     cudaStream_t st);
+                     int head, cudaStream_t st);
 cudaError_t labels(int N, double s0, double sigma, const double* Vx, const double* Ox, const double* Vs,
                    const double* Os, double* out, double* sq_part, cudaStream_t st);
+// labels[n] = sigma / s0 * (QHx - QH1)[n][0..4], 0 (rows of h); block partial sums of squares
+cudaError_t labels_q(int N, int h, double s0, double sigma, const double* QHx, const double* QH1, double* out,
+                     double* sq_part, cudaStream_t st);
 }  // namespace mlpk
 
 // Flop counts per ordered pair used for the roofline accounting.

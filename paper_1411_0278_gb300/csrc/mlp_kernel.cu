@@ -430,7 +430,8 @@ __device__ __forceinline__ void hidden_layer(const __nv_bfloat16* in, const __nv
 }
 
 __global__ void __launch_bounds__(128) k_infer(int P, const float* __restrict__ F, const float* __restrict__ FR,
-                                                const __nv_bfloat16* __restrict__ pk, float* __restrict__ out) {
+                                                const __nv_bfloat16* __restrict__ pk, float* __restrict__ out,
+                                                int head) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __nv_bfloat16* sW = reinterpret_cast<__nv_bfloat16*>(smem_raw);                 // PK_END
   float* sB = reinterpret_cast<float*>(sW + PK_END);                                // biases
@@ -488,12 +489,7 @@ __global__ void __launch_bounds__(128) k_infer(int P, const float* __restrict__ 
         const float* o = ow + lane * 8;
         float* dst = out + (size_t)pp * NOUT;
         if (FR != nullptr) {
-          const float* fr = FR + (size_t)pp * 9;   // rows e_x, e_y, e_z
-#pragma unroll
-          for (int i = 0; i < 3; ++i) {
-            dst[i] = o[0] * fr[i] + o[1] * fr[3 + i] + o[2] * fr[6 + i];
-            dst[3 + i] = o[3] * fr[i] + o[4] * fr[3 + i] + o[5] * fr[6 + i];
-          }
+          pair_out_to_lab(head, FR + (size_t)pp * 9, o, dst);   // frame rows e_x, e_y, e_z
         } else {
 #pragma unroll
           for (int c = 0; c < NOUT; ++c) dst[c] = o[c];
@@ -509,7 +505,7 @@ size_t infer_smem_bytes() {
          sizeof(__nv_bfloat16) * TILE_P * (LDF + LDA) + sizeof(float) * TILE_P * 8;
 }
 
-cudaError_t infer(int P, const float* F, const float* FR, const void* packed, float* out, int num_sms,
+cudaError_t infer(int P, const float* F, const float* FR, const void* packed, float* out, int num_sms, int head,
                   cudaStream_t st) {
   if (P <= 0) return cudaSuccess;
   const size_t smem = infer_smem_bytes();
@@ -517,7 +513,7 @@ cudaError_t infer(int P, const float* F, const float* FR, const void* packed, fl
   if (e != cudaSuccess) return e;
   const int ntiles = (P + TILE_P - 1) / TILE_P;
   const int grid = ntiles < 2 * num_sms ? ntiles : 2 * num_sms;
-  k_infer<<<grid, 128, smem, st>>>(P, F, FR, static_cast<const __nv_bfloat16*>(packed), out);
+  k_infer<<<grid, 128, smem, st>>>(P, F, FR, static_cast<const __nv_bfloat16*>(packed), out, head);
   return cudaGetLastError();
 }
 
@@ -539,6 +535,24 @@ cudaError_t sphere_sums(int N, const int* start, const float* lab, double scale,
                         cudaStream_t st) {
   if (N <= 0) return cudaSuccess;
   k_sphere_sums<<<(N + 127) / 128, 128, 0, st>>>(N, start, lab, scale, V, Om);
+  return cudaGetLastError();
+}
+
+// the same for the strain-mode head: the first five outputs into the 2s block of Q^H
+__global__ void k_sphere_sums_q(int N, const int* __restrict__ start, const float* __restrict__ lab, double scale,
+                                double* __restrict__ QH, int h) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  double s[5] = {0, 0, 0, 0, 0};
+  for (int k = start[n]; k < start[n + 1]; ++k)
+    for (int c = 0; c < 5; ++c) s[c] += double(lab[(size_t)k * 6 + c]);
+  for (int c = 0; c < 5; ++c) QH[(size_t)h * n + c] += scale * s[c];
+}
+
+cudaError_t sphere_sums_q(int N, const int* start, const float* lab, double scale, double* QH, int h,
+                          cudaStream_t st) {
+  if (N <= 0) return cudaSuccess;
+  k_sphere_sums_q<<<(N + 127) / 128, 128, 0, st>>>(N, start, lab, scale, QH, h);
   return cudaGetLastError();
 }
 
@@ -609,26 +623,21 @@ __device__ void train_forward_tile(const float* __restrict__ thq, const float* _
 // lab [P][6] = rotated outputs of the pairs [p_begin, p_end)
 __global__ void __launch_bounds__(NH) k_train_forward(const float* __restrict__ thq, const float* __restrict__ F,
                                                       const float* __restrict__ FR, int p_begin, int p_end,
-                                                      float* __restrict__ lab) {
+                                                      float* __restrict__ lab, int head) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   TrainSmem& s = *reinterpret_cast<TrainSmem*>(smem_raw);
   const int p0 = p_begin + blockIdx.x * TP;
   const int np = min(TP, p_end - p0);
   train_forward_tile(thq, F, p0, np, s);
-  for (int i = threadIdx.x; i < np * 3; i += blockDim.x) {
-    const int r = i / 3, d = i % 3;
-    const float* fr = FR + (size_t)(p0 + r) * 9;
-    float* dst = lab + (size_t)(p0 + r) * 6;
-    dst[d] = s.o[r][0] * fr[d] + s.o[r][1] * fr[3 + d] + s.o[r][2] * fr[6 + d];
-    dst[3 + d] = s.o[r][3] * fr[d] + s.o[r][4] * fr[3 + d] + s.o[r][5] * fr[6 + d];
-  }
+  for (int r = threadIdx.x; r < np; r += blockDim.x)
+    pair_out_to_lab(head, FR + (size_t)(p0 + r) * 9, s.o[r], lab + (size_t)(p0 + r) * 6);
 }
 
 // per sphere n of [n_begin, n_end): P_n = sum of its pairs' rotated outputs; loss term
 // |P_n - L_n|^2 / (6 Ns); dO of each of its pairs = FR * dP_n.  Block partial losses.
 __global__ void k_train_loss(int n_begin, int n_end, const int* __restrict__ start, const float* __restrict__ lab,
                              const float* __restrict__ FR, const double* __restrict__ labels, double inv6ns,
-                             float* __restrict__ dO, double* __restrict__ loss_part) {
+                             float* __restrict__ dO, double* __restrict__ loss_part, int head) {
   __shared__ double s[128];
   const int n = n_begin + blockIdx.x * blockDim.x + threadIdx.x;
   double l = 0.0;
@@ -642,14 +651,7 @@ __global__ void k_train_loss(int n_begin, int n_end, const int* __restrict__ sta
       l += d * d;
       dp[c] = float(2.0 * d * inv6ns);
     }
-    for (int k = start[n]; k < start[n + 1]; ++k) {
-      const float* fr = FR + (size_t)k * 9;
-      float* g = dO + (size_t)k * 6;
-      for (int c = 0; c < 3; ++c) {
-        g[c] = fr[3 * c] * dp[0] + fr[3 * c + 1] * dp[1] + fr[3 * c + 2] * dp[2];
-        g[3 + c] = fr[3 * c] * dp[3] + fr[3 * c + 1] * dp[4] + fr[3 * c + 2] * dp[5];
-      }
-    }
+    for (int k = start[n]; k < start[n + 1]; ++k) lab_grad_to_pair(head, FR + (size_t)k * 9, dp, dO + (size_t)k * 6);
   }
   s[threadIdx.x] = l * inv6ns;
   __syncthreads();
@@ -761,7 +763,7 @@ __global__ void k_grad_reduce(int ntiles, const float* __restrict__ part, float*
 
 cudaError_t train_batch(const float* thq, const float* F, const float* FR, const int* start, const double* labels,
                         int p_begin, int p_end, int n_begin, int n_end, int ns_total, float* lab, float* dO,
-                        float* part, double* loss_part, float* grad, cudaStream_t st) {
+                        float* part, double* loss_part, float* grad, int head, cudaStream_t st) {
   const int np = p_end - p_begin;
   const int ntiles = (np + TP - 1) / TP;
   const size_t smem_f = sizeof(TrainSmem), smem_b = train_smem_bytes();
@@ -769,11 +771,11 @@ cudaError_t train_batch(const float* thq, const float* F, const float* FR, const
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_train_backward, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_b));
   if (e != cudaSuccess) return e;
-  if (ntiles > 0) k_train_forward<<<ntiles, NH, smem_f, st>>>(thq, F, FR, p_begin, p_end, lab);
+  if (ntiles > 0) k_train_forward<<<ntiles, NH, smem_f, st>>>(thq, F, FR, p_begin, p_end, lab, head);
   const int nb = (n_end - n_begin + 127) / 128;
   if (nb > 0)
     k_train_loss<<<nb, 128, 0, st>>>(n_begin, n_end, start, lab, FR, labels, 1.0 / (6.0 * ns_total), dO,
-                                     loss_part);
+                                     loss_part, head);
   if (ntiles > 0) {
     k_train_backward<<<ntiles, NH, smem_b, st>>>(thq, F, dO, p_begin, p_end, part);
     k_grad_reduce<<<(NPARAM + 255) / 256, 256, 0, st>>>(ntiles, part, grad);
@@ -944,6 +946,35 @@ __global__ void k_labels(int N, double s0, double sigma, const double* __restric
 cudaError_t labels(int N, double s0, double sigma, const double* Vx, const double* Ox, const double* Vs,
                    const double* Os, double* out, double* sq_part, cudaStream_t st) {
   k_labels<<<(N + 255) / 256, 256, 0, st>>>(N, s0, sigma, Vx, Ox, Vs, Os, out, sq_part);
+  return cudaGetLastError();
+}
+
+// strain-mode head: labels[n] = sigma / s0 (Q^(2s) of the solve - the one-body Q^(2s)), 0
+__global__ void k_labels_q(int N, int h, double s0, double sigma, const double* __restrict__ QHx,
+                           const double* __restrict__ QH1, double* __restrict__ labels, double* __restrict__ sq_part) {
+  __shared__ double s[256];
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  double q = 0.0;
+  if (n < N) {
+    for (int c = 0; c < 5; ++c) {
+      const double d = (QHx[(size_t)h * n + c] - QH1[(size_t)h * n + c]) / s0;
+      q += d * d;
+      if (labels != nullptr) labels[(size_t)n * 6 + c] = sigma * d;
+    }
+    if (labels != nullptr) labels[(size_t)n * 6 + 5] = 0.0;
+  }
+  s[threadIdx.x] = q;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && sq_part != nullptr) sq_part[blockIdx.x] = s[0];
+}
+
+cudaError_t labels_q(int N, int h, double s0, double sigma, const double* QHx, const double* QH1, double* out,
+                     double* sq_part, cudaStream_t st) {
+  k_labels_q<<<(N + 255) / 256, 256, 0, st>>>(N, h, s0, sigma, QHx, QH1, out, sq_part);
   return cudaGetLastError();
 }
 

@@ -149,7 +149,7 @@ constexpr int kTcThreads = 256;   // eight warps: two per tensor-memory lane qua
 
 __global__ void __launch_bounds__(kTcThreads) k_infer_tc(int P, const float* __restrict__ F, const float* __restrict__ FR,
                                                    const __nv_bfloat16* __restrict__ pk, float* __restrict__ out,
-                                                   int* __restrict__ err) {
+                                                   int* __restrict__ err, int head) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   TcSmem& s = *reinterpret_cast<TcSmem*>(smem_raw);
   const int tid = threadIdx.x, warp = tid >> 5;
@@ -259,12 +259,7 @@ __global__ void __launch_bounds__(kTcThreads) k_infer_tc(int P, const float* __r
       for (int c = 0; c < NOUT; ++c) y[c] = o[c] + b4[c];
       float* dst = out + (size_t)p * NOUT;
       if (FR != nullptr) {
-        const float* fr = FR + (size_t)p * 9;
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-          dst[i] = y[0] * fr[i] + y[1] * fr[3 + i] + y[2] * fr[6 + i];
-          dst[3 + i] = y[3] * fr[i] + y[4] * fr[3 + i] + y[5] * fr[6 + i];
-        }
+        pair_out_to_lab(head, FR + (size_t)p * 9, y, dst);
       } else {
 #pragma unroll
         for (int c = 0; c < NOUT; ++c) dst[c] = y[c];
@@ -294,14 +289,14 @@ cudaError_t pack_weights_tc(const float* theta, void* packed, cudaStream_t st) {
 }
 
 cudaError_t infer_tc(int P, const float* F, const float* FR, const void* packed, float* out, int* err, int num_sms,
-                     cudaStream_t st) {
+                     int head, cudaStream_t st) {
   if (P <= 0) return cudaSuccess;
   const size_t smem = sizeof(TcSmem);
   cudaError_t e = cudaFuncSetAttribute(k_infer_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
   const int ntiles = (P + TM - 1) / TM;
   const int grid = ntiles < 2 * num_sms ? ntiles : 2 * num_sms;
-  k_infer_tc<<<grid, kTcThreads, smem, st>>>(P, F, FR, static_cast<const __nv_bfloat16*>(packed), out, err);
+  k_infer_tc<<<grid, kTcThreads, smem, st>>>(P, F, FR, static_cast<const __nv_bfloat16*>(packed), out, err, head);
   return cudaGetLastError();
 }
 

@@ -123,11 +123,12 @@ gbi_status mlp_prepare(gbi_ctx* ctx, int N, const double* R, const double* p, do
 // gave up through a device flag that gbi_mlp_status reads back.
 gbi_status mlp_infer(gbi_ctx* ctx, int np_, const float* F, const float* FR, float* out) {
   if (ctx->mlp_engine == 1) {
-    GBI_CHECK(mlpk::infer_tc(np_, F, FR, ctx->mlp_pk_tc.p, out, P<int>(ctx->mlp_err), sm_count(ctx), ctx->stream));
+    GBI_CHECK(mlpk::infer_tc(np_, F, FR, ctx->mlp_pk_tc.p, out, P<int>(ctx->mlp_err), sm_count(ctx), ctx->mlp_head,
+                             ctx->stream));
     ++ctx->launches;
     return GBI_OK;
   }
-  GBI_CHECK(mlpk::infer(np_, F, FR, ctx->mlp_pk.p, out, sm_count(ctx), ctx->stream));
+  GBI_CHECK(mlpk::infer(np_, F, FR, ctx->mlp_pk.p, out, sm_count(ctx), ctx->mlp_head, ctx->stream));
   ++ctx->launches;
   return GBI_OK;
 }
@@ -239,11 +240,21 @@ gbi_status gbi_mlp_set_engine(gbi_ctx* ctx, int engine) {
   return GBI_OK;
 }
 
+gbi_status gbi_mlp_set_head(gbi_ctx* ctx, int head) {
+  if (!ctx || (head != mlpk::HEAD_VELOCITY && head != mlpk::HEAD_QSTRAIN)) return GBI_ERR_ARG;
+  ctx->mlp_head = head;
+  return GBI_OK;
+}
+
 gbi_status gbi_mlp_correct(gbi_ctx* ctx, int N, const double* R, const double* p, double a, double s0, int nsys,
                            const int* offsets_host, double* V, double* Omega, int* npairs) {
   if (!ctx || N < 0 || !(a > 0) || nsys < 0 || (nsys > 1 && !offsets_host)) return GBI_ERR_ARG;
   if (nsys > 1 && (!valid_offsets(nsys, offsets_host) || offsets_host[nsys] != N)) return GBI_ERR_ARG;
   GBI_TRY(mlp_require(ctx));
+  if (ctx->mlp_head != mlpk::HEAD_VELOCITY) {
+    ctx->err = "gbi_mlp_correct needs the velocity head (gbi_mlp_set_head 0)";
+    return GBI_ERR_ARG;
+  }
   if (npairs) *npairs = 0;
   if (N == 0) return GBI_OK;
   if (!R || !p || !V || !Omega) return GBI_ERR_ARG;
@@ -252,6 +263,28 @@ gbi_status gbi_mlp_correct(gbi_ctx* ctx, int N, const double* R, const double* p
   GBI_TRY(mlp_infer(ctx, np_, P<float>(ctx->mf_F), P<float>(ctx->mf_FR), P<float>(ctx->mf_lab)));
   GBI_CHECK(mlpk::sphere_sums(N, P<int>(ctx->nb_start), P<float>(ctx->mf_lab), s0 / ctx->mlp_sigma, V, Omega,
                               ctx->stream));
+  ctx->launches += 1;
+  if (npairs) *npairs = np_;
+  return GBI_OK;
+}
+
+gbi_status gbi_mlp_correct_qh(gbi_ctx* ctx, int N, const double* R, const double* p, double a, double s0, int nsys,
+                              const int* offsets_host, int h, double* QH, int* npairs) {
+  if (!ctx || N < 0 || !(a > 0) || nsys < 0 || (nsys > 1 && !offsets_host) || h < 5) return GBI_ERR_ARG;
+  if (nsys > 1 && (!valid_offsets(nsys, offsets_host) || offsets_host[nsys] != N)) return GBI_ERR_ARG;
+  GBI_TRY(mlp_require(ctx));
+  if (ctx->mlp_head != mlpk::HEAD_QSTRAIN) {
+    ctx->err = "gbi_mlp_correct_qh needs the strain-mode head (gbi_mlp_set_head 1)";
+    return GBI_ERR_ARG;
+  }
+  if (npairs) *npairs = 0;
+  if (N == 0) return GBI_OK;
+  if (!R || !p || !QH) return GBI_ERR_ARG;
+  int np_ = 0;
+  GBI_TRY(mlp_prepare(ctx, N, R, p, a, nsys, offsets_host, np_));
+  GBI_TRY(mlp_infer(ctx, np_, P<float>(ctx->mf_F), P<float>(ctx->mf_FR), P<float>(ctx->mf_lab)));
+  GBI_CHECK(mlpk::sphere_sums_q(N, P<int>(ctx->nb_start), P<float>(ctx->mf_lab), s0 / ctx->mlp_sigma, QH, h,
+                                ctx->stream));
   ctx->launches += 1;
   if (npairs) *npairs = np_;
   return GBI_OK;
@@ -273,7 +306,7 @@ gbi_status gbi_mlp_loss_grad(gbi_ctx* ctx, int N, const double* R, const double*
   GBI_CHECK(mlpk::train_batch(P<float>(ctx->mlp_thq), P<float>(ctx->mf_F), P<float>(ctx->mf_FR),
                               P<int>(ctx->nb_start), labels, 0, np_, 0, N, N, P<float>(ctx->mf_lab),
                               P<float>(ctx->mf_dO), P<float>(ctx->mf_part), P<double>(ctx->mf_loss), grad,
-                              ctx->stream));
+                              ctx->mlp_head, ctx->stream));
   GBI_CHECK(mlpk::sum_into(P<double>(ctx->mf_loss), nlb, P<double>(ctx->mf_loss) + nlb, ctx->stream));
   ctx->launches += 5;
   GBI_CHECK(cudaMemcpyAsync(loss, P<double>(ctx->mf_loss) + nlb, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
@@ -309,6 +342,28 @@ gbi_status gbi_mlp_labels(gbi_ctx* ctx, int N, double s0, const double* Vx, cons
     *sigma = std::ldexp(1.0, (int)std::lround(-std::log2(rms)));
   }
   GBI_CHECK(mlpk::labels(N, s0, *sigma, Vx, Ox, Vs, Os, labels, nullptr, ctx->stream));
+  ++ctx->launches;
+  return GBI_OK;
+}
+
+gbi_status gbi_mlp_labels_qh(gbi_ctx* ctx, int N, int h, double s0, const double* QHx, const double* QH1,
+                             double* sigma, double* labels) {
+  if (!ctx || N <= 0 || h < 5 || !(s0 != 0) || !QHx || !QH1 || !sigma || !labels) return GBI_ERR_ARG;
+  if (!(*sigma > 0)) {
+    // sigma = the power of two nearest to 1 / rms of (exact - one-body) / s0 over 6 N numbers
+    const int nb = (N + 255) / 256;
+    GBI_TRY(ensure(ctx, ctx->mf_loss, sizeof(double) * (size_t)(nb + 1)));
+    GBI_CHECK(mlpk::labels_q(N, h, s0, 1.0, QHx, QH1, nullptr, P<double>(ctx->mf_loss), ctx->stream));
+    GBI_CHECK(mlpk::sum_into(P<double>(ctx->mf_loss), nb, P<double>(ctx->mf_loss) + nb, ctx->stream));
+    ctx->launches += 2;
+    double sq = 0.0;
+    GBI_CHECK(cudaMemcpyAsync(&sq, P<double>(ctx->mf_loss) + nb, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    GBI_CHECK(cudaStreamSynchronize(ctx->stream));
+    const double rms = std::sqrt(sq / (6.0 * N));
+    if (!(rms > 0)) return GBI_ERR_ARG;
+    *sigma = std::ldexp(1.0, (int)std::lround(-std::log2(rms)));
+  }
+  GBI_CHECK(mlpk::labels_q(N, h, s0, *sigma, QHx, QH1, labels, nullptr, ctx->stream));
   ++ctx->launches;
   return GBI_OK;
 }
@@ -352,7 +407,7 @@ gbi_status gbi_mlp_train(gbi_ctx* ctx, int N, const double* R, const double* p, 
       GBI_CHECK(mlpk::train_batch(P<float>(ctx->mlp_thq), P<float>(ctx->mf_F), P<float>(ctx->mf_FR),
                                   P<int>(ctx->nb_start), labels, hstart[n0], hstart[n1], n0, n1, n1 - n0,
                                   P<float>(ctx->mf_lab), P<float>(ctx->mf_dO), P<float>(ctx->mf_part), lpart,
-                                  P<float>(ctx->mlp_grad), ctx->stream));
+                                  P<float>(ctx->mlp_grad), ctx->mlp_head, ctx->stream));
       GBI_CHECK(mlpk::sum_into(lpart, (n1 - n0 + 127) / 128, lstep + b, ctx->stream));
       // learning rate: geometric from lr0 to lr1 over all steps
       const double frac = total_steps > 1 ? double(step) / double(total_steps - 1) : 0.0;

@@ -498,9 +498,10 @@ __global__ void bk_sub_scale(double* V, size_t n, const double* __restrict__ w, 
 // blocks, each owning a contiguous slice of the vectors, separated by three grid-wide
 // barriers.  Partial sums are combined in block order by every block (identical
 // results everywhere), so the result does not depend on timing.  The blocks must be
-// co-resident: 64 blocks of 256 threads on a 152-SM GPU that runs nothing else in the
-// stream meanwhile.  Each barrier wait is bounded; a block that gives up records an
-// error (bar[2]) and returns, and the host reports GBI_ERR_TIMEOUT.
+// co-resident: the kernel is launched cooperatively (64 blocks of 256 threads), so the
+// launch either places every block at once or fails.  Each barrier wait is bounded as
+// well; a block that gives up records an error (bar[2]) and returns, and the host
+// reports GBI_ERR_TIMEOUT.
 // ---------------------------------------------------------------------------------
 
 constexpr long long kBarrierLimit = 1ll << 22;   // polling rounds (with back-off) per barrier
@@ -1018,8 +1019,21 @@ gbi_status launch_chunk(gbi_ctx* ctx, const Setup& s, const Batch& B, int precis
     pa.pdl = pdl && c > 0;
     GBI_CHECK(run_pairs(ctx, s.trunc, SET_H, SET_H, precision, pa));
     if (fused && S == 1) {
-      // a single system launched step by step: the whole orthogonalisation in one kernel
-      bk_step_fused<<<kFusedBlocks, 256, 0, ctx->stream>>>(Vb, n, w, Ntot, h, gp, so, two);
+      // a single system launched step by step: the whole orthogonalisation in one kernel.
+      // Its grid barriers need every block resident at once: a cooperative launch
+      // guarantees that (or fails with cudaErrorCooperativeLaunchTooLarge) instead of
+      // assuming it.
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(kFusedBlocks);
+      cfg.blockDim = dim3(256);
+      cfg.dynamicSmemBytes = 0;
+      cfg.stream = ctx->stream;
+      cudaLaunchAttribute coop[1];
+      coop[0].id = cudaLaunchAttributeCooperative;
+      coop[0].val.cooperative = 1;
+      cfg.attrs = coop;
+      cfg.numAttrs = 1;
+      GBI_CHECK(cudaLaunchKernelEx(&cfg, bk_step_fused, Vb, n, w, Ntot, h, gp, so, two));
       ++ctx->launches;
       continue;
     }
@@ -1289,6 +1303,12 @@ __global__ void gk_guard(GPtr p, const unsigned int* __restrict__ minr2, const i
 }
 
 // the sweep loop runs while some system still needs a correction
+// warm start in the solve graph: the first pass of the sweep loop is the initial guess's
+// residual (sweep 0, not a refinement)
+__global__ void gk_warm_begin(DSolve* d) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) d->refinements = -1;
+}
+
 __global__ void gk_sweep_start(GPtr p, cudaGraphConditionalHandle hsw) {
   int any = 0;
   for (int s = threadIdx.x; s < p.S; s += blockDim.x) any |= p.st[s].enabled;
@@ -1563,7 +1583,11 @@ gbi_status solve_core(gbi_ctx* ctx, const gbi_params* prm, const Batch& B, const
 
   // ---- the mixed-precision solve as one graph (see GraphBuild): every device step of
   // the sequence below, the decisions taken by kernels instead of the host
-  if (prm->precision >= 1 && !warm_start && ctx->allow_graphs && ctx->stream != nullptr && !ctx->prof) {
+  // (a warm start replays the graph too, with the guess packed ahead of it; a trap step
+  // with its hooks and a warm start takes the host-driven sequence)
+  const bool warm = warm_start != 0;
+  if (prm->precision >= 1 && (!warm || hooks == nullptr) && ctx->allow_graphs && ctx->stream != nullptr &&
+      !ctx->prof) {
     auto bits = [](double v) {
       long long b;
       std::memcpy(&b, &v, sizeof(b));
@@ -1591,7 +1615,7 @@ gbi_status solve_core(gbi_ctx* ctx, const gbi_params* prm, const Batch& B, const
     std::vector<long long> key = {N, S, pairs_all, max_system(B), prm->trunc, prm->precision, restart, max_iter,
                                   max_refine,
                                   bits(rtol), bits(inner), bits(prm->min_sep), bits(prm->a), bits(prm->eta),
-                                  ctx->wpt_gen, ctx->force_wpt};
+                                  ctx->wpt_gen, ctx->force_wpt, warm ? 1 : 0};
     for (const void* q : ptrs) key.push_back((long long)(uintptr_t)q);
     if (hooks != nullptr) {
       // the caller's work and arrays go into the graph as well
@@ -1627,7 +1651,7 @@ gbi_status solve_core(gbi_ctx* ctx, const gbi_params* prm, const Batch& B, const
                 GBI_TRY(pack_inputs());
               }
               GBI_TRY(rhs_pass());
-              GBI_CHECK(cudaMemsetAsync(xQH, 0, sizeof(double) * nh, ctx->stream));
+              if (!warm) GBI_CHECK(cudaMemsetAsync(xQH, 0, sizeof(double) * nh, ctx->stream));
               {
                 NormCtl nc{};
                 nc.follow = kFollowRefine0;
@@ -1638,12 +1662,18 @@ gbi_status solve_core(gbi_ctx* ctx, const gbi_params* prm, const Batch& B, const
               gk_guard<<<1, 256, 0, ctx->stream>>>(gp, P<unsigned int>(ctx->minr2), bad_in, s.a,
                                                    pairs_all > 0 ? prm->min_sep : 0.0, d);
               ++ctx->launches;
-              // sweep 0: the residual is b
-              GBI_CHECK(cudaMemcpyAsync(r, b, sizeof(double) * nh, cudaMemcpyDeviceToDevice, ctx->stream));
-              GBI_CHECK(cudaMemsetAsync(dl, 0, sizeof(double) * nh, ctx->stream));
-              GBI_TRY(emit_gmres(gb, s, B, gp, restart, r, dl, inner, max_iter, rtol, d));
-              bk_axpy_enabled<<<g2, 256, 0, ctx->stream>>>(dl, N, B.sys, gp.st, xQH);
-              ++ctx->launches;
+              if (!warm) {
+                // sweep 0: the residual is b
+                GBI_CHECK(cudaMemcpyAsync(r, b, sizeof(double) * nh, cudaMemcpyDeviceToDevice, ctx->stream));
+                GBI_CHECK(cudaMemsetAsync(dl, 0, sizeof(double) * nh, ctx->stream));
+                GBI_TRY(emit_gmres(gb, s, B, gp, restart, r, dl, inner, max_iter, rtol, d));
+                bk_axpy_enabled<<<g2, 256, 0, ctx->stream>>>(dl, N, B.sys, gp.st, xQH);
+                ++ctx->launches;
+              } else {
+                // the guess (packed before the graph) enters the loop as sweep 0
+                gk_warm_begin<<<1, 32, 0, ctx->stream>>>(d);
+                ++ctx->launches;
+              }
               // sweeps 1, 2, ...: residual in the high precision, refinement test, inner solve
               const cudaGraphConditionalHandle hsw = gb.handle();
               gk_sweep_start<<<1, 256, 0, ctx->stream>>>(gp, hsw);
@@ -1715,6 +1745,11 @@ gbi_status solve_core(gbi_ctx* ctx, const gbi_params* prm, const Batch& B, const
       DSolve* d = P<DSolve>(ctx->dsolve);
       if (hooks == nullptr) {
         GBI_TRY(pack_inputs());
+        if (warm) {
+          k_pack_higher<<<grid1(nh), 256, 0, ctx->stream>>>(N, h, QH, hscale, 1.0, xQH, bad_in);
+          ++ctx->launches;
+          GBI_CHECK(cudaGetLastError());
+        }
       }
       GBI_CHECK(cudaGraphLaunch(ctx->solve_exec, ctx->stream));
       ++ctx->solve_replays;
@@ -1728,7 +1763,7 @@ gbi_status solve_core(gbi_ctx* ctx, const gbi_params* prm, const Batch& B, const
       }
       if (hbits[2] != 0 || hrec->bad_input) return GBI_ERR_ARG;
       const DSolve& hd = *hrec;
-      ctx->launches += ctx->solve_own[0] + (long long)hd.refinements * ctx->solve_own[1] +
+      ctx->launches += ctx->solve_own[0] + (long long)(hd.refinements + (warm ? 1 : 0)) * ctx->solve_own[1] +
                        (long long)hd.ifs * ctx->solve_own[2] + hd.cycles * ctx->solve_own[3] +
                        hd.steps * ctx->solve_own[4];
       // the right-hand-side and output passes are the two the host knows of

@@ -9,6 +9,11 @@ Every step runs in libgbi's kernels; this module only orders the C-ABI calls:
 * training: gbi_mlp_train (forward, loss, backward and Adam kernels);
 * use: superposition plus gbi_mlp_correct, compared with the plain solve.
 
+A second head (gbi_mlp_set_head 1) predicts the correction of the strain-mode flow
+coefficient Q^(2s) beyond its one-body value (gbi_qh_onebody); one-body Q^H plus that
+correction (guess_qh) is the initial guess of a warm-started gbi_solve, so the solve --
+not the network -- decides the result.
+
 The network and its training have no counterpart in the paper.
 """
 import numpy as np
@@ -61,6 +66,63 @@ def exact_and_superposition(ctx, R, p, offsets, a, eta, vs, s0, precision=2, rto
     inp = _inputs(ctx, R, p, 2, vs, s0)
     Vs, Os = ctx.batch_superpose(prm2, offsets, R, inp["Va"], inp["Oa"], inp["VH"], inp["Fe"], inp["Te"])
     return Vx, Ox, Vs, Os, info
+
+
+def exact_qh(ctx, R, p, offsets, a, eta, vs, s0, trunc=4, precision=2, rtol=1e-10, chunk=20000):
+    """Q^H of the Galerkin solve (truncation trunc) and the one-body Q^H of every system."""
+    import torch
+    N = R.shape[0]
+    h = _native.h(trunc)
+    QHx = torch.empty((N, h), dtype=torch.float64, device=R.device)
+    QH1 = torch.empty_like(QHx)
+    prm = _native.params(a=a, eta=eta, trunc=trunc, precision=precision, rtol=rtol, restart=40, max_iter=4000,
+                         inner_rtol=1e-5)
+    nsys = len(offsets) - 1
+    for c0 in range(0, nsys, chunk):
+        c1 = min(nsys, c0 + chunk)
+        lo, hi = offsets[c0], offsets[c1]
+        sub = [o - lo for o in offsets[c0:c1 + 1]]
+        Rc, pc = R[lo:hi].contiguous(), p[lo:hi].contiguous()
+        inp = _inputs(ctx, Rc, pc, trunc, vs, s0)
+        _, _, QH, _, _ = ctx.batch_solve(prm, sub, Rc, inp["Va"], inp["Oa"], inp["VH"], inp["Fe"], inp["Te"])
+        QHx[lo:hi] = QH
+        QH1[lo:hi] = ctx.qh_onebody(prm, inp["VH"])
+    return QHx, QH1
+
+
+def make_dataset_qh(ctx, R, p, offsets, a, eta, vs, s0, sigma=0.0, chunk=20000):
+    """Training data of the strain-mode head: labels sigma/s0 (Q^(2s)_solve - one-body)."""
+    QHx, QH1 = exact_qh(ctx, R, p, offsets, a, eta, vs, s0, chunk=chunk)
+    labels, sigma = ctx.mlp_labels_qh(s0, QHx, QH1, sigma)
+    return dict(R=R, p=p, offsets=list(offsets), a=a, eta=eta, vs=vs, s0=s0, QHx=QHx, QH1=QH1, labels=labels,
+                sigma=sigma)
+
+
+def train_qh(ctx, data, epochs=30, batch_systems=512, lr0=3e-3, lr1=1e-4, seed=0, theta=None):
+    """The strain-mode head: select it, initialise (or take theta), train."""
+    ctx.mlp_set_head(1)
+    return train(ctx, data, epochs, batch_systems, lr0, lr1, seed, theta)
+
+
+def guess_qh(ctx, prm, R, p, VH, s0, offsets=None, network=True):
+    """Initial guess of Q^H: one-body values, plus the strain-mode head's correction."""
+    QH = ctx.qh_onebody(prm, VH)
+    if network:
+        ctx.mlp_correct_qh(R, p, prm.a, s0, QH, offsets)
+    return QH
+
+
+def evaluate_qh(ctx, data):
+    """Relative 2-norm error of the one-body and the learned Q^(2s) against the solve's,
+    and of the whole Q^H guess."""
+    QHx, QH1 = data["QHx"], data["QH1"]
+    QHg = QH1.clone()
+    ctx.mlp_correct_qh(data["R"], data["p"], data["a"], data["s0"], QHg, data["offsets"])
+
+    def rel(a, b):
+        return float((a - b).norm() / b.norm())
+    return dict(one_body=dict(Q2s=rel(QH1[:, :5], QHx[:, :5]), QH=rel(QH1, QHx)),
+                with_network=dict(Q2s=rel(QHg[:, :5], QHx[:, :5]), QH=rel(QHg, QHx)))
 
 
 def make_dataset(ctx, R, p, offsets, a, eta, vs, s0, sigma=0.0, chunk=20000):

@@ -273,3 +273,159 @@ def test_nearfield_edge_cases(ctx, gbi):
     assert list(zip(tg.cpu().tolist(), sr.cpu().tolist())) == [(0, 1), (1, 0)]
     with pytest.raises(gbi.GbiError):
         ctx.pairs(R, 1.0, 4.0, [0, 2, 3])          # offsets must end at N
+
+
+# ------------------------------------------------------------------ strain-mode head
+
+@pytest.mark.parametrize("engine", [0, 1])
+def test_strain_head_forward_matches_oracle(ctx, gbi, engine):
+    """Head 1: the pair-frame outputs as before, the lab-frame ones as packed tensors
+    sum_kl S'_kl e_k e_l (the oracle's map, pinned against uniaxial tensors)."""
+    from paper_1411_0278_gb300 import nearfield
+    th = nearfield.init_theta(17)
+    th[omlp.NPARAM - 6:] = [0.1, -0.2, 0.3, 0.05, -0.05, 0.02]
+    ctx.mlp_set(th, 4.0)
+    ctx.mlp_set_head(1)
+    ctx.mlp_set_engine(engine)
+    R, p, tg, sr = _random_pairs(333, 40)
+    Fo, FRo = omlp.features_for_pairs(R, p, 1.0, tg, sr)
+    ref, _ = omlp.forward(th.astype(np.float64), Fo.astype(np.float32).astype(np.float64), bf16=True)
+    lab = ctx.mlp_forward(dev(Fo, torch.float32), dev(FRo.reshape(-1, 9), torch.float32)).cpu().numpy()
+    ctx.mlp_status()
+    want = omlp.rotate_out(ref, FRo, head=1)
+    assert np.abs(lab - want).max() <= 1e-2 * np.abs(want).max()
+
+
+def test_strain_head_gradient_matches_oracle(ctx, gbi):
+    from paper_1411_0278_gb300 import nearfield
+    d = workloads.nearfield_systems(30, 50, k=12)
+    th = nearfield.init_theta(19)
+    ctx.mlp_set(th, 2.0)
+    ctx.mlp_set_head(1)
+    labels = np.random.default_rng(5).normal(size=(len(d["R"]), 6))
+    loss, g = ctx.mlp_loss_grad(dev(d["R"]), dev(d["p"]), 1.0, dev(labels), d["offsets"])
+    tg, sr = omlp.pair_list(d["R"], 1.0, d["offsets"])
+    F, FR = omlp.features_for_pairs(d["R"], d["p"], 1.0, tg, sr)
+    lo, go = omlp.loss_and_grad(th.astype(np.float64), F, FR, tg, labels, bf16=True, head=1)
+    assert abs(loss - lo) <= 2e-3 * lo
+    g = g.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(g - go) <= 2e-2 * np.linalg.norm(go)
+
+
+def test_qh_onebody_matches_oracle(ctx, gbi):
+    from oracle import dynamics, galerkin
+    rng = np.random.default_rng(6)
+    for trunc in (2, 3, 4):
+        R = rng.normal(size=(9, 3)) * 5
+        p = workloads.unit_vectors(9, rng)
+        inp = dynamics.trap_inputs(R, p, dict(a=1.3, eta=0.7, k=0.0, vs=0.1, s0=0.05, d0=0.02), trunc)
+        VH = inp["VH"] + rng.normal(size=inp["VH"].shape) * 0.01
+        prm = gbi.params(a=1.3, eta=0.7, trunc=trunc, precision=0)
+        got = ctx.qh_onebody(prm, dev(VH)).cpu().numpy()
+        np.testing.assert_allclose(got, galerkin.one_body_QH(VH, 1.3, 0.7, trunc), rtol=1e-13, atol=0)
+
+
+def test_strain_labels_match_oracle(ctx, gbi):
+    """Labels of the strain head from the GPU's batched l <= 4 solve and one-body Q^H,
+    against the oracle's dense solve of the same 2- and 3-sphere systems."""
+    from oracle import dynamics, galerkin
+    from paper_1411_0278_gb300 import nearfield
+    d = workloads.nearfield_systems(3, 3, k=13)
+    data = nearfield.make_dataset_qh(ctx, dev(d["R"]), dev(d["p"]), d["offsets"], 1.0, d["eta"], d["vs"], d["s0"])
+    prm_o = dict(a=1.0, eta=d["eta"], k=0.0, vs=d["vs"], s0=d["s0"], d0=0.0)
+    for s in range(len(d["offsets"]) - 1):
+        lo, hi = d["offsets"][s], d["offsets"][s + 1]
+        R, p = d["R"][lo:hi], d["p"][lo:hi]
+        inp = dynamics.trap_inputs(R, p, prm_o, 4)
+        _, _, QH = galerkin.solve(R, inp["Va"], inp["Oa"], inp["VH"], inp["Fe"], inp["Te"], 1.0, d["eta"], 4)
+        want = omlp.labels_qstrain(QH, galerkin.one_body_QH(inp["VH"], 1.0, d["eta"], 4), d["s0"], data["sigma"])
+        got = data["labels"][lo:hi].cpu().numpy()
+        assert np.abs(got - want).max() <= 1e-7 * np.abs(want).max(), s
+
+
+def test_correct_qh_adds_scaled_sums(ctx, gbi):
+    from paper_1411_0278_gb300 import nearfield
+    s = workloads.suspension(400, 0.1, 2.05, workloads.SEED_BASE + 78)
+    th = nearfield.init_theta(6)
+    ctx.mlp_set(th, 8.0)
+    ctx.mlp_set_head(1)
+    R, p = dev(s["R"]), dev(s["p"])
+    Q0 = torch.randn(400, 48, dtype=torch.float64, device="cuda")
+    Q = Q0.clone()
+    npairs = ctx.mlp_correct_qh(R, p, 1.0, 0.05, Q)
+    tg, sr = omlp.pair_list(s["R"], 1.0)
+    assert npairs == len(tg)
+    F, FR = omlp.features_for_pairs(s["R"], s["p"], 1.0, tg, sr)
+    pred = omlp.predict(th.astype(np.float64), F, FR, tg, 400, bf16=True, head=1) * (0.05 / 8.0)
+    got = (Q - Q0).cpu().numpy()
+    assert np.abs(got[:, :5] - pred[:, :5]).max() <= 1e-2 * np.abs(pred[:, :5]).max()
+    assert np.all(got[:, 5:] == 0.0)
+    # each correction needs its own head
+    with pytest.raises(gbi.GbiError):
+        ctx.mlp_correct(R, p, 1.0, 0.05, Q0[:, :3].contiguous(), Q0[:, 3:6].contiguous())
+    ctx.mlp_set_head(0)
+    with pytest.raises(gbi.GbiError):
+        ctx.mlp_correct_qh(R, p, 1.0, 0.05, Q)
+
+
+def test_warm_started_graph_solve_matches_host_sequence(gbi):
+    """A repeated warm-started mixed solve on a user stream replays the solve graph (the
+    guess packed ahead of it); it returns the host-driven sequence's solution."""
+    from oracle import dynamics
+    c = workloads.small_cloud(80, 90, phi=0.1)
+    inp = dynamics.trap_inputs(c["R"], c["p"], dict(a=c["a"], eta=c["eta"], k=c["k"], vs=c["vs"], s0=c["s0"],
+                                                     d0=0.0), 3)
+    t = {k: dev(v) for k, v in inp.items()}
+    prm = gbi.params(a=c["a"], eta=c["eta"], trunc=3, precision=2, rtol=1e-10)
+    guess = torch.randn(80, gbi.h(3), dtype=torch.float64, device="cuda") * 1e-3
+    host = gbi.Context(0)
+    Q0 = guess.clone()
+    V0, O0, Q0, i0, _ = host.solve(prm, dev(c["R"]), t["Va"], t["Oa"], t["VH"], t["Fe"], t["Te"], QH=Q0,
+                                   warm_start=True)
+    torch.cuda.synchronize()
+    host.close()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        g = gbi.Context(0, stream=stream)
+        for _ in range(3):
+            Q1 = guess.clone()
+            V1, O1, Q1, i1, _ = g.solve(prm, dev(c["R"]), t["Va"], t["Oa"], t["VH"], t["Fe"], t["Te"], QH=Q1,
+                                        warm_start=True)
+        stream.synchronize()
+        assert g.solve_graph_replays() >= 1
+        g.close()
+    assert i1.rel_residual <= 1e-10 and i0.rel_residual <= 1e-10
+    assert i1.refinements == i0.refinements and abs(i1.iters - i0.iters) <= 2
+    assert float((V1 - V0).abs().max()) <= 1e-10 * float(V0.abs().max())
+    assert float((Q1 - Q0).abs().max()) <= 1e-9 * float(Q0.abs().max())
+
+
+def test_trained_strain_head_improves_the_warm_start(ctx, gbi):
+    """Train the strain head on 2- and 3-sphere systems; on held-out systems and a dense
+    suspension the learned Q^(2s) is closer to the solve's than the one-body value, and
+    the solve warm-started from the learned guess reaches the same solution."""
+    from paper_1411_0278_gb300 import nearfield
+    tr = workloads.nearfield_systems(2000, 2000, k=20)
+    te = workloads.nearfield_systems(300, 300, k=21)
+    a, eta, vs, s0 = 1.0, tr["eta"], tr["vs"], tr["s0"]
+    dtr = nearfield.make_dataset_qh(ctx, dev(tr["R"]), dev(tr["p"]), tr["offsets"], a, eta, vs, s0)
+    hist = nearfield.train_qh(ctx, dtr, epochs=30, batch_systems=256, lr0=3e-3, lr1=1e-4, seed=2)
+    assert hist[-1] < 0.5 * hist[0]
+    dte = nearfield.make_dataset_qh(ctx, dev(te["R"]), dev(te["p"]), te["offsets"], a, eta, vs, s0,
+                                    sigma=dtr["sigma"])
+    ev = nearfield.evaluate_qh(ctx, dte)
+    assert ev["with_network"]["Q2s"] < 0.5 * ev["one_body"]["Q2s"], ev
+    s = workloads.suspension(300, 0.1, 2.05, workloads.SEED_BASE + 5301)
+    R, p = dev(s["R"]), dev(s["p"])
+    dsus = nearfield.make_dataset_qh(ctx, R, p, [0, 300], a, eta, vs, s0, sigma=dtr["sigma"])
+    ev2 = nearfield.evaluate_qh(ctx, dsus)
+    assert ev2["with_network"]["Q2s"] < ev2["one_body"]["Q2s"], ev2
+    prm = gbi.params(a=a, eta=eta, trunc=4, precision=2, rtol=1e-10)
+    inp = ctx.trap_inputs(300, 4, 0.0, vs, s0, 0.0, R, p)
+    Vz, Oz, Qz, iz, _ = ctx.solve(prm, R, inp["Va"], inp["Oa"], inp["VH"], inp["Fe"], inp["Te"])
+    Qg = nearfield.guess_qh(ctx, prm, R, p, inp["VH"], s0)
+    Vg, Og, Qg, ig, _ = ctx.solve(prm, R, inp["Va"], inp["Oa"], inp["VH"], inp["Fe"], inp["Te"], QH=Qg,
+                                  warm_start=True)
+    torch.cuda.synchronize()
+    assert ig.rel_residual <= 1e-10
+    assert float((Vg - Vz).abs().max()) <= 1e-8 * float((Vz - inp["Va"]).abs().max())

@@ -555,3 +555,49 @@ def test_batch_workload_sampled_against_single_solves(ctx, gbi):
         torch.cuda.synchronize()
         assert float((V[sl] - Vk).abs().max() / Vk.abs().max()) < 1e-9, k
         assert float((Om[sl] - Ok).abs().max() / Ok.abs().max()) < 1e-8, k
+
+
+@pytest.mark.parametrize("precision", [2, 3])
+def test_batch_workload_oracle_rows(ctx, gbi, precision):
+    """The full 256-suspension workload (N log-uniform in [32, 4096], l <= 2) solved as one
+    batch; for four systems (the first, one in the middle, the last, the largest) sampled rows of that
+    system's equations and outputs evaluated by the oracle with the batch's Q^H.
+    Precision 2 (double-float right-hand side, residual and outputs) meets the FP64 system
+    to 1e-8 in the H rows and 1e-10 in V, Omega; precision 3 (FP32 right-hand side and
+    outputs) to the 1e-5 pair-velocity bar."""
+    c = workloads.config4()
+    systems = c["systems"]
+    offs = [0]
+    for sy in systems:
+        offs.append(offs[-1] + len(sy["R"]))
+    R = np.concatenate([sy["R"] for sy in systems])
+    p = np.concatenate([sy["p"] for sy in systems])
+    prm = gbi.params(a=1.0, eta=c["eta"], trunc=2, precision=precision, rtol=1e-10)
+    Rd, pd = dev(R), dev(p)
+    inp = ctx.trap_inputs(len(R), 2, c["k"], c["vs"], c["s0"], c["d0"], Rd, pd)
+    V, Om, QH, info, st = ctx.batch_solve(prm, offs, Rd, inp["Va"], inp["Oa"], inp["VH"], inp["Fe"], inp["Te"])
+    torch.cuda.synchronize()
+    assert st == gbi.GBI_OK and info.rel_residual <= 1e-10
+    V, Om, QH = V.cpu().numpy(), Om.cpu().numpy(), QH.cpu().numpy()
+    h_in = {k: v.cpu().numpy() for k, v in inp.items()}
+    MB = tensors.ModeBasis(2)
+    eta = c["eta"]
+    tol_h, tol_v = (1e-8, 1e-10) if precision == 2 else (1e-5, 1e-5)
+    rng = np.random.default_rng(12)
+    largest = int(np.argmax(np.diff(offs)))
+    for k in (0, 97, 255, largest):
+        sl = slice(offs[k], offs[k + 1])
+        Rk = R[sl]
+        Nk = len(Rk)
+        tgt = rng.choice(Nk, size=min(4, Nk), replace=False)
+        rows = _oracle_rows(Rk, tgt, 1.0, 2)
+        xF = galerkin.lower_trial(h_in["Fe"][sl], h_in["Te"][sl], 1.0, MB)
+        x = np.concatenate([xF, QH[sl] * MB.scale[6:]], axis=1)
+        xVH = h_in["VH"][sl] * MB.scale[6:]
+        Ax = np.einsum("kpmq,mq->kp", rows, x)
+        res = Ax[:, 6:] + 8 * np.pi * eta * xVH[tgt]
+        assert np.abs(res).max() / np.abs(8 * np.pi * eta * xVH).max() < tol_h, (k, Nk)
+        V_o, Om_o = galerkin.lower_velocity(-Ax[:, :6] / (8 * np.pi * eta), h_in["Va"][sl][tgt], h_in["Oa"][sl][tgt],
+                                            1.0, MB)
+        assert relerr(V[sl][tgt], V_o) < tol_v, (k, Nk)
+        assert relerr(Om[sl][tgt], Om_o) < tol_v, (k, Nk)

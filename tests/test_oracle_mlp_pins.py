@@ -137,3 +137,95 @@ def test_zero_network_outputs_last_bias():
     F = np.random.default_rng(4).normal(size=(5, mlp.NIN))
     o, _ = mlp.forward(theta, F)
     np.testing.assert_allclose(o, np.tile([1, 2, 3, 4, 5, 6], (5, 1)))
+
+
+# ------------------------------------------------------------------ strain-mode head
+
+def _pack_uniaxial(u):
+    from oracle import tensors
+    return tensors.pack_stf(np.outer(u, u) - np.eye(3) / 3)
+
+
+def test_strain_head_takes_frame_tensors_to_the_lab():
+    """A uniaxial tensor along a frame axis (pair-frame coordinates e_k e_k - I/3) becomes
+    e_k e_k - I/3 in the lab, for every axis of random frames; the map is orthogonal
+    on the five tensor outputs and leaves the spare output alone."""
+    rng = np.random.default_rng(11)
+    for _ in range(20):
+        rho = rng.normal(size=3) * 3
+        pn, pm = unit(rng, 2)
+        fr = mlp.pair_frame(rho, pn, pm)
+        for k in range(3):
+            o = np.zeros((1, 6))
+            o[0, :5] = _pack_uniaxial(np.eye(3)[k])
+            o[0, 5] = 0.7
+            lab = mlp.rotate_out(o, fr[None], head=1)
+            np.testing.assert_allclose(lab[0, :5], _pack_uniaxial(fr[k]), atol=1e-14)
+            assert lab[0, 5] == 0.7
+        M = mlp.head_matrices(fr[None], head=1)[0]
+        np.testing.assert_allclose(M[:5, :5] @ M[:5, :5].T, np.eye(5), atol=1e-13)
+        assert np.all(M[5, :5] == 0) and np.all(M[:5, 5] == 0) and M[5, 5] == 1.0
+
+
+def test_strain_head_prediction_equivariant_under_rotation():
+    """Rotating the configuration rotates every predicted Q^(2s) tensor with it:
+    S -> Q S Q^T (the frame is attached to the pair)."""
+    from oracle import tensors
+    rng = np.random.default_rng(12)
+    theta = random_theta(rng)
+    R, p = three_body(rng)
+    tg, sr = mlp.pair_list(R, 1.0)
+    F, FR = mlp.features_for_pairs(R, p, 1.0, tg, sr)
+    out = mlp.predict(theta, F, FR, tg, 3, head=1)
+    Q = random_rotation(rng)
+    F2, FR2 = mlp.features_for_pairs((R + [1.0, 2.0, -3.0]) @ Q.T, p @ Q.T, 1.0, tg, sr)
+    out2 = mlp.predict(theta, F2, FR2, tg, 3, head=1)
+    for n in range(3):
+        S = tensors.unpack_stf(out[n, :5], 2)
+        np.testing.assert_allclose(out2[n, :5], tensors.pack_stf(Q @ S @ Q.T), atol=1e-12)
+    np.testing.assert_allclose(out2[:, 5], out[:, 5], atol=1e-12)
+
+
+def test_finite_difference_gradient_strain_head():
+    rng = np.random.default_rng(13)
+    theta = random_theta(rng, 0.2)
+    R, p = three_body(rng)
+    tg, sr = mlp.pair_list(R, 1.0)
+    F, FR = mlp.features_for_pairs(R, p, 1.0, tg, sr)
+    labels = rng.normal(size=(3, 6))
+    loss, g = mlp.loss_and_grad(theta, F, FR, tg, labels, head=1)
+    starts = np.cumsum([0] + [int(np.prod(s)) for _, s in mlp.SHAPES])[:-1]
+    idx = np.concatenate([rng.choice(mlp.NPARAM, size=40, replace=False), starts, starts + 1])
+    h = 1e-6
+    for i in idx:
+        tp, tm = theta.copy(), theta.copy()
+        tp[i] += h
+        tm[i] -= h
+        lp, _ = mlp.loss_and_grad(tp, F, FR, tg, labels, head=1)
+        lm, _ = mlp.loss_and_grad(tm, F, FR, tg, labels, head=1)
+        fd = (lp - lm) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(fd)), (i, fd, g[i])
+
+
+def test_strain_labels_vanish_when_spheres_separate():
+    """The strain-mode label is the solve's Q^(2s) minus the one-body one: it decays with
+    the separation of two spheres (as (a/r)^3 from the leading strain-strain coupling,
+    Sec. III) and is exactly zero for a single sphere."""
+    from oracle import dynamics, galerkin
+    prm = dict(a=1.0, eta=1.0, k=0.0, vs=0.1, s0=0.05, d0=0.0)
+    p = np.array([[0.0, 0.6, 0.8], [1.0, 0.0, 0.0]])
+    mags = []
+    for r in (3.0, 6.0, 12.0):
+        R = np.array([[0.0, 0.0, 0.0], [r, 0.0, 0.0]])
+        inp = dynamics.trap_inputs(R, p, prm, 4)
+        _, _, QH = galerkin.solve(R, inp["Va"], inp["Oa"], inp["VH"], inp["Fe"], inp["Te"], 1.0, 1.0, 4)
+        lab = mlp.labels_qstrain(QH, galerkin.one_body_QH(inp["VH"], 1.0, 1.0, 4), 0.05, 1.0)
+        assert np.all(lab[:, 5] == 0.0)
+        mags.append(np.abs(lab[:, :5]).max())
+    assert mags[0] > mags[1] > mags[2] > 0
+    assert 4.0 < mags[1] / mags[2] < 16.0          # between (a/r)^2 and (a/r)^4 at large r
+    R1 = np.zeros((1, 3))
+    inp = dynamics.trap_inputs(R1, p[:1], prm, 4)
+    _, _, QH = galerkin.solve(R1, inp["Va"], inp["Oa"], inp["VH"], inp["Fe"], inp["Te"], 1.0, 1.0, 4)
+    lab = mlp.labels_qstrain(QH, galerkin.one_body_QH(inp["VH"], 1.0, 1.0, 4), 0.05, 1.0)
+    assert np.abs(lab).max() < 1e-12
