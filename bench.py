@@ -370,16 +370,17 @@ def learned_nearfield(ctx, gbi, dev, stream, peaks):
 
 
 
-def learned_warm_start(ctx, gbi, T, timed, a, eta, vs, s0, c5, rtol=1e-7):
+def learned_warm_start(ctx, gbi, T, timed, a, eta, vs, s0, c5):
     """The strain-mode head as a warm start of the l <= 4 solve, at equal velocity error.
 
     Trains head 1 on 2- and 3-sphere systems (labels: Q^(2s) of the l <= 4 solve minus the
     one-body value), then solves dense suspensions -- the 2000-sphere one (volume fraction
     0.1, 2.05a exclusion) and the 5000 spheres of the N = 10^5 workload nearest its centre --
-    in several forms with the same refinement tolerance: plain FP64 GMRES from zero, mixed
-    precision from zero, from the one-body Q^H and from the learned guess (the guess's own
-    time included).  Velocity error: max_n |V_n - V_n,ref| / max_n |V_n,ref - V^a_n| against
-    an FP64 solve to 1e-12."""
+    in several forms: plain FP64 GMRES from zero, mixed precision from zero, from the
+    one-body Q^H and from the learned guess (the guess's own time included).  Each form
+    runs at each of a few (refinement tolerance, inner tolerance) settings and reports
+    the fastest one whose velocity error is at most 1e-6: max_n |V_n - V_n,ref| /
+    max_n |V_n,ref - V^a_n| against an FP64 solve to 1e-12."""
     import time
     import numpy as np
     import torch
@@ -401,8 +402,11 @@ def learned_warm_start(ctx, gbi, T, timed, a, eta, vs, s0, c5, rtol=1e-7):
     R5 = np.asarray(c5["R"])
     near = np.argsort(np.linalg.norm(R5 - R5.mean(axis=0), axis=1))[:5000]
     cases = [("N2000_phi0.1", ss["R"], ss["p"]), ("config5_central_5000", R5[near], np.asarray(c5["p"])[near])]
-    out = {"rtol": rtol, "training": {"systems": len(tr["offsets"]) - 1, "label_s": t_label, "train_s": t_train,
-                                      "loss_first": hist[0], "loss_last": hist[-1], "sigma": dtr["sigma"]},
+    settings = {0: [(1e-6, 0.0), (1e-7, 0.0)], 2: [(1e-6, 1e-5), (1e-6, 1e-6), (1e-7, 1e-5)],
+                3: [(1e-6, 1e-5), (1e-6, 1e-6), (1e-7, 1e-5)]}
+    out = {"target_V_error": 1e-6,
+           "training": {"systems": len(tr["offsets"]) - 1, "label_s": t_label, "train_s": t_train,
+                        "loss_first": hist[0], "loss_last": hist[-1], "sigma": dtr["sigma"]},
            "heldout_Q2s_error": held, "cases": {}}
     for name, Rn, pn in cases:
         N = len(Rn)
@@ -416,25 +420,37 @@ def learned_warm_start(ctx, gbi, T, timed, a, eta, vs, s0, c5, rtol=1e-7):
         for form, prec, guess in (("fp64_gmres_from_zero", 0, None), ("mixed2_from_zero", 2, None),
                                   ("mixed2_from_one_body", 2, "one_body"), ("mixed2_from_learned", 2, "learned"),
                                   ("mixed3_from_zero", 3, None), ("mixed3_from_learned", 3, "learned")):
-            prm = gbi.params(a=a, eta=eta, trunc=4, precision=prec, rtol=rtol, restart=40, max_iter=4000,
-                             inner_rtol=1e-5)
+            tried = []
+            for rtol, inner in settings[prec]:
+                prm = gbi.params(a=a, eta=eta, trunc=4, precision=prec, rtol=rtol, restart=40, max_iter=4000,
+                                 inner_rtol=inner if inner > 0 else 1e-5)
 
-            def run():
-                if guess is None:
-                    return ctx.solve(prm, *args)
-                Q0 = nearfield.guess_qh(ctx, prm, R, p, inp["VH"], s0, network=(guess == "learned"))
-                return ctx.solve(prm, *args, QH=Q0, warm_start=True)
-            reps = 1 if prec == 0 else 3
-            run()                                       # first call (and the graph build of a repeat)
-            (V, _, _, info, _), ms = timed(run, reps)
-            err = float((V - Vr).norm(dim=1).max()) / scale
-            forms[form] = {"ms": ms, "solves_per_s": 1e3 / ms, "V_error": err, "iters": info.iters,
-                           "refinements": info.refinements, "rel_residual": info.rel_residual}
-        base = forms["fp64_gmres_from_zero"]["ms"]
+                def run():
+                    if guess is None:
+                        return ctx.solve(prm, *args)
+                    Q0 = nearfield.guess_qh(ctx, prm, R, p, inp["VH"], s0, network=(guess == "learned"))
+                    return ctx.solve(prm, *args, QH=Q0, warm_start=True)
+                reps = 1 if prec == 0 else 3
+                if prec != 0:
+                    run()                       # first call: the host-driven sequence
+                run()                           # a repeat: builds (then replays) the solve graph
+                (V, _, _, info, _), ms = timed(run, reps)
+                err = float((V - Vr).norm(dim=1).max()) / scale
+                tried.append({"rtol": rtol, "inner_rtol": inner if prec else None, "ms": ms, "V_error": err,
+                              "iters": info.iters, "refinements": info.refinements,
+                              "rel_residual": info.rel_residual})
+            ok = [t for t in tried if t["V_error"] <= 1e-6]
+            best = min(ok, key=lambda t: t["ms"]) if ok else None
+            forms[form] = {"best": best, "solves_per_s": 1e3 / best["ms"] if best else None, "settings": tried}
+        base = forms["fp64_gmres_from_zero"]["best"]["ms"]
         for f in forms.values():
-            f["speedup_vs_fp64_gmres"] = base / f["ms"]
+            f["speedup_vs_fp64_gmres"] = base / f["best"]["ms"] if f["best"] else None
         out["cases"][name] = {"N": N, "forms": forms,
-                              "all_within_1e-6": all(f["V_error"] <= 1e-6 for f in forms.values())}
+                              "learned_vs_mixed_from_zero": {
+                                  "precision2": forms["mixed2_from_zero"]["best"]["ms"] /
+                                  forms["mixed2_from_learned"]["best"]["ms"],
+                                  "precision3": forms["mixed3_from_zero"]["best"]["ms"] /
+                                  forms["mixed3_from_learned"]["best"]["ms"]}}
     return out
 
 
@@ -827,7 +843,8 @@ def run_ours(args):
                     for k, v in stats.items() if v["launches"]}
     roofline = {"bound": "alu", "kernel": names.get(dom, "class%d" % dom),
                 "form": "tiled (lanes = targets, TMA-staged sources)" if form == 1 else
-                        "streaming, %d warps per target" % form,
+                        ("chunk-balanced streaming (32-source chunks split evenly over the resident warps)"
+                         if form == 3 else "streaming, %d warps per target" % form),
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": None,
                 "traffic_note": "DRAM bytes per launch are not counted in this run; they come from an ncu capture "

@@ -7,6 +7,7 @@
 #include <cstring>
 
 #include "ctx.cuh"
+#include "pair_chunk.cuh"
 #include "pair_tile.cuh"
 
 namespace gbi {
@@ -190,27 +191,53 @@ gbi_status pass_error_reset(gbi_ctx* ctx) {
   return GBI_OK;
 }
 
-// The tiled form for this pass if the caller's (or the tuned) choice asks for it and its
-// scratch can be had (a context bound to static storage may not have it): fills the
-// plan and scratch fields of a; otherwise a's wpt is set back to a streaming choice.
+gbi_status chunk_reserve(gbi_ctx* ctx, int trunc, int rows, int precision, int N, ChunkPlan* out) {
+  const ChunkPlan c = chunk_plan(N, sm_count(ctx), chunk_warps_sm(trunc, precision));
+  if (c.P <= 0) return GBI_ERR_ARG;
+  const int D = d_of(trunc);
+  const int nr = rows == SET_L ? 6 : (rows == SET_H ? D - 6 : D);
+  GBI_TRY(ensure(ctx, ctx->tile, chunk_part_bytes(c, N, nr, precision == 2 ? sizeof(df) : sizeof(float))));
+  const void* old = ctx->tilecnt.p;
+  GBI_TRY(ensure(ctx, ctx->tilecnt, sizeof(unsigned int) * (size_t)N));
+  // counters start at zero and every launch leaves them so; a new buffer is cleared
+  if (ctx->tilecnt.p != old) GBI_CHECK(cudaMemsetAsync(ctx->tilecnt.p, 0, ctx->tilecnt.bytes, ctx->stream));
+  GBI_TRY(status_words(ctx));
+  if (out) *out = c;
+  return GBI_OK;
+}
+
+bool balanced_args(gbi_ctx* ctx, int trunc, int rows, int precision, int N, PairArgs& a) {
+  if (a.wpt == kFormTile) {
+    TilePlan t;
+    if (tile_reserve(ctx, trunc, rows, precision, N, &t) != GBI_OK) return false;
+    a.tile_P = t.P;
+    a.tile_G = t.G;
+    a.tile_maxseg = t.maxseg;
+  } else {
+    ChunkPlan c;
+    if (chunk_reserve(ctx, trunc, rows, precision, N, &c) != GBI_OK) return false;
+    a.tile_P = c.P;
+    a.tile_G = c.G;
+    a.tile_maxseg = c.maxseg;
+  }
+  a.tile_part = ctx->tile.p;
+  a.tile_cnt = P<unsigned int>(ctx->tilecnt);
+  a.err = pass_error_word(ctx);
+  a.wait_limit = ctx->wait_limit;
+  return true;
+}
+
+// A balanced form (tiled or chunk-balanced) for this pass if the caller's (or the tuned)
+// choice asks for it and its scratch can be had (a context bound to static storage may
+// not have it): fills the plan and scratch fields of a; otherwise a's wpt is set back to
+// a streaming choice.
 void tile_select(gbi_ctx* ctx, int trunc, int rows, int precision, PairArgs& a) {
   const bool batched = a.sys_of != nullptr && a.nsys > 1;
   if (precision == 0 || !balanced_form(a.wpt) || batched || a.N <= 1) {
     if (balanced_form(a.wpt)) a.wpt = 0;
     return;
   }
-  TilePlan t;
-  if (tile_reserve(ctx, trunc, rows, precision, a.N, &t) != GBI_OK) {
-    a.wpt = 0;
-    return;
-  }
-  a.tile_part = ctx->tile.p;
-  a.tile_cnt = P<unsigned int>(ctx->tilecnt);
-  a.tile_P = t.P;
-  a.tile_G = t.G;
-  a.tile_maxseg = t.maxseg;
-  a.err = pass_error_word(ctx);
-  a.wait_limit = ctx->wait_limit;
+  if (!balanced_args(ctx, trunc, rows, precision, a.N, a)) a.wpt = 0;
 }
 
 cudaError_t run_pairs(gbi_ctx* ctx, int trunc, int rows, int cols, int precision, const PairArgs& args_in) {

@@ -172,6 +172,9 @@ gbi_status pass_error_reset(gbi_ctx* ctx);
 struct TilePlan;
 // scratch of a tiled pass over N spheres with these rows in this precision
 gbi_status tile_reserve(gbi_ctx* ctx, int trunc, int rows, int precision, int N, TilePlan* out);
+// plan and scratch of the balanced form a.wpt (tiled or chunk-balanced) for a pass over N
+// spheres, into a; false if the scratch cannot be had
+bool balanced_args(gbi_ctx* ctx, int trunc, int rows, int precision, int N, PairArgs& a);
 cudaError_t run_trap(gbi_ctx* ctx, const TrapArgs& t, int precision);
 int d_of(int trunc);
 const double* scale_tab(int trunc);

@@ -182,22 +182,15 @@ gbi_status tune_impl(gbi_ctx* ctx, int trunc, int nsys, const int* offsets, int 
     // candidates: the tiled form (1, one system only) and 2, 4, ... warps per target of
     // the streaming form
     std::vector<int> cand;
-    if (!batched) cand.push_back(kFormTile);
+    if (!batched) {
+      cand.push_back(kFormTile);
+      cand.push_back(kFormChunk);
+    }
     for (int w = 2; w <= max_wpt(trunc, ps.precision); w *= 2) cand.push_back(w);
     for (const int w : cand) {
       if (e != cudaSuccess) break;
       pa.wpt = w;
-      if (balanced_form(w)) {
-        TilePlan t;
-        if (tile_reserve(ctx, trunc, ps.rows, ps.precision, Ntot, &t) != GBI_OK) continue;
-        pa.tile_part = ctx->tile.p;
-        pa.tile_cnt = P<unsigned int>(ctx->tilecnt);
-        pa.tile_P = t.P;
-        pa.tile_G = t.G;
-        pa.tile_maxseg = t.maxseg;
-        pa.err = pass_error_word(ctx);
-        pa.wait_limit = ctx->wait_limit;
-      }
+      if (balanced_form(w) && !balanced_args(ctx, trunc, ps.rows, ps.precision, Ntot, pa)) continue;
       e = launch_pairs(trunc, ps.rows, ps.cols, ps.precision, pa, ctx->stream);   // warm-up
       if (e == cudaSuccess) e = cudaEventRecord(e0, ctx->stream);
       for (int r = 0; r < reps && e == cudaSuccess; ++r)
@@ -631,7 +624,7 @@ gbi_status gbi_tune(gbi_ctx* ctx, int trunc, int nsys, const int* offsets, int r
 }
 
 gbi_status gbi_set_wpt(gbi_ctx* ctx, int wpt) {
-  if (!ctx || !(wpt == 0 || wpt == 1 || wpt == 2 || wpt == 4 || wpt == 8 || wpt == 16)) return GBI_ERR_ARG;
+  if (!ctx || !(wpt == 0 || wpt == 1 || wpt == 2 || wpt == 3 || wpt == 4 || wpt == 8 || wpt == 16)) return GBI_ERR_ARG;
   ctx->force_wpt = wpt;
   ++ctx->wpt_gen;
   return GBI_OK;

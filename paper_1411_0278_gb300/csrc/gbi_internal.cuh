@@ -115,10 +115,12 @@ inline int max_wpt(int trunc, int precision) { return (trunc == 4 || precision =
 
 // Code of the tiled form of pair_tile.cuh (lanes are targets; single systems only).
 constexpr int kFormTile = 1;
-inline bool balanced_form(int w) { return w == kFormTile; }
+constexpr int kFormChunk = 3;   // chunk-balanced streaming form (pair_chunk.cuh), one system
+inline bool balanced_form(int w) { return w == kFormTile || w == kFormChunk; }
 
 // Warps per target of the FP32 / double-float pair kernel: the requested value (2, 4,
-// 8 or 16; 1 selects the tiled form, which serves one system only), else
+// 8 or 16; 1 selects the tiled form and 3 the chunk-balanced streaming form, which
+// serve one system only), else
 // enough warps to cover 152 SMs at small N and fewer (less reduction work per target)
 // once the N targets alone fill the GPU; capped by max_wpt.
 inline int stream_wpt(int trunc, int precision, int N, int requested, bool batched = false) {

@@ -1,6 +1,7 @@
 // Instantiation and launch of the pair kernel for one arithmetic type and truncation.
 #pragma once
 
+#include "pair_chunk.cuh"
 #include "pair_kernel.cuh"
 #include "pair_tile.cuh"
 
@@ -35,6 +36,22 @@ cudaError_t launch_pairs_tt(int rows, int cols, const PairArgs& args, cudaStream
     // cap), 8 for l <= 4 and double-float; stream_wpt keeps WPT within the same bound
     constexpr bool DF = std::is_same<T, df>::value;
     constexpr int WARPS_SM = (TRN == 4 || DF) ? 8 : 16;
+    if (args.wpt == kFormChunk) {
+      // chunk-balanced streaming form (pair_chunk.cuh): plan and scratch in PairArgs
+#define GBI_K(RV, CV)                                                                              \
+  if (rows == RV && cols == CV) {                                                                  \
+    return launch_pdl(args.pdl != 0, dim3(args.tile_P), dim3(kChunkWarps * 32), stream,            \
+                      pair_chunk_kernel<TRN, RV, CV, T, WARPS_SM / kChunkWarps>, args);            \
+  }
+      GBI_K(SET_H, SET_L)
+      GBI_K(SET_H, SET_H)
+      GBI_K(SET_L, SET_ALL)
+      if constexpr (FULL) {
+        GBI_K(SET_ALL, SET_ALL)
+      }
+#undef GBI_K
+      return cudaErrorInvalidValue;
+    }
     if (args.wpt == kFormTile) {
       // tiled form (pair_tile.cuh): the caller filled the plan and scratch of PairArgs
 #define GBI_T(RV, CV)                                                                              \

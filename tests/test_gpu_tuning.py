@@ -63,7 +63,7 @@ def _case(N, trunc, seed):
 @pytest.mark.parametrize("trunc,N", [(2, 333), (3, 150), (4, 61)])
 @pytest.mark.parametrize("rows,cols", [(2, 2), (2, 1), (1, 0)])
 @pytest.mark.parametrize("precision", [1, 2])
-@pytest.mark.parametrize("wpt", [1, 2, 4, 8, 16])
+@pytest.mark.parametrize("wpt", [1, 2, 3, 4, 8, 16])
 def test_every_wpt_matches_oracle(ctx, gbi, trunc, N, rows, cols, precision, wpt):
     R, A4, d = _case(N, trunc, 70 + trunc)
     g = galerkin.self_scalars(trunc, 1.0)
@@ -81,7 +81,7 @@ def test_every_wpt_matches_oracle(ctx, gbi, trunc, N, rows, cols, precision, wpt
     ref = 1.3 * ref + 0.5 * y0
     ctx.set_wpt(wpt)
     used = ctx.pass_wpt(trunc, rows, cols, precision, N)
-    assert used == (1 if wpt == 1 else min(wpt, 8 if (trunc == 4 or precision == 2) else 16))
+    assert used == (wpt if wpt in (1, 3) else min(wpt, 8 if (trunc == 4 or precision == 2) else 16))
     yd = dev(y0)
     ctx.apply(N, trunc, 1.0, rows, cols, precision, dev(R), dev(x), yd, 1.3, 0.5, add_self)
     torch.cuda.synchronize()
@@ -102,9 +102,9 @@ def test_tune_picks_valid_choices_and_keeps_results(ctx, gbi):
     chosen = ctx.tune(trunc, [0, N], reps=2)
     assert len(chosen) == 6
     fp32_cap = 8 if trunc == 4 else 16
-    assert chosen[0] in (1, 2, 4, 8, 16) and chosen[0] <= fp32_cap
-    assert all(w in (1, 2, 4, 8) for w in chosen[1:4])
-    assert all(w in (1, 2, 4, 8, 16) and w <= fp32_cap for w in chosen[4:])
+    assert chosen[0] in (1, 2, 3, 4, 8, 16) and chosen[0] <= fp32_cap
+    assert all(w in (1, 2, 3, 4, 8) for w in chosen[1:4])
+    assert all(w in (1, 2, 3, 4, 8, 16) and w <= fp32_cap for w in chosen[4:])
     assert ctx.pass_wpt(trunc, 2, 2, 1, N) == chosen[0]
     assert ctx.pass_wpt(trunc, 2, 2, 2, N) == chosen[1]
     assert ctx.pass_wpt(trunc, 2, 1, 2, N) == chosen[2]
@@ -133,16 +133,20 @@ def test_tune_rejects_bad_layouts(ctx, gbi):
         with pytest.raises(gbi.GbiError):
             ctx.tune(2, offs)
     with pytest.raises(gbi.GbiError):
-        ctx.set_wpt(3)
+        ctx.set_wpt(5)
 
 
-@pytest.mark.parametrize("trunc,N", [(2, 2), (2, 33), (3, 64), (3, 97), (2, 1024), (3, 517), (3, 1300)])
+@pytest.mark.parametrize("trunc,N", [(2, 2), (2, 33), (3, 64), (3, 97), (2, 1024), (3, 517), (3, 1300),
+                                     (4, 203)])
 @pytest.mark.parametrize("precision", [1, 2])
-def test_tiled_form_partitions(ctx, gbi, trunc, N, precision):
-    """The tiled form splits (group of 32 targets, source) units evenly over the blocks;
-    whatever the number of groups, partial groups and block ranges that cross groups, it
-    sums the same pairs as the streaming form (to rounding) on three launches in a row
-    (its arrival counters must be back at zero after each)."""
+@pytest.mark.parametrize("form", [1, 3])
+def test_tiled_form_partitions(ctx, gbi, trunc, N, precision, form):
+    """The balanced forms split their units evenly over the grid -- (group of 32 targets,
+    source) units over blocks for the tiled form (1), (target, 32-source chunk) units over
+    warps for the chunk-balanced form (3); whatever the number of groups or chunks,
+    partial groups and ranges that cross them, each sums the same pairs as the streaming
+    form (to rounding) on three launches in a row (its arrival counters must be back at
+    zero after each)."""
     s = workloads.small_cloud(N, 90 + N, phi=0.05)
     R = dev(s["R"])
     d = tensors.ModeBasis(trunc).d
@@ -152,8 +156,8 @@ def test_tiled_form_partitions(ctx, gbi, trunc, N, precision):
     ctx.set_wpt(4)
     y_ref = torch.zeros((h, N), dtype=torch.float64, device="cuda")
     ctx.apply(N, trunc, 1.0, 2, 2, precision, R, x, y_ref, 1.0, 0.0, True)
-    ctx.set_wpt(1)
-    assert ctx.pass_wpt(trunc, 2, 2, precision, N) == 1
+    ctx.set_wpt(form)
+    assert ctx.pass_wpt(trunc, 2, 2, precision, N) == form
     for _ in range(3):
         y = torch.full((h, N), 7.0, dtype=torch.float64, device="cuda")
         ctx.apply(N, trunc, 1.0, 2, 2, precision, R, x, y, 1.0, 0.0, True)
@@ -162,9 +166,10 @@ def test_tiled_form_partitions(ctx, gbi, trunc, N, precision):
     ctx.set_wpt(0)
 
 
-def test_tiled_form_full_size_sampled_rows(ctx, gbi):
-    """N = 1024 at l <= 3 (the solve workload), FP32 H/H pass in the tiled form, against
-    the oracle's dense pair blocks for sampled target spheres."""
+@pytest.mark.parametrize("form", [1, 3])
+def test_tiled_form_full_size_sampled_rows(ctx, gbi, form):
+    """N = 1024 at l <= 3 (the solve workload), FP32 H/H pass in the tiled (1) and the
+    chunk-balanced (3) form, against the oracle's dense pair blocks for sampled targets."""
     c = workloads.config2()
     R = c["R"]
     N, trunc = len(R), 3
@@ -172,7 +177,7 @@ def test_tiled_form_full_size_sampled_rows(ctx, gbi):
     h = d - 6
     rng = np.random.default_rng(5)
     x = rng.normal(size=(h, N))
-    ctx.set_wpt(1)
+    ctx.set_wpt(form)
     y = torch.zeros((h, N), dtype=torch.float64, device="cuda")
     ctx.apply(N, trunc, c["a"], 2, 2, 1, dev(R), dev(x), y, 1.0, 0.0, False)
     torch.cuda.synchronize()
