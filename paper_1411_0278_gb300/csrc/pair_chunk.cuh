@@ -128,23 +128,26 @@ __global__ void __launch_bounds__(kChunkWarps * 32, MINB) pair_chunk_kernel(cons
   if (c0 < c1) {
     const T a = T(args.a);
     const float4* __restrict__ rec = reinterpret_cast<const float4*>(args.x32);
+    // target n and its chunk k, advanced without divisions inside the loop
     int n = int(c0 / cpt);
+    int k = int(c0 - (long long)n * cpt);
+    const int nchunks = int(c1 - c0);
     float4 th = args.pos.hi[n], tl = args.pos.lo[n];
     T acc[NR];
 #pragma unroll
     for (int p = 0; p < NR; ++p) acc[p] = T(0);
-    for (long long c = c0; c < c1; ++c) {
-      const int nc = int(c / cpt);
-      if (nc != n) {
+    for (int i = 0; i < nchunks; ++i, ++k) {
+      if (k == cpt) {
         chunk_flush<TR, ROWS, COLS, T>(args, n, g, cpt, C, G, acc);
-        n = nc;
+        ++n;
+        k = 0;
         th = args.pos.hi[n];
         tl = args.pos.lo[n];
 #pragma unroll
         for (int p = 0; p < NR; ++p) acc[p] = T(0);
       }
       // source index j of target n (its own index skipped)
-      const int j = int(c - (long long)nc * cpt) * 32 + lane;
+      const int j = k * 32 + lane;
       if (j < N - 1) stream_source<TR, ROWS, COLS, T>(args, rec, th, tl, j < n ? j : j + 1, a, acc, min_r2);
     }
     chunk_flush<TR, ROWS, COLS, T>(args, n, g, cpt, C, G, acc);

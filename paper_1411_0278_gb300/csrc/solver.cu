@@ -823,7 +823,9 @@ __global__ void bk_update(const double* __restrict__ V, size_t n, int Ntot, cons
 }
 
 // refinement bookkeeping of system s: mode 0 stores |b_s| (from nrm), mode 1 sets rel and
-// enabled
+// enabled, mode 2 sets rel only (the FP32 residual of a warm start's guess, which sizes
+// the first inner solve but decides nothing: only the high-precision residual may stop a
+// system)
 __device__ void refine_sys(const GPtr& p, int s, int mode, double rtol) {
   GDev* st = p.st + s;
   double v, iv;
@@ -835,13 +837,15 @@ __device__ void refine_sys(const GPtr& p, int s, int mode, double rtol) {
     st->rel = v > 0 ? 1.0 : 0.0;
   } else if (st->enabled) {
     st->rel = v * st->inv_nb;
-    st->enabled = st->rel > rtol ? 1 : 0;
+    if (mode == 1) st->enabled = st->rel > rtol ? 1 : 0;
   }
 }
 
 
 // What follows the norms of bk_norm_then, per system (see there).
-enum NormFollow : int { kFollowNone = 0, kFollowCycle = 1, kFollowRefine0 = 2, kFollowRefine1 = 3, kFollowSweep = 4 };
+enum NormFollow : int {
+  kFollowNone = 0, kFollowCycle = 1, kFollowRefine0 = 2, kFollowRefine1 = 3, kFollowSweep = 4, kFollowWarm = 5
+};
 
 struct NormCtl {
   int follow;                        // NormFollow
@@ -904,6 +908,7 @@ __global__ void __launch_bounds__(256) bk_norm_then(const double* __restrict__ x
       case kFollowRefine0: refine_sys(p, s, 0, nc.rtol); break;
       case kFollowRefine1:
       case kFollowSweep: refine_sys(p, s, 1, nc.rtol); break;
+      case kFollowWarm: refine_sys(p, s, 2, nc.rtol); break;
       default: break;
     }
     s_glob = 0;
@@ -1303,12 +1308,6 @@ __global__ void gk_guard(GPtr p, const unsigned int* __restrict__ minr2, const i
 }
 
 // the sweep loop runs while some system still needs a correction
-// warm start in the solve graph: the first pass of the sweep loop is the initial guess's
-// residual (sweep 0, not a refinement)
-__global__ void gk_warm_begin(DSolve* d) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) d->refinements = -1;
-}
-
 __global__ void gk_sweep_start(GPtr p, cudaGraphConditionalHandle hsw) {
   int any = 0;
   for (int s = threadIdx.x; s < p.S; s += blockDim.x) any |= p.st[s].enabled;
@@ -1670,8 +1669,20 @@ gbi_status solve_core(gbi_ctx* ctx, const gbi_params* prm, const Batch& B, const
                 bk_axpy_enabled<<<g2, 256, 0, ctx->stream>>>(dl, N, B.sys, gp.st, xQH);
                 ++ctx->launches;
               } else {
-                // the guess (packed before the graph) enters the loop as sweep 0
-                gk_warm_begin<<<1, 32, 0, ctx->stream>>>(d);
+                // sweep 0 of a warm start (the guess packed before the graph): its residual
+                // from an FP32 pass sizes the inner solve; the sweeps below check the result
+                // in the high precision
+                GBI_CHECK(cudaMemcpyAsync(r, b, sizeof(double) * nh, cudaMemcpyDeviceToDevice, ctx->stream));
+                PairArgs p = batched(pair_args(s, xQH, r, -1.0, 1.0, 1, s.ones, 6), nullptr);
+                GBI_CHECK(run_pairs(ctx, s.trunc, SET_H, SET_H, 1, p));
+                NormCtl nc{};
+                nc.follow = kFollowWarm;
+                nc.rtol = rtol;
+                bk_norm_then<<<dim3(S, gp.CH), 256, 0, ctx->stream>>>(r, N, h, B.off, gp, 1, nc);
+                ++ctx->launches;
+                GBI_CHECK(cudaMemsetAsync(dl, 0, sizeof(double) * nh, ctx->stream));
+                GBI_TRY(emit_gmres(gb, s, B, gp, restart, r, dl, inner, max_iter, rtol, d));
+                bk_axpy_enabled<<<g2, 256, 0, ctx->stream>>>(dl, N, B.sys, gp.st, xQH);
                 ++ctx->launches;
               }
               // sweeps 1, 2, ...: residual in the high precision, refinement test, inner solve
@@ -1763,15 +1774,15 @@ gbi_status solve_core(gbi_ctx* ctx, const gbi_params* prm, const Batch& B, const
       }
       if (hbits[2] != 0 || hrec->bad_input) return GBI_ERR_ARG;
       const DSolve& hd = *hrec;
-      ctx->launches += ctx->solve_own[0] + (long long)(hd.refinements + (warm ? 1 : 0)) * ctx->solve_own[1] +
+      ctx->launches += ctx->solve_own[0] + (long long)hd.refinements * ctx->solve_own[1] +
                        (long long)hd.ifs * ctx->solve_own[2] + hd.cycles * ctx->solve_own[3] +
                        hd.steps * ctx->solve_own[4];
       // the right-hand-side and output passes are the two the host knows of
       inf->iters = (int)hd.iters;
       inf->refinements = hd.refinements;
-      inf->matvecs_f32 = (int)hd.mv32 + (io == 1 ? 2 : 0);
+      inf->matvecs_f32 = (int)hd.mv32 + (io == 1 ? 2 : 0) + (warm ? 1 : 0);
       inf->matvecs_f64 = (int)hd.mv64 + (io == 1 ? 0 : 2);
-      inf->pair_interactions = hd.pairs + 2 * pairs_all;
+      inf->pair_interactions = hd.pairs + (2 + (warm ? 1 : 0)) * pairs_all;
       inf->rel_residual = hd.rel_max;
       float mr2;
       std::memcpy(&mr2, hbits, sizeof(float));
@@ -1860,11 +1871,14 @@ gbi_status solve_core(gbi_ctx* ctx, const gbi_params* prm, const Batch& B, const
     for (int sweep = 0;; ++sweep) {
       GBI_CHECK(cudaMemcpyAsync(r, b, sizeof(double) * nh, cudaMemcpyDeviceToDevice, ctx->stream));
       if (!(zero && sweep == 0)) {
+        // sweep 0 of a warm start: the guess's residual from an FP32 pass, which only
+        // sizes the inner solve (the later sweeps check in the high precision)
+        const bool warm0 = !zero && sweep == 0;
         PairArgs p = batched(pair_args(s, xQH, r, -1.0, 1.0, 1, s.ones, 6), &gp.st[0].enabled);
-        GBI_CHECK(run_pairs(ctx, s.trunc, SET_H, SET_H, hp, p));
-        inf->matvecs_f64 += 1;
+        GBI_CHECK(run_pairs(ctx, s.trunc, SET_H, SET_H, warm0 ? 1 : hp, p));
+        (warm0 ? inf->matvecs_f32 : inf->matvecs_f64) += 1;
         inf->pair_interactions += pairs_enabled();
-        norm_refine(r, 1, kFollowRefine1);
+        norm_refine(r, 1, warm0 ? kFollowWarm : kFollowRefine1);
       }
       if (sweep > 0) inf->refinements += 1;
       if (sweep >= max_refine || inf->iters >= max_iter) {
