@@ -920,6 +920,35 @@ def run_ours(args):
                                   "traffic": None, "avg_launch_ms": s3["ms"] / max(1, s3["launches"])},
                      "note": "inputs resident (L2-sized), not flushed"}
 
+    # ---- the same cloud above a plane no-slip wall (lowest centre at 2a): unbounded
+    # superposition plus the wall's image flows (FP32)
+    Rw = R3.clone()
+    Rw[:, 2] += 2.0 * c3["a"] - Rw[:, 2].min()
+    inw = ctx.trap_inputs(len(Rw), 2, c3["k"], c3["vs"], c3["s0"], c3["d0"], Rw, p3)
+    for _ in range(2):
+        ctx.wall_superpose(prm3, Rw, inw["Va"], inw["Oa"], inw["VH"], inw["Fe"], inw["Te"], V3, O3)
+    ctx.set_profiling(True)
+    ev0.record(stream)
+    nw = 5
+    for _ in range(nw):
+        ctx.wall_superpose(prm3, Rw, inw["Va"], inw["Oa"], inw["VH"], inw["Fe"], inw["Te"], V3, O3)
+    ev1.record(stream)
+    ev1.synchronize()
+    tw = ev0.elapsed_time(ev1) / 1e3
+    sw = ctx.kernel_stats(gbi._native.WALL_F32)
+    ctx.set_profiling(False)
+    achw = sw["flops"] / (sw["ms"] * 1e-3) / 1e12
+    wall_line = {"workload": c3["name"] + "_above_wall", "N": N3,
+                 "value": nw * N3 * (N3 - 1) / tw, "unit": UNIT, "image_terms_per_s": nw * N3 * N3 / tw,
+                 "ms_per_evaluation": 1e3 * tw / nw,
+                 "roofline": {"bound": "alu",
+                              "kernel": "wall images (records + k_wall_pairs<float>, nested dual numbers + reduce)",
+                              "achieved": achw, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achw / fp32_peak,
+                              "flops_per_image_term": sw["flops"] / max(1, sw["launches"]) / (N3 * N3),
+                              "traffic": None, "avg_launch_ms": sw["ms"] / max(1, sw["launches"])},
+                 "note": "value counts the unbounded pairs N(N-1) per evaluation; the image terms are N^2 "
+                         "(every sphere's own image included)"}
+
     # ---- flow field after the solve: a 64^3 grid through the N = 1024 suspension (FP32)
     V2, O2, Q2, _, _ = ctx.solve(prm, R0, inp["Va"], inp["Oa"], inp["VH"], inp["Fe"], inp["Te"])
     side = float(c["side"])
@@ -1060,7 +1089,7 @@ def run_ours(args):
                              "start": "cold (zero initial guess) every step: mixed precision"},
                 "roofline": roofline,
                 "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
-                "superposition": superposition, "flow_field": flowline, "config1_trajectory": traj64, "config3_trajectory": traj3,
+                "superposition": superposition, "wall_superposition": wall_line, "flow_field": flowline, "config1_trajectory": traj64, "config3_trajectory": traj3,
                 "config3_paper_geometry": trajp, "squirmer_pair_orbits": pair_orbits, "batched": batched, "learned_nearfield": learned,
                 "tuned_wpt": dict(zip(TUNED_PASSES, tuned))}
         print(json.dumps(line), flush=True)

@@ -175,6 +175,20 @@ gbi_status gbi_superpose(gbi_ctx* ctx, const gbi_params* params, int N,
                          const double* R, const double* Va, const double* Oa, const double* VH,
                          const double* Fe, const double* Te, double* V, double* Omega);
 
+/* Superposition approximation above a plane no-slip wall z = 0 (fluid z > 0; every
+ * centre must have z > 0): Sec. VI extends the method to other geometries through their
+ * Green's function, here Blake's (the Oseen tensor plus its image system at the mirror
+ * point).  V, Omega = the unbounded superposition of gbi_superpose (params.trunc must be
+ * 2) plus, at every centre, the image flows of every sphere's force Fe, torque Te and
+ * stresslet S = (20/3) pi eta a^2 V^(2s) (the force dipole it exerts on the fluid), its
+ * own images included, at the point-singularity level (V += u, Omega += curl u / 2).
+ * The image of the potential dipole V^(3t) and the finite-size terms of the images are
+ * not included.  params.precision 0 or 2: FP64 images; 1 or 3: FP32.  Arguments as
+ * gbi_superpose.  Asynchronous. */
+gbi_status gbi_wall_superpose(gbi_ctx* ctx, const gbi_params* params, int N, const double* R, const double* Va,
+                              const double* Oa, const double* VH, const double* Fe, const double* Te, double* V,
+                              double* Omega);
+
 /* One-body flow coefficients of the higher modes, the Q^H of the superposition
  * approximation (Sec. IV): QH = -8 pi eta a VH / g per component (g the self scalars
  * of the truncation, gbi_self_scalars, for a unit sphere).  VH, QH are [N][h] device
@@ -429,7 +443,8 @@ gbi_status gbi_pass_status(gbi_ctx* ctx);
  * precision * 9 + rows * 3 + cols for gbi_apply-style passes (precision 0 = FP64,
  * 1 = FP32, 2 = double-float; rows/cols 0 = all, 1 = rigid-body, 2 = higher),
  * 27 = closed-form trap pass in FP64, 28 = in FP32, 29 = flow field (gbi_flow) in FP64,
- * 30 = in FP32.  gbi_kernel_stats synchronizes
+ * 30 = in FP32, 31 = wall images (gbi_wall_superpose) in FP64, 32 = in FP32 (flops: the
+ * dual-number arithmetic per (target, source) term times N^2).  gbi_kernel_stats synchronizes
  * on the recorded events. */
 long long gbi_kernel_launches(gbi_ctx* ctx);
 /* Number of solves this context has run as one replayed CUDA graph (-1 for a NULL

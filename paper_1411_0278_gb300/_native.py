@@ -99,6 +99,7 @@ _SIGS = {
                                 ctypes.POINTER(ctypes.c_int)]),
     "gbi_mlp_labels_qh": (_I, [_VP, _I, _I, _D, _VP, _VP, c_double_p, _VP]),
     "gbi_qh_onebody": (_I, [_VP, ctypes.POINTER(gbi_params), _I, _VP, _VP]),
+    "gbi_wall_superpose": (_I, [_VP, ctypes.POINTER(gbi_params), _I] + [_VP] * 8),
     "gbi_kernel_launches": (ctypes.c_longlong, [_VP]),
     "gbi_solve_graph_replays": (ctypes.c_longlong, [_VP]),
     "gbi_set_profiling": (_I, [_VP, _I]),
@@ -112,8 +113,9 @@ def kernel_class(precision, rows, cols):
 
 TRAP_F64, TRAP_F32 = 27, 28
 FLOW_F64, FLOW_F32 = 29, 30
+WALL_F64, WALL_F32 = 31, 32
 MLP_NPARAM = 35078
-N_KERNEL_CLASSES = 31
+N_KERNEL_CLASSES = 33
 
 
 def lib():
@@ -439,6 +441,18 @@ class Context:
         self._check(lib().gbi_mlp_labels_qh(self._h, N, int(QHx.shape[1]), float(s0), _ptr(QHx), _ptr(QH1),
                                             ctypes.byref(sig), _ptr(lab)), "gbi_mlp_labels_qh")
         return lab, sig.value
+
+    def wall_superpose(self, prm, R, Va, Oa, VH, Fe, Te, V=None, Om=None):
+        """gbi_wall_superpose: superposition above the wall z = 0 (outputs allocated if None)."""
+        import torch
+        N = R.shape[0]
+        if V is None:
+            V = torch.empty((N, 3), dtype=torch.float64, device=R.device)
+        if Om is None:
+            Om = torch.empty_like(V)
+        self._check(lib().gbi_wall_superpose(self._h, ctypes.byref(prm), int(N), _ptr(R), _ptr(Va), _ptr(Oa),
+                                             _ptr(VH), _ptr(Fe), _ptr(Te), _ptr(V), _ptr(Om)), "gbi_wall_superpose")
+        return V, Om
 
     def qh_onebody(self, prm, VH):
         import torch

@@ -21,6 +21,9 @@ struct Buf {
 };
 // nesting depth of the conditional bodies in the solve graph (one capture stream each)
 constexpr int kCapLevels = 4;
+// classes of gbi_kernel_stats: pair passes 0..26 (precision x 9 + rows x 3 + cols), closed-form
+// trap kernel 27 (FP64) / 28 (FP32), flow field 29 / 30, wall images 31 / 32
+constexpr int kStatClasses = 33;
 }  // namespace gbi
 
 struct gbi_ctx {
@@ -32,6 +35,7 @@ struct gbi_ctx {
   gbi::Buf boff, bsys;                           // system offsets / ids of the current batch
   gbi::Buf tile, tilecnt;                        // tiled pair passes: partial sums, arrival counters
   gbi::Buf flowx, flowrec, flowcnt;              // gbi_flow: coefficients, FP32 records, inside count
+  gbi::Buf wallbuf;                              // gbi_wall_superpose: source records and slice partials
   long long wait_limit = 1ll << 24;              // try_wait rounds of a tiled pass's stage waits
                                                  // (kTileWaitLimit; gbi_set_wait_limit)
   int single_N = -1;                             // boff / bsys hold one system of this many spheres
@@ -69,10 +73,10 @@ struct gbi_ctx {
   };
   std::vector<Rec> pending;
   std::vector<cudaEvent_t> pool;
-  double stat_ms[32] = {0};
-  double stat_flops[32] = {0};
-  long long stat_n[32] = {0};
-  long long stat_dead[32] = {0};
+  double stat_ms[gbi::kStatClasses] = {0};
+  double stat_flops[gbi::kStatClasses] = {0};
+  long long stat_n[gbi::kStatClasses] = {0};
+  long long stat_dead[gbi::kStatClasses] = {0};
   // learned near-field correction: FP32 master weights, Adam moments, bf16-rounded
   // copy (training), padded bf16 copy (inference), gradient; neighbour lists; pair
   // features, outputs and training scratch

@@ -251,7 +251,7 @@ gbi_status gbi_destroy(gbi_ctx* ctx) {
                  &ctx->mlp_grad, &ctx->mlp_pk_tc, &ctx->mlp_err, &ctx->nb_cnt, &ctx->nb_start, &ctx->nb_tg, &ctx->nb_sr, &ctx->nb_scan,
                  &ctx->cell_of, &ctx->cell_cnt, &ctx->cell_start, &ctx->cell_fill, &ctx->cell_items, &ctx->nb_aux,
                  &ctx->mf_F, &ctx->mf_FR, &ctx->mf_lab, &ctx->mf_dO, &ctx->mf_part, &ctx->mf_loss, &ctx->dsolve,
-                 &ctx->tile, &ctx->tilecnt, &ctx->flowx, &ctx->flowrec, &ctx->flowcnt};
+                 &ctx->tile, &ctx->tilecnt, &ctx->flowx, &ctx->flowrec, &ctx->flowcnt, &ctx->wallbuf};
   for (Buf* b : bufs)
     if (b->p) cudaFree(b->p);
   drain_profile(ctx);
@@ -664,7 +664,7 @@ gbi_status gbi_set_profiling(gbi_ctx* ctx, int on) {
   if (!ctx) return GBI_ERR_ARG;
   drain_profile(ctx);
   ctx->prof = on != 0;
-  for (int i = 0; i < 32; ++i) {
+  for (int i = 0; i < kStatClasses; ++i) {
     ctx->stat_dead[i] = 0;
     ctx->stat_ms[i] = 0.0;
     ctx->stat_flops[i] = 0.0;
@@ -675,7 +675,7 @@ gbi_status gbi_set_profiling(gbi_ctx* ctx, int on) {
 
 gbi_status gbi_kernel_stats(gbi_ctx* ctx, int kernel_class, double* total_ms, long long* launches,
                             double* flops) {
-  if (!ctx || kernel_class < 0 || kernel_class >= 31) return GBI_ERR_ARG;
+  if (!ctx || kernel_class < 0 || kernel_class >= kStatClasses) return GBI_ERR_ARG;
   drain_profile(ctx);
   if (total_ms) *total_ms = ctx->stat_ms[kernel_class];
   const long long live = ctx->stat_n[kernel_class] - (ctx->prof ? ctx->stat_dead[kernel_class] : 0);
