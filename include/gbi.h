@@ -189,6 +189,24 @@ gbi_status gbi_wall_superpose(gbi_ctx* ctx, const gbi_params* params, int N, con
                               const double* Oa, const double* VH, const double* Fe, const double* Te, double* V,
                               double* Omega);
 
+/* Superposition approximation in a periodic cube of side L (point forces): Sec. VI
+ * notes that the flow sum of a periodic domain converges only conditionally; the limit
+ * taken is Hasimoto's (zero mean flow over the cell).  V_n = Va_n + Fe_n / (6 pi eta a) +
+ * [sum_{m != n} G^per(R_n - R_m) Fe_m + G^per_self Fe_n] / (8 pi eta), G^per the Oseen
+ * tensor summed over the lattice by Ewald's method: a cell list for the real-space part
+ * (cost ~ N^2 / M^3) and structure factors for the wave-space part (~ N n_k), with the
+ * split chosen to balance the two (so ~ N^1.5 overall).  Positions may lie anywhere
+ * (they are wrapped into the cell).  Rotation rates, force dipoles and finite-size
+ * terms are not included.  params.precision 1 or 3: FP32 sums (truncation ~1e-6);
+ * 0 or 2: FP64 (~1e-13).  *cells_per_side in: 0 chooses the split by the work estimate,
+ * a value >= 3 imposes that many cells per side, a negative value every pair by the
+ * minimum image (NULL: choose); out: the cells used (0 for every pair).  xi (the
+ * splitting parameter) and n_wave (wave vectors in a half space) report the plan and may
+ * be NULL.  R, Va, Fe, V are [N][3] device arrays.  Synchronizes the stream. */
+gbi_status gbi_periodic_superpose(gbi_ctx* ctx, const gbi_params* params, int N, double L, const double* R,
+                                  const double* Va, const double* Fe, double* V, int* cells_per_side, double* xi,
+                                  long long* n_wave);
+
 /* One-body flow coefficients of the higher modes, the Q^H of the superposition
  * approximation (Sec. IV): QH = -8 pi eta a VH / g per component (g the self scalars
  * of the truncation, gbi_self_scalars, for a unit sphere).  VH, QH are [N][h] device

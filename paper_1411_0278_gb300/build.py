@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libgbi.so")
 SOURCES = ["gbi_api.cu", "common.cu", "solver.cu", "nearfield_api.cu", "trap_kernel.cu", "mlp_kernel.cu",
-           "mlp_tc.cu", "flow.cu", "wall.cu"] + ["pairs_%s_%d.cu" % (p, t) for p in ("f32", "f64", "df") for t in (2, 3, 4)] + \
+           "mlp_tc.cu", "flow.cu", "wall.cu", "periodic.cu"] + ["pairs_%s_%d.cu" % (p, t) for p in ("f32", "f64", "df") for t in (2, 3, 4)] + \
     ["pairs_f64_5.cu", "pairs_f64_40.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wno-deprecated-declarations",

@@ -36,6 +36,7 @@ struct gbi_ctx {
   gbi::Buf tile, tilecnt;                        // tiled pair passes: partial sums, arrival counters
   gbi::Buf flowx, flowrec, flowcnt;              // gbi_flow: coefficients, FP32 records, inside count
   gbi::Buf wallbuf;                              // gbi_wall_superpose: source records and slice partials
+  gbi::Buf perbuf;                               // gbi_periodic_superpose: records, cells, wave vectors, S(k)
   long long wait_limit = 1ll << 24;              // try_wait rounds of a tiled pass's stage waits
                                                  // (kTileWaitLimit; gbi_set_wait_limit)
   int single_N = -1;                             // boff / bsys hold one system of this many spheres

@@ -251,7 +251,7 @@ gbi_status gbi_destroy(gbi_ctx* ctx) {
                  &ctx->mlp_grad, &ctx->mlp_pk_tc, &ctx->mlp_err, &ctx->nb_cnt, &ctx->nb_start, &ctx->nb_tg, &ctx->nb_sr, &ctx->nb_scan,
                  &ctx->cell_of, &ctx->cell_cnt, &ctx->cell_start, &ctx->cell_fill, &ctx->cell_items, &ctx->nb_aux,
                  &ctx->mf_F, &ctx->mf_FR, &ctx->mf_lab, &ctx->mf_dO, &ctx->mf_part, &ctx->mf_loss, &ctx->dsolve,
-                 &ctx->tile, &ctx->tilecnt, &ctx->flowx, &ctx->flowrec, &ctx->flowcnt, &ctx->wallbuf};
+                 &ctx->tile, &ctx->tilecnt, &ctx->flowx, &ctx->flowrec, &ctx->flowcnt, &ctx->wallbuf, &ctx->perbuf};
   for (Buf* b : bufs)
     if (b->p) cudaFree(b->p);
   drain_profile(ctx);
