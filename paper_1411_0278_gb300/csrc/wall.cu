@@ -37,13 +37,12 @@ constexpr int kWallThreads = 128;
 constexpr int kWallTile = 64;
 constexpr int kWallRec = 16;   // per source: x y z, F (3), D (9, row-major), pad
 
-// Flops of one (target, source) term as written (FMA = 2): a product of dual numbers
-// D1 = Dual3<T> costs 1 + 3 x 3 = 10, of D2 = Dual3<D1> 10 + 3 (10 + 10 + 4) = 82; a sum
-// or a scaling of D2 16; the D2 reciprocal square root 7 (D1) + 2 x 10 + 4 + 3 x 10 = 61.
-// Shared factors: 14 products, 4 sums / scalings, one reciprocal root; the nine entries:
-// 27 products and 9 x 2 + 9 (diagonal) + 3 + 3 sums / scalings = 33; the accumulation of
-// u and of the curl: 9 x (3 + 2 x 3) = 81.
-constexpr int kWallPairFlops = (14 + 27) * 82 + (4 + 33) * 16 + 61 + 81;
+// Flops of one (target, source) term (FMA = 2) as the compiled FP32 kernel executes them:
+// 392.6 FFMA and 696 other FP32 instructions per term (ncu instruction statistics of the
+// N = 10^4 launch).  The nested dual numbers as written would count 4 096 -- a D2 product
+// is 82 flops -- but most derivative entries are structurally zero (the target-side
+// derivatives of the source height, the constant derivatives of R) and fold away.
+constexpr int kWallPairFlops = 1481;
 
 // ---------------------------------------------------------------------------------
 // dual numbers: a value and its derivatives along three directions.  D1 = Dual3<T>
