@@ -64,7 +64,10 @@ def recip_tensors(L, xi, mmax):
 
 
 def periodic_tensor(x, L, xi, nmax=3, mmax=8):
-    """G^per(x) for x not on the lattice (x: (3,))."""
+    """G^per(x) for x not on the lattice (x: (3,)).  G^per is L-periodic and the lattice
+    sum below is truncated, so x is first reduced to its nearest image."""
+    x = np.asarray(x, float)
+    x = x - L * np.rint(x / L)
     n = lattice(L, nmax)
     G = real_tensor(x + n, xi).sum(0)
     k, Gk = recip_tensors(L, xi, mmax)
@@ -74,6 +77,7 @@ def periodic_tensor(x, L, xi, nmax=3, mmax=8):
 def periodic_tensors(X, L, xi, nmax=3, mmax=8, chunk=256):
     """G^per(x) for many separations X (M, 3) (none on the lattice): (M, 3, 3)."""
     X = np.atleast_2d(np.asarray(X, float))
+    X = X - L * np.rint(X / L)                 # nearest images (G^per is L-periodic)
     n = lattice(L, nmax)
     k, Gk = recip_tensors(L, xi, mmax)
     out = np.zeros((len(X), 3, 3))

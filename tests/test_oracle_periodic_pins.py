@@ -54,6 +54,7 @@ def test_even_periodic_and_regular_at_the_origin():
         G = P.periodic_tensor(x, L, xi)
         np.testing.assert_allclose(P.periodic_tensor(-x, L, xi), G, atol=1e-13)
         np.testing.assert_allclose(P.periodic_tensor(x + [0.0, L, 0.0], L, xi), G, atol=1e-12)
+        np.testing.assert_allclose(P.periodic_tensor(x + [3 * L, -4 * L, 5 * L], L, xi), G, atol=1e-12)
     S = P.self_tensor(L, xi)
     for eps in (1e-3, 1e-4):
         x = eps * np.array([0.3, -0.5, 0.8])
