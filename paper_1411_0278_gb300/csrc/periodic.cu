@@ -19,8 +19,10 @@
 // The split parameter balances the two sums: the cube is cut into M^3 cells of side
 // rc = L / M (M >= 3; M = 0 means every pair by the minimum image, rc = L / 2) and
 // xi = c_r / rc, the wave vectors kept up to |k| = 2 xi sqrt(q_max), with (c_r, q_max) =
-// (3.6, 22) in FP32 and (5.6, 40) in FP64 -- truncation errors below 1e-6 and 1e-13 of
-// the terms.  M minimises the estimated work 27 N^2 / M^3 (pairs) + 2 N n_k (wave terms),
+// (4.2, 30) in FP32 and (5.6, 40) in FP64.  The real-space, wave-space and self parts
+// cancel to a small net velocity, so the truncation must sit well below the target:
+// these give ~1e-6 (FP32, whose accumulations are also compensated) and ~1e-13 of the
+// velocities.  M minimises the estimated work 27 N^2 / M^3 (pairs) + 2 N n_k (wave terms),
 // so the cost grows as N^1.5 instead of N^2.  Real space: a cell list (cells sorted by a
 // stable radix sort, so every sum runs in a fixed order), one thread per target over the
 // 27 neighbouring cells; wave space: the structure factors S(k), one thread per k over
@@ -57,11 +59,11 @@ struct EwaldPlan {
   long long nk = 0;   // wave vectors kept (half space)
 };
 
-// the FP32 phases need |m_i| <= 127 (mmax is about 5.4 M there)
-inline int ewald_max_cells(bool fp32) { return fp32 ? 23 : 128; }
+// the FP32 phases need |m_i| <= 127 (mmax is about 7.3 M there)
+inline int ewald_max_cells(bool fp32) { return fp32 ? 17 : 128; }
 
 EwaldPlan ewald_plan_for(int M, double L, bool fp32) {
-  const double cr = fp32 ? 3.6 : 5.6, qmax = fp32 ? 22.0 : 40.0;
+  const double cr = fp32 ? 4.2 : 5.6, qmax = fp32 ? 30.0 : 40.0;
   EwaldPlan p;
   p.M = M;
   p.rc = M == 0 ? 0.5 * L : L / M;
@@ -176,8 +178,20 @@ __global__ void k_per_cell_bounds(int N, const unsigned int* __restrict__ skey, 
   if (i == N - 1 || skey[i + 1] != k) cend[k] = i + 1;
 }
 
+// u += t, compensated (Kahan) in FP32: the parts of the Ewald sum cancel to a small net
+template <typename T> __device__ __forceinline__ void per_add(T& u, T& c, T t) {
+  if constexpr (std::is_same<T, float>::value) {
+    const T y = t - c;
+    const T s = u + y;
+    c = (s - u) - y;
+    u = s;
+  } else {
+    u += t;
+  }
+}
+
 template <typename T>
-__device__ __forceinline__ void per_real_term(T dx, T dy, T dz, T rc2, T xi, const T* f, T* u) {
+__device__ __forceinline__ void per_real_term(T dx, T dy, T dz, T rc2, T xi, const T* f, T* u, T* uc) {
   const T r2 = dx * dx + dy * dy + dz * dz;
   if (!(r2 < rc2)) return;
   const T r = sqrt(r2);
@@ -189,9 +203,9 @@ __device__ __forceinline__ void per_real_term(T dx, T dy, T dz, T rc2, T xi, con
   const T a = f2 + f1 / r;
   const T b = (f2 - f1 / r) / r2;
   const T dF = dx * f[0] + dy * f[1] + dz * f[2];
-  u[0] += a * f[0] - b * dF * dx;
-  u[1] += a * f[1] - b * dF * dy;
-  u[2] += a * f[2] - b * dF * dz;
+  per_add(u[0], uc[0], a * f[0] - b * dF * dx);
+  per_add(u[1], uc[1], a * f[1] - b * dF * dy);
+  per_add(u[2], uc[2], a * f[2] - b * dF * dz);
 }
 
 // real-space sum of target n: the sources of the 27 cells around its own (M >= 3), or
@@ -206,7 +220,7 @@ __global__ void __launch_bounds__(kPerThreads) k_per_real(int N, double L, int M
   if (n >= N) return;
   const T Lt = T(L), rc2 = T(rc * rc), xit = T(xi);
   const T* pn = pos + 16 * (size_t)n;
-  T u[3] = {T(0), T(0), T(0)};
+  T u[3] = {T(0), T(0), T(0)}, uc[3] = {T(0), T(0), T(0)};
   auto term = [&](int m) {
     if (m == n) return;
     const T* pm = pos + 16 * (size_t)m;
@@ -217,7 +231,7 @@ __global__ void __launch_bounds__(kPerThreads) k_per_real(int N, double L, int M
       ds[d] = v * Lt;
     }
     const T f[3] = {frc[4 * (size_t)m], frc[4 * (size_t)m + 1], frc[4 * (size_t)m + 2]};
-    per_real_term<T>(ds[0], ds[1], ds[2], rc2, xit, f, u);
+    per_real_term<T>(ds[0], ds[1], ds[2], rc2, xit, f, u, uc);
   };
   if (M == 0) {
     for (int m = 0; m < N; ++m) term(m);
@@ -294,7 +308,7 @@ __global__ void __launch_bounds__(kPerThreads) k_per_recip(int N, long long nk, 
       w15[d] = pos[16 * (size_t)n + 8 + d];
       wr[d] = pos[16 * (size_t)n + 12 + d];
     }
-  T u[3] = {T(0), T(0), T(0)};
+  T u[3] = {T(0), T(0), T(0)}, uc[3] = {T(0), T(0), T(0)};
   for (long long base = 0; base < nk; base += kPerTile) {
     const int len = (int)min((long long)kPerTile, nk - base);
     __syncthreads();
@@ -313,9 +327,9 @@ __global__ void __launch_bounds__(kPerThreads) k_per_recip(int N, long long nk, 
       const T wy = ss[6 * j + 1] * c - ss[6 * j + 4] * s;
       const T wz = ss[6 * j + 2] * c - ss[6 * j + 5] * s;
       const T kw = (kx * wx + ky * wy + kz * wz) / (kx * kx + ky * ky + kz * kz);
-      u[0] += pref * (wx - kw * kx);
-      u[1] += pref * (wy - kw * ky);
-      u[2] += pref * (wz - kw * kz);
+      per_add(u[0], uc[0], pref * (wx - kw * kx));
+      per_add(u[1], uc[1], pref * (wy - kw * ky));
+      per_add(u[2], uc[2], pref * (wz - kw * kz));
     }
   }
   if (!live) return;
