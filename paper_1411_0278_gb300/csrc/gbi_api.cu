@@ -187,7 +187,6 @@ gbi_status tune_impl(gbi_ctx* ctx, int trunc, int nsys, const int* offsets, int 
       cand.push_back(kFormChunk);
     }
     for (int w = 2; w <= max_wpt(trunc, ps.precision); w *= 2) cand.push_back(w);
-    if (ps.precision == 1 && trunc <= 3) cand.push_back(kFormPrefetch);
     for (const int w : cand) {
       if (e != cudaSuccess) break;
       pa.wpt = w;
@@ -625,8 +624,7 @@ gbi_status gbi_tune(gbi_ctx* ctx, int trunc, int nsys, const int* offsets, int r
 }
 
 gbi_status gbi_set_wpt(gbi_ctx* ctx, int wpt) {
-  if (!ctx || !(wpt == 0 || wpt == 1 || wpt == 2 || wpt == 3 || wpt == 4 || wpt == 5 || wpt == 8 || wpt == 16))
-    return GBI_ERR_ARG;
+  if (!ctx || !(wpt == 0 || wpt == 1 || wpt == 2 || wpt == 3 || wpt == 4 || wpt == 8 || wpt == 16)) return GBI_ERR_ARG;
   ctx->force_wpt = wpt;
   ++ctx->wpt_gen;
   return GBI_OK;

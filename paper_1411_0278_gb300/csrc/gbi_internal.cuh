@@ -116,9 +116,6 @@ inline int max_wpt(int trunc, int precision) { return (trunc == 4 || precision =
 // Code of the tiled form of pair_tile.cuh (lanes are targets; single systems only).
 constexpr int kFormTile = 1;
 constexpr int kFormChunk = 3;   // chunk-balanced streaming form (pair_chunk.cuh), one system
-// streaming form, 4 warps per target, the next source record loaded ahead (FP32 at l <= 3;
-// 12 resident warps per SM); other passes take 4 warps per target without it
-constexpr int kFormPrefetch = 5;
 inline bool balanced_form(int w) { return w == kFormTile || w == kFormChunk; }
 
 // Warps per target of the FP32 / double-float pair kernel: the requested value (2, 4,
@@ -129,7 +126,6 @@ inline bool balanced_form(int w) { return w == kFormTile || w == kFormChunk; }
 inline int stream_wpt(int trunc, int precision, int N, int requested, bool batched = false) {
   const int d = N >= 8192 ? 2 : (N >= 4096 ? 4 : (N >= 1024 ? 8 : 16));
   if (balanced_form(requested) && !batched && N > 1) return requested;
-  if (requested == kFormPrefetch) return (precision == 1 && trunc <= 3) ? kFormPrefetch : 4;
   const int w = (requested > 1 && !balanced_form(requested)) ? requested : d;
   const int cap = max_wpt(trunc, precision);
   return w < cap ? w : cap;

@@ -422,35 +422,21 @@ __device__ __forceinline__ void warp_transpose_sum(const T* v, T* out) {
 
 // One source m (not the target) of target n, centre th + tl, in the streaming forms:
 // the pair body on m's record, accumulated into acc; min_r2 keeps the smallest r^2.
-template <int TR, int ROWS, int COLS, typename T> struct StreamRec {
-  static constexpr int NV = RecShape<PassShape<TR, ROWS, COLS>::NC>::NV;
-  static constexpr int RECV = std::is_same<T, df>::value ? 2 * NV : NV;
-  float4 sh, sl;        // source centre, two-float split
-  float4 r[RECV];       // source record
-};
-
 template <int TR, int ROWS, int COLS, typename T>
-__device__ __forceinline__ void stream_load(const PairArgs& args, const float4* __restrict__ rec, int m,
-                                            StreamRec<TR, ROWS, COLS, T>& o) {
-  constexpr int RECV = StreamRec<TR, ROWS, COLS, T>::RECV;
-  o.sh = __ldg(args.pos.hi + m);
-  o.sl = __ldg(args.pos.lo + m);
-#pragma unroll
-  for (int i = 0; i < RECV; ++i) o.r[i] = __ldg(rec + (size_t)m * RECV + i);
-}
-
-// the pair body on a loaded source record
-template <int TR, int ROWS, int COLS, typename T>
-__device__ __forceinline__ void stream_compute(const StreamRec<TR, ROWS, COLS, T>& sr, float4 th, float4 tl, T a,
-                                               T* acc, float& min_r2) {
+__device__ __forceinline__ void stream_source(const PairArgs& args, const float4* __restrict__ rec, float4 th,
+                                              float4 tl, int m, T a, T* acc, float& min_r2) {
   using S = PassShape<TR, ROWS, COLS>;
   constexpr int D = S::D;
   constexpr int C0 = S::C0;
   constexpr int NC = S::NC;
   constexpr bool DF = std::is_same<T, df>::value;
   constexpr int NCP = RecShape<NC>::NCP;
-  const float4 sh = sr.sh, sl = sr.sl;
-  const float4* r4 = sr.r;
+  constexpr int NV = RecShape<NC>::NV;
+  constexpr int RECV = DF ? 2 * NV : NV;
+  const float4 sh = __ldg(args.pos.hi + m), sl = __ldg(args.pos.lo + m);
+  float4 r4[RECV];
+#pragma unroll
+  for (int i = 0; i < RECV; ++i) r4[i] = __ldg(rec + (size_t)m * RECV + i);
   T dx, dy, dz;
   if constexpr (DF) {
     // exact difference of the hi parts, plus the (tiny) difference of the lo parts
@@ -470,14 +456,6 @@ __device__ __forceinline__ void stream_compute(const StreamRec<TR, ROWS, COLS, T
     else xl[C0 + q] = f4c(r4, q);
   }
   pair_body<TR, ROWS, COLS, T>(dx, dy, dz, a, xl, acc);
-}
-
-template <int TR, int ROWS, int COLS, typename T>
-__device__ __forceinline__ void stream_source(const PairArgs& args, const float4* __restrict__ rec, float4 th,
-                                              float4 tl, int m, T a, T* acc, float& min_r2) {
-  StreamRec<TR, ROWS, COLS, T> sr;
-  stream_load<TR, ROWS, COLS, T>(args, rec, m, sr);
-  stream_compute<TR, ROWS, COLS, T>(sr, th, tl, a, acc, min_r2);
 }
 
 // Row p (counted from the pass's first row) of target n in the streaming forms: the
@@ -504,9 +482,7 @@ __device__ __forceinline__ void store_target(const PairArgs& args, int n, int p,
   *dst = args.alpha * v + (args.beta != 0.0 ? args.beta * (*dst) : 0.0);
 }
 
-// PF: the next source's record is loaded while the current one is computed (more
-// registers, fewer resident warps; a tuner candidate).
-template <int TR, int ROWS, int COLS, typename T, int WPT, int MINB, bool PF = false>
+template <int TR, int ROWS, int COLS, typename T, int WPT, int MINB>
 __global__ void __launch_bounds__(WPT * 32, MINB) pair_stream_kernel(const PairArgs args) {
   using S = PassShape<TR, ROWS, COLS>;
   constexpr int NR = S::NR;
@@ -537,21 +513,9 @@ __global__ void __launch_bounds__(WPT * 32, MINB) pair_stream_kernel(const PairA
   for (int p = 0; p < NR; ++p) acc[p] = T(0);
   float min_r2 = 3.0e38f;
 
-  if constexpr (PF) {
-    int m = src_lo + warp * 32 + lane;
-    StreamRec<TR, ROWS, COLS, T> cur;
-    if (m < src_hi) stream_load<TR, ROWS, COLS, T>(args, rec, m, cur);
-    for (; m < src_hi; m += WPT * 32) {
-      StreamRec<TR, ROWS, COLS, T> nxt;
-      if (m + WPT * 32 < src_hi) stream_load<TR, ROWS, COLS, T>(args, rec, m + WPT * 32, nxt);
-      if (m != n) stream_compute<TR, ROWS, COLS, T>(cur, th, tl, a, acc, min_r2);
-      cur = nxt;
-    }
-  } else {
-    for (int m = src_lo + warp * 32 + lane; m < src_hi; m += WPT * 32) {
-      if (m == n) continue;
-      stream_source<TR, ROWS, COLS, T>(args, rec, th, tl, m, a, acc, min_r2);
-    }
+  for (int m = src_lo + warp * 32 + lane; m < src_hi; m += WPT * 32) {
+    if (m == n) continue;
+    stream_source<TR, ROWS, COLS, T>(args, rec, th, tl, m, a, acc, min_r2);
   }
 
   T tot[NRC];

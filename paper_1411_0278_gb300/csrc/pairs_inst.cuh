@@ -78,22 +78,6 @@ cudaError_t launch_pairs_tt(int rows, int cols, const PairArgs& args, cudaStream
       return cudaErrorInvalidValue;
     }
     const int wpt = stream_wpt(TRN, DF ? 2 : 1, N, args.wpt);
-    if constexpr (!DF && TRN <= 3) {
-      if (wpt == kFormPrefetch) {
-#define GBI_P(RV, CV)                                                                                  \
-  if (rows == RV && cols == CV)                                                                        \
-    return launch_pdl(args.pdl != 0, dim3(N), dim3(4 * 32), stream, pair_stream_kernel<TRN, RV, CV, T, 4, 3, true>, \
-                      args);
-        GBI_P(SET_H, SET_L)
-        GBI_P(SET_H, SET_H)
-        GBI_P(SET_L, SET_ALL)
-        if constexpr (FULL) {
-          GBI_P(SET_ALL, SET_ALL)
-        }
-#undef GBI_P
-        return cudaErrorInvalidValue;
-      }
-    }
 #define GBI_S(RV, CV, WPT)                                                                         \
   if (rows == RV && cols == CV && wpt == WPT) {                                                    \
     constexpr int MINB = WARPS_SM / WPT > 0 ? WARPS_SM / WPT : 1;                                  \

@@ -63,7 +63,7 @@ def _case(N, trunc, seed):
 @pytest.mark.parametrize("trunc,N", [(2, 333), (3, 150), (4, 61)])
 @pytest.mark.parametrize("rows,cols", [(2, 2), (2, 1), (1, 0)])
 @pytest.mark.parametrize("precision", [1, 2])
-@pytest.mark.parametrize("wpt", [1, 2, 3, 4, 5, 8, 16])
+@pytest.mark.parametrize("wpt", [1, 2, 3, 4, 8, 16])
 def test_every_wpt_matches_oracle(ctx, gbi, trunc, N, rows, cols, precision, wpt):
     R, A4, d = _case(N, trunc, 70 + trunc)
     g = galerkin.self_scalars(trunc, 1.0)
@@ -81,10 +81,7 @@ def test_every_wpt_matches_oracle(ctx, gbi, trunc, N, rows, cols, precision, wpt
     ref = 1.3 * ref + 0.5 * y0
     ctx.set_wpt(wpt)
     used = ctx.pass_wpt(trunc, rows, cols, precision, N)
-    if wpt == 5:      # the prefetching streaming form: FP32 at l <= 3, else 4 warps per target
-        assert used == (5 if precision == 1 and trunc <= 3 else 4)
-    else:
-        assert used == (wpt if wpt in (1, 3) else min(wpt, 8 if (trunc == 4 or precision == 2) else 16))
+    assert used == (wpt if wpt in (1, 3) else min(wpt, 8 if (trunc == 4 or precision == 2) else 16))
     yd = dev(y0)
     ctx.apply(N, trunc, 1.0, rows, cols, precision, dev(R), dev(x), yd, 1.3, 0.5, add_self)
     torch.cuda.synchronize()
@@ -105,9 +102,9 @@ def test_tune_picks_valid_choices_and_keeps_results(ctx, gbi):
     chosen = ctx.tune(trunc, [0, N], reps=2)
     assert len(chosen) == 6
     fp32_cap = 8 if trunc == 4 else 16
-    assert chosen[0] in (1, 2, 3, 4, 5, 8, 16) and chosen[0] <= fp32_cap
+    assert chosen[0] in (1, 2, 3, 4, 8, 16) and chosen[0] <= fp32_cap
     assert all(w in (1, 2, 3, 4, 8) for w in chosen[1:4])
-    assert all(w in (1, 2, 3, 4, 5, 8, 16) and w <= fp32_cap for w in chosen[4:])
+    assert all(w in (1, 2, 3, 4, 8, 16) and w <= fp32_cap for w in chosen[4:])
     assert ctx.pass_wpt(trunc, 2, 2, 1, N) == chosen[0]
     assert ctx.pass_wpt(trunc, 2, 2, 2, N) == chosen[1]
     assert ctx.pass_wpt(trunc, 2, 1, 2, N) == chosen[2]
@@ -136,7 +133,7 @@ def test_tune_rejects_bad_layouts(ctx, gbi):
         with pytest.raises(gbi.GbiError):
             ctx.tune(2, offs)
     with pytest.raises(gbi.GbiError):
-        ctx.set_wpt(6)
+        ctx.set_wpt(5)
 
 
 @pytest.mark.parametrize("trunc,N", [(2, 2), (2, 33), (3, 64), (3, 97), (2, 1024), (3, 517), (3, 1300),
