@@ -193,19 +193,30 @@ gbi_status gbi_wall_superpose(gbi_ctx* ctx, const gbi_params* params, int N, con
  * notes that the flow sum of a periodic domain converges only conditionally; the limit
  * taken is Hasimoto's (zero mean flow over the cell).  V_n = Va_n + Fe_n / (6 pi eta a) +
  * [sum_{m != n} G^per(R_n - R_m) Fe_m + G^per_self Fe_n] / (8 pi eta), G^per the Oseen
- * tensor summed over the lattice by Ewald's method: a cell list for the real-space part
- * (cost ~ N^2 / M^3) and structure factors for the wave-space part (~ N n_k), with the
- * split chosen to balance the two (so ~ N^1.5 overall).  Positions may lie anywhere
- * (they are wrapped into the cell).  Rotation rates, force dipoles and finite-size
- * terms are not included.  params.precision 1 or 3: FP32 sums (truncation ~1e-6);
- * 0 or 2: FP64 (~1e-13).  *cells_per_side in: 0 chooses the split by the work estimate,
- * a value >= 3 imposes that many cells per side, a negative value every pair by the
- * minimum image (NULL: choose); out: the cells used (0 for every pair).  xi (the
- * splitting parameter) and n_wave (wave vectors in a half space) report the plan and may
- * be NULL.  R, Va, Fe, V are [N][3] device arrays.  Synchronizes the stream. */
+ * tensor summed over the lattice by Ewald's method.  Real space: a cell list of M^3 cells
+ * (cost ~ N^2 / M^3) or every pair by the minimum image.  Wave space: either directly over
+ * the wave vectors kept (structure factors, cost ~ N n_k; with the split balanced the
+ * whole sum grows as N^1.5), or on a K^3 mesh (smooth particle-mesh Ewald, order-8
+ * B-splines, cost ~ N + K^3 log K, so ~ N log N overall).  Positions may lie anywhere
+ * (they are wrapped into the cell).  Rotation rates, force dipoles and finite-size terms
+ * are not included.  params.precision 1 or 3: FP32 sums (truncation ~1e-6 of the
+ * velocities, direct or mesh); 0 or 2: FP64 (direct: ~1e-13; a mesh, only when imposed,
+ * is limited by K: ~1e-6 at K = 5 xi L, falling as K^-10).
+ * *cells_per_side in: 0 chooses the split by the work estimate, a value >= 3 imposes that
+ * many cells per side, a negative value every pair by the minimum image (NULL: choose);
+ * out: the cells used (0 for every pair).
+ * *mesh in: 0 chooses between the direct and the mesh form by the work estimate (FP32
+ * only; FP64 keeps the direct sum), a power of 2 in [16, 512] imposes that mesh (with the
+ * cells imposed, at most 128 per side, or else the most cells per side, at least 3, that
+ * it resolves), a negative value the direct sum (NULL: choose); out: the mesh used (0 for
+ * the direct sum).  Other values of *mesh, or a mesh with every pair: GBI_ERR_ARG.
+ * xi (the splitting parameter) and n_wave (the wave vectors of the direct sum in a half
+ * space, or K^3 for the mesh) report the plan and may be NULL.  R, Va, Fe, V are [N][3]
+ * device arrays.  The mesh form's spreading adds with atomics: its last bits depend on
+ * timing.  Synchronizes the stream. */
 gbi_status gbi_periodic_superpose(gbi_ctx* ctx, const gbi_params* params, int N, double L, const double* R,
-                                  const double* Va, const double* Fe, double* V, int* cells_per_side, double* xi,
-                                  long long* n_wave);
+                                  const double* Va, const double* Fe, double* V, int* cells_per_side, int* mesh,
+                                  double* xi, long long* n_wave);
 
 /* One-body flow coefficients of the higher modes, the Q^H of the superposition
  * approximation (Sec. IV): QH = -8 pi eta a VH / g per component (g the self scalars

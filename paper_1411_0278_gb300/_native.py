@@ -101,7 +101,8 @@ _SIGS = {
     "gbi_qh_onebody": (_I, [_VP, ctypes.POINTER(gbi_params), _I, _VP, _VP]),
     "gbi_wall_superpose": (_I, [_VP, ctypes.POINTER(gbi_params), _I] + [_VP] * 8),
     "gbi_periodic_superpose": (_I, [_VP, ctypes.POINTER(gbi_params), _I, _D, _VP, _VP, _VP, _VP,
-                                    ctypes.POINTER(ctypes.c_int), c_double_p, ctypes.POINTER(ctypes.c_longlong)]),
+                                    ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), c_double_p,
+                                    ctypes.POINTER(ctypes.c_longlong)]),
     "gbi_kernel_launches": (ctypes.c_longlong, [_VP]),
     "gbi_solve_graph_replays": (ctypes.c_longlong, [_VP]),
     "gbi_set_profiling": (_I, [_VP, _I]),
@@ -456,21 +457,23 @@ class Context:
                                              _ptr(VH), _ptr(Fe), _ptr(Te), _ptr(V), _ptr(Om)), "gbi_wall_superpose")
         return V, Om
 
-    def periodic_superpose(self, prm, L, R, Va, Fe, V=None, cells=0):
+    def periodic_superpose(self, prm, L, R, Va, Fe, V=None, cells=0, mesh=0):
         """gbi_periodic_superpose: point-force superposition in the periodic cube of side L
-        (cells: 0 choose, >= 3 impose, < 0 every pair).  Returns (V, plan) with
-        plan = dict(cells_per_side, xi, n_wave)."""
+        (cells: 0 choose, >= 3 impose, < 0 every pair; mesh: 0 choose, a power of 2 in
+        [16, 512] impose, < 0 the direct wave-space sum).  Returns (V, plan) with
+        plan = dict(cells_per_side, mesh, xi, n_wave)."""
         import torch
         N = R.shape[0]
         if V is None:
             V = torch.empty((N, 3), dtype=torch.float64, device=R.device)
         M = ctypes.c_int(int(cells))
+        K = ctypes.c_int(int(mesh))
         xi = ctypes.c_double()
         nk = ctypes.c_longlong()
         self._check(lib().gbi_periodic_superpose(self._h, ctypes.byref(prm), int(N), float(L), _ptr(R), _ptr(Va),
-                                                 _ptr(Fe), _ptr(V), ctypes.byref(M), ctypes.byref(xi),
-                                                 ctypes.byref(nk)), "gbi_periodic_superpose")
-        return V, dict(cells_per_side=M.value, xi=xi.value, n_wave=nk.value)
+                                                 _ptr(Fe), _ptr(V), ctypes.byref(M), ctypes.byref(K),
+                                                 ctypes.byref(xi), ctypes.byref(nk)), "gbi_periodic_superpose")
+        return V, dict(cells_per_side=M.value, mesh=K.value, xi=xi.value, n_wave=nk.value)
 
     def qh_onebody(self, prm, VH):
         import torch
