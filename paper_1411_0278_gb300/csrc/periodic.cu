@@ -785,65 +785,138 @@ __global__ void __launch_bounds__(kPmeFftThreads)
   }
 }
 
-// Wave space on the mesh.  A = FT(Q_x + i Q_y), B = FT(Q_z) in natural order: index i_d
-// holds m_d = i_d for i_d < K/2 and i_d - K otherwise.  For each frequency m and its mirror
-// -m: Q_x^(m) = (A(m) + conj A(-m)) / 2, Q_y^(m) = (A(m) - conj A(-m)) / (2 i), Q_z^(m) =
-// B(m); U(m) = T(m) Q^(m) with the real symmetric
-//   T(m) = G^rec(k_m) |b(m)|^2 / L^3 = 8 pi (I - k k / k^2) / k^2 (1 + q + 2 q^2) e^{-q} |b|^2 / L^3,
-// U(-m) = conj U(m); then A = U_x + i U_y and B = U_z at m and -m (T(0) = 0: zero mean
-// flow).  Blocks take rows (iy, iz) in turn; a row whose mirror row ((K - iy) mod K,
-// (K - iz) mod K) is not lower is done together with it (a row that is its own mirror: the
-// pairs ix <= K - ix);
-// bmod[i] = |b_i|^2 of one axis.
+// Wave space on the mesh, fused with the transforms along x.  On entry A = FT_yz(Q_x + i Q_y)
+// and B = FT_yz(Q_z) (transformed along z and y); rows are the x-lines (y, z), K = 2^logK
+// contiguous values each.  A block takes P = 2^logP consecutive rows (same z) and, for each
+// row that owns its pair (row (y, z) and its mirror ((K - y) mod K, (K - z) mod K) with the
+// row not above its mirror; a row that is its own mirror pairs with itself), loads the row
+// and its mirror row of A and of B: 4P rows in shared memory.  It transforms them along x
+// (now A = FT(Q_x + i Q_y), B = FT(Q_z) for those rows, natural order: index i holds
+// m = i for i < K/2 and i - K otherwise), and at every frequency m forms
+//   Q_x^(m) = (A(m) + conj A(-m)) / 2,  Q_y^(m) = (A(m) - conj A(-m)) / (2 i),  Q_z^(m) = B(m),
+//   U(m) = T(m) Q^(m),  T(m) = G^rec(k_m) |b(m)|^2 / L^3
+//        = 8 pi (I - k k / k^2) / k^2 (1 + q + 2 q^2) e^{-q} |b|^2 / L^3  (T(0) = 0: zero mean flow),
+// A(m) = U_x + i U_y, B(m) = U_z (the mirror -m lies in the mirror row at (K - i) mod K), then
+// transforms back along x and stores the rows it owns.  bmod[i] = |b_i|^2 of one axis.
 template <typename G>
-__global__ void k_pme_convolve(typename Cplx<G>::t* __restrict__ A, typename Cplx<G>::t* __restrict__ B, int K,
-                               int logK, double L, double xi, const G* __restrict__ bmod) {
+__global__ void __launch_bounds__(kPmeFftThreads)
+    k_pme_xconv(typename Cplx<G>::t* __restrict__ A, typename Cplx<G>::t* __restrict__ B, int logK, int logP,
+                double L, double xi, const G* __restrict__ bmod, const typename Cplx<G>::t* __restrict__ tw) {
   using C = typename Cplx<G>::t;
-  const unsigned int mask = (unsigned)K - 1u;
+  extern __shared__ __align__(16) unsigned char pme_smem[];
+  const unsigned int K = 1u << logK, mask = K - 1u, stride = K + 1u, P = 1u << logP;
+  const int logLB = logP + 2;   // rows: A own, A mirror, B own, B mirror
+  C* sx = reinterpret_cast<C*>(pme_smem);
+  C* stw = sx + (stride << logLB);
+  const unsigned int r0 = blockIdx.x << logP;
+  const unsigned int z = r0 >> logK, nz = (K - z) & mask;
+  if (nz < z) return;   // the whole block's rows are mirrors of rows done elsewhere
+  // row slot s: own row r0 + s, active unless its mirror is the lower row
+  auto own_row = [&](unsigned int sl) { return r0 + sl; };
+  auto mir_row = [&](unsigned int sl) {
+    const unsigned int y = (r0 + sl) & mask;
+    return ((K - y) & mask) + (nz << logK);
+  };
+  auto active = [&](unsigned int sl) { return own_row(sl) <= mir_row(sl); };
+  // shared row q -> global element base
+  auto row_base = [&](unsigned int q) -> C* {
+    const unsigned int sl = q & (P - 1u);
+    const bool mir = ((q >> logP) & 1u) != 0u;
+    C* g = q < 2u * P ? A : B;
+    return g + ((size_t)(mir ? mir_row(sl) : own_row(sl)) << logK);
+  };
+  for (unsigned int j = threadIdx.x; j < K; j += blockDim.x) stw[j] = tw[j];
+  const unsigned int tot = 1u << (logLB + logK);
+  constexpr int kMaxE = pme_max_line_elems<G>() / kPmeFftThreads;
+  C v[kMaxE];
+#pragma unroll
+  for (int k = 0; k < kMaxE; ++k) {
+    const unsigned int e = threadIdx.x + k * kPmeFftThreads;
+    if (e < tot) v[k] = row_base(e >> logK)[e & mask];
+  }
+#pragma unroll
+  for (int k = 0; k < kMaxE; ++k) {
+    const unsigned int e = threadIdx.x + k * kPmeFftThreads;
+    if (e < tot) sx[(e >> logK) * stride + (e & mask)] = v[k];
+  }
+  __syncthreads();
+  int logNs = 0;
+  if (logK & 1) {
+    pme_fft_pass<G, 1>(sx, stw, logK, logLB, logNs, false);
+    logNs = 1;
+  }
+  for (; logNs < logK; logNs += 2) pme_fft_pass<G, 2>(sx, stw, logK, logLB, logNs, false);
+  // the products: element e of the A rows (own and mirror) and the same element of B
   const G s = G(2.0 * kPi / L);
   const G c0 = G(8.0 * kPi / (L * L * L)), cq = G(0.25 / (xi * xi));
-  for (unsigned int r = blockIdx.x; r < (unsigned)K * K; r += gridDim.x) {
-  const unsigned int iy = r & mask, iz = r >> logK;
-  const unsigned int ny = (K - iy) & mask, nz = (K - iz) & mask;
-  const unsigned int rn = ny + (nz << logK);
-  if (rn < r) continue;   // done with the mirror row
-  const int my = (int)iy < K / 2 ? (int)iy : (int)iy - K, mz = (int)iz < K / 2 ? (int)iz : (int)iz - K;
-  const G ky = s * G(my), kz = s * G(mz);
-  const G byz = bmod[iy] * bmod[iz];
-  C* Ar = A + ((size_t)r << logK);
-  C* Br = B + ((size_t)r << logK);
-  C* An = A + ((size_t)rn << logK);
-  C* Bn = B + ((size_t)rn << logK);
-  for (unsigned int ix = threadIdx.x; ix < (unsigned)K; ix += blockDim.x) {
-    const unsigned int nx = (K - ix) & mask;
-    if (rn == r && nx < ix) continue;   // a self-mirror row: the other element's thread
-    if (r == 0 && ix == 0) {
-      Ar[0] = C{G(0), G(0)};
-      Br[0] = C{G(0), G(0)};
-      continue;
-    }
-    const C a = Ar[ix], an = An[nx], b = Br[ix];
-    const G qx_r = G(0.5) * (a.x + an.x), qx_i = G(0.5) * (a.y - an.y);
-    const G qy_r = G(0.5) * (a.y + an.y), qy_i = G(0.5) * (an.x - a.x);
-    const G qz_r = b.x, qz_i = b.y;
-    const int mx = (int)ix < K / 2 ? (int)ix : (int)ix - K;
-    const G kx = s * G(mx);
-    const G k2 = kx * kx + ky * ky + kz * kz;
-    const G ik2 = G(1) / k2;
-    const G q = k2 * cq;
-    const G pref = c0 * ik2 * (G(1) + q + G(2) * q * q) * per_exp(-q) * bmod[ix] * byz;
-    const G dr = (kx * qx_r + ky * qy_r + kz * qz_r) * ik2, di = (kx * qx_i + ky * qy_i + kz * qz_i) * ik2;
-    const G ux_r = pref * (qx_r - kx * dr), ux_i = pref * (qx_i - kx * di);
-    const G uy_r = pref * (qy_r - ky * dr), uy_i = pref * (qy_i - ky * di);
-    const G uz_r = pref * (qz_r - kz * dr), uz_i = pref * (qz_i - kz * di);
-    // A(m) = U_x + i U_y, A(-m) = conj U_x + i conj U_y
-    Ar[ix] = C{ux_r - uy_i, ux_i + uy_r};
-    Br[ix] = C{uz_r, uz_i};
-    if (rn != r || nx != ix) {
-      An[nx] = C{ux_r + uy_i, uy_r - ux_i};
-      Bn[nx] = C{uz_r, -uz_i};
+  const unsigned int ntot = 1u << (logP + 1 + logK);   // A own and mirror rows
+  C ua[kMaxE / 2], ub[kMaxE / 2];
+#pragma unroll
+  for (int k = 0; k < kMaxE / 2; ++k) {
+    const unsigned int e = threadIdx.x + k * kPmeFftThreads;
+    if (e < ntot) {
+      const unsigned int q = e >> logK, ix = e & mask;
+      const unsigned int sl = q & (P - 1u);
+      const bool mir = q >= P;
+      const unsigned int row = mir ? mir_row(sl) : own_row(sl);
+      const unsigned int iy = row & mask, iz = row >> logK;
+      const unsigned int qm = mir ? sl : sl + P;   // the paired row in shared memory
+      const unsigned int nx = (K - ix) & mask;
+      const C a = sx[q * stride + ix], an = sx[qm * stride + nx], b = sx[(q + 2u * P) * stride + ix];
+      if (row == 0u && ix == 0u) {
+        ua[k] = C{G(0), G(0)};
+        ub[k] = C{G(0), G(0)};
+        continue;
+      }
+      const G qx_r = G(0.5) * (a.x + an.x), qx_i = G(0.5) * (a.y - an.y);
+      const G qy_r = G(0.5) * (a.y + an.y), qy_i = G(0.5) * (an.x - a.x);
+      const G qz_r = b.x, qz_i = b.y;
+      const int mx = (int)ix < (int)K / 2 ? (int)ix : (int)ix - (int)K;
+      const int my = (int)iy < (int)K / 2 ? (int)iy : (int)iy - (int)K;
+      const int mz = (int)iz < (int)K / 2 ? (int)iz : (int)iz - (int)K;
+      const G kx = s * G(mx), ky = s * G(my), kz = s * G(mz);
+      const G k2 = kx * kx + ky * ky + kz * kz;
+      const G ik2 = G(1) / k2;
+      const G qq = k2 * cq;
+      const G pref = c0 * ik2 * (G(1) + qq + G(2) * qq * qq) * per_exp(-qq) * bmod[ix] * bmod[iy] * bmod[iz];
+      const G dr = (kx * qx_r + ky * qy_r + kz * qz_r) * ik2, di = (kx * qx_i + ky * qy_i + kz * qz_i) * ik2;
+      const G ux_r = pref * (qx_r - kx * dr), ux_i = pref * (qx_i - kx * di);
+      const G uy_r = pref * (qy_r - ky * dr), uy_i = pref * (qy_i - ky * di);
+      const G uz_r = pref * (qz_r - kz * dr), uz_i = pref * (qz_i - kz * di);
+      ua[k] = C{ux_r - uy_i, ux_i + uy_r};
+      ub[k] = C{uz_r, uz_i};
     }
   }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < kMaxE / 2; ++k) {
+    const unsigned int e = threadIdx.x + k * kPmeFftThreads;
+    if (e < ntot) {
+      const unsigned int q = e >> logK, ix = e & mask;
+      sx[q * stride + ix] = ua[k];
+      sx[(q + 2u * P) * stride + ix] = ub[k];
+    }
+  }
+  __syncthreads();
+  for (unsigned int j = threadIdx.x; j < K; j += blockDim.x) stw[j].y = -stw[j].y;   // the inverse's twiddles
+  __syncthreads();
+  logNs = 0;
+  if (logK & 1) {
+    pme_fft_pass<G, 1>(sx, stw, logK, logLB, logNs, true);
+    logNs = 1;
+  }
+  for (; logNs < logK; logNs += 2) pme_fft_pass<G, 2>(sx, stw, logK, logLB, logNs, true);
+  // store the rows this block owns: own rows of active slots, mirror rows of active slots
+  // that are not their own mirror
+#pragma unroll
+  for (int k = 0; k < kMaxE; ++k) {
+    const unsigned int e = threadIdx.x + k * kPmeFftThreads;
+    if (e < tot) {
+      const unsigned int q = e >> logK;
+      const unsigned int sl = q & (P - 1u);
+      const bool mir = ((q >> logP) & 1u) != 0u;
+      if (active(sl) && !(mir && mir_row(sl) == own_row(sl))) row_base(q)[e & mask] = sx[q * stride + (e & mask)];
+    }
   }
 }
 
@@ -1057,14 +1130,17 @@ gbi_status run_periodic(gbi_ctx* ctx, int N, double L, double a, double eta, con
     while ((1 << logLB) < LB) ++logLB;
     const dim3 lines((unsigned)((size_t)K * K / LB), 2);
     const size_t fsm = sizeof(C) * ((size_t)LB * (K + 1) + K);
-    for (int ax = 0; ax < 3; ++ax)
-      k_pme_fft<G><<<lines, kPmeFftThreads, fsm, ctx->stream>>>(A, ax == 0 ? Qs : nullptr, logK, logLB, ax, 0, twd);
-    k_pme_convolve<G><<<(unsigned)std::min((size_t)K * K, (size_t)sm_count(ctx) * 16), std::min(K, 256), 0,
-                        ctx->stream>>>(A, B, K, logK, L, p.xi, bmd);
-    for (int ax = 0; ax < 3; ++ax)
-      k_pme_fft<G><<<lines, kPmeFftThreads, fsm, ctx->stream>>>(A, nullptr, logK, logLB, ax, 1, twd);
+    // forward along z (from the staging points) and y, then x with the products and x back,
+    // then y and z back
+    k_pme_fft<G><<<lines, kPmeFftThreads, fsm, ctx->stream>>>(A, Qs, logK, logLB, 2, 0, twd);
+    k_pme_fft<G><<<lines, kPmeFftThreads, fsm, ctx->stream>>>(A, nullptr, logK, logLB, 1, 0, twd);
+    const int logP = logLB - 2;   // 4 P rows = LB rows in shared memory
+    k_pme_xconv<G><<<(unsigned)((size_t)K * K >> logP), kPmeFftThreads, fsm, ctx->stream>>>(A, B, logK, logP, L, p.xi,
+                                                                                              bmd, twd);
+    k_pme_fft<G><<<lines, kPmeFftThreads, fsm, ctx->stream>>>(A, nullptr, logK, logLB, 1, 1, twd);
+    k_pme_fft<G><<<lines, kPmeFftThreads, fsm, ctx->stream>>>(A, nullptr, logK, logLB, 2, 1, twd);
     k_pme_gather<G, T><<<lane_blocks, 128, 0, ctx->stream>>>(N, K, R, L, Fe, sidx, A, B, p.xi, a, eta, ur, Va, V);
-    ctx->launches += 9;
+    ctx->launches += 7;
   }
   GBI_CHECK(cudaGetLastError());
   // the host copies (wave vectors, B-spline moduli) must outlive the transfers

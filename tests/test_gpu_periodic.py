@@ -196,3 +196,28 @@ def test_mesh_argument_checks(ctx, gbi):
     for K in (8, 24, 1024):
         with pytest.raises(RuntimeError):
             ctx.periodic_superpose(prm, 12.0, dev(R), dev(Va), dev(F), cells=3, mesh=K)
+
+
+def test_mesh_bench_workload_sampled(ctx, gbi):
+    """The periodic bench workload (N = 10^5 at volume fraction 0.1, FP32): the chosen plan
+    (particle mesh) against the every-pair sum on every sphere and the oracle's lattice sums
+    for a sampled sphere."""
+    N = 100000
+    L = (N * 4.0 * math.pi / 3.0 / 0.1) ** (1.0 / 3.0)
+    rng = np.random.default_rng(12345 + N)
+    R = rng.uniform(0.0, L, size=(N, 3))
+    F = rng.normal(size=(N, 3)) * 0.1
+    Va = np.zeros_like(R)
+    prm = gbi.params(a=A, eta=ETA, trunc=2, precision=1)
+    V, plan = ctx.periodic_superpose(prm, L, dev(R), dev(Va), dev(F))
+    torch.cuda.synchronize()
+    assert plan["mesh"] > 0, plan
+    V0, _ = ctx.periodic_superpose(prm, L, dev(R), dev(Va), dev(F), cells=-1, mesh=-1)
+    torch.cuda.synchronize()
+    ref = V0.cpu().numpy()
+    scale = np.abs(ref).max()
+    Vg = V.cpu().numpy()
+    assert np.abs(Vg - ref).max() <= 1e-5 * scale, plan
+    tg = [31337]
+    V_o = periodic.periodic_superpose(R, Va, F, A, ETA, L, targets=tg, nmax=1, mmax=10)
+    assert np.abs(Vg[tg] - V_o).max() <= 1e-5 * scale
