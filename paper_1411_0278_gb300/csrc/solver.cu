@@ -856,6 +856,7 @@ struct NormCtl {
   cudaGraphConditionalHandle hsw;    // kFollowSweep: the sweep loop and the inner-solve IF
   cudaGraphConditionalHandle hif;
   int max_refine, max_iter;
+  int incr;                          // kFollowSweep: residuals after the first sweep are updates
 };
 
 // |x_s|^2 per system (partials per row chunk as bk_norm_part forms them, added by one warp
@@ -928,7 +929,12 @@ __global__ void __launch_bounds__(256) bk_norm_then(const double* __restrict__ x
   if (threadIdx.x == 0) {
     p.cnt[p.S] = 0u;
     DSolve* d = nc.d;
-    d->mv64 += 1;
+    // the residual just tested: the high-precision pass (the first sweep, or every sweep
+    // without updates) or the FP32 update r -= A_32 d of the previous sweep's inner solve
+    if (nc.incr && d->refinements > 0)
+      d->mv32 += 1;
+    else
+      d->mv64 += 1;
     d->refinements += 1;
     const int go = any && d->refinements < nc.max_refine && d->iters < nc.max_iter;
     d->ifs += go;
@@ -1498,6 +1504,9 @@ gbi_status solve_core(gbi_ctx* ctx, const gbi_params* prm, const Batch& B, const
   // and of the right-hand-side and output passes (the same, or FP32 for precision 3)
   const int hp = prm->precision >= 2 ? 2 : 0;
   const int io = prm->precision == 3 ? 1 : hp;
+  // residual updates after the first refinement sweep (the double-float modes; precision 1
+  // computes every sweep's residual in FP64)
+  const bool incr = hp == 2;
   const int restart = std::max(1, std::min(prm->restart > 0 ? prm->restart : 40, kMaxRestart));
   GBI_TRY(ensure(ctx, ctx->xQ, sizeof(double) * (size_t)N * D));
   GBI_TRY(ensure(ctx, ctx->b, sizeof(double) * nh));
@@ -1685,15 +1694,26 @@ gbi_status solve_core(gbi_ctx* ctx, const gbi_params* prm, const Batch& B, const
                 bk_axpy_enabled<<<g2, 256, 0, ctx->stream>>>(dl, N, B.sys, gp.st, xQH);
                 ++ctx->launches;
               }
-              // sweeps 1, 2, ...: residual in the high precision, refinement test, inner solve
-              const cudaGraphConditionalHandle hsw = gb.handle();
-              gk_sweep_start<<<1, 256, 0, ctx->stream>>>(gp, hsw);
-              ++ctx->launches;
-              GBI_TRY(gb.body(gb.node(hsw, cudaGraphCondTypeWhile), kBodySweep, [&]() -> gbi_status {
+              // sweeps 1, 2, ...: residual, refinement test, inner solve.  With updates (the
+              // double-float modes) the first sweep's residual b - A_hp x is the only
+              // high-precision pass; each inner solve's correction d then updates it as
+              // r -= A_32 d (d is some 1e-6 of x, so FP32 adds ~1e-13 of |b|)
+              if (incr) {
                 gk_copy<<<grid1(nh), 256, 0, ctx->stream>>>(r, b, nh);
                 ++ctx->launches;
                 PairArgs p = batched(pair_args(s, xQH, r, -1.0, 1.0, 1, s.ones, 6), &gp.st[0].enabled);
                 GBI_CHECK(run_pairs(ctx, s.trunc, SET_H, SET_H, hp, p));
+              }
+              const cudaGraphConditionalHandle hsw = gb.handle();
+              gk_sweep_start<<<1, 256, 0, ctx->stream>>>(gp, hsw);
+              ++ctx->launches;
+              GBI_TRY(gb.body(gb.node(hsw, cudaGraphCondTypeWhile), kBodySweep, [&]() -> gbi_status {
+                if (!incr) {
+                  gk_copy<<<grid1(nh), 256, 0, ctx->stream>>>(r, b, nh);
+                  ++ctx->launches;
+                  PairArgs p = batched(pair_args(s, xQH, r, -1.0, 1.0, 1, s.ones, 6), &gp.st[0].enabled);
+                  GBI_CHECK(run_pairs(ctx, s.trunc, SET_H, SET_H, hp, p));
+                }
                 const cudaGraphConditionalHandle hif = gb.handle();
                 {
                   NormCtl nc{};
@@ -1704,6 +1724,7 @@ gbi_status solve_core(gbi_ctx* ctx, const gbi_params* prm, const Batch& B, const
                   nc.hif = hif;
                   nc.max_refine = max_refine;
                   nc.max_iter = max_iter;
+                  nc.incr = incr ? 1 : 0;
                   bk_norm_then<<<dim3(S, gp.CH), 256, 0, ctx->stream>>>(r, N, h, B.off, gp, 1, nc);
                   ++ctx->launches;
                 }
@@ -1714,6 +1735,10 @@ gbi_status solve_core(gbi_ctx* ctx, const gbi_params* prm, const Batch& B, const
                   GBI_TRY(emit_gmres(gb, s, B, gp, restart, r, dl, inner, max_iter, rtol, d));
                   bk_axpy_enabled<<<g2, 256, 0, ctx->stream>>>(dl, N, B.sys, gp.st, xQH);
                   ++ctx->launches;
+                  if (incr) {
+                    PairArgs p = batched(pair_args(s, dl, r, -1.0, 1.0, 1, s.ones, 6), &gp.st[0].enabled);
+                    GBI_CHECK(run_pairs(ctx, s.trunc, SET_H, SET_H, 1, p));
+                  }
                   GBI_CHECK(cudaGetLastError());
                   return GBI_OK;
                 });
@@ -1869,8 +1894,17 @@ gbi_status solve_core(gbi_ctx* ctx, const gbi_params* prm, const Batch& B, const
   } else {
     // mixed precision: r = b - A_hp x; A_32 d = r (FP32 pair sums, FP64 Arnoldi); x += d
     for (int sweep = 0;; ++sweep) {
-      GBI_CHECK(cudaMemcpyAsync(r, b, sizeof(double) * nh, cudaMemcpyDeviceToDevice, ctx->stream));
-      if (!(zero && sweep == 0)) {
+      if (incr && sweep >= 2) {
+        // the previous inner solve's correction updates the residual: r -= A_32 d
+        PairArgs p = batched(pair_args(s, dl, r, -1.0, 1.0, 1, s.ones, 6), &gp.st[0].enabled);
+        GBI_CHECK(run_pairs(ctx, s.trunc, SET_H, SET_H, 1, p));
+        inf->matvecs_f32 += 1;
+        inf->pair_interactions += pairs_enabled();
+        norm_refine(r, 1, kFollowRefine1);
+      } else {
+        GBI_CHECK(cudaMemcpyAsync(r, b, sizeof(double) * nh, cudaMemcpyDeviceToDevice, ctx->stream));
+      }
+      if (!(zero && sweep == 0) && !(incr && sweep >= 2)) {
         // sweep 0 of a warm start: the guess's residual from an FP32 pass, which only
         // sizes the inner solve (the later sweeps check in the high precision)
         const bool warm0 = !zero && sweep == 0;
