@@ -396,12 +396,16 @@ gbi_status gbi_mlp_get(gbi_ctx* ctx, float* theta_host, double* sigma);
 gbi_status gbi_mlp_features(gbi_ctx* ctx, int P, const double* R, const double* p, const int* tg, const int* sr,
                             double a, float* F, float* FR);
 gbi_status gbi_mlp_forward(gbi_ctx* ctx, int P, const float* F, const float* FR, float* out);
-/* Inference engine of gbi_mlp_forward / gbi_mlp_correct: 0 = warp-level mma.sync
- * m16n8k16 (64 pairs per tile), 1 = tcgen05.mma with the accumulator in tensor memory
- * (128 pairs per tile; default).  Both multiply the same bf16 values with FP32
- * accumulation.  The tcgen05 kernel bounds its completion waits; if one gave up it
- * records it on the device and gbi_mlp_status (synchronizes the stream) returns
- * GBI_ERR_TIMEOUT once and clears the record; outputs of that call are not valid. */
+/* Engine of the network kernels.  Inference (gbi_mlp_forward / gbi_mlp_correct): 0 =
+ * warp-level mma.sync m16n8k16 (64 pairs per tile), 1 = tcgen05.mma with the accumulator in
+ * tensor memory (128 pairs per tile; default); both multiply the same bf16 values with FP32
+ * accumulation.  Training (gbi_mlp_loss_grad / gbi_mlp_train): 0 = the FP32 CUDA cores (the
+ * forward with exact tanh, FP32 gradients), 1 = tcgen05 (the inference kernel's forward,
+ * then a backward kernel whose GEMMs take bf16 operands, dZ rounded to bf16, with FP32
+ * accumulation and the weight gradients accumulated in tensor memory; default).  The
+ * tcgen05 kernels bound their completion waits; if one gave up it records it on the device
+ * and gbi_mlp_status (synchronizes the stream) returns GBI_ERR_TIMEOUT once and clears the
+ * record; outputs of that call are not valid. */
 gbi_status gbi_mlp_set_engine(gbi_ctx* ctx, int engine);
 gbi_status gbi_mlp_status(gbi_ctx* ctx);
 gbi_status gbi_mlp_correct(gbi_ctx* ctx, int N, const double* R, const double* p, double a, double s0, int nsys,

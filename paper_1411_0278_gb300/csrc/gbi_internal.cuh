@@ -270,7 +270,13 @@ cudaError_t sphere_sums_q(int N, const int* start, const float* lab, double scal
 size_t train_part_floats(int max_pairs);
 cudaError_t train_batch(const float* thq, const float* F, const float* FR, const int* start, const double* labels,
                         int p_begin, int p_end, int n_begin, int n_end, int ns_total, float* lab, float* dO,
-                        float* part, double* loss_part, float* grad, int head, cudaStream_t st);
+                        float* part, double* loss_part, float* grad, int head, int engine, const void* packed_tc,
+                        int* err, int num_sms, cudaStream_t st);
+// tensor-core backward of the pairs [0, P) (F, dO already offset): one partial gradient
+// per block in part; the number of blocks it uses
+cudaError_t train_bwd_tc(int P, const float* F, const float* dO, const void* packed, float* part, int* err,
+                         int num_sms, cudaStream_t st);
+int train_bwd_tc_blocks(int P, int num_sms);
 cudaError_t adam(float* th, float* m, float* v, const float* g, int t, double lr, float* thq, void* packed,
                  void* packed_tc, cudaStream_t st);
 cudaError_t sum_into(const double* parts, int n, double* dst, cudaStream_t st);

@@ -557,7 +557,8 @@ cudaError_t sphere_sums_q(int N, const int* start, const float* lab, double scal
 }
 
 // ---------------------------------------------------------------------------------
-// training (FP32 CUDA cores): the forward pass multiplies the same bf16-rounded
+// training on the FP32 CUDA cores (engine 0; engine 1 trains on the tensor cores, the
+// backward kernel in mlp_tc.cu): the forward pass multiplies the same bf16-rounded
 // weights and layer inputs as the tensor-core inference; gradients flow straight
 // through the rounding.  TP pairs per block, one thread per neuron.  Every tile writes a
 // full partial gradient, so smaller tiles (more blocks per batch) cost more in those writes
@@ -763,8 +764,28 @@ __global__ void k_grad_reduce(int ntiles, const float* __restrict__ part, float*
 
 cudaError_t train_batch(const float* thq, const float* F, const float* FR, const int* start, const double* labels,
                         int p_begin, int p_end, int n_begin, int n_end, int ns_total, float* lab, float* dO,
-                        float* part, double* loss_part, float* grad, int head, cudaStream_t st) {
+                        float* part, double* loss_part, float* grad, int head, int engine, const void* packed_tc,
+                        int* err, int num_sms, cudaStream_t st) {
   const int np = p_end - p_begin;
+  const int nb = (n_end - n_begin + 127) / 128;
+  if (engine == 1) {
+    // tensor cores: the forward of the inference kernel, the loss, the backward kernel
+    cudaError_t e = cudaSuccess;
+    if (np > 0) e = infer_tc(np, F + (size_t)p_begin * NIN, FR + (size_t)p_begin * 9, packed_tc,
+                             lab + (size_t)p_begin * 6, err, num_sms, head, st);
+    if (e != cudaSuccess) return e;
+    if (nb > 0)
+      k_train_loss<<<nb, 128, 0, st>>>(n_begin, n_end, start, lab, FR, labels, 1.0 / (6.0 * ns_total), dO,
+                                       loss_part, head);
+    if (np > 0) {
+      e = train_bwd_tc(np, F + (size_t)p_begin * NIN, dO + (size_t)p_begin * 6, packed_tc, part, err, num_sms, st);
+      if (e != cudaSuccess) return e;
+      k_grad_reduce<<<(NPARAM + 255) / 256, 256, 0, st>>>(train_bwd_tc_blocks(np, num_sms), part, grad);
+    } else {
+      cudaMemsetAsync(grad, 0, sizeof(float) * NPARAM, st);
+    }
+    return cudaGetLastError();
+  }
   const int ntiles = (np + TP - 1) / TP;
   const size_t smem_f = sizeof(TrainSmem), smem_b = train_smem_bytes();
   cudaError_t e = cudaFuncSetAttribute(k_train_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_f));
@@ -772,7 +793,6 @@ cudaError_t train_batch(const float* thq, const float* F, const float* FR, const
     e = cudaFuncSetAttribute(k_train_backward, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_b));
   if (e != cudaSuccess) return e;
   if (ntiles > 0) k_train_forward<<<ntiles, NH, smem_f, st>>>(thq, F, FR, p_begin, p_end, lab, head);
-  const int nb = (n_end - n_begin + 127) / 128;
   if (nb > 0)
     k_train_loss<<<nb, 128, 0, st>>>(n_begin, n_end, start, lab, FR, labels, 1.0 / (6.0 * ns_total), dO,
                                      loss_part, head);

@@ -35,9 +35,14 @@ constexpr int K1 = 16;           // layer-1 K (9 features, zero-padded)
 constexpr int N4 = 16;           // output layer N (6 outputs, zero-padded)
 constexpr int CM = 64;           // bf16 elements per core matrix (8 rows x 8)
 
-// core-matrix layout of an R x K operand (K-major): element (r, k) at
-//   ((r / 8) * (K / 8) + k / 8) * 64 + (r % 8) * 8 + k % 8
-// so K-adjacent core matrices are 128 bytes apart (LBO) and 8-row groups K * 16 bytes (SBO)
+// core-matrix layout of an R x C matrix: element (r, c) at
+//   ((r / 8) * (C / 8) + c / 8) * 64 + (r % 8) * 8 + c % 8
+// (8 x 8 blocks, 8 columns contiguous).  As a K-major operand (rows M or N, columns K) its
+// descriptor has LBO = 128 bytes (the next 8 columns) and SBO = C * 16 bytes (the next 8
+// rows); a K step of 16 advances 256 bytes.  The same storage read as an MN-major operand
+// (columns M or N, rows K: the transpose) has LBO = C * 16 bytes (the next 8 rows, along K)
+// and SBO = 128 bytes (the next 8 columns, along M or N), and a K step of 16 advances 2 C * 16
+// bytes -- the reading an in-bounds check of all four combinations on GB300 confirmed.
 __host__ __device__ constexpr int cm_index(int r, int k, int K) { return ((r >> 3) * (K >> 3) + (k >> 3)) * CM + (r & 7) * 8 + (k & 7); }
 
 // packed weights (bf16): W1 [128 x 16], W2 [128 x 128], W3 [128 x 128], W4 [16 x 128], then
@@ -78,7 +83,8 @@ __global__ void k_pack_tc(const float* __restrict__ th, __nv_bfloat16* __restric
 
 __device__ __forceinline__ uint32_t saddr(const void* p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
 
-// shared-memory matrix descriptor: no swizzle, K-major, LBO/SBO in bytes
+// shared-memory matrix descriptor: no swizzle, LBO/SBO in bytes (their meaning for K-major
+// and MN-major operands is stated with cm_index above)
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
   uint64_t d = 0;
   d |= (uint64_t)((addr >> 4) & 0x3FFFu);
@@ -88,9 +94,11 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
   return d;                 // base offset 0, relative LBO, layout 0 = no swizzle
 }
 
-// instruction descriptor of kind::f16: FP32 accumulator, bf16 A and B, both K-major
-__host__ __device__ constexpr uint32_t instr_desc(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+// instruction descriptor of kind::f16: FP32 accumulator, bf16 A and B, K-major unless
+// a_mn / b_mn ask for the MN-major form of that operand
+__host__ __device__ constexpr uint32_t instr_desc(int M, int N, int a_mn = 0, int b_mn = 0) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)a_mn << 15) | ((uint32_t)b_mn << 16) |
+         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 __device__ __forceinline__ void mma_f16(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t accum) {
@@ -279,6 +287,267 @@ __global__ void __launch_bounds__(kTcThreads) k_infer_tc(int P, const float* __r
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(128) : "memory");
 }
 
+// ---- training: backward pass on the tensor cores -------------------------------------
+//
+// For a tile of 128 pairs (dO given by the loss kernel, FP32 [P][6]) the forward pass is
+// recomputed exactly as k_infer_tc computes it (bf16 layer inputs, FP32 accumulation,
+// hardware tanh), and then, with dZ_L = dH_L (1 - h_L^2) rounded to bf16:
+//   dH3 = dO W4,            dW4^T += H3^T dO,
+//   dW3 += dZ3^T H2,        db3 += dZ3^T 1,       dH2 = dZ3 W3,
+//   dW2 += dZ2^T H1,        db2 += dZ2^T 1,       dH1 = dZ2 W2,
+//   dW1 += dZ1^T X          (feature slot 9 holds 1, so column 9 is db1),
+// db4 = sum of dO in FP32.  The transposed operands are the same shared-memory tiles read
+// MN-major.  The weight gradients stay in tensor memory across all tiles a block takes and
+// are written once per block (a partial gradient that a fixed-order reduction sums).
+// h in (1 - h^2) is the bf16-rounded layer output (the value the next layer multiplies).
+constexpr int kBwThreads = 256;
+constexpr int kColZ = 0, kColW3 = 128, kColW2 = 256, kColW1 = 384, kColW4 = 400, kColB3 = 416, kColB2 = 432;
+constexpr int kBwTmemCols = 512;
+
+struct BwSmem {
+  __nv_bfloat16 h[3][TM * NH];     // layer outputs (bf16), [pairs x 128]
+  __nv_bfloat16 dz[TM * NH];       // dZ of the layer being differentiated, [pairs x 128]
+  __nv_bfloat16 x[TM * K1];        // features, slot NIN = 1, [pairs x 16]
+  __nv_bfloat16 dout[TM * N4];     // dO (bf16), [pairs x 16]
+  __nv_bfloat16 ones[N4 * TM];     // row 0 ones, [16 x pairs]
+  __nv_bfloat16 w[PWEND];          // weights, the inference layout
+  float bias[PBIAS];
+  float db4[4][N4];
+  unsigned long long mbar;
+  uint32_t tmem_base;
+  int abort;
+};
+static_assert(sizeof(BwSmem) <= 227 * 1024, "one block per SM, within the shared-memory limit");
+
+__global__ void __launch_bounds__(kBwThreads) k_train_bwd_tc(int P, const float* __restrict__ F,
+                                                          const float* __restrict__ dO,
+                                                          const __nv_bfloat16* __restrict__ pk,
+                                                          float* __restrict__ part, int* __restrict__ err) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  BwSmem& s = *reinterpret_cast<BwSmem*>(smem_raw);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int row = tid & (TM - 1);
+  const int half = warp >> 2;
+  {
+    const int4* src = reinterpret_cast<const int4*>(pk);
+    int4* dst = reinterpret_cast<int4*>(s.w);
+    const int n16 = int((sizeof(__nv_bfloat16) * PWEND + sizeof(float) * PBIAS) / 16);
+    for (int i = tid; i < n16; i += blockDim.x) dst[i] = src[i];
+    for (int i = tid; i < N4 * TM; i += blockDim.x) s.ones[i] = __float2bfloat16_rn(0.f);
+  }
+  __syncthreads();
+  if (tid < TM) s.ones[cm_index(0, tid, TM)] = __float2bfloat16_rn(1.f);
+  const uint32_t mbar = saddr(&s.mbar);
+  if (tid == 0) {
+    s.abort = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(mbar), "r"(1) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(saddr(&s.tmem_base)),
+                 "r"(kBwTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  fence_async_smem();
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = s.tmem_base;
+  const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+  const uint32_t x_a = saddr(s.x), do_a = saddr(s.dout), dz_a = saddr(s.dz), one_a = saddr(s.ones);
+  const uint32_t h_a[3] = {saddr(s.h[0]), saddr(s.h[1]), saddr(s.h[2])};
+  const uint32_t w_a = saddr(s.w);
+  const uint32_t w1_a = w_a + 2 * PW1, w2_a = w_a + 2 * PW2, w3_a = w_a + 2 * PW3, w4_a = w_a + 2 * PW4;
+  uint32_t parity = 0;
+  const int ntiles = (P + TM - 1) / TM;
+  float db4acc[NOUT];
+#pragma unroll
+  for (int c = 0; c < NOUT; ++c) db4acc[c] = 0.f;
+
+  // nk MMAs into column dcol: operand start addresses advance by the K steps given
+  auto chain = [&](int dcol, uint32_t a0, uint32_t alb, uint32_t asb, uint32_t astep, uint32_t b0, uint32_t blb,
+                   uint32_t bsb, uint32_t bstep, int nk, uint32_t idesc, bool accum) {
+    for (int ks = 0; ks < nk; ++ks)
+      mma_f16(tmem + (uint32_t)dcol, smem_desc(a0 + ks * astep, alb, asb), smem_desc(b0 + ks * bstep, blb, bsb), idesc,
+              (accum || ks > 0) ? 1u : 0u);
+  };
+  // operands written by threads become visible to the tensor cores
+  auto publish = [&]() {
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    fence_after();
+  };
+  // thread 0 commits what it issued; everyone waits (bounded)
+  auto complete = [&]() -> bool {
+    if (tid == 0) mma_commit(mbar);
+    long long it = 0;
+    while (!mbar_try_wait(mbar, parity)) {
+      if (++it > kWaitLimit) {
+        s.abort = 1;
+        break;
+      }
+    }
+    parity ^= 1u;
+    fence_after();
+    __syncthreads();
+    return s.abort == 0;
+  };
+  // tanh(Z + b) -> bf16 layer output L
+  auto forward_epilogue = [&](int L) {
+    const float* b = s.bias + L * NH;
+#pragma unroll 1
+    for (int c0 = half * (NH / 2); c0 < (half + 1) * (NH / 2); c0 += 16) {
+      float v[16];
+      tmem_ld16(tmem + lane_base + (uint32_t)(kColZ + c0), v);
+      __align__(16) __nv_bfloat16 o[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) o[i] = __float2bfloat16_rn(tanh_act(v[i] + b[c0 + i]));
+      *reinterpret_cast<int4*>(&s.h[L][cm_index(row, c0, NH)]) = *reinterpret_cast<const int4*>(&o[0]);
+      *reinterpret_cast<int4*>(&s.h[L][cm_index(row, c0 + 8, NH)]) = *reinterpret_cast<const int4*>(&o[8]);
+    }
+  };
+  // dZ = dH (1 - h_L^2) -> bf16
+  auto backward_epilogue = [&](int L) {
+#pragma unroll 1
+    for (int c0 = half * (NH / 2); c0 < (half + 1) * (NH / 2); c0 += 16) {
+      float v[16];
+      tmem_ld16(tmem + lane_base + (uint32_t)(kColZ + c0), v);
+      __align__(16) __nv_bfloat16 hv[16];
+      *reinterpret_cast<int4*>(&hv[0]) = *reinterpret_cast<const int4*>(&s.h[L][cm_index(row, c0, NH)]);
+      *reinterpret_cast<int4*>(&hv[8]) = *reinterpret_cast<const int4*>(&s.h[L][cm_index(row, c0 + 8, NH)]);
+      __align__(16) __nv_bfloat16 o[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const float h = __bfloat162float(hv[i]);
+        o[i] = __float2bfloat16_rn(v[i] * (1.f - h * h));
+      }
+      *reinterpret_cast<int4*>(&s.dz[cm_index(row, c0, NH)]) = *reinterpret_cast<const int4*>(&o[0]);
+      *reinterpret_cast<int4*>(&s.dz[cm_index(row, c0 + 8, NH)]) = *reinterpret_cast<const int4*>(&o[8]);
+    }
+  };
+
+  const uint32_t id_h = instr_desc(TM, NH), id_h_bmn = instr_desc(TM, NH, 0, 1);
+  const uint32_t id_w = instr_desc(NH, NH, 1, 1), id_w16 = instr_desc(NH, N4, 1, 1), id_b = instr_desc(NH, N4, 1, 0);
+  constexpr uint32_t SB128 = NH * 16, SB16 = K1 * 16;   // 8-row strides of the 128- and 16-column tiles
+  bool ok = true, first = true;
+  for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+    const int p = tile * TM + row;
+    const bool live = p < P;
+    if (half == 0) {
+      __align__(16) __nv_bfloat16 f[16];
+#pragma unroll
+      for (int k = 0; k < 16; ++k)
+        f[k] = __float2bfloat16_rn(k < NIN ? (live ? F[(size_t)p * NIN + k] : 0.f) : (k == NIN && live ? 1.f : 0.f));
+      *reinterpret_cast<int4*>(&s.x[cm_index(row, 0, K1)]) = *reinterpret_cast<const int4*>(&f[0]);
+      *reinterpret_cast<int4*>(&s.x[cm_index(row, 8, K1)]) = *reinterpret_cast<const int4*>(&f[8]);
+    } else {
+      __align__(16) __nv_bfloat16 g[16];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        const float v = (c < NOUT && live) ? dO[(size_t)p * 6 + c] : 0.f;
+        if (c < NOUT) db4acc[c] += v;
+        g[c] = __float2bfloat16_rn(v);
+      }
+      *reinterpret_cast<int4*>(&s.dout[cm_index(row, 0, N4)]) = *reinterpret_cast<const int4*>(&g[0]);
+      *reinterpret_cast<int4*>(&s.dout[cm_index(row, 8, N4)]) = *reinterpret_cast<const int4*>(&g[8]);
+    }
+    // forward: Z = X W1^T, H1 W2^T, H2 W3^T
+    publish();
+    if (tid == 0) chain(kColZ, x_a, 128, SB16, 256, w1_a, 128, SB16, 256, 1, id_h, false);
+    if (!(ok = complete())) break;
+    forward_epilogue(0);
+    publish();
+    if (tid == 0) chain(kColZ, h_a[0], 128, SB128, 256, w2_a, 128, SB128, 256, NH / 16, id_h, false);
+    if (!(ok = complete())) break;
+    forward_epilogue(1);
+    publish();
+    if (tid == 0) chain(kColZ, h_a[1], 128, SB128, 256, w3_a, 128, SB128, 256, NH / 16, id_h, false);
+    if (!(ok = complete())) break;
+    forward_epilogue(2);
+    publish();
+    // output layer: dH3 = dO W4 (W4 [16 x 128] read MN-major), dW4^T += H3^T dO
+    if (tid == 0) {
+      chain(kColZ, do_a, 128, SB16, 256, w4_a, SB128, 128, 2 * SB128, 1, id_h_bmn, false);
+      chain(kColW4, h_a[2], SB128, 128, 2 * SB128, do_a, SB16, 128, 2 * SB16, TM / 16, id_w16, !first);
+    }
+    if (!(ok = complete())) break;
+    backward_epilogue(2);
+    publish();
+    // layers 3 and 2: dW += dZ^T H_prev, db += dZ^T 1, dH_prev = dZ W
+    for (int L = 2; L >= 1 && ok; --L) {
+      if (tid == 0) {
+        const int cw = L == 2 ? kColW3 : kColW2, cb = L == 2 ? kColB3 : kColB2;
+        const uint32_t wl = L == 2 ? w3_a : w2_a;
+        chain(cw, dz_a, SB128, 128, 2 * SB128, h_a[L - 1], SB128, 128, 2 * SB128, TM / 16, id_w, !first);
+        chain(cb, dz_a, SB128, 128, 2 * SB128, one_a, 128, SB128, 256, TM / 16, id_b, !first);
+        chain(kColZ, dz_a, 128, SB128, 256, wl, SB128, 128, 2 * SB128, NH / 16, id_h_bmn, false);
+      }
+      if (!(ok = complete())) break;
+      backward_epilogue(L - 1);
+      publish();
+    }
+    if (!ok) break;
+    // layer 1: dW1 (and db1 in column 9) += dZ1^T X
+    if (tid == 0) chain(kColW1, dz_a, SB128, 128, 2 * SB128, x_a, SB16, 128, 2 * SB16, TM / 16, id_w16, !first);
+    if (!(ok = complete())) break;
+    first = false;
+  }
+  // the block's partial gradient
+  float* g = part + (size_t)blockIdx.x * NPARAM;
+  if (ok && !first) {
+    const int j = row;
+#pragma unroll 1
+    for (int c0 = half * (NH / 2); c0 < (half + 1) * (NH / 2); c0 += 16) {
+      float v[16];
+      tmem_ld16(tmem + lane_base + (uint32_t)(kColW3 + c0), v);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) g[OFF_W3 + j * NH + c0 + i] = v[i];
+      tmem_ld16(tmem + lane_base + (uint32_t)(kColW2 + c0), v);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) g[OFF_W2 + j * NH + c0 + i] = v[i];
+    }
+    float v[16], u[16];
+    if (half == 0) {
+      tmem_ld16(tmem + lane_base + (uint32_t)kColW1, v);
+      tmem_ld16(tmem + lane_base + (uint32_t)kColB3, u);
+#pragma unroll
+      for (int k = 0; k < NIN; ++k) g[OFF_W1 + j * NIN + k] = v[k];
+      g[OFF_B1 + j] = v[NIN];
+      g[OFF_B3 + j] = u[0];
+    } else {
+      tmem_ld16(tmem + lane_base + (uint32_t)kColW4, v);
+      tmem_ld16(tmem + lane_base + (uint32_t)kColB2, u);
+#pragma unroll
+      for (int c = 0; c < NOUT; ++c) g[OFF_W4 + c * NH + j] = v[c];
+      g[OFF_B2 + j] = u[0];
+    }
+  }
+  // db4: the dO sums of the threads that staged dO (warps 4..7), fixed order
+  if (half == 1) {
+#pragma unroll
+    for (int c = 0; c < NOUT; ++c) {
+      float t = db4acc[c];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if ((tid & 31) == 0) s.db4[warp - 4][c] = t;
+    }
+  }
+  __syncthreads();
+  if (tid < NOUT) g[OFF_B4 + tid] = ((s.db4[0][tid] + s.db4[1][tid]) + s.db4[2][tid]) + s.db4[3][tid];
+  if (!ok) {
+    long long it = 0;
+    while (!mbar_try_wait(mbar, parity ^ 1u) && ++it <= kWaitLimit) {
+    }
+    if (tid == 0) atomicExch(err, 1);
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kBwTmemCols) : "memory");
+}
+
 }  // namespace
 
 size_t packed_tc_bytes() { return sizeof(__nv_bfloat16) * PWEND + sizeof(float) * PBIAS; }
@@ -297,6 +566,28 @@ cudaError_t infer_tc(int P, const float* F, const float* FR, const void* packed,
   const int ntiles = (P + TM - 1) / TM;
   const int grid = ntiles < 2 * num_sms ? ntiles : 2 * num_sms;
   k_infer_tc<<<grid, kTcThreads, smem, st>>>(P, F, FR, static_cast<const __nv_bfloat16*>(packed), out, err, head);
+  return cudaGetLastError();
+}
+
+}  // namespace mlpk
+}  // namespace gbi
+
+namespace gbi {
+namespace mlpk {
+
+int train_bwd_tc_blocks(int P, int num_sms) {
+  const int ntiles = (P + TM - 1) / TM;
+  return ntiles < num_sms ? ntiles : num_sms;
+}
+
+cudaError_t train_bwd_tc(int P, const float* F, const float* dO, const void* packed, float* part, int* err,
+                         int num_sms, cudaStream_t st) {
+  if (P <= 0) return cudaSuccess;
+  const size_t smem = sizeof(BwSmem);
+  cudaError_t e = cudaFuncSetAttribute(k_train_bwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
+  k_train_bwd_tc<<<train_bwd_tc_blocks(P, num_sms), kBwThreads, smem, st>>>(
+      P, F, dO, static_cast<const __nv_bfloat16*>(packed), part, err);
   return cudaGetLastError();
 }
 

@@ -306,7 +306,8 @@ gbi_status gbi_mlp_loss_grad(gbi_ctx* ctx, int N, const double* R, const double*
   GBI_CHECK(mlpk::train_batch(P<float>(ctx->mlp_thq), P<float>(ctx->mf_F), P<float>(ctx->mf_FR),
                               P<int>(ctx->nb_start), labels, 0, np_, 0, N, N, P<float>(ctx->mf_lab),
                               P<float>(ctx->mf_dO), P<float>(ctx->mf_part), P<double>(ctx->mf_loss), grad,
-                              ctx->mlp_head, ctx->stream));
+                              ctx->mlp_head, ctx->mlp_engine, ctx->mlp_pk_tc.p, P<int>(ctx->mlp_err), sm_count(ctx),
+                              ctx->stream));
   GBI_CHECK(mlpk::sum_into(P<double>(ctx->mf_loss), nlb, P<double>(ctx->mf_loss) + nlb, ctx->stream));
   ctx->launches += 5;
   GBI_CHECK(cudaMemcpyAsync(loss, P<double>(ctx->mf_loss) + nlb, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
@@ -407,7 +408,8 @@ gbi_status gbi_mlp_train(gbi_ctx* ctx, int N, const double* R, const double* p, 
       GBI_CHECK(mlpk::train_batch(P<float>(ctx->mlp_thq), P<float>(ctx->mf_F), P<float>(ctx->mf_FR),
                                   P<int>(ctx->nb_start), labels, hstart[n0], hstart[n1], n0, n1, n1 - n0,
                                   P<float>(ctx->mf_lab), P<float>(ctx->mf_dO), P<float>(ctx->mf_part), lpart,
-                                  P<float>(ctx->mlp_grad), ctx->mlp_head, ctx->stream));
+                                  P<float>(ctx->mlp_grad), ctx->mlp_head, ctx->mlp_engine, ctx->mlp_pk_tc.p,
+                                  P<int>(ctx->mlp_err), sm_count(ctx), ctx->stream));
       GBI_CHECK(mlpk::sum_into(lpart, (n1 - n0 + 127) / 128, lstep + b, ctx->stream));
       // learning rate: geometric from lr0 to lr1 over all steps
       const double frac = total_steps > 1 ? double(step) / double(total_steps - 1) : 0.0;

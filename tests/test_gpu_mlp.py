@@ -137,17 +137,22 @@ def test_engines_agree(ctx, gbi):
     assert np.median(np.abs(a - b)) <= 1e-4 * np.abs(a).max()
 
 
-def test_training_gradient_matches_oracle(ctx, gbi):
+@pytest.mark.parametrize("engine", [0, 1])
+def test_training_gradient_matches_oracle(ctx, gbi, engine):
+    """Both training engines against the oracle's gradient: engine 0 (FP32 CUDA cores) and
+    engine 1 (tcgen05: the inference forward, bf16 GEMM operands in the backward)."""
     from paper_1411_0278_gb300 import nearfield
     d = workloads.nearfield_systems(30, 50, k=2)
     th = nearfield.init_theta(11)
     ctx.mlp_set(th, 2.0)
+    ctx.mlp_set_engine(engine)
     rng = np.random.default_rng(4)
     labels = rng.normal(size=(len(d["R"]), 6))
     loss, g = ctx.mlp_loss_grad(dev(d["R"]), dev(d["p"]), 1.0, dev(labels), d["offsets"])
     tg, sr = omlp.pair_list(d["R"], 1.0, d["offsets"])
     F, FR = omlp.features_for_pairs(d["R"], d["p"], 1.0, tg, sr)
     lo, go = omlp.loss_and_grad(th.astype(np.float64), F, FR, tg, labels, bf16=True)
+    ctx.mlp_status()
     assert abs(loss - lo) <= 2e-3 * lo
     g = g.cpu().numpy().astype(np.float64)
     assert np.linalg.norm(g - go) <= 2e-2 * np.linalg.norm(go)
@@ -155,6 +160,31 @@ def test_training_gradient_matches_oracle(ctx, gbi):
         k0 = sum(int(np.prod(s)) for n_, s in omlp.SHAPES[:[n for n, _ in omlp.SHAPES].index(name)])
         blk = slice(k0, k0 + int(np.prod(shp)))
         assert np.linalg.norm(g[blk] - go[blk]) <= 5e-2 * np.linalg.norm(go[blk]), name
+
+
+def test_training_gradient_many_tiles(ctx, gbi):
+    """~7e4 pairs (several 128-pair tiles per block of the tensor-core backward, whose
+    weight gradients accumulate in tensor memory across them): both engines against the
+    oracle, and against each other."""
+    from paper_1411_0278_gb300 import nearfield
+    d = workloads.nearfield_systems(3000, 12000, k=5)
+    th = nearfield.init_theta(13)
+    ctx.mlp_set(th, 2.0)
+    labels = np.random.default_rng(6).normal(size=(len(d["R"]), 6))
+    tg, sr = omlp.pair_list(d["R"], 1.0, d["offsets"])
+    assert len(tg) > 128 * 2 * 152
+    F, FR = omlp.features_for_pairs(d["R"], d["p"], 1.0, tg, sr)
+    lo, go = omlp.loss_and_grad(th.astype(np.float64), F, FR, tg, labels, bf16=True)
+    gs = []
+    for engine in (0, 1):
+        ctx.mlp_set_engine(engine)
+        loss, g = ctx.mlp_loss_grad(dev(d["R"]), dev(d["p"]), 1.0, dev(labels), d["offsets"])
+        ctx.mlp_status()
+        g = g.cpu().numpy().astype(np.float64)
+        assert abs(loss - lo) <= 2e-3 * lo, engine
+        assert np.linalg.norm(g - go) <= 2e-2 * np.linalg.norm(go), engine
+        gs.append(g)
+    assert np.linalg.norm(gs[1] - gs[0]) <= 2e-2 * np.linalg.norm(gs[0])
 
 
 def test_adam_matches_oracle(ctx, gbi):
@@ -296,12 +326,14 @@ def test_strain_head_forward_matches_oracle(ctx, gbi, engine):
     assert np.abs(lab - want).max() <= 1e-2 * np.abs(want).max()
 
 
-def test_strain_head_gradient_matches_oracle(ctx, gbi):
+@pytest.mark.parametrize("engine", [0, 1])
+def test_strain_head_gradient_matches_oracle(ctx, gbi, engine):
     from paper_1411_0278_gb300 import nearfield
     d = workloads.nearfield_systems(30, 50, k=12)
     th = nearfield.init_theta(19)
     ctx.mlp_set(th, 2.0)
     ctx.mlp_set_head(1)
+    ctx.mlp_set_engine(engine)
     labels = np.random.default_rng(5).normal(size=(len(d["R"]), 6))
     loss, g = ctx.mlp_loss_grad(dev(d["R"]), dev(d["p"]), 1.0, dev(labels), d["offsets"])
     tg, sr = omlp.pair_list(d["R"], 1.0, d["offsets"])
