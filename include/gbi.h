@@ -447,9 +447,19 @@ gbi_status gbi_mlp_labels_qh(gbi_ctx* ctx, int N, int h, double s0, const double
  * buffers and synchronizes the stream (not capturable).
  * gbi_set_wpt forces one WPT for every later pass (0 = back to tuned/default).
  * gbi_pass_wpt returns the WPT a pass with these parameters would use (0 for the
- * FP64 tiled pass, -1 for invalid arguments). */
+ * FP64 tiled pass, -1 for invalid arguments).
+ * Split tail (streaming form, one system; off by default): when the N target blocks do not
+ * fill whole waves of the resident block slots, the targets of the last, partly filled
+ * wave have their sources split into 2..8 blocks each (the count that best fills the
+ * slots), whose rows are added in part order by the last part to finish -- the result does
+ * not depend on timing, only the summation order of those targets changes.  On GB300 at
+ * N = 1024 (l <= 3, H/H) it measured slower in FP32 (each part's reduction costs as much
+ * as the pairs it takes over) and within 3% in double-float, so it is off unless asked for.
+ * gbi_set_split_tail(ctx, 1) turns it on (0 off); gbi_tune times with the setting in
+ * force. */
 gbi_status gbi_tune(gbi_ctx* ctx, int trunc, int nsys, const int* offsets, int reps, int* chosen);
 gbi_status gbi_set_wpt(gbi_ctx* ctx, int wpt);
+gbi_status gbi_set_split_tail(gbi_ctx* ctx, int on);
 int gbi_pass_wpt(gbi_ctx* ctx, int trunc, int rows, int cols, int precision, int N, int batched);
 
 /* Bounded waits of the tiled pair passes (engineering; the paper has no counterpart).

@@ -76,6 +76,7 @@ _SIGS = {
     "gbi_solve_static": (_I, [_VP, ctypes.POINTER(gbi_params), _I] + [_VP] * 9 + [_I, ctypes.POINTER(gbi_info)]),
     "gbi_tune": (_I, [_VP, _I, _I, ctypes.POINTER(ctypes.c_int), _I, ctypes.POINTER(ctypes.c_int)]),
     "gbi_set_wpt": (_I, [_VP, _I]),
+    "gbi_set_split_tail": (_I, [_VP, _I]),
     "gbi_pass_wpt": (_I, [_VP, _I, _I, _I, _I, _I, _I]),
     "gbi_set_wait_limit": (_I, [_VP, ctypes.c_longlong]),
     "gbi_pass_status": (_I, [_VP]),
@@ -341,6 +342,9 @@ class Context:
 
     def set_wpt(self, wpt):
         self._check(lib().gbi_set_wpt(self._h, int(wpt)), "gbi_set_wpt")
+
+    def set_split_tail(self, on):
+        self._check(lib().gbi_set_split_tail(self._h, int(on)), "gbi_set_split_tail")
 
     def set_wait_limit(self, rounds):
         self._check(lib().gbi_set_wait_limit(self._h, int(rounds)), "gbi_set_wait_limit")

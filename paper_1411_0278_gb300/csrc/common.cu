@@ -240,6 +240,51 @@ void tile_select(gbi_ctx* ctx, int trunc, int rows, int precision, PairArgs& a) 
   if (!balanced_args(ctx, trunc, rows, precision, a.N, a)) a.wpt = 0;
 }
 
+// Split of the streaming form's last, partly filled wave (see PairArgs::split_from): with
+// `slots` resident blocks, N = full * slots + r targets take full + 1 waves of whole-target
+// blocks; split into ns parts, the last r targets take ceil(r ns / slots) waves of 1/ns of a
+// block instead.  ns (2..8) minimises that, charging 2% of a block per part for the extra
+// reductions and stores; no split unless it saves more than that.
+void split_plan(int N, int slots, int& split_from, int& nsplit) {
+  split_from = 0x7fffffff;
+  nsplit = 1;
+  if (slots <= 0 || N <= slots || N % slots == 0) return;
+  const int r = N % slots, full = N / slots;
+  double best = full + 1.0;
+  for (int ns = 2; ns <= 8; ++ns) {
+    const double c = full + double((r * ns + slots - 1) / slots) / ns + 0.02 * ns;
+    if (c < best - 1e-9) {
+      best = c;
+      nsplit = ns;
+    }
+  }
+  if (nsplit > 1) split_from = N - r;
+}
+
+// the split's scratch: one row block per part of each split target, one arrival counter
+// per split target (zero between launches; a new buffer is cleared)
+bool split_reserve(gbi_ctx* ctx, int trunc, int rows, int precision, PairArgs& a) {
+  const int wpt = stream_wpt(trunc, precision, a.N, a.wpt);
+  const int warps_sm = (trunc == 4 || precision == 2) ? 8 : 16;
+  int from = 0, ns = 1;
+  split_plan(a.N, sm_count(ctx) * std::max(1, warps_sm / wpt), from, ns);
+  if (ns <= 1) return false;
+  const int D = d_of(trunc);
+  const int nr = rows == SET_L ? 6 : (rows == SET_H ? D - 6 : (rows == SET_P ? 3 : D));
+  const size_t nrc32 = (size_t)((nr + 31) / 32) * 32;
+  const int tail = a.N - from;
+  if (ensure(ctx, ctx->tile, sizeof(double) * (size_t)tail * ns * nrc32) != GBI_OK) return false;
+  const void* old = ctx->tilecnt.p;
+  if (ensure(ctx, ctx->tilecnt, sizeof(unsigned int) * (size_t)a.N) != GBI_OK) return false;
+  if (ctx->tilecnt.p != old && cudaMemsetAsync(ctx->tilecnt.p, 0, ctx->tilecnt.bytes, ctx->stream) != cudaSuccess)
+    return false;
+  a.tile_part = ctx->tile.p;
+  a.tile_cnt = P<unsigned int>(ctx->tilecnt);
+  a.split_from = from;
+  a.nsplit = ns;
+  return true;
+}
+
 cudaError_t run_pairs(gbi_ctx* ctx, int trunc, int rows, int cols, int precision, const PairArgs& args_in) {
   const double pairs = args_in.npairs > 0 ? double(args_in.npairs) : double(args_in.N) * double(args_in.N - 1);
   const double flops = pair_flops(trunc, rows, cols) * pairs;
@@ -250,6 +295,9 @@ cudaError_t run_pairs(gbi_ctx* ctx, int trunc, int rows, int cols, int precision
                                   : ctx->tuned_wpt(trunc, rows, cols, precision, args.N,
                                                    args.sys_of != nullptr && args.nsys > 1);
   tile_select(ctx, trunc, rows, precision, args);
+  if (precision >= 1 && !balanced_form(args.wpt) && !(args.sys_of != nullptr && args.nsys > 1) &&
+      ctx->split_tail)
+    split_reserve(ctx, trunc, rows, precision, args);
   if (precision == 2 || (precision == 1 && args.x32 == nullptr)) {
     // per-sphere source records (FP32, or the double-float hi/lo pair), once per pass,
     // so that the pair loop touches no FP64
@@ -450,6 +498,8 @@ PairArgs pair_args(const Setup& s, const double* x, double* y, double alpha, dou
   p.tile_P = p.tile_G = p.tile_maxseg = 0;
   p.err = nullptr;
   p.wait_limit = 0;
+  p.split_from = 0x7fffffff;
+  p.nsplit = 1;
   return p;
 }
 

@@ -82,6 +82,7 @@ struct gbi_ctx {
   // copy (training), padded bf16 copy (inference), gradient; neighbour lists; pair
   // features, outputs and training scratch
   gbi::Buf mlp_th, mlp_m, mlp_v, mlp_thq, mlp_pk, mlp_grad, mlp_pk_tc, mlp_err;
+  int split_tail = 0;                            // split the streaming pass's partly filled last wave
   int mlp_engine = 1;                            // inference: 0 mma.sync, 1 tcgen05
   int mlp_head = 0;                              // what the outputs are (mlpk::HEAD_*)
   double mlp_sigma = 0.0;
@@ -180,6 +181,10 @@ gbi_status tile_reserve(gbi_ctx* ctx, int trunc, int rows, int precision, int N,
 // plan and scratch of the balanced form a.wpt (tiled or chunk-balanced) for a pass over N
 // spheres, into a; false if the scratch cannot be had
 bool balanced_args(gbi_ctx* ctx, int trunc, int rows, int precision, int N, PairArgs& a);
+// the split of the streaming form's partly filled last wave (split_from, nsplit of
+// PairArgs) and its scratch in the context; false (and no split) if it does not pay or its
+// scratch cannot be had
+bool split_reserve(gbi_ctx* ctx, int trunc, int rows, int precision, PairArgs& a);
 cudaError_t run_trap(gbi_ctx* ctx, const TrapArgs& t, int precision);
 int d_of(int trunc);
 const double* scale_tab(int trunc);

@@ -190,7 +190,9 @@ gbi_status tune_impl(gbi_ctx* ctx, int trunc, int nsys, const int* offsets, int 
     for (const int w : cand) {
       if (e != cudaSuccess) break;
       pa.wpt = w;
+      pa.nsplit = 0;
       if (balanced_form(w) && !balanced_args(ctx, trunc, ps.rows, ps.precision, Ntot, pa)) continue;
+      if (!balanced_form(w) && !batched && ctx->split_tail) split_reserve(ctx, trunc, ps.rows, ps.precision, pa);
       e = launch_pairs(trunc, ps.rows, ps.cols, ps.precision, pa, ctx->stream);   // warm-up
       if (e == cudaSuccess) e = cudaEventRecord(e0, ctx->stream);
       for (int r = 0; r < reps && e == cudaSuccess; ++r)
@@ -627,6 +629,13 @@ gbi_status gbi_set_wpt(gbi_ctx* ctx, int wpt) {
   if (!ctx || !(wpt == 0 || wpt == 1 || wpt == 2 || wpt == 3 || wpt == 4 || wpt == 8 || wpt == 16)) return GBI_ERR_ARG;
   ctx->force_wpt = wpt;
   ++ctx->wpt_gen;
+  return GBI_OK;
+}
+
+gbi_status gbi_set_split_tail(gbi_ctx* ctx, int on) {
+  if (!ctx || (on != 0 && on != 1)) return GBI_ERR_ARG;
+  ctx->split_tail = on;
+  ++ctx->wpt_gen;   // captured solve graphs hold the old launches
   return GBI_OK;
 }
 

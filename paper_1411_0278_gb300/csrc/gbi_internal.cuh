@@ -75,6 +75,11 @@ struct PairArgs {
   int tile_P, tile_G, tile_maxseg;
   int* err;
   long long wait_limit;
+  // streaming form, single system: targets [split_from, N) (the last, partly filled wave of
+  // blocks) have their sources split over nsplit blocks each; each part writes its rows to
+  // tile_part (doubles, 32-row chunks) and the last to arrive (tile_cnt, one counter per
+  // split target, zero between launches) adds the parts in part order and stores
+  int split_from, nsplit;
 };
 
 // Programmatic dependent launch: with pdl set the kernel's blocks may be scheduled while

@@ -379,7 +379,10 @@ __global__ void __launch_bounds__(TPB * WPT * 32) pair_kernel(const PairArgs arg
 // One block per target sphere, WPT warps splitting its sources lane by lane: no
 // shared-memory tiles and no block barrier inside the loop.  The per-lane partial
 // sums are combined by a transposing warp reduction and then across the WPT warps in
-// shared memory, both in a fixed order, so the result does not depend on timing.
+// shared memory, both in a fixed order, so the result does not depend on timing.  For a
+// single system whose blocks do not fill whole waves, the targets of the last wave may be
+// split into nsplit blocks over their sources (PairArgs::split_from; off unless the caller
+// asks for it), added in part order.
 // ---------------------------------------------------------------------------------
 
 template <int NC> struct RecShape {
@@ -493,7 +496,14 @@ __global__ void __launch_bounds__(WPT * 32, MINB) pair_stream_kernel(const PairA
 
   pdl_wait();
   if (args.active != nullptr && *args.active == 0) return;   // device-side GMRES has stopped
-  const int n = blockIdx.x;
+  // block -> target n and, for the split tail, which part of its sources
+  int n = blockIdx.x, part = 0, nparts = 1;
+  if (args.nsplit > 1 && n >= args.split_from) {
+    const int t = n - args.split_from;
+    n = args.split_from + t / args.nsplit;
+    part = t - (n - args.split_from) * args.nsplit;
+    nparts = args.nsplit;
+  }
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   int src_lo = 0, src_hi = args.N;
@@ -513,6 +523,12 @@ __global__ void __launch_bounds__(WPT * 32, MINB) pair_stream_kernel(const PairA
   for (int p = 0; p < NR; ++p) acc[p] = T(0);
   float min_r2 = 3.0e38f;
 
+  if (nparts > 1) {
+    const int len = src_hi - src_lo;
+    const int lo = src_lo + (int)((long long)len * part / nparts);
+    src_hi = src_lo + (int)((long long)len * (part + 1) / nparts);
+    src_lo = lo;
+  }
   for (int m = src_lo + warp * 32 + lane; m < src_hi; m += WPT * 32) {
     if (m == n) continue;
     stream_source<TR, ROWS, COLS, T>(args, rec, th, tl, m, a, acc, min_r2);
@@ -537,6 +553,28 @@ __global__ void __launch_bounds__(WPT * 32, MINB) pair_stream_kernel(const PairA
       for (int w = 1; w < WPT; ++w) v += red[w][32 * c + lane];
       tot[c] = v;
     }
+  }
+  if (nparts > 1) {
+    // this part's rows; the last part of the target to arrive adds all parts in order
+    const int ts = n - args.split_from;
+    double* slots = static_cast<double*>(args.tile_part) + (size_t)ts * nparts * (NRC * 32);
+#pragma unroll
+    for (int c = 0; c < NRC; ++c) slots[(size_t)part * (NRC * 32) + 32 * c + lane] = gbi_to_double(tot[c]);
+    __threadfence();
+    unsigned int prev = 0;
+    if (lane == 0) prev = atomicAdd(args.tile_cnt + ts, 1u);
+    prev = __shfl_sync(0xffffffffu, prev, 0);
+    if (prev != (unsigned int)(nparts - 1)) return;
+    __threadfence();
+#pragma unroll
+    for (int c = 0; c < NRC; ++c) {
+      double v = 0.0;
+      for (int q = 0; q < nparts; ++q) v += __ldcg(slots + (size_t)q * (NRC * 32) + 32 * c + lane);
+      const int p = 32 * c + lane;
+      if (p < NR) store_target<TR, ROWS, COLS, T>(args, n, p, v);
+    }
+    if (lane == 0) args.tile_cnt[ts] = 0u;   // zero again for the next launch
+    return;
   }
 #pragma unroll
   for (int c = 0; c < NRC; ++c) {

@@ -81,7 +81,8 @@ cudaError_t launch_pairs_tt(int rows, int cols, const PairArgs& args, cudaStream
 #define GBI_S(RV, CV, WPT)                                                                         \
   if (rows == RV && cols == CV && wpt == WPT) {                                                    \
     constexpr int MINB = WARPS_SM / WPT > 0 ? WARPS_SM / WPT : 1;                                  \
-    return launch_pdl(args.pdl != 0, dim3(N), dim3(WPT * 32), stream,                              \
+    const int blocks = (args.nsplit > 1 && args.split_from < N) ? args.split_from + (N - args.split_from) * args.nsplit : N; \
+    return launch_pdl(args.pdl != 0, dim3(blocks), dim3(WPT * 32), stream,                         \
                       pair_stream_kernel<TRN, RV, CV, T, WPT, MINB>, args);                        \
   }
 #define GBI_SW(RV, CV) \

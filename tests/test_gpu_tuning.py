@@ -188,3 +188,51 @@ def test_tiled_form_full_size_sampled_rows(ctx, gbi, form):
     ref = galerkin.apply_offdiag(R, xf, c["a"], trunc, rows=slice(6, d), targets=tg)
     got = y.cpu().numpy()[:, tg].T
     assert relerr(got, ref) < 1e-5
+
+
+@pytest.mark.parametrize("trunc,N", [(2, 333), (3, 1024), (3, 700), (2, 1300), (4, 1024)])
+@pytest.mark.parametrize("precision", [1, 2])
+@pytest.mark.parametrize("wpt", [4, 8, 16])
+def test_split_tail_matches_unsplit(ctx, gbi, trunc, N, precision, wpt):
+    """The streaming form with the last, partly filled wave's targets split over several
+    blocks (the default) sums the same pairs as without the split; three launches in a
+    row (the arrival counters must be back at zero after each)."""
+    s = workloads.small_cloud(N, 40 + N, phi=0.05)
+    R = dev(s["R"])
+    d = tensors.ModeBasis(trunc).d
+    h = d - 6
+    x = dev(np.random.default_rng(N + wpt).normal(size=(h, N)))
+    ctx.set_wpt(wpt)
+    ctx.set_split_tail(0)
+    y_ref = torch.zeros((h, N), dtype=torch.float64, device="cuda")
+    ctx.apply(N, trunc, 1.0, 2, 2, precision, R, x, y_ref, 1.0, 0.0, True)
+    ctx.set_split_tail(1)
+    for _ in range(3):
+        y = torch.full((h, N), 7.0, dtype=torch.float64, device="cuda")
+        ctx.apply(N, trunc, 1.0, 2, 2, precision, R, x, y, 1.0, 0.0, True)
+        torch.cuda.synchronize()
+        assert relerr(y.cpu().numpy(), y_ref.cpu().numpy()) < (2e-6 if precision == 1 else 1e-12)
+    ctx.set_wpt(0)
+
+
+@pytest.mark.parametrize("precision,tol", [(1, 1e-5), (2, 1e-11)])
+def test_split_tail_full_size_sampled_rows(ctx, gbi, precision, tol):
+    """N = 1024 at l <= 3 with 4 warps per target (608 resident blocks: the last 416 targets
+    split), against the oracle's dense pair blocks for sampled targets of both waves."""
+    c = workloads.config2()
+    R = c["R"]
+    N, trunc = len(R), 3
+    d = tensors.ModeBasis(trunc).d
+    h = d - 6
+    x = np.random.default_rng(6).normal(size=(h, N))
+    ctx.set_wpt(4)
+    y = torch.zeros((h, N), dtype=torch.float64, device="cuda")
+    ctx.apply(N, trunc, c["a"], 2, 2, precision, dev(R), dev(x), y, 1.0, 0.0, False)
+    torch.cuda.synchronize()
+    ctx.set_wpt(0)
+    tg = np.array([0, 300, 607, 608, 609, 900, 1023])
+    xf = np.zeros((N, d))
+    xf[:, 6:] = x.T
+    ref = galerkin.apply_offdiag(R, xf, c["a"], trunc, rows=slice(6, d), targets=tg)
+    got = y.cpu().numpy()[:, tg].T
+    assert relerr(got, ref) < tol
