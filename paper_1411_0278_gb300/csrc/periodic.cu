@@ -223,14 +223,22 @@ template <typename T>
 __device__ __forceinline__ void per_real_term(T dx, T dy, T dz, T rc2, T xi, const T* f, T* u, T* uc) {
   const T r2 = dx * dx + dy * dy + dz * dz;
   if (!(r2 < rc2)) return;
-  const T r = sqrt(r2);
+  T r, rinv;
+  if constexpr (std::is_same<T, float>::value) {
+    rinv = rsqrtf(r2);   // one reciprocal square root for r, 1/r and 1/r^2
+    r = r2 * rinv;
+  } else {
+    r = sqrt(r2);
+    rinv = T(1) / r;
+  }
   const T xr = xi * r;
   const T e = per_exp(-xr * xr);
   const T c = T(2.0 / kSqrtPi) * xi;
   const T f1 = per_erfc(xr) - c * r * e;
   const T f2 = T(2) * c * (xr * xr - T(1)) * e;
-  const T a = f2 + f1 / r;
-  const T b = (f2 - f1 / r) / r2;
+  const T f1r = f1 * rinv;
+  const T a = f2 + f1r;
+  const T b = (f2 - f1r) * (rinv * rinv);
   const T dF = dx * f[0] + dy * f[1] + dz * f[2];
   per_add(u[0], uc[0], a * f[0] - b * dF * dx);
   per_add(u[1], uc[1], a * f[1] - b * dF * dy);
@@ -362,14 +370,15 @@ __global__ void __launch_bounds__(kPerCellThreads)
       const int ni = (n - quarter + kPerCellQuarters - 1) / kPerCellQuarters;   // j = quarter + 4 i
       for (int ib = 0; ib < ni; ib += 32) {
         unsigned int mask = 0u;
+        // the cut-off test on the high parts alone (a pair it misjudges sits at r_c, where
+        // its term is erfc(xi r_c) ~ 3e-9 of a near pair's); the target itself gives r2 = 0
 #pragma unroll
         for (int bit = 0; bit < 32; ++bit) {
           const int i = ib + bit;
           if (i < ni) {
             const int j = quarter + kPerCellQuarters * i;
-            const Q4 qa = sa[j], qb = sb[j];
-            T v0 = (pn[0] - qa.x) + (pn[4] - qb.x), v1 = (pn[1] - qa.y) + (pn[5] - qb.y),
-              v2 = (pn[2] - qa.z) + (pn[6] - qb.z);
+            const Q4 qa = sa[j];
+            T v0 = pn[0] - qa.x, v1 = pn[1] - qa.y, v2 = pn[2] - qa.z;
             v0 = (v0 - per_rint(v0)) * Lt;
             v1 = (v1 - per_rint(v1)) * Lt;
             v2 = (v2 - per_rint(v2)) * Lt;
@@ -629,76 +638,131 @@ __global__ void k_pme_spread(int N, int K, const double* __restrict__ R, double 
   }
 }
 
-// the most elements (LB K) an FFT block holds: rows of at most 36 KB
+// the most elements (LB K) an FFT block holds
 template <typename G> __host__ __device__ constexpr int pme_max_line_elems() { return sizeof(G) == 4 ? 4096 : 2048; }
 
-// One Stockham pass of radix R = 2^logR (4 or 2) over the LB = 2^logLB rows of the block
-// (rows of K = 2^logK complex values, padded to K + 1): with Ns = 2^logNs the length of the
-// sub-transforms done so far, butterfly j of a row takes x[j + r K / R] times
-// e^{-+2 pi i r k / (Ns R)}, k = j mod Ns, does an R-point DFT and stores output q at
-// (j - k) R + k + q Ns.  Inputs are held in registers across a barrier, so the pass works
-// in place.  twf[t] = e^{-+2 pi i t / K} (conjugated for the inverse).  At most LB K / R
-// butterflies per block (LB K <= 4096 in FP32, 2048 in FP64).  Every index is a shift.
-template <typename G, int logR>
-__device__ __forceinline__ void pme_fft_pass(typename Cplx<G>::t* sx, const typename Cplx<G>::t* twf, int logK,
-                                             int logLB, int logNs, bool inverse) {
-  using C = typename Cplx<G>::t;
-  constexpr int R = 1 << logR;
-  constexpr int kMaxB = pme_max_line_elems<G>() / R / kPmeFftThreads;
-  const int logKR = logK - logR;
-  const unsigned int nb = 1u << (logLB + logKR);
-  const unsigned int jmask = (1u << logKR) - 1u, kmask = (1u << logNs) - 1u;
-  const int twsh = logK - logNs - logR;
-  const unsigned int stride = (1u << logK) + 1u;
-  C v[kMaxB][R];
+// ---- line FFT: four steps (K = 16 N2, N2 in {1, 2, 4, 8, 16, 32}) --------------------
+//
+// x[N2 n1 + n2] -> X[k1 + 16 k2] = sum_n2 e^{-+2 pi i n2 k2 / N2} [e^{-+2 pi i n2 k1 / K}
+// sum_n1 x[N2 n1 + n2] e^{-+2 pi i n1 k1 / 16}]: a 16-point DFT per n2 in registers (reading
+// and writing the same 16 elements, so no barrier), the twiddles, then an N2-point DFT per
+// k1 in registers.  Rows are padded by one element after every 16 (pme_pad) so that both
+// the strided and the contiguous register loads avoid bank conflicts.
+
+// e^{2 pi i k / 32}: cos and sin of k pi / 16, k = 0..15
+__device__ __forceinline__ constexpr double pme_c32(int k) {
+  constexpr double c[16] = {1.0,
+                            0.98078528040323043,
+                            0.92387953251128674,
+                            0.83146961230254524,
+                            0.70710678118654752,
+                            0.55557023301960218,
+                            0.38268343236508977,
+                            0.19509032201612826,
+                            0.0,
+                            -0.19509032201612826,
+                            -0.38268343236508977,
+                            -0.55557023301960218,
+                            -0.70710678118654752,
+                            -0.83146961230254524,
+                            -0.92387953251128674,
+                            -0.98078528040323043};
+  return c[k];
+}
+__device__ __forceinline__ constexpr double pme_s32(int k) { return pme_c32(k >= 8 ? k - 8 : 8 - k); }
+
+__host__ __device__ constexpr int pme_log2(int n) { return n <= 1 ? 0 : 1 + pme_log2(n >> 1); }
+
+// In-register DFT of N (<= 32) values, natural order in and out, e^{-2 pi i j k / N}
+// (forward) or e^{+2 pi i j k / N} (INV): radix-2 Stockham passes between two register
+// arrays (no permutation), every index a compile-time constant after unrolling.  With Ns
+// the length done so far, butterfly j takes a[j] and a[j + N/2] e^{-+2 pi i k / (2 Ns)},
+// k = j mod Ns, and writes outputs (j - k) 2 + k and that + Ns.
+template <typename C, int N, bool INV>
+__device__ __forceinline__ void pme_reg_fft(C* v) {
+  using G = decltype(v[0].x);
+  if constexpr (N > 1) {
+    C a[N], b[N];
 #pragma unroll
-  for (int b = 0; b < kMaxB; ++b) {
-    const unsigned int t = threadIdx.x + b * kPmeFftThreads;
-    if (t < nb) {
-      const unsigned int lane = t >> logKR, j = t & jmask;
-      const unsigned int tstep = (j & kmask) << twsh;
-      const C* row = sx + lane * stride;
+    for (int i = 0; i < N; ++i) a[i] = v[i];
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const C x = row[j + ((unsigned)r << logKR)];
-        const C w = twf[r * tstep];
-        v[b][r] = C{w.x * x.x - w.y * x.y, w.x * x.y + w.y * x.x};
+    for (int Ns = 1; Ns < N; Ns <<= 1) {
+#pragma unroll
+      for (int j = 0; j < N / 2; ++j) {
+        const int k = j & (Ns - 1);
+        const int t = k * (16 / Ns);   // e^{-+2 pi i k / (2 Ns)} = e^{-+2 pi i t / 32}
+        const G wc = G(pme_c32(t)), ws = INV ? G(pme_s32(t)) : G(-pme_s32(t));
+        const C x0 = a[j], y = a[j + N / 2];
+        const G x1r = wc * y.x - ws * y.y, x1i = wc * y.y + ws * y.x;
+        const int o = (j - k) * 2 + k;
+        b[o] = C{x0.x + x1r, x0.y + x1i};
+        b[o + Ns] = C{x0.x - x1r, x0.y - x1i};
       }
+#pragma unroll
+      for (int i = 0; i < N; ++i) a[i] = b[i];
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i) v[i] = a[i];
+  }
+}
+
+__host__ __device__ constexpr int pme_pad(int i) { return i + (i >> 4); }
+__host__ __device__ constexpr int pme_row(int K) { return K + K / 16 + 1; }
+
+// The four-step transform of LB padded rows of K = 16 N2 values in shared memory (twf the
+// K twiddles e^{-+2 pi i t / K}, conjugated for the inverse); barriers inside.
+template <typename G, int N2, bool INV>
+__device__ __forceinline__ void pme_fft4_rows(typename Cplx<G>::t* sx, const typename Cplx<G>::t* twf, int LB) {
+  using C = typename Cplx<G>::t;
+  constexpr int K = 16 * N2, RS = pme_row(K);
+  // stage 1: task (row, n2)
+  for (int task = threadIdx.x; task < LB * N2; task += blockDim.x) {
+    const int lane = task / N2, n2 = task - lane * N2;
+    C* row = sx + lane * RS;
+    C v[16];
+#pragma unroll
+    for (int n1 = 0; n1 < 16; ++n1) v[n1] = row[pme_pad(N2 * n1 + n2)];
+    pme_reg_fft<C, 16, INV>(v);
+#pragma unroll
+    for (int k1 = 1; k1 < 16; ++k1) {
+      const C w = twf[n2 * k1];
+      const C a = v[k1];
+      v[k1] = C{w.x * a.x - w.y * a.y, w.x * a.y + w.y * a.x};
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < 16; ++k1) row[pme_pad(N2 * k1 + n2)] = v[k1];
+  }
+  __syncthreads();
+  // stage 2: task (row, k1), read everything before anything is written
+  constexpr int kT = (16 * 4096 / K + kPmeFftThreads - 1) / kPmeFftThreads;   // tasks per thread at most
+  C u[kT][N2];
+#pragma unroll
+  for (int t = 0; t < kT; ++t) {
+    const int task = threadIdx.x + t * kPmeFftThreads;
+    if (task < LB * 16) {
+      const int lane = task >> 4, k1 = task & 15;
+      const C* row = sx + lane * RS;
+#pragma unroll
+      for (int n2 = 0; n2 < N2; ++n2) u[t][n2] = row[pme_pad(N2 * k1 + n2)];
+      pme_reg_fft<C, N2, INV>(u[t]);
     }
   }
   __syncthreads();
 #pragma unroll
-  for (int b = 0; b < kMaxB; ++b) {
-    const unsigned int t = threadIdx.x + b * kPmeFftThreads;
-    if (t < nb) {
-      const unsigned int lane = t >> logKR, j = t & jmask;
-      const unsigned int k = j & kmask;
-      C* row = sx + lane * stride;
-      const unsigned int base = ((j - k) << logR) + k;
-      const unsigned int Ns = 1u << logNs;
-      if (R == 2) {
-        const C a0 = v[b][0], a1 = v[b][1];
-        row[base] = C{a0.x + a1.x, a0.y + a1.y};
-        row[base + Ns] = C{a0.x - a1.x, a0.y - a1.y};
-      } else {
-        // 4-point DFT; forward multiplies (b - d) by -i, the inverse by +i
-        const C a = v[b][0], bb = v[b][1], c = v[b][2 % R], d = v[b][3 % R];
-        const C s0 = C{a.x + c.x, a.y + c.y}, s1 = C{a.x - c.x, a.y - c.y};
-        const C s2 = C{bb.x + d.x, bb.y + d.y}, s3 = C{bb.x - d.x, bb.y - d.y};
-        const C s3i = inverse ? C{-s3.y, s3.x} : C{s3.y, -s3.x};   // +-i (b - d)
-        row[base] = C{s0.x + s2.x, s0.y + s2.y};
-        row[base + Ns] = C{s1.x + s3i.x, s1.y + s3i.y};
-        row[base + 2 * Ns] = C{s0.x - s2.x, s0.y - s2.y};
-        row[base + 3 * Ns] = C{s1.x - s3i.x, s1.y - s3i.y};
-      }
+  for (int t = 0; t < kT; ++t) {
+    const int task = threadIdx.x + t * kPmeFftThreads;
+    if (task < LB * 16) {
+      const int lane = task >> 4, k1 = task & 15;
+      C* row = sx + lane * RS;
+#pragma unroll
+      for (int k2 = 0; k2 < N2; ++k2) row[pme_pad(k1 + 16 * k2)] = u[t][k2];
     }
   }
   __syncthreads();
 }
 
-// In-place FFT of the K-point lines of one axis (K a power of 2, 16 <= K <= 512),
-// unnormalised, e^{-2 pi i m g / K} (forward) or e^{+2 pi i m g / K} (inverse), natural
-// order in and out: Stockham passes of radix 4 (one of radix 2 first when log2 K is odd).
+// In-place FFT of the K-point lines of one axis (K = 16 N2 <= 512), unnormalised,
+// e^{-2 pi i m g / K} (forward) or e^{+2 pi i m g / K} (inverse), natural order in and out.
 // The K^2 lines of a grid are numbered l = a + K b over the two other axes; line l holds
 //   axis 0: K l + i,   axis 1: a + K^2 b + K i,   axis 2: l + K^2 i   (i = 0..K-1).
 // A block transforms LB = 2^logLB consecutive lines (LB | K, LB K <= 4096 in FP32, 2048 in
@@ -706,42 +770,40 @@ __device__ __forceinline__ void pme_fft_pass(typename Cplx<G>::t* sx, const type
 // those loads coalesce in runs of LB elements.  grids = A (blockIdx.y = 0) and B (1); with
 // src the lines are read from the staging points instead (A = x + i y, B = z).
 // tw[t] = e^{-2 pi i t / K}, t < K.  Indices are 32-bit (K^3 <= 2^27).
-template <typename G>
+template <typename G, int N2>
 __global__ void __launch_bounds__(kPmeFftThreads)
-    k_pme_fft(typename Cplx<G>::t* __restrict__ grids, const typename Cplx<G>::q* __restrict__ src, int logK,
-              int logLB, int axis, int inverse, const typename Cplx<G>::t* __restrict__ tw) {
+    k_pme_fft4(typename Cplx<G>::t* __restrict__ grids, const typename Cplx<G>::q* __restrict__ src, int logLB,
+               int axis, int inverse, const typename Cplx<G>::t* __restrict__ tw) {
   using C = typename Cplx<G>::t;
+  constexpr int K = 16 * N2, RS = pme_row(K), logK = pme_log2(K);
   extern __shared__ __align__(16) unsigned char pme_smem[];
-  const unsigned int K = 1u << logK, stride = K + 1u;
   C* sx = reinterpret_cast<C*>(pme_smem);
-  C* stw = sx + (stride << logLB);
-  const unsigned int goff = blockIdx.y << (3 * logK);
-  C* g = grids + goff;
-  const typename Cplx<G>::q* sq = src ? src : nullptr;
+  const int LB = 1 << logLB;
+  C* stw = sx + (size_t)LB * RS;
+  const unsigned int K2 = (unsigned)K * K;
+  C* g = grids + (size_t)blockIdx.y * K2 * K;
   const unsigned int l0 = blockIdx.x << logLB;
-  const unsigned int tot = 1u << (logLB + logK);
-  for (unsigned int j = threadIdx.x; j < K; j += blockDim.x) {
+  const unsigned int tot = (unsigned)LB * K;
+  for (unsigned int j = threadIdx.x; j < (unsigned)K; j += blockDim.x) {
     C w = tw[j];
     if (inverse) w.y = -w.y;
     stw[j] = w;
   }
-  // element e of the block: its row (lane), position i and grid index
-  auto at = [&](unsigned int e, unsigned int& sidx) -> unsigned int {
+  auto at = [&](unsigned int e, unsigned int& si) -> unsigned int {
     unsigned int lane, i;
     if (axis == 0) {
       lane = e >> logK;
       i = e & (K - 1u);
-      sidx = lane * stride + i;
+      si = lane * RS + pme_pad((int)i);
       return ((l0 + lane) << logK) + i;
     }
-    lane = e & ((1u << logLB) - 1u);
+    lane = e & ((unsigned)LB - 1u);
     i = e >> logLB;
-    sidx = lane * stride + i;
+    si = lane * RS + pme_pad((int)i);
     const unsigned int l = l0 + lane;
     if (axis == 1) return (l & (K - 1u)) + ((l >> logK) << (2 * logK)) + (i << logK);
     return l + (i << (2 * logK));
   };
-  // every load of the thread issued before the first store
   constexpr int kMaxE = pme_max_line_elems<G>() / kPmeFftThreads;
   C v[kMaxE];
 #pragma unroll
@@ -750,8 +812,8 @@ __global__ void __launch_bounds__(kPmeFftThreads)
     if (e < tot) {
       unsigned int si;
       const unsigned int ad = at(e, si);
-      if (sq) {
-        const typename Cplx<G>::q q = sq[ad];
+      if (src) {
+        const typename Cplx<G>::q q = src[ad];
         v[k] = blockIdx.y == 0 ? C{q.x, q.y} : C{q.z, G(0)};
       } else {
         v[k] = g[ad];
@@ -768,12 +830,10 @@ __global__ void __launch_bounds__(kPmeFftThreads)
     }
   }
   __syncthreads();
-  int logNs = 0;
-  if (logK & 1) {
-    pme_fft_pass<G, 1>(sx, stw, logK, logLB, logNs, inverse != 0);
-    logNs = 1;
-  }
-  for (; logNs < logK; logNs += 2) pme_fft_pass<G, 2>(sx, stw, logK, logLB, logNs, inverse != 0);
+  if (inverse)
+    pme_fft4_rows<G, N2, true>(sx, stw, LB);
+  else
+    pme_fft4_rows<G, N2, false>(sx, stw, LB);
 #pragma unroll
   for (int k = 0; k < kMaxE; ++k) {
     const unsigned int e = threadIdx.x + k * kPmeFftThreads;
@@ -798,16 +858,18 @@ __global__ void __launch_bounds__(kPmeFftThreads)
 //        = 8 pi (I - k k / k^2) / k^2 (1 + q + 2 q^2) e^{-q} |b|^2 / L^3  (T(0) = 0: zero mean flow),
 // A(m) = U_x + i U_y, B(m) = U_z (the mirror -m lies in the mirror row at (K - i) mod K), then
 // transforms back along x and stores the rows it owns.  bmod[i] = |b_i|^2 of one axis.
-template <typename G>
+template <typename G, int N2>
 __global__ void __launch_bounds__(kPmeFftThreads)
-    k_pme_xconv(typename Cplx<G>::t* __restrict__ A, typename Cplx<G>::t* __restrict__ B, int logK, int logP,
-                double L, double xi, const G* __restrict__ bmod, const typename Cplx<G>::t* __restrict__ tw) {
+    k_pme_xconv(typename Cplx<G>::t* __restrict__ A, typename Cplx<G>::t* __restrict__ B, int logP, double L,
+                double xi, const G* __restrict__ bmod, const typename Cplx<G>::t* __restrict__ tw) {
   using C = typename Cplx<G>::t;
   extern __shared__ __align__(16) unsigned char pme_smem[];
-  const unsigned int K = 1u << logK, mask = K - 1u, stride = K + 1u, P = 1u << logP;
+  constexpr int RS = pme_row(16 * N2), logK = pme_log2(16 * N2);
+  const unsigned int K = 16u * N2, mask = K - 1u, P = 1u << logP;
   const int logLB = logP + 2;   // rows: A own, A mirror, B own, B mirror
+  const int LB = 1 << logLB;
   C* sx = reinterpret_cast<C*>(pme_smem);
-  C* stw = sx + (stride << logLB);
+  C* stw = sx + (size_t)LB * RS;
   const unsigned int r0 = blockIdx.x << logP;
   const unsigned int z = r0 >> logK, nz = (K - z) & mask;
   if (nz < z) return;   // the whole block's rows are mirrors of rows done elsewhere
@@ -837,15 +899,10 @@ __global__ void __launch_bounds__(kPmeFftThreads)
 #pragma unroll
   for (int k = 0; k < kMaxE; ++k) {
     const unsigned int e = threadIdx.x + k * kPmeFftThreads;
-    if (e < tot) sx[(e >> logK) * stride + (e & mask)] = v[k];
+    if (e < tot) sx[(e >> logK) * RS + pme_pad((int)(e & mask))] = v[k];
   }
   __syncthreads();
-  int logNs = 0;
-  if (logK & 1) {
-    pme_fft_pass<G, 1>(sx, stw, logK, logLB, logNs, false);
-    logNs = 1;
-  }
-  for (; logNs < logK; logNs += 2) pme_fft_pass<G, 2>(sx, stw, logK, logLB, logNs, false);
+  pme_fft4_rows<G, N2, false>(sx, stw, LB);
   // the products: element e of the A rows (own and mirror) and the same element of B
   const G s = G(2.0 * kPi / L);
   const G c0 = G(8.0 * kPi / (L * L * L)), cq = G(0.25 / (xi * xi));
@@ -862,7 +919,8 @@ __global__ void __launch_bounds__(kPmeFftThreads)
       const unsigned int iy = row & mask, iz = row >> logK;
       const unsigned int qm = mir ? sl : sl + P;   // the paired row in shared memory
       const unsigned int nx = (K - ix) & mask;
-      const C a = sx[q * stride + ix], an = sx[qm * stride + nx], b = sx[(q + 2u * P) * stride + ix];
+      const C a = sx[q * RS + pme_pad((int)ix)], an = sx[qm * RS + pme_pad((int)nx)],
+              b = sx[(q + 2u * P) * RS + pme_pad((int)ix)];
       if (row == 0u && ix == 0u) {
         ua[k] = C{G(0), G(0)};
         ub[k] = C{G(0), G(0)};
@@ -893,19 +951,14 @@ __global__ void __launch_bounds__(kPmeFftThreads)
     const unsigned int e = threadIdx.x + k * kPmeFftThreads;
     if (e < ntot) {
       const unsigned int q = e >> logK, ix = e & mask;
-      sx[q * stride + ix] = ua[k];
-      sx[(q + 2u * P) * stride + ix] = ub[k];
+      sx[q * RS + pme_pad((int)ix)] = ua[k];
+      sx[(q + 2u * P) * RS + pme_pad((int)ix)] = ub[k];
     }
   }
   __syncthreads();
   for (unsigned int j = threadIdx.x; j < K; j += blockDim.x) stw[j].y = -stw[j].y;   // the inverse's twiddles
   __syncthreads();
-  logNs = 0;
-  if (logK & 1) {
-    pme_fft_pass<G, 1>(sx, stw, logK, logLB, logNs, true);
-    logNs = 1;
-  }
-  for (; logNs < logK; logNs += 2) pme_fft_pass<G, 2>(sx, stw, logK, logLB, logNs, true);
+  pme_fft4_rows<G, N2, true>(sx, stw, LB);
   // store the rows this block owns: own rows of active slots, mirror rows of active slots
   // that are not their own mirror
 #pragma unroll
@@ -915,7 +968,8 @@ __global__ void __launch_bounds__(kPmeFftThreads)
       const unsigned int q = e >> logK;
       const unsigned int sl = q & (P - 1u);
       const bool mir = ((q >> logP) & 1u) != 0u;
-      if (active(sl) && !(mir && mir_row(sl) == own_row(sl))) row_base(q)[e & mask] = sx[q * stride + (e & mask)];
+      if (active(sl) && !(mir && mir_row(sl) == own_row(sl)))
+        row_base(q)[e & mask] = sx[q * RS + pme_pad((int)(e & mask))];
     }
   }
 }
@@ -999,11 +1053,12 @@ std::vector<double> pme_bmod(int K) {
   return out;
 }
 
-// lines per FFT block: at most 36 KB of rows (plus K twiddles), at most 32, dividing K,
-// LB K <= 4096 (the butterflies a pass holds in registers)
+// lines per FFT block: at most 36 KB of padded rows (plus K twiddles), at most 32, at least
+// 4 (the fused x kernel's row quartets), dividing K, LB K within the elements a block holds
 int pme_lines_per_block(int K, size_t elem) {
+  const int cap = elem == sizeof(float2) ? 4096 : 2048;
   int lb = 1;
-  while (lb < 32 && lb * 2 <= K && (size_t)(lb * 2) * (K + 1) * elem <= 36864 && lb * 2 * K <= 4096) lb *= 2;
+  while (lb < 32 && lb * 2 <= K && (size_t)(lb * 2) * pme_row(K) * elem <= 36864 && lb * 2 * K <= cap) lb *= 2;
   return lb;
 }
 
@@ -1129,16 +1184,31 @@ gbi_status run_periodic(gbi_ctx* ctx, int N, double L, double a, double eta, con
     int logLB = 0;
     while ((1 << logLB) < LB) ++logLB;
     const dim3 lines((unsigned)((size_t)K * K / LB), 2);
-    const size_t fsm = sizeof(C) * ((size_t)LB * (K + 1) + K);
+    const size_t fsm = sizeof(C) * ((size_t)LB * pme_row(K) + K);
     // forward along z (from the staging points) and y, then x with the products and x back,
     // then y and z back
-    k_pme_fft<G><<<lines, kPmeFftThreads, fsm, ctx->stream>>>(A, Qs, logK, logLB, 2, 0, twd);
-    k_pme_fft<G><<<lines, kPmeFftThreads, fsm, ctx->stream>>>(A, nullptr, logK, logLB, 1, 0, twd);
     const int logP = logLB - 2;   // 4 P rows = LB rows in shared memory
-    k_pme_xconv<G><<<(unsigned)((size_t)K * K >> logP), kPmeFftThreads, fsm, ctx->stream>>>(A, B, logK, logP, L, p.xi,
-                                                                                              bmd, twd);
-    k_pme_fft<G><<<lines, kPmeFftThreads, fsm, ctx->stream>>>(A, nullptr, logK, logLB, 1, 1, twd);
-    k_pme_fft<G><<<lines, kPmeFftThreads, fsm, ctx->stream>>>(A, nullptr, logK, logLB, 2, 1, twd);
+    const unsigned xblocks = (unsigned)((size_t)K * K >> logP);
+    cudaError_t e = cudaSuccess;
+    switch (K / 16) {
+#define GBI_PME_FFT(N2)                                                                                     \
+  case N2:                                                                                                  \
+    k_pme_fft4<G, N2><<<lines, kPmeFftThreads, fsm, ctx->stream>>>(A, Qs, logLB, 2, 0, twd);                \
+    k_pme_fft4<G, N2><<<lines, kPmeFftThreads, fsm, ctx->stream>>>(A, nullptr, logLB, 1, 0, twd);           \
+    k_pme_xconv<G, N2><<<xblocks, kPmeFftThreads, fsm, ctx->stream>>>(A, B, logP, L, p.xi, bmd, twd);       \
+    k_pme_fft4<G, N2><<<lines, kPmeFftThreads, fsm, ctx->stream>>>(A, nullptr, logLB, 1, 1, twd);           \
+    k_pme_fft4<G, N2><<<lines, kPmeFftThreads, fsm, ctx->stream>>>(A, nullptr, logLB, 2, 1, twd);           \
+    break;
+      GBI_PME_FFT(1)
+      GBI_PME_FFT(2)
+      GBI_PME_FFT(4)
+      GBI_PME_FFT(8)
+      GBI_PME_FFT(16)
+      GBI_PME_FFT(32)
+#undef GBI_PME_FFT
+      default: e = cudaErrorInvalidValue;
+    }
+    GBI_CHECK(e);
     k_pme_gather<G, T><<<lane_blocks, 128, 0, ctx->stream>>>(N, K, R, L, Fe, sidx, A, B, p.xi, a, eta, ur, Va, V);
     ctx->launches += 7;
   }

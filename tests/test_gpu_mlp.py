@@ -116,6 +116,10 @@ def test_tensor_core_forward_matches_oracle(ctx, gbi, P, engine):
     ref, _ = omlp.forward(th.astype(np.float64), Fo.astype(np.float32).astype(np.float64), bf16=True)
     scale = np.abs(ref).max()
     assert np.abs(out - ref).max() <= 1e-2 * scale
+    if P >= 64:
+        # the bulk of the outputs much closer, and no systematic offset
+        assert np.median(np.abs(out - ref)) <= 3e-3 * scale
+        assert np.abs(np.mean(out - ref, axis=0)).max() <= 1e-3 * scale
     lab = ctx.mlp_forward(Fd, dev(FRo.reshape(-1, 9), torch.float32)).cpu().numpy()
     np.testing.assert_allclose(lab, omlp.rotate_out(ref, FRo), atol=1e-2 * scale, rtol=0)
     ctx.mlp_status()
