@@ -771,7 +771,7 @@ __device__ __forceinline__ void pme_fft4_rows(typename Cplx<G>::t* sx, const typ
 // src the lines are read from the staging points instead (A = x + i y, B = z).
 // tw[t] = e^{-2 pi i t / K}, t < K.  Indices are 32-bit (K^3 <= 2^27).
 template <typename G, int N2>
-__global__ void __launch_bounds__(kPmeFftThreads)
+__global__ void __launch_bounds__(kPmeFftThreads, (sizeof(G) == 4 && N2 >= 16) ? 3 : 1)
     k_pme_fft4(typename Cplx<G>::t* __restrict__ grids, const typename Cplx<G>::q* __restrict__ src, int logLB,
                int axis, int inverse, const typename Cplx<G>::t* __restrict__ tw) {
   using C = typename Cplx<G>::t;
