@@ -158,7 +158,7 @@ struct TrapArgs {
 // hold trap_scratch_bytes(N, precision) bytes, 256-byte aligned.
 cudaError_t launch_trap(const TrapArgs& args, int precision, void* scratch, cudaStream_t stream);
 size_t trap_scratch_bytes(int N, int precision);
-int trap_splits(int N);
+int trap_splits(int N, int precision);
 
 // Learned near-field correction (mlp_kernel.cu).  Layout and definitions: gbi.h.
 namespace mlpk {

@@ -136,6 +136,147 @@ __device__ __forceinline__ void trap_source(const T* __restrict__ s_rec, int j, 
   }
 }
 
+// Two FP32 values per instruction (the paired FFMA2 / FMUL2 / FADD2 of sm_100 and later).
+// Each element is rounded exactly as the scalar operation rounds it, so the paired pass
+// gives the scalar pass's results bit for bit; it halves the issued FP32 instructions,
+// not the FMA pipe's work (a paired FMA occupies the pipe for two lanes' worth).
+struct f2 {
+  float2 v;
+  __device__ __forceinline__ f2() {}
+  __device__ __forceinline__ explicit f2(float s) : v(make_float2(s, s)) {}
+  __device__ __forceinline__ f2(float a, float b) : v(make_float2(a, b)) {}
+  __device__ __forceinline__ explicit f2(float2 p) : v(p) {}
+};
+__device__ __forceinline__ f2 operator+(f2 a, f2 b) { return f2(__fadd2_rn(a.v, b.v)); }
+__device__ __forceinline__ f2 operator*(f2 a, f2 b) { return f2(__fmul2_rn(a.v, b.v)); }
+__device__ __forceinline__ f2 operator-(f2 a) { return f2(-a.v.x, -a.v.y); }
+__device__ __forceinline__ f2 operator-(f2 a, f2 b) { return a + (-b); }
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return f2(__ffma2_rn(a.v, b.v, c.v)); }
+__device__ __forceinline__ f2 rsqrt2(f2 a) { return f2(rsqrtf(a.v.x), rsqrtf(a.v.y)); }
+
+// trap_source for FP32 targets taken two at a time: pair g holds targets n0 + 2g (x) and
+// n0 + 2g + 1 (y).  The source record sits in shared memory with every word duplicated
+// ((w, w) pairs), so each 16-byte load yields two broadcast operands.  The operations and
+// their order per element are those of trap_source.  SELF: the tile may hold one of the
+// thread's targets.  Its rho is exactly zero (same position words), so with 1/r set to 0
+// for that lane every one of its terms is a product with 0 and its sums do not change.
+template <int TG, bool SELF>
+__device__ __forceinline__ void trap_source_f2(const float4* __restrict__ s_dup, int j, int m, int n0, const f2* px, const f2* py,
+                                               const f2* pz, const f2* lx, const f2* ly, const f2* lz, f2 a2,
+                                               f2* v0, f2* v1, f2* v2, f2* w0, f2* w1, f2* w2) {
+  const float4* r4 = s_dup + j * (kRec / 2);
+  f2 q[kRec];
+#pragma unroll
+  for (int i = 0; i < kRec / 2; ++i) {
+    const float4 w = r4[i];
+    q[2 * i] = f2(w.x, w.y);
+    q[2 * i + 1] = f2(w.z, w.w);
+  }
+  const f2 sx = q[0], sy = q[1], sz = q[2], slx = q[3], sly = q[4], slz = q[5];
+  const f2 Fx = q[6], Fy = q[7], Fz = q[8];
+  const f2 Tx = q[9], Ty = q[10], Tz = q[11];
+  const f2 Sxx = q[12], Sxy = q[13], Sxz = q[14], Syy = q[15], Syz = q[16], Szz = q[17];
+  const f2 dx = q[18], dy = q[19], dz = q[20];
+  const f2 hx = q[21], hy = q[22], hz = q[23];
+  const f2 c23 = f2(2.0f / 3.0f) * a2, c2a = f2(-2.0f) * a2, c8a = f2(8.0f) * a2, c165 = f2(-16.0f / 5.0f) * a2;
+#pragma unroll
+  for (int g = 0; g < TG; ++g) {
+    const f2 x = (px[g] - sx) + (lx[g] - slx);
+    const f2 y = (py[g] - sy) + (ly[g] - sly);
+    const f2 z = (pz[g] - sz) + (lz[g] - slz);
+    const f2 r2 = fma2(z, z, fma2(y, y, x * x));
+    f2 ri = rsqrt2(r2);
+    if (SELF) {
+      if (m == n0 + 2 * g) ri.v.x = 0.0f;
+      if (m == n0 + 2 * g + 1) ri.v.y = 0.0f;
+    }
+    const f2 ri2 = ri * ri, ri3 = ri * ri2, ri5 = ri3 * ri2, ri7 = ri5 * ri2;
+    const f2 rF = fma2(z, Fz, fma2(y, Fy, x * Fx));
+    const f2 Sx = fma2(Sxz, z, fma2(Sxy, y, Sxx * x));
+    const f2 Sy = fma2(Syz, z, fma2(Syy, y, Sxy * x));
+    const f2 Sz = fma2(Szz, z, fma2(Syz, y, Sxz * x));
+    const f2 rSr = fma2(z, Sz, fma2(y, Sy, x * Sx));
+    const f2 rd = fma2(z, dz, fma2(y, dy, x * dx));
+    const f2 rT = fma2(z, Tz, fma2(y, Ty, x * Tx));
+    const f2 c1 = fma2(c23, ri3, ri);
+    const f2 t3 = f2(3.0f) * ri5;
+    const f2 cx = fma2(fma2(c2a, ri5, ri3), rF, fma2(fma2(c8a, ri7, -t3), rSr, t3 * rd));
+    const f2 cs2 = c165 * ri5;
+    const f2 u0 = fma2(Ty, z, fma2(-Tz, y, -dx));
+    const f2 u1 = fma2(Tz, x, fma2(-Tx, z, -dy));
+    const f2 u2 = fma2(Tx, y, fma2(-Ty, x, -dz));
+    v0[g] = fma2(ri3, u0, fma2(cs2, Sx, fma2(cx, x, fma2(c1, Fx, v0[g]))));
+    v1[g] = fma2(ri3, u1, fma2(cs2, Sy, fma2(cx, y, fma2(c1, Fy, v1[g]))));
+    v2[g] = fma2(ri3, u2, fma2(cs2, Sz, fma2(cx, z, fma2(c1, Fz, v2[g]))));
+    const f2 e0 = fma2(Fy, z, fma2(-Fz, y, hx));
+    const f2 e1 = fma2(Fz, x, fma2(-Fx, z, hy));
+    const f2 e2 = fma2(Fx, y, fma2(-Fy, x, hz));
+    const f2 ct = (f2(1.5f) * ri5) * rT;
+    const f2 tx = t3 * x, ty = t3 * y, tz = t3 * z;
+    w0[g] = fma2(ty, Sz, fma2(-tz, Sy, fma2(ct, x, fma2(ri3, e0, w0[g]))));
+    w1[g] = fma2(tz, Sx, fma2(-tx, Sz, fma2(ct, y, fma2(ri3, e1, w1[g]))));
+    w2[g] = fma2(tx, Sy, fma2(-ty, Sx, fma2(ct, z, fma2(ri3, e2, w2[g]))));
+  }
+}
+
+// FP32 pair pass with paired instructions: as trap_pairs, TI = 2 TG targets per thread.
+template <int TG, int THREADS, int TILE>
+__global__ void __launch_bounds__(THREADS, 4) trap_pairs_f2(const TrapArgs args, const float* __restrict__ rec, int chunk,
+                                                         float* __restrict__ partial) {
+  constexpr int TI = 2 * TG;
+  __shared__ __align__(16) float4 s_dup[TILE * kRec / 2];
+  const int N = args.N;
+  const int n0 = (blockIdx.x * THREADS + threadIdx.x) * TI;
+  const int m_begin = blockIdx.y * chunk;
+  const int m_end = min(N, m_begin + chunk);
+  const f2 a2(float(args.a * args.a));
+  const int blk_n0 = blockIdx.x * THREADS * TI, blk_n1 = blk_n0 + THREADS * TI;
+
+  f2 px[TG], py[TG], pz[TG], lx[TG], ly[TG], lz[TG];
+  f2 v0[TG], v1[TG], v2[TG], w0[TG], w1[TG], w2[TG];
+#pragma unroll
+  for (int g = 0; g < TG; ++g) {
+    const int na = min(n0 + 2 * g, N - 1), nb = min(n0 + 2 * g + 1, N - 1);
+    const float4 ha = args.pos.hi[na], la = args.pos.lo[na], hb = args.pos.hi[nb], lb = args.pos.lo[nb];
+    px[g] = f2(ha.x, hb.x); py[g] = f2(ha.y, hb.y); pz[g] = f2(ha.z, hb.z);
+    lx[g] = f2(la.x, lb.x); ly[g] = f2(la.y, lb.y); lz[g] = f2(la.z, lb.z);
+    v0[g] = v1[g] = v2[g] = w0[g] = w1[g] = w2[g] = f2(0.0f);
+  }
+
+  for (int base = m_begin; base < m_end; base += TILE) {
+    const int len = min(TILE, m_end - base);
+    __syncthreads();
+    {
+      const float2* src = reinterpret_cast<const float2*>(rec + (size_t)base * kRec);
+      for (int i = threadIdx.x; i < len * (kRec / 2); i += THREADS) {
+        const float2 w = src[i];
+        s_dup[i] = make_float4(w.x, w.x, w.y, w.y);
+      }
+    }
+    __syncthreads();
+    // only a tile that holds one of this block's targets can hold a thread's own sphere
+    const bool self_tile = base < blk_n1 && base + len > blk_n0;
+    if (self_tile) {
+      for (int j = 0; j < len; ++j)
+        trap_source_f2<TG, true>(s_dup, j, base + j, n0, px, py, pz, lx, ly, lz, a2, v0, v1, v2, w0, w1, w2);
+    } else {
+      for (int j = 0; j < len; ++j)
+        trap_source_f2<TG, false>(s_dup, j, base + j, n0, px, py, pz, lx, ly, lz, a2, v0, v1, v2, w0, w1, w2);
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < TI; ++t) {
+    const int n = n0 + t;
+    if (n < N) {
+      const int g = t >> 1;
+      const bool hi = t & 1;
+      float* o = partial + ((size_t)blockIdx.y * N + n) * 6;
+      o[0] = hi ? v0[g].v.y : v0[g].v.x; o[1] = hi ? v1[g].v.y : v1[g].v.x; o[2] = hi ? v2[g].v.y : v2[g].v.x;
+      o[3] = hi ? w0[g].v.y : w0[g].v.x; o[4] = hi ? w1[g].v.y : w1[g].v.x; o[5] = hi ? w2[g].v.y : w2[g].v.x;
+    }
+  }
+}
+
 // partial[split][n][6] = sum over this split's sources of the pair terms for target n
 template <typename T, int TI, int THREADS, int TILE>
 __global__ void __launch_bounds__(THREADS) trap_pairs(const TrapArgs args, const T* __restrict__ rec,
@@ -194,23 +335,32 @@ __global__ void __launch_bounds__(THREADS) trap_pairs(const TrapArgs args, const
   }
 }
 
-// V = V^a + F/(6 pi eta a) + sum_split partial, Omega likewise (fixed split order).
+// V = V^a + F/(6 pi eta a) + sum_split partial, Omega likewise (fixed split order).  One
+// thread per (sphere, component), component fastest, so the split rows are read coalesced;
+// four splits' loads are issued before their (ordered) FP64 additions.  mt = 1/(6 pi eta a),
+// mr = 1/(8 pi eta a^3).
 template <typename T>
-__global__ void trap_finish(const TrapArgs args, const T* __restrict__ partial, int nsplit) {
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= args.N) return;
-  double acc[6] = {0, 0, 0, 0, 0, 0};
-  for (int s = 0; s < nsplit; ++s) {
-    const T* p = partial + ((size_t)s * args.N + n) * 6;
-#pragma unroll
-    for (int c = 0; c < 6; ++c) acc[c] += double(p[c]);
+__global__ void trap_finish(const TrapArgs args, const T* __restrict__ partial, int nsplit, double mt, double mr) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long rows = 6LL * args.N;
+  if (i >= rows) return;
+  const long long n = i / 6;
+  const int c = (int)(i - 6 * n);
+  double acc = 0.0;
+  int s = 0;
+  for (; s + 4 <= nsplit; s += 4) {
+    const T p0 = partial[(long long)s * rows + i], p1 = partial[(long long)(s + 1) * rows + i];
+    const T p2 = partial[(long long)(s + 2) * rows + i], p3 = partial[(long long)(s + 3) * rows + i];
+    acc += double(p0);
+    acc += double(p1);
+    acc += double(p2);
+    acc += double(p3);
   }
-  const double mt = 1.0 / (6.0 * kPi * args.eta * args.a);
-  const double mr = 1.0 / (8.0 * kPi * args.eta * args.a * args.a * args.a);
-  for (int c = 0; c < 3; ++c) {
-    args.V[3 * (size_t)n + c] = args.Va[3 * (size_t)n + c] + mt * args.Fe[3 * (size_t)n + c] + acc[c];
-    args.Om[3 * (size_t)n + c] = args.Oa[3 * (size_t)n + c] + mr * args.Te[3 * (size_t)n + c] + acc[3 + c];
-  }
+  for (; s < nsplit; ++s) acc += double(partial[(long long)s * rows + i]);
+  if (c < 3)
+    args.V[3 * n + c] = args.Va[3 * n + c] + mt * args.Fe[3 * n + c] + acc;
+  else
+    args.Om[3 * n + c - 3] = args.Oa[3 * n + c - 3] + mr * args.Te[3 * n + c - 3] + acc;
 }
 
 constexpr int kTI = 4, kThreads = 128;
@@ -222,8 +372,13 @@ cudaError_t trap_launch_t(const TrapArgs& args, void* scratch, int nsplit, cudaS
   trap_pack<T><<<(args.N + 255) / 256, 256, 0, stream>>>(args, rec);
   const int chunk = (args.N + nsplit - 1) / nsplit;
   const dim3 grid((args.N + kThreads * kTI - 1) / (kThreads * kTI), nsplit);
-  trap_pairs<T, kTI, kThreads, TILE><<<grid, kThreads, 0, stream>>>(args, rec, chunk, partial);
-  trap_finish<T><<<(args.N + 255) / 256, 256, 0, stream>>>(args, partial, nsplit);
+  if constexpr (std::is_same<T, float>::value)
+    trap_pairs_f2<kTI / 2, kThreads, TILE><<<grid, kThreads, 0, stream>>>(args, rec, chunk, partial);
+  else
+    trap_pairs<T, kTI, kThreads, TILE><<<grid, kThreads, 0, stream>>>(args, rec, chunk, partial);
+  const double mt = 1.0 / (6.0 * kPi * args.eta * args.a);
+  const double mr = 1.0 / (8.0 * kPi * args.eta * args.a * args.a * args.a);
+  trap_finish<T><<<(int)((6LL * args.N + 255) / 256), 256, 0, stream>>>(args, partial, nsplit, mt, mr);
   return cudaGetLastError();
 }
 
@@ -236,10 +391,30 @@ double trap_flops() {
   return 9 + 5 + 1 + 4 + 14 + 15 + 5 + 5 + 5 + 8 + 48 + 49;
 }
 
-int trap_splits(int N) {
-  // about four blocks per SM on 152 SMs, at least 64 sources per split
+// Blocks of the pair kernel resident at once on this device (SMs x blocks per SM at its
+// registers and shared memory), per precision; taken once per process.
+static int trap_resident(int precision) {
+  static int cached[2] = {0, 0};
+  int& c = cached[precision == 1 ? 1 : 0];
+  if (c == 0) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (precision == 1)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, trap_pairs_f2<kTI / 2, kThreads, 128>, kThreads, 0);
+    else
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, trap_pairs<double, kTI, kThreads, 64>, kThreads, 0);
+    c = sms * per > 0 ? sms * per : 608;
+  }
+  return c;
+}
+
+int trap_splits(int N, int precision) {
+  // as many source splits as keep every target block's splits within one wave of the
+  // resident blocks (a wave and a few stragglers costs a second wave), at least 64
+  // sources per split
   const int tblocks = (N + kThreads * kTI - 1) / (kThreads * kTI);
-  int s = (608 + tblocks - 1) / tblocks;
+  int s = trap_resident(precision) / tblocks;
   const int maxs = (N + 63) / 64;
   if (s > maxs) s = maxs;
   return s < 1 ? 1 : s;
@@ -247,13 +422,13 @@ int trap_splits(int N) {
 
 size_t trap_scratch_bytes(int N, int precision) {
   const size_t w = precision == 1 ? sizeof(float) : sizeof(double);
-  return w * ((size_t)N * kRec + (size_t)trap_splits(N) * N * 6) + 256;
+  return w * ((size_t)N * kRec + (size_t)trap_splits(N, precision) * N * 6) + 256;
 }
 
 // Three launches: record packing, pair sums per split, fixed-order reduction.
 cudaError_t launch_trap(const TrapArgs& args, int precision, void* scratch, cudaStream_t stream) {
   if (args.N <= 0) return cudaSuccess;
-  const int ns = trap_splits(args.N);
+  const int ns = trap_splits(args.N, precision);
   if (precision == 1) return trap_launch_t<float, 128>(args, scratch, ns, stream);
   return trap_launch_t<double, 64>(args, scratch, ns, stream);
 }
