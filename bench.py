@@ -915,7 +915,7 @@ def run_ours(args):
     ach3 = s3["flops"] / (s3["ms"] * 1e-3) / 1e12
     superposition = {"workload": c3["name"], "N": N3, "value": n3 * N3 * (N3 - 1) / t3, "unit": UNIT,
                      "ms_per_pass": 1e3 * t3 / n3,
-                     "roofline": {"bound": "alu", "kernel": "trap superposition pass (pack + trap_pairs<float> + finish)",
+                     "roofline": {"bound": "alu", "kernel": "trap superposition pass (pack + trap_pairs_f2 + finish)",
                                   "achieved": ach3, "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach3 / fp32_peak,
                                   "traffic": None, "avg_launch_ms": s3["ms"] / max(1, s3["launches"])},
                      "note": "inputs resident (L2-sized), not flushed"}

@@ -337,7 +337,7 @@ __global__ void __launch_bounds__(THREADS) trap_pairs(const TrapArgs args, const
 
 // V = V^a + F/(6 pi eta a) + sum_split partial, Omega likewise (fixed split order).  One
 // thread per (sphere, component), component fastest, so the split rows are read coalesced;
-// four splits' loads are issued before their (ordered) FP64 additions.  mt = 1/(6 pi eta a),
+// eight splits' loads are issued before their (ordered) FP64 additions.  mt = 1/(6 pi eta a),
 // mr = 1/(8 pi eta a^3).
 template <typename T>
 __global__ void trap_finish(const TrapArgs args, const T* __restrict__ partial, int nsplit, double mt, double mr) {
@@ -348,15 +348,21 @@ __global__ void trap_finish(const TrapArgs args, const T* __restrict__ partial, 
   const int c = (int)(i - 6 * n);
   double acc = 0.0;
   int s = 0;
-  for (; s + 4 <= nsplit; s += 4) {
-    const T p0 = partial[(long long)s * rows + i], p1 = partial[(long long)(s + 1) * rows + i];
-    const T p2 = partial[(long long)(s + 2) * rows + i], p3 = partial[(long long)(s + 3) * rows + i];
-    acc += double(p0);
-    acc += double(p1);
-    acc += double(p2);
-    acc += double(p3);
+  for (; s + 8 <= nsplit; s += 8) {
+    T p[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) p[u] = partial[(long long)(s + u) * rows + i];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc += double(p[u]);
   }
-  for (; s < nsplit; ++s) acc += double(partial[(long long)s * rows + i]);
+  if (s < nsplit) {
+    T p[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) p[u] = s + u < nsplit ? partial[(long long)(s + u) * rows + i] : T(0);
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (s + u < nsplit) acc += double(p[u]);
+  }
   if (c < 3)
     args.V[3 * n + c] = args.Va[3 * n + c] + mt * args.Fe[3 * n + c] + acc;
   else
