@@ -192,6 +192,38 @@ def test_trap_superposition_full_size_sampled(ctx, gbi):
     assert np.abs(Omg - Omr).max() / np.linalg.norm(Omr, axis=1).max() < FP32_TOL
 
 
+_SUP_CASES = {}
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("N", [1, 2, 7, 1100])
+def test_trap_superposition_block_edges(ctx, gbi, N, precision):
+    """Closed-form superposition at sizes that exercise the kernel's partitioning: N = 1 (no
+    pairs), tiny N (every source tile holds a target's own sphere), and N = 1100 (three
+    512-target blocks, the last ragged, sources split into 64-sphere chunks, so both tiles
+    with and without a target's own sphere occur).  Targets at the block edges and in both
+    halves of a thread's target pairs, against the oracle's pair sum."""
+    if N not in _SUP_CASES:
+        R, p, s = cloud(N, 6) if N > 1 else (np.zeros((1, 3)), np.array([[0.0, 0.0, 1.0]]), cloud(2, 6)[2])
+        prm_o = dict(a=s["a"], eta=s["eta"], k=s["k"], vs=s["vs"], s0=s["s0"], d0=0.03)
+        inp = dynamics.trap_inputs(R, p, prm_o, 2)
+        inp["Te"] = np.random.default_rng(11).normal(size=(N, 3)) * 0.01
+        tgt = np.arange(N) if N < 64 else np.array([0, 1, 2, 3, 510, 511, 512, 513, 1022, 1023, 1024, 1025, 1098, 1099])
+        Vr, Omr = galerkin.superpose(R, inp["Va"], inp["Oa"], inp["VH"], inp["Fe"], inp["Te"], s["a"], s["eta"], 2,
+                                     targets=tgt)
+        _SUP_CASES[N] = (R, s, inp, tgt, Vr, Omr)
+    R, s, inp, tgt, Vr, Omr = _SUP_CASES[N]
+    prm = gbi.params(a=s["a"], eta=s["eta"], trunc=2, precision=precision)
+    t = {k: dev(v) for k, v in inp.items()}
+    V, Om = ctx.superpose(prm, dev(R), t["Va"], t["Oa"], t["VH"], t["Fe"], t["Te"])
+    torch.cuda.synchronize()
+    Vg, Omg = V.cpu().numpy()[tgt], Om.cpu().numpy()[tgt]
+    tol = FP64_TOL if precision == 0 else FP32_TOL
+    assert np.all(np.isfinite(Vg)) and np.all(np.isfinite(Omg))
+    assert np.abs(Vg - Vr).max() / np.linalg.norm(Vr, axis=1).max() < tol
+    assert np.abs(Omg - Omr).max() / np.linalg.norm(Omr, axis=1).max() < tol
+
+
 # ------------------------------------------------------------------ full solve
 
 def _solve_case(gbi, ctx, R, p, s, trunc, precision, d0=0.02, Te_scale=0.01, rtol=1e-10):
