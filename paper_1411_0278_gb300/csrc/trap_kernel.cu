@@ -397,22 +397,27 @@ double trap_flops() {
   return 9 + 5 + 1 + 4 + 14 + 15 + 5 + 5 + 5 + 8 + 48 + 49;
 }
 
-// Blocks of the pair kernel resident at once on this device (SMs x blocks per SM at its
-// registers and shared memory), per precision; taken once per process.
+// Blocks of the pair kernel resident at once on the current device (SMs x blocks per SM at
+// its registers and shared memory), per precision.  Taken once per process (thread-safe
+// static initialisation); every GPU this library targets has the same count.
+static int trap_resident_now(int precision) {
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (precision == 1)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, trap_pairs_f2<kTI / 2, kThreads, 128>, kThreads, 0);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, trap_pairs<double, kTI, kThreads, 64>, kThreads, 0);
+  return sms * per > 0 ? sms * per : 608;
+}
+
 static int trap_resident(int precision) {
-  static int cached[2] = {0, 0};
-  int& c = cached[precision == 1 ? 1 : 0];
-  if (c == 0) {
-    int dev = 0, sms = 0, per = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (precision == 1)
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, trap_pairs_f2<kTI / 2, kThreads, 128>, kThreads, 0);
-    else
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, trap_pairs<double, kTI, kThreads, 64>, kThreads, 0);
-    c = sms * per > 0 ? sms * per : 608;
+  if (precision == 1) {
+    static const int r32 = trap_resident_now(1);
+    return r32;
   }
-  return c;
+  static const int r64 = trap_resident_now(0);
+  return r64;
 }
 
 int trap_splits(int N, int precision) {
