@@ -220,8 +220,9 @@ __device__ __forceinline__ void trap_source_f2(const float4* __restrict__ s_dup,
 }
 
 // FP32 pair pass with paired instructions: as trap_pairs, TI = 2 TG targets per thread.
+constexpr int kMinBlocks32 = 4;   // resident blocks per SM the FP32 pass is compiled for
 template <int TG, int THREADS, int TILE>
-__global__ void __launch_bounds__(THREADS, 4) trap_pairs_f2(const TrapArgs args, const float* __restrict__ rec, int chunk,
+__global__ void __launch_bounds__(THREADS, kMinBlocks32) trap_pairs_f2(const TrapArgs args, const float* __restrict__ rec, int chunk,
                                                          float* __restrict__ partial) {
   constexpr int TI = 2 * TG;
   __shared__ __align__(16) float4 s_dup[TILE * kRec / 2];
@@ -369,7 +370,9 @@ __global__ void trap_finish(const TrapArgs args, const T* __restrict__ partial, 
     args.Om[3 * n + c - 3] = args.Oa[3 * n + c - 3] + mr * args.Te[3 * n + c - 3] + acc;
 }
 
-constexpr int kTI = 4, kThreads = 128;
+// targets per thread: FP32 in kTG32 pairs, FP64 kTI64 one at a time
+constexpr int kTG32 = 2, kTI64 = 4, kThreads = 128;
+constexpr int trap_ti(int precision) { return precision == 1 ? 2 * kTG32 : kTI64; }
 
 template <typename T, int TILE>
 cudaError_t trap_launch_t(const TrapArgs& args, void* scratch, int nsplit, cudaStream_t stream) {
@@ -377,11 +380,12 @@ cudaError_t trap_launch_t(const TrapArgs& args, void* scratch, int nsplit, cudaS
   T* partial = rec + (size_t)args.N * kRec;
   trap_pack<T><<<(args.N + 255) / 256, 256, 0, stream>>>(args, rec);
   const int chunk = (args.N + nsplit - 1) / nsplit;
-  const dim3 grid((args.N + kThreads * kTI - 1) / (kThreads * kTI), nsplit);
+  constexpr int TI = trap_ti(std::is_same<T, float>::value ? 1 : 0);
+  const dim3 grid((args.N + kThreads * TI - 1) / (kThreads * TI), nsplit);
   if constexpr (std::is_same<T, float>::value)
-    trap_pairs_f2<kTI / 2, kThreads, TILE><<<grid, kThreads, 0, stream>>>(args, rec, chunk, partial);
+    trap_pairs_f2<kTG32, kThreads, TILE><<<grid, kThreads, 0, stream>>>(args, rec, chunk, partial);
   else
-    trap_pairs<T, kTI, kThreads, TILE><<<grid, kThreads, 0, stream>>>(args, rec, chunk, partial);
+    trap_pairs<T, kTI64, kThreads, TILE><<<grid, kThreads, 0, stream>>>(args, rec, chunk, partial);
   const double mt = 1.0 / (6.0 * kPi * args.eta * args.a);
   const double mr = 1.0 / (8.0 * kPi * args.eta * args.a * args.a * args.a);
   trap_finish<T><<<(int)((6LL * args.N + 255) / 256), 256, 0, stream>>>(args, partial, nsplit, mt, mr);
@@ -405,9 +409,9 @@ static int trap_resident_now(int precision) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (precision == 1)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, trap_pairs_f2<kTI / 2, kThreads, 128>, kThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, trap_pairs_f2<kTG32, kThreads, 128>, kThreads, 0);
   else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, trap_pairs<double, kTI, kThreads, 64>, kThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, trap_pairs<double, kTI64, kThreads, 64>, kThreads, 0);
   return sms * per > 0 ? sms * per : 608;
 }
 
@@ -424,7 +428,8 @@ int trap_splits(int N, int precision) {
   // as many source splits as keep every target block's splits within one wave of the
   // resident blocks (a wave and a few stragglers costs a second wave), at least 64
   // sources per split
-  const int tblocks = (N + kThreads * kTI - 1) / (kThreads * kTI);
+  const int ti = trap_ti(precision);
+  const int tblocks = (N + kThreads * ti - 1) / (kThreads * ti);
   int s = trap_resident(precision) / tblocks;
   const int maxs = (N + 63) / 64;
   if (s > maxs) s = maxs;
